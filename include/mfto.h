@@ -1,0 +1,225 @@
+/*
+ * mfto -- matrix-free 3D SIMP topology optimisation on one GB300 (sm_103a).
+ *
+ * C ABI of the library libmfto.so.  Plain pointers and sizes only.
+ *
+ * Method (arXiv 2604.18020, "Matrix-Free 3D SIMP Topology Optimization with
+ * Fused Gather-GEMM-Scatter Kernels"):
+ *   minimise f^T u  s.t.  K(rho) u = f,  mean(rho) = V_f          (Eq. tomin)
+ *   K(rho) = sum_e B_e^T E(rho_phys_e) KE B_e                       (Eq. simp)
+ *   E(r)   = Emin + (E0 - Emin) r^p
+ * with KE the 24x24 unit-modulus stiffness of a trilinear 8-node hexahedron on
+ * a structured nelx x nely x nelz grid, K.v applied matrix-free
+ * (Eq. matfree, Sec. 3.2-3.3), Jacobi-PCG (Sec. 3.6), cone density filter,
+ * analytic sensitivities and OC bisection (Sec. 3.1).
+ *
+ * Conventions (the paper fixes none of them):
+ *   element e = i + nelx*(j + nely*k), i fastest; element edge h (mfto_mesh.h);
+ *   node    n = i + (nelx+1)*(j + (nely+1)*k);  DOF = 3*n + c, c = x, y, z;
+ *   local node l = a + 2b + 4c for the element corner (i+a, j+b, k+c),
+ *   local DOF 3*l + c (the row/column order of mfto_unit_ke);
+ *   element fields (rho, E, dc) are [nelz][nely][nelx]; DOF vectors are
+ *   [nelz+1][nely+1][nelx+1][3] (node-major, components interleaved).
+ *   Fixed DOFs are given by a per-node uint8 mask, bit c set when DOF c is
+ *   clamped.  The operator is the masked K:  (Kv)_free = (K P v)_free with P
+ *   zeroing fixed DOFs, and (Kv)_fixed = v_fixed; so it is SPD and its Jacobi
+ *   diagonal is 1 on fixed DOFs.  Loads f must be zero on fixed DOFs.
+ *
+ * Memory and streams: every array argument named d_* is a DEVICE pointer
+ * owned by the caller (the library never frees it); h_* is a HOST pointer.
+ * All device work is enqueued on the stream given at mfto_create; calls that
+ * return host scalars synchronise that stream before returning.  The library
+ * allocates device memory only in mfto_create (its own workspace, freed by
+ * mfto_destroy).  Arguments must not alias unless a function says so.
+ *
+ * Errors: every function returns an mfto_status; nothing is thrown across the
+ * ABI.  On an error the handle's message is available from mfto_last_error.
+ * A CUDA error inside a call is reported as MFTO_CUDA_ERROR and leaves the
+ * handle usable only if the CUDA context is.
+ */
+#ifndef MFTO_H
+#define MFTO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mfto_status;
+enum {
+  MFTO_OK = 0,
+  MFTO_INVALID_ARG = 1,     /* null pointer, bad size or unknown enum     */
+  MFTO_CUDA_ERROR = 2,      /* a CUDA runtime call or launch failed       */
+  MFTO_OOM = 3,             /* cudaMalloc of the workspace failed         */
+  MFTO_NOT_CONVERGED = 4,   /* iteration cap reached before the tolerance */
+  MFTO_STALLED = 5,         /* residual stopped decreasing (IR / FPCG)    */
+  MFTO_BREAKDOWN = 6,       /* NaN/Inf or non-positive curvature in CG    */
+  MFTO_UNSUPPORTED = 7      /* form or feature not available             */
+};
+
+/* Arithmetic forms of the K.v contraction. */
+typedef enum {
+  MFTO_FORM_F64 = 0,        /* FP64 data, FP64 arithmetic                 */
+  MFTO_FORM_F32 = 1         /* FP32 data, FP32 arithmetic                 */
+} mfto_form;
+
+typedef struct {
+  int32_t nelx, nely, nelz; /* elements per axis, each >= 1               */
+  double h;                 /* element edge length (> 0)                  */
+} mfto_mesh;
+
+typedef struct {
+  double E0;                /* solid modulus                              */
+  double Emin;              /* void modulus (Eq. simp: rho_min)           */
+  double nu;                /* Poisson ratio, in (-1, 0.5)                */
+  double penal;             /* SIMP penalty p                             */
+  double rmin;              /* cone filter radius (elements), > 0         */
+  double volfrac;           /* target mean design density V_f             */
+  double move;              /* OC move limit m                            */
+  double rtol;              /* PCG stop: ||r|| <= rtol ||f||              */
+  int32_t maxit;            /* PCG iteration cap                          */
+  int32_t check_every;      /* PCG: host polls convergence every k iters  */
+} mfto_params;
+
+typedef struct {
+  int32_t iterations;       /* CG iterations performed                    */
+  int32_t status;           /* MFTO_OK, MFTO_NOT_CONVERGED, MFTO_BREAKDOWN */
+  double rel_residual;      /* recursive ||r|| / ||f|| at exit            */
+  double fnorm;             /* ||f||                                      */
+} mfto_solve_stats;
+
+typedef struct {
+  double compliance;        /* c = sum_e E_e u_e^T KE u_e                 */
+  double change;            /* max |rho_new - rho|                        */
+  double volume;            /* mean(rho_new)                              */
+  double grayness;          /* (4/n) sum rho_phys (1 - rho_phys)          */
+  double lambda;            /* OC multiplier at exit of the bisection     */
+  int32_t cg_iterations;
+  int32_t cg_status;
+  double rel_residual;
+} mfto_iter_stats;
+
+typedef struct mfto_handle mfto_handle;
+
+/* Library version string (static storage). */
+const char* mfto_version(void);
+
+/* Default parameters: E0=1, Emin=1e-9, nu=0.3, p=3, rmin=1.5, V_f=0.3,
+ * move=0.2, rtol=1e-8, maxit=10000, check_every=32. */
+void mfto_default_params(mfto_params* p);
+
+/* ---------------------------------------------------------------- host -- */
+
+/* Unit element stiffness KE (24x24, row-major, local DOF order above) of the
+ * trilinear hexahedron with edge h, modulus E0 and Poisson ratio nu, from the
+ * exact integrals of the linear shape functions (Sec. 3.1: KE is the
+ * unit-modulus element matrix of Eq. simp).  h_ke_out: 576 doubles. */
+mfto_status mfto_unit_ke(double E0, double nu, double h, double* h_ke_out);
+
+/* The element -> DOF table of Sec. 3.2 (edof), [n_elem][24] int32, host.
+ * The device kernels never read it (they compute DOFs from (i, j, k)); it is
+ * exported so the indexing can be checked exactly. */
+mfto_status mfto_edof(const mfto_mesh* mesh, int32_t* h_edof_out);
+
+/* Cone-filter stencil (Sec. 3.1): every offset (dx, dy, dz) with
+ * |d|_inf <= ceil(rmin) - 1 and weight w = rmin - |d| > 0, in dz, dy, dx
+ * ascending order (dx fastest).  h_offsets: 3*cap int32; h_weights: cap
+ * doubles; *count receives the number of offsets (<= cap or
+ * MFTO_INVALID_ARG). */
+mfto_status mfto_filter_stencil(double rmin, int32_t cap, int32_t* h_offsets,
+                                double* h_weights, int32_t* count);
+
+/* -------------------------------------------------------------- handle -- */
+
+/* Create a handle for one mesh.  h_fixed: per-node uint8 mask
+ * ([n_node], copied to the device).  stream: a cudaStream_t (0 = legacy
+ * default stream) on which every later call enqueues its work.  Allocates the
+ * device workspace (PCG vectors and reduction buffers, about 12 FP64 DOF
+ * vectors); returns MFTO_OOM if that fails. */
+mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* params,
+                        const uint8_t* h_fixed, void* stream,
+                        mfto_handle** out);
+mfto_status mfto_destroy(mfto_handle* h);
+/* Replace the parameters (mesh and fixed set stay). */
+mfto_status mfto_set_params(mfto_handle* h, const mfto_params* params);
+/* Message of the last failing call on this handle (static per handle). */
+const char* mfto_last_error(const mfto_handle* h);
+/* Sizes of the mesh: elements, nodes, DOFs. */
+mfto_status mfto_sizes(const mfto_handle* h, int64_t* n_elem, int64_t* n_node,
+                       int64_t* n_dof);
+
+/* -------------------------------------------------------- device steps -- */
+
+/* SIMP modulus (Eq. simp): d_E[e] = Emin + (E0 - Emin) d_rho_phys[e]^p.
+ * FP64 in, FP64 out (form F64) or FP64 in, FP32 out (form F32). */
+mfto_status mfto_simp_modulus(mfto_handle* h, mfto_form form,
+                              const double* d_rho_phys, void* d_E);
+
+/* Masked matrix-free K.v (Eq. matfree; Alg. 1 computes the same sum):
+ * d_y = K(E) d_v.  d_E, d_v, d_y are in the form's type (double for F64,
+ * float for F32).  d_y must not alias d_v. */
+mfto_status mfto_kv(mfto_handle* h, mfto_form form, const void* d_E,
+                    const void* d_v, void* d_y);
+
+/* Jacobi diagonal of the masked K (Sec. 3.6), one element pass:
+ * d_diag[k] = sum_{e owning k} E_e KE[l, l], 1 on fixed DOFs. */
+mfto_status mfto_jacobi_diag(mfto_handle* h, mfto_form form, const void* d_E,
+                             void* d_diag);
+
+/* Jacobi-PCG in FP64 (Sec. 3.6) on K(E) u = f with warm start: d_u holds the
+ * initial guess on entry and the solution on exit.  Stops at
+ * ||r|| <= rtol ||f|| (recursive residual) or maxit.  Returns MFTO_OK also
+ * when the cap is hit; the outcome is in st->status. */
+mfto_status mfto_pcg(mfto_handle* h, const double* d_E, const double* d_f,
+                     double* d_u, mfto_solve_stats* st);
+
+/* Cone density filter (Sec. 3.1): transpose = 0 gives
+ * d_y = (H d_x) / W;  transpose = 1 gives d_y = H (d_x / W)
+ * (the chain rule for sensitivities).  FP64, element fields. */
+mfto_status mfto_filter(mfto_handle* h, const double* d_x, double* d_y,
+                        int32_t transpose);
+
+/* Compliance and sensitivity (Sec. 3.1): ce_e = u_e^T KE u_e,
+ * *c_out = sum_e E_e ce_e (FP64, fixed reduction order),
+ * d_dc[e] = -p rho_phys_e^(p-1) (E0 - Emin) ce_e  (derivative with respect
+ * to rho_phys; chain through mfto_filter(transpose=1) for the design field).
+ * d_dc may be NULL.  Synchronises the stream. */
+mfto_status mfto_compliance_sens(mfto_handle* h, const double* d_rho_phys,
+                                 const double* d_u, double* c_out,
+                                 double* d_dc);
+
+/* OC update with bisection on the volume multiplier (Sec. 3.1):
+ * B_e = max(0, -dc_e) / (lambda / n); candidate rho sqrt(B_e) clipped to
+ * [max(0, rho - m), min(1, rho + m)]; lambda bisected on [0, 1e9] while
+ * sum(rho_new) > V_f n raises the lower end, until
+ * (l2 - l1)/(l1 + l2) <= 1e-10.  d_rho_new receives the candidate of the
+ * last midpoint.  Synchronises the stream; st may be NULL. */
+mfto_status mfto_oc_update(mfto_handle* h, const double* d_rho,
+                           const double* d_dc, double* d_rho_new,
+                           mfto_iter_stats* st);
+
+/* One SIMP iteration (the loop of Sec. 3.1 / 3.7): rho_phys = filter(rho);
+ * E = E(rho_phys); Jacobi-PCG on K(E) u = f warm-started from d_u;
+ * compliance and sensitivities; filter transpose; OC.  d_rho is updated in
+ * place, d_u holds the new displacement, d_rho_phys (may be NULL) receives
+ * the filtered field used in this iteration. */
+mfto_status mfto_simp_step(mfto_handle* h, double* d_rho, double* d_u,
+                           const double* d_f, double* d_rho_phys,
+                           mfto_iter_stats* st);
+
+/* ------------------------------------------------------------- timing -- */
+
+/* When on, every K.v launch issued by the library on this handle is
+ * bracketed by CUDA events on the handle's stream; mfto_kv_timing_read
+ * synchronises and returns the number of timed launches and their summed
+ * device time in milliseconds, then resets the accumulators. */
+mfto_status mfto_kv_timing(mfto_handle* h, int32_t on);
+mfto_status mfto_kv_timing_read(mfto_handle* h, int64_t* launches,
+                                double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFTO_H */

@@ -1,0 +1,243 @@
+// Internal definitions shared by the library's translation units: the handle,
+// error plumbing, deterministic block reductions and a bounded grid barrier.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mfto.h"
+
+#define MFTO_BLOCK 256            // threads per block of the element/node kernels
+#define MFTO_RED_MAX_BLOCKS 1024  // partial-sum slots of one grid reduction
+
+// Device-resident scalars of the PCG driver and the other reductions.  Each
+// reduction site owns a ticket counter (reset by the last block).
+struct PcgScalars {
+  double rz;        // r.z of the current iterate
+  double pq;        // p.q
+  double alpha, beta;
+  double rr;        // r.r
+  double ff;        // f.f
+  double rtol2ff;   // rtol^2 * f.f
+  int32_t it, maxit, done, status;
+  unsigned int ticket_a, ticket_b, ticket_c;
+};
+
+struct MiscScalars {
+  double sum[4];            // results of small reductions
+  double lambda, change, volume;
+  int32_t oc_steps;
+  int32_t error;            // set by device code that gave up on a wait
+  unsigned int ticket;
+  unsigned int bar_count, bar_gen;
+};
+
+struct KvEventPool {
+  std::vector<cudaEvent_t> start, stop;
+  int used = 0;
+  int64_t launches = 0;
+  double total_ms = 0.0;
+};
+
+struct mfto_handle {
+  mfto_mesh mesh;
+  mfto_params p;
+  int64_t n_elem, n_node, n_dof;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;  // private stream used only to capture CUDA graphs
+  int num_sms;
+  // device copies of the unit element matrix (row-major 24x24)
+  double* d_ke64;
+  float* d_ke32;
+  double ke_diag;           // KE[l][l] (equal for every local DOF on a cube)
+  uint8_t* d_fixed;         // per-node mask
+  // cone filter
+  int32_t n_stencil;
+  int32_t* d_stencil_off;   // [3 * n_stencil]
+  double* d_stencil_w;      // [n_stencil]
+  double* d_filter_W;       // row sums W_e
+  // PCG workspace (FP64)
+  double *d_r, *d_z, *d_p0, *d_p1, *d_q, *d_dinv;
+  double* d_partials;       // [4 * MFTO_RED_MAX_BLOCKS]
+  double* d_partials2;      // [4 * MFTO_RED_MAX_BLOCKS]
+  PcgScalars* d_pcg;
+  MiscScalars* d_misc;
+  PcgScalars* h_pcg;        // pinned mirror
+  MiscScalars* h_misc;      // pinned mirror
+  // SIMP step workspace
+  double *d_rho_phys, *d_E, *d_dc, *d_dc_phys;
+  // PCG graph cache (one captured chunk of check_every iterations)
+  struct PcgGraph* pcg_graph;
+  // timing
+  bool kv_timing;
+  KvEventPool ev;
+  char msg[512];
+};
+
+// --------------------------------------------------------------- errors
+mfto_status mfto_fail(mfto_handle* h, mfto_status code, const char* fmt, ...);
+
+#define MFTO_CUDA(h, call)                                                   \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      return mfto_fail((h), MFTO_CUDA_ERROR, "%s: %s (%s:%d)", #call,        \
+                       cudaGetErrorString(e_), __FILE__, __LINE__);          \
+  } while (0)
+
+#define MFTO_LAUNCH_CHECK(h) MFTO_CUDA(h, cudaGetLastError())
+
+#define MFTO_REQUIRE(h, cond, msg)                                           \
+  do {                                                                       \
+    if (!(cond)) return mfto_fail((h), MFTO_INVALID_ARG, "%s", msg);        \
+  } while (0)
+
+// --------------------------------------------------------- index helpers
+struct Grid {
+  int nelx, nely, nelz;   // elements
+  int nx, ny, nz;         // nodes per axis (nel + 1)
+};
+
+static inline Grid make_grid(const mfto_mesh& m) {
+  Grid g;
+  g.nelx = m.nelx; g.nely = m.nely; g.nelz = m.nelz;
+  g.nx = m.nelx + 1; g.ny = m.nely + 1; g.nz = m.nelz + 1;
+  return g;
+}
+
+static inline int reduction_blocks(int64_t n, int block) {
+  int64_t b = (n + block - 1) / block;
+  if (b > MFTO_RED_MAX_BLOCKS) b = MFTO_RED_MAX_BLOCKS;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ----------------------------------------------------- device reductions
+// Sum of one double over the block in a fixed order (warp shuffles, then
+// warp 0 over the per-warp sums).  The result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (warp == 0) {
+    v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (warp == 0) {
+    v = lane < nw ? sh[lane] : -1.0e300;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// Publish K per-block partial sums and let the last block to arrive reduce
+// them in block-index order.  Returns true in every thread of that last
+// block, with out[0..K) holding the totals (valid in all its threads).
+template <int K>
+__device__ __forceinline__ bool last_block_reduce(const double (&v)[K],
+                                                  double* partials,
+                                                  unsigned int* ticket,
+                                                  double* out, double* sh) {
+  // partials: K rows of MFTO_RED_MAX_BLOCKS slots; gridDim.x must not exceed
+  // MFTO_RED_MAX_BLOCKS (callers use grid-stride loops).
+  __shared__ bool s_last;
+  double bs[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) bs[c] = block_sum(v[c], sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) partials[c * MFTO_RED_MAX_BLOCKS + blockIdx.x] = bs[c];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s += __ldcg(&partials[c * MFTO_RED_MAX_BLOCKS + b]);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) sh[32 + c] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < K; ++c) out[c] = sh[32 + c];
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// Grid-wide barrier for a cooperative launch.  Every wait is bounded: after
+// MFTO_SPIN_LIMIT polls the block sets *error and stops waiting; once *error
+// is set no later barrier waits at all, so the kernel always terminates.
+#define MFTO_SPIN_LIMIT (1u << 24)
+__device__ __forceinline__ void grid_barrier(unsigned int* count,
+                                             unsigned int* gen,
+                                             int32_t* error) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = gen;
+    volatile int32_t* verr = error;
+    const unsigned int g = *vgen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      *count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned int spins = 0;
+      while (*vgen == g) {
+        if (*verr) break;
+        if (++spins > MFTO_SPIN_LIMIT) { atomicExch(error, 1); break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------ host-side entries
+// (defined in the .cu files, used across them)
+mfto_status kv_launch(mfto_handle* h, mfto_form form, const void* E,
+                      const void* v, void* y);
+mfto_status diag_launch(mfto_handle* h, mfto_form form, const void* E,
+                        void* diag, bool inverse);
+mfto_status modulus_launch(mfto_handle* h, mfto_form form,
+                           const double* rho_phys, void* E);
+mfto_status filter_launch(mfto_handle* h, const double* x, double* y,
+                          int transpose);
+mfto_status compliance_launch(mfto_handle* h, const double* rho_phys,
+                              const double* u, double* dc, double* c_out,
+                              double* gray_out);
+mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc,
+                      double* rho_new, mfto_iter_stats* st);
+mfto_status pcg_run(mfto_handle* h, const double* E, const double* f,
+                    double* u, mfto_solve_stats* st);
+void pcg_graph_release(mfto_handle* h);
+void kv_timing_begin(mfto_handle* h);
+void kv_timing_end(mfto_handle* h);
+mfto_status kv_timing_harvest(mfto_handle* h, bool sync);

@@ -1,0 +1,206 @@
+// Compliance and sensitivities, the OC bisection update and one SIMP
+// iteration (Sec. 3.1, Sec. 3.6 warm start).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+// ce_e = u_e^T KE u_e;  c = sum_e E_e ce_e;  dc_e = -p rho^(p-1) (E0-Emin) ce_e;
+// grayness sum 4 rho (1 - rho).  One thread per element, fixed-order sums.
+__global__ void __launch_bounds__(MFTO_BLOCK)
+compliance_kernel(const double* __restrict__ rho, const double* __restrict__ u,
+                  double* __restrict__ dc, const double* __restrict__ ke_g, Grid g,
+                  double E0, double Emin, double penal, MiscScalars* s, double* partials) {
+  __shared__ double ke[576];
+  __shared__ double sh[64];
+  for (int t = threadIdx.x; t < 576; t += blockDim.x) ke[t] = ke_g[t];
+  __syncthreads();
+  const int n = g.nelx * g.nely * g.nelz;
+  double acc[2] = {0.0, 0.0};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int i = e % g.nelx, j = (e / g.nelx) % g.nely, k = e / (g.nelx * g.nely);
+    double ue[24];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int m = (i + (l & 1)) + g.nx * ((j + ((l >> 1) & 1)) + g.ny * (k + (l >> 2)));
+      ue[3 * l + 0] = u[3 * m + 0];
+      ue[3 * l + 1] = u[3 * m + 1];
+      ue[3 * l + 2] = u[3 * m + 2];
+    }
+    double ce = 0.0;
+#pragma unroll 4
+    for (int a = 0; a < 24; ++a) {
+      double row = 0.0;
+#pragma unroll
+      for (int b = 0; b < 24; ++b) row += ke[a * 24 + b] * ue[b];
+      ce += ue[a] * row;
+    }
+    const double r = rho[e];
+    const double E = Emin + (E0 - Emin) * pow(r, penal);
+    acc[0] += E * ce;
+    acc[1] += 4.0 * r * (1.0 - r);
+    if (dc) dc[e] = -penal * pow(r, penal - 1.0) * (E0 - Emin) * ce;
+  }
+  double tot[2];
+  if (last_block_reduce<2>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0) {
+    s->sum[0] = tot[0];
+    s->sum[1] = tot[1];
+  }
+}
+
+// OC with bisection on lambda.  One cooperative grid; each bisection step
+// sums the candidate field, crosses a bounded grid barrier and lets every
+// block reduce the per-block partials in the same order, so every block takes
+// the same branch.  Partials are double-buffered by step parity.
+__global__ void __launch_bounds__(MFTO_BLOCK)
+oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
+          double* __restrict__ rho_new, int n, double volfrac, double move,
+          MiscScalars* s, double* partials) {
+  __shared__ double sh[64];
+  const double dv = 1.0 / (double)n;
+  const double target = volfrac * (double)n;
+  double l1 = 0.0, l2 = 1e9, total = 0.0;
+  int step = 0;
+  while ((l2 - l1) / (l1 + l2) > 1e-10) {
+    const double lmid = 0.5 * (l1 + l2);
+    double acc = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+      const double r = rho[e];
+      const double neg = fmax(0.0, -dc[e]);
+      const double cand = r * sqrt(neg / (lmid * dv));
+      const double lo = fmax(0.0, r - move), hi = fmin(1.0, r + move);
+      const double rn = fmax(lo, fmin(hi, cand));
+      rho_new[e] = rn;
+      acc += rn;
+    }
+    double* buf = partials + (step & 1) * MFTO_RED_MAX_BLOCKS;
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) buf[blockIdx.x] = bs;
+    grid_barrier(&s->bar_count, &s->bar_gen, &s->error);
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&buf[b]);
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) sh[40] = t;
+    __syncthreads();
+    total = sh[40];
+    if (total > target) l1 = lmid; else l2 = lmid;
+    ++step;
+    if (*(volatile int32_t*)&s->error) break;
+  }
+  // change = max |rho_new - rho|
+  double mx = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs(rho_new[e] - rho[e]));
+  double* buf = partials + 2 * MFTO_RED_MAX_BLOCKS;
+  const double bm = block_max(mx, sh);
+  if (threadIdx.x == 0) buf[blockIdx.x] = bm;
+  grid_barrier(&s->bar_count, &s->bar_gen, &s->error);
+  if (blockIdx.x == 0) {
+    double m2 = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m2 = fmax(m2, __ldcg(&buf[b]));
+    m2 = block_max(m2, sh);
+    if (threadIdx.x == 0) {
+      s->change = m2;
+      s->volume = total / (double)n;
+      s->lambda = 0.5 * (l1 + l2);
+      s->oc_steps = step;
+    }
+  }
+}
+
+}  // namespace
+
+mfto_status compliance_launch(mfto_handle* h, const double* rho, const double* u, double* dc,
+                              double* c_out, double* gray_out) {
+  const Grid g = make_grid(h->mesh);
+  const int nb = reduction_blocks(h->n_elem, MFTO_BLOCK);
+  compliance_kernel<<<nb, MFTO_BLOCK, 0, h->stream>>>(rho, u, dc, h->d_ke64, g, h->p.E0,
+                                                     h->p.Emin, h->p.penal, h->d_misc,
+                                                     h->d_partials);
+  MFTO_LAUNCH_CHECK(h);
+  MFTO_CUDA(h, cudaMemcpyAsync(h->h_misc, h->d_misc, sizeof(MiscScalars), cudaMemcpyDeviceToHost,
+                               h->stream));
+  MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (c_out) *c_out = h->h_misc->sum[0];
+  if (gray_out) *gray_out = h->h_misc->sum[1] / (double)h->n_elem;
+  return MFTO_OK;
+}
+
+mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc, double* rho_new,
+                      mfto_iter_stats* st) {
+  int per_sm = 0;
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oc_kernel, MFTO_BLOCK, 0));
+  int blocks = per_sm * h->num_sms;
+  const int need = (int)((h->n_elem + MFTO_BLOCK - 1) / MFTO_BLOCK);
+  if (blocks > need) blocks = need;
+  if (blocks > MFTO_RED_MAX_BLOCKS) blocks = MFTO_RED_MAX_BLOCKS;
+  if (blocks < 1) blocks = 1;
+  MFTO_CUDA(h, cudaMemsetAsync(&h->d_misc->error, 0, sizeof(int32_t), h->stream));
+  MFTO_CUDA(h, cudaMemsetAsync(&h->d_misc->bar_count, 0, sizeof(unsigned int), h->stream));
+  int n = (int)h->n_elem;
+  double volfrac = h->p.volfrac, move = h->p.move;
+  MiscScalars* s = h->d_misc;
+  double* partials = h->d_partials2;
+  void* args[] = {(void*)&rho, (void*)&dc, (void*)&rho_new, &n, &volfrac, &move, &s, &partials};
+  MFTO_CUDA(h, cudaLaunchCooperativeKernel((const void*)oc_kernel, dim3(blocks), dim3(MFTO_BLOCK),
+                                           args, 0, h->stream));
+  MFTO_CUDA(h, cudaMemcpyAsync(h->h_misc, h->d_misc, sizeof(MiscScalars), cudaMemcpyDeviceToHost,
+                               h->stream));
+  MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->h_misc->error)
+    return mfto_fail(h, MFTO_CUDA_ERROR, "OC: a grid barrier wait gave up (bounded spin)");
+  if (st) {
+    st->change = h->h_misc->change;
+    st->volume = h->h_misc->volume;
+    st->lambda = h->h_misc->lambda;
+  }
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_compliance_sens(mfto_handle* h, const double* rho_phys,
+                                            const double* u, double* c_out, double* dc) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, rho_phys && u && c_out, "mfto_compliance_sens: null pointer");
+  return compliance_launch(h, rho_phys, u, dc, c_out, nullptr);
+}
+
+extern "C" mfto_status mfto_oc_update(mfto_handle* h, const double* rho, const double* dc,
+                                      double* rho_new, mfto_iter_stats* st) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, rho && dc && rho_new, "mfto_oc_update: null pointer");
+  MFTO_REQUIRE(h, rho != rho_new, "mfto_oc_update: rho_new must not alias rho");
+  return oc_launch(h, rho, dc, rho_new, st);
+}
+
+extern "C" mfto_status mfto_simp_step(mfto_handle* h, double* rho, double* u, const double* f,
+                                      double* rho_phys_out, mfto_iter_stats* st) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, rho && u && f, "mfto_simp_step: null pointer");
+  double* rho_phys = rho_phys_out ? rho_phys_out : h->d_rho_phys;
+  mfto_status s = filter_launch(h, rho, rho_phys, 0);
+  if (s != MFTO_OK) return s;
+  s = modulus_launch(h, MFTO_FORM_F64, rho_phys, h->d_E);
+  if (s != MFTO_OK) return s;
+  mfto_solve_stats ss;
+  s = pcg_run(h, h->d_E, f, u, &ss);
+  if (s != MFTO_OK) return s;
+  double c = 0.0, gray = 0.0;
+  s = compliance_launch(h, rho_phys, u, h->d_dc_phys, &c, &gray);
+  if (s != MFTO_OK) return s;
+  s = filter_launch(h, h->d_dc_phys, h->d_dc, 1);
+  if (s != MFTO_OK) return s;
+  mfto_iter_stats local;
+  mfto_iter_stats* out = st ? st : &local;
+  // the OC candidate goes to scratch (the bisection re-reads rho every step)
+  s = oc_launch(h, rho, h->d_dc, h->d_dc_phys, out);
+  if (s != MFTO_OK) return s;
+  MFTO_CUDA(h, cudaMemcpyAsync(rho, h->d_dc_phys, sizeof(double) * h->n_elem,
+                               cudaMemcpyDeviceToDevice, h->stream));
+  out->compliance = c;
+  out->grayness = gray;
+  out->cg_iterations = ss.iterations;
+  out->cg_status = ss.status;
+  out->rel_residual = ss.rel_residual;
+  return MFTO_OK;
+}

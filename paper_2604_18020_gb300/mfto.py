@@ -1,0 +1,284 @@
+"""Thin Python binding of libmfto.so (the C ABI declared in include/mfto.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Device arrays are torch tensors on a CUDA device (torch supplies the memory
+and the stream); the functions carry the C names without the ``mfto_``
+prefix.  Loading fails loudly when the library is missing -- there is no CPU
+path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+LIB_PATH = HERE / "libmfto.so"
+
+OK, INVALID_ARG, CUDA_ERROR, OOM, NOT_CONVERGED, STALLED, BREAKDOWN, UNSUPPORTED = range(8)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA_ERROR", 3: "OOM", 4: "NOT_CONVERGED",
+                5: "STALLED", 6: "BREAKDOWN", 7: "UNSUPPORTED"}
+
+FORM_F64, FORM_F32 = 0, 1
+FORMS = {"f64": FORM_F64, "f32": FORM_F32}
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nelx", C.c_int32), ("nely", C.c_int32), ("nelz", C.c_int32),
+                ("h", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double),
+                ("penal", C.c_double), ("rmin", C.c_double), ("volfrac", C.c_double),
+                ("move", C.c_double), ("rtol", C.c_double), ("maxit", C.c_int32),
+                ("check_every", C.c_int32)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32),
+                ("rel_residual", C.c_double), ("fnorm", C.c_double)]
+
+
+class IterStats(C.Structure):
+    _fields_ = [("compliance", C.c_double), ("change", C.c_double), ("volume", C.c_double),
+                ("grayness", C.c_double), ("lambda_", C.c_double),
+                ("cg_iterations", C.c_int32), ("cg_status", C.c_int32),
+                ("rel_residual", C.c_double)]
+
+
+class MftoError(RuntimeError):
+    def __init__(self, fn, code, msg=""):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes); the full exported surface of include/mfto.h
+_P = C.c_void_p
+SIGNATURES = {
+    "mfto_version": (C.c_char_p, []),
+    "mfto_default_params": (None, [C.POINTER(Params)]),
+    "mfto_unit_ke": (C.c_int32, [C.c_double, C.c_double, C.c_double, _P]),
+    "mfto_edof": (C.c_int32, [C.POINTER(Mesh), _P]),
+    "mfto_filter_stencil": (C.c_int32, [C.c_double, C.c_int32, _P, _P, C.POINTER(C.c_int32)]),
+    "mfto_create": (C.c_int32, [C.POINTER(Mesh), C.POINTER(Params), _P, _P, C.POINTER(_P)]),
+    "mfto_destroy": (C.c_int32, [_P]),
+    "mfto_set_params": (C.c_int32, [_P, C.POINTER(Params)]),
+    "mfto_last_error": (C.c_char_p, [_P]),
+    "mfto_sizes": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int64)]),
+    "mfto_simp_modulus": (C.c_int32, [_P, C.c_int32, _P, _P]),
+    "mfto_kv": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
+    "mfto_jacobi_diag": (C.c_int32, [_P, C.c_int32, _P, _P]),
+    "mfto_pcg": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
+    "mfto_filter": (C.c_int32, [_P, _P, _P, C.c_int32]),
+    "mfto_compliance_sens": (C.c_int32, [_P, _P, _P, C.POINTER(C.c_double), _P]),
+    "mfto_oc_update": (C.c_int32, [_P, _P, _P, _P, C.POINTER(IterStats)]),
+    "mfto_simp_step": (C.c_int32, [_P, _P, _P, _P, _P, C.POINTER(IterStats)]),
+    "mfto_kv_timing": (C.c_int32, [_P, C.c_int32]),
+    "mfto_kv_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+}
+
+
+def lib() -> C.CDLL:
+    """Load libmfto.so (built by paper_2604_18020_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        path = Path(os.environ.get("MFTO_LIB", LIB_PATH))
+        if not path.exists():
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(str(path))
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(fn, code, handle=None):
+    if code != OK:
+        msg = ""
+        if handle:
+            raw = lib().mfto_last_error(handle)
+            msg = raw.decode() if raw else ""
+        raise MftoError(fn, code, msg)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().mfto_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# ------------------------------------------------------------------ host calls
+
+def unit_ke(E0=1.0, nu=0.3, h=1.0) -> np.ndarray:
+    out = np.zeros(576)
+    _check("mfto_unit_ke", lib().mfto_unit_ke(E0, nu, h, out.ctypes.data))
+    return out.reshape(24, 24)
+
+
+def edof(nelx, nely, nelz) -> np.ndarray:
+    m = Mesh(nelx, nely, nelz, 1.0)
+    out = np.zeros(nelx * nely * nelz * 24, dtype=np.int32)
+    _check("mfto_edof", lib().mfto_edof(C.byref(m), out.ctypes.data))
+    return out.reshape(-1, 24)
+
+
+def filter_stencil(rmin):
+    n = C.c_int32(0)
+    lib().mfto_filter_stencil(rmin, 0, None, None, C.byref(n))
+    off = np.zeros(3 * n.value, dtype=np.int32)
+    w = np.zeros(n.value)
+    _check("mfto_filter_stencil",
+           lib().mfto_filter_stencil(rmin, n.value, off.ctypes.data, w.ctypes.data, C.byref(n)))
+    return off.reshape(-1, 3), w
+
+
+# ----------------------------------------------------------------- the handle
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class Handle:
+    """Owns one mfto_handle (mesh, parameters, fixed set, device workspace)."""
+
+    def __init__(self, nelx, nely, nelz, fixed, params: Params | None = None, h=1.0,
+                 stream=None):
+        import torch
+        self.mesh = Mesh(nelx, nely, nelz, h)
+        self.params = params if params is not None else default_params()
+        fixed = np.ascontiguousarray(fixed, dtype=np.uint8)
+        self.n_elem = nelx * nely * nelz
+        self.n_node = (nelx + 1) * (nely + 1) * (nelz + 1)
+        self.n_dof = 3 * self.n_node
+        if fixed.size != self.n_node:
+            raise ValueError(f"fixed mask must have {self.n_node} entries")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        hp = C.c_void_p()
+        code = lib().mfto_create(C.byref(self.mesh), C.byref(self.params), fixed.ctypes.data,
+                                 C.c_void_p(self.stream.cuda_stream), C.byref(hp))
+        _check("mfto_create", code)
+        self._h = hp
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mfto_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- helpers
+    def _dt(self, form):
+        import torch
+        return torch.float64 if form == FORM_F64 else torch.float32
+
+    def set_params(self, params: Params):
+        _check("mfto_set_params", lib().mfto_set_params(self._h, C.byref(params)), self._h)
+        self.params = params
+
+    def sizes(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check("mfto_sizes", lib().mfto_sizes(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    # ---- device steps
+    def simp_modulus(self, rho_phys, E, form=FORM_F64):
+        import torch
+        _check("mfto_simp_modulus", lib().mfto_simp_modulus(
+            self._h, form, _ptr(rho_phys, torch.float64, self.n_elem, "rho_phys"),
+            _ptr(E, self._dt(form), self.n_elem, "E")), self._h)
+
+    def kv(self, E, v, y, form=FORM_F64):
+        dt = self._dt(form)
+        _check("mfto_kv", lib().mfto_kv(
+            self._h, form, _ptr(E, dt, self.n_elem, "E"), _ptr(v, dt, self.n_dof, "v"),
+            _ptr(y, dt, self.n_dof, "y")), self._h)
+
+    def jacobi_diag(self, E, d, form=FORM_F64):
+        dt = self._dt(form)
+        _check("mfto_jacobi_diag", lib().mfto_jacobi_diag(
+            self._h, form, _ptr(E, dt, self.n_elem, "E"), _ptr(d, dt, self.n_dof, "diag")),
+            self._h)
+
+    def pcg(self, E, f, u) -> SolveStats:
+        import torch
+        st = SolveStats()
+        _check("mfto_pcg", lib().mfto_pcg(
+            self._h, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(f, torch.float64, self.n_dof, "f"), _ptr(u, torch.float64, self.n_dof, "u"),
+            C.byref(st)), self._h)
+        return st
+
+    def filter(self, x, y, transpose=False):
+        import torch
+        _check("mfto_filter", lib().mfto_filter(
+            self._h, _ptr(x, torch.float64, self.n_elem, "x"),
+            _ptr(y, torch.float64, self.n_elem, "y"), 1 if transpose else 0), self._h)
+
+    def compliance_sens(self, rho_phys, u, dc=None) -> float:
+        import torch
+        c = C.c_double()
+        _check("mfto_compliance_sens", lib().mfto_compliance_sens(
+            self._h, _ptr(rho_phys, torch.float64, self.n_elem, "rho_phys"),
+            _ptr(u, torch.float64, self.n_dof, "u"), C.byref(c),
+            _ptr(dc, torch.float64, self.n_elem, "dc")), self._h)
+        return c.value
+
+    def oc_update(self, rho, dc, rho_new) -> IterStats:
+        import torch
+        st = IterStats()
+        _check("mfto_oc_update", lib().mfto_oc_update(
+            self._h, _ptr(rho, torch.float64, self.n_elem, "rho"),
+            _ptr(dc, torch.float64, self.n_elem, "dc"),
+            _ptr(rho_new, torch.float64, self.n_elem, "rho_new"), C.byref(st)), self._h)
+        return st
+
+    def simp_step(self, rho, u, f, rho_phys=None) -> IterStats:
+        import torch
+        st = IterStats()
+        _check("mfto_simp_step", lib().mfto_simp_step(
+            self._h, _ptr(rho, torch.float64, self.n_elem, "rho"),
+            _ptr(u, torch.float64, self.n_dof, "u"), _ptr(f, torch.float64, self.n_dof, "f"),
+            _ptr(rho_phys, torch.float64, self.n_elem, "rho_phys"), C.byref(st)), self._h)
+        return st
+
+    # ---- timing
+    def kv_timing(self, on: bool):
+        _check("mfto_kv_timing", lib().mfto_kv_timing(self._h, 1 if on else 0), self._h)
+
+    def kv_timing_read(self):
+        n, ms = C.c_int64(), C.c_double()
+        _check("mfto_kv_timing_read",
+               lib().mfto_kv_timing_read(self._h, C.byref(n), C.byref(ms)), self._h)
+        return n.value, ms.value
