@@ -19,10 +19,14 @@ Readings where the paper is silent (identical in the CUDA library):
   * the volume constraint acts on the design field rho (Eq. tomin literally),
     dV/drho_e = 1/n;
   * OC: B_e = max(0, -dc_e) / (lambda dV_e); the candidate is
-    rho * sqrt(B_e) clipped to [max(0, rho - m), min(1, rho + m)], m = move;
+    rho * sqrt(B_e) clipped to [max(0, rho - m), min(1, rho + m)], m = move
+    (a NaN candidate, 0 * inf at an underflowed lambda, is clipped to the bound);
     lambda is bisected on [0, 1e9], raising the lower end while
-    sum(rho_new) > V_f n, until (l2 - l1) / (l1 + l2) <= 1e-10; the returned
-    field is the candidate of the last midpoint;
+    sum(rho_new) > V_f n, until (l2 - l1) / (l1 + l2) <= 1e-10, or until the
+    midpoint no longer lies strictly inside the bracket (the bracket cannot
+    shrink further in floating point: this happens when even the smallest
+    lambda gives too little volume and lambda underflows), or after 4096
+    steps; the returned field is the candidate of the last midpoint;
   * grayness is evaluated on the physical field rho_phys.
 """
 from __future__ import annotations
@@ -52,6 +56,11 @@ def compliance_sens(KE, edof, u, rho_phys, penal, E0=1.0, Emin=1e-9):
 def oc_update(rho, dc, volfrac, move=0.2, l1=0.0, l2=1e9, tol=1e-10):
     """Optimality-Criteria update with bisection on the volume multiplier."""
     rho = np.asarray(rho, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        return _oc_bisect(rho, dc, volfrac, move, l1, l2, tol)
+
+
+def _oc_bisect(rho, dc, volfrac, move, l1, l2, tol):
     n = rho.size
     dv = 1.0 / n
     target = volfrac * n
@@ -60,10 +69,12 @@ def oc_update(rho, dc, volfrac, move=0.2, l1=0.0, l2=1e9, tol=1e-10):
     hi = np.minimum(1.0, rho + move)
     rho_new = rho.copy()
     steps = 0
-    while (l2 - l1) / (l1 + l2) > tol:
+    while l1 + l2 > 0.0 and (l2 - l1) / (l1 + l2) > tol and steps < 4096:
         lmid = 0.5 * (l1 + l2)
+        if not (l1 < lmid < l2):
+            break
         cand = rho * np.sqrt(neg / (lmid * dv))
-        rho_new = np.maximum(lo, np.minimum(hi, cand))
+        rho_new = np.fmax(lo, np.fmin(hi, cand))   # a NaN candidate (0 * inf) is clipped away
         if np.sum(rho_new) > target:
             l1 = lmid
         else:

@@ -138,3 +138,13 @@ def test_paper_printed_compliance(idx):
     c_paper = case["c_max_fp32"] / (1.0 + case["max_delta_c"])
     assert abs(c - c_paper) / c_paper <= case["rel_tol"]
     assert abs(its - case["cg_iterations_fp32"]) <= case["iter_tol"]
+
+
+def test_oc_unreachable_target_collapses_bracket():
+    """All sensitivities zero: every candidate sits at the lower move limit,
+    the volume target cannot be met from above, lambda underflows and the
+    bisection stops with the lower bounds."""
+    rho = np.full(64, 0.3)
+    new, info = simp.oc_update(rho, np.zeros(64), 0.3, 0.2)
+    assert np.array_equal(new, np.maximum(0.0, rho - 0.2))
+    assert info["lambda"] < 1e-300 and info["steps"] < 1200
