@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the matrix-free SIMP hot path on one GB300.
+
+A step is one SIMP iteration of the 120 x 60 x 30 cantilever (216,000 Q1
+elements, 686,433 DOFs; x=0 face clamped, unit -y load on the bottom edge of
+the free end; V_f = 0.3, r_min = 1.5, E0 = 1, Emin = 1e-9, nu = 0.3, p = 3):
+cone filter -> SIMP modulus -> Jacobi diagonal -> Jacobi-PCG to
+||r||/||f|| <= 1e-8 (warm start) -> compliance and sensitivities -> filter
+transpose -> OC bisection.  Every step runs in the library's CUDA kernels;
+the steps continue one SIMP run from the uniform start (the warm-up steps are
+its first iterations).
+
+value: K.v throughput of the whole step, n_elem x (K.v applications in the
+timed steps) / (device time of the timed steps), in Gelem/s, with inputs
+resident in HBM and L2 flushed (256 MiB write) before every step.
+e2e: the same through the public API from pinned host buffers, the per-step
+host->device copy of rho, u, f and the device->host copy of rho, u inside
+the timed region.  roofline: the dominant kernel (the K.v of the PCG), its
+average launch duration from CUDA events recorded around every launch in a
+replay of the same steps.  cpu_baseline: the CPU oracle on a bounded sample
+of the same step (its PCG capped), single-threaded.
+
+--impl reference times the CPU oracle alone (the method's plain restatement)
+on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "K·v Gelem/s & % roofline; SIMP iter time, plain FP64 vs chosen forms @1e-6"
+WORKLOAD = "cantilever_120x60x30"
+FLOP_PER_ELEM = 1152.0                       # 2 * 24 * 24, dense element contraction
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="mfto_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={SMI_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = sorted({REASONS[i] for _, _, flags in rows for i, f in enumerate(flags)
+                          if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+def oracle_step(P, rho, u, maxit, rtol=1e-8):
+    """One SIMP iteration of the CPU oracle with the PCG capped at maxit;
+    returns (rho_new, u, kv_applications)."""
+    import numpy as np
+    from oracle import fem, filter as cone, simp, solve
+    m = P.mesh
+    KE = fem.ke_exact(1.0, 0.3)
+    edof = fem.edof_table_fast(m.nelx, m.nely, m.nelz)
+    fixed = fem.dof_mask(P.fixed)
+    count = [0]
+
+    def apply_K(v):
+        count[0] += 1
+        return fem.kv(KE, E, edof, v, fixed)
+
+    rho_phys = cone.filter_fwd(rho, m.nelx, m.nely, m.nelz, P.rmin)
+    E = fem.simp_modulus(rho_phys, 3.0)
+    d = fem.jacobi_diag(KE, E, edof, fixed)
+    u, _ = solve.pcg(apply_K, d, P.f, u, rtol, maxit)
+    _, dc_phys = simp.compliance_sens(KE, edof, u, rho_phys, 3.0)
+    dc = cone.filter_T(dc_phys, m.nelx, m.nely, m.nelz, P.rmin)
+    rho_new, _ = simp.oc_update(rho, dc, P.volfrac, 0.2)
+    return rho_new, u, count[0]
+
+
+def cpu_sample(workload: str, steps: int, maxit: int):
+    import numpy as np
+    from paper_2604_18020_gb300 import workloads as W
+    P = W.WORKLOADS[workload]()
+    rho = np.full(P.mesh.n_elem, P.volfrac)
+    u = np.zeros(P.mesh.n_dof)
+    times, kvs = [], []
+    for _ in range(steps):
+        t = time.perf_counter()
+        rho, u, n = oracle_step(P, rho, u, maxit)
+        times.append(time.perf_counter() - t)
+        kvs.append(n)
+    return {"times": times, "kv": kvs, "n_elem": P.mesh.n_elem}
+
+
+def run_cpu_sample(workload, steps, maxit):
+    """The oracle in a fresh process (spawned, no CUDA), one BLAS thread."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--cpu-sample", workload,
+                          "--steps", str(steps), "--maxit", str(maxit)],
+                         capture_output=True, text=True, env=env, cwd=str(ROOT))
+    if out.returncode != 0:
+        raise RuntimeError(f"CPU oracle sample failed:\n{out.stderr[-2000:]}")
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(res, maxit):
+    tot_t = sum(res["times"])
+    tot_kv = sum(res["kv"])
+    return {"value": res["n_elem"] * tot_kv / tot_t / 1e9, "unit": "Gelem/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{len(res['times'])} SIMP iteration(s) of {WORKLOAD} by the FP64 numpy "
+                      f"oracle from the uniform start, PCG capped at {maxit} iterations "
+                      f"({tot_kv} K.v applications, {tot_t:.1f} s, 1 BLAS thread)"}
+
+
+# ------------------------------------------------------------- GPU leg
+
+def gpu_bench(args, rank, local_rank, world):
+    import numpy as np
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    P = W.WORKLOADS[WORKLOAD]()
+    m = P.mesh
+    params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
+    h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
+    rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
+    u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+    f = torch.tensor(P.f, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        h.simp_step(rho, u, f)
+    torch.cuda.synchronize()
+    rho0, u0 = rho.clone(), u.clone()
+
+    def timed_pass(kv_timed: bool):
+        rho.copy_(rho0)
+        u.copy_(u0)
+        h.kv_timing(kv_timed)
+        total_ms, stats = 0.0, []
+        l0 = h.launch_count()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = h.simp_step(rho, u, f)
+            b.record(stream)
+            b.synchronize()
+            total_ms += a.elapsed_time(b)
+            stats.append(st)
+        launches = h.launch_count() - l0
+        kv_n, kv_ms = h.kv_timing_read()
+        h.kv_timing(False)
+        return total_ms, stats, launches, kv_n, kv_ms
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        t_ms, stats, launches, _, _ = timed_pass(False)
+    torch.cuda.synchronize()
+    if dist:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = tt.item()
+    clk = clocks.summary()
+    # replay with events around every K.v launch (same steps, same state)
+    _, stats_b, _, kv_n, kv_ms = timed_pass(True)
+    cg = [s.cg_iterations for s in stats]
+    assert cg == [s.cg_iterations for s in stats_b], "replay diverged"
+    kv_per_pass = kv_n
+
+    # e2e: public API from pinned host buffers, copies inside the timed region
+    h_rho = rho0.cpu().pin_memory()
+    h_u = u0.cpu().pin_memory()
+    h_f = f.cpu().pin_memory()
+    o_rho = torch.empty_like(h_rho).pin_memory()
+    o_u = torch.empty_like(h_u).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rho.copy_(h_rho, non_blocking=True)
+        u.copy_(h_u, non_blocking=True)
+        f.copy_(h_f, non_blocking=True)
+        h.simp_step(rho, u, f)
+        o_rho.copy_(rho, non_blocking=True)
+        o_u.copy_(u, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+        h_rho.copy_(o_rho)
+        h_u.copy_(o_u)
+    h2d = (h_rho.numel() + h_u.numel() + h_f.numel()) * 8
+    d2h = (o_rho.numel() + o_u.numel()) * 8
+    if dist:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = tt.item()
+
+    units = m.n_elem * kv_per_pass * world
+    value = units / (t_ms * 1e-3) / 1e9
+    e2e_value = units / (e2e_ms * 1e-3) / 1e9
+    kv_avg_s = kv_ms * 1e-3 / max(kv_n, 1)
+    sm_mhz = clk["sm_mhz"] or 1950.0
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    fp64_peak_tflops = n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12   # 2 DFMA/clk/SM, measured clock
+    achieved = FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": m.n_elem, "dofs": m.n_dof,
+                   "form": "f64", "pcg_rtol": 1e-8, "kv_kernel": "tiled mode-space",
+                   "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "simp_iter_ms": t_ms / args.steps,
+        "cg_iterations": cg,
+        "compliance": [s.compliance for s in stats],
+        "kv_per_step": kv_per_pass / args.steps,
+        "kv_kernel_us": kv_avg_s * 1e6,
+        "kv_kernel_gelem_s": m.n_elem / kv_avg_s / 1e9,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": None,
+                     "kernel": "pcg_kv_tile_kernel<double>",
+                     "peak_source": f"FP64 FMA pipe, {n_sm} SMs x 2 DFMA/clk x 2 flop x "
+                                    f"{sm_mhz:.0f} MHz median SM clock under load",
+                     "flop_per_elem": FLOP_PER_ELEM},
+        "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"]},
+    }
+    h.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def profile_run(args):
+    """Short runs for ncu: 'profile' = W + K SIMP steps of the benchmark
+    workload, nothing else; 'pcg' = one PCG capped at --maxit iterations on
+    --workload with a seeded random density (exercises the CG K.v kernel on
+    a mesh larger than L2)."""
+    import numpy as np
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+    P = W.WORKLOADS[args.workload]()
+    m = P.mesh
+    params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8,
+                                 maxit=args.maxit if args.mode == "pcg" else 10000)
+    h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
+    f = torch.tensor(P.f, device=dev)
+    u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+    if args.mode == "profile":
+        rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup + args.steps):
+            h.simp_step(rho, u, f)
+    else:
+        rho = torch.tensor(W.rho_random(m, seed=1, lo=0.1, hi=1.0), device=dev)
+        E = torch.empty_like(rho)
+        h.simp_modulus(rho, E)
+        st = h.pcg(E, f, u)
+        print(json.dumps({"workload": args.workload, "cg_iterations": st.iterations,
+                          "rel_residual": st.rel_residual}))
+    torch.cuda.synchronize()
+    h.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-maxit", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "pcg"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--maxit", type=int, default=40, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.cpu_sample, args.steps, args.maxit)))
+        return
+
+    if args.mode != "bench":
+        profile_run(args)
+        return
+
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the oracle as it stands, on the host cores: warm-up steps untimed
+        res = run_cpu_sample(WORKLOAD, args.warmup + args.steps, args.cpu_maxit)
+        times, kvs = res["times"][args.warmup:], res["kv"][args.warmup:]
+        value = res["n_elem"] * sum(kvs) / sum(times) / 1e9
+        base = cpu_baseline_entry({"times": times, "kv": kvs, "n_elem": res["n_elem"]},
+                                  args.cpu_maxit)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "Gelem/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "f64", "pcg_maxit": args.cpu_maxit},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+
+    out = gpu_bench(args, rank, local_rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res = run_cpu_sample(WORKLOAD, 1, args.cpu_maxit)
+            out["cpu_baseline"] = cpu_baseline_entry(res, args.cpu_maxit)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -163,6 +163,14 @@ mfto_status mfto_simp_modulus(mfto_handle* h, mfto_form form,
 mfto_status mfto_kv(mfto_handle* h, mfto_form form, const void* d_E,
                     const void* d_v, void* d_y);
 
+/* Choose the K.v kernel used by mfto_kv, mfto_pcg and mfto_simp_step:
+ * 0 (default) = node-owned tiles streaming along z, element operator in the
+ * per-axis (sum, difference) mode basis, about 220 arithmetic operations per
+ * element; 1 = one thread per node gathering its 8 elements with the dense
+ * 24x24 KE from shared memory (576 multiply-adds per node, the operation
+ * count of Alg. 1).  Both are atomic-free and bit-reproducible. */
+mfto_status mfto_set_kv_variant(mfto_handle* h, int32_t variant);
+
 /* Jacobi diagonal of the masked K (Sec. 3.6), one element pass:
  * d_diag[k] = sum_{e owning k} E_e KE[l, l], 1 on fixed DOFs. */
 mfto_status mfto_jacobi_diag(mfto_handle* h, mfto_form form, const void* d_E,
@@ -194,8 +202,9 @@ mfto_status mfto_compliance_sens(mfto_handle* h, const double* d_rho_phys,
  * B_e = max(0, -dc_e) / (lambda / n); candidate rho sqrt(B_e) clipped to
  * [max(0, rho - m), min(1, rho + m)]; lambda bisected on [0, 1e9] while
  * sum(rho_new) > V_f n raises the lower end, until
- * (l2 - l1)/(l1 + l2) <= 1e-10.  d_rho_new receives the candidate of the
- * last midpoint.  Synchronises the stream; st may be NULL. */
+ * (l2 - l1)/(l1 + l2) <= 1e-10, or until the midpoint no longer lies strictly
+ * inside the bracket (lambda underflow), or 4096 steps.  d_rho_new receives
+ * the candidate of the last midpoint.  Synchronises the stream; st may be NULL. */
 mfto_status mfto_oc_update(mfto_handle* h, const double* d_rho,
                            const double* d_dc, double* d_rho_new,
                            mfto_iter_stats* st);
@@ -218,6 +227,21 @@ mfto_status mfto_simp_step(mfto_handle* h, double* d_rho, double* d_u,
 mfto_status mfto_kv_timing(mfto_handle* h, int32_t on);
 mfto_status mfto_kv_timing_read(mfto_handle* h, int64_t* launches,
                                 double* total_ms);
+
+/* Number of kernels the library has launched for this handle so far (the
+ * kernel nodes of every launched CUDA graph included). */
+mfto_status mfto_launch_count(const mfto_handle* h, int64_t* n);
+
+/* ------------------------------------------------------- measurement aid -- */
+
+/* Arithmetic-pipe probe: launches `blocks` x 256 threads, each running
+ * `iters` iterations of 8 independent fused multiply-add chains in the given
+ * form (F64 or F32) on the current device and stream 0, and returns the
+ * elapsed device time (CUDA events) in *ms_out.  Work done:
+ * blocks * 256 * iters * 8 FMAs.  Used to measure the FMA-pipe peak that the
+ * roofline of the FP64 and FP32 K.v forms is quoted against; it has no
+ * counterpart in the paper. */
+mfto_status mfto_fma_probe(mfto_form form, int32_t blocks, int32_t iters, double* ms_out);
 
 #ifdef __cplusplus
 }

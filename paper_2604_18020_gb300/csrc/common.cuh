@@ -11,8 +11,19 @@
 
 #include "../../include/mfto.h"
 
+// Mode-space coefficients for unit modulus; the 1/8 of the inverse transform
+// is folded in.  diag[i][m]: out[i][m] += diag[i][m] in[i][m];
+// lamM[t], muM[t]: off-diagonal couplings lam*M(t), mu*M(t) (t = mode bit of
+// the remaining axis).  Applied by element_apply() in kv_tile.cuh.
+template <typename T>
+struct ModeCoef {
+  T diag[3][8];
+  T lamM[2], muM[2];
+};
+
 #define MFTO_BLOCK 256            // threads per block of the element/node kernels
-#define MFTO_RED_MAX_BLOCKS 1024  // partial-sum slots of one grid reduction
+#define MFTO_RED_MAX_BLOCKS 1024  // grid cap of the grid-stride vector kernels
+#define MFTO_RED_SLOTS 16384      // partial-sum slots per row of one grid reduction
 
 // Device-resident scalars of the PCG driver and the other reductions.  Each
 // reduction site owns a ticket counter (reset by the last block).
@@ -54,6 +65,9 @@ struct mfto_handle {
   double* d_ke64;
   float* d_ke32;
   double ke_diag;           // KE[l][l] (equal for every local DOF on a cube)
+  ModeCoef<double> mc64;    // mode-space element operator (kv_tile.cuh)
+  ModeCoef<float> mc32;
+  int kv_variant;           // 0: tiled mode-space kernel, 1: node-centric dense KE
   uint8_t* d_fixed;         // per-node mask
   // cone filter
   int32_t n_stencil;
@@ -62,8 +76,8 @@ struct mfto_handle {
   double* d_filter_W;       // row sums W_e
   // PCG workspace (FP64)
   double *d_r, *d_z, *d_p0, *d_p1, *d_q, *d_dinv;
-  double* d_partials;       // [4 * MFTO_RED_MAX_BLOCKS]
-  double* d_partials2;      // [4 * MFTO_RED_MAX_BLOCKS]
+  double* d_partials;       // [4 * MFTO_RED_SLOTS]
+  double* d_partials2;      // [4 * MFTO_RED_SLOTS]
   PcgScalars* d_pcg;
   MiscScalars* d_misc;
   PcgScalars* h_pcg;        // pinned mirror
@@ -72,6 +86,8 @@ struct mfto_handle {
   double *d_rho_phys, *d_E, *d_dc, *d_dc_phys;
   // PCG graph cache (one captured chunk of check_every iterations)
   struct PcgGraph* pcg_graph;
+  // kernels launched on behalf of this handle (graph kernel nodes included)
+  int64_t launches;
   // timing
   bool kv_timing;
   KvEventPool ev;
@@ -159,18 +175,20 @@ __device__ __forceinline__ bool last_block_reduce(const double (&v)[K],
                                                   double* partials,
                                                   unsigned int* ticket,
                                                   double* out, double* sh) {
-  // partials: K rows of MFTO_RED_MAX_BLOCKS slots; gridDim.x must not exceed
-  // MFTO_RED_MAX_BLOCKS (callers use grid-stride loops).
+  // partials: K rows of MFTO_RED_SLOTS slots; the grid (any shape) must not
+  // have more than MFTO_RED_SLOTS blocks.
   __shared__ bool s_last;
+  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   double bs[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) bs[c] = block_sum(v[c], sh);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int c = 0; c < K; ++c) partials[c * MFTO_RED_MAX_BLOCKS + blockIdx.x] = bs[c];
+    for (int c = 0; c < K; ++c) partials[c * MFTO_RED_SLOTS + bid] = bs[c];
     __threadfence();
     unsigned int t = atomicAdd(ticket, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == nb - 1);
   }
   __syncthreads();
   if (!s_last) return false;
@@ -178,8 +196,8 @@ __device__ __forceinline__ bool last_block_reduce(const double (&v)[K],
 #pragma unroll
   for (int c = 0; c < K; ++c) {
     double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      s += __ldcg(&partials[c * MFTO_RED_MAX_BLOCKS + b]);
+    for (int b = threadIdx.x; b < (int)nb; b += blockDim.x)
+      s += __ldcg(&partials[c * MFTO_RED_SLOTS + b]);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) sh[32 + c] = s;
   }
@@ -238,6 +256,12 @@ mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc,
 mfto_status pcg_run(mfto_handle* h, const double* E, const double* f,
                     double* u, mfto_solve_stats* st);
 void pcg_graph_release(mfto_handle* h);
+mfto_status kv_tile_init(mfto_handle* h);
+template <typename T>
+mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStream_t st);
+template <typename T>
+mfto_status pcg_kv_tile_launch(mfto_handle* h, const T* E, const T* z, const T* p_old, T* p_new,
+                               T* q, PcgScalars* s, double* partials, cudaStream_t st);
 void kv_timing_begin(mfto_handle* h);
 void kv_timing_end(mfto_handle* h);
 mfto_status kv_timing_harvest(mfto_handle* h, bool sync);

@@ -57,6 +57,7 @@ static mfto_status launch_filter(mfto_handle* h, const double* x, double* y, int
     MFTO_CUDA(h, cudaFuncSetAttribute(filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   int blocks = (int)((h->n_elem + MFTO_BLOCK - 1) / MFTO_BLOCK);
+  h->launches++;
   if (blocks > 16 * h->num_sms) blocks = 16 * h->num_sms;
   filter_kernel<<<blocks, MFTO_BLOCK, smem, h->stream>>>(x, y, h->d_filter_W, h->d_stencil_off,
                                                          h->d_stencil_w, h->n_stencil, g,

@@ -147,6 +147,27 @@ static mfto_status upload_params(mfto_handle* h) {
   mfto_unit_ke(1.0, h->p.nu, h->mesh.h, ke);
   for (int i = 0; i < 576; ++i) ke32[i] = (float)ke[i];
   h->ke_diag = ke[0];
+  // mode-space coefficients (unit modulus, 1/8 of the inverse folded in)
+  {
+    const ModeOperator op = mode_operator(1.0, h->p.nu, h->mesh.h);
+    memset(&h->mc64, 0, sizeof(h->mc64));
+    for (int t = 0; t < op.n_terms; ++t)
+      if (op.out_comp[t] == op.in_comp[t] && op.out_mode[t] == op.in_mode[t])
+        h->mc64.diag[op.out_comp[t]][op.out_mode[t]] = op.coef[t] / 8.0;
+    const double nu = h->p.nu, hh = h->mesh.h;
+    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
+    const double M[2] = {hh / 2.0, hh / 6.0};
+    for (int t = 0; t < 2; ++t) {
+      h->mc64.lamM[t] = lam * M[t] / 8.0;
+      h->mc64.muM[t] = mu * M[t] / 8.0;
+    }
+    for (int c = 0; c < 3; ++c)
+      for (int m = 0; m < 8; ++m) h->mc32.diag[c][m] = (float)h->mc64.diag[c][m];
+    for (int t = 0; t < 2; ++t) {
+      h->mc32.lamM[t] = (float)h->mc64.lamM[t];
+      h->mc32.muM[t] = (float)h->mc64.muM[t];
+    }
+  }
   MFTO_CUDA(h, cudaMemcpyAsync(h->d_ke64, ke, sizeof(ke), cudaMemcpyHostToDevice, h->stream));
   MFTO_CUDA(h, cudaMemcpyAsync(h->d_ke32, ke32, sizeof(ke32), cudaMemcpyHostToDevice, h->stream));
   int32_t n = 0;
@@ -211,8 +232,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   A((void**)&h->d_p1, nd);
   A((void**)&h->d_q, nd);
   A((void**)&h->d_dinv, nd);
-  A((void**)&h->d_partials, sizeof(double) * 4 * MFTO_RED_MAX_BLOCKS);
-  A((void**)&h->d_partials2, sizeof(double) * 4 * MFTO_RED_MAX_BLOCKS);
+  A((void**)&h->d_partials, sizeof(double) * 4 * MFTO_RED_SLOTS);
+  A((void**)&h->d_partials2, sizeof(double) * 4 * MFTO_RED_SLOTS);
   A((void**)&h->d_pcg, sizeof(PcgScalars));
   A((void**)&h->d_misc, sizeof(MiscScalars));
   A((void**)&h->d_rho_phys, ne);
@@ -233,7 +254,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
     free_handle(h);
     return MFTO_CUDA_ERROR;
   }
-  mfto_status s = upload_params(h);
+  mfto_status s = kv_tile_init(h);
+  if (s == MFTO_OK) s = upload_params(h);
   if (s != MFTO_OK) { free_handle(h); return s; }
   *out = h;
   return MFTO_OK;
@@ -307,6 +329,12 @@ extern "C" mfto_status mfto_kv_timing(mfto_handle* h, int32_t on) {
   mfto_status s = kv_timing_harvest(h, true);
   h->kv_timing = on != 0;
   return s;
+}
+
+extern "C" mfto_status mfto_launch_count(const mfto_handle* h, int64_t* n) {
+  if (!h || !n) return MFTO_INVALID_ARG;
+  *n = h->launches;
+  return MFTO_OK;
 }
 
 extern "C" mfto_status mfto_kv_timing_read(mfto_handle* h, int64_t* launches,

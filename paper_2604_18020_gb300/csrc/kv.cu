@@ -76,7 +76,17 @@ static inline int node_blocks(const mfto_handle* h) { return reduction_blocks(h-
 
 mfto_status kv_launch(mfto_handle* h, mfto_form form, const void* E, const void* v, void* y) {
   const Grid g = make_grid(h->mesh);
+  if (form != MFTO_FORM_F64 && form != MFTO_FORM_F32)
+    return mfto_fail(h, MFTO_UNSUPPORTED, "mfto_kv: unsupported form %d", (int)form);
   kv_timing_begin(h);
+  h->launches++;
+  if (h->kv_variant == 0) {
+    mfto_status s = form == MFTO_FORM_F64
+        ? kv_tile_launch<double>(h, (const double*)E, (const double*)v, (double*)y, h->stream)
+        : kv_tile_launch<float>(h, (const float*)E, (const float*)v, (float*)y, h->stream);
+    kv_timing_end(h);
+    return s;
+  }
   if (form == MFTO_FORM_F64) {
     kv_node_dense<double><<<node_blocks(h), MFTO_BLOCK, 0, h->stream>>>(
         (const double*)E, (const double*)v, (double*)y, h->d_fixed, h->d_ke64, g, (int)h->n_node);
@@ -93,6 +103,7 @@ mfto_status kv_launch(mfto_handle* h, mfto_form form, const void* E, const void*
 
 mfto_status diag_launch(mfto_handle* h, mfto_form form, const void* E, void* d, bool inverse) {
   const Grid g = make_grid(h->mesh);
+  h->launches++;
   if (form == MFTO_FORM_F64) {
     diag_node<double><<<blocks_for(h->n_node), MFTO_BLOCK, 0, h->stream>>>(
         (const double*)E, (double*)d, h->d_fixed, h->ke_diag, g, (int)h->n_node, inverse);
@@ -108,6 +119,7 @@ mfto_status diag_launch(mfto_handle* h, mfto_form form, const void* E, void* d, 
 
 mfto_status modulus_launch(mfto_handle* h, mfto_form form, const double* rho, void* E) {
   const int n = (int)h->n_elem;
+  h->launches++;
   if (form == MFTO_FORM_F64) {
     modulus_kernel<double><<<blocks_for(n), MFTO_BLOCK, 0, h->stream>>>(
         rho, (double*)E, h->p.E0, h->p.Emin, h->p.penal, n);
@@ -127,6 +139,14 @@ extern "C" mfto_status mfto_kv(mfto_handle* h, mfto_form form, const void* E, co
   MFTO_REQUIRE(h, E && v && y, "mfto_kv: null pointer");
   MFTO_REQUIRE(h, v != y, "mfto_kv: y must not alias v");
   return kv_launch(h, form, E, v, y);
+}
+
+extern "C" mfto_status mfto_set_kv_variant(mfto_handle* h, int32_t variant) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, variant == 0 || variant == 1, "mfto_set_kv_variant: variant must be 0 or 1");
+  if (h->kv_variant != variant) pcg_graph_release(h);
+  h->kv_variant = variant;
+  return MFTO_OK;
 }
 
 extern "C" mfto_status mfto_jacobi_diag(mfto_handle* h, mfto_form form, const void* E,

@@ -149,11 +149,19 @@ static mfto_status enqueue_chunk(mfto_handle* h, cudaStream_t st, const double* 
   for (int it = 0; it < chunk; ++it) {
     double* p_old = (it & 1) ? h->d_p1 : h->d_p0;
     double* p_new = (it & 1) ? h->d_p0 : h->d_p1;
-    if (ev) MFTO_CUDA(h, cudaEventRecord(ev[2 * it], st));
-    pcg_kv_step<<<nb_node, MFTO_BLOCK, 0, st>>>(E, h->d_z, p_old, p_new, h->d_q,
-                                                      h->d_fixed, h->d_ke64, g,
-                                                      (int)h->n_node, h->d_pcg, h->d_partials);
-    if (ev) MFTO_CUDA(h, cudaEventRecord(ev[2 * it + 1], st));
+    // external record nodes: a plain record inside a capture would only add a
+    // dependency edge, not record the event on each graph launch
+    if (ev) MFTO_CUDA(h, cudaEventRecordWithFlags(ev[2 * it], st, cudaEventRecordExternal));
+    if (h->kv_variant == 0) {
+      mfto_status s = pcg_kv_tile_launch<double>(h, E, h->d_z, p_old, p_new, h->d_q, h->d_pcg,
+                                                 h->d_partials, st);
+      if (s != MFTO_OK) return s;
+    } else {
+      pcg_kv_step<<<nb_node, MFTO_BLOCK, 0, st>>>(E, h->d_z, p_old, p_new, h->d_q, h->d_fixed,
+                                                  h->d_ke64, g, (int)h->n_node, h->d_pcg,
+                                                  h->d_partials);
+    }
+    if (ev) MFTO_CUDA(h, cudaEventRecordWithFlags(ev[2 * it + 1], st, cudaEventRecordExternal));
     pcg_update<<<nb_dof, MFTO_BLOCK, 0, st>>>(u, p_new, h->d_q, h->d_r, h->d_z,
                                                     h->d_dinv, (int)h->n_dof, h->d_pcg,
                                                     h->d_partials2);
@@ -230,6 +238,7 @@ mfto_status pcg_run(mfto_handle* h, const double* E, const double* f, double* u,
   s = kv_launch(h, MFTO_FORM_F64, E, u, h->d_q);
   if (s != MFTO_OK) return s;
   MFTO_CUDA(h, cudaMemsetAsync(h->d_p0, 0, sizeof(double) * h->n_dof, h->stream));
+  h->launches++;
   pcg_init<<<nb_dof, MFTO_BLOCK, 0, h->stream>>>(f, h->d_q, h->d_dinv, h->d_r, h->d_z,
                                                  (int)h->n_dof, h->p.rtol, h->p.maxit,
                                                  h->d_pcg, h->d_partials);
@@ -247,15 +256,15 @@ mfto_status pcg_run(mfto_handle* h, const double* E, const double* f, double* u,
       const int ran = h->h_pcg->it - it_before + (h->h_pcg->status == MFTO_BREAKDOWN ? 1 : 0);
       for (int i = 0; i < ran && i < pg->chunk; ++i) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pg->ev[2 * i], pg->ev[2 * i + 1]) == cudaSuccess) {
-          h->ev.total_ms += ms;
-          h->ev.launches++;
-        }
+        MFTO_CUDA(h, cudaEventElapsedTime(&ms, pg->ev[2 * i], pg->ev[2 * i + 1]));
+        h->ev.total_ms += ms;
+        h->ev.launches++;
       }
       it_before = h->h_pcg->it;
     }
     if (h->h_pcg->done) break;
     MFTO_CUDA(h, cudaGraphLaunch(pg->exec, h->stream));
+    h->launches += 2 * (int64_t)pg->chunk;
   }
   if (h->h_pcg->ff == 0.0) MFTO_CUDA(h, cudaMemsetAsync(u, 0, sizeof(double) * h->n_dof, h->stream));
   if (st) {

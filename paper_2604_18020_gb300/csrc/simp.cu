@@ -62,8 +62,12 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
   const double target = volfrac * (double)n;
   double l1 = 0.0, l2 = 1e9, total = 0.0;
   int step = 0;
-  while ((l2 - l1) / (l1 + l2) > 1e-10) {
+  // Stops at the relative bracket width 1e-10, or when the midpoint no
+  // longer lies strictly inside the bracket (lambda underflow when the target
+  // is unreachable from above), and after at most 4096 steps in any case.
+  while (l1 + l2 > 0.0 && (l2 - l1) / (l1 + l2) > 1e-10 && step < 4096) {
     const double lmid = 0.5 * (l1 + l2);
+    if (!(l1 < lmid && lmid < l2)) break;   // uniform: every block holds the same l1, l2
     double acc = 0.0;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
       const double r = rho[e];
@@ -74,7 +78,7 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
       rho_new[e] = rn;
       acc += rn;
     }
-    double* buf = partials + (step & 1) * MFTO_RED_MAX_BLOCKS;
+    double* buf = partials + (step & 1) * MFTO_RED_SLOTS;
     const double bs = block_sum(acc, sh);
     if (threadIdx.x == 0) buf[blockIdx.x] = bs;
     grid_barrier(&s->bar_count, &s->bar_gen, &s->error);
@@ -92,7 +96,7 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
   double mx = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
     mx = fmax(mx, fabs(rho_new[e] - rho[e]));
-  double* buf = partials + 2 * MFTO_RED_MAX_BLOCKS;
+  double* buf = partials + 2 * MFTO_RED_SLOTS;
   const double bm = block_max(mx, sh);
   if (threadIdx.x == 0) buf[blockIdx.x] = bm;
   grid_barrier(&s->bar_count, &s->bar_gen, &s->error);
@@ -115,6 +119,7 @@ mfto_status compliance_launch(mfto_handle* h, const double* rho, const double* u
                               double* c_out, double* gray_out) {
   const Grid g = make_grid(h->mesh);
   const int nb = reduction_blocks(h->n_elem, MFTO_BLOCK);
+  h->launches++;
   compliance_kernel<<<nb, MFTO_BLOCK, 0, h->stream>>>(rho, u, dc, h->d_ke64, g, h->p.E0,
                                                      h->p.Emin, h->p.penal, h->d_misc,
                                                      h->d_partials);
@@ -143,6 +148,7 @@ mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc, doubl
   MiscScalars* s = h->d_misc;
   double* partials = h->d_partials2;
   void* args[] = {(void*)&rho, (void*)&dc, (void*)&rho_new, &n, &volfrac, &move, &s, &partials};
+  h->launches++;
   MFTO_CUDA(h, cudaLaunchCooperativeKernel((const void*)oc_kernel, dim3(blocks), dim3(MFTO_BLOCK),
                                            args, 0, h->stream));
   MFTO_CUDA(h, cudaMemcpyAsync(h->h_misc, h->d_misc, sizeof(MiscScalars), cudaMemcpyDeviceToHost,

@@ -74,11 +74,14 @@ SIGNATURES = {
     "mfto_simp_modulus": (C.c_int32, [_P, C.c_int32, _P, _P]),
     "mfto_kv": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     "mfto_jacobi_diag": (C.c_int32, [_P, C.c_int32, _P, _P]),
+    "mfto_set_kv_variant": (C.c_int32, [_P, C.c_int32]),
     "mfto_pcg": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
     "mfto_filter": (C.c_int32, [_P, _P, _P, C.c_int32]),
     "mfto_compliance_sens": (C.c_int32, [_P, _P, _P, C.POINTER(C.c_double), _P]),
     "mfto_oc_update": (C.c_int32, [_P, _P, _P, _P, C.POINTER(IterStats)]),
     "mfto_simp_step": (C.c_int32, [_P, _P, _P, _P, _P, C.POINTER(IterStats)]),
+    "mfto_launch_count": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
+    "mfto_fma_probe": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "mfto_kv_timing": (C.c_int32, [_P, C.c_int32]),
     "mfto_kv_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 }
@@ -141,6 +144,16 @@ def filter_stencil(rmin):
     _check("mfto_filter_stencil",
            lib().mfto_filter_stencil(rmin, n.value, off.ctypes.data, w.ctypes.data, C.byref(n)))
     return off.reshape(-1, 3), w
+
+
+def fma_probe(form=FORM_F64, blocks=0, iters=4096):
+    """FMA-pipe peak probe: returns (FMA/s, elapsed ms)."""
+    import torch
+    if blocks <= 0:
+        blocks = 8 * torch.cuda.get_device_properties(0).multi_processor_count
+    ms = C.c_double()
+    _check("mfto_fma_probe", lib().mfto_fma_probe(form, blocks, iters, C.byref(ms)))
+    return blocks * 256.0 * iters * 8 / (ms.value * 1e-3), ms.value
 
 
 # ----------------------------------------------------------------- the handle
@@ -225,6 +238,9 @@ class Handle:
             self._h, form, _ptr(E, dt, self.n_elem, "E"), _ptr(v, dt, self.n_dof, "v"),
             _ptr(y, dt, self.n_dof, "y")), self._h)
 
+    def set_kv_variant(self, variant: int):
+        _check("mfto_set_kv_variant", lib().mfto_set_kv_variant(self._h, variant), self._h)
+
     def jacobi_diag(self, E, d, form=FORM_F64):
         dt = self._dt(form)
         _check("mfto_jacobi_diag", lib().mfto_jacobi_diag(
@@ -274,6 +290,11 @@ class Handle:
         return st
 
     # ---- timing
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        _check("mfto_launch_count", lib().mfto_launch_count(self._h, C.byref(n)), self._h)
+        return n.value
+
     def kv_timing(self, on: bool):
         _check("mfto_kv_timing", lib().mfto_kv_timing(self._h, 1 if on else 0), self._h)
 

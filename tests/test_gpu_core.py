@@ -29,9 +29,13 @@ def _rel_inf(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-@pytest.mark.parametrize("shape", MESHES)
+MESHES_BIG = [(40, 30, 9), (17, 13, 33)]   # several tiles and z-chunks, ragged edges
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("shape", MESHES + MESHES_BIG)
 @pytest.mark.parametrize("face", ["x0", "z0"])
-def test_kv_f64(cuda, shape, face):
+def test_kv_f64(cuda, shape, face, variant):
     import torch
     from paper_2604_18020_gb300 import mfto
     m, fixed, edof, fd = _setup(*shape, face)
@@ -40,6 +44,7 @@ def test_kv_f64(cuda, shape, face):
     E = fem.simp_modulus(rho, 3.0)
     v = W.vec_random(m.n_dof, seed=12)
     with mfto.Handle(*shape, fixed) as h:
+        h.set_kv_variant(variant)
         y = torch.empty(m.n_dof, dtype=torch.float64, device=cuda)
         h.kv(torch.tensor(E, device=cuda), torch.tensor(v, device=cuda), y)
         got = y.cpu().numpy()
@@ -49,8 +54,9 @@ def test_kv_f64(cuda, shape, face):
     assert np.array_equal(got[fd], v[fd])
 
 
-@pytest.mark.parametrize("shape", MESHES)
-def test_kv_f32(cuda, shape):
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("shape", MESHES + MESHES_BIG)
+def test_kv_f32(cuda, shape, variant):
     import torch
     from paper_2604_18020_gb300 import mfto
     m, fixed, edof, fd = _setup(*shape)
@@ -58,6 +64,7 @@ def test_kv_f32(cuda, shape):
     E32 = fem.simp_modulus(W.rho_random(m, seed=21), 3.0).astype(np.float32)
     v32 = W.vec_random(m.n_dof, seed=22).astype(np.float32)
     with mfto.Handle(*shape, fixed) as h:
+        h.set_kv_variant(variant)
         y = torch.empty(m.n_dof, dtype=torch.float32, device=cuda)
         h.kv(torch.tensor(E32, device=cuda), torch.tensor(v32, device=cuda), y,
              form=mfto.FORM_F32)
@@ -66,8 +73,10 @@ def test_kv_f32(cuda, shape):
     assert _rel_inf(got, ref) <= 1e-5
 
 
-def test_kv_full_size_f64(cuda):
-    """120x60x30 (216,000 elements, 686,433 DOFs): the whole output."""
+@pytest.mark.parametrize("form", ["f64", "f32"])
+def test_kv_full_size(cuda, form):
+    """120x60x30 (216,000 elements, 686,433 DOFs), the launch configuration
+    the benchmark times: the whole output against the oracle."""
     import torch
     from paper_2604_18020_gb300 import mfto
     P = W.cantilever(120, 60, 30)
@@ -76,11 +85,54 @@ def test_kv_full_size_f64(cuda):
     fd = fem.dof_mask(P.fixed)
     E = fem.simp_modulus(W.rho_random(m, seed=1), 3.0)
     v = W.vec_random(m.n_dof, seed=2)
+    dt, tol = (torch.float64, 1e-12) if form == "f64" else (torch.float32, 1e-5)
+    if form == "f32":
+        E, v = E.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64)
     with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
-        y = torch.empty(m.n_dof, dtype=torch.float64, device=cuda)
-        h.kv(torch.tensor(E, device=cuda), torch.tensor(v, device=cuda), y)
+        y = torch.empty(m.n_dof, dtype=dt, device=cuda)
+        h.kv(torch.tensor(E, dtype=dt, device=cuda), torch.tensor(v, dtype=dt, device=cuda), y,
+             form=mfto.FORMS[form])
+        got = y.cpu().numpy().astype(np.float64)
+    assert _rel_inf(got, fem.kv(fem.ke_exact(), E, edof, v, fd)) <= tol
+
+
+def test_kv_sampled_at_4_9M_elements(cuda):
+    """256x128x150 (4,915,200 elements): sampled outputs, each recomputed by
+    the oracle from its own 27-node neighbourhood."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(256, 128, 150, 0.12)
+    m = P.mesh
+    rng = np.random.default_rng(0)
+    E = torch.rand(m.n_elem, dtype=torch.float64, device=cuda, generator=torch.Generator(
+        device=cuda).manual_seed(1)) + 0.01
+    v = torch.rand(m.n_dof, dtype=torch.float64, device=cuda, generator=torch.Generator(
+        device=cuda).manual_seed(2)) * 2 - 1
+    with mfto.Handle(256, 128, 150, P.fixed) as h:
+        y = torch.empty_like(v)
+        h.kv(E, v, y)
         got = y.cpu().numpy()
-    assert _rel_inf(got, fem.kv(fem.ke_exact(), E, edof, v, fd)) <= 1e-12
+    Eh, vh = E.cpu().numpy(), v.cpu().numpy()
+    KE = fem.ke_exact()
+    nx, ny = m.nelx + 1, m.nely + 1
+    fixed = fem.dof_mask(P.fixed)
+    picks = list(rng.integers(0, m.n_node, 300)) + [0, m.n_node - 1, nx - 1, nx * ny * 75 + 5]
+    for n in picks:
+        i, j, k = n % nx, (n // nx) % ny, n // (nx * ny)
+        acc = np.zeros(3)
+        for ce in range(8):
+            ei, ej, ek = i - 1 + (ce & 1), j - 1 + ((ce >> 1) & 1), k - 1 + (ce >> 2)
+            if not (0 <= ei < m.nelx and 0 <= ej < m.nely and 0 <= ek < m.nelz):
+                continue
+            e = ei + m.nelx * (ej + m.nely * ek)
+            nodes = [(ei + (l & 1)) + nx * ((ej + ((l >> 1) & 1)) + ny * (ek + (l >> 2)))
+                     for l in range(8)]
+            dofs = np.array([3 * nd + c for nd in nodes for c in range(3)])
+            ue = np.where(fixed[dofs], 0.0, vh[dofs])
+            ln = (i - ei) + 2 * (j - ej) + 4 * (k - ek)
+            acc += Eh[e] * (KE[3 * ln:3 * ln + 3] @ ue)
+        ref = np.where(fixed[3 * n:3 * n + 3], vh[3 * n:3 * n + 3], acc)
+        assert np.abs(got[3 * n:3 * n + 3] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
 
 
 def test_kv_contrast_and_bounds(cuda):
@@ -102,10 +154,10 @@ def test_kv_contrast_and_bounds(cuda):
 def test_kv_deterministic(cuda):
     import torch
     from paper_2604_18020_gb300 import mfto
-    m, fixed, _, _ = _setup(24, 12, 12)
+    m, fixed, _, _ = _setup(40, 30, 9)
     E = torch.tensor(fem.simp_modulus(W.rho_random(m, seed=3), 3.0), device=cuda)
     v = torch.tensor(W.vec_random(m.n_dof, seed=4), device=cuda)
-    with mfto.Handle(24, 12, 12, fixed) as h:
+    with mfto.Handle(40, 30, 9, fixed) as h:
         outs = []
         for _ in range(3):
             y = torch.empty_like(v)
@@ -259,3 +311,19 @@ def test_simp_20_iterations(cuda):
             cs.append(st.compliance)
     assert abs(cs[-1] - hist.compliance[-1]) / hist.compliance[-1] <= 1e-6
     assert np.allclose(cs, hist.compliance, rtol=1e-6)
+
+
+def test_oc_unreachable_target_terminates(cuda):
+    """All sensitivities zero: the bisection must stop (bracket collapse) and
+    return the lower move limits, like the oracle."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    m, fixed, _, _ = _setup(8, 4, 4)
+    rho = np.full(m.n_elem, 0.3)
+    ref, _ = osimp.oc_update(rho, np.zeros(m.n_elem), 0.3, 0.2)
+    with mfto.Handle(8, 4, 4, fixed) as h:
+        out = torch.empty(m.n_elem, dtype=torch.float64, device=cuda)
+        h.oc_update(torch.tensor(rho, device=cuda), torch.zeros(m.n_elem, dtype=torch.float64,
+                                                                device=cuda), out)
+        got = out.cpu().numpy()
+    assert np.array_equal(got, ref)
