@@ -56,7 +56,8 @@ enum {
   MFTO_NOT_CONVERGED = 4,   /* iteration cap reached before the tolerance */
   MFTO_STALLED = 5,         /* residual stopped decreasing (IR / FPCG)    */
   MFTO_BREAKDOWN = 6,       /* NaN/Inf or non-positive curvature in CG    */
-  MFTO_UNSUPPORTED = 7      /* form or feature not available             */
+  MFTO_UNSUPPORTED = 7,     /* form or feature not available             */
+  MFTO_TOO_LARGE = 8        /* problem exceeds a fixed capacity          */
 };
 
 /* Arithmetic forms of the K.v contraction. */
@@ -231,6 +232,38 @@ mfto_status mfto_kv_timing_read(mfto_handle* h, int64_t* launches,
 /* Number of kernels the library has launched for this handle so far (the
  * kernel nodes of every launched CUDA graph included). */
 mfto_status mfto_launch_count(const mfto_handle* h, int64_t* n);
+
+/* ------------------------------------------------- no-allocation variant -- */
+
+/* mfto_compliance_sens for callers that cannot allocate device memory: the
+ * same c = sum_e E_e u_e^T KE u_e and (if d_dc is not NULL)
+ * d_dc[e] = -p rho_e^(p-1) (E0 - Emin) u_e^T KE u_e, computed without a
+ * handle and without any cudaMalloc, cudaFree or allocating library call.
+ * It exists for programs whose device memory belongs entirely to another
+ * allocator (a framework's caching pool, a budget reserved at start-up) and
+ * for latency-bound loops that cannot accept the device-wide synchronisation
+ * an allocation may cause.  The paper has no counterpart to this entry point.
+ *
+ * mesh: the structured grid (elements per axis, edge h); E0, Emin, nu, penal:
+ * as in mfto_params; d_rho_phys [n_elem], d_u [n_dof], d_dc [n_elem] or NULL:
+ * device arrays in the layouts of this header, owned by the caller; h_c_out:
+ * host double receiving c; stream: cudaStream_t of the work (0 = legacy
+ * default), synchronised before returning.
+ *
+ * Capacity: the only scratch is one file-scope device array of 21 KB (unit
+ * KE, 2048 per-block partial sums, a ticket and the result) that every GPU
+ * which loads the library holds until the process exits; meshes of more than
+ * 2048 x 256 = 524,288 elements are rejected with MFTO_TOO_LARGE.  The first
+ * call on a device looks up the array's device address (set-up); make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (the ticket is cleared by every call), so
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  Returns MFTO_INVALID_ARG for null
+ * pointers or bad sizes or parameters, MFTO_CUDA_ERROR on a CUDA failure. */
+mfto_status mfto_compliance_sens_noalloc(const mfto_mesh* mesh, double E0, double Emin,
+                                         double nu, double penal, const double* d_rho_phys,
+                                         const double* d_u, double* d_dc, double* h_c_out,
+                                         void* stream);
 
 /* ------------------------------------------------------- measurement aid -- */
 

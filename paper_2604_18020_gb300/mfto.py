@@ -17,9 +17,11 @@ import numpy as np
 HERE = Path(__file__).resolve().parent
 LIB_PATH = HERE / "libmfto.so"
 
-OK, INVALID_ARG, CUDA_ERROR, OOM, NOT_CONVERGED, STALLED, BREAKDOWN, UNSUPPORTED = range(8)
+(OK, INVALID_ARG, CUDA_ERROR, OOM, NOT_CONVERGED, STALLED, BREAKDOWN, UNSUPPORTED,
+ TOO_LARGE) = range(9)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA_ERROR", 3: "OOM", 4: "NOT_CONVERGED",
-                5: "STALLED", 6: "BREAKDOWN", 7: "UNSUPPORTED"}
+                5: "STALLED", 6: "BREAKDOWN", 7: "UNSUPPORTED", 8: "TOO_LARGE"}
+NOALLOC_MAX_ELEMENTS = 2048 * 256
 
 FORM_F64, FORM_F32 = 0, 1
 FORMS = {"f64": FORM_F64, "f32": FORM_F32}
@@ -82,6 +84,9 @@ SIGNATURES = {
     "mfto_simp_step": (C.c_int32, [_P, _P, _P, _P, _P, C.POINTER(IterStats)]),
     "mfto_launch_count": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
     "mfto_fma_probe": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "mfto_compliance_sens_noalloc": (C.c_int32, [C.POINTER(Mesh), C.c_double, C.c_double,
+                                                 C.c_double, C.c_double, _P, _P, _P,
+                                                 C.POINTER(C.c_double), _P]),
     "mfto_kv_timing": (C.c_int32, [_P, C.c_int32]),
     "mfto_kv_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 }
@@ -154,6 +159,30 @@ def fma_probe(form=FORM_F64, blocks=0, iters=4096):
     ms = C.c_double()
     _check("mfto_fma_probe", lib().mfto_fma_probe(form, blocks, iters, C.byref(ms)))
     return blocks * 256.0 * iters * 8 / (ms.value * 1e-3), ms.value
+
+
+def compliance_sens_noalloc(nelx, nely, nelz, rho_phys, u, dc=None, E0=1.0, Emin=1e-9,
+                            nu=0.3, penal=3.0, h=1.0, stream=None) -> float:
+    """Compliance (returned) and sensitivities (into dc) without a handle and
+    without any device allocation by the library; see
+    mfto_compliance_sens_noalloc in include/mfto.h for who needs it, its
+    524,288-element capacity and why overlapping calls race."""
+    import torch
+    n_elem = nelx * nely * nelz
+    n_dof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    c = C.c_double()
+    m = Mesh(nelx, nely, nelz, h)
+    code = lib().mfto_compliance_sens_noalloc(
+        C.byref(m), E0, Emin, nu, penal, _ptr(rho_phys, torch.float64, n_elem, "rho_phys"),
+        _ptr(u, torch.float64, n_dof, "u"), _ptr(dc, torch.float64, n_elem, "dc"), C.byref(c),
+        C.c_void_p(st.cuda_stream))
+    if code == TOO_LARGE:
+        raise MftoError("mfto_compliance_sens_noalloc", code,
+                        f"mesh has {n_elem} elements; this entry point takes at most "
+                        f"{NOALLOC_MAX_ELEMENTS}")
+    _check("mfto_compliance_sens_noalloc", code)
+    return c.value
 
 
 # ----------------------------------------------------------------- the handle
