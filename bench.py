@@ -47,6 +47,13 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
 REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
 
+def measured_hbm_gbs():
+    try:
+        return float(json.loads((ROOT / "MEASURED_PEAKS.json").read_text())["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0          # the profiling recipe's fallback figure
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -185,6 +192,8 @@ def gpu_bench(args, rank, local_rank, world):
     m = P.mesh
     params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
+    if args.form == "mixed":
+        h.set_solver(mfto.FORM_F32, args.inner_tol)
     rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     f = torch.tensor(P.f, device=dev)
@@ -212,9 +221,10 @@ def gpu_bench(args, rank, local_rank, world):
             total_ms += a.elapsed_time(b)
             stats.append(st)
         launches = h.launch_count() - l0
-        kv_n, kv_ms = h.kv_timing_read()
+        kv64 = h.kv_timing_read(mfto.FORM_F64)
+        kv32 = h.kv_timing_read(mfto.FORM_F32)
         h.kv_timing(False)
-        return total_ms, stats, launches, kv_n, kv_ms
+        return total_ms, stats, launches, kv64, kv32
 
     if dist:
         dist.barrier()
@@ -228,10 +238,12 @@ def gpu_bench(args, rank, local_rank, world):
         t_ms = tt.item()
     clk = clocks.summary()
     # replay with events around every K.v launch (same steps, same state)
-    _, stats_b, _, kv_n, kv_ms = timed_pass(True)
+    _, stats_b, _, kv64, kv32 = timed_pass(True)
     cg = [s.cg_iterations for s in stats]
     assert cg == [s.cg_iterations for s in stats_b], "replay diverged"
-    kv_per_pass = kv_n
+    kv_per_pass = kv64[0] + kv32[0]
+    dom = kv32 if args.form == "mixed" else kv64       # the K.v that dominates the step
+    kv_n, kv_ms = dom
 
     # e2e: public API from pinned host buffers, copies inside the timed region
     h_rho = rho0.cpu().pin_memory()
@@ -268,29 +280,46 @@ def gpu_bench(args, rank, local_rank, world):
     kv_avg_s = kv_ms * 1e-3 / max(kv_n, 1)
     sm_mhz = clk["sm_mhz"] or 1950.0
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    fp64_peak_tflops = n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12   # 2 DFMA/clk/SM, measured clock
-    achieved = FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12
+    if args.form == "mixed":
+        # FP32 CG K.v: reads z, p_old (FP32 DOF vectors), E (FP32), the node
+        # mask; writes p_new, q: 4 x 12 B per node + 4 B + 1 B per node
+        bytes_per_launch = m.n_node * (4 * 12 + 1) + 4 * m.n_elem
+        peak = measured_hbm_gbs()
+        roof = {"bound": "hbm", "achieved": bytes_per_launch / kv_avg_s / 1e9, "peak": peak,
+                "unit": "GB/s", "traffic": None, "kernel": "pcg_kv_tile_kernel<float>",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy benchmark), of measured",
+                "bytes_per_launch": bytes_per_launch}
+    else:
+        fp64_peak_tflops = n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12   # 2 DFMA/clk/SM, measured clock
+        roof = {"bound": "alu", "achieved": FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12,
+                "peak": fp64_peak_tflops, "unit": "TFLOP/s", "traffic": None,
+                "kernel": "pcg_kv_tile_kernel<double>",
+                "peak_source": f"FP64 FMA pipe, {n_sm} SMs x 2 DFMA/clk x 2 flop x "
+                               f"{sm_mhz:.0f} MHz median SM clock under load",
+                "flop_per_elem": FLOP_PER_ELEM}
+    roof["frac"] = roof["achieved"] / roof["peak"]
     out = {
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.form == "f64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": m.n_elem, "dofs": m.n_dof,
-                   "form": "f64", "pcg_rtol": 1e-8, "kv_kernel": "tiled mode-space",
+                   "form": args.form, "pcg_rtol": 1e-8,
+                   "inner_tol": args.inner_tol if args.form == "mixed" else None,
+                   "kv_kernel": "tiled mode-space",
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "simp_iter_ms": t_ms / args.steps,
         "cg_iterations": cg,
         "compliance": [s.compliance for s in stats],
         "kv_per_step": kv_per_pass / args.steps,
+        "kv_f64_per_step": kv64[0] / args.steps,
+        "kv_f32_per_step": kv32[0] / args.steps,
         "kv_kernel_us": kv_avg_s * 1e6,
         "kv_kernel_gelem_s": m.n_elem / kv_avg_s / 1e9,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / fp64_peak_tflops, "traffic": None,
-                     "kernel": "pcg_kv_tile_kernel<double>",
-                     "peak_source": f"FP64 FMA pipe, {n_sm} SMs x 2 DFMA/clk x 2 flop x "
-                                    f"{sm_mhz:.0f} MHz median SM clock under load",
-                     "flop_per_elem": FLOP_PER_ELEM},
+        "kv_f64_kernel_us": kv64[1] * 1e3 / max(kv64[0], 1),
+        "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -318,6 +347,8 @@ def profile_run(args):
     params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8,
                                  maxit=args.maxit if args.mode == "pcg" else 10000)
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
+    if args.form == "mixed":
+        h.set_solver(mfto.FORM_F32, args.inner_tol)
     f = torch.tensor(P.f, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     if args.mode == "profile":
@@ -345,6 +376,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "profile", "pcg"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--form", default="f64", choices=["f64", "mixed"],
+                    help="f64: plain FP64 Jacobi-PCG; mixed: FP64 iterative refinement "
+                         "around an FP32 inner PCG")
+    ap.add_argument("--inner-tol", type=float, default=1e-2)
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--maxit", type=int, default=40, help=argparse.SUPPRESS)
     args = ap.parse_args()

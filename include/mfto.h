@@ -102,6 +102,17 @@ typedef struct {
   double rel_residual;
 } mfto_iter_stats;
 
+typedef struct {
+  int32_t outer_iterations; /* FP64 residual evaluations that led to a correction */
+  int32_t inner_iterations; /* CG iterations of all inner solves               */
+  int32_t status;           /* MFTO_OK, MFTO_NOT_CONVERGED, MFTO_STALLED,       */
+                            /* MFTO_BREAKDOWN                                   */
+  int32_t kv_f64;           /* FP64 K.v applications (outer residuals)          */
+  double rel_residual;      /* true FP64 ||f - K u|| / ||f|| at exit            */
+  double fnorm;             /* ||f||                                            */
+  double history[64];       /* rel. residual before each outer step (first 64)  */
+} mfto_ir_stats;
+
 typedef struct mfto_handle mfto_handle;
 
 /* Library version string (static storage). */
@@ -184,6 +195,30 @@ mfto_status mfto_jacobi_diag(mfto_handle* h, mfto_form form, const void* d_E,
 mfto_status mfto_pcg(mfto_handle* h, const double* d_E, const double* d_f,
                      double* d_u, mfto_solve_stats* st);
 
+/* Mixed-precision solve of K(E) u = f: FP64 iterative refinement (Sec. 3.5's
+ * residual correction, with the outer loop in FP64) around an inner
+ * Jacobi-PCG in a lower precision:
+ *   r = f - K u in FP64 (FP64 K.v);  stop if ||r|| <= rtol ||f||;
+ *   solve K e = r approximately with the inner PCG (inner form K.v, FP32
+ *   vectors, FP64 dot products) to ||r_e|| <= inner_tol ||r||, from e = 0;
+ *   u += e in FP64.
+ * d_E and d_f FP64; d_u FP64, initial guess on entry, solution on exit.
+ * Stops with MFTO_STALLED when the outer residual fails twice in a row to fall
+ * below 0.9 of its previous value (the stagnation the paper reports for BF16),
+ * MFTO_NOT_CONVERGED after max_outer corrections (mfto_set_solver).
+ * inner: MFTO_FORM_F32.  Returns MFTO_OK also when not converged; see
+ * st->status.  Synchronises the stream. */
+mfto_status mfto_ir_solve(mfto_handle* h, mfto_form inner, double inner_tol,
+                          const double* d_E, const double* d_f, double* d_u,
+                          mfto_ir_stats* st);
+
+/* Select the linear solver of mfto_simp_step: form MFTO_FORM_F64 = plain FP64
+ * Jacobi-PCG (default); any other form = mfto_ir_solve with that inner form,
+ * inner tolerance inner_tol (> 0, < 1), inner iteration cap inner_maxit and
+ * at most max_outer corrections. */
+mfto_status mfto_set_solver(mfto_handle* h, mfto_form form, double inner_tol,
+                            int32_t inner_maxit, int32_t max_outer);
+
 /* Cone density filter (Sec. 3.1): transpose = 0 gives
  * d_y = (H d_x) / W;  transpose = 1 gives d_y = H (d_x / W)
  * (the chain rule for sensitivities).  FP64, element fields. */
@@ -222,11 +257,14 @@ mfto_status mfto_simp_step(mfto_handle* h, double* d_rho, double* d_u,
 /* ------------------------------------------------------------- timing -- */
 
 /* When on, every K.v launch issued by the library on this handle is
- * bracketed by CUDA events on the handle's stream; mfto_kv_timing_read
- * synchronises and returns the number of timed launches and their summed
- * device time in milliseconds, then resets the accumulators. */
+ * bracketed by CUDA events on the handle's stream (inside the captured CG
+ * graphs as external event nodes); mfto_kv_timing_read synchronises and
+ * returns, for the K.v launches of one form (MFTO_FORM_F64 or MFTO_FORM_F32;
+ * the mixed solver runs both), the number of timed launches that did work
+ * and their summed device time in milliseconds, then resets that form's
+ * accumulators. */
 mfto_status mfto_kv_timing(mfto_handle* h, int32_t on);
-mfto_status mfto_kv_timing_read(mfto_handle* h, int64_t* launches,
+mfto_status mfto_kv_timing_read(mfto_handle* h, mfto_form form, int64_t* launches,
                                 double* total_ms);
 
 /* Number of kernels the library has launched for this handle so far (the

@@ -24,6 +24,7 @@ struct ModeCoef {
 #define MFTO_BLOCK 256            // threads per block of the element/node kernels
 #define MFTO_RED_MAX_BLOCKS 1024  // grid cap of the grid-stride vector kernels
 #define MFTO_RED_SLOTS 16384      // partial-sum slots per row of one grid reduction
+#define MFTO_PCG_SLOTS 2          // cached PCG graphs: FP64 solver, FP32 inner solver
 
 // Device-resident scalars of the PCG driver and the other reductions.  Each
 // reduction site owns a ticket counter (reset by the last block).
@@ -49,9 +50,10 @@ struct MiscScalars {
 
 struct KvEventPool {
   std::vector<cudaEvent_t> start, stop;
+  std::vector<int> form;      // form index (0 FP64, 1 FP32) of each recorded pair
   int used = 0;
-  int64_t launches = 0;
-  double total_ms = 0.0;
+  int64_t launches[2] = {0, 0};
+  double total_ms[2] = {0.0, 0.0};
 };
 
 struct mfto_handle {
@@ -68,6 +70,7 @@ struct mfto_handle {
   ModeCoef<double> mc64;    // mode-space element operator (kv_tile.cuh)
   ModeCoef<float> mc32;
   int kv_variant;           // 0: tiled mode-space kernel, 1: node-centric dense KE
+  int occ_kv32, occ_pcg32;  // resident CTAs per SM of the FP32 block kernels
   uint8_t* d_fixed;         // per-node mask
   // cone filter
   int32_t n_stencil;
@@ -84,8 +87,17 @@ struct mfto_handle {
   MiscScalars* h_misc;      // pinned mirror
   // SIMP step workspace
   double *d_rho_phys, *d_E, *d_dc, *d_dc_phys;
-  // PCG graph cache (one captured chunk of check_every iterations)
-  struct PcgGraph* pcg_graph;
+  // FP32 workspace of the inner solve of the iterative refinement
+  float *d_r32, *d_z32, *d_p0_32, *d_p1_32, *d_q32, *d_dinv32, *d_e32, *d_E32;
+  PcgScalars* d_pcg32;
+  PcgScalars* h_pcg32;      // pinned mirror
+  // solver used by mfto_simp_step (mfto_set_solver)
+  int32_t solver_form;      // MFTO_FORM_F64: plain FP64 PCG; else IR with this inner form
+  double inner_tol;
+  int32_t inner_maxit;
+  int32_t max_outer;
+  // PCG graph cache: one captured chunk of check_every iterations per solver
+  struct PcgGraph* pcg_graph[MFTO_PCG_SLOTS];
   // kernels launched on behalf of this handle (graph kernel nodes included)
   int64_t launches;
   // timing
@@ -166,6 +178,68 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   }
   return v;
 }
+
+// Dot-product accumulators.  FP64 vectors accumulate in FP64.  FP32 vectors
+// accumulate in double-float (an unevaluated sum hi + lo of two FP32 values,
+// ~48-bit significand): each product is split exactly with an FMA
+// (TwoProduct), sums use TwoSum, a warp combines its 32 pairs with shuffles,
+// and only then is the pair converted to FP64 for the block and grid sums.
+// On this GPU the FP64 pipe, conversions included, runs at a small fraction
+// of the FP32 rate, so one conversion per warp instead of one FP64
+// operation per term keeps the reductions off the critical path without
+// giving up FP64-level accuracy.
+struct DFloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DFloat df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float err = (a - (s - bb)) + (b - bb);
+  return {s, err};
+}
+
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+  DFloat s = df_two_sum(a.hi, b.hi);
+  const float lo = s.lo + a.lo + b.lo;
+  const float hi = s.hi + lo;
+  return {hi, lo - (hi - s.hi)};
+}
+
+__device__ __forceinline__ DFloat df_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+
+template <typename T>
+struct DotAcc;
+
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s += a * b; }
+  // every thread returns its own FP64 partial
+  __device__ __forceinline__ double finish() const { return s; }
+};
+
+template <>
+struct DotAcc<float> {
+  DFloat s{0.f, 0.f};
+  __device__ __forceinline__ void add_prod(float a, float b) { s = df_add(s, df_prod(a, b)); }
+  // must be called by all 32 lanes of the warp: lane 0 returns the warp's
+  // sum in FP64, the other lanes 0
+  __device__ __forceinline__ double finish() const {
+    DFloat v = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      DFloat w;
+      w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+      w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+      v = df_add(v, w);
+    }
+    return (threadIdx.x & 31) == 0 ? (double)v.hi + (double)v.lo : 0.0;
+  }
+};
 
 // Publish K per-block partial sums and let the last block to arrive reduce
 // them in block-index order.  Returns true in every thread of that last
@@ -255,6 +329,22 @@ mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc,
                       double* rho_new, mfto_iter_stats* st);
 mfto_status pcg_run(mfto_handle* h, const double* E, const double* f,
                     double* u, mfto_solve_stats* st);
+mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const double* E,
+                   const double* f, double* u, mfto_ir_stats* st);
+
+// The vectors of one PCG solve (see pcg.cu).
+template <typename T>
+struct PcgVecs {
+  const T* E;
+  T *u, *r, *z, *p0, *p1, *q, *dinv;
+  PcgScalars* s;
+  double *part_a, *part_b;
+};
+template <typename T>
+mfto_status pcg_start(mfto_handle* h, const PcgVecs<T>& v, const T* rhs, const T* Ku, double rtol,
+                      int maxit);
+template <typename T>
+mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalars* host_s);
 void pcg_graph_release(mfto_handle* h);
 mfto_status kv_tile_init(mfto_handle* h);
 template <typename T>
@@ -262,6 +352,6 @@ mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStr
 template <typename T>
 mfto_status pcg_kv_tile_launch(mfto_handle* h, const T* E, const T* z, const T* p_old, T* p_new,
                                T* q, PcgScalars* s, double* partials, cudaStream_t st);
-void kv_timing_begin(mfto_handle* h);
+void kv_timing_begin(mfto_handle* h, int form);
 void kv_timing_end(mfto_handle* h);
 mfto_status kv_timing_harvest(mfto_handle* h, bool sync);

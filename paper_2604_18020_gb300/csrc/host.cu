@@ -126,12 +126,14 @@ static void free_handle(mfto_handle* h) {
   void* ptrs[] = {h->d_ke64, h->d_ke32, h->d_fixed, h->d_stencil_off, h->d_stencil_w,
                   h->d_filter_W, h->d_r, h->d_z, h->d_p0, h->d_p1, h->d_q, h->d_dinv,
                   h->d_partials, h->d_partials2, h->d_pcg, h->d_misc, h->d_rho_phys,
-                  h->d_E, h->d_dc, h->d_dc_phys};
+                  h->d_E, h->d_dc, h->d_dc_phys, h->d_r32, h->d_z32, h->d_p0_32,
+                  h->d_p1_32, h->d_q32, h->d_dinv32, h->d_e32, h->d_E32, h->d_pcg32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->h_pcg) cudaFreeHost(h->h_pcg);
   if (h->h_misc) cudaFreeHost(h->h_misc);
+  if (h->h_pcg32) cudaFreeHost(h->h_pcg32);
   for (size_t i = 0; i < h->ev.start.size(); ++i) {
     cudaEventDestroy(h->ev.start[i]);
     cudaEventDestroy(h->ev.stop[i]);
@@ -211,6 +213,10 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   if (h->n_dof > (int64_t)INT32_MAX) { free_handle(h); return MFTO_INVALID_ARG; }
   if (check_params(h, params) != MFTO_OK) { free_handle(h); return MFTO_INVALID_ARG; }
   h->p = *params;
+  h->solver_form = MFTO_FORM_F64;
+  h->inner_tol = 1e-2;
+  h->inner_maxit = 10000;
+  h->max_outer = 50;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -240,8 +246,19 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   A((void**)&h->d_E, ne);
   A((void**)&h->d_dc, ne);
   A((void**)&h->d_dc_phys, ne);
+  const size_t nd32 = sizeof(float) * h->n_dof;
+  A((void**)&h->d_r32, nd32);
+  A((void**)&h->d_z32, nd32);
+  A((void**)&h->d_p0_32, nd32);
+  A((void**)&h->d_p1_32, nd32);
+  A((void**)&h->d_q32, nd32);
+  A((void**)&h->d_dinv32, nd32);
+  A((void**)&h->d_e32, nd32);
+  A((void**)&h->d_E32, sizeof(float) * h->n_elem);
+  A((void**)&h->d_pcg32, sizeof(PcgScalars));
   if (ok && (cudaMallocHost(&h->h_pcg, sizeof(PcgScalars)) != cudaSuccess ||
-             cudaMallocHost(&h->h_misc, sizeof(MiscScalars)) != cudaSuccess))
+             cudaMallocHost(&h->h_misc, sizeof(MiscScalars)) != cudaSuccess ||
+             cudaMallocHost(&h->h_pcg32, sizeof(PcgScalars)) != cudaSuccess))
     ok = false;
   if (!ok) {
     cudaGetLastError();
@@ -250,7 +267,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   }
   if (cudaMemcpyAsync(h->d_fixed, h_fixed, h->n_node, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_pcg, 0, sizeof(PcgScalars), h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->d_misc, 0, sizeof(MiscScalars), h->stream) != cudaSuccess) {
+      cudaMemsetAsync(h->d_misc, 0, sizeof(MiscScalars), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->d_pcg32, 0, sizeof(PcgScalars), h->stream) != cudaSuccess) {
     free_handle(h);
     return MFTO_CUDA_ERROR;
   }
@@ -292,7 +310,7 @@ extern "C" mfto_status mfto_sizes(const mfto_handle* h, int64_t* ne, int64_t* nn
 // ------------------------------------------------------------ K.v timing
 static const int kEventPool = 4096;
 
-void kv_timing_begin(mfto_handle* h) {
+void kv_timing_begin(mfto_handle* h, int form) {
   if (!h->kv_timing) return;
   if (h->ev.used >= kEventPool) kv_timing_harvest(h, true);
   if ((int)h->ev.start.size() <= h->ev.used) {
@@ -301,7 +319,9 @@ void kv_timing_begin(mfto_handle* h) {
     cudaEventCreate(&b);
     h->ev.start.push_back(a);
     h->ev.stop.push_back(b);
+    h->ev.form.push_back(0);
   }
+  h->ev.form[h->ev.used] = form == MFTO_FORM_F64 ? 0 : 1;
   cudaEventRecord(h->ev.start[h->ev.used], h->stream);
 }
 
@@ -317,8 +337,8 @@ mfto_status kv_timing_harvest(mfto_handle* h, bool sync) {
   for (int i = 0; i < h->ev.used; ++i) {
     float ms = 0.f;
     MFTO_CUDA(h, cudaEventElapsedTime(&ms, h->ev.start[i], h->ev.stop[i]));
-    h->ev.total_ms += ms;
-    h->ev.launches++;
+    h->ev.total_ms[h->ev.form[i]] += ms;
+    h->ev.launches[h->ev.form[i]]++;
   }
   h->ev.used = 0;
   return MFTO_OK;
@@ -337,13 +357,16 @@ extern "C" mfto_status mfto_launch_count(const mfto_handle* h, int64_t* n) {
   return MFTO_OK;
 }
 
-extern "C" mfto_status mfto_kv_timing_read(mfto_handle* h, int64_t* launches,
+extern "C" mfto_status mfto_kv_timing_read(mfto_handle* h, mfto_form form, int64_t* launches,
                                            double* total_ms) {
   if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, form == MFTO_FORM_F64 || form == MFTO_FORM_F32,
+               "mfto_kv_timing_read: form must be F64 or F32");
   mfto_status s = kv_timing_harvest(h, true);
-  if (launches) *launches = h->ev.launches;
-  if (total_ms) *total_ms = h->ev.total_ms;
-  h->ev.launches = 0;
-  h->ev.total_ms = 0.0;
+  const int f = form == MFTO_FORM_F64 ? 0 : 1;
+  if (launches) *launches = h->ev.launches[f];
+  if (total_ms) *total_ms = h->ev.total_ms[f];
+  h->ev.launches[f] = 0;
+  h->ev.total_ms[f] = 0.0;
   return s;
 }

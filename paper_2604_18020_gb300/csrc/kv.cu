@@ -78,7 +78,7 @@ mfto_status kv_launch(mfto_handle* h, mfto_form form, const void* E, const void*
   const Grid g = make_grid(h->mesh);
   if (form != MFTO_FORM_F64 && form != MFTO_FORM_F32)
     return mfto_fail(h, MFTO_UNSUPPORTED, "mfto_kv: unsupported form %d", (int)form);
-  kv_timing_begin(h);
+  kv_timing_begin(h, form);
   h->launches++;
   if (h->kv_variant == 0) {
     mfto_status s = form == MFTO_FORM_F64

@@ -7,15 +7,31 @@ namespace {
 
 constexpr int kTX = 16, kTY = 12;   // owned nodes per CTA in x, y; 256 threads
 using Shape = TileShape<kTX, kTY>;
+
+// FP64 runs the z-streaming ring variant (bound by the FP64 pipe, little halo
+// recompute); FP32 runs the one-element-per-thread block variant (bound by
+// memory latency otherwise, so it trades halo arithmetic for parallelism).
+template <typename T>
+struct UseBlock { static constexpr bool value = sizeof(T) == 4; };
 static_assert(Shape::NE <= MFTO_BLOCK && Shape::NV <= MFTO_BLOCK, "tile larger than the block");
+
+template <typename T, typename Load, typename Epi>
+__device__ __forceinline__ double tile_body(const T* E, const uint8_t* fixed, const ModeCoef<T>& K,
+                                            const Grid& g, int nzc, const Load& ld, const Epi& epi,
+                                            T* smem) {
+  if constexpr (UseBlock<T>::value)
+    return kv_block_body<T>(E, fixed, K, g, ld, epi, smem);
+  else
+    return kv_tile_body<T, kTX, kTY>(E, fixed, K, g, nzc, ld, epi, smem);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(MFTO_BLOCK)
 kv_tile_kernel(const T* __restrict__ E, const T* __restrict__ v, T* __restrict__ y,
                const uint8_t* __restrict__ fixed, ModeCoef<T> K, Grid g, int nzc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  kv_tile_body<T, kTX, kTY>(E, fixed, K, g, nzc, TileLoadPlain<T>{v}, TileStore<T>{v, y},
-                            reinterpret_cast<T*>(smem_raw));
+  tile_body<T>(E, fixed, K, g, nzc, TileLoadPlain<T>{v}, TileStore<T>{v, y},
+               reinterpret_cast<T*>(smem_raw));
 }
 
 template <typename T>
@@ -28,8 +44,8 @@ pcg_kv_tile_kernel(const T* __restrict__ E, const T* __restrict__ z, const T* __
   __shared__ double sh[64];
   const T beta = (T)s->beta;
   double red[1];
-  red[0] = kv_tile_body<T, kTX, kTY>(E, fixed, K, g, nzc, TileLoadDirection<T>{z, p_old, beta},
-                                     TilePcg<T>{p_new, q}, reinterpret_cast<T*>(smem_raw));
+  red[0] = tile_body<T>(E, fixed, K, g, nzc, TileLoadDirection<T>{z, p_old, beta},
+                        TilePcg<T>{p_new, q}, reinterpret_cast<T*>(smem_raw));
   double tot[1];
   if (last_block_reduce<1>(red, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
     s->pq = tot[0];
@@ -44,8 +60,16 @@ pcg_kv_tile_kernel(const T* __restrict__ E, const T* __restrict__ z, const T* __
 }
 
 template <typename T>
-dim3 tile_grid(const mfto_handle* h, int* nzc_out) {
+dim3 tile_grid(const mfto_handle* h, int* nzc_out, int per_sm = 1) {
   const Grid g = make_grid(h->mesh);
+  if (UseBlock<T>::value) {
+    // grid-stride over 7 x 7 x 3 node blocks; one wave of resident CTAs
+    const int64_t nb = (int64_t)((g.nx + 6) / 7) * ((g.ny + 6) / 7) * ((g.nz + 2) / 3);
+    int64_t grid = (int64_t)per_sm * h->num_sms;
+    if (grid > nb) grid = nb;
+    *nzc_out = 0;
+    return dim3((unsigned)grid, 1, 1);
+  }
   const int tx = (g.nx + kTX - 1) / kTX, ty = (g.ny + kTY - 1) / kTY;
   const int target = (sizeof(T) == 8 ? 2 : 4) * h->num_sms;
   int zch = (target + tx * ty / 2) / (tx * ty);
@@ -55,17 +79,19 @@ dim3 tile_grid(const mfto_handle* h, int* nzc_out) {
   if (nzc < 4) nzc = g.nz < 4 ? g.nz : 4;
   int tz = (g.nz + nzc - 1) / nzc;
   // the CG form reduces one partial per block
-  while ((int64_t)tx * ty * tz > MFTO_RED_SLOTS) {
-    nzc *= 2;
-    tz = (g.nz + nzc - 1) / nzc;
-  }
+  if ((int64_t)tx * ty * tz > MFTO_RED_SLOTS) return dim3(0, 0, 0);
   *nzc_out = nzc;
   return dim3(tx, ty, tz);
 }
 
 template <typename T>
+size_t tile_smem() {
+  return UseBlock<T>::value ? BlockShape::smem_bytes<T>() : Shape::smem_bytes<T>();
+}
+
+template <typename T>
 mfto_status set_attrs(mfto_handle* h) {
-  const int smem = (int)Shape::smem_bytes<T>();
+  const int smem = (int)tile_smem<T>();
   MFTO_CUDA(h, cudaFuncSetAttribute(kv_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_tile_kernel<T>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -76,8 +102,15 @@ mfto_status set_attrs(mfto_handle* h) {
 
 mfto_status kv_tile_init(mfto_handle* h) {
   mfto_status s = set_attrs<double>(h);
+  if (s == MFTO_OK) s = set_attrs<float>(h);
   if (s != MFTO_OK) return s;
-  return set_attrs<float>(h);
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                   &h->occ_kv32, kv_tile_kernel<float>, MFTO_BLOCK, tile_smem<float>()));
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                   &h->occ_pcg32, pcg_kv_tile_kernel<float>, MFTO_BLOCK, tile_smem<float>()));
+  if (h->occ_kv32 < 1) h->occ_kv32 = 1;
+  if (h->occ_pcg32 < 1) h->occ_pcg32 = 1;
+  return MFTO_OK;
 }
 
 template <typename T>
@@ -90,8 +123,9 @@ const ModeCoef<float>& coef<float>(const mfto_handle* h) { return h->mc32; }
 template <typename T>
 mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStream_t st) {
   int nzc = 0;
-  const dim3 grid = tile_grid<T>(h, &nzc);
-  kv_tile_kernel<T><<<grid, MFTO_BLOCK, Shape::smem_bytes<T>(), st>>>(
+  const dim3 grid = tile_grid<T>(h, &nzc, h->occ_kv32);
+  if (grid.x == 0) return mfto_fail(h, MFTO_TOO_LARGE, "mesh too large for the K.v tiling");
+  kv_tile_kernel<T><<<grid, MFTO_BLOCK, tile_smem<T>(), st>>>(
       E, v, y, h->d_fixed, coef<T>(h), make_grid(h->mesh), nzc);
   MFTO_LAUNCH_CHECK(h);
   return MFTO_OK;
@@ -101,8 +135,9 @@ template <typename T>
 mfto_status pcg_kv_tile_launch(mfto_handle* h, const T* E, const T* z, const T* p_old, T* p_new,
                                T* q, PcgScalars* s, double* partials, cudaStream_t st) {
   int nzc = 0;
-  const dim3 grid = tile_grid<T>(h, &nzc);
-  pcg_kv_tile_kernel<T><<<grid, MFTO_BLOCK, Shape::smem_bytes<T>(), st>>>(
+  const dim3 grid = tile_grid<T>(h, &nzc, h->occ_pcg32);
+  if (grid.x == 0) return mfto_fail(h, MFTO_TOO_LARGE, "mesh too large for the K.v tiling");
+  pcg_kv_tile_kernel<T><<<grid, MFTO_BLOCK, tile_smem<T>(), st>>>(
       E, z, p_old, p_new, q, h->d_fixed, coef<T>(h), make_grid(h->mesh), nzc, s, partials);
   MFTO_LAUNCH_CHECK(h);
   return MFTO_OK;

@@ -102,7 +102,7 @@ struct TileStore {           // plain K.v: y = sum, y_fixed = v
   const T* v;
   T* y;
   __device__ __forceinline__ void operator()(int node, const T (&acc)[3], const T (&pn)[3],
-                                             uint8_t fm, double& red) const {
+                                             uint8_t fm, DotAcc<T>& red) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c) y[3 * node + c] = ((fm >> c) & 1) ? v[3 * node + c] : acc[c];
   }
@@ -113,13 +113,13 @@ struct TilePcg {             // CG: p_new stored, q = K p_new, p_new.q accumulat
   T* p_new;
   T* q;
   __device__ __forceinline__ void operator()(int node, const T (&acc)[3], const T (&pn)[3],
-                                             uint8_t fm, double& red) const {
+                                             uint8_t fm, DotAcc<T>& red) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T qc = ((fm >> c) & 1) ? pn[c] : acc[c];
       p_new[3 * node + c] = pn[c];
       q[3 * node + c] = qc;
-      red += (double)pn[c] * (double)qc;
+      red.add_prod(pn[c], qc);
     }
   }
 };
@@ -136,7 +136,8 @@ struct TileShape {
 };
 
 // Block (bx, by, bz) owns nodes [bx*TX, +TX) x [by*TY, +TY) x [bz*nzc, +nzc).
-// Returns the block's partial of the epilogue reduction (0 for plain K.v).
+// Returns this thread's share of the epilogue reduction (0 for plain K.v),
+// to be summed over the block.
 template <typename T, int TX, int TY, typename Load, typename Epi>
 __device__ __forceinline__ double kv_tile_body(const T* __restrict__ E,
                                                const uint8_t* __restrict__ fixed,
@@ -149,7 +150,7 @@ __device__ __forceinline__ double kv_tile_body(const T* __restrict__ E,
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * nzc;
   const int k_end = min(k0 + nzc, g.nz);   // owned node layers [k0, k_end)
-  double red = 0.0;
+  DotAcc<T> red;
 
   auto load_layer = [&](int nk) {
     T* dst = vs + ((nk + 3) % 3) * 3 * S::NV;
@@ -237,5 +238,116 @@ __device__ __forceinline__ double kv_tile_body(const T* __restrict__ E,
     }
     cur ^= 1;
   }
-  return red;
+  return red.finish();
+}
+
+// Block variant (FP32 forms): one element per thread, no layer loop.  A CTA
+// of 256 threads computes the 8 x 8 x 4 elements whose corners span a
+// 9 x 9 x 5 node block and owns the 7 x 7 x 3 interior nodes (all 8 of their
+// elements lie in the block).  Per block: stage the 405 nodes (masked values
+// and masks), compute one element per thread into a [24][256] output buffer,
+// and let each owned node sum its 8 contributions in a fixed order.  The
+// halo costs 256/147 = 1.74 element evaluations per node, cheap in FP32;
+// in exchange every thread works and there are two barriers per block.
+// Blocks are visited by a grid-stride loop (z fastest after x, y), so the
+// grid -- and the number of reduction partials -- stays small.
+struct BlockShape {
+  static constexpr int BX = 8, BY = 8, BZ = 4;          // elements
+  static constexpr int VX = 9, VY = 9, VZ = 5;          // nodes
+  static constexpr int NV = VX * VY * VZ;               // 405
+  static constexpr int OX = 7, OY = 7, OZ = 3;          // owned nodes
+  static constexpr int NO = OX * OY * OZ;               // 147
+  template <typename T>
+  static constexpr size_t smem_bytes() {
+    return sizeof(T) * (size_t)(3 * NV + 24 * BX * BY * BZ) + NV;
+  }
+};
+
+template <typename T, typename Load, typename Epi>
+__device__ __forceinline__ double kv_block_body(const T* __restrict__ E,
+                                                const uint8_t* __restrict__ fixed,
+                                                const ModeCoef<T>& K, const Grid& g,
+                                                const Load& ld, const Epi& epi, T* smem) {
+  using B = BlockShape;
+  static_assert(B::BX * B::BY * B::BZ == MFTO_BLOCK, "one element per thread");
+  T* vs = smem;                                                  // [3][NV]
+  T* out = vs + 3 * B::NV;                                       // [24][256]
+  uint8_t* ms = reinterpret_cast<uint8_t*>(out + 24 * MFTO_BLOCK);  // [NV]
+  const int tid = threadIdx.x;
+  const int tx = (g.nx + B::OX - 1) / B::OX, ty = (g.ny + B::OY - 1) / B::OY;
+  const int tz = (g.nz + B::OZ - 1) / B::OZ;
+  const int n_blocks = tx * ty * tz;
+  const int ex = tid & 7, ey = (tid >> 3) & 7, ez = tid >> 6;
+  DotAcc<T> red;
+  for (int b = blockIdx.x; b < n_blocks; b += gridDim.x) {
+    const int bx = b % tx, by = (b / tx) % ty, bz = b / (tx * ty);
+    const int ox = bx * B::OX, oy = by * B::OY, oz = bz * B::OZ;   // first owned node
+    // ---- stage the node block (masked values, masks) and this thread's E
+    for (int idx = tid; idx < B::NV; idx += MFTO_BLOCK) {
+      const int lx = idx % B::VX, ly = (idx / B::VX) % B::VY, lz = idx / (B::VX * B::VY);
+      const int gi = ox - 1 + lx, gj = oy - 1 + ly, gk = oz - 1 + lz;
+      T a = 0, bb = 0, c = 0;
+      uint8_t fm = 0;
+      if (gi >= 0 && gj >= 0 && gk >= 0 && gi < g.nx && gj < g.ny && gk < g.nz) {
+        const int node = gi + g.nx * (gj + g.ny * gk);
+        fm = fixed[node];
+        a = ld(3 * node + 0);
+        bb = ld(3 * node + 1);
+        c = ld(3 * node + 2);
+        a = (fm & 1) ? T(0) : a;
+        bb = (fm & 2) ? T(0) : bb;
+        c = (fm & 4) ? T(0) : c;
+      }
+      vs[idx] = a;
+      vs[B::NV + idx] = bb;
+      vs[2 * B::NV + idx] = c;
+      ms[idx] = fm;
+    }
+    const int ei = ox - 1 + ex, ej = oy - 1 + ey, ek = oz - 1 + ez;
+    T Ee = 0;
+    if (ei >= 0 && ej >= 0 && ek >= 0 && ei < g.nelx && ej < g.nely && ek < g.nelz)
+      Ee = E[ei + g.nelx * (ej + g.nely * ek)];
+    __syncthreads();
+    // ---- element phase (out-of-domain elements have E = 0: zero outputs)
+    {
+      T x[3][8];
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        const int vi = (ex + (l & 1)) + B::VX * ((ey + ((l >> 1) & 1)) + B::VY * (ez + (l >> 2)));
+        x[0][l] = vs[vi];
+        x[1][l] = vs[B::NV + vi];
+        x[2][l] = vs[2 * B::NV + vi];
+      }
+      element_apply<T>(x, Ee, K);
+#pragma unroll
+      for (int l = 0; l < 8; ++l)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[(3 * l + c) * MFTO_BLOCK + tid] = x[c][l];
+    }
+    __syncthreads();
+    // ---- node phase: owned node (ox+ix, oy+iy, oz+iz)
+    if (tid < B::NO) {
+      const int ix = tid % B::OX, iy = (tid / B::OX) % B::OY, iz = tid / (B::OX * B::OY);
+      const int gi = ox + ix, gj = oy + iy, gk = oz + iz;
+      if (gi < g.nx && gj < g.ny && gk < g.nz) {
+        T acc[3] = {0, 0, 0};
+#pragma unroll
+        for (int ec = 0; ec < 2; ++ec)
+#pragma unroll
+          for (int eb = 0; eb < 2; ++eb)
+#pragma unroll
+            for (int ea = 0; ea < 2; ++ea) {
+              const int e = (ix + ea) + B::BX * ((iy + eb) + B::BY * (iz + ec));
+              const int corner = (1 - ea) + 2 * (1 - eb) + 4 * (1 - ec);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) acc[c] += out[(3 * corner + c) * MFTO_BLOCK + e];
+            }
+        const int vi = (ix + 1) + B::VX * ((iy + 1) + B::VY * (iz + 1));
+        const T pn[3] = {vs[vi], vs[B::NV + vi], vs[2 * B::NV + vi]};
+        epi(gi + g.nx * (gj + g.ny * gk), acc, pn, ms[vi], red);
+      }
+    }
+    __syncthreads();   // vs, ms and out are rewritten for the next block
+  }
+  return red.finish();
 }

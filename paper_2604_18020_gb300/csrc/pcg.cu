@@ -1,4 +1,7 @@
-// FP64 Jacobi-preconditioned CG (Sec. 3.6) with warm start.
+// Jacobi-preconditioned CG (Sec. 3.6) with warm start, templated on the
+// vector type: FP64 for the plain solver, FP32 for the inner solve of the
+// iterative refinement (ir.cu).  Dot products are always accumulated in FP64
+// (the product of two FP32 values is exact in FP64).
 //
 // Iteration (left Jacobi, Hestenes-Stiefel):
 //   q = K p;  alpha = rz / p.q;  u += alpha p;  r -= alpha q;
@@ -19,31 +22,35 @@
 #include "kv_node.cuh"
 
 struct PcgGraph {
-  const void* E = nullptr;
-  const void* u = nullptr;
+  const void* key[3] = {nullptr, nullptr, nullptr};
   int chunk = 0;
   bool timed = false;
+  int variant = 0;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> ev;  // 2 per K.v launch when timed
 };
 
 namespace {
 
+// r = f - Ku, z = r / d; r.z, r.r, f.f reduced; the solver state is reset.
+// f may alias r (each entry is read before it is written); Ku may be NULL.
+template <typename T>
 __global__ void __launch_bounds__(MFTO_BLOCK)
-pcg_init(const double* __restrict__ f, const double* __restrict__ Ku, const double* __restrict__ dinv,
-         double* __restrict__ r, double* __restrict__ z, int n, double rtol, int maxit,
-         PcgScalars* s, double* partials) {
+pcg_init(const T* f, const T* __restrict__ Ku, const T* __restrict__ dinv, T* r,
+         T* __restrict__ z, int n, double rtol, int maxit, PcgScalars* s, double* partials) {
   __shared__ double sh[64];
-  double acc[3] = {0.0, 0.0, 0.0};
+  DotAcc<T> d0, d1, d2;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double ri = f[i] - Ku[i];
-    const double zi = ri * dinv[i];
+    const T fi = f[i];
+    const T ri = fi - (Ku ? Ku[i] : T(0));
+    const T zi = ri * dinv[i];
     r[i] = ri;
     z[i] = zi;
-    acc[0] += ri * zi;
-    acc[1] += ri * ri;
-    acc[2] += f[i] * f[i];
+    d0.add_prod(ri, zi);
+    d1.add_prod(ri, ri);
+    d2.add_prod(fi, fi);
   }
+  const double acc[3] = {d0.finish(), d1.finish(), d2.finish()};
   double tot[3];
   if (last_block_reduce<3>(acc, partials, &s->ticket_a, tot, sh) && threadIdx.x == 0) {
     s->rz = tot[0];
@@ -60,33 +67,32 @@ pcg_init(const double* __restrict__ f, const double* __restrict__ Ku, const doub
   }
 }
 
-// A: p_new = z + beta p_old (own nodes written), q = K p_new, alpha = rz / p_new.q
+// A (dense node-centric variant): p_new = z + beta p_old, q = K p_new, alpha
+// (p_new.q accumulated in FP64 per DOF: this variant exists for comparison)
+template <typename T>
 __global__ void __launch_bounds__(MFTO_BLOCK)
-pcg_kv_step(const double* __restrict__ E, const double* __restrict__ z,
-            const double* __restrict__ p_old, double* __restrict__ p_new,
-            double* __restrict__ q, const uint8_t* __restrict__ fixed,
-            const double* __restrict__ ke_g, Grid g, int n_node, PcgScalars* s,
-            double* partials) {
+pcg_kv_step(const T* __restrict__ E, const T* __restrict__ z, const T* __restrict__ p_old,
+            T* __restrict__ p_new, T* __restrict__ q, const uint8_t* __restrict__ fixed,
+            const T* __restrict__ ke_g, Grid g, int n_node, PcgScalars* s, double* partials) {
   if (*(volatile int32_t*)&s->done) return;  // uniform over the grid
-  __shared__ double ke[576];
+  __shared__ T ke[576];
   __shared__ double sh[64];
   for (int t = threadIdx.x; t < 576; t += blockDim.x) ke[t] = ke_g[t];
   __syncthreads();
-  const double beta = s->beta;
-  const LoadDirection<double> ld{z, p_old, beta};
+  const LoadDirection<T> ld{z, p_old, (T)s->beta};
   double acc[1] = {0.0};
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n_node;
        node += gridDim.x * blockDim.x) {
-    double a[3];
-    node_kv<double>(node, E, fixed, ke, g, ld, a[0], a[1], a[2]);
+    T a[3];
+    node_kv<T>(node, E, fixed, ke, g, ld, a[0], a[1], a[2]);
     const uint8_t fm = fixed[node];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double pn = ((fm >> c) & 1) ? 0.0 : ld(3 * node + c);
-      const double qc = ((fm >> c) & 1) ? pn : a[c];
+      const T pn = ((fm >> c) & 1) ? T(0) : ld(3 * node + c);
+      const T qc = ((fm >> c) & 1) ? pn : a[c];
       p_new[3 * node + c] = pn;
       q[3 * node + c] = qc;
-      acc[0] += pn * qc;
+      acc[0] += (double)pn * (double)qc;
     }
   }
   double tot[1];
@@ -103,22 +109,23 @@ pcg_kv_step(const double* __restrict__ E, const double* __restrict__ z,
 }
 
 // B: u += alpha p; r -= alpha q; z = r / d; beta = r.z / rz; convergence test
+template <typename T>
 __global__ void __launch_bounds__(MFTO_BLOCK)
-pcg_update(double* __restrict__ u, const double* __restrict__ p, const double* __restrict__ q,
-           double* __restrict__ r, double* __restrict__ z, const double* __restrict__ dinv,
-           int n, PcgScalars* s, double* partials) {
+pcg_update(T* __restrict__ u, const T* __restrict__ p, const T* __restrict__ q,
+           T* __restrict__ r, T* __restrict__ z, const T* __restrict__ dinv, int n,
+           PcgScalars* s, double* partials) {
   if (*(volatile int32_t*)&s->done) return;
   __shared__ double sh[64];
-  const double alpha = s->alpha;
+  const T alpha = (T)s->alpha;
   double acc[2] = {0.0, 0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     u[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
-    const double zi = ri * dinv[i];
+    const T ri = r[i] - alpha * q[i];
+    const T zi = ri * dinv[i];
     r[i] = ri;
     z[i] = zi;
-    acc[0] += ri * zi;
-    acc[1] += ri * ri;
+    acc[0] += (double)ri * (double)zi;
+    acc[1] += (double)ri * (double)ri;
   }
   double tot[2];
   if (last_block_reduce<2>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
@@ -139,62 +146,125 @@ pcg_update(double* __restrict__ u, const double* __restrict__ p, const double* _
   }
 }
 
-}  // namespace
+// B for FP32 vectors: one node (3 DOFs) per thread; r.z and r.r accumulate
+// in double-float within each warp and in FP64 across warps and blocks
+// (DotAcc<float>: no FP64 instruction per DOF).
+__global__ void __launch_bounds__(MFTO_BLOCK)
+pcg_update_f32(float* __restrict__ u, const float* __restrict__ p, const float* __restrict__ q,
+               float* __restrict__ r, float* __restrict__ z, const float* __restrict__ dinv,
+               int n_node, PcgScalars* s, double* partials) {
+  if (*(volatile int32_t*)&s->done) return;
+  __shared__ double sh[64];
+  const float alpha = (float)s->alpha;
+  DotAcc<float> d0, d1;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < n_node; nd += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int i = 3 * nd + c;
+      u[i] += alpha * p[i];
+      const float ri = r[i] - alpha * q[i];
+      const float zi = ri * dinv[i];
+      r[i] = ri;
+      z[i] = zi;
+      d0.add_prod(ri, zi);
+      d1.add_prod(ri, ri);
+    }
+  }
+  const double acc[2] = {d0.finish(), d1.finish()};
+  double tot[2];
+  if (last_block_reduce<2>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
+    s->it += 1;
+    s->rr = tot[1];
+    s->beta = tot[0] / s->rz;
+    s->rz = tot[0];
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      s->done = 1;
+      s->status = MFTO_BREAKDOWN;
+    } else if (tot[1] <= s->rtol2ff) {
+      s->done = 1;
+      s->status = MFTO_OK;
+    } else if (s->it >= s->maxit) {
+      s->done = 1;
+      s->status = MFTO_NOT_CONVERGED;
+    }
+  }
+}
 
-static mfto_status enqueue_chunk(mfto_handle* h, cudaStream_t st, const double* E, double* u,
-                                 int chunk, cudaEvent_t* ev) {
+template <typename T>
+void launch_update(const mfto_handle* h, cudaStream_t st, const PcgVecs<T>& v, T* p_new);
+template <>
+void launch_update<double>(const mfto_handle* h, cudaStream_t st, const PcgVecs<double>& v,
+                           double* p_new) {
+  pcg_update<double><<<reduction_blocks(h->n_dof, MFTO_BLOCK), MFTO_BLOCK, 0, st>>>(
+      v.u, p_new, v.q, v.r, v.z, v.dinv, (int)h->n_dof, v.s, v.part_b);
+}
+template <>
+void launch_update<float>(const mfto_handle* h, cudaStream_t st, const PcgVecs<float>& v,
+                          float* p_new) {
+  int blocks = (int)((h->n_node + MFTO_BLOCK - 1) / MFTO_BLOCK);
+  if (blocks > MFTO_RED_SLOTS) blocks = MFTO_RED_SLOTS;
+  pcg_update_f32<<<blocks, MFTO_BLOCK, 0, st>>>(v.u, p_new, v.q, v.r, v.z, v.dinv,
+                                                (int)h->n_node, v.s, v.part_b);
+}
+
+template <typename T>
+const T* ke_of(const mfto_handle* h);
+template <>
+const double* ke_of<double>(const mfto_handle* h) { return h->d_ke64; }
+template <>
+const float* ke_of<float>(const mfto_handle* h) { return h->d_ke32; }
+
+template <typename T>
+mfto_status enqueue_chunk(mfto_handle* h, cudaStream_t st, const PcgVecs<T>& v, int chunk,
+                          cudaEvent_t* ev) {
   const Grid g = make_grid(h->mesh);
   const int nb_node = reduction_blocks(h->n_node, MFTO_BLOCK);
-  const int nb_dof = reduction_blocks(h->n_dof, MFTO_BLOCK);
   for (int it = 0; it < chunk; ++it) {
-    double* p_old = (it & 1) ? h->d_p1 : h->d_p0;
-    double* p_new = (it & 1) ? h->d_p0 : h->d_p1;
+    T* p_old = (it & 1) ? v.p1 : v.p0;
+    T* p_new = (it & 1) ? v.p0 : v.p1;
     // external record nodes: a plain record inside a capture would only add a
     // dependency edge, not record the event on each graph launch
     if (ev) MFTO_CUDA(h, cudaEventRecordWithFlags(ev[2 * it], st, cudaEventRecordExternal));
     if (h->kv_variant == 0) {
-      mfto_status s = pcg_kv_tile_launch<double>(h, E, h->d_z, p_old, p_new, h->d_q, h->d_pcg,
-                                                 h->d_partials, st);
+      mfto_status s = pcg_kv_tile_launch<T>(h, v.E, v.z, p_old, p_new, v.q, v.s, v.part_a, st);
       if (s != MFTO_OK) return s;
     } else {
-      pcg_kv_step<<<nb_node, MFTO_BLOCK, 0, st>>>(E, h->d_z, p_old, p_new, h->d_q, h->d_fixed,
-                                                  h->d_ke64, g, (int)h->n_node, h->d_pcg,
-                                                  h->d_partials);
+      pcg_kv_step<T><<<nb_node, MFTO_BLOCK, 0, st>>>(v.E, v.z, p_old, p_new, v.q, h->d_fixed,
+                                                     ke_of<T>(h), g, (int)h->n_node, v.s,
+                                                     v.part_a);
     }
     if (ev) MFTO_CUDA(h, cudaEventRecordWithFlags(ev[2 * it + 1], st, cudaEventRecordExternal));
-    pcg_update<<<nb_dof, MFTO_BLOCK, 0, st>>>(u, p_new, h->d_q, h->d_r, h->d_z,
-                                                    h->d_dinv, (int)h->n_dof, h->d_pcg,
-                                                    h->d_partials2);
+    launch_update<T>(h, st, v, p_new);
   }
   MFTO_LAUNCH_CHECK(h);
   return MFTO_OK;
 }
 
-static void destroy_graph(PcgGraph* pg) {
+void destroy_graph(PcgGraph* pg) {
   if (!pg) return;
   if (pg->exec) cudaGraphExecDestroy(pg->exec);
   for (cudaEvent_t e : pg->ev) cudaEventDestroy(e);
   delete pg;
 }
 
-void pcg_graph_release(mfto_handle* h) {
-  destroy_graph(h->pcg_graph);
-  h->pcg_graph = nullptr;
-}
-
-static mfto_status get_graph(mfto_handle* h, const double* E, double* u, PcgGraph** out) {
+template <typename T>
+mfto_status get_graph(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgGraph** out) {
   const int chunk = h->p.check_every;
-  PcgGraph* pg = h->pcg_graph;
-  if (pg && pg->E == E && pg->u == u && pg->chunk == chunk && pg->timed == h->kv_timing) {
+  PcgGraph* pg = h->pcg_graph[slot];
+  if (pg && pg->key[0] == v.E && pg->key[1] == v.u && pg->key[2] == v.s && pg->chunk == chunk &&
+      pg->timed == h->kv_timing && pg->variant == h->kv_variant) {
     *out = pg;
     return MFTO_OK;
   }
-  pcg_graph_release(h);
+  destroy_graph(pg);
+  h->pcg_graph[slot] = nullptr;
   pg = new PcgGraph();
-  pg->E = E;
-  pg->u = u;
+  pg->key[0] = v.E;
+  pg->key[1] = v.u;
+  pg->key[2] = v.s;
   pg->chunk = chunk;
   pg->timed = h->kv_timing;
+  pg->variant = h->kv_variant;
   if (pg->timed) {
     pg->ev.resize(2 * chunk);
     for (auto& e : pg->ev) cudaEventCreate(&e);
@@ -212,12 +282,13 @@ static mfto_status get_graph(mfto_handle* h, const double* E, double* u, PcgGrap
     destroy_graph(pg);
     return mfto_fail(h, MFTO_CUDA_ERROR, "PCG graph capture: %s", cudaGetErrorString(e));
   }
-  mfto_status s = enqueue_chunk(h, h->cap_stream, E, u, chunk, pg->timed ? pg->ev.data() : nullptr);
+  mfto_status s = enqueue_chunk<T>(h, h->cap_stream, v, chunk, pg->timed ? pg->ev.data() : nullptr);
   e = cudaStreamEndCapture(h->cap_stream, &graph);
   if (s != MFTO_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     destroy_graph(pg);
-    return s != MFTO_OK ? s : mfto_fail(h, MFTO_CUDA_ERROR, "PCG graph capture: %s", cudaGetErrorString(e));
+    return s != MFTO_OK ? s
+                        : mfto_fail(h, MFTO_CUDA_ERROR, "PCG graph capture: %s", cudaGetErrorString(e));
   }
   e = cudaGraphInstantiate(&pg->exec, graph, 0);
   cudaGraphDestroy(graph);
@@ -225,47 +296,79 @@ static mfto_status get_graph(mfto_handle* h, const double* E, double* u, PcgGrap
     destroy_graph(pg);
     return mfto_fail(h, MFTO_CUDA_ERROR, "PCG graph instantiate: %s", cudaGetErrorString(e));
   }
-  h->pcg_graph = pg;
+  h->pcg_graph[slot] = pg;
   *out = pg;
   return MFTO_OK;
 }
 
+}  // namespace
+
+void pcg_graph_release(mfto_handle* h) {
+  for (int i = 0; i < MFTO_PCG_SLOTS; ++i) {
+    destroy_graph(h->pcg_graph[i]);
+    h->pcg_graph[i] = nullptr;
+  }
+}
+
+template <typename T>
+mfto_status pcg_start(mfto_handle* h, const PcgVecs<T>& v, const T* rhs, const T* Ku, double rtol,
+                      int maxit) {
+  const int nb_dof = reduction_blocks(h->n_dof, MFTO_BLOCK);
+  MFTO_CUDA(h, cudaMemsetAsync(v.p0, 0, sizeof(T) * h->n_dof, h->stream));
+  h->launches++;
+  pcg_init<T><<<nb_dof, MFTO_BLOCK, 0, h->stream>>>(rhs, Ku, v.dinv, v.r, v.z, (int)h->n_dof,
+                                                    rtol, maxit, v.s, v.part_a);
+  MFTO_LAUNCH_CHECK(h);
+  return MFTO_OK;
+}
+
+template <typename T>
+mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalars* host_s) {
+  PcgGraph* pg = nullptr;
+  mfto_status s = get_graph<T>(h, v, slot, &pg);
+  if (s != MFTO_OK) return s;
+  int it_before = 0;
+  for (;;) {
+    MFTO_CUDA(h, cudaMemcpyAsync(host_s, v.s, sizeof(PcgScalars), cudaMemcpyDeviceToHost, h->stream));
+    MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (pg->timed) {
+      // harvest the K.v launches of the previous chunk that did work
+      const int ran = host_s->it - it_before + (host_s->status == MFTO_BREAKDOWN ? 1 : 0);
+      for (int i = 0; i < ran && i < pg->chunk; ++i) {
+        float ms = 0.f;
+        MFTO_CUDA(h, cudaEventElapsedTime(&ms, pg->ev[2 * i], pg->ev[2 * i + 1]));
+        const int f = sizeof(T) == 8 ? 0 : 1;
+        h->ev.total_ms[f] += ms;
+        h->ev.launches[f]++;
+      }
+      it_before = host_s->it;
+    }
+    if (host_s->done) break;
+    MFTO_CUDA(h, cudaGraphLaunch(pg->exec, h->stream));
+    h->launches += 2 * (int64_t)pg->chunk;
+  }
+  return MFTO_OK;
+}
+
+template mfto_status pcg_start<double>(mfto_handle*, const PcgVecs<double>&, const double*,
+                                       const double*, double, int);
+template mfto_status pcg_start<float>(mfto_handle*, const PcgVecs<float>&, const float*,
+                                      const float*, double, int);
+template mfto_status pcg_iterate<double>(mfto_handle*, const PcgVecs<double>&, int, PcgScalars*);
+template mfto_status pcg_iterate<float>(mfto_handle*, const PcgVecs<float>&, int, PcgScalars*);
+
 mfto_status pcg_run(mfto_handle* h, const double* E, const double* f, double* u,
                     mfto_solve_stats* st) {
-  const int nb_dof = reduction_blocks(h->n_dof, MFTO_BLOCK);
   mfto_status s = diag_launch(h, MFTO_FORM_F64, E, h->d_dinv, true);
   if (s != MFTO_OK) return s;
   s = kv_launch(h, MFTO_FORM_F64, E, u, h->d_q);
   if (s != MFTO_OK) return s;
-  MFTO_CUDA(h, cudaMemsetAsync(h->d_p0, 0, sizeof(double) * h->n_dof, h->stream));
-  h->launches++;
-  pcg_init<<<nb_dof, MFTO_BLOCK, 0, h->stream>>>(f, h->d_q, h->d_dinv, h->d_r, h->d_z,
-                                                 (int)h->n_dof, h->p.rtol, h->p.maxit,
-                                                 h->d_pcg, h->d_partials);
-  MFTO_LAUNCH_CHECK(h);
-  PcgGraph* pg = nullptr;
-  s = get_graph(h, E, u, &pg);
+  const PcgVecs<double> v{E, u, h->d_r, h->d_z, h->d_p0, h->d_p1, h->d_q, h->d_dinv,
+                          h->d_pcg, h->d_partials, h->d_partials2};
+  s = pcg_start<double>(h, v, f, h->d_q, h->p.rtol, h->p.maxit);
   if (s != MFTO_OK) return s;
-  int it_before = 0;
-  for (;;) {
-    MFTO_CUDA(h, cudaMemcpyAsync(h->h_pcg, h->d_pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
-                                 h->stream));
-    MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (pg->timed) {
-      // harvest the K.v launches of the previous chunk that did work
-      const int ran = h->h_pcg->it - it_before + (h->h_pcg->status == MFTO_BREAKDOWN ? 1 : 0);
-      for (int i = 0; i < ran && i < pg->chunk; ++i) {
-        float ms = 0.f;
-        MFTO_CUDA(h, cudaEventElapsedTime(&ms, pg->ev[2 * i], pg->ev[2 * i + 1]));
-        h->ev.total_ms += ms;
-        h->ev.launches++;
-      }
-      it_before = h->h_pcg->it;
-    }
-    if (h->h_pcg->done) break;
-    MFTO_CUDA(h, cudaGraphLaunch(pg->exec, h->stream));
-    h->launches += 2 * (int64_t)pg->chunk;
-  }
+  s = pcg_iterate<double>(h, v, 0, h->h_pcg);
+  if (s != MFTO_OK) return s;
   if (h->h_pcg->ff == 0.0) MFTO_CUDA(h, cudaMemsetAsync(u, 0, sizeof(double) * h->n_dof, h->stream));
   if (st) {
     st->iterations = h->h_pcg->it;

@@ -189,8 +189,18 @@ extern "C" mfto_status mfto_simp_step(mfto_handle* h, double* rho, double* u, co
   s = modulus_launch(h, MFTO_FORM_F64, rho_phys, h->d_E);
   if (s != MFTO_OK) return s;
   mfto_solve_stats ss;
-  s = pcg_run(h, h->d_E, f, u, &ss);
-  if (s != MFTO_OK) return s;
+  if (h->solver_form == MFTO_FORM_F64) {
+    s = pcg_run(h, h->d_E, f, u, &ss);
+    if (s != MFTO_OK) return s;
+  } else {
+    mfto_ir_stats is;
+    s = ir_run(h, (mfto_form)h->solver_form, h->inner_tol, h->d_E, f, u, &is);
+    if (s != MFTO_OK) return s;
+    ss.iterations = is.inner_iterations;
+    ss.status = is.status;
+    ss.rel_residual = is.rel_residual;
+    ss.fnorm = is.fnorm;
+  }
   double c = 0.0, gray = 0.0;
   s = compliance_launch(h, rho_phys, u, h->d_dc_phys, &c, &gray);
   if (s != MFTO_OK) return s;

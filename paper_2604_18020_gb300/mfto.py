@@ -51,6 +51,12 @@ class IterStats(C.Structure):
                 ("rel_residual", C.c_double)]
 
 
+class IrStats(C.Structure):
+    _fields_ = [("outer_iterations", C.c_int32), ("inner_iterations", C.c_int32),
+                ("status", C.c_int32), ("kv_f64", C.c_int32), ("rel_residual", C.c_double),
+                ("fnorm", C.c_double), ("history", C.c_double * 64)]
+
+
 class MftoError(RuntimeError):
     def __init__(self, fn, code, msg=""):
         super().__init__(f"{fn} -> {STATUS_NAMES.get(code, code)}: {msg}")
@@ -78,6 +84,8 @@ SIGNATURES = {
     "mfto_jacobi_diag": (C.c_int32, [_P, C.c_int32, _P, _P]),
     "mfto_set_kv_variant": (C.c_int32, [_P, C.c_int32]),
     "mfto_pcg": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
+    "mfto_ir_solve": (C.c_int32, [_P, C.c_int32, C.c_double, _P, _P, _P, C.POINTER(IrStats)]),
+    "mfto_set_solver": (C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, C.c_int32]),
     "mfto_filter": (C.c_int32, [_P, _P, _P, C.c_int32]),
     "mfto_compliance_sens": (C.c_int32, [_P, _P, _P, C.POINTER(C.c_double), _P]),
     "mfto_oc_update": (C.c_int32, [_P, _P, _P, _P, C.POINTER(IterStats)]),
@@ -88,7 +96,8 @@ SIGNATURES = {
                                                  C.c_double, C.c_double, _P, _P, _P,
                                                  C.POINTER(C.c_double), _P]),
     "mfto_kv_timing": (C.c_int32, [_P, C.c_int32]),
-    "mfto_kv_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "mfto_kv_timing_read": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_double)]),
 }
 
 
@@ -285,6 +294,19 @@ class Handle:
             C.byref(st)), self._h)
         return st
 
+    def ir_solve(self, E, f, u, inner=FORM_F32, inner_tol=1e-2) -> IrStats:
+        import torch
+        st = IrStats()
+        _check("mfto_ir_solve", lib().mfto_ir_solve(
+            self._h, inner, inner_tol, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(f, torch.float64, self.n_dof, "f"), _ptr(u, torch.float64, self.n_dof, "u"),
+            C.byref(st)), self._h)
+        return st
+
+    def set_solver(self, form=FORM_F64, inner_tol=1e-2, inner_maxit=10000, max_outer=50):
+        _check("mfto_set_solver", lib().mfto_set_solver(self._h, form, inner_tol, inner_maxit,
+                                                        max_outer), self._h)
+
     def filter(self, x, y, transpose=False):
         import torch
         _check("mfto_filter", lib().mfto_filter(
@@ -327,8 +349,8 @@ class Handle:
     def kv_timing(self, on: bool):
         _check("mfto_kv_timing", lib().mfto_kv_timing(self._h, 1 if on else 0), self._h)
 
-    def kv_timing_read(self):
+    def kv_timing_read(self, form=FORM_F64):
         n, ms = C.c_int64(), C.c_double()
         _check("mfto_kv_timing_read",
-               lib().mfto_kv_timing_read(self._h, C.byref(n), C.byref(ms)), self._h)
+               lib().mfto_kv_timing_read(self._h, form, C.byref(n), C.byref(ms)), self._h)
         return n.value, ms.value
