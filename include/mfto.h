@@ -60,10 +60,22 @@ enum {
   MFTO_TOO_LARGE = 8        /* problem exceeds a fixed capacity          */
 };
 
-/* Arithmetic forms of the K.v contraction. */
+/* Arithmetic forms of the K.v contraction.  F64 and F32 run on the FMA
+ * pipes; the others keep FP32 vectors and moduli, put the element
+ * contraction on the tcgen05 tensor cores with FP32 accumulation, and round
+ * the operands (E_e u_e and KE) to the form's type first.  The X3 forms split
+ * each operand x into hi = round(x) and lo = round(x - hi) and add
+ * A_hi B_lo + A_lo B_hi to A_hi B_hi (three products).  FP16 forms scale each
+ * element's row by a power of two into [1, 2) to stay in range. */
 typedef enum {
   MFTO_FORM_F64 = 0,        /* FP64 data, FP64 arithmetic                 */
-  MFTO_FORM_F32 = 1         /* FP32 data, FP32 arithmetic                 */
+  MFTO_FORM_F32 = 1,        /* FP32 data, FP32 arithmetic                 */
+  MFTO_FORM_TF32 = 2,       /* tensor cores, TF32 operands                */
+  MFTO_FORM_TF32X3 = 3,     /* tensor cores, split TF32 (3 products)      */
+  MFTO_FORM_BF16 = 4,       /* tensor cores, BF16 operands                */
+  MFTO_FORM_BF16X3 = 5,     /* tensor cores, split BF16 (3 products)      */
+  MFTO_FORM_F16 = 6,        /* tensor cores, FP16 operands (row-scaled)   */
+  MFTO_FORM_F16X3 = 7       /* tensor cores, split FP16 (3 products)      */
 } mfto_form;
 
 typedef struct {
@@ -170,8 +182,10 @@ mfto_status mfto_simp_modulus(mfto_handle* h, mfto_form form,
                               const double* d_rho_phys, void* d_E);
 
 /* Masked matrix-free K.v (Eq. matfree; Alg. 1 computes the same sum):
- * d_y = K(E) d_v.  d_E, d_v, d_y are in the form's type (double for F64,
- * float for F32).  d_y must not alias d_v. */
+ * d_y = K(E) d_v.  d_E, d_v, d_y are double for MFTO_FORM_F64 and float for
+ * every other form.  d_y must not alias d_v.  A tensor-core form whose
+ * completion wait times out sets the handle's device error flag (reported
+ * by the next synchronising call) instead of hanging. */
 mfto_status mfto_kv(mfto_handle* h, mfto_form form, const void* d_E,
                     const void* d_v, void* d_y);
 
@@ -206,8 +220,8 @@ mfto_status mfto_pcg(mfto_handle* h, const double* d_E, const double* d_f,
  * Stops with MFTO_STALLED when the outer residual fails twice in a row to fall
  * below 0.9 of its previous value (the stagnation the paper reports for BF16),
  * MFTO_NOT_CONVERGED after max_outer corrections (mfto_set_solver).
- * inner: MFTO_FORM_F32.  Returns MFTO_OK also when not converged; see
- * st->status.  Synchronises the stream. */
+ * inner: any form but MFTO_FORM_F64 (the inner K.v form).  Returns MFTO_OK
+ * also when not converged; see st->status.  Synchronises the stream. */
 mfto_status mfto_ir_solve(mfto_handle* h, mfto_form inner, double inner_tol,
                           const double* d_E, const double* d_f, double* d_u,
                           mfto_ir_stats* st);

@@ -25,6 +25,7 @@ struct ModeCoef {
 #define MFTO_RED_MAX_BLOCKS 1024  // grid cap of the grid-stride vector kernels
 #define MFTO_RED_SLOTS 16384      // partial-sum slots per row of one grid reduction
 #define MFTO_PCG_SLOTS 2          // cached PCG graphs: FP64 solver, FP32 inner solver
+#define MFTO_TC_BTILE 3072        // bytes of one tensor-core B operand (KE, one part)
 
 // Device-resident scalars of the PCG driver and the other reductions.  Each
 // reduction site owns a ticket counter (reset by the last block).
@@ -37,6 +38,7 @@ struct PcgScalars {
   double rtol2ff;   // rtol^2 * f.f
   int32_t it, maxit, done, status;
   unsigned int ticket_a, ticket_b, ticket_c;
+  int32_t tc_error;         // a tensor-core completion wait gave up
 };
 
 struct MiscScalars {
@@ -71,6 +73,8 @@ struct mfto_handle {
   ModeCoef<float> mc32;
   int kv_variant;           // 0: tiled mode-space kernel, 1: node-centric dense KE
   int occ_kv32, occ_pcg32;  // resident CTAs per SM of the FP32 block kernels
+  int occ_tc[12];           // ... of the tensor-core kernels, [2 * (2 kind + split) + pcg]
+  unsigned char* d_btc;     // tensor-core B operands: [kind][hi | lo]
   uint8_t* d_fixed;         // per-node mask
   // cone filter
   int32_t n_stencil;
@@ -339,7 +343,16 @@ struct PcgVecs {
   T *u, *r, *z, *p0, *p1, *q, *dinv;
   PcgScalars* s;
   double *part_a, *part_b;
+  int form;                 // K.v form of this solve
 };
+mfto_status tc_init(mfto_handle* h);
+mfto_status tc_upload_b(mfto_handle* h, const double* ke);
+bool tc_form(int form);
+mfto_status kv_tc_launch(mfto_handle* h, int form, const float* E, const float* v, float* y,
+                         cudaStream_t st);
+mfto_status pcg_kv_tc_launch(mfto_handle* h, int form, const float* E, const float* z,
+                             const float* p_old, float* p_new, float* q, PcgScalars* s,
+                             double* partials, cudaStream_t st);
 template <typename T>
 mfto_status pcg_start(mfto_handle* h, const PcgVecs<T>& v, const T* rhs, const T* Ku, double rtol,
                       int maxit);

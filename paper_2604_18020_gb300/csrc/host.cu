@@ -127,7 +127,8 @@ static void free_handle(mfto_handle* h) {
                   h->d_filter_W, h->d_r, h->d_z, h->d_p0, h->d_p1, h->d_q, h->d_dinv,
                   h->d_partials, h->d_partials2, h->d_pcg, h->d_misc, h->d_rho_phys,
                   h->d_E, h->d_dc, h->d_dc_phys, h->d_r32, h->d_z32, h->d_p0_32,
-                  h->d_p1_32, h->d_q32, h->d_dinv32, h->d_e32, h->d_E32, h->d_pcg32};
+                  h->d_p1_32, h->d_q32, h->d_dinv32, h->d_e32, h->d_E32, h->d_pcg32,
+                  h->d_btc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -149,6 +150,10 @@ static mfto_status upload_params(mfto_handle* h) {
   mfto_unit_ke(1.0, h->p.nu, h->mesh.h, ke);
   for (int i = 0; i < 576; ++i) ke32[i] = (float)ke[i];
   h->ke_diag = ke[0];
+  {
+    mfto_status s = tc_upload_b(h, ke);
+    if (s != MFTO_OK) return s;
+  }
   // mode-space coefficients (unit modulus, 1/8 of the inverse folded in)
   {
     const ModeOperator op = mode_operator(1.0, h->p.nu, h->mesh.h);
@@ -256,6 +261,7 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   A((void**)&h->d_e32, nd32);
   A((void**)&h->d_E32, sizeof(float) * h->n_elem);
   A((void**)&h->d_pcg32, sizeof(PcgScalars));
+  A((void**)&h->d_btc, 3 * 2 * MFTO_TC_BTILE);
   if (ok && (cudaMallocHost(&h->h_pcg, sizeof(PcgScalars)) != cudaSuccess ||
              cudaMallocHost(&h->h_misc, sizeof(MiscScalars)) != cudaSuccess ||
              cudaMallocHost(&h->h_pcg32, sizeof(PcgScalars)) != cudaSuccess))
@@ -273,6 +279,7 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
     return MFTO_CUDA_ERROR;
   }
   mfto_status s = kv_tile_init(h);
+  if (s == MFTO_OK) s = tc_init(h);
   if (s == MFTO_OK) s = upload_params(h);
   if (s != MFTO_OK) { free_handle(h); return s; }
   *out = h;

@@ -46,7 +46,7 @@ ir_accumulate(double* __restrict__ u, const float* __restrict__ e, int n) {
 
 mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const double* E,
                    const double* f, double* u, mfto_ir_stats* st) {
-  if (inner != MFTO_FORM_F32)
+  if (inner != MFTO_FORM_F32 && !tc_form(inner))
     return mfto_fail(h, MFTO_UNSUPPORTED, "mfto_ir_solve: unsupported inner form %d", (int)inner);
   if (!(inner_tol > 0.0 && inner_tol < 1.0))
     return mfto_fail(h, MFTO_INVALID_ARG, "mfto_ir_solve: inner_tol must lie in (0, 1)");
@@ -65,7 +65,8 @@ mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const doub
   // inner solve K e = r: the FP32 right-hand side is written into the inner
   // residual buffer, which pcg_init turns into r = rhs in place
   const PcgVecs<float> v{h->d_E32, h->d_e32, h->d_r32, h->d_z32, h->d_p0_32, h->d_p1_32,
-                         h->d_q32, h->d_dinv32, h->d_pcg32, h->d_partials, h->d_partials2};
+                         h->d_q32, h->d_dinv32, h->d_pcg32, h->d_partials, h->d_partials2,
+                         (int)inner};
   double prev = 0.0;
   int stalls = 0;
   out->status = MFTO_NOT_CONVERGED;
@@ -126,7 +127,7 @@ extern "C" mfto_status mfto_ir_solve(mfto_handle* h, mfto_form inner, double inn
 extern "C" mfto_status mfto_set_solver(mfto_handle* h, mfto_form form, double inner_tol,
                                        int32_t inner_maxit, int32_t max_outer) {
   if (!h) return MFTO_INVALID_ARG;
-  MFTO_REQUIRE(h, form == MFTO_FORM_F64 || form == MFTO_FORM_F32,
+  MFTO_REQUIRE(h, form == MFTO_FORM_F64 || form == MFTO_FORM_F32 || tc_form(form),
                "mfto_set_solver: unsupported form");
   MFTO_REQUIRE(h, inner_tol > 0.0 && inner_tol < 1.0, "mfto_set_solver: inner_tol in (0, 1)");
   MFTO_REQUIRE(h, inner_maxit >= 1 && max_outer >= 1, "mfto_set_solver: caps must be >= 1");

@@ -76,10 +76,15 @@ static inline int node_blocks(const mfto_handle* h) { return reduction_blocks(h-
 
 mfto_status kv_launch(mfto_handle* h, mfto_form form, const void* E, const void* v, void* y) {
   const Grid g = make_grid(h->mesh);
-  if (form != MFTO_FORM_F64 && form != MFTO_FORM_F32)
+  if (form != MFTO_FORM_F64 && form != MFTO_FORM_F32 && !tc_form(form))
     return mfto_fail(h, MFTO_UNSUPPORTED, "mfto_kv: unsupported form %d", (int)form);
   kv_timing_begin(h, form);
   h->launches++;
+  if (tc_form(form)) {
+    mfto_status s = kv_tc_launch(h, form, (const float*)E, (const float*)v, (float*)y, h->stream);
+    kv_timing_end(h);
+    return s;
+  }
   if (h->kv_variant == 0) {
     mfto_status s = form == MFTO_FORM_F64
         ? kv_tile_launch<double>(h, (const double*)E, (const double*)v, (double*)y, h->stream)

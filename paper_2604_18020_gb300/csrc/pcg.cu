@@ -26,6 +26,7 @@ struct PcgGraph {
   int chunk = 0;
   bool timed = false;
   int variant = 0;
+  int form = 0;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> ev;  // 2 per K.v launch when timed
 };
@@ -62,6 +63,7 @@ pcg_init(const T* f, const T* __restrict__ Ku, const T* __restrict__ dinv, T* r,
     s->it = 0;
     s->maxit = maxit;
     s->status = MFTO_OK;
+    s->tc_error = 0;
     s->done = (tot[2] == 0.0 || tot[1] <= s->rtol2ff) ? 1 : 0;
     if (!isfinite(tot[0]) || !isfinite(tot[1])) { s->done = 1; s->status = MFTO_BREAKDOWN; }
   }
@@ -225,7 +227,12 @@ mfto_status enqueue_chunk(mfto_handle* h, cudaStream_t st, const PcgVecs<T>& v, 
     // external record nodes: a plain record inside a capture would only add a
     // dependency edge, not record the event on each graph launch
     if (ev) MFTO_CUDA(h, cudaEventRecordWithFlags(ev[2 * it], st, cudaEventRecordExternal));
-    if (h->kv_variant == 0) {
+    if (sizeof(T) == 4 && tc_form(v.form)) {
+      mfto_status s = pcg_kv_tc_launch(h, v.form, (const float*)v.E, (const float*)v.z,
+                                       (const float*)p_old, (float*)p_new, (float*)v.q, v.s,
+                                       v.part_a, st);
+      if (s != MFTO_OK) return s;
+    } else if (h->kv_variant == 0) {
       mfto_status s = pcg_kv_tile_launch<T>(h, v.E, v.z, p_old, p_new, v.q, v.s, v.part_a, st);
       if (s != MFTO_OK) return s;
     } else {
@@ -252,7 +259,7 @@ mfto_status get_graph(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgGraph** 
   const int chunk = h->p.check_every;
   PcgGraph* pg = h->pcg_graph[slot];
   if (pg && pg->key[0] == v.E && pg->key[1] == v.u && pg->key[2] == v.s && pg->chunk == chunk &&
-      pg->timed == h->kv_timing && pg->variant == h->kv_variant) {
+      pg->timed == h->kv_timing && pg->variant == h->kv_variant && pg->form == v.form) {
     *out = pg;
     return MFTO_OK;
   }
@@ -265,6 +272,7 @@ mfto_status get_graph(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgGraph** 
   pg->chunk = chunk;
   pg->timed = h->kv_timing;
   pg->variant = h->kv_variant;
+  pg->form = v.form;
   if (pg->timed) {
     pg->ev.resize(2 * chunk);
     for (auto& e : pg->ev) cudaEventCreate(&e);
@@ -343,6 +351,8 @@ mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalar
       }
       it_before = host_s->it;
     }
+    if (host_s->tc_error)
+      return mfto_fail(h, MFTO_CUDA_ERROR, "tensor-core completion wait timed out");
     if (host_s->done) break;
     MFTO_CUDA(h, cudaGraphLaunch(pg->exec, h->stream));
     h->launches += 2 * (int64_t)pg->chunk;
@@ -364,7 +374,7 @@ mfto_status pcg_run(mfto_handle* h, const double* E, const double* f, double* u,
   s = kv_launch(h, MFTO_FORM_F64, E, u, h->d_q);
   if (s != MFTO_OK) return s;
   const PcgVecs<double> v{E, u, h->d_r, h->d_z, h->d_p0, h->d_p1, h->d_q, h->d_dinv,
-                          h->d_pcg, h->d_partials, h->d_partials2};
+                          h->d_pcg, h->d_partials, h->d_partials2, MFTO_FORM_F64};
   s = pcg_start<double>(h, v, f, h->d_q, h->p.rtol, h->p.maxit);
   if (s != MFTO_OK) return s;
   s = pcg_iterate<double>(h, v, 0, h->h_pcg);

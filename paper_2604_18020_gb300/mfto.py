@@ -23,8 +23,10 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA_ERROR", 3: "OOM", 4: "NOT_CO
                 5: "STALLED", 6: "BREAKDOWN", 7: "UNSUPPORTED", 8: "TOO_LARGE"}
 NOALLOC_MAX_ELEMENTS = 2048 * 256
 
-FORM_F64, FORM_F32 = 0, 1
-FORMS = {"f64": FORM_F64, "f32": FORM_F32}
+(FORM_F64, FORM_F32, FORM_TF32, FORM_TF32X3, FORM_BF16, FORM_BF16X3, FORM_F16,
+ FORM_F16X3) = range(8)
+FORMS = {"f64": FORM_F64, "f32": FORM_F32, "tf32": FORM_TF32, "tf32x3": FORM_TF32X3,
+         "bf16": FORM_BF16, "bf16x3": FORM_BF16X3, "f16": FORM_F16, "f16x3": FORM_F16X3}
 
 
 class Mesh(C.Structure):
