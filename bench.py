@@ -193,7 +193,7 @@ def gpu_bench(args, rank, local_rank, world):
     params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
     if args.form == "mixed":
-        h.set_solver(mfto.FORM_F32, args.inner_tol)
+        h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
     rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     f = torch.tensor(P.f, device=dev)
@@ -286,7 +286,9 @@ def gpu_bench(args, rank, local_rank, world):
         bytes_per_launch = m.n_node * (4 * 12 + 1) + 4 * m.n_elem
         peak = measured_hbm_gbs()
         roof = {"bound": "hbm", "achieved": bytes_per_launch / kv_avg_s / 1e9, "peak": peak,
-                "unit": "GB/s", "traffic": None, "kernel": "pcg_kv_tile_kernel<float>",
+                "unit": "GB/s", "traffic": None,
+                "kernel": ("pcg_kv_tile_kernel<float>" if args.inner_form == "f32"
+                           else f"pcg_kv_tc_kernel ({args.inner_form})"),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy benchmark), of measured",
                 "bytes_per_launch": bytes_per_launch}
     else:
@@ -307,6 +309,7 @@ def gpu_bench(args, rank, local_rank, world):
         "config": {"workload": WORKLOAD, "elements": m.n_elem, "dofs": m.n_dof,
                    "form": args.form, "pcg_rtol": 1e-8,
                    "inner_tol": args.inner_tol if args.form == "mixed" else None,
+                   "inner_form": args.inner_form if args.form == "mixed" else None,
                    "kv_kernel": "tiled mode-space",
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -348,7 +351,7 @@ def profile_run(args):
                                  maxit=args.maxit if args.mode == "pcg" else 10000)
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
     if args.form == "mixed":
-        h.set_solver(mfto.FORM_F32, args.inner_tol)
+        h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
     f = torch.tensor(P.f, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     if args.mode == "profile":
@@ -380,6 +383,9 @@ def main():
                     help="f64: plain FP64 Jacobi-PCG; mixed: FP64 iterative refinement "
                          "around an FP32 inner PCG")
     ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--inner-form", default="f32",
+                    choices=["f32", "tf32", "tf32x3", "bf16", "bf16x3", "f16", "f16x3"],
+                    help="K.v form of the inner solve of --form mixed")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--maxit", type=int, default=40, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -94,6 +94,7 @@ typedef struct {
   double rtol;              /* PCG stop: ||r|| <= rtol ||f||              */
   int32_t maxit;            /* PCG iteration cap                          */
   int32_t check_every;      /* PCG: host polls convergence every k iters  */
+  int32_t max_rhs;          /* load cases of the multi-RHS calls, 1..8    */
 } mfto_params;
 
 typedef struct {
@@ -131,7 +132,7 @@ typedef struct mfto_handle mfto_handle;
 const char* mfto_version(void);
 
 /* Default parameters: E0=1, Emin=1e-9, nu=0.3, p=3, rmin=1.5, V_f=0.3,
- * move=0.2, rtol=1e-8, maxit=10000, check_every=32. */
+ * move=0.2, rtol=1e-8, maxit=10000, check_every=32, max_rhs=1. */
 void mfto_default_params(mfto_params* p);
 
 /* ---------------------------------------------------------------- host -- */
@@ -225,6 +226,25 @@ mfto_status mfto_pcg(mfto_handle* h, const double* d_E, const double* d_f,
 mfto_status mfto_ir_solve(mfto_handle* h, mfto_form inner, double inner_tol,
                           const double* d_E, const double* d_f, double* d_u,
                           mfto_ir_stats* st);
+
+/* Several load cases at once (multi-RHS).  V and Y hold nrhs DOF vectors
+ * one after the other ([nrhs][n_dof]); every case uses the same moduli and
+ * fixed set.  mfto_kv_multi: Y_r = K(E) V_r for r < nrhs (1..8), one launch,
+ * forms MFTO_FORM_F64 (double) and MFTO_FORM_F32 (float).  The paper treats
+ * one load case; this batches the operator it defines (Eq. matfree). */
+mfto_status mfto_kv_multi(mfto_handle* h, mfto_form form, const void* d_E, const void* d_V,
+                          void* d_Y, int32_t nrhs);
+
+/* Mixed-precision solve of K(E) U_r = F_r for nrhs load cases (nrhs <=
+ * max_rhs of mfto_create): the refinement of mfto_ir_solve for every case
+ * (FP64 residuals, norms and accumulation), around one inner FP32 CG that
+ * advances all live cases together (one multi-RHS K.V and one vector update
+ * per iteration, per-case scalars and stopping).  d_E FP64 [n_elem];
+ * d_F, d_U FP64 [nrhs][n_dof] (d_U: initial guesses in, solutions out);
+ * st: nrhs entries.  Synchronises the stream. */
+mfto_status mfto_ir_solve_multi(mfto_handle* h, double inner_tol, const double* d_E,
+                                const double* d_F, double* d_U, int32_t nrhs,
+                                mfto_ir_stats* st);
 
 /* Select the linear solver of mfto_simp_step: form MFTO_FORM_F64 = plain FP64
  * Jacobi-PCG (default); any other form = mfto_ir_solve with that inner form,

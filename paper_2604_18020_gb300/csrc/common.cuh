@@ -26,6 +26,8 @@ struct ModeCoef {
 #define MFTO_RED_SLOTS 16384      // partial-sum slots per row of one grid reduction
 #define MFTO_PCG_SLOTS 2          // cached PCG graphs: FP64 solver, FP32 inner solver
 #define MFTO_TC_BTILE 3072        // bytes of one tensor-core B operand (KE, one part)
+#define MFTO_MAX_RHS 8            // load cases of the multi-RHS calls
+#define MFTO_RED_ROWS 16          // rows of the partial-sum buffers (2 per load case)
 
 // Device-resident scalars of the PCG driver and the other reductions.  Each
 // reduction site owns a ticket counter (reset by the last block).
@@ -39,6 +41,16 @@ struct PcgScalars {
   int32_t it, maxit, done, status;
   unsigned int ticket_a, ticket_b, ticket_c;
   int32_t tc_error;         // a tensor-core completion wait gave up
+};
+
+// Scalars of the multi-RHS inner CG: one set per load case, plus the flag
+// raised when every case is done.
+struct MultiScalars {
+  double rz[MFTO_MAX_RHS], pq[MFTO_MAX_RHS], alpha[MFTO_MAX_RHS], beta[MFTO_MAX_RHS];
+  double rr[MFTO_MAX_RHS], ff[MFTO_MAX_RHS], rtol2ff[MFTO_MAX_RHS];
+  int32_t done[MFTO_MAX_RHS], status[MFTO_MAX_RHS], it[MFTO_MAX_RHS];
+  int32_t all_done, maxit, nrhs;
+  unsigned int ticket_a, ticket_b, ticket_c;
 };
 
 struct MiscScalars {
@@ -74,6 +86,7 @@ struct mfto_handle {
   int kv_variant;           // 0: tiled mode-space kernel, 1: node-centric dense KE
   int occ_kv32, occ_pcg32;  // resident CTAs per SM of the FP32 block kernels
   int occ_tc[12];           // ... of the tensor-core kernels, [2 * (2 kind + split) + pcg]
+  int occ_multi[3];         // ... of the multi-RHS kernels (F64 K.V, F32 K.V, F32 CG step)
   unsigned char* d_btc;     // tensor-core B operands: [kind][hi | lo]
   uint8_t* d_fixed;         // per-node mask
   // cone filter
@@ -83,8 +96,8 @@ struct mfto_handle {
   double* d_filter_W;       // row sums W_e
   // PCG workspace (FP64)
   double *d_r, *d_z, *d_p0, *d_p1, *d_q, *d_dinv;
-  double* d_partials;       // [4 * MFTO_RED_SLOTS]
-  double* d_partials2;      // [4 * MFTO_RED_SLOTS]
+  double* d_partials;       // [MFTO_RED_ROWS * MFTO_RED_SLOTS]
+  double* d_partials2;      // [MFTO_RED_ROWS * MFTO_RED_SLOTS]
   PcgScalars* d_pcg;
   MiscScalars* d_misc;
   PcgScalars* h_pcg;        // pinned mirror
@@ -95,6 +108,14 @@ struct mfto_handle {
   float *d_r32, *d_z32, *d_p0_32, *d_p1_32, *d_q32, *d_dinv32, *d_e32, *d_E32;
   PcgScalars* d_pcg32;
   PcgScalars* h_pcg32;      // pinned mirror
+  // multi-RHS workspace ([max_rhs][n_dof] each), allocated when max_rhs > 1
+  int max_rhs;
+  double* m_q64;
+  float *m_r32, *m_z32, *m_p0, *m_p1, *m_q32, *m_e32;
+  MultiScalars* m_pcg;
+  MultiScalars* h_mpcg;     // pinned mirror
+  double* m_out;            // [2 * MFTO_MAX_RHS] outer residual sums
+  struct MultiGraph* m_graph;  // captured chunk of the multi-RHS inner CG
   // solver used by mfto_simp_step (mfto_set_solver)
   int32_t solver_form;      // MFTO_FORM_F64: plain FP64 PCG; else IR with this inner form
   double inner_tol;
@@ -346,6 +367,8 @@ struct PcgVecs {
   int form;                 // K.v form of this solve
 };
 mfto_status tc_init(mfto_handle* h);
+mfto_status multi_init(mfto_handle* h);
+void multi_graph_release(mfto_handle* h);
 mfto_status tc_upload_b(mfto_handle* h, const double* ke);
 bool tc_form(int form);
 mfto_status kv_tc_launch(mfto_handle* h, int form, const float* E, const float* v, float* y,

@@ -31,6 +31,7 @@ extern "C" void mfto_default_params(mfto_params* p) {
   p->rtol = 1e-8;
   p->maxit = 10000;
   p->check_every = 32;
+  p->max_rhs = 1;
 }
 
 // KE = T^-1 Kt T: Kt is the element operator in the per-axis (sum, difference)
@@ -117,24 +118,28 @@ static mfto_status check_params(mfto_handle* h, const mfto_params* p) {
   MFTO_REQUIRE(h, p->maxit >= 1, "maxit must be >= 1");
   MFTO_REQUIRE(h, p->check_every >= 2 && p->check_every % 2 == 0,
                "check_every must be even and >= 2");
+  MFTO_REQUIRE(h, p->max_rhs >= 1 && p->max_rhs <= MFTO_MAX_RHS, "max_rhs must lie in 1..8");
   return MFTO_OK;
 }
 
 static void free_handle(mfto_handle* h) {
   if (!h) return;
   pcg_graph_release(h);
+  multi_graph_release(h);
   void* ptrs[] = {h->d_ke64, h->d_ke32, h->d_fixed, h->d_stencil_off, h->d_stencil_w,
                   h->d_filter_W, h->d_r, h->d_z, h->d_p0, h->d_p1, h->d_q, h->d_dinv,
                   h->d_partials, h->d_partials2, h->d_pcg, h->d_misc, h->d_rho_phys,
                   h->d_E, h->d_dc, h->d_dc_phys, h->d_r32, h->d_z32, h->d_p0_32,
                   h->d_p1_32, h->d_q32, h->d_dinv32, h->d_e32, h->d_E32, h->d_pcg32,
-                  h->d_btc};
+                  h->d_btc, h->m_q64, h->m_r32, h->m_z32, h->m_p0, h->m_p1, h->m_q32,
+                  h->m_e32, h->m_pcg, h->m_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->h_pcg) cudaFreeHost(h->h_pcg);
   if (h->h_misc) cudaFreeHost(h->h_misc);
   if (h->h_pcg32) cudaFreeHost(h->h_pcg32);
+  if (h->h_mpcg) cudaFreeHost(h->h_mpcg);
   for (size_t i = 0; i < h->ev.start.size(); ++i) {
     cudaEventDestroy(h->ev.start[i]);
     cudaEventDestroy(h->ev.stop[i]);
@@ -217,6 +222,7 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   h->n_dof = 3 * h->n_node;
   if (h->n_dof > (int64_t)INT32_MAX) { free_handle(h); return MFTO_INVALID_ARG; }
   if (check_params(h, params) != MFTO_OK) { free_handle(h); return MFTO_INVALID_ARG; }
+  h->max_rhs = params->max_rhs;
   h->p = *params;
   h->solver_form = MFTO_FORM_F64;
   h->inner_tol = 1e-2;
@@ -243,8 +249,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   A((void**)&h->d_p1, nd);
   A((void**)&h->d_q, nd);
   A((void**)&h->d_dinv, nd);
-  A((void**)&h->d_partials, sizeof(double) * 4 * MFTO_RED_SLOTS);
-  A((void**)&h->d_partials2, sizeof(double) * 4 * MFTO_RED_SLOTS);
+  A((void**)&h->d_partials, sizeof(double) * MFTO_RED_ROWS * MFTO_RED_SLOTS);
+  A((void**)&h->d_partials2, sizeof(double) * MFTO_RED_ROWS * MFTO_RED_SLOTS);
   A((void**)&h->d_pcg, sizeof(PcgScalars));
   A((void**)&h->d_misc, sizeof(MiscScalars));
   A((void**)&h->d_rho_phys, ne);
@@ -262,6 +268,19 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   A((void**)&h->d_E32, sizeof(float) * h->n_elem);
   A((void**)&h->d_pcg32, sizeof(PcgScalars));
   A((void**)&h->d_btc, 3 * 2 * MFTO_TC_BTILE);
+  if (h->max_rhs > 1) {
+    const size_t m = (size_t)h->max_rhs;
+    A((void**)&h->m_q64, m * nd);
+    A((void**)&h->m_r32, m * nd32);
+    A((void**)&h->m_z32, m * nd32);
+    A((void**)&h->m_p0, m * nd32);
+    A((void**)&h->m_p1, m * nd32);
+    A((void**)&h->m_q32, m * nd32);
+    A((void**)&h->m_e32, m * nd32);
+    A((void**)&h->m_pcg, sizeof(MultiScalars));
+    A((void**)&h->m_out, sizeof(double) * 2 * MFTO_MAX_RHS);
+    if (ok && cudaMallocHost(&h->h_mpcg, sizeof(MultiScalars)) != cudaSuccess) ok = false;
+  }
   if (ok && (cudaMallocHost(&h->h_pcg, sizeof(PcgScalars)) != cudaSuccess ||
              cudaMallocHost(&h->h_misc, sizeof(MiscScalars)) != cudaSuccess ||
              cudaMallocHost(&h->h_pcg32, sizeof(PcgScalars)) != cudaSuccess))
@@ -274,12 +293,14 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   if (cudaMemcpyAsync(h->d_fixed, h_fixed, h->n_node, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_pcg, 0, sizeof(PcgScalars), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_misc, 0, sizeof(MiscScalars), h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->d_pcg32, 0, sizeof(PcgScalars), h->stream) != cudaSuccess) {
+      cudaMemsetAsync(h->d_pcg32, 0, sizeof(PcgScalars), h->stream) != cudaSuccess ||
+      (h->m_pcg && cudaMemsetAsync(h->m_pcg, 0, sizeof(MultiScalars), h->stream) != cudaSuccess)) {
     free_handle(h);
     return MFTO_CUDA_ERROR;
   }
   mfto_status s = kv_tile_init(h);
   if (s == MFTO_OK) s = tc_init(h);
+  if (s == MFTO_OK) s = multi_init(h);
   if (s == MFTO_OK) s = upload_params(h);
   if (s != MFTO_OK) { free_handle(h); return s; }
   *out = h;
@@ -297,6 +318,7 @@ extern "C" mfto_status mfto_set_params(mfto_handle* h, const mfto_params* p) {
   if (!h) return MFTO_INVALID_ARG;
   mfto_status s = check_params(h, p);
   if (s != MFTO_OK) return s;
+  MFTO_REQUIRE(h, p->max_rhs == h->max_rhs, "mfto_set_params: max_rhs is fixed at mfto_create");
   h->p = *p;
   return upload_params(h);
 }

@@ -44,6 +44,13 @@ ir_accumulate(double* __restrict__ u, const float* __restrict__ e, int n) {
 
 }  // namespace
 
+mfto_status mfto_to_f32(mfto_handle* h, const double* a, float* b, int64_t n) {
+  h->launches++;
+  to_f32<<<reduction_blocks(n, MFTO_BLOCK), MFTO_BLOCK, 0, h->stream>>>(a, b, (int)n);
+  MFTO_LAUNCH_CHECK(h);
+  return MFTO_OK;
+}
+
 mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const double* E,
                    const double* f, double* u, mfto_ir_stats* st) {
   if (inner != MFTO_FORM_F32 && !tc_form(inner))

@@ -38,7 +38,7 @@ class Params(C.Structure):
     _fields_ = [("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double),
                 ("penal", C.c_double), ("rmin", C.c_double), ("volfrac", C.c_double),
                 ("move", C.c_double), ("rtol", C.c_double), ("maxit", C.c_int32),
-                ("check_every", C.c_int32)]
+                ("check_every", C.c_int32), ("max_rhs", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -88,6 +88,9 @@ SIGNATURES = {
     "mfto_pcg": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
     "mfto_ir_solve": (C.c_int32, [_P, C.c_int32, C.c_double, _P, _P, _P, C.POINTER(IrStats)]),
     "mfto_set_solver": (C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, C.c_int32]),
+    "mfto_kv_multi": (C.c_int32, [_P, C.c_int32, _P, _P, _P, C.c_int32]),
+    "mfto_ir_solve_multi": (C.c_int32, [_P, C.c_double, _P, _P, _P, C.c_int32,
+                                        C.POINTER(IrStats)]),
     "mfto_filter": (C.c_int32, [_P, _P, _P, C.c_int32]),
     "mfto_compliance_sens": (C.c_int32, [_P, _P, _P, C.POINTER(C.c_double), _P]),
     "mfto_oc_update": (C.c_int32, [_P, _P, _P, _P, C.POINTER(IterStats)]),
@@ -304,6 +307,21 @@ class Handle:
             _ptr(f, torch.float64, self.n_dof, "f"), _ptr(u, torch.float64, self.n_dof, "u"),
             C.byref(st)), self._h)
         return st
+
+    def kv_multi(self, E, V, Y, nrhs, form=FORM_F64):
+        dt = self._dt(form)
+        _check("mfto_kv_multi", lib().mfto_kv_multi(
+            self._h, form, _ptr(E, dt, self.n_elem, "E"), _ptr(V, dt, nrhs * self.n_dof, "V"),
+            _ptr(Y, dt, nrhs * self.n_dof, "Y"), nrhs), self._h)
+
+    def ir_solve_multi(self, E, F, U, nrhs, inner_tol=1e-2):
+        import torch
+        st = (IrStats * nrhs)()
+        _check("mfto_ir_solve_multi", lib().mfto_ir_solve_multi(
+            self._h, inner_tol, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(F, torch.float64, nrhs * self.n_dof, "F"),
+            _ptr(U, torch.float64, nrhs * self.n_dof, "U"), nrhs, st), self._h)
+        return list(st)
 
     def set_solver(self, form=FORM_F64, inner_tol=1e-2, inner_maxit=10000, max_outer=50):
         _check("mfto_set_solver", lib().mfto_set_solver(self._h, form, inner_tol, inner_maxit,
