@@ -246,6 +246,46 @@ mfto_status mfto_ir_solve_multi(mfto_handle* h, double inner_tol, const double* 
                                 const double* d_F, double* d_U, int32_t nrhs,
                                 mfto_ir_stats* st);
 
+/* ------------------------------------------------------------- batches -- */
+
+/* Many independent problems of uneven size solved together: every step is
+ * one persistent launch over all instances (a work list of (instance,
+ * element block) items), the inner CG chunks are captured in one CUDA graph,
+ * and per-instance sums are reduced deterministically.  The paper solves
+ * one problem at a time; a batch applies its operator (Eq. matfree) and its
+ * solver (Sec. 3.6, refined as in mfto_ir_solve) to each instance.
+ *
+ * mfto_batch_create: count (1..256) meshes with the same element edge h,
+ * shared parameters (E0, Emin, nu, rtol, maxit, check_every are used),
+ * h_fixed: the instances' per-node masks concatenated in instance order.
+ * Arrays passed to the batch calls concatenate the instances' arrays in the
+ * same order; mfto_batch_layout returns the offsets (count + 1 entries each,
+ * elements and DOFs). */
+typedef struct mfto_batch mfto_batch;
+mfto_status mfto_batch_create(int32_t count, const mfto_mesh* meshes, const mfto_params* params,
+                              const uint8_t* h_fixed, void* stream, mfto_batch** out);
+mfto_status mfto_batch_destroy(mfto_batch* b);
+const char* mfto_batch_last_error(const mfto_batch* b);
+mfto_status mfto_batch_layout(const mfto_batch* b, int64_t* h_elem_off, int64_t* h_dof_off);
+/* d_Y = K(E) d_V for every instance, one launch (forms F64, F32). */
+mfto_status mfto_batch_kv(mfto_batch* b, mfto_form form, const void* d_E, const void* d_V,
+                          void* d_Y);
+/* Element-block shape of the batch kernels (8x8x4, 8x4x8, 4x8x8, 16x4x4
+ * elements = 0..3): mfto_batch_autotune times an FP32 K.V of the batch
+ * `reps` times per shape (CUDA events), keeps the fastest, and reports the
+ * per-launch times in h_ms_out[4] (may be NULL) and the choice. */
+mfto_status mfto_batch_autotune(mfto_batch* b, int32_t reps, double* h_ms_out, int32_t* chosen);
+mfto_status mfto_batch_set_shape(mfto_batch* b, int32_t shape);
+/* Mixed-precision solve of every instance (FP64 refinement per instance
+ * around one FP32 inner CG over all live instances): d_E FP64 [elements],
+ * d_F, d_U FP64 [DOFs] (d_U: initial guesses in, solutions out), st: count
+ * entries.  Synchronises the stream. */
+mfto_status mfto_batch_solve(mfto_batch* b, double inner_tol, const double* d_E, const double* d_F,
+                             double* d_U, int32_t inner_maxit, int32_t max_outer,
+                             mfto_ir_stats* st);
+/* Kernels launched for this batch so far (graph kernel nodes included). */
+mfto_status mfto_batch_launch_count(const mfto_batch* b, int64_t* n);
+
 /* Select the linear solver of mfto_simp_step: form MFTO_FORM_F64 = plain FP64
  * Jacobi-PCG (default); any other form = mfto_ir_solve with that inner form,
  * inner tolerance inner_tol (> 0, < 1), inner iteration cap inner_maxit and

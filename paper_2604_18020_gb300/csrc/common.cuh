@@ -366,6 +366,7 @@ struct PcgVecs {
   double *part_a, *part_b;
   int form;                 // K.v form of this solve
 };
+void mode_coefficients(double nu, double h, ModeCoef<double>* c64, ModeCoef<float>* c32);
 mfto_status tc_init(mfto_handle* h);
 mfto_status multi_init(mfto_handle* h);
 void multi_graph_release(mfto_handle* h);

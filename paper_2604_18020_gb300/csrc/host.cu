@@ -149,6 +149,29 @@ static void free_handle(mfto_handle* h) {
 
 mfto_status filter_rowsums(mfto_handle* h);  // filter.cu
 
+// Mode-space coefficients of the unit element operator (kv_tile.cuh): the
+// diagonal terms of mode_operator() and the off-diagonal couplings, with
+// the 1/8 of the inverse transform folded in.
+void mode_coefficients(double nu, double hh, ModeCoef<double>* c64, ModeCoef<float>* c32) {
+  const ModeOperator op = mode_operator(1.0, nu, hh);
+  memset(c64, 0, sizeof(*c64));
+  for (int t = 0; t < op.n_terms; ++t)
+    if (op.out_comp[t] == op.in_comp[t] && op.out_mode[t] == op.in_mode[t])
+      c64->diag[op.out_comp[t]][op.out_mode[t]] = op.coef[t] / 8.0;
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
+  const double M[2] = {hh / 2.0, hh / 6.0};
+  for (int t = 0; t < 2; ++t) {
+    c64->lamM[t] = lam * M[t] / 8.0;
+    c64->muM[t] = mu * M[t] / 8.0;
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int m = 0; m < 8; ++m) c32->diag[c][m] = (float)c64->diag[c][m];
+  for (int t = 0; t < 2; ++t) {
+    c32->lamM[t] = (float)c64->lamM[t];
+    c32->muM[t] = (float)c64->muM[t];
+  }
+}
+
 static mfto_status upload_params(mfto_handle* h) {
   double ke[576];
   float ke32[576];
@@ -159,27 +182,7 @@ static mfto_status upload_params(mfto_handle* h) {
     mfto_status s = tc_upload_b(h, ke);
     if (s != MFTO_OK) return s;
   }
-  // mode-space coefficients (unit modulus, 1/8 of the inverse folded in)
-  {
-    const ModeOperator op = mode_operator(1.0, h->p.nu, h->mesh.h);
-    memset(&h->mc64, 0, sizeof(h->mc64));
-    for (int t = 0; t < op.n_terms; ++t)
-      if (op.out_comp[t] == op.in_comp[t] && op.out_mode[t] == op.in_mode[t])
-        h->mc64.diag[op.out_comp[t]][op.out_mode[t]] = op.coef[t] / 8.0;
-    const double nu = h->p.nu, hh = h->mesh.h;
-    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
-    const double M[2] = {hh / 2.0, hh / 6.0};
-    for (int t = 0; t < 2; ++t) {
-      h->mc64.lamM[t] = lam * M[t] / 8.0;
-      h->mc64.muM[t] = mu * M[t] / 8.0;
-    }
-    for (int c = 0; c < 3; ++c)
-      for (int m = 0; m < 8; ++m) h->mc32.diag[c][m] = (float)h->mc64.diag[c][m];
-    for (int t = 0; t < 2; ++t) {
-      h->mc32.lamM[t] = (float)h->mc64.lamM[t];
-      h->mc32.muM[t] = (float)h->mc64.muM[t];
-    }
-  }
+  mode_coefficients(h->p.nu, h->mesh.h, &h->mc64, &h->mc32);
   MFTO_CUDA(h, cudaMemcpyAsync(h->d_ke64, ke, sizeof(ke), cudaMemcpyHostToDevice, h->stream));
   MFTO_CUDA(h, cudaMemcpyAsync(h->d_ke32, ke32, sizeof(ke32), cudaMemcpyHostToDevice, h->stream));
   int32_t n = 0;

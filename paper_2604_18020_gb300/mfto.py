@@ -89,6 +89,17 @@ SIGNATURES = {
     "mfto_ir_solve": (C.c_int32, [_P, C.c_int32, C.c_double, _P, _P, _P, C.POINTER(IrStats)]),
     "mfto_set_solver": (C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, C.c_int32]),
     "mfto_kv_multi": (C.c_int32, [_P, C.c_int32, _P, _P, _P, C.c_int32]),
+    "mfto_batch_create": (C.c_int32, [C.c_int32, C.POINTER(Mesh), C.POINTER(Params), _P, _P,
+                                      C.POINTER(_P)]),
+    "mfto_batch_destroy": (C.c_int32, [_P]),
+    "mfto_batch_last_error": (C.c_char_p, [_P]),
+    "mfto_batch_layout": (C.c_int32, [_P, _P, _P]),
+    "mfto_batch_kv": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
+    "mfto_batch_autotune": (C.c_int32, [_P, C.c_int32, _P, C.POINTER(C.c_int32)]),
+    "mfto_batch_set_shape": (C.c_int32, [_P, C.c_int32]),
+    "mfto_batch_solve": (C.c_int32, [_P, C.c_double, _P, _P, _P, C.c_int32, C.c_int32,
+                                     C.POINTER(IrStats)]),
+    "mfto_batch_launch_count": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
     "mfto_ir_solve_multi": (C.c_int32, [_P, C.c_double, _P, _P, _P, C.c_int32,
                                         C.POINTER(IrStats)]),
     "mfto_filter": (C.c_int32, [_P, _P, _P, C.c_int32]),
@@ -374,3 +385,80 @@ class Handle:
         _check("mfto_kv_timing_read",
                lib().mfto_kv_timing_read(self._h, form, C.byref(n), C.byref(ms)), self._h)
         return n.value, ms.value
+
+
+class Batch:
+    """Owns one mfto_batch: many independent meshes solved together."""
+
+    def __init__(self, meshes, fixed_masks, params: Params | None = None, h=1.0, stream=None):
+        import torch
+        self.count = len(meshes)
+        self.meshes = (Mesh * self.count)(*[Mesh(a, b, c, h) for (a, b, c) in meshes])
+        self.params = params if params is not None else default_params()
+        fixed = np.ascontiguousarray(np.concatenate([np.asarray(f, np.uint8) for f in fixed_masks]))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        bp = C.c_void_p()
+        code = lib().mfto_batch_create(self.count, self.meshes, C.byref(self.params),
+                                       fixed.ctypes.data, C.c_void_p(self.stream.cuda_stream),
+                                       C.byref(bp))
+        _check("mfto_batch_create", code)
+        self._b = bp
+        eo = np.zeros(self.count + 1, dtype=np.int64)
+        do = np.zeros(self.count + 1, dtype=np.int64)
+        self._chk("mfto_batch_layout", lib().mfto_batch_layout(self._b, eo.ctypes.data,
+                                                               do.ctypes.data))
+        self.elem_off, self.dof_off = eo, do
+        self.n_elem, self.n_dof = int(eo[-1]), int(do[-1])
+
+    def _chk(self, fn, code):
+        if code != OK:
+            raw = lib().mfto_batch_last_error(self._b) if getattr(self, "_b", None) else b""
+            raise MftoError(fn, code, raw.decode() if raw else "")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().mfto_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def kv(self, E, V, Y, form=FORM_F64):
+        import torch
+        dt = torch.float64 if form == FORM_F64 else torch.float32
+        self._chk("mfto_batch_kv", lib().mfto_batch_kv(
+            self._b, form, _ptr(E, dt, self.n_elem, "E"), _ptr(V, dt, self.n_dof, "V"),
+            _ptr(Y, dt, self.n_dof, "Y")))
+
+    def autotune(self, reps=5):
+        ms = np.zeros(4)
+        ch = C.c_int32()
+        self._chk("mfto_batch_autotune", lib().mfto_batch_autotune(self._b, reps, ms.ctypes.data,
+                                                                   C.byref(ch)))
+        return ch.value, ms
+
+    def set_shape(self, shape):
+        self._chk("mfto_batch_set_shape", lib().mfto_batch_set_shape(self._b, shape))
+
+    def solve(self, E, F, U, inner_tol=1e-2, inner_maxit=10000, max_outer=50):
+        import torch
+        st = (IrStats * self.count)()
+        self._chk("mfto_batch_solve", lib().mfto_batch_solve(
+            self._b, inner_tol, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(F, torch.float64, self.n_dof, "F"), _ptr(U, torch.float64, self.n_dof, "U"),
+            inner_maxit, max_outer, st))
+        return list(st)
+
+    def launch_count(self):
+        n = C.c_int64()
+        self._chk("mfto_batch_launch_count", lib().mfto_batch_launch_count(self._b, C.byref(n)))
+        return n.value
