@@ -4,11 +4,15 @@
 A step is one SIMP iteration of the 120 x 60 x 30 cantilever (216,000 Q1
 elements, 686,433 DOFs; x=0 face clamped, unit -y load on the bottom edge of
 the free end; V_f = 0.3, r_min = 1.5, E0 = 1, Emin = 1e-9, nu = 0.3, p = 3):
-cone filter -> SIMP modulus -> Jacobi diagonal -> Jacobi-PCG to
-||r||/||f|| <= 1e-8 (warm start) -> compliance and sensitivities -> filter
-transpose -> OC bisection.  Every step runs in the library's CUDA kernels;
-the steps continue one SIMP run from the uniform start (the warm-up steps are
-its first iterations).
+cone filter -> SIMP modulus -> Jacobi diagonal -> linear solve to
+||f - Ku||/||f|| <= 1e-8 (warm start) -> compliance and sensitivities ->
+filter transpose -> OC bisection.  Every step runs in the library's CUDA
+kernels; the steps continue one SIMP run from the uniform start (the warm-up
+steps are its first iterations).  The solve is the chosen form (--form
+mixed, default: FP64 iterative refinement around an FP32 inner Jacobi-PCG)
+or plain FP64 Jacobi-PCG (--form f64); with the mixed form the same steps
+are also run with plain FP64 from the same state ("plain_fp64": its SIMP
+iteration time and the largest relative compliance difference).
 
 value: K.v throughput of the whole step, n_elem x (K.v applications in the
 timed steps) / (device time of the timed steps), in Gelem/s, with inputs
@@ -267,6 +271,20 @@ def gpu_bench(args, rank, local_rank, world):
         e2e_ms += a.elapsed_time(b)
         h_rho.copy_(o_rho)
         h_u.copy_(o_u)
+    # plain FP64 Jacobi-PCG over the same steps from the same state, for the
+    # "plain FP64 vs chosen form" comparison (skipped when the bench is FP64)
+    fp64 = None
+    if args.form != "f64":
+        h.set_solver(mfto.FORM_F64)
+        t64, stats64, _, _, _ = timed_pass(False)
+        c64 = [s.compliance for s in stats64]
+        cf = [s.compliance for s in stats]
+        fp64 = {"simp_iter_ms": t64 / args.steps,
+                "cg_iterations": [s.cg_iterations for s in stats64],
+                "compliance": c64,
+                "max_compliance_rel_err": max(abs(a - b) / abs(b) for a, b in zip(cf, c64)),
+                "speedup_of_chosen_form": t64 / t_ms}
+        h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
     h2d = (h_rho.numel() + h_u.numel() + h_f.numel()) * 8
     d2h = (o_rho.numel() + o_u.numel()) * 8
     if dist:
@@ -326,6 +344,7 @@ def gpu_bench(args, rank, local_rank, world):
         "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "plain_fp64": fp64,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"]},
     }
@@ -369,6 +388,131 @@ def profile_run(args):
     h.close()
 
 
+def compare_run(args):
+    """Forms side by side on the GPU, one JSON line each (plain FP64 is the
+    reference; the oracle is not used here):
+      torsion 55x55x165: SIMP iterations with plain FP64 and the mixed solve
+        with every inner form and tolerance, from the same state;
+      100x50x50 cantilever, 8 load cases: the multi-RHS mixed solve against
+        8 single mixed solves and 8 plain FP64 solves;
+      64 uneven cantilevers (16x8x8 .. 48x24x24): the batched mixed solve
+        against 64 single mixed and 64 plain FP64 solves."""
+    import numpy as np
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+    out = []
+
+    def sync_time(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
+    # ---- torsion: forms
+    P = W.WORKLOADS["torsion_55x55x165"]()
+    m = P.mesh
+    h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed,
+                    params=mfto.default_params(volfrac=P.volfrac, rmin=P.rmin))
+    rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
+    u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+    f = torch.tensor(P.f, device=dev)
+    for _ in range(args.warmup):
+        h.simp_step(rho, u, f)
+    rho0, u0 = rho.clone(), u.clone()
+    forms = [("f64", None), ("f32", 1e-2), ("f32", 1e-4), ("tf32x3", 1e-2), ("f16x3", 1e-2),
+             ("bf16x3", 1e-2), ("tf32", 1e-2), ("f16", 1e-2), ("bf16", 1e-2)]
+    ref_c = None
+    for name, tol in forms:
+        h.set_solver(mfto.FORMS[name], tol or 1e-2, 10000, 30)
+        rho.copy_(rho0)
+        u.copy_(u0)
+        cs, ts, its, stat = [], [], [], []
+        for _ in range(args.steps):
+            dt, st = sync_time(lambda: h.simp_step(rho, u, f))
+            cs.append(st.compliance)
+            ts.append(dt)
+            its.append(st.cg_iterations)
+            stat.append(mfto.STATUS_NAMES[st.cg_status])
+        if ref_c is None:
+            ref_c = cs
+        out.append({"case": "torsion_55x55x165", "form": name, "inner_tol": tol,
+                    "simp_iter_ms": 1e3 * float(np.mean(ts)), "cg_iterations": its,
+                    "solve_status": stat, "compliance": cs,
+                    "compliance_rel_err_vs_f64": max(abs(a - b) / abs(b)
+                                                     for a, b in zip(cs, ref_c))})
+    h.close()
+
+    # ---- 8 load cases
+    P = W.WORKLOADS["cantilever_100x50x50_8rhs"]()
+    m = P.mesh
+    nr = P.f.shape[0]
+    h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=mfto.default_params(max_rhs=nr))
+    E = torch.full((m.n_elem,), 0.3 ** 3, dtype=torch.float64, device=dev)
+    F = torch.tensor(P.f.reshape(-1), device=dev)
+    U = torch.zeros(nr * m.n_dof, dtype=torch.float64, device=dev)
+    t_multi, sts = sync_time(lambda: h.ir_solve_multi(E, F, U, nr))
+    c_multi = [float(F[r * m.n_dof:(r + 1) * m.n_dof] @ U[r * m.n_dof:(r + 1) * m.n_dof])
+               for r in range(nr)]
+    t_single = t_f64 = 0.0
+    c64 = []
+    for r in range(nr):
+        fr = F[r * m.n_dof:(r + 1) * m.n_dof].contiguous()
+        ur = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+        dt, _ = sync_time(lambda: h.ir_solve(E, fr, ur))
+        t_single += dt
+        ur.zero_()
+        dt, _ = sync_time(lambda: h.pcg(E, fr, ur))
+        t_f64 += dt
+        c64.append(float(fr @ ur))
+    out.append({"case": "cantilever_100x50x50_8rhs", "multi_rhs_mixed_s": t_multi,
+                "single_mixed_x8_s": t_single, "plain_f64_x8_s": t_f64,
+                "statuses": [mfto.STATUS_NAMES[s.status] for s in sts],
+                "max_rel_residual": max(s.rel_residual for s in sts),
+                "compliance_rel_err_vs_f64": max(abs(a - b) / abs(b) for a, b in zip(c_multi, c64))})
+    h.close()
+
+    # ---- 64 uneven instances
+    probs = W.uneven_instances(count=64, seed=5)
+    with mfto.Batch([(p.mesh.nelx, p.mesh.nely, p.mesh.nelz) for p in probs],
+                    [p.fixed for p in probs]) as b:
+        shape, ms = b.autotune(reps=5)
+        Eb = torch.full((b.n_elem,), 0.3 ** 3, dtype=torch.float64, device=dev)
+        Fb = torch.tensor(np.concatenate([p.f for p in probs]), device=dev)
+        Ub = torch.zeros(b.n_dof, dtype=torch.float64, device=dev)
+        b.solve(Eb, Fb, Ub)                      # warm-up (graph capture)
+        Ub.zero_()
+        t_batch, sts = sync_time(lambda: b.solve(Eb, Fb, Ub))
+        offs = b.dof_off
+        c_batch = [float(Fb[offs[i]:offs[i + 1]] @ Ub[offs[i]:offs[i + 1]]) for i in range(64)]
+    t_single = t_f64 = 0.0
+    c64 = []
+    for i, p in enumerate(probs):
+        mm = p.mesh
+        with mfto.Handle(mm.nelx, mm.nely, mm.nelz, p.fixed) as hs:
+            Ei = torch.full((mm.n_elem,), 0.3 ** 3, dtype=torch.float64, device=dev)
+            fi = torch.tensor(p.f, device=dev)
+            ui = torch.zeros(mm.n_dof, dtype=torch.float64, device=dev)
+            hs.ir_solve(Ei, fi, ui)               # warm-up
+            ui.zero_()
+            dt, _ = sync_time(lambda: hs.ir_solve(Ei, fi, ui))
+            t_single += dt
+            ui.zero_()
+            hs.pcg(Ei, fi, ui)
+            ui.zero_()
+            dt, _ = sync_time(lambda: hs.pcg(Ei, fi, ui))
+            t_f64 += dt
+            c64.append(float(fi @ ui))
+    out.append({"case": "64_uneven_cantilevers", "autotuned_shape": shape,
+                "shape_ms": [float(x) for x in ms], "batched_mixed_s": t_batch,
+                "single_mixed_x64_s": t_single, "plain_f64_x64_s": t_f64,
+                "all_ok": all(s.status == mfto.OK for s in sts),
+                "compliance_rel_err_vs_f64": max(abs(a - b) / abs(b) for a, b in zip(c_batch, c64))})
+    for o in out:
+        print(json.dumps(o))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,9 +521,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-maxit", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "pcg"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "pcg", "compare"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--form", default="f64", choices=["f64", "mixed"],
+    ap.add_argument("--form", default="mixed", choices=["f64", "mixed"],
                     help="f64: plain FP64 Jacobi-PCG; mixed: FP64 iterative refinement "
                          "around an FP32 inner PCG")
     ap.add_argument("--inner-tol", type=float, default=1e-2)
@@ -394,6 +538,9 @@ def main():
         print(json.dumps(cpu_sample(args.cpu_sample, args.steps, args.maxit)))
         return
 
+    if args.mode == "compare":
+        compare_run(args)
+        return
     if args.mode != "bench":
         profile_run(args)
         return
