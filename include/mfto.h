@@ -328,6 +328,115 @@ mfto_status mfto_simp_step(mfto_handle* h, double* d_rho, double* d_u,
                            const double* d_f, double* d_rho_phys,
                            mfto_iter_stats* st);
 
+/* ------------------------------------------------------- learned part -- */
+
+/* The paper has no learned component; this part adds one on top of its
+ * solver (Sec. 3.5 refinement, Sec. 3.6 Jacobi-PCG).
+ *
+ * Network: a 3D convolutional U-Net on the node grid, padded with zeros to a
+ * multiple of 2^(levels-1) per axis.  Tensors are FP32 [channels][D][H][W]
+ * with D along z (nodes k), H along y (j), W along x (i).  levels - 1
+ * encoder levels of two 3x3x3 convolutions + ReLU with base 2^l channels,
+ * 2x2x2 average pooling between them, a bottleneck of base 2^(levels-1)
+ * channels, decoder levels with nearest upsampling and channel
+ * concatenation [upsampled, encoder output], two 3x3x3 convolutions + ReLU,
+ * and a 1x1x1 output convolution: 4 input channels (node density, load x, y,
+ * z), 3 output channels (displacement direction).  Zero padding at the grid
+ * boundary.  Parameters are one FP32 vector, layer by layer in that order,
+ * each layer's weights [c_out][c_in][kz][ky][kx] then its biases; the
+ * convolutions compute with a BF16 copy of the weights (FP32 activations and
+ * accumulation), Adam updates the FP32 master copy.  Reductions (weight and
+ * bias gradients, loss) run in a fixed order: results are reproducible.
+ *
+ * mfto_nn_create: base 1..64 channels, levels 2..6, max_voxels: the largest
+ * D*H*W that forward will see (activations are allocated for it),
+ * max_train_voxels (<= max_voxels, 0 = inference only): the largest grid of
+ * gradient / train_step; seed: He-normal initial weights, zero biases;
+ * stream: cudaStream_t of all the network's work.  MFTO_OOM when the
+ * buffers do not fit. */
+typedef struct mfto_nn mfto_nn;
+mfto_status mfto_nn_create(int32_t base, int32_t levels, int64_t max_voxels,
+                           int64_t max_train_voxels, uint64_t seed, void* stream, mfto_nn** out);
+mfto_status mfto_nn_destroy(mfto_nn* n);
+const char* mfto_nn_last_error(const mfto_nn* n);
+mfto_status mfto_nn_num_params(const mfto_nn* n, int64_t* count);
+/* host copies of the FP32 parameter vector (set_params also resets Adam) */
+mfto_status mfto_nn_get_params(mfto_nn* n, float* h_out);
+mfto_status mfto_nn_set_params(mfto_nn* n, const float* h_in);
+/* d_out [3][D][H][W] = network(d_in [4][D][H][W]); D, H, W multiples of
+ * 2^(levels-1); asynchronous.  MFTO_TOO_LARGE above max_voxels. */
+mfto_status mfto_nn_forward(mfto_nn* n, int32_t D, int32_t H, int32_t W, const float* d_in,
+                            float* d_out);
+/* Masked mean squared error of the output against d_target [3][D][H][W]
+ * (d_mask 1 where an entry counts, 0 elsewhere; the mean is over the
+ * counted entries), its gradient with respect to every parameter (copied to
+ * h_grad [num_params] when not NULL) and *loss.  Synchronises the stream. */
+mfto_status mfto_nn_gradient(mfto_nn* n, int32_t D, int32_t H, int32_t W, const float* d_in,
+                             const float* d_target, const float* d_mask, double* loss,
+                             float* h_grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * gradient of mfto_nn_gradient; *loss (may be NULL: no synchronisation) is
+ * the loss before the step. */
+mfto_status mfto_nn_train_step(mfto_nn* n, int32_t D, int32_t H, int32_t W, const float* d_in,
+                               const float* d_target, const float* d_mask, float lr,
+                               double* loss);
+mfto_status mfto_nn_launch_count(const mfto_nn* n, int64_t* count);
+
+/* Padded network grid {D, H, W} of a mesh's nodes. */
+mfto_status mfto_nn_grid(const mfto_mesh* m, int32_t levels, int32_t dims[3]);
+/* Network input [4][D][H][W] of a (density, load) pair: channel 0 is the
+ * mean rho_phys of the elements around each node, channels 1..3 the load
+ * components divided by max |load|; zero on padding. */
+mfto_status mfto_nn_features(mfto_handle* h, int32_t levels, const double* d_rho_phys,
+                             const double* d_load, float* d_x_out);
+/* Training target [3][D][H][W] = u / max |u| on the real nodes (zero on
+ * padding) and mask [3][D][H][W] = 1 on the free DOFs of the real nodes. */
+mfto_status mfto_nn_target(mfto_handle* h, int32_t levels, const double* d_u, float* d_y_out,
+                           float* d_mask_out);
+/* Network output [3][D][H][W] -> DOF vector (zero on fixed DOFs). */
+mfto_status mfto_nn_to_dofs(mfto_handle* h, int32_t levels, const float* d_y, double* d_c_out);
+/* One training sample from a solved state (E, rho_phys, f, u* = K^-1 f):
+ * k_iters = 0 gives (features(rho_phys, f), target(u*)); k_iters > 0 runs
+ * k_iters Jacobi-PCG iterations from zero to u_k and gives
+ * (features(rho_phys, f - K u_k), target(u* - u_k)), the residual and error
+ * of a partly converged solve. */
+mfto_status mfto_nn_sample(mfto_handle* h, int32_t levels, const double* d_E,
+                           const double* d_rho_phys, const double* d_f, const double* d_u_star,
+                           int32_t k_iters, float* d_x_out, float* d_y_out, float* d_mask_out);
+
+typedef struct {
+  int32_t outer_iterations;  /* FP64 refinement steps */
+  int32_t inner_iterations;  /* FP32 flexible-PCG iterations */
+  int32_t fp64_iterations;   /* FP64 Jacobi-PCG iterations of the last fallback */
+  int32_t nn_calls;          /* network evaluations */
+  int32_t fallback;          /* 0 none, 1 network switched off, 2 FP64 Jacobi-PCG */
+  int32_t status;            /* MFTO_OK only at ||f - Ku|| / ||f|| <= rtol (FP64) */
+  double rel_residual, fnorm;
+  double nn_ms;              /* device time of the network evaluations */
+  double history[64];        /* relative FP64 residual before each outer step */
+} mfto_learned_stats;
+
+/* Attach a network to the handle (NULL detaches): mfto_learned_solve and,
+ * while attached, mfto_simp_step use it.  every = 0: the network supplies
+ * the initial guess only (first iteration of the first inner solve);
+ * every > 0: also the first direction of every later inner solve and a
+ * correction at every every-th inner iteration.  MFTO_TOO_LARGE if the mesh's padded node grid
+ * exceeds the network's max_voxels.  The network must outlive the
+ * attachment. */
+mfto_status mfto_set_learned(mfto_handle* h, mfto_nn* nn, int32_t every);
+/* The learned solve: FP64 iterative refinement (outer residual f - Ku in
+ * FP64) around an inner flexible PCG in FP32 (Polak-Ribiere beta) whose
+ * preconditioner is Jacobi, replaced by the network's direction for
+ * (rho_phys, r) at the correction iterations; the first correction with
+ * u = 0 is the network's initial guess, energy-optimally scaled.  Inner
+ * tolerance, caps and rtol come from mfto_set_solver and mfto_params.  When
+ * two outer steps in a row reduce the residual by less than 10 % the
+ * network is switched off; when that stalls too, FP64 Jacobi-PCG finishes
+ * from the current iterate.  st->status is MFTO_OK only if the recomputed
+ * FP64 residual meets rtol.  Synchronises the stream. */
+mfto_status mfto_learned_solve(mfto_handle* h, const double* d_E, const double* d_rho_phys,
+                               const double* d_f, double* d_u, mfto_learned_stats* st);
+
 /* ------------------------------------------------------------- timing -- */
 
 /* When on, every K.v launch issued by the library on this handle is

@@ -22,6 +22,14 @@ applies them:
   output = conv1x1(d_0) (3 channels, no activation);
   loss = sum over unmasked entries of (output - target)^2 / (number of them).
 Arrays are [channels, nz, ny, nx]; grid sizes are multiples of 2^(L-1).
+
+Network input and target on the node grid of a mesh (nelx, nely, nelz),
+padded with zeros to multiples of 2^(L-1) per axis:
+  density channel: the mean physical density of the (up to 8) elements
+      around a node;
+  load channels:   a[3 n + c] / max |a| (a = load or residual), float32;
+  target:          u[3 n + c] / max |u|, mask 1 on free DOFs of real nodes;
+  to_dofs:         the inverse map, zero on fixed DOFs.
 """
 from __future__ import annotations
 
@@ -164,3 +172,61 @@ def mse_loss(pred, target, mask):
     n = max(float(mask.sum()), 1.0)
     diff = (pred - target) * mask
     return float((diff ** 2).sum() / n), 2.0 * diff / n
+
+
+def grid_dims(nelx, nely, nelz, levels=4):
+    """Padded node grid (D, H, W) = (z, y, x)."""
+    m = 2 ** (levels - 1)
+    up = lambda a: -(-a // m) * m
+    return up(nelz + 1), up(nely + 1), up(nelx + 1)
+
+
+def node_density(rho_phys, nelx, nely, nelz, levels=4):
+    """[D, H, W] float32: mean density of the elements around each node."""
+    D, H, W = grid_dims(nelx, nely, nelz, levels)
+    rho = np.asarray(rho_phys, dtype=np.float64).reshape(nelz, nely, nelx)
+    out = np.zeros((D, H, W), dtype=np.float32)
+    for k in range(nelz + 1):
+        for j in range(nely + 1):
+            for i in range(nelx + 1):
+                vals = [rho[ek, ej, ei]
+                        for ek in (k - 1, k) for ej in (j - 1, j) for ei in (i - 1, i)
+                        if 0 <= ek < nelz and 0 <= ej < nely and 0 <= ei < nelx]
+                out[k, j, i] = np.float32(np.mean(vals))
+    return out
+
+
+def dof_channels(a, nelx, nely, nelz, levels=4):
+    """[3, D, H, W] float32: a[3 n + c] / max |a| on the real nodes."""
+    D, H, W = grid_dims(nelx, nely, nelz, levels)
+    a32 = np.asarray(a, dtype=np.float64).astype(np.float32)
+    m = np.float32(np.abs(a32).max()) if a32.size else np.float32(0)
+    inv = np.float32(1.0) / m if m > 0 else np.float32(0)
+    out = np.zeros((3, D, H, W), dtype=np.float32)
+    out[:, :nelz + 1, :nely + 1, :nelx + 1] = (
+        a32.reshape(nelz + 1, nely + 1, nelx + 1, 3).transpose(3, 0, 1, 2) * inv)
+    return out
+
+
+def features(rho_phys, load, nelx, nely, nelz, levels=4):
+    return np.concatenate([node_density(rho_phys, nelx, nely, nelz, levels)[None],
+                           dof_channels(load, nelx, nely, nelz, levels)])
+
+
+def target_mask(fixed_dofs_mask, nelx, nely, nelz, levels=4):
+    """[3, D, H, W] float32 mask: 1 on free DOFs of real nodes.
+    fixed_dofs_mask: bool [n_dof] (True = fixed)."""
+    D, H, W = grid_dims(nelx, nely, nelz, levels)
+    out = np.zeros((3, D, H, W), dtype=np.float32)
+    free = (~np.asarray(fixed_dofs_mask, dtype=bool)).astype(np.float32)
+    out[:, :nelz + 1, :nely + 1, :nelx + 1] = free.reshape(
+        nelz + 1, nely + 1, nelx + 1, 3).transpose(3, 0, 1, 2)
+    return out
+
+
+def to_dofs(y, fixed_dofs_mask, nelx, nely, nelz):
+    """[3, D, H, W] -> DOF vector, zero on fixed DOFs."""
+    c = np.asarray(y)[:, :nelz + 1, :nely + 1, :nelx + 1].transpose(1, 2, 3, 0).reshape(-1)
+    c = c.astype(np.float64)
+    c[np.asarray(fixed_dofs_mask, dtype=bool)] = 0.0
+    return c

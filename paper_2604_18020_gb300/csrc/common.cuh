@@ -121,6 +121,8 @@ struct mfto_handle {
   double inner_tol;
   int32_t inner_maxit;
   int32_t max_outer;
+  // learned solve (learned.cu): network, correction period and its buffers
+  struct LearnedWs* learned;
   // PCG graph cache: one captured chunk of check_every iterations per solver
   struct PcgGraph* pcg_graph[MFTO_PCG_SLOTS];
   // kernels launched on behalf of this handle (graph kernel nodes included)
@@ -366,6 +368,10 @@ struct PcgVecs {
   double *part_a, *part_b;
   int form;                 // K.v form of this solve
 };
+mfto_status learned_run(mfto_handle* h, const double* E, const double* rho_phys, const double* f,
+                        double* u, mfto_learned_stats* st);
+bool learned_active(const mfto_handle* h);
+void learned_release(mfto_handle* h);
 void mode_coefficients(double nu, double h, ModeCoef<double>* c64, ModeCoef<float>* c32);
 mfto_status tc_init(mfto_handle* h);
 mfto_status multi_init(mfto_handle* h);

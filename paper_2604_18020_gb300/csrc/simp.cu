@@ -189,7 +189,15 @@ extern "C" mfto_status mfto_simp_step(mfto_handle* h, double* rho, double* u, co
   s = modulus_launch(h, MFTO_FORM_F64, rho_phys, h->d_E);
   if (s != MFTO_OK) return s;
   mfto_solve_stats ss;
-  if (h->solver_form == MFTO_FORM_F64) {
+  if (learned_active(h)) {
+    mfto_learned_stats ls;
+    s = learned_run(h, h->d_E, rho_phys, f, u, &ls);
+    if (s != MFTO_OK) return s;
+    ss.iterations = ls.inner_iterations + ls.fp64_iterations;
+    ss.status = ls.status;
+    ss.rel_residual = ls.rel_residual;
+    ss.fnorm = ls.fnorm;
+  } else if (h->solver_form == MFTO_FORM_F64) {
     s = pcg_run(h, h->d_E, f, u, &ss);
     if (s != MFTO_OK) return s;
   } else {

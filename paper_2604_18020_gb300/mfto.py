@@ -59,6 +59,14 @@ class IrStats(C.Structure):
                 ("fnorm", C.c_double), ("history", C.c_double * 64)]
 
 
+class LearnedStats(C.Structure):
+    _fields_ = [("outer_iterations", C.c_int32), ("inner_iterations", C.c_int32),
+                ("fp64_iterations", C.c_int32), ("nn_calls", C.c_int32),
+                ("fallback", C.c_int32), ("status", C.c_int32),
+                ("rel_residual", C.c_double), ("fnorm", C.c_double), ("nn_ms", C.c_double),
+                ("history", C.c_double * 64)]
+
+
 class MftoError(RuntimeError):
     def __init__(self, fn, code, msg=""):
         super().__init__(f"{fn} -> {STATUS_NAMES.get(code, code)}: {msg}")
@@ -112,6 +120,26 @@ SIGNATURES = {
                                                  C.c_double, C.c_double, _P, _P, _P,
                                                  C.POINTER(C.c_double), _P]),
     "mfto_kv_timing": (C.c_int32, [_P, C.c_int32]),
+    "mfto_nn_create": (C.c_int32, [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_uint64, _P,
+                                   C.POINTER(_P)]),
+    "mfto_nn_destroy": (C.c_int32, [_P]),
+    "mfto_nn_last_error": (C.c_char_p, [_P]),
+    "mfto_nn_num_params": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
+    "mfto_nn_get_params": (C.c_int32, [_P, _P]),
+    "mfto_nn_set_params": (C.c_int32, [_P, _P]),
+    "mfto_nn_forward": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P]),
+    "mfto_nn_gradient": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P,
+                                     C.POINTER(C.c_double), _P]),
+    "mfto_nn_train_step": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P,
+                                       C.c_float, C.POINTER(C.c_double)]),
+    "mfto_nn_launch_count": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
+    "mfto_nn_grid": (C.c_int32, [C.POINTER(Mesh), C.c_int32, _P]),
+    "mfto_nn_features": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
+    "mfto_nn_target": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
+    "mfto_nn_to_dofs": (C.c_int32, [_P, C.c_int32, _P, _P]),
+    "mfto_nn_sample": (C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, _P, _P, _P]),
+    "mfto_set_learned": (C.c_int32, [_P, _P, C.c_int32]),
+    "mfto_learned_solve": (C.c_int32, [_P, _P, _P, _P, _P, C.POINTER(LearnedStats)]),
     "mfto_kv_timing_read": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double)]),
 }
@@ -385,6 +413,149 @@ class Handle:
         _check("mfto_kv_timing_read",
                lib().mfto_kv_timing_read(self._h, form, C.byref(n), C.byref(ms)), self._h)
         return n.value, ms.value
+
+
+    # ---- learned part
+    def nn_grid(self, levels=4):
+        return nn_grid(self.mesh.nelx, self.mesh.nely, self.mesh.nelz, levels)
+
+    def _vox(self, levels):
+        D, H, W = self.nn_grid(levels)
+        return D * H * W
+
+    def nn_features(self, rho_phys, load, x, levels=4):
+        import torch
+        _check("mfto_nn_features", lib().mfto_nn_features(
+            self._h, levels, _ptr(rho_phys, torch.float64, self.n_elem, "rho_phys"),
+            _ptr(load, torch.float64, self.n_dof, "load"),
+            _ptr(x, torch.float32, 4 * self._vox(levels), "x")), self._h)
+
+    def nn_target(self, u, y, mask, levels=4):
+        import torch
+        V = self._vox(levels)
+        _check("mfto_nn_target", lib().mfto_nn_target(
+            self._h, levels, _ptr(u, torch.float64, self.n_dof, "u"),
+            _ptr(y, torch.float32, 3 * V, "y"), _ptr(mask, torch.float32, 3 * V, "mask")),
+            self._h)
+
+    def nn_to_dofs(self, y, c, levels=4):
+        import torch
+        _check("mfto_nn_to_dofs", lib().mfto_nn_to_dofs(
+            self._h, levels, _ptr(y, torch.float32, 3 * self._vox(levels), "y"),
+            _ptr(c, torch.float64, self.n_dof, "c")), self._h)
+
+    def nn_sample(self, E, rho_phys, f, u_star, k_iters, x, y, mask, levels=4):
+        import torch
+        V = self._vox(levels)
+        _check("mfto_nn_sample", lib().mfto_nn_sample(
+            self._h, levels, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(rho_phys, torch.float64, self.n_elem, "rho_phys"),
+            _ptr(f, torch.float64, self.n_dof, "f"), _ptr(u_star, torch.float64, self.n_dof, "u"),
+            k_iters, _ptr(x, torch.float32, 4 * V, "x"), _ptr(y, torch.float32, 3 * V, "y"),
+            _ptr(mask, torch.float32, 3 * V, "mask")), self._h)
+
+    def set_learned(self, net, every=0):
+        self._net = net   # keep the network alive while attached
+        _check("mfto_set_learned", lib().mfto_set_learned(
+            self._h, net._n if net is not None else None, every), self._h)
+
+    def learned_solve(self, E, rho_phys, f, u) -> LearnedStats:
+        import torch
+        st = LearnedStats()
+        _check("mfto_learned_solve", lib().mfto_learned_solve(
+            self._h, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(rho_phys, torch.float64, self.n_elem, "rho_phys"),
+            _ptr(f, torch.float64, self.n_dof, "f"), _ptr(u, torch.float64, self.n_dof, "u"),
+            C.byref(st)), self._h)
+        return st
+
+
+def nn_grid(nelx, nely, nelz, levels=4):
+    dims = np.zeros(3, dtype=np.int32)
+    m = Mesh(nelx, nely, nelz, 1.0)
+    _check("mfto_nn_grid", lib().mfto_nn_grid(C.byref(m), levels, dims.ctypes.data))
+    return tuple(int(d) for d in dims)
+
+
+class Net:
+    """Owns one mfto_nn (the U-Net of the learned solve)."""
+
+    def __init__(self, base=14, levels=4, max_voxels=1, max_train_voxels=0, seed=0, stream=None):
+        import torch
+        self.base, self.levels = base, levels
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        np_ = C.c_void_p()
+        _check("mfto_nn_create", lib().mfto_nn_create(
+            base, levels, int(max_voxels), int(max_train_voxels), seed,
+            C.c_void_p(self.stream.cuda_stream), C.byref(np_)))
+        self._n = np_
+        cnt = C.c_int64()
+        self._chk("mfto_nn_num_params", lib().mfto_nn_num_params(self._n, C.byref(cnt)))
+        self.num_params = cnt.value
+
+    def _chk(self, fn, code):
+        if code != OK:
+            raw = lib().mfto_nn_last_error(self._n) if getattr(self, "_n", None) else b""
+            raise MftoError(fn, code, raw.decode() if raw else "")
+
+    def close(self):
+        if getattr(self, "_n", None):
+            lib().mfto_nn_destroy(self._n)
+            self._n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params, dtype=np.float32)
+        self._chk("mfto_nn_get_params", lib().mfto_nn_get_params(self._n, out.ctypes.data))
+        return out
+
+    def set_params(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        if params.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters, got {params.size}")
+        self._chk("mfto_nn_set_params", lib().mfto_nn_set_params(self._n, params.ctypes.data))
+
+    def forward(self, x, out, dims):
+        import torch
+        D, H, W = dims
+        V = D * H * W
+        self._chk("mfto_nn_forward", lib().mfto_nn_forward(
+            self._n, D, H, W, _ptr(x, torch.float32, 4 * V, "x"),
+            _ptr(out, torch.float32, 3 * V, "out")))
+
+    def gradient(self, x, target, mask, dims):
+        """(loss, gradient as a float32 numpy vector)"""
+        import torch
+        D, H, W = dims
+        V = D * H * W
+        loss = C.c_double()
+        g = np.zeros(self.num_params, dtype=np.float32)
+        self._chk("mfto_nn_gradient", lib().mfto_nn_gradient(
+            self._n, D, H, W, _ptr(x, torch.float32, 4 * V, "x"),
+            _ptr(target, torch.float32, 3 * V, "target"), _ptr(mask, torch.float32, 3 * V, "mask"),
+            C.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def train_step(self, x, target, mask, dims, lr=1e-3, want_loss=True):
+        import torch
+        D, H, W = dims
+        V = D * H * W
+        loss = C.c_double()
+        self._chk("mfto_nn_train_step", lib().mfto_nn_train_step(
+            self._n, D, H, W, _ptr(x, torch.float32, 4 * V, "x"),
+            _ptr(target, torch.float32, 3 * V, "target"), _ptr(mask, torch.float32, 3 * V, "mask"),
+            lr, C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def launch_count(self):
+        n = C.c_int64()
+        self._chk("mfto_nn_launch_count", lib().mfto_nn_launch_count(self._n, C.byref(n)))
+        return n.value
 
 
 class Batch:

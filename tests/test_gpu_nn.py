@@ -1,0 +1,216 @@
+"""The learned part on the GPU against the FP64 oracle: the U-Net forward
+pass and every parameter gradient (BF16 weights on both sides, FP32 against
+FP64 arithmetic: max error <= 1e-4 of the largest reference value per
+tensor), the network input/target builders, training, and the learned
+solve (accepted only at the FP64 residual tolerance, checked by the
+oracle's own residual)."""
+import numpy as np
+import pytest
+
+from oracle import fem, nn as onn
+from paper_2604_18020_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_values(a):
+    """float32 values of a rounded to bfloat16 (nearest, ties to even)."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def oracle_params(base, levels, seed):
+    specs = onn.layer_specs(in_ch=4, out_ch=3, base=base, levels=levels)
+    params = onn.init_params(specs, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    for name, _, _, _ in specs:
+        params[name + ".w"] = bf16_values(params[name + ".w"]).astype(np.float64)
+        params[name + ".b"] = rng.normal(0, 0.1, params[name + ".b"].shape).astype(
+            np.float32).astype(np.float64)
+    flat = np.concatenate([np.concatenate([params[n + ".w"].reshape(-1), params[n + ".b"]])
+                           for n, _, _, _ in specs]).astype(np.float32)
+    return specs, params, flat
+
+
+def rel_err(got, ref):
+    return np.abs(np.asarray(got, np.float64) - ref).max() / max(np.abs(ref).max(), 1e-30)
+
+
+@pytest.mark.parametrize("base,dims", [(3, (8, 16, 24)), (2, (16, 16, 24))])
+def test_forward_matches_oracle(cuda, base, dims):
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    specs, params, flat = oracle_params(base, 4, seed=11)
+    D, H, Wd = dims
+    x = np.random.default_rng(2).standard_normal((4, D, H, Wd)).astype(np.float32)
+    ref, _ = onn.forward(params, x.astype(np.float64), levels=4)
+    net = mfto.Net(base=base, levels=4, max_voxels=D * H * Wd)
+    net.set_params(flat)
+    assert net.num_params == flat.size
+    assert np.array_equal(net.get_params(), flat)
+    out = torch.zeros(3 * D * H * Wd, dtype=torch.float32, device=cuda)
+    net.forward(torch.tensor(x, device=cuda).reshape(-1), out, dims)
+    got = out.cpu().numpy().reshape(3, D, H, Wd)
+    assert rel_err(got, ref) <= 1e-4
+
+
+def test_gradients_match_oracle(cuda):
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    base, dims = 2, (16, 16, 24)            # 6144 voxels: 2 gradient chunks at level 0
+    specs, params, flat = oracle_params(base, 4, seed=5)
+    D, H, Wd = dims
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((4, D, H, Wd)).astype(np.float32)
+    t = rng.standard_normal((3, D, H, Wd)).astype(np.float32)
+    mask = (rng.random((3, D, H, Wd)) > 0.3).astype(np.float32)
+    out, cache = onn.forward(params, x.astype(np.float64))
+    loss_ref, dout = onn.mse_loss(out, t.astype(np.float64), mask.astype(np.float64))
+    g_ref = onn.backward(params, cache, dout)
+    net = mfto.Net(base=base, levels=4, max_voxels=D * H * Wd, max_train_voxels=D * H * Wd)
+    net.set_params(flat)
+    dev = lambda a: torch.tensor(a, device=cuda).reshape(-1)
+    loss, g = net.gradient(dev(x), dev(t), dev(mask), dims)
+    assert abs(loss - loss_ref) <= 1e-5 * abs(loss_ref)
+    off = 0
+    for name, ci, co, k in specs:
+        nw = co * ci * k ** 3
+        assert rel_err(g[off:off + nw], g_ref[name + ".w"].reshape(-1)) <= 1e-4, name
+        off += nw
+        assert rel_err(g[off:off + co], g_ref[name + ".b"]) <= 1e-4, name
+        off += co
+    assert off == g.size
+    # fixed reduction order: a second evaluation is bit-identical
+    loss2, g2 = net.gradient(dev(x), dev(t), dev(mask), dims)
+    assert loss2 == loss and np.array_equal(g2, g)
+
+
+def test_features_targets_match_oracle(cuda):
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(13, 6, 5)
+    m = P.mesh
+    rng = np.random.default_rng(9)
+    rho = rng.uniform(0.01, 1.0, m.n_elem)
+    u = rng.standard_normal(m.n_dof)
+    fd = fem.dof_mask(P.fixed)
+    u[fd] = 0.0
+    dims = onn.grid_dims(m.nelx, m.nely, m.nelz)
+    V = int(np.prod(dims))
+    with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
+        assert h.nn_grid() == dims
+        x = torch.zeros(4 * V, dtype=torch.float32, device=cuda)
+        y = torch.zeros(3 * V, dtype=torch.float32, device=cuda)
+        mk = torch.zeros(3 * V, dtype=torch.float32, device=cuda)
+        h.nn_features(torch.tensor(rho, device=cuda), torch.tensor(P.f, device=cuda), x)
+        h.nn_target(torch.tensor(u, device=cuda), y, mk)
+        c = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+        h.nn_to_dofs(y, c)
+        xg = x.cpu().numpy().reshape(4, *dims)
+        yg = y.cpu().numpy().reshape(3, *dims)
+    xr = onn.features(rho, P.f, m.nelx, m.nely, m.nelz)
+    assert np.abs(xg[0] - xr[0]).max() <= 1e-7
+    assert np.abs(xg[1:] - xr[1:]).max() <= 1e-6
+    yr = onn.dof_channels(u, m.nelx, m.nely, m.nelz)
+    assert np.abs(yg - yr).max() <= 1e-6
+    assert np.array_equal(mk.cpu().numpy().reshape(3, *dims),
+                          onn.target_mask(fd, m.nelx, m.nely, m.nelz))
+    assert np.array_equal(c.cpu().numpy(), onn.to_dofs(yg, fd, m.nelx, m.nely, m.nelz))
+
+
+def test_training_reduces_loss(cuda):
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(16, 8, 8)
+    m = P.mesh
+    dims = onn.grid_dims(m.nelx, m.nely, m.nelz)
+    V = int(np.prod(dims))
+    with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
+        rho = torch.tensor(W.rho_random(m, seed=3, lo=0.1, hi=1.0), device=cuda)
+        E = torch.zeros(m.n_elem, dtype=torch.float64, device=cuda)
+        h.simp_modulus(rho, E)
+        f = torch.tensor(P.f, device=cuda)
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+        assert h.pcg(E, f, u).status == mfto.OK
+        x = torch.zeros(4 * V, dtype=torch.float32, device=cuda)
+        y = torch.zeros(3 * V, dtype=torch.float32, device=cuda)
+        mk = torch.zeros(3 * V, dtype=torch.float32, device=cuda)
+        h.nn_sample(E, rho, f, u, 0, x, y, mk)
+        net = mfto.Net(base=4, levels=4, max_voxels=V, max_train_voxels=V, seed=1)
+        losses = [net.train_step(x, y, mk, dims, lr=3e-3) for _ in range(80)]
+    assert all(np.isfinite(losses))
+    assert losses[-1] < 0.3 * losses[0], (losses[0], losses[-1])
+
+
+def _setup_solve(cuda, P, seed):
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    m = P.mesh
+    h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed)
+    rho = torch.tensor(W.rho_random(m, seed=seed, lo=0.05, hi=1.0), device=cuda)
+    E = torch.zeros(m.n_elem, dtype=torch.float64, device=cuda)
+    h.simp_modulus(rho, E)
+    return h, rho, E, torch.tensor(P.f, device=cuda)
+
+
+def _true_rel(P, E, u):
+    m = P.mesh
+    edof = fem.edof_table_fast(m.nelx, m.nely, m.nelz)
+    fd = fem.dof_mask(P.fixed)
+    r = P.f - fem.kv(fem.ke_exact(), E, edof, u, fd)
+    return np.linalg.norm(r) / np.linalg.norm(P.f)
+
+
+@pytest.mark.parametrize("every", [0, 25])
+def test_learned_solve_accepts_only_at_rtol(cuda, every):
+    """An untrained network: the flexible PCG must still reach the FP64
+    tolerance (the line search makes a poor direction harmless)."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(24, 12, 12)
+    h, rho, E, f = _setup_solve(cuda, P, seed=21)
+    dims = h.nn_grid()
+    net = mfto.Net(base=4, levels=4, max_voxels=int(np.prod(dims)), seed=2)
+    h.set_learned(net, every=every)
+    h.set_solver(mfto.FORM_F32, inner_tol=1e-2)
+    u = torch.zeros(P.mesh.n_dof, dtype=torch.float64, device=cuda)
+    st = h.learned_solve(E, rho, f, u)
+    assert st.status == mfto.OK, (st.status, st.fallback, st.rel_residual)
+    assert st.nn_calls >= 1 and st.outer_iterations >= 1
+    assert st.rel_residual <= 1e-8
+    assert _true_rel(P, E.cpu().numpy(), u.cpu().numpy()) <= 1.5e-8
+    h.close()
+
+
+def test_learned_solve_fallback_chain(cuda):
+    """One inner iteration per outer step cannot reduce the residual by 10 %
+    twice in a row: the network is switched off, then FP64 Jacobi-PCG
+    finishes; the result is still accepted only at rtol."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(16, 8, 8)
+    h, rho, E, f = _setup_solve(cuda, P, seed=4)
+    dims = h.nn_grid()
+    net = mfto.Net(base=2, levels=4, max_voxels=int(np.prod(dims)), seed=3)
+    h.set_learned(net, every=0)
+    h.set_solver(mfto.FORM_F32, inner_tol=1e-2, inner_maxit=1, max_outer=200)
+    u = torch.zeros(P.mesh.n_dof, dtype=torch.float64, device=cuda)
+    st = h.learned_solve(E, rho, f, u)
+    assert st.fallback == 2
+    assert st.fp64_iterations > 0
+    assert st.status == mfto.OK
+    assert _true_rel(P, E.cpu().numpy(), u.cpu().numpy()) <= 1.5e-8
+    h.close()
+
+
+def test_set_learned_checks_size(cuda):
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(24, 12, 12)
+    m = P.mesh
+    with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
+        net = mfto.Net(base=2, levels=4, max_voxels=1000)
+        with pytest.raises(mfto.MftoError) as e:
+            h.set_learned(net)
+        assert e.value.code == mfto.TOO_LARGE

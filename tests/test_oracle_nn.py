@@ -59,3 +59,41 @@ def test_gradients_central_differences():
             fd = (lp - lm) / (2 * eps)
             an = grads[name].reshape(-1)[idx]
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, idx, fd, an)
+
+
+def test_node_density_closed_forms():
+    # uniform density: every real node sees the same mean, padding is zero
+    D, H, W = nn.grid_dims(3, 2, 2)
+    assert (D, H, W) == (8, 8, 8)
+    dens = nn.node_density(np.full(12, 0.4), 3, 2, 2)
+    assert np.allclose(dens[:3, :3, :4], np.float32(0.4))
+    assert not dens[3:].any() and not dens[:, 3:].any() and not dens[:, :, 4:].any()
+    # one solid element in a void grid: its corner nodes average it with the
+    # elements around them (1 / number of elements touching the node)
+    rho = np.zeros(2 * 2 * 2)
+    rho[0] = 1.0                      # element (0, 0, 0)
+    dens = nn.node_density(rho, 2, 2, 2)
+    assert dens[0, 0, 0] == np.float32(1.0)           # corner node: 1 element
+    assert dens[0, 0, 1] == np.float32(0.5)           # edge node: 2 elements
+    assert dens[0, 1, 1] == np.float32(0.25)          # face node: 4 elements
+    assert dens[1, 1, 1] == np.float32(0.125)         # interior node: 8 elements
+    assert dens[2, 2, 2] == 0.0
+
+
+def test_dof_channels_and_inverse_map():
+    rng = np.random.default_rng(7)
+    nelx, nely, nelz = 5, 3, 2
+    n_dof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
+    a = rng.standard_normal(n_dof)
+    ch = nn.dof_channels(a, nelx, nely, nelz)
+    assert np.abs(ch).max() == np.float32(1.0)
+    # node (i, j, k) = (4, 2, 1), component 1
+    n = 4 + (nelx + 1) * (2 + (nely + 1) * 1)
+    assert abs(ch[1, 1, 2, 4] - a[3 * n + 1] / np.abs(a).max()) <= 1e-7
+    fixed = np.zeros(n_dof, dtype=bool)
+    fixed[:9] = True
+    back = nn.to_dofs(ch, fixed, nelx, nely, nelz)
+    assert not back[:9].any()
+    assert np.allclose(back[9:], (a / np.abs(a).max())[9:], rtol=1e-6, atol=1e-7)
+    mask = nn.target_mask(fixed, nelx, nely, nelz)
+    assert mask.sum() == n_dof - 9
