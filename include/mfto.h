@@ -404,6 +404,21 @@ mfto_status mfto_nn_sample(mfto_handle* h, int32_t levels, const double* d_E,
                            const double* d_rho_phys, const double* d_f, const double* d_u_star,
                            int32_t k_iters, float* d_x_out, float* d_y_out, float* d_mask_out);
 
+/* One Adam step (learning rate lr) of the network nn on the energy loss of
+ * one state (E, rho_phys, f): with c = the network's displacement direction
+ * for (rho_phys, f) on the DOFs (mfto_nn_to_dofs), a = f.c, b = c.Kc,
+ *   loss = 1 - a^2 / (b * compliance),
+ * the squared energy-norm error of the optimally scaled prediction
+ * (a / b) c relative to the solution u* of K u* = f, whose compliance f.u*
+ * the caller passes (> 0).  No displacement enters: the loss is minimal
+ * (0) exactly when c is parallel to K^-1 f (the minimum of the potential
+ * energy).  The gradient uses one FP64 K.v.  The network must have been
+ * created with max_train_voxels >= the mesh's padded node grid.  *loss (may
+ * be NULL: no synchronisation) is the loss before the step. */
+mfto_status mfto_nn_train_energy(mfto_handle* h, mfto_nn* nn, const double* d_E,
+                                 const double* d_rho_phys, const double* d_f, double compliance,
+                                 float lr, double* loss);
+
 typedef struct {
   int32_t outer_iterations;  /* FP64 refinement steps */
   int32_t inner_iterations;  /* FP32 flexible-PCG iterations */

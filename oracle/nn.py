@@ -30,6 +30,12 @@ padded with zeros to multiples of 2^(L-1) per axis:
   load channels:   a[3 n + c] / max |a| (a = load or residual), float32;
   target:          u[3 n + c] / max |u|, mask 1 on free DOFs of real nodes;
   to_dofs:         the inverse map, zero on fixed DOFs.
+
+Energy loss of a predicted direction c for the load f (no displacement
+needed): with a = f.c and b = c.Kc, the optimally scaled prediction (a/b) c
+has potential energy -a^2 / (2b); against the solution's -S/2 (S = f.u*,
+the compliance) the squared relative energy-norm error is
+  loss = 1 - a^2 / (b S),   d loss / d c = (2 a^2 / b^2 Kc - 2 a / b f) / S.
 """
 from __future__ import annotations
 
@@ -230,3 +236,22 @@ def to_dofs(y, fixed_dofs_mask, nelx, nely, nelz):
     c = c.astype(np.float64)
     c[np.asarray(fixed_dofs_mask, dtype=bool)] = 0.0
     return c
+
+
+def energy_loss(c, f, Kc, S):
+    """(loss, d loss / d c) of the energy loss above."""
+    a = float(f @ c)
+    b = float(c @ Kc)
+    return 1.0 - a * a / (b * S), (2 * a * a / (b * b) * Kc - 2 * a / b * f) / S
+
+
+def dofs_to_grid(g, fixed_dofs_mask, nelx, nely, nelz, levels=4):
+    """DOF vector -> [3, D, H, W] (zero on fixed DOFs and padding): the
+    adjoint of to_dofs."""
+    D, H, W = grid_dims(nelx, nely, nelz, levels)
+    g = np.array(g, dtype=np.float64)
+    g[np.asarray(fixed_dofs_mask, dtype=bool)] = 0.0
+    out = np.zeros((3, D, H, W))
+    out[:, :nelz + 1, :nely + 1, :nelx + 1] = g.reshape(
+        nelz + 1, nely + 1, nelx + 1, 3).transpose(3, 0, 1, 2)
+    return out

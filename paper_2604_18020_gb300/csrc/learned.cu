@@ -32,6 +32,9 @@ mfto_status nn_infer(mfto_nn* n, cudaStream_t st, int D, int H, int W, const flo
 int nn_levels(const mfto_nn* n);
 long long nn_max_voxels(const mfto_nn* n);
 const char* nn_message(const mfto_nn* n);
+mfto_status nn_train_forward(mfto_nn* n, cudaStream_t st, int D, int H, int W, const float* x,
+                             float** out);
+mfto_status nn_train_backward(mfto_nn* n, cudaStream_t st, int D, int H, int W, float lr);
 
 // decision of one correction (device)
 struct FpcgCtl {
@@ -276,6 +279,49 @@ __global__ void __launch_bounds__(MFTO_BLOCK)
 accumulate_kernel(double* __restrict__ u, const float* __restrict__ e, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     u[i] += (double)e[i];
+}
+
+// a = f.c, b = c.Kc (sum[0], sum[1])
+__global__ void __launch_bounds__(MFTO_BLOCK)
+energy_dots(const double* __restrict__ f, const double* __restrict__ c,
+            const double* __restrict__ Kc, int n, MiscScalars* s, double* partials) {
+  __shared__ double sh[64];
+  double acc[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    acc[0] += f[i] * c[i];
+    acc[1] += c[i] * Kc[i];
+  }
+  double tot[2];
+  if (last_block_reduce<2>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0) {
+    s->sum[0] = tot[0];
+    s->sum[1] = tot[1];
+  }
+}
+
+// d loss / d output on the grid for loss = 1 - a^2 / (b S):
+//   d loss / d c = (2 a^2 / b^2 Kc - 2 a / b f) / S, zero on fixed DOFs and
+// padding; the loss goes to sum[2] (1 and a zero gradient when b <= 0).
+__global__ void __launch_bounds__(MFTO_BLOCK)
+energy_grad(const double* __restrict__ f, const double* __restrict__ Kc,
+            const uint8_t* __restrict__ fixed, MiscScalars* s, double S, float* __restrict__ g,
+            Grid gr, VoxGrid vg) {
+  const int V = vg.D * vg.H * vg.W;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const double a = s->sum[0], b = s->sum[1];
+  const bool ok = b > 0.0 && S > 0.0;
+  if (v == 0) s->sum[2] = ok ? 1.0 - a * a / (b * S) : 1.0;
+  const int i = v % vg.W, j = (v / vg.W) % vg.H, k = v / (vg.W * vg.H);
+  const bool real = ok && i < gr.nx && j < gr.ny && k < gr.nz;
+  const int node = real ? i + gr.nx * (j + gr.ny * k) : 0;
+  const double ca = ok ? 2.0 * a * a / (b * b * S) : 0.0;
+  const double cf = ok ? 2.0 * a / (b * S) : 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float out = 0.f;
+    if (real && !((fixed[node] >> c) & 1)) out = (float)(ca * Kc[3 * node + c] - cf * f[3 * node + c]);
+    g[(size_t)c * V + v] = out;
+  }
 }
 
 unsigned nblk(int64_t n) { return (unsigned)((n + MFTO_BLOCK - 1) / MFTO_BLOCK); }
@@ -652,4 +698,41 @@ extern "C" mfto_status mfto_learned_solve(mfto_handle* h, const double* E, const
   if (!h) return MFTO_INVALID_ARG;
   MFTO_REQUIRE(h, E && rho_phys && f && u, "mfto_learned_solve: null pointer");
   return learned_run(h, E, rho_phys, f, u, st);
+}
+
+extern "C" mfto_status mfto_nn_train_energy(mfto_handle* h, mfto_nn* nn, const double* E,
+                                            const double* rho_phys, const double* f,
+                                            double compliance, float lr, double* loss) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, nn && E && rho_phys && f, "mfto_nn_train_energy: null pointer");
+  MFTO_REQUIRE(h, compliance > 0.0 && lr > 0.f, "mfto_nn_train_energy: compliance, lr > 0");
+  mfto_status s = ensure_ws(h, nn_levels(nn));
+  if (s != MFTO_OK) return s;
+  LearnedWs* w = h->learned;
+  s = build_features<double>(h, rho_phys, f);
+  if (s != MFTO_OK) return s;
+  float* out = nullptr;
+  s = nn_train_forward(nn, h->stream, w->D, w->H, w->W, w->x, &out);
+  if (s != MFTO_OK) return mfto_fail(h, s, "network: %s", nn_message(nn));
+  const Grid g = make_grid(h->mesh);
+  h->launches += 3;
+  to_dofs_kernel<double><<<nblk(h->n_node), MFTO_BLOCK, 0, h->stream>>>(out, w->uk, h->d_fixed, g,
+                                                                        vox(w), (int)h->n_node);
+  MFTO_LAUNCH_CHECK(h);
+  s = kv_launch(h, MFTO_FORM_F64, E, w->uk, h->d_q);
+  if (s != MFTO_OK) return s;
+  energy_dots<<<reduction_blocks(h->n_dof, MFTO_BLOCK), MFTO_BLOCK, 0, h->stream>>>(
+      f, w->uk, h->d_q, (int)h->n_dof, h->d_misc, h->d_partials);
+  energy_grad<<<nblk((int64_t)w->D * w->H * w->W), MFTO_BLOCK, 0, h->stream>>>(
+      f, h->d_q, h->d_fixed, h->d_misc, compliance, out, g, vox(w));
+  MFTO_LAUNCH_CHECK(h);
+  s = nn_train_backward(nn, h->stream, w->D, w->H, w->W, lr);
+  if (s != MFTO_OK) return mfto_fail(h, s, "network: %s", nn_message(nn));
+  if (loss) {
+    MFTO_CUDA(h, cudaMemcpyAsync(h->h_misc, h->d_misc, sizeof(MiscScalars), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+    *loss = h->h_misc->sum[2];
+  }
+  return MFTO_OK;
 }

@@ -702,6 +702,17 @@ extern "C" mfto_status mfto_nn_forward(mfto_nn* n, int32_t D, int32_t H, int32_t
 }
 
 namespace {
+mfto_status adam(mfto_nn* n, float lr) {
+  n->adam_t++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)n->adam_t), c2 = 1.f - powf(b2, (float)n->adam_t);
+  n->launches++;
+  adam_step<<<cdiv(n->n_params, 256), 256, 0, n->stream>>>(n->w32, n->w16, n->grad, n->m1, n->m2,
+                                                           n->n_params, lr, b1, b2, 1e-8f, c1, c2);
+  NCUDA(n, cudaGetLastError());
+  return MFTO_OK;
+}
+
 mfto_status gradient(mfto_nn* n, int32_t D, int32_t H, int32_t W, const float* d_in,
                      const float* d_target, const float* d_mask) {
   if (!d_in || !d_target || !d_mask) return nfail(n, MFTO_INVALID_ARG, "null pointer");
@@ -733,13 +744,8 @@ extern "C" mfto_status mfto_nn_train_step(mfto_nn* n, int32_t D, int32_t H, int3
   if (!n || !(lr > 0.f)) return MFTO_INVALID_ARG;
   mfto_status s = gradient(n, D, H, W, d_in, d_target, d_mask);
   if (s != MFTO_OK) return s;
-  n->adam_t++;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - powf(b1, (float)n->adam_t), c2 = 1.f - powf(b2, (float)n->adam_t);
-  n->launches++;
-  adam_step<<<cdiv(n->n_params, 256), 256, 0, n->stream>>>(n->w32, n->w16, n->grad, n->m1, n->m2,
-                                                           n->n_params, lr, b1, b2, 1e-8f, c1, c2);
-  NCUDA(n, cudaGetLastError());
+  s = adam(n, lr);
+  if (s != MFTO_OK) return s;
   return loss ? read_loss(n, loss) : MFTO_OK;
 }
 
@@ -764,3 +770,28 @@ mfto_status nn_infer(mfto_nn* n, cudaStream_t st, int D, int H, int W, const flo
 int nn_levels(const mfto_nn* n) { return n->levels; }
 long long nn_max_voxels(const mfto_nn* n) { return n->max_vox; }
 const char* nn_message(const mfto_nn* n) { return n->msg; }
+
+// Training with a loss the caller computes from the output (the learned
+// solve's energy loss): train_forward leaves the output in the returned
+// buffer [3][D][H][W]; the caller overwrites it with d loss / d output and
+// calls train_backward, which back-propagates and takes one Adam step.
+mfto_status nn_train_forward(mfto_nn* n, cudaStream_t st, int D, int H, int W, const float* x,
+                             float** out) {
+  mfto_status s = check_dims(n, D, H, W, true);
+  if (s != MFTO_OK) return s;
+  cudaStream_t keep = n->stream;
+  n->stream = st;
+  s = net_forward(n, x, n->dpred, Dims{D, H, W});
+  n->stream = keep;
+  *out = n->dpred;
+  return s;
+}
+
+mfto_status nn_train_backward(mfto_nn* n, cudaStream_t st, int D, int H, int W, float lr) {
+  cudaStream_t keep = n->stream;
+  n->stream = st;
+  mfto_status s = net_backward(n, n->dpred, Dims{D, H, W});
+  if (s == MFTO_OK) s = adam(n, lr);
+  n->stream = keep;
+  return s;
+}

@@ -1,11 +1,14 @@
 """Training data and training for the learned solve (the U-Net of nn.cu).
 
-Samples are (density, load, displacement) triples that the SIMP loop
-itself produces: for each SIMP iteration of a cantilever run, the filtered
-density, the load and the solved displacement, and, from the same state,
-the residual and error of partly converged Jacobi-PCG iterates (k
-iterations from zero).  Every array is built on the device by the library
-(mfto_nn_sample); this module only orders the calls and keeps the tensors.
+Training data comes from the SIMP loop itself.  The default (energy) loss
+needs, per SIMP iteration of a cantilever run, the state (modulus E, filtered
+density rho_phys) and its compliance f.u, and trains the network to minimise
+the energy-norm error of its optimally scaled prediction
+(mfto_nn_train_energy).  The MSE loss instead fits (density, load,
+displacement) triples: the solved displacement, and the residual and error
+of partly converged Jacobi-PCG iterates (mfto_nn_sample).  Every array is
+built on the device by the library; this module only orders the calls and
+keeps the tensors.
 
     python -m paper_2604_18020_gb300.learned --out weights.npz
 trains the default network (base 14, 4 levels) on SIMP runs at 64x32x32 and
@@ -56,6 +59,54 @@ def simp_samples(nelx, nely, nelz, volfrac, iters, ks=(0, 10, 50, 200), every=1,
     return out
 
 
+class StateSet:
+    """SIMP states (E, rho_phys, compliance) of one mesh, with its handle."""
+
+    def __init__(self, nelx, nely, nelz, volfracs, iters, cuda="cuda", every=1):
+        import torch
+        P = W.cantilever(nelx, nely, nelz)
+        m = P.mesh
+        self.dims = mfto.nn_grid(nelx, nely, nelz, LEVELS)
+        self.h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed,
+                             mfto.default_params(rtol=1e-8, maxit=20000))
+        self.h.set_solver(mfto.FORM_F32, inner_tol=1e-2)
+        self.f = torch.tensor(P.f, device=cuda)
+        self.states = []
+        for vf in volfracs:
+            self.h.set_params(mfto.default_params(volfrac=vf, rtol=1e-8, maxit=20000))
+            rho = torch.full((m.n_elem,), vf, dtype=torch.float64, device=cuda)
+            u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+            for it in range(iters):
+                rp = torch.zeros_like(rho)
+                st = self.h.simp_step(rho, u, self.f, rp)
+                if it % every == 0:
+                    E = torch.zeros_like(rho)
+                    self.h.simp_modulus(rp, E)
+                    self.states.append((E, rp, st.compliance))
+
+    @property
+    def voxels(self):
+        return int(np.prod(self.dims))
+
+
+def train_energy(net, sets, steps, lr=1e-3, lr_final=1e-4, seed=0, log_every=0):
+    """Adam on the energy loss (mfto_nn_train_energy) of states drawn in a
+    seeded order from the StateSets, learning rate decayed geometrically.
+    Returns [(step, loss)] every log_every steps."""
+    rng = np.random.default_rng(seed)
+    pool = [(s, i) for s in sets for i in range(len(s.states))]
+    hist = []
+    for k in range(steps):
+        ss, i = pool[int(rng.integers(len(pool)))]
+        E, rp, c = ss.states[i]
+        cur = lr * (lr_final / lr) ** (k / max(steps - 1, 1))
+        want = bool(log_every) and (k % log_every == 0 or k == steps - 1)
+        loss = ss.h.nn_train_energy(net, E, rp, ss.f, c, lr=cur, want_loss=want)
+        if want:
+            hist.append((k, loss))
+    return hist
+
+
 def train(net, samples, steps, lr=1e-3, lr_final=1e-4, seed=0, log_every=0):
     """Adam on single samples drawn in a seeded order, learning rate decayed
     geometrically from lr to lr_final.  Returns the loss history."""
@@ -71,15 +122,35 @@ def train(net, samples, steps, lr=1e-3, lr_final=1e-4, seed=0, log_every=0):
     return hist
 
 
-def save(net, path):
-    np.savez(path, params=net.get_params(), base=net.base, levels=net.levels)
+WEIGHTS = mfto.HERE / "weights" / "unet_b14_l4_cantilever.npz"
 
 
-def load(path, max_voxels, stream=None):
+def _to_bf16_bits(p):
+    """float32 -> bfloat16 bit patterns, round to nearest even (the rounding
+    the network applies to its working copy of the weights)."""
+    b = np.ascontiguousarray(p, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def save(net, path, bf16=True):
+    """Parameters, compressed; bf16=True keeps only the BF16 values the
+    forward pass uses (the FP32 master copy is dropped)."""
+    p = net.get_params()
+    if bf16:
+        np.savez_compressed(path, params_bf16=_to_bf16_bits(p), base=net.base, levels=net.levels)
+    else:
+        np.savez_compressed(path, params=p, base=net.base, levels=net.levels)
+
+
+def load(path=WEIGHTS, max_voxels=1, max_train_voxels=0, stream=None):
     d = np.load(path)
+    if "params_bf16" in d:
+        params = (d["params_bf16"].astype(np.uint32) << 16).view(np.float32)
+    else:
+        params = d["params"]
     net = mfto.Net(base=int(d["base"]), levels=int(d["levels"]), max_voxels=max_voxels,
-                   stream=stream)
-    net.set_params(d["params"])
+                   max_train_voxels=max_train_voxels, stream=stream)
+    net.set_params(params)
     return net
 
 
@@ -92,22 +163,34 @@ def main(argv=None):
     ap.add_argument("--small-iters", type=int, default=40)
     ap.add_argument("--large-iters", type=int, default=20)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--loss", choices=("energy", "mse"), default="energy")
     a = ap.parse_args(argv)
     import torch
     t0 = time.time()
-    samples = []
-    for vf in (0.12, 0.2):
-        samples += simp_samples(64, 32, 32, vf, a.small_iters, every=2)
-        samples += simp_samples(128, 64, 64, vf, a.large_iters, every=2)
+    if a.loss == "energy":
+        sets = [StateSet(64, 32, 32, (0.12, 0.2, 0.3), a.small_iters),
+                StateSet(128, 64, 64, (0.12, 0.2), a.large_iters)]
+        n_samples = sum(len(s.states) for s in sets)
+        big = max(s.voxels for s in sets)
+    else:
+        samples = []
+        for vf in (0.12, 0.2):
+            samples += simp_samples(64, 32, 32, vf, a.small_iters, every=2)
+            samples += simp_samples(128, 64, 64, vf, a.large_iters, every=2)
+        n_samples = len(samples)
+        big = max(int(np.prod(s[3])) for s in samples)
     torch.cuda.synchronize()
     t1 = time.time()
-    big = max(int(np.prod(s[3])) for s in samples)
     net = mfto.Net(base=a.base, levels=LEVELS, max_voxels=big, max_train_voxels=big, seed=a.seed)
-    hist = train(net, samples, a.steps, lr=a.lr, seed=a.seed, log_every=max(a.steps // 20, 1))
+    log = max(a.steps // 20, 1)
+    if a.loss == "energy":
+        hist = train_energy(net, sets, a.steps, lr=a.lr, seed=a.seed, log_every=log)
+    else:
+        hist = train(net, samples, a.steps, lr=a.lr, seed=a.seed, log_every=log)
     torch.cuda.synchronize()
     t2 = time.time()
     save(net, a.out)
-    print(f"samples {len(samples)} in {t1 - t0:.1f} s; {a.steps} steps in {t2 - t1:.1f} s; "
+    print(f"samples {n_samples} in {t1 - t0:.1f} s; {a.steps} steps in {t2 - t1:.1f} s; "
           f"params {net.num_params}")
     for s, l in hist:
         print(f"step {s:6d} loss {l:.4e}")

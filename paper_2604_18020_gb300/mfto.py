@@ -139,6 +139,8 @@ SIGNATURES = {
     "mfto_nn_to_dofs": (C.c_int32, [_P, C.c_int32, _P, _P]),
     "mfto_nn_sample": (C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, _P, _P, _P]),
     "mfto_set_learned": (C.c_int32, [_P, _P, C.c_int32]),
+    "mfto_nn_train_energy": (C.c_int32, [_P, _P, _P, _P, _P, C.c_double, C.c_float,
+                                         C.POINTER(C.c_double)]),
     "mfto_learned_solve": (C.c_int32, [_P, _P, _P, _P, _P, C.POINTER(LearnedStats)]),
     "mfto_kv_timing_read": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double)]),
@@ -453,6 +455,16 @@ class Handle:
             _ptr(f, torch.float64, self.n_dof, "f"), _ptr(u_star, torch.float64, self.n_dof, "u"),
             k_iters, _ptr(x, torch.float32, 4 * V, "x"), _ptr(y, torch.float32, 3 * V, "y"),
             _ptr(mask, torch.float32, 3 * V, "mask")), self._h)
+
+    def nn_train_energy(self, net, E, rho_phys, f, compliance, lr=1e-3, want_loss=True):
+        import torch
+        loss = C.c_double()
+        _check("mfto_nn_train_energy", lib().mfto_nn_train_energy(
+            self._h, net._n, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(rho_phys, torch.float64, self.n_elem, "rho_phys"),
+            _ptr(f, torch.float64, self.n_dof, "f"), compliance, lr,
+            C.byref(loss) if want_loss else None), self._h)
+        return loss.value if want_loss else None
 
     def set_learned(self, net, every=0):
         self._net = net   # keep the network alive while attached

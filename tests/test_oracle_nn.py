@@ -97,3 +97,42 @@ def test_dof_channels_and_inverse_map():
     assert np.allclose(back[9:], (a / np.abs(a).max())[9:], rtol=1e-6, atol=1e-7)
     mask = nn.target_mask(fixed, nelx, nely, nelz)
     assert mask.sum() == n_dof - 9
+
+
+def test_energy_loss_closed_forms_and_gradient():
+    from oracle import fem
+    rng = np.random.default_rng(3)
+    nelx, nely, nelz = 4, 2, 2
+    n_dof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
+    fixed_nodes = np.zeros((nelx + 1) * (nely + 1) * (nelz + 1), dtype=np.uint8)
+    fixed_nodes[::nelx + 1] = 7                      # x = 0 face clamped
+    fd = fem.dof_mask(fixed_nodes)
+    E = rng.uniform(0.2, 1.0, nelx * nely * nelz)
+    edof = fem.edof_table_fast(nelx, nely, nelz)
+    K = fem.assemble_masked(fem.ke_exact(), E, edof, n_dof, fd)
+    f = np.zeros(n_dof)
+    f[-2] = -1.0
+    u = np.linalg.solve(K, f)
+    S = f @ u
+    # the exact solution (any scale) has loss 0; a direction K-orthogonal to it, loss 1
+    assert abs(onn_loss(-3.0 * u, f, K, S)) <= 1e-12
+    w = rng.standard_normal(n_dof)
+    w[fd] = 0
+    w -= (w @ K @ u) / (u @ K @ u) * u
+    assert abs(onn_loss(w, f, K, S) - 1.0) <= 1e-12
+    # gradient against central differences
+    c = u + 0.3 * w
+    _, g = nn.energy_loss(c, f, K @ c, S)
+    for idx in rng.choice(np.flatnonzero(~fd), 5, replace=False):
+        e = np.zeros(n_dof)
+        e[idx] = 1e-6
+        fdiff = (onn_loss(c + e, f, K, S) - onn_loss(c - e, f, K, S)) / 2e-6
+        assert abs(fdiff - g[idx]) <= 1e-6 * max(1.0, abs(g[idx]))
+    # dofs_to_grid is the adjoint of to_dofs
+    y = rng.standard_normal((3,) + nn.grid_dims(nelx, nely, nelz))
+    assert abs((nn.to_dofs(y, fd, nelx, nely, nelz) * g).sum()
+               - (y * nn.dofs_to_grid(g, fd, nelx, nely, nelz)).sum()) <= 1e-10
+
+
+def onn_loss(c, f, K, S):
+    return nn.energy_loss(c, f, K @ c, S)[0]
