@@ -513,6 +513,60 @@ def compare_run(args):
         print(json.dumps(o))
 
 
+def learned_run(args):
+    """The learned form at the 256 x 128 x 150 cantilever (4,915,200 elements,
+    V_f 0.12): `warmup` SIMP iterations from the uniform start with the mixed
+    solve, then, from that same state, `steps` SIMP iterations with each
+    solver: plain FP64 Jacobi-PCG, the mixed solve, and the learned solve
+    with the committed trained network and with an untrained one (initial
+    guess only, every = 0).  One JSON line per solver: SIMP iteration time,
+    inner iterations, network time, and the largest relative compliance
+    difference to plain FP64."""
+    import numpy as np
+    import torch
+    from paper_2604_18020_gb300 import learned as L, mfto, workloads as W
+    dev = torch.device("cuda:0")
+    nx, ny, nz, vf = 256, 128, 150, 0.12
+    P = W.cantilever(nx, ny, nz)
+    m = P.mesh
+    V = int(np.prod(mfto.nn_grid(nx, ny, nz)))
+    nets = {"learned_trained": L.load(L.WEIGHTS, V),
+            "learned_untrained": mfto.Net(base=14, levels=4, max_voxels=V, seed=0)}
+    h = mfto.Handle(nx, ny, nz, P.fixed,
+                    params=mfto.default_params(volfrac=vf, rtol=1e-8, maxit=100000))
+    h.set_solver(mfto.FORM_F32, args.inner_tol, 100000, 50)
+    rho = torch.full((m.n_elem,), vf, dtype=torch.float64, device=dev)
+    u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+    f = torch.tensor(P.f, device=dev)
+    for _ in range(args.warmup):
+        h.simp_step(rho, u, f)
+    rho0, u0 = rho.clone(), u.clone()
+    ref_c = None
+    for name in ("f64", "mixed", "learned_trained", "learned_untrained"):
+        h.set_learned(nets.get(name), every=0)
+        h.set_solver(mfto.FORM_F64 if name == "f64" else mfto.FORM_F32, args.inner_tol, 100000, 50)
+        rho.copy_(rho0)
+        u.copy_(u0)
+        cs, ts, its = [], [], []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st = h.simp_step(rho, u, f)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+            cs.append(st.compliance)
+            its.append(st.cg_iterations)
+        ref_c = ref_c or cs
+        print(json.dumps({"case": "cantilever_256x128x150_vf0.12", "solver": name,
+                          "warmup_simp_iters": args.warmup, "simp_iter_ms": 1e3 * float(np.mean(ts)),
+                          "iterations": its, "compliance": cs,
+                          "compliance_rel_err_vs_f64": max(abs(a - b) / abs(b)
+                                                           for a, b in zip(cs, ref_c))}),
+              flush=True)
+    h.set_learned(None)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,7 +575,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-maxit", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "pcg", "compare"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "pcg", "compare", "learned"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--form", default="mixed", choices=["f64", "mixed"],
                     help="f64: plain FP64 Jacobi-PCG; mixed: FP64 iterative refinement "
@@ -540,6 +594,9 @@ def main():
 
     if args.mode == "compare":
         compare_run(args)
+        return
+    if args.mode == "learned":
+        learned_run(args)
         return
     if args.mode != "bench":
         profile_run(args)

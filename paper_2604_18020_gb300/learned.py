@@ -154,9 +154,76 @@ def load(path=WEIGHTS, max_voxels=1, max_train_voxels=0, stream=None):
     return net
 
 
+def evaluate(path=WEIGHTS, sizes=((64, 32, 32), (128, 64, 64)), simp_iters=25, cuda="cuda"):
+    """Compare, on the state after `simp_iters` SIMP iterations of each
+    cantilever size (V_f 0.12), the trained network with an untrained one and
+    with no network: the energy-norm error of the optimally scaled initial
+    guess, and the inner iterations and wall time of the solve from u = 0 to
+    rtol 1.5e-2 (one refinement step) and 1e-8.  Prints one line per case."""
+    import torch
+    rows = []
+    for nx, ny, nz in sizes:
+        P = W.cantilever(nx, ny, nz)
+        m = P.mesh
+        dims = mfto.nn_grid(nx, ny, nz, LEVELS)
+        V = int(np.prod(dims))
+        nets = {"trained": load(path, V), "untrained": mfto.Net(base=14, levels=LEVELS,
+                                                               max_voxels=V, seed=123)}
+        h = mfto.Handle(nx, ny, nz, P.fixed, mfto.default_params(volfrac=0.12, rtol=1e-8,
+                                                                  maxit=100000))
+        h.set_solver(mfto.FORM_F32, inner_tol=1e-2)
+        rho = torch.full((m.n_elem,), 0.12, dtype=torch.float64, device=cuda)
+        rp, E = torch.zeros_like(rho), torch.zeros_like(rho)
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+        f = torch.tensor(P.f, device=cuda)
+        for _ in range(simp_iters):
+            st = h.simp_step(rho, u, f, rp)
+        h.filter(rho, rp)
+        h.simp_modulus(rp, E)
+        # compliance of the current state from a tight solve
+        us = u.clone()
+        h.set_params(mfto.default_params(volfrac=0.12, rtol=1e-11, maxit=100000))
+        h.ir_solve(E, f, us, inner=mfto.FORM_F32, inner_tol=1e-2)
+        S = float(torch.dot(f, us))
+        x = torch.zeros(4 * V, dtype=torch.float32, device=cuda)
+        y = torch.zeros(3 * V, dtype=torch.float32, device=cuda)
+        c, Kc = torch.zeros_like(u), torch.zeros_like(u)
+        h.nn_features(rp, f, x, LEVELS)
+        for name, net in nets.items():
+            net.forward(x, y, dims)
+            h.nn_to_dofs(y, c, LEVELS)
+            h.kv(E, c, Kc)
+            a, b = float(torch.dot(f, c)), float(torch.dot(c, Kc))
+            err = float(np.sqrt(max(1.0 - a * a / (b * S), 0.0))) if b > 0 else 1.0
+            rows.append({"mesh": f"{nx}x{ny}x{nz}", "net": name, "guess_energy_error": err})
+        for tol in (1.5e-2, 1e-8):
+            h.set_params(mfto.default_params(volfrac=0.12, rtol=tol, maxit=100000))
+            for name in ("none", "untrained", "trained"):
+                uu = torch.zeros_like(u)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if name == "none":
+                    h.set_learned(None)
+                    s2 = h.ir_solve(E, f, uu, inner=mfto.FORM_F32, inner_tol=1e-2)
+                else:
+                    h.set_learned(nets[name], every=0)
+                    s2 = h.learned_solve(E, rp, f, uu)
+                torch.cuda.synchronize()
+                rows.append({"mesh": f"{nx}x{ny}x{nz}", "rtol": tol, "net": name,
+                             "outer": s2.outer_iterations, "inner": s2.inner_iterations,
+                             "status": mfto.STATUS_NAMES[s2.status],
+                             "ms": 1e3 * (time.perf_counter() - t0)})
+        h.set_learned(None)
+        h.close()
+    for r in rows:
+        print(r)
+    return rows
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--out")
+    ap.add_argument("--eval", metavar="WEIGHTS", help="evaluate a trained network and exit")
     ap.add_argument("--base", type=int, default=14)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=1e-3)
@@ -165,6 +232,11 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--loss", choices=("energy", "mse"), default="energy")
     a = ap.parse_args(argv)
+    if a.eval:
+        evaluate(a.eval)
+        return
+    if not a.out:
+        ap.error("--out is required for training")
     import torch
     t0 = time.time()
     if a.loss == "energy":
