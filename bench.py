@@ -299,16 +299,28 @@ def gpu_bench(args, rank, local_rank, world):
     sm_mhz = clk["sm_mhz"] or 1950.0
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
     if args.form == "mixed":
-        # FP32 CG K.v: reads z, p_old (FP32 DOF vectors), E (FP32), the node
-        # mask; writes p_new, q: 4 x 12 B per node + 4 B + 1 B per node
+        # the CG K.v launch: reads z, p_old, E, the node mask; writes p_new, q
         bytes_per_launch = m.n_node * (4 * 12 + 1) + 4 * m.n_elem
-        peak = measured_hbm_gbs()
-        roof = {"bound": "hbm", "achieved": bytes_per_launch / kv_avg_s / 1e9, "peak": peak,
-                "unit": "GB/s", "traffic": None,
-                "kernel": ("pcg_kv_tile_kernel<float>" if args.inner_form == "f32"
-                           else f"pcg_kv_tc_kernel ({args.inner_form})"),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy benchmark), of measured",
-                "bytes_per_launch": bytes_per_launch}
+        kname = ("pcg_kv_tile_kernel<float>" if args.inner_form == "f32"
+                 else f"pcg_kv_tc_kernel ({args.inner_form})")
+        hbm = measured_hbm_gbs()
+        fp32_peak_tflops = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+        t_bytes = bytes_per_launch / (hbm * 1e9)
+        t_flops = FLOP_PER_ELEM * m.n_elem / (fp32_peak_tflops * 1e12)
+        frac_hbm = t_bytes / kv_avg_s
+        frac_alu = t_flops / kv_avg_s
+        if t_bytes >= t_flops:
+            roof = {"bound": "hbm", "achieved": bytes_per_launch / kv_avg_s / 1e9, "peak": hbm,
+                    "unit": "GB/s",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy benchmark), of measured"}
+        else:
+            roof = {"bound": "alu", "achieved": FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12,
+                    "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "peak_source": f"FP32 FMA pipe, {n_sm} SMs x 128 FMA/clk x 2 flop x "
+                                   f"{sm_mhz:.0f} MHz median SM clock under load"}
+        roof.update({"traffic": None, "kernel": kname, "bytes_per_launch": bytes_per_launch,
+                     "flop_per_elem": FLOP_PER_ELEM, "frac_hbm": frac_hbm,
+                     "frac_fp32_pipe": frac_alu})
     else:
         fp64_peak_tflops = n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12   # 2 DFMA/clk/SM, measured clock
         roof = {"bound": "alu", "achieved": FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12,

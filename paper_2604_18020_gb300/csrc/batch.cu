@@ -280,7 +280,7 @@ batch_pcg_kv(const float* __restrict__ E, const float* __restrict__ Z, const flo
       batch_block<float, S>(E + in.elem_off, fixed + in.node_off, K, in, gb - in.kv_blk0,
                             TileLoadDirection<float>{Z + o, P0 + o, beta},
                             TilePcg<float>{P1 + o, Q + o}, reinterpret_cast<float*>(smem_raw), red);
-      pq = block_sum(red.finish(), sh);
+      pq = block_sum_w0(red.finish(), sh);
     }
     if (threadIdx.x == 0) part[gb] = pq;
   }
@@ -346,8 +346,8 @@ batch_update(float* __restrict__ U, const float* __restrict__ P, const float* __
       }
     });
     (void)inst_i;
-    const double a = block_sum(d0.finish(), sh);
-    const double b = block_sum(d1.finish(), sh);
+    const double a = block_sum_w0(d0.finish(), sh);
+    const double b = block_sum_w0(d1.finish(), sh);
     if (threadIdx.x == 0) {
       part[gb] = a;
       part[stride + gb] = b;
@@ -408,8 +408,8 @@ batch_init(float* R, float* __restrict__ Z, const float* __restrict__ dinv,
         d1.add_prod(ri, ri);
       }
     });
-    const double a = block_sum(d0.finish(), sh);
-    const double b = block_sum(d1.finish(), sh);
+    const double a = block_sum_w0(d0.finish(), sh);
+    const double b = block_sum_w0(d1.finish(), sh);
     if (threadIdx.x == 0) {
       part[gb] = a;
       part[stride + gb] = b;

@@ -190,6 +190,23 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
+// Sum over the warps of values that live in lane 0 of each warp (every other
+// lane's value is ignored): the per-warp results of DotAcc<float>::finish.
+// One FP64 add per warp instead of a shuffle tree over every lane (the FP64
+// pipe is narrow).  The result is valid in thread 0; fixed order.
+__device__ __forceinline__ double block_sum_w0(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) t += sh[w];
+  }
+  return t;
+}
+
 __device__ __forceinline__ double block_max(double v, double* sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -243,6 +260,7 @@ struct DotAcc;
 
 template <>
 struct DotAcc<double> {
+  static constexpr bool kWarpReduced = false;   // finish(): one partial per thread
   double s = 0.0;
   __device__ __forceinline__ void add_prod(double a, double b) { s += a * b; }
   // every thread returns its own FP64 partial
@@ -251,6 +269,7 @@ struct DotAcc<double> {
 
 template <>
 struct DotAcc<float> {
+  static constexpr bool kWarpReduced = true;    // finish(): one partial per warp (lane 0)
   DFloat s{0.f, 0.f};
   __device__ __forceinline__ void add_prod(float a, float b) { s = df_add(s, df_prod(a, b)); }
   // must be called by all 32 lanes of the warp: lane 0 returns the warp's
@@ -271,7 +290,9 @@ struct DotAcc<float> {
 // Publish K per-block partial sums and let the last block to arrive reduce
 // them in block-index order.  Returns true in every thread of that last
 // block, with out[0..K) holding the totals (valid in all its threads).
-template <int K>
+// W0: the values live in lane 0 of each warp only (DotAcc<float>::finish),
+// so the block stage sums the warps' values instead of every lane's.
+template <int K, bool W0 = false>
 __device__ __forceinline__ bool last_block_reduce(const double (&v)[K],
                                                   double* partials,
                                                   unsigned int* ticket,
@@ -283,7 +304,7 @@ __device__ __forceinline__ bool last_block_reduce(const double (&v)[K],
   const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   double bs[K];
 #pragma unroll
-  for (int c = 0; c < K; ++c) bs[c] = block_sum(v[c], sh);
+  for (int c = 0; c < K; ++c) bs[c] = W0 ? block_sum_w0(v[c], sh) : block_sum(v[c], sh);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int c = 0; c < K; ++c) partials[c * MFTO_RED_SLOTS + bid] = bs[c];

@@ -337,7 +337,7 @@ pcg_kv_tc_kernel(const float* __restrict__ E, const float* __restrict__ z,
                                    TileLoadDirection<float>{z, p_old, (float)s->beta},
                                    TilePcg<float>{p_new, q}, smem, err);
   double tot[1];
-  if (last_block_reduce<1>(red, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce<1, true>(red, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
     s->pq = tot[0];
     if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
       s->done = 1;

@@ -47,7 +47,8 @@ pcg_kv_tile_kernel(const T* __restrict__ E, const T* __restrict__ z, const T* __
   red[0] = tile_body<T>(E, fixed, K, g, nzc, TileLoadDirection<T>{z, p_old, beta},
                         TilePcg<T>{p_new, q}, reinterpret_cast<T*>(smem_raw));
   double tot[1];
-  if (last_block_reduce<1>(red, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce<1, DotAcc<T>::kWarpReduced>(red, partials, &s->ticket_b, tot, sh) &&
+      threadIdx.x == 0) {
     s->pq = tot[0];
     if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
       s->done = 1;

@@ -186,7 +186,7 @@ fpcg_update(float* __restrict__ u, const float* __restrict__ p, const float* __r
   }
   const double acc[3] = {d0.finish(), d1.finish(), d2.finish()};
   double tot[3];
-  if (last_block_reduce<3>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce<3, true>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
     s->it += 1;
     s->rr = tot[1];
     s->beta = (tot[0] - tot[2]) / s->rz;
@@ -223,7 +223,7 @@ fpcg_corr_dots(const float* __restrict__ c, const float* __restrict__ r,
   }
   const double acc[4] = {d0.finish(), d1.finish(), d2.finish(), d3.finish()};
   double tot[4];
-  if (last_block_reduce<4>(acc, partials, &ctl->ticket, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce<4, true>(acc, partials, &ctl->ticket, tot, sh) && threadIdx.x == 0) {
     ctl->cr = tot[0];
     ctl->cq = tot[1];
     ctl->cc = tot[2];

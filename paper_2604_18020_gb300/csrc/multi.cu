@@ -162,7 +162,8 @@ pcg_kv_multi(const float* __restrict__ E, const float* __restrict__ Z, const flo
 #pragma unroll
   for (int r = 0; r < MFTO_MAX_RHS; ++r) part[r] = red[r].finish();
   double tot[MFTO_MAX_RHS];
-  if (last_block_reduce<MFTO_MAX_RHS>(part, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce<MFTO_MAX_RHS, true>(part, partials, &s->ticket_b, tot, sh) &&
+      threadIdx.x == 0) {
     for (int r = 0; r < nrhs; ++r) {
       if (s->done[r]) continue;
       s->pq[r] = tot[r];
@@ -214,7 +215,7 @@ pcg_update_multi(float* __restrict__ U, const float* __restrict__ P, const float
 #pragma unroll
   for (int k = 0; k < 2 * MFTO_MAX_RHS; ++k) part[k] = d[k].finish();
   double tot[2 * MFTO_MAX_RHS];
-  if (last_block_reduce<2 * MFTO_MAX_RHS>(part, partials, &s->ticket_c, tot, sh) &&
+  if (last_block_reduce<2 * MFTO_MAX_RHS, true>(part, partials, &s->ticket_c, tot, sh) &&
       threadIdx.x == 0) {
     int all = 1;
     for (int r = 0; r < nrhs; ++r) {
@@ -290,7 +291,7 @@ pcg_init_multi(float* R, float* __restrict__ Z, const float* __restrict__ dinv, 
 #pragma unroll
   for (int k = 0; k < 2 * MFTO_MAX_RHS; ++k) part[k] = d[k].finish();
   double tot[2 * MFTO_MAX_RHS];
-  if (last_block_reduce<2 * MFTO_MAX_RHS>(part, partials, &s->ticket_a, tot, sh) &&
+  if (last_block_reduce<2 * MFTO_MAX_RHS, true>(part, partials, &s->ticket_a, tot, sh) &&
       threadIdx.x == 0) {
     int all = 1;
     for (int r = 0; r < MFTO_MAX_RHS; ++r) {

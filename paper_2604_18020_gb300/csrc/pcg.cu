@@ -53,7 +53,8 @@ pcg_init(const T* f, const T* __restrict__ Ku, const T* __restrict__ dinv, T* r,
   }
   const double acc[3] = {d0.finish(), d1.finish(), d2.finish()};
   double tot[3];
-  if (last_block_reduce<3>(acc, partials, &s->ticket_a, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce<3, DotAcc<T>::kWarpReduced>(acc, partials, &s->ticket_a, tot, sh) &&
+      threadIdx.x == 0) {
     s->rz = tot[0];
     s->rr = tot[1];
     s->ff = tot[2];
@@ -174,7 +175,7 @@ pcg_update_f32(float* __restrict__ u, const float* __restrict__ p, const float* 
   }
   const double acc[2] = {d0.finish(), d1.finish()};
   double tot[2];
-  if (last_block_reduce<2>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce<2, true>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
     s->it += 1;
     s->rr = tot[1];
     s->beta = tot[0] / s->rz;
