@@ -198,6 +198,7 @@ def gpu_bench(args, rank, local_rank, world):
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
     if args.form == "mixed":
         h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
+        h.set_cg_engine(args.cg_engine)
     rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     f = torch.tensor(P.f, device=dev)
@@ -227,14 +228,15 @@ def gpu_bench(args, rank, local_rank, world):
         launches = h.launch_count() - l0
         kv64 = h.kv_timing_read(mfto.FORM_F64)
         kv32 = h.kv_timing_read(mfto.FORM_F32)
+        cgt = h.cg_timing_read()
         h.kv_timing(False)
-        return total_ms, stats, launches, kv64, kv32
+        return total_ms, stats, launches, kv64, kv32, cgt
 
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clocks:
-        t_ms, stats, launches, _, _ = timed_pass(False)
+        t_ms, stats, launches, _, _, _ = timed_pass(False)
     torch.cuda.synchronize()
     if dist:
         tt = torch.tensor([t_ms], device=dev)
@@ -242,12 +244,17 @@ def gpu_bench(args, rank, local_rank, world):
         t_ms = tt.item()
     clk = clocks.summary()
     # replay with events around every K.v launch (same steps, same state)
-    _, stats_b, _, kv64, kv32 = timed_pass(True)
+    _, stats_b, _, kv64, kv32, cgt = timed_pass(True)
     cg = [s.cg_iterations for s in stats]
     assert cg == [s.cg_iterations for s in stats_b], "replay diverged"
-    kv_per_pass = kv64[0] + kv32[0]
-    dom = kv32 if args.form == "mixed" else kv64       # the K.v that dominates the step
-    kv_n, kv_ms = dom
+    # K.v applications: FP64 launches, FP32 launches of the graph engine, and
+    # the iterations of the persistent CG launches (one K.v each)
+    kv_per_pass = kv64[0] + kv32[0] + cgt[1]
+    persistent = args.form == "mixed" and cgt[0] > 0
+    if persistent:
+        kv_n, kv_ms = cgt[1], cgt[2]      # per CG iteration of the persistent kernel
+    else:
+        kv_n, kv_ms = kv32 if args.form == "mixed" else kv64   # the dominant K.v launches
 
     # e2e: public API from pinned host buffers, copies inside the timed region
     h_rho = rho0.cpu().pin_memory()
@@ -276,7 +283,7 @@ def gpu_bench(args, rank, local_rank, world):
     fp64 = None
     if args.form != "f64":
         h.set_solver(mfto.FORM_F64)
-        t64, stats64, _, _, _ = timed_pass(False)
+        t64, stats64, _, _, _, _ = timed_pass(False)
         c64 = [s.compliance for s in stats64]
         cf = [s.compliance for s in stats]
         fp64 = {"simp_iter_ms": t64 / args.steps,
@@ -303,6 +310,12 @@ def gpu_bench(args, rank, local_rank, world):
         bytes_per_launch = m.n_node * (4 * 12 + 1) + 4 * m.n_elem
         kname = ("pcg_kv_tile_kernel<float>" if args.inner_form == "f32"
                  else f"pcg_kv_tc_kernel ({args.inner_form})")
+        if persistent:
+            # one CG iteration of the persistent kernel: the K.v phase above plus
+            # the vector update (reads u, p, q, r, 1/d; writes u, r, z: 32 B/DOF);
+            # its time includes both grid barriers
+            bytes_per_launch += 32 * m.n_dof
+            kname = "pcg_persist_f32 (per CG iteration: K.v + vector update + 2 grid barriers)"
         hbm = measured_hbm_gbs()
         fp32_peak_tflops = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
         t_bytes = bytes_per_launch / (hbm * 1e9)
@@ -321,6 +334,10 @@ def gpu_bench(args, rank, local_rank, world):
         roof.update({"traffic": None, "kernel": kname, "bytes_per_launch": bytes_per_launch,
                      "flop_per_elem": FLOP_PER_ELEM, "frac_hbm": frac_hbm,
                      "frac_fp32_pipe": frac_alu})
+        if persistent:
+            roof.update({"unit_of_work": "one CG iteration (one K.v application)",
+                         "launches": cgt[0], "iterations_per_launch": cgt[1] / cgt[0],
+                         "launch_us": cgt[2] * 1e3 / cgt[0]})
     else:
         fp64_peak_tflops = n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12   # 2 DFMA/clk/SM, measured clock
         roof = {"bound": "alu", "achieved": FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12,
@@ -341,6 +358,7 @@ def gpu_bench(args, rank, local_rank, world):
                    "inner_tol": args.inner_tol if args.form == "mixed" else None,
                    "inner_form": args.inner_form if args.form == "mixed" else None,
                    "kv_kernel": "tiled mode-space",
+                   "cg_engine": ("persistent" if persistent else "graph") if args.form == "mixed" else "graph",
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "simp_iter_ms": t_ms / args.steps,
@@ -383,6 +401,7 @@ def profile_run(args):
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
     if args.form == "mixed":
         h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
+        h.set_cg_engine(args.cg_engine)
     f = torch.tensor(P.f, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     if args.mode == "profile":
@@ -593,6 +612,8 @@ def main():
                     help="f64: plain FP64 Jacobi-PCG; mixed: FP64 iterative refinement "
                          "around an FP32 inner PCG")
     ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--cg-engine", type=int, default=0, choices=[0, 1],
+                    help="FP32 inner CG: 1 persistent cooperative kernel, 0 per-iteration graph")
     ap.add_argument("--inner-form", default="f32",
                     choices=["f32", "tf32", "tf32x3", "bf16", "bf16x3", "f16", "f16x3"],
                     help="K.v form of the inner solve of --form mixed")

@@ -191,12 +191,29 @@ mfto_status mfto_kv(mfto_handle* h, mfto_form form, const void* d_E,
                     const void* d_v, void* d_y);
 
 /* Choose the K.v kernel used by mfto_kv, mfto_pcg and mfto_simp_step:
- * 0 (default) = node-owned tiles streaming along z, element operator in the
- * per-axis (sum, difference) mode basis, about 220 arithmetic operations per
- * element; 1 = one thread per node gathering its 8 elements with the dense
- * 24x24 KE from shared memory (576 multiply-adds per node, the operation
- * count of Alg. 1).  Both are atomic-free and bit-reproducible. */
+ * 0 (default) = element operator in the per-axis (sum, difference) mode
+ * basis, about 220 arithmetic operations per element; FP64 runs node-owned
+ * tiles streaming along z through a shared-memory ring, FP32 runs one
+ * z-column of elements per thread with the face transforms carried from
+ * layer to layer (about 170 operations per element); 1 = one thread per node
+ * gathering its 8 elements with the dense 24x24 KE from shared memory (576
+ * multiply-adds per node, the operation count of Alg. 1); 2 = as 0 for FP64,
+ * and for FP32 one element per thread over 8 x 8 x 4 element blocks that own
+ * their 7 x 7 x 3 interior nodes.  All are atomic-free and bit-reproducible. */
 mfto_status mfto_set_kv_variant(mfto_handle* h, int32_t variant);
+
+/* Choose how the FP32 inner Jacobi-PCG of the mixed solve (mfto_ir_solve and
+ * mfto_simp_step with an F32 inner form) runs its iterations (Sec. 3.6):
+ * 0 (default) = two kernels per iteration (K.v, vector update) replayed
+ * from a captured CUDA graph; 1 = one persistent cooperative kernel per
+ * inner solve: each iteration's K.v with the direction update, the vector
+ * update and both dot products run between two bounded grid barriers, every
+ * CTA reducing the per-CTA partials in the same order.  Both compute the same per-entry arithmetic;
+ * the dot products add the per-block partials in a different order.  The
+ * tensor-core inner forms and mfto_set_kv_variant(h, 1) always use 0.
+ * MFTO_UNSUPPORTED for 1 without cooperative launch.  A barrier wait that
+ * gives up (about a second) makes the solve return MFTO_CUDA_ERROR. */
+mfto_status mfto_set_cg_engine(mfto_handle* h, int32_t engine);
 
 /* Jacobi diagonal of the masked K (Sec. 3.6), one element pass:
  * d_diag[k] = sum_{e owning k} E_e KE[l, l], 1 on fixed DOFs. */
@@ -463,6 +480,14 @@ mfto_status mfto_learned_solve(mfto_handle* h, const double* d_E, const double* 
  * accumulators. */
 mfto_status mfto_kv_timing(mfto_handle* h, int32_t on);
 mfto_status mfto_kv_timing_read(mfto_handle* h, mfto_form form, int64_t* launches,
+                                double* total_ms);
+
+/* Persistent CG launches timed while mfto_kv_timing is on (they contain the
+ * FP32 K.v applications of the inner solves, which then have no launches of
+ * their own): number of launches, CG iterations they completed (K.v
+ * applications) and their summed device time in milliseconds; resets the
+ * accumulators. */
+mfto_status mfto_cg_timing_read(mfto_handle* h, int64_t* launches, int64_t* iterations,
                                 double* total_ms);
 
 /* Number of kernels the library has launched for this handle so far (the

@@ -41,6 +41,7 @@ struct PcgScalars {
   int32_t it, maxit, done, status;
   unsigned int ticket_a, ticket_b, ticket_c;
   int32_t tc_error;         // a tensor-core completion wait gave up
+  int32_t bar_error;        // a grid-barrier wait of the persistent CG gave up
 };
 
 // Scalars of the multi-RHS inner CG: one set per load case, plus the flag
@@ -68,6 +69,10 @@ struct KvEventPool {
   int used = 0;
   int64_t launches[2] = {0, 0};
   double total_ms[2] = {0.0, 0.0};
+  // persistent CG launches (pcg_persist.cu): launches, CG iterations, device time
+  int64_t cg_launches = 0, cg_iterations = 0;
+  double cg_ms = 0.0;
+  cudaEvent_t cg_start = nullptr, cg_stop = nullptr;
 };
 
 struct mfto_handle {
@@ -84,7 +89,12 @@ struct mfto_handle {
   ModeCoef<double> mc64;    // mode-space element operator (kv_tile.cuh)
   ModeCoef<float> mc32;
   int kv_variant;           // 0: tiled mode-space kernel, 1: node-centric dense KE
+  int cg_engine;            // FP32 inner CG: 0 graph of per-iteration kernels, 1 persistent
+  int persist_grid;         // CTAs of the persistent CG launch (0: unavailable)
+  int persist_tiling[4];    // its column tiling: tiles in x, y, z and node layers per chunk
   int occ_kv32, occ_pcg32;  // resident CTAs per SM of the FP32 block kernels
+  int occ_col[2];           // ... of the FP32 column kernels (K.v, CG K.v)
+  unsigned int* d_bar;      // tree grid-barrier counters of the persistent CG (zeroed)
   int occ_tc[12];           // ... of the tensor-core kernels, [2 * (2 kind + split) + pcg]
   int occ_multi[3];         // ... of the multi-RHS kernels (F64 K.V, F32 K.V, F32 CG step)
   unsigned char* d_btc;     // tensor-core B operands: [kind][hi | lo]
@@ -410,6 +420,8 @@ mfto_status pcg_start(mfto_handle* h, const PcgVecs<T>& v, const T* rhs, const T
 template <typename T>
 mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalars* host_s);
 void pcg_graph_release(mfto_handle* h);
+mfto_status pcg_persist_init(mfto_handle* h);
+mfto_status pcg_persist_iterate(mfto_handle* h, const PcgVecs<float>& v, PcgScalars* host_s);
 mfto_status kv_tile_init(mfto_handle* h);
 template <typename T>
 mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStream_t st);

@@ -133,7 +133,7 @@ static void free_handle(mfto_handle* h) {
                   h->d_E, h->d_dc, h->d_dc_phys, h->d_r32, h->d_z32, h->d_p0_32,
                   h->d_p1_32, h->d_q32, h->d_dinv32, h->d_e32, h->d_E32, h->d_pcg32,
                   h->d_btc, h->m_q64, h->m_r32, h->m_z32, h->m_p0, h->m_p1, h->m_q32,
-                  h->m_e32, h->m_pcg, h->m_out};
+                  h->m_e32, h->m_pcg, h->m_out, h->d_bar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -141,6 +141,8 @@ static void free_handle(mfto_handle* h) {
   if (h->h_misc) cudaFreeHost(h->h_misc);
   if (h->h_pcg32) cudaFreeHost(h->h_pcg32);
   if (h->h_mpcg) cudaFreeHost(h->h_mpcg);
+  if (h->ev.cg_start) cudaEventDestroy(h->ev.cg_start);
+  if (h->ev.cg_stop) cudaEventDestroy(h->ev.cg_stop);
   for (size_t i = 0; i < h->ev.start.size(); ++i) {
     cudaEventDestroy(h->ev.start[i]);
     cudaEventDestroy(h->ev.stop[i]);
@@ -303,6 +305,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
     return MFTO_CUDA_ERROR;
   }
   mfto_status s = kv_tile_init(h);
+  if (s == MFTO_OK) s = pcg_persist_init(h);
+  if (s == MFTO_OK) h->cg_engine = 0;
   if (s == MFTO_OK) s = tc_init(h);
   if (s == MFTO_OK) s = multi_init(h);
   if (s == MFTO_OK) s = upload_params(h);

@@ -111,7 +111,10 @@ mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const doub
     MFTO_CUDA(h, cudaMemsetAsync(h->d_e32, 0, sizeof(float) * h->n_dof, h->stream));
     s = pcg_start<float>(h, v, h->d_r32, nullptr, inner_tol, h->inner_maxit);
     if (s != MFTO_OK) return s;
-    s = pcg_iterate<float>(h, v, 1, h->h_pcg32);
+    if (h->cg_engine == 1 && inner == MFTO_FORM_F32 && h->kv_variant == 0)
+      s = pcg_persist_iterate(h, v, h->h_pcg32);
+    else
+      s = pcg_iterate<float>(h, v, 1, h->h_pcg32);
     if (s != MFTO_OK) return s;
     out->inner_iterations += h->h_pcg32->it;
     if (h->h_pcg32->status == MFTO_BREAKDOWN) { out->status = MFTO_BREAKDOWN; break; }

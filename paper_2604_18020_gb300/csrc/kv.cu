@@ -85,7 +85,7 @@ mfto_status kv_launch(mfto_handle* h, mfto_form form, const void* E, const void*
     kv_timing_end(h);
     return s;
   }
-  if (h->kv_variant == 0) {
+  if (h->kv_variant != 1) {
     mfto_status s = form == MFTO_FORM_F64
         ? kv_tile_launch<double>(h, (const double*)E, (const double*)v, (double*)y, h->stream)
         : kv_tile_launch<float>(h, (const float*)E, (const float*)v, (float*)y, h->stream);
@@ -148,7 +148,7 @@ extern "C" mfto_status mfto_kv(mfto_handle* h, mfto_form form, const void* E, co
 
 extern "C" mfto_status mfto_set_kv_variant(mfto_handle* h, int32_t variant) {
   if (!h) return MFTO_INVALID_ARG;
-  MFTO_REQUIRE(h, variant == 0 || variant == 1, "mfto_set_kv_variant: variant must be 0 or 1");
+  MFTO_REQUIRE(h, variant >= 0 && variant <= 2, "mfto_set_kv_variant: variant must be 0, 1 or 2");
   if (h->kv_variant != variant) pcg_graph_release(h);
   h->kv_variant = variant;
   return MFTO_OK;

@@ -1,0 +1,350 @@
+// Column-streaming FP32 K.v (Eq. matfree): the element operator of
+// modes.cuh applied along z-columns of elements, one column per thread, with
+// the per-face halves of the mode transform carried from one element layer
+// to the next.
+//
+// A CTA of 256 threads covers CX x CY = 32 x 8 element columns and walks
+// their element layers bottom to top over a chunk of node layers.  It owns
+// the interior (CX-1) x (CY-1) nodes of every node layer of the chunk; the
+// one-column halo on the low x/y side and one element layer below the chunk
+// are recomputed by the neighbouring CTA (no atomics, no second pass).
+//
+// Per element layer ez a thread
+//   1. stages its own node of layer ez+1 (threads 0..40 also the tile's
+//      last node row / column) into a double-buffered shared layer, with the
+//      fixed DOFs zeroed; the global loads of layer ez+2 are issued at once
+//      and land in registers while the layer is computed;
+//   2. reads the 4 upper corners of its element and forms their face modes
+//      (x and y stages of the butterfly); the face modes of the lower corners
+//      are those of the previous layer, kept in registers, so each node
+//      layer's face transform is computed once per column, not twice;
+//   3. completes the z stage, applies the unit mode operator, and undoes the z
+//      stage with the modulus folded in: lower = E (s - d), upper = E (s + d);
+//   4. adds its lower-face output to the upper-face output of the element
+//      below (still in mode space), undoes the y and x stages once per node
+//      layer, and publishes the 4 corner sums of the column (12 values);
+//   5. if it owns node (ex, ey) of layer ez, sums the 4 columns around the
+//      node in a fixed order and hands the result to the epilogue.
+// The element operator costs 48 (forward) + 48 (mode operator) + 36 (inverse
+// z with E) + 12 (face sum) + 24 (inverse y, x) = 168 FP32 operations per
+// element, against 1152 for the dense 24 x 24 product; every output is
+// written once, by one thread, in a fixed order, so results are
+// bit-reproducible.
+#pragma once
+#include "common.cuh"
+
+struct ColShape {
+  static constexpr int CX = 32, CY = 8;            // element columns of a CTA
+  static constexpr int NX = CX + 1, NY = CY + 1;   // node tile of one layer
+  static constexpr int NV = NX * NY;               // 297 staged nodes
+  static constexpr int OX = CX - 1, OY = CY - 1;   // owned nodes per layer: 31 x 7
+  static constexpr int NEXTRA = NV - CX * CY;      // 41 nodes staged by a second thread
+  static constexpr size_t smem_bytes = sizeof(float) * (2 * 3 * NV + 12 * CX * CY);
+};
+static_assert(ColShape::CX * ColShape::CY == MFTO_BLOCK, "one column per thread");
+static_assert(ColShape::NEXTRA <= MFTO_BLOCK, "extra nodes fit one pass");
+
+// Tiling of the node grid by column tiles: tile (tx, ty, tz) owns nodes
+// [tx OX, +OX) x [ty OY, +OY) x [tz nzc, +nzc) (clipped to the grid).
+struct ColTiling {
+  int tx, ty, tz, nzc;
+  __host__ __device__ int count() const { return tx * ty * tz; }
+};
+
+static inline ColTiling col_tiling(const Grid& g, int nzc) {
+  ColTiling t;
+  t.tx = (g.nx + ColShape::OX - 1) / ColShape::OX;
+  t.ty = (g.ny + ColShape::OY - 1) / ColShape::OY;
+  if (nzc < 1) nzc = 1;
+  if (nzc > g.nz) nzc = g.nz;
+  t.nzc = nzc;
+  t.tz = (g.nz + nzc - 1) / nzc;
+  return t;
+}
+
+// Chunk length along z for a grid of at most `ctas` resident CTAs: split
+// the columns just enough to give every CTA a tile, but keep chunks of at
+// least `min_nzc` node layers (a chunk of n layers recomputes n + 1 element
+// layers).
+static inline int col_chunk(const Grid& g, int64_t ctas, int min_nzc) {
+  const int64_t txy = (int64_t)((g.nx + ColShape::OX - 1) / ColShape::OX) *
+                      ((g.ny + ColShape::OY - 1) / ColShape::OY);
+  int64_t zch = ctas / txy;
+  if (zch < 1) zch = 1;
+  int nzc = (int)((g.nz + zch - 1) / zch);
+  if (nzc < min_nzc) nzc = min_nzc;
+  if (nzc > g.nz) nzc = g.nz;
+  return nzc;
+}
+
+// Loaders of one node's 3 components (already masked by the caller).
+struct ColLoadPlain {                 // v, through L1
+  const float* v;
+  __device__ __forceinline__ float operator()(int idx) const { return v[idx]; }
+};
+
+struct ColLoadDirectionL2 {           // z + beta p, from L2 (written inside a persistent launch)
+  const float* z;
+  const float* p;
+  float beta;
+  __device__ __forceinline__ float operator()(int idx) const {
+    return __ldcg(z + idx) + beta * __ldcg(p + idx);
+  }
+};
+
+struct ColLoadDirection {             // z + beta p, through L1 (separate launches)
+  const float* z;
+  const float* p;
+  float beta;
+  __device__ __forceinline__ float operator()(int idx) const { return z[idx] + beta * p[idx]; }
+};
+
+// Epilogues: what the owner of a node does with its 3 sums.  red accumulates
+// the node's p.q (double-float; the three products are summed in FP32 first).
+struct ColStore {                     // plain K.v: y = sum, y_fixed = v
+  const float* v;
+  float* y;
+  __device__ __forceinline__ void operator()(int node, const float (&acc)[3], const float (&pn)[3],
+                                             uint8_t fm, DFloat& red) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[3 * node + c] = ((fm >> c) & 1) ? v[3 * node + c] : acc[c];
+  }
+};
+
+struct ColPcg {                       // CG: p_new stored, q = K p_new, p_new.q accumulated
+  float* p_new;
+  float* q;
+  __device__ __forceinline__ void operator()(int node, const float (&acc)[3], const float (&pn)[3],
+                                             uint8_t fm, DFloat& red) const {
+    float qc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      qc[c] = ((fm >> c) & 1) ? pn[c] : acc[c];
+      p_new[3 * node + c] = pn[c];
+      q[3 * node + c] = qc[c];
+    }
+    const float t = fmaf(pn[0], qc[0], fmaf(pn[1], qc[1], pn[2] * qc[2]));
+    red = df_add(red, DFloat{t, 0.f});
+  }
+};
+
+// One node's masked values and mask, fetched for a later stage.
+struct ColNode {
+  float v[3];
+  uint8_t fm;
+};
+
+template <typename Load>
+__device__ __forceinline__ ColNode col_fetch(const Load& ld, const uint8_t* __restrict__ fixed,
+                                             const Grid& g, int gi, int gj, int gk) {
+  ColNode n{{0.f, 0.f, 0.f}, 0};
+  if (gi >= 0 && gj >= 0 && gk >= 0 && gi < g.nx && gj < g.ny && gk < g.nz) {
+    const int node = gi + g.nx * (gj + g.ny * gk);
+    const uint8_t fm = fixed[node];
+    const float a = ld(3 * node + 0), b = ld(3 * node + 1), c = ld(3 * node + 2);
+    n.v[0] = (fm & 1) ? 0.f : a;
+    n.v[1] = (fm & 2) ? 0.f : b;
+    n.v[2] = (fm & 4) ? 0.f : c;
+    n.fm = fm;
+  }
+  return n;
+}
+
+__device__ __forceinline__ float col_modulus(const float* __restrict__ E, const Grid& g, int ei,
+                                             int ej, int ek) {
+  return (ei >= 0 && ej >= 0 && ek >= 0 && ei < g.nelx && ej < g.nely && ek < g.nelz)
+             ? E[ei + g.nelx * (ej + g.nely * ek)]
+             : 0.f;
+}
+
+// face modes (x then y stage) of the 4 corners (a + 2b) of one face, per component
+__device__ __forceinline__ void face_forward(const float* __restrict__ layer, int base,
+                                             float (&F)[3][4]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* L = layer + c * ColShape::NV + base;
+    const float c0 = L[0], c1 = L[1], c2 = L[ColShape::NX], c3 = L[ColShape::NX + 1];
+    const float m0 = c0 + c1, m1 = c1 - c0, m2 = c2 + c3, m3 = c3 - c2;
+    F[c][0] = m0 + m2;
+    F[c][2] = m2 - m0;
+    F[c][1] = m1 + m3;
+    F[c][3] = m3 - m1;
+  }
+}
+
+// Applies the element to face modes Flo (node layer ez) and Fup (layer ez+1):
+// lo, up receive E * (the inverse z stage of the mode operator's output).
+__device__ __forceinline__ void col_element(const float (&Flo)[3][4], const float (&Fup)[3][4],
+                                            float E, const ModeCoef<float>& K,
+                                            float (&lo)[3][4], float (&up)[3][4]) {
+  float x[3][8], y[3][8];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      x[c][f] = Flo[c][f] + Fup[c][f];       // z sum
+      x[c][f | 4] = Fup[c][f] - Flo[c][f];   // z difference
+    }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) y[c][m] = K.diag[c][m] * x[c][m];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (i == j) continue;
+      const int t = 3 - i - j;
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int tb = mt << t;
+        y[i][(1 << i) | tb] = fmaf(K.lamM[mt], x[j][(1 << j) | tb], y[i][(1 << i) | tb]);
+        y[i][(1 << j) | tb] = fmaf(K.muM[mt], x[j][(1 << i) | tb], y[i][(1 << j) | tb]);
+      }
+    }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float ed = E * y[c][f | 4];
+      lo[c][f] = fmaf(E, y[c][f], -ed);
+      up[c][f] = fmaf(E, y[c][f], ed);
+    }
+}
+
+// The 4 corner values (a + 2b) of summed face modes: inverse y, then x stage.
+__device__ __forceinline__ void face_inverse(const float (&M)[3][4], float (&S)[3][4]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float a0 = M[c][0] - M[c][2], a2 = M[c][0] + M[c][2];
+    const float a1 = M[c][1] - M[c][3], a3 = M[c][1] + M[c][3];
+    S[c][0] = a0 - a1;
+    S[c][1] = a0 + a1;
+    S[c][2] = a2 - a3;
+    S[c][3] = a2 + a3;
+  }
+}
+
+// Tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of `tl`.  Returns this
+// thread's double-float share of the epilogue reduction (sum over the block
+// with DotAcc-style finishing by the caller).
+template <typename Load, typename Epi>
+__device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
+                                                 const uint8_t* __restrict__ fixed,
+                                                 const ModeCoef<float>& K, const Grid& g,
+                                                 const ColTiling& tl, const Load& ld,
+                                                 const Epi& epi, float* smem) {
+  using S = ColShape;
+  float* nodes = smem;                          // [2][3][NV], slot of node layer k: k & 1
+  float* sums = smem + 2 * 3 * S::NV;           // [12][256] corner sums of each column
+  const int tid = threadIdx.x;
+  const int ex = tid % S::CX, ey = tid / S::CX;
+  // second staged node of threads < NEXTRA: the top row (y = CY), then the
+  // right column (x = CX)
+  const bool has_extra = tid < S::NEXTRA;
+  const int xx = tid < S::CX ? tid : S::CX;
+  const int xy = tid < S::CX ? S::CY : tid - S::CX;
+  const bool owner = ex >= 1 && ey >= 1;
+  DFloat red{0.f, 0.f};
+  const int ntiles = tl.count();
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int bx = t % tl.tx, by = (t / tl.tx) % tl.ty, bz = t / (tl.tx * tl.ty);
+    const int x0 = bx * S::OX - 1, y0 = by * S::OY - 1;   // node / element origin of column 0
+    const int kb = bz * tl.nzc;
+    const int ke = min(kb + tl.nzc, g.nz);                // owned node layers [kb, ke)
+    const int gi = x0 + ex, gj = y0 + ey;                  // this column's element (and node)
+    const int hi = x0 + xx, hj = y0 + xy;                  // the extra node
+    auto stage = [&](int k, const ColNode& own, const ColNode& extra) {
+      float* L = nodes + (k & 1) * 3 * S::NV;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) L[c * S::NV + ey * S::NX + ex] = own.v[c];
+      if (has_extra) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) L[c * S::NV + xy * S::NX + xx] = extra.v[c];
+      }
+    };
+    // prologue: node layer kb - 1 (face modes of the first element's lower face)
+    ColNode own = col_fetch(ld, fixed, g, gi, gj, kb - 1);
+    ColNode extra{{0.f, 0.f, 0.f}, 0};
+    if (has_extra) extra = col_fetch(ld, fixed, g, hi, hj, kb - 1);
+    stage(kb - 1, own, extra);
+    own = col_fetch(ld, fixed, g, gi, gj, kb);
+    if (has_extra) extra = col_fetch(ld, fixed, g, hi, hj, kb);
+    float Ecur = col_modulus(E, g, gi, gj, kb - 1);
+    __syncthreads();
+    float Flo[3][4], upp[3][4];
+    face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, ey * S::NX + ex, Flo);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) upp[c][f] = 0.f;
+    ColNode mine = own;          // this thread's node of layer ez + 1 (pn and mask of the owner)
+    for (int ez = kb - 1; ez < ke; ++ez) {
+      // 1. stage node layer ez + 1; fetch layer ez + 2 and the next modulus
+      stage(ez + 1, own, extra);
+      const ColNode mine_cur = mine;   // node layer ez of this column (owned node values)
+      mine = own;
+      const float Ee = Ecur;
+      if (ez + 1 < ke) {
+        own = col_fetch(ld, fixed, g, gi, gj, ez + 2);
+        if (has_extra) extra = col_fetch(ld, fixed, g, hi, hj, ez + 2);
+        Ecur = col_modulus(E, g, gi, gj, ez + 1);
+      }
+      __syncthreads();
+      // 2, 3. upper face modes, element operator
+      float Fup[3][4], lo[3][4], up[3][4];
+      face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, ey * S::NX + ex, Fup);
+      col_element(Flo, Fup, Ee, K, lo, up);
+      if (ez >= kb) {
+        // 4. node layer ez: upper face of element ez - 1 plus lower face of ez
+        float Ms[3][4], Sc[3][4];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) Ms[c][f] = upp[c][f] + lo[c][f];
+        face_inverse(Ms, Sc);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int a = 0; a < 4; ++a) sums[(4 * c + a) * MFTO_BLOCK + tid] = Sc[c][a];
+        __syncthreads();
+        // 5. owned node (x0 + ex, y0 + ey, ez): columns (ex-1, ey-1), (ex, ey-1),
+        //    (ex-1, ey), (ex, ey) contribute their corners 3, 2, 1, 0
+        if (owner && gi < g.nx && gj < g.ny) {
+          float acc[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float s = sums[(4 * c + 3) * MFTO_BLOCK + tid - S::CX - 1];
+            s += sums[(4 * c + 2) * MFTO_BLOCK + tid - S::CX];
+            s += sums[(4 * c + 1) * MFTO_BLOCK + tid - 1];
+            s += sums[(4 * c + 0) * MFTO_BLOCK + tid];
+            acc[c] = s;
+          }
+          epi(gi + g.nx * (gj + g.ny * ez), acc, mine_cur.v, mine_cur.fm, red);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          upp[c][f] = up[c][f];
+          Flo[c][f] = Fup[c][f];
+        }
+    }
+    __syncthreads();   // the shared layers are restaged by the next tile
+  }
+  return red;
+}
+
+// Warp sum of double-float shares; lane 0 returns the warp's total in FP64,
+// the other lanes 0 (the convention of DotAcc<float>::finish).
+__device__ __forceinline__ double col_warp_finish(DFloat v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DFloat w;
+    w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return (threadIdx.x & 31) == 0 ? (double)v.hi + (double)v.lo : 0.0;
+}

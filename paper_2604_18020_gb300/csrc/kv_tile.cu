@@ -1,6 +1,7 @@
 // Launchers of the tiled mode-space K.v (kv_tile.cuh): plain y = K v and the
 // CG form that also forms p_new = z + beta p_old, q = K p_new and alpha.
 #include "common.cuh"
+#include "kv_column.cuh"
 #include "kv_tile.cuh"
 
 namespace {
@@ -60,6 +61,52 @@ pcg_kv_tile_kernel(const T* __restrict__ E, const T* __restrict__ z, const T* __
   }
 }
 
+// FP32, variant 0: column-streaming body (kv_column.cuh)
+__global__ void __launch_bounds__(MFTO_BLOCK, 2)
+kv_col_kernel(const float* __restrict__ E, const float* __restrict__ v, float* __restrict__ y,
+              const uint8_t* __restrict__ fixed, ModeCoef<float> K, Grid g, ColTiling tl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  kv_column_body(E, fixed, K, g, tl, ColLoadPlain{v}, ColStore{v, y},
+                 reinterpret_cast<float*>(smem_raw));
+}
+
+__global__ void __launch_bounds__(MFTO_BLOCK, 2)
+pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
+                  const float* __restrict__ p_old, float* __restrict__ p_new,
+                  float* __restrict__ q, const uint8_t* __restrict__ fixed, ModeCoef<float> K,
+                  Grid g, ColTiling tl, PcgScalars* s, double* partials) {
+  if (*(volatile int32_t*)&s->done) return;  // uniform over the grid
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sh[64];
+  const float beta = (float)s->beta;
+  const DFloat red = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{z, p_old, beta},
+                                    ColPcg{p_new, q}, reinterpret_cast<float*>(smem_raw));
+  const double w[1] = {col_warp_finish(red)};
+  double tot[1];
+  if (last_block_reduce<1, true>(w, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
+    s->pq = tot[0];
+    if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+      s->done = 1;
+      s->status = MFTO_BREAKDOWN;
+      s->alpha = 0.0;
+    } else {
+      s->alpha = s->rz / tot[0];
+    }
+  }
+}
+
+// column tiling for a standalone launch: chunks sized for the resident CTAs
+ColTiling col_launch_tiling(const mfto_handle* h, int per_sm, int* grid) {
+  const Grid g = make_grid(h->mesh);
+  const int64_t ctas = (int64_t)per_sm * h->num_sms;
+  const ColTiling tl = col_tiling(g, col_chunk(g, ctas, 4));
+  int64_t n = tl.count();
+  if (n > ctas) n = ctas;
+  if (n > MFTO_RED_SLOTS) n = MFTO_RED_SLOTS;
+  *grid = (int)n;
+  return tl;
+}
+
 template <typename T>
 dim3 tile_grid(const mfto_handle* h, int* nzc_out, int per_sm = 1) {
   const Grid g = make_grid(h->mesh);
@@ -105,6 +152,16 @@ mfto_status kv_tile_init(mfto_handle* h) {
   mfto_status s = set_attrs<double>(h);
   if (s == MFTO_OK) s = set_attrs<float>(h);
   if (s != MFTO_OK) return s;
+  const int csm = (int)ColShape::smem_bytes;
+  MFTO_CUDA(h, cudaFuncSetAttribute(kv_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[0], kv_col_kernel,
+                                                             MFTO_BLOCK, csm));
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[1], pcg_kv_col_kernel,
+                                                             MFTO_BLOCK, csm));
+  if (h->occ_col[0] < 1) h->occ_col[0] = 1;
+  if (h->occ_col[1] < 1) h->occ_col[1] = 1;
   MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                    &h->occ_kv32, kv_tile_kernel<float>, MFTO_BLOCK, tile_smem<float>()));
   MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -123,6 +180,14 @@ const ModeCoef<float>& coef<float>(const mfto_handle* h) { return h->mc32; }
 
 template <typename T>
 mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStream_t st) {
+  if (sizeof(T) == 4 && h->kv_variant == 0) {
+    int grid = 0;
+    const ColTiling tl = col_launch_tiling(h, h->occ_col[0], &grid);
+    kv_col_kernel<<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+        (const float*)E, (const float*)v, (float*)y, h->d_fixed, h->mc32, make_grid(h->mesh), tl);
+    MFTO_LAUNCH_CHECK(h);
+    return MFTO_OK;
+  }
   int nzc = 0;
   const dim3 grid = tile_grid<T>(h, &nzc, h->occ_kv32);
   if (grid.x == 0) return mfto_fail(h, MFTO_TOO_LARGE, "mesh too large for the K.v tiling");
@@ -135,6 +200,15 @@ mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStr
 template <typename T>
 mfto_status pcg_kv_tile_launch(mfto_handle* h, const T* E, const T* z, const T* p_old, T* p_new,
                                T* q, PcgScalars* s, double* partials, cudaStream_t st) {
+  if (sizeof(T) == 4 && h->kv_variant == 0) {
+    int grid = 0;
+    const ColTiling tl = col_launch_tiling(h, h->occ_col[1], &grid);
+    pcg_kv_col_kernel<<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+        (const float*)E, (const float*)z, (const float*)p_old, (float*)p_new, (float*)q,
+        h->d_fixed, h->mc32, make_grid(h->mesh), tl, s, partials);
+    MFTO_LAUNCH_CHECK(h);
+    return MFTO_OK;
+  }
   int nzc = 0;
   const dim3 grid = tile_grid<T>(h, &nzc, h->occ_pcg32);
   if (grid.x == 0) return mfto_fail(h, MFTO_TOO_LARGE, "mesh too large for the K.v tiling");

@@ -233,7 +233,7 @@ mfto_status enqueue_chunk(mfto_handle* h, cudaStream_t st, const PcgVecs<T>& v, 
                                        (const float*)p_old, (float*)p_new, (float*)v.q, v.s,
                                        v.part_a, st);
       if (s != MFTO_OK) return s;
-    } else if (h->kv_variant == 0) {
+    } else if (h->kv_variant != 1) {
       mfto_status s = pcg_kv_tile_launch<T>(h, v.E, v.z, p_old, p_new, v.q, v.s, v.part_a, st);
       if (s != MFTO_OK) return s;
     } else {

@@ -93,6 +93,9 @@ SIGNATURES = {
     "mfto_kv": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     "mfto_jacobi_diag": (C.c_int32, [_P, C.c_int32, _P, _P]),
     "mfto_set_kv_variant": (C.c_int32, [_P, C.c_int32]),
+    "mfto_set_cg_engine": (C.c_int32, [_P, C.c_int32]),
+    "mfto_cg_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_double)]),
     "mfto_pcg": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
     "mfto_ir_solve": (C.c_int32, [_P, C.c_int32, C.c_double, _P, _P, _P, C.POINTER(IrStats)]),
     "mfto_set_solver": (C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, C.c_int32]),
@@ -325,6 +328,11 @@ class Handle:
     def set_kv_variant(self, variant: int):
         _check("mfto_set_kv_variant", lib().mfto_set_kv_variant(self._h, variant), self._h)
 
+    def set_cg_engine(self, engine: int):
+        """FP32 inner CG: 1 = one persistent cooperative kernel per solve,
+        0 = per-iteration kernels replayed from a CUDA graph."""
+        _check("mfto_set_cg_engine", lib().mfto_set_cg_engine(self._h, engine), self._h)
+
     def jacobi_diag(self, E, d, form=FORM_F64):
         dt = self._dt(form)
         _check("mfto_jacobi_diag", lib().mfto_jacobi_diag(
@@ -416,6 +424,12 @@ class Handle:
                lib().mfto_kv_timing_read(self._h, form, C.byref(n), C.byref(ms)), self._h)
         return n.value, ms.value
 
+    def cg_timing_read(self):
+        """(launches, CG iterations, device ms) of the timed persistent CG launches."""
+        n, it, ms = C.c_int64(), C.c_int64(), C.c_double()
+        _check("mfto_cg_timing_read",
+               lib().mfto_cg_timing_read(self._h, C.byref(n), C.byref(it), C.byref(ms)), self._h)
+        return n.value, it.value, ms.value
 
     # ---- learned part
     def nn_grid(self, levels=4):

@@ -54,7 +54,7 @@ def test_kv_f64(cuda, shape, face, variant):
     assert np.array_equal(got[fd], v[fd])
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("shape", MESHES + MESHES_BIG)
 def test_kv_f32(cuda, shape, variant):
     import torch
