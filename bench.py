@@ -48,6 +48,7 @@ FLOP_PER_ELEM = 1152.0                       # 2 * 24 * 24, dense element contra
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+IR_MODES = {"restart": 0, "continue": 1}
 REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
 
@@ -196,9 +197,13 @@ def gpu_bench(args, rank, local_rank, world):
     m = P.mesh
     params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params)
+    tuned = None
     if args.form == "mixed":
         h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
         h.set_cg_engine(args.cg_engine)
+        h.set_ir_mode(IR_MODES[args.ir_mode])
+        if not args.no_autotune:
+            tuned = h.kv_autotune()
     rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     f = torch.tensor(P.f, device=dev)
@@ -359,6 +364,9 @@ def gpu_bench(args, rank, local_rank, world):
                    "inner_form": args.inner_form if args.form == "mixed" else None,
                    "kv_kernel": "tiled mode-space",
                    "cg_engine": ("persistent" if persistent else "graph") if args.form == "mixed" else "graph",
+                   "kv_f32_zchunk": tuned[0] if tuned else None,
+                   "kv_f32_ctas_per_sm": tuned[1] if tuned else None,
+                   "ir_mode": args.ir_mode if args.form == "mixed" else None,
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "simp_iter_ms": t_ms / args.steps,
@@ -402,6 +410,7 @@ def profile_run(args):
     if args.form == "mixed":
         h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
         h.set_cg_engine(args.cg_engine)
+        h.set_ir_mode(IR_MODES[args.ir_mode])
     f = torch.tensor(P.f, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     if args.mode == "profile":
@@ -611,7 +620,11 @@ def main():
     ap.add_argument("--form", default="mixed", choices=["f64", "mixed"],
                     help="f64: plain FP64 Jacobi-PCG; mixed: FP64 iterative refinement "
                          "around an FP32 inner PCG")
-    ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--inner-tol", type=float, default=1e-1)
+    ap.add_argument("--ir-mode", default="continue", choices=sorted(IR_MODES),
+                    help="inner CG at each outer step: restart (p = z) or continue the direction")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default z-chunk of the FP32 column K.v")
     ap.add_argument("--cg-engine", type=int, default=0, choices=[0, 1],
                     help="FP32 inner CG: 1 persistent cooperative kernel, 0 per-iteration graph")
     ap.add_argument("--inner-form", default="f32",

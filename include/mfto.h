@@ -215,6 +215,16 @@ mfto_status mfto_set_kv_variant(mfto_handle* h, int32_t variant);
  * gives up (about a second) makes the solve return MFTO_CUDA_ERROR. */
 mfto_status mfto_set_cg_engine(mfto_handle* h, int32_t engine);
 
+/* Autotune the FP32 K.v (variant 0): times the column kernel for several
+ * lengths of its z-chunks (node layers per CTA tile; longer chunks recompute
+ * fewer element layers, shorter ones give more CTAs) and two register
+ * budgets (2 or 3 resident CTAs per SM) on the handle's own work vectors, and
+ * keeps the fastest pair for mfto_kv and the FP32 inner CG.  Returns the
+ * chosen chunk length, CTAs per SM and time per launch in microseconds (any
+ * may be NULL).  Overwrites the handle's FP32 work vectors; synchronises the
+ * stream. */
+mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc, int32_t* ctas_per_sm, float* us);
+
 /* Jacobi diagonal of the masked K (Sec. 3.6), one element pass:
  * d_diag[k] = sum_{e owning k} E_e KE[l, l], 1 on fixed DOFs. */
 mfto_status mfto_jacobi_diag(mfto_handle* h, mfto_form form, const void* d_E,
@@ -243,6 +253,22 @@ mfto_status mfto_pcg(mfto_handle* h, const double* d_E, const double* d_f,
 mfto_status mfto_ir_solve(mfto_handle* h, mfto_form inner, double inner_tol,
                           const double* d_E, const double* d_f, double* d_u,
                           mfto_ir_stats* st);
+
+/* How the inner Jacobi-PCG of mfto_ir_solve (and of mfto_simp_step with a
+ * mixed solver) starts at each outer step:
+ *   MFTO_IR_RESTART (default): from e = 0 with the direction p = z, the
+ *     residual correction of Sec. 3.5 as written (each inner solve is a new
+ *     Krylov process);
+ *   MFTO_IR_CONTINUE: from e = 0 on the new FP64 residual, but keeping the
+ *     last search direction: the first direction is z + (rho / rho_prev) p
+ *     with rho_prev the r.z that formed p.  This is reliable updating
+ *     (residual replacement): one Krylov process whose FP32 recursive
+ *     residual is replaced by the true FP64 residual whenever it has fallen by
+ *     inner_tol, so the inner iterations add up to about those of one long CG
+ *     instead of restarting the superlinear phase at every outer step.
+ * Outer residual, accumulation, stopping and stall rules are the same. */
+enum { MFTO_IR_RESTART = 0, MFTO_IR_CONTINUE = 1 };
+mfto_status mfto_set_ir_mode(mfto_handle* h, int32_t mode);
 
 /* Several load cases at once (multi-RHS).  V and Y hold nrhs DOF vectors
  * one after the other ([nrhs][n_dof]); every case uses the same moduli and

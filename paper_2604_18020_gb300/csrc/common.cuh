@@ -94,6 +94,8 @@ struct mfto_handle {
   int persist_tiling[4];    // its column tiling: tiles in x, y, z and node layers per chunk
   int occ_kv32, occ_pcg32;  // resident CTAs per SM of the FP32 block kernels
   int occ_col[2];           // ... of the FP32 column kernels (K.v, CG K.v)
+  int col_nzc;              // node layers per z-chunk of the column kernels (0: automatic)
+  int col_minb;             // register budget of the column kernels: 2 or 3 CTAs per SM
   unsigned int* d_bar;      // tree grid-barrier counters of the persistent CG (zeroed)
   int occ_tc[12];           // ... of the tensor-core kernels, [2 * (2 kind + split) + pcg]
   int occ_multi[3];         // ... of the multi-RHS kernels (F64 K.V, F32 K.V, F32 CG step)
@@ -131,6 +133,7 @@ struct mfto_handle {
   double inner_tol;
   int32_t inner_maxit;
   int32_t max_outer;
+  int32_t ir_mode;          // MFTO_IR_RESTART or MFTO_IR_CONTINUE (mfto_set_ir_mode)
   // learned solve (learned.cu): network, correction period and its buffers
   struct LearnedWs* learned;
   // PCG graph cache: one captured chunk of check_every iterations per solver
@@ -282,6 +285,8 @@ struct DotAcc<float> {
   static constexpr bool kWarpReduced = true;    // finish(): one partial per warp (lane 0)
   DFloat s{0.f, 0.f};
   __device__ __forceinline__ void add_prod(float a, float b) { s = df_add(s, df_prod(a, b)); }
+  // adds one FP32 value (e.g. a short FP32 sum of products)
+  __device__ __forceinline__ void add(float t) { s = df_add(s, DFloat{t, 0.f}); }
   // must be called by all 32 lanes of the warp: lane 0 returns the warp's
   // sum in FP64, the other lanes 0
   __device__ __forceinline__ double finish() const {
@@ -416,7 +421,7 @@ mfto_status pcg_kv_tc_launch(mfto_handle* h, int form, const float* E, const flo
                              double* partials, cudaStream_t st);
 template <typename T>
 mfto_status pcg_start(mfto_handle* h, const PcgVecs<T>& v, const T* rhs, const T* Ku, double rtol,
-                      int maxit);
+                      int maxit, double rz_prev = 0.0);
 template <typename T>
 mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalars* host_s);
 void pcg_graph_release(mfto_handle* h);

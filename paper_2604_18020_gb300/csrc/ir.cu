@@ -75,6 +75,7 @@ mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const doub
                          h->d_q32, h->d_dinv32, h->d_pcg32, h->d_partials, h->d_partials2,
                          (int)inner};
   double prev = 0.0;
+  double rz_prev = 0.0;   // > 0: the next inner solve continues the last direction
   int stalls = 0;
   out->status = MFTO_NOT_CONVERGED;
   for (int outer = 0;; ++outer) {
@@ -109,15 +110,30 @@ mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const doub
     prev = rel;
     // inner solve from e = 0
     MFTO_CUDA(h, cudaMemsetAsync(h->d_e32, 0, sizeof(float) * h->n_dof, h->stream));
-    s = pcg_start<float>(h, v, h->d_r32, nullptr, inner_tol, h->inner_maxit);
+    s = pcg_start<float>(h, v, h->d_r32, nullptr, inner_tol, h->inner_maxit, rz_prev);
     if (s != MFTO_OK) return s;
     if (h->cg_engine == 1 && inner == MFTO_FORM_F32 && h->kv_variant == 0)
       s = pcg_persist_iterate(h, v, h->h_pcg32);
     else
       s = pcg_iterate<float>(h, v, 1, h->h_pcg32);
     if (s != MFTO_OK) return s;
-    out->inner_iterations += h->h_pcg32->it;
-    if (h->h_pcg32->status == MFTO_BREAKDOWN) { out->status = MFTO_BREAKDOWN; break; }
+    const PcgScalars& fin = *h->h_pcg32;
+    out->inner_iterations += fin.it;
+    if (fin.status == MFTO_BREAKDOWN) { out->status = MFTO_BREAKDOWN; break; }
+    // Continued direction (reliable updating): the next inner solve starts
+    // from the true FP64 residual but keeps the last search direction p_{k-1}
+    // and the r.z of the iteration that formed it, rho_{k-1} = rho_k / beta_k,
+    // so the first new direction is z + (rho / rho_{k-1}) p_{k-1}.  Iteration j
+    // writes its direction into p1 (j even) or p0 (j odd); the next solve reads
+    // p0 first.
+    rz_prev = 0.0;
+    if (h->ir_mode == MFTO_IR_CONTINUE && fin.it >= 1 && fin.beta > 0.0 &&
+        isfinite(fin.rz / fin.beta)) {
+      if (fin.it & 1)
+        MFTO_CUDA(h, cudaMemcpyAsync(h->d_p0_32, h->d_p1_32, sizeof(float) * h->n_dof,
+                                     cudaMemcpyDeviceToDevice, h->stream));
+      rz_prev = fin.rz / fin.beta;
+    }
     h->launches++;
     ir_accumulate<<<nb_dof, MFTO_BLOCK, 0, h->stream>>>(u, h->d_e32, n);
     MFTO_LAUNCH_CHECK(h);
@@ -145,5 +161,13 @@ extern "C" mfto_status mfto_set_solver(mfto_handle* h, mfto_form form, double in
   h->inner_tol = inner_tol;
   h->inner_maxit = inner_maxit;
   h->max_outer = max_outer;
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_set_ir_mode(mfto_handle* h, int32_t mode) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, mode == MFTO_IR_RESTART || mode == MFTO_IR_CONTINUE,
+               "mfto_set_ir_mode: mode must be MFTO_IR_RESTART or MFTO_IR_CONTINUE");
+  h->ir_mode = mode;
   return MFTO_OK;
 }

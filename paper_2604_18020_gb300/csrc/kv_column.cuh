@@ -272,14 +272,20 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
     if (has_extra) extra = col_fetch(ld, fixed, g, hi, hj, kb);
     float Ecur = col_modulus(E, g, gi, gj, kb - 1);
     __syncthreads();
-    float Flo[3][4], upp[3][4];
-    face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, ey * S::NX + ex, Flo);
+    // face modes and upper-face outputs ping-pong between two register sets
+    // (the z loop is unrolled by two, so nothing is copied between layers)
+    float F0[3][4], F1[3][4], U0[3][4], U1[3][4];
+    face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, ey * S::NX + ex, F0);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int f = 0; f < 4; ++f) upp[c][f] = 0.f;
+      for (int f = 0; f < 4; ++f) U0[c][f] = 0.f;
     ColNode mine = own;          // this thread's node of layer ez + 1 (pn and mask of the owner)
-    for (int ez = kb - 1; ez < ke; ++ez) {
+    // one element layer: Flo = face modes of node layer ez (in), Fup = those of
+    // ez + 1 (out), upp = upper-face outputs of element ez - 1 (in), up = those
+    // of element ez (out)
+    auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
+                     const float (&upp)[3][4], float (&up)[3][4]) {
       // 1. stage node layer ez + 1; fetch layer ez + 2 and the next modulus
       stage(ez + 1, own, extra);
       const ColNode mine_cur = mine;   // node layer ez of this column (owned node values)
@@ -292,7 +298,7 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
       }
       __syncthreads();
       // 2, 3. upper face modes, element operator
-      float Fup[3][4], lo[3][4], up[3][4];
+      float lo[3][4];
       face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, ey * S::NX + ex, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
       if (ez >= kb) {
@@ -314,22 +320,19 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
           float acc[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            float s = sums[(4 * c + 3) * MFTO_BLOCK + tid - S::CX - 1];
-            s += sums[(4 * c + 2) * MFTO_BLOCK + tid - S::CX];
-            s += sums[(4 * c + 1) * MFTO_BLOCK + tid - 1];
-            s += sums[(4 * c + 0) * MFTO_BLOCK + tid];
-            acc[c] = s;
+            float sacc = sums[(4 * c + 3) * MFTO_BLOCK + tid - S::CX - 1];
+            sacc += sums[(4 * c + 2) * MFTO_BLOCK + tid - S::CX];
+            sacc += sums[(4 * c + 1) * MFTO_BLOCK + tid - 1];
+            sacc += sums[(4 * c + 0) * MFTO_BLOCK + tid];
+            acc[c] = sacc;
           }
           epi(gi + g.nx * (gj + g.ny * ez), acc, mine_cur.v, mine_cur.fm, red);
         }
       }
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          upp[c][f] = up[c][f];
-          Flo[c][f] = Fup[c][f];
-        }
+    };
+    for (int ez = kb - 1; ez < ke; ez += 2) {
+      layer(ez, F0, F1, U0, U1);
+      if (ez + 1 < ke) layer(ez + 1, F1, F0, U1, U0);
     }
     __syncthreads();   // the shared layers are restaged by the next tile
   }

@@ -61,8 +61,11 @@ pcg_kv_tile_kernel(const T* __restrict__ E, const T* __restrict__ z, const T* __
   }
 }
 
-// FP32, variant 0: column-streaming body (kv_column.cuh)
-__global__ void __launch_bounds__(MFTO_BLOCK, 2)
+// FP32, variant 0: column-streaming body (kv_column.cuh).  MINB: resident
+// CTAs per SM the register allocation is held to (2: up to 128 registers per
+// thread, 3: up to 80); mfto_kv_autotune picks one.
+template <int MINB>
+__global__ void __launch_bounds__(MFTO_BLOCK, MINB)
 kv_col_kernel(const float* __restrict__ E, const float* __restrict__ v, float* __restrict__ y,
               const uint8_t* __restrict__ fixed, ModeCoef<float> K, Grid g, ColTiling tl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -70,7 +73,8 @@ kv_col_kernel(const float* __restrict__ E, const float* __restrict__ v, float* _
                  reinterpret_cast<float*>(smem_raw));
 }
 
-__global__ void __launch_bounds__(MFTO_BLOCK, 2)
+template <int MINB>
+__global__ void __launch_bounds__(MFTO_BLOCK, MINB)
 pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
                   const float* __restrict__ p_old, float* __restrict__ p_new,
                   float* __restrict__ q, const uint8_t* __restrict__ fixed, ModeCoef<float> K,
@@ -95,11 +99,12 @@ pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
   }
 }
 
-// column tiling for a standalone launch: chunks sized for the resident CTAs
+// column tiling for a standalone launch: chunks of h->col_nzc node layers if
+// set (mfto_kv_autotune), else sized for the resident CTAs
 ColTiling col_launch_tiling(const mfto_handle* h, int per_sm, int* grid) {
   const Grid g = make_grid(h->mesh);
   const int64_t ctas = (int64_t)per_sm * h->num_sms;
-  const ColTiling tl = col_tiling(g, col_chunk(g, ctas, 4));
+  const ColTiling tl = col_tiling(g, h->col_nzc > 0 ? h->col_nzc : col_chunk(g, ctas, 4));
   int64_t n = tl.count();
   if (n > ctas) n = ctas;
   if (n > MFTO_RED_SLOTS) n = MFTO_RED_SLOTS;
@@ -153,12 +158,15 @@ mfto_status kv_tile_init(mfto_handle* h) {
   if (s == MFTO_OK) s = set_attrs<float>(h);
   if (s != MFTO_OK) return s;
   const int csm = (int)ColShape::smem_bytes;
-  MFTO_CUDA(h, cudaFuncSetAttribute(kv_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
-  MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel,
+  MFTO_CUDA(h, cudaFuncSetAttribute(kv_col_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(kv_col_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel<2>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
-  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[0], kv_col_kernel,
+  MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel<3>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[0], kv_col_kernel<2>,
                                                              MFTO_BLOCK, csm));
-  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[1], pcg_kv_col_kernel,
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[1], kv_col_kernel<3>,
                                                              MFTO_BLOCK, csm));
   if (h->occ_col[0] < 1) h->occ_col[0] = 1;
   if (h->occ_col[1] < 1) h->occ_col[1] = 1;
@@ -182,9 +190,13 @@ template <typename T>
 mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStream_t st) {
   if (sizeof(T) == 4 && h->kv_variant == 0) {
     int grid = 0;
-    const ColTiling tl = col_launch_tiling(h, h->occ_col[0], &grid);
-    kv_col_kernel<<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
-        (const float*)E, (const float*)v, (float*)y, h->d_fixed, h->mc32, make_grid(h->mesh), tl);
+    const ColTiling tl = col_launch_tiling(h, h->occ_col[h->col_minb == 3], &grid);
+    if (h->col_minb == 3)
+      kv_col_kernel<3><<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+          (const float*)E, (const float*)v, (float*)y, h->d_fixed, h->mc32, make_grid(h->mesh), tl);
+    else
+      kv_col_kernel<2><<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+          (const float*)E, (const float*)v, (float*)y, h->d_fixed, h->mc32, make_grid(h->mesh), tl);
     MFTO_LAUNCH_CHECK(h);
     return MFTO_OK;
   }
@@ -202,10 +214,15 @@ mfto_status pcg_kv_tile_launch(mfto_handle* h, const T* E, const T* z, const T* 
                                T* q, PcgScalars* s, double* partials, cudaStream_t st) {
   if (sizeof(T) == 4 && h->kv_variant == 0) {
     int grid = 0;
-    const ColTiling tl = col_launch_tiling(h, h->occ_col[1], &grid);
-    pcg_kv_col_kernel<<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
-        (const float*)E, (const float*)z, (const float*)p_old, (float*)p_new, (float*)q,
-        h->d_fixed, h->mc32, make_grid(h->mesh), tl, s, partials);
+    const ColTiling tl = col_launch_tiling(h, h->occ_col[h->col_minb == 3], &grid);
+    if (h->col_minb == 3)
+      pcg_kv_col_kernel<3><<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+          (const float*)E, (const float*)z, (const float*)p_old, (float*)p_new, (float*)q,
+          h->d_fixed, h->mc32, make_grid(h->mesh), tl, s, partials);
+    else
+      pcg_kv_col_kernel<2><<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+          (const float*)E, (const float*)z, (const float*)p_old, (float*)p_new, (float*)q,
+          h->d_fixed, h->mc32, make_grid(h->mesh), tl, s, partials);
     MFTO_LAUNCH_CHECK(h);
     return MFTO_OK;
   }
@@ -228,3 +245,66 @@ template mfto_status pcg_kv_tile_launch<double>(mfto_handle*, const double*, con
 template mfto_status pcg_kv_tile_launch<float>(mfto_handle*, const float*, const float*,
                                                const float*, float*, float*, PcgScalars*,
                                                double*, cudaStream_t);
+
+// Times the FP32 column K.v for several chunk lengths along z and both
+// register budgets on the handle's FP32 work vectors and keeps the fastest
+// (mfto_kv, the CG K.v of the FP32 inner solves).
+extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_t* minb_out,
+                                        float* us_out) {
+  if (!h) return MFTO_INVALID_ARG;
+  const Grid g = make_grid(h->mesh);
+  const int cand[] = {2, 3, 4, 5, 6, 8, 11, 16, 24, 32};
+  MFTO_CUDA(h, cudaMemsetAsync(h->d_r32, 0, sizeof(float) * h->n_dof, h->stream));
+  MFTO_CUDA(h, cudaMemsetAsync(h->d_E32, 0, sizeof(float) * h->n_elem, h->stream));
+  cudaEvent_t a, b;
+  MFTO_CUDA(h, cudaEventCreate(&a));
+  MFTO_CUDA(h, cudaEventCreate(&b));
+  const int saved_nzc = h->col_nzc, saved_minb = h->col_minb;
+  int best = 0, best_minb = 2;
+  float best_ms = 0.f;
+  for (int minb = 2; minb <= 3; ++minb) {
+    int last = -1;
+    for (int c : cand) {
+      const int nzc = c > g.nz ? g.nz : c;
+      if (nzc == last) continue;
+      last = nzc;
+      h->col_nzc = nzc;
+      h->col_minb = minb;
+      const int reps = 20;
+      for (int rep = 0; rep < reps + 2; ++rep) {   // 2 warm-up launches
+        if (rep == 2) cudaEventRecord(a, h->stream);
+        mfto_status st = kv_tile_launch<float>(h, h->d_E32, h->d_r32, h->d_q32, h->stream);
+        if (st != MFTO_OK) {
+          h->col_nzc = saved_nzc;
+          h->col_minb = saved_minb;
+          cudaEventDestroy(a);
+          cudaEventDestroy(b);
+          return st;
+        }
+      }
+      cudaEventRecord(b, h->stream);
+      cudaError_t e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess) {
+        h->col_nzc = saved_nzc;
+        h->col_minb = saved_minb;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return mfto_fail(h, MFTO_CUDA_ERROR, "mfto_kv_autotune: %s", cudaGetErrorString(e));
+      }
+      h->launches += reps + 2;
+      ms /= reps;
+      if (best == 0 || ms < best_ms) { best = nzc; best_minb = minb; best_ms = ms; }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->col_nzc = best;
+  h->col_minb = best_minb;
+  pcg_graph_release(h);   // captured CG graphs hold the old launch shape
+  if (nzc_out) *nzc_out = best;
+  if (minb_out) *minb_out = best_minb;
+  if (us_out) *us_out = best_ms * 1000.f;
+  return MFTO_OK;
+}

@@ -18,6 +18,7 @@
 // CUDA graph) and reads the scalars after each chunk.
 #include <math.h>
 
+#include "cg_update.cuh"
 #include "common.cuh"
 #include "kv_node.cuh"
 
@@ -35,10 +36,13 @@ namespace {
 
 // r = f - Ku, z = r / d; r.z, r.r, f.f reduced; the solver state is reset.
 // f may alias r (each entry is read before it is written); Ku may be NULL.
+// rz_prev > 0 continues an earlier direction (the caller left it in p0):
+// the first K.v then uses p = z + (r.z / rz_prev) p0 instead of p = z.
 template <typename T>
 __global__ void __launch_bounds__(MFTO_BLOCK)
 pcg_init(const T* f, const T* __restrict__ Ku, const T* __restrict__ dinv, T* r,
-         T* __restrict__ z, int n, double rtol, int maxit, PcgScalars* s, double* partials) {
+         T* __restrict__ z, int n, double rtol, int maxit, double rz_prev, PcgScalars* s,
+         double* partials) {
   __shared__ double sh[64];
   DotAcc<T> d0, d1, d2;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -59,7 +63,7 @@ pcg_init(const T* f, const T* __restrict__ Ku, const T* __restrict__ dinv, T* r,
     s->rr = tot[1];
     s->ff = tot[2];
     s->rtol2ff = rtol * rtol * tot[2];
-    s->beta = 0.0;
+    s->beta = rz_prev > 0.0 ? tot[0] / rz_prev : 0.0;
     s->alpha = 0.0;
     s->it = 0;
     s->maxit = maxit;
@@ -149,30 +153,19 @@ pcg_update(T* __restrict__ u, const T* __restrict__ p, const T* __restrict__ q,
   }
 }
 
-// B for FP32 vectors: one node (3 DOFs) per thread; r.z and r.r accumulate
-// in double-float within each warp and in FP64 across warps and blocks
-// (DotAcc<float>: no FP64 instruction per DOF).
+// B for FP32 vectors: groups of 4 DOFs per thread in a grid-stride loop over
+// few, fat blocks (cg_update.cuh), so the per-thread cost of the reductions
+// is spread over many DOFs; warps finish in double-float, blocks in FP64.
 __global__ void __launch_bounds__(MFTO_BLOCK)
 pcg_update_f32(float* __restrict__ u, const float* __restrict__ p, const float* __restrict__ q,
                float* __restrict__ r, float* __restrict__ z, const float* __restrict__ dinv,
-               int n_node, PcgScalars* s, double* partials) {
+               int n, PcgScalars* s, double* partials) {
   if (*(volatile int32_t*)&s->done) return;
   __shared__ double sh[64];
   const float alpha = (float)s->alpha;
   DotAcc<float> d0, d1;
-  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < n_node; nd += gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int i = 3 * nd + c;
-      u[i] += alpha * p[i];
-      const float ri = r[i] - alpha * q[i];
-      const float zi = ri * dinv[i];
-      r[i] = ri;
-      z[i] = zi;
-      d0.add_prod(ri, zi);
-      d1.add_prod(ri, ri);
-    }
-  }
+  cg_update_f32<false>(u, p, q, r, z, dinv, n, alpha, blockIdx.x * blockDim.x + threadIdx.x,
+                       gridDim.x * blockDim.x, d0, d1);
   const double acc[2] = {d0.finish(), d1.finish()};
   double tot[2];
   if (last_block_reduce<2, true>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
@@ -204,10 +197,12 @@ void launch_update<double>(const mfto_handle* h, cudaStream_t st, const PcgVecs<
 template <>
 void launch_update<float>(const mfto_handle* h, cudaStream_t st, const PcgVecs<float>& v,
                           float* p_new) {
-  int blocks = (int)((h->n_node + MFTO_BLOCK - 1) / MFTO_BLOCK);
-  if (blocks > MFTO_RED_SLOTS) blocks = MFTO_RED_SLOTS;
-  pcg_update_f32<<<blocks, MFTO_BLOCK, 0, st>>>(v.u, p_new, v.q, v.r, v.z, v.dinv,
-                                                (int)h->n_node, v.s, v.part_b);
+  // two resident blocks per SM, at most one float4 group per thread per pass
+  int64_t blocks = (h->n_dof / 4 + MFTO_BLOCK - 1) / MFTO_BLOCK;
+  if (blocks > 2 * (int64_t)h->num_sms) blocks = 2 * (int64_t)h->num_sms;
+  if (blocks < 1) blocks = 1;
+  pcg_update_f32<<<(int)blocks, MFTO_BLOCK, 0, st>>>(v.u, p_new, v.q, v.r, v.z, v.dinv,
+                                                     (int)h->n_dof, v.s, v.part_b);
 }
 
 template <typename T>
@@ -321,12 +316,15 @@ void pcg_graph_release(mfto_handle* h) {
 
 template <typename T>
 mfto_status pcg_start(mfto_handle* h, const PcgVecs<T>& v, const T* rhs, const T* Ku, double rtol,
-                      int maxit) {
+                      int maxit, double rz_prev) {
   const int nb_dof = reduction_blocks(h->n_dof, MFTO_BLOCK);
-  MFTO_CUDA(h, cudaMemsetAsync(v.p0, 0, sizeof(T) * h->n_dof, h->stream));
+  if (!(rz_prev > 0.0)) {
+    rz_prev = 0.0;
+    MFTO_CUDA(h, cudaMemsetAsync(v.p0, 0, sizeof(T) * h->n_dof, h->stream));
+  }
   h->launches++;
   pcg_init<T><<<nb_dof, MFTO_BLOCK, 0, h->stream>>>(rhs, Ku, v.dinv, v.r, v.z, (int)h->n_dof,
-                                                    rtol, maxit, v.s, v.part_a);
+                                                    rtol, maxit, rz_prev, v.s, v.part_a);
   MFTO_LAUNCH_CHECK(h);
   return MFTO_OK;
 }
@@ -362,9 +360,9 @@ mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalar
 }
 
 template mfto_status pcg_start<double>(mfto_handle*, const PcgVecs<double>&, const double*,
-                                       const double*, double, int);
+                                       const double*, double, int, double);
 template mfto_status pcg_start<float>(mfto_handle*, const PcgVecs<float>&, const float*,
-                                      const float*, double, int);
+                                      const float*, double, int, double);
 template mfto_status pcg_iterate<double>(mfto_handle*, const PcgVecs<double>&, int, PcgScalars*);
 template mfto_status pcg_iterate<float>(mfto_handle*, const PcgVecs<float>&, int, PcgScalars*);
 

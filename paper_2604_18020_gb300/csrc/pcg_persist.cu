@@ -22,6 +22,7 @@
 // bar_error and returns; the host reports it.
 #include <math.h>
 
+#include "cg_update.cuh"
 #include "common.cuh"
 #include "kv_column.cuh"
 
@@ -29,49 +30,33 @@ namespace {
 
 constexpr int kItersPerLaunch = 4096;   // iterations per launch before the host looks
 
-// Tree grid barrier: CTA b arrives at counter b % kBarGroups (one 128-byte
-// line each); the last arrival of a group arrives at the root counter, and
-// the last arrival there releases everyone by advancing the generation.
-// Same-address atomics serialise in L2, so a flat counter costs one atomic
-// round per CTA; the tree costs about G / kBarGroups + kBarGroups.  Every
-// wait is bounded: after MFTO_SPIN_LIMIT polls the CTA raises *error and
-// stops waiting, and no later barrier waits once *error is set.
-constexpr int kBarGroups = 32;
-constexpr int kBarStride = 32;          // unsigned ints per counter (128 bytes)
+// Grid barrier on one monotonic counter: each CTA adds 1 with release
+// semantics (no return value, no reset) and polls the counter with acquire
+// loads until it reaches (barriers passed so far) x G.  The counter is zeroed
+// before every launch.  Every wait is bounded: after MFTO_SPIN_LIMIT polls
+// the CTA raises *error and stops waiting, and no later barrier waits once
+// *error is set.
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
-__device__ __forceinline__ void grid_barrier_tree(unsigned int* bar, int32_t* error) {
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void grid_barrier_count(unsigned int* count, unsigned int target,
+                                                   int32_t* error) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int* gen = bar + kBarGroups * kBarStride + kBarStride;   // own line
-    unsigned int* root = bar + kBarGroups * kBarStride;
-    volatile unsigned int* vgen = gen;
+    red_release_add(count, 1u);
     volatile int32_t* verr = error;
-    const unsigned int G = gridDim.x;
-    const unsigned int grp = blockIdx.x % kBarGroups;
-    const unsigned int n_grp = G < kBarGroups ? G : kBarGroups;
-    const unsigned int in_grp = (G - grp + kBarGroups - 1) / kBarGroups;
-    const unsigned int g0 = *vgen;
-    __threadfence();
-    bool released = false;
-    if (atomicAdd(bar + grp * kBarStride, 1u) == in_grp - 1) {
-      bar[grp * kBarStride] = 0u;
-      __threadfence();
-      if (atomicAdd(root, 1u) == n_grp - 1) {
-        *root = 0u;
-        __threadfence();
-        atomicAdd(gen, 1u);
-        released = true;
-      }
+    unsigned int spins = 0;
+    while (ld_acquire(count) < target) {
+      if (*verr) break;
+      if (++spins > MFTO_SPIN_LIMIT) { atomicExch(error, 1); break; }
     }
-    if (!released) {
-      unsigned int spins = 0;
-      while (*vgen == g0) {
-        if (*verr) break;
-        if (++spins > MFTO_SPIN_LIMIT) { atomicExch(error, 1); break; }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
   }
   __syncthreads();
 }
@@ -128,6 +113,7 @@ pcg_persist_f32(const float* __restrict__ E, const uint8_t* __restrict__ fixed,
   const int maxit = s->maxit;
   int it = s->it;
   int done = 0, status = s->status;
+  unsigned int nbar = 0;   // barrier arrivals expected so far
   for (int k = 0; k < max_iters; ++k) {
     float* p_old = (it & 1) ? p1 : p0;
     float* p_new = (it & 1) ? p0 : p1;
@@ -139,7 +125,8 @@ pcg_persist_f32(const float* __restrict__ E, const uint8_t* __restrict__ fixed,
       const double bs = block_sum_w0(col_warp_finish(red), sh);
       if (tid == 0) part[blockIdx.x] = bs;
     }
-    grid_barrier_tree(bar, &s->bar_error);
+    nbar += G;
+    grid_barrier_count(bar, nbar, &s->bar_error);
     if (*(volatile int32_t*)&s->bar_error) break;
     {
       double t[1];
@@ -155,21 +142,9 @@ pcg_persist_f32(const float* __restrict__ E, const uint8_t* __restrict__ fixed,
     alpha = rz / pq;
     // ---- B: u, r, z; shares of r.z and r.r
     {
-      const float a = (float)alpha;
       DotAcc<float> d0, d1;
-      for (int nd = blockIdx.x * blockDim.x + tid; nd < n_node; nd += G * blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const int i = 3 * nd + c;
-          u[i] += a * __ldcg(p_new + i);
-          const float ri = r[i] - a * __ldcg(q + i);
-          const float zi = ri * dinv[i];
-          r[i] = ri;
-          z[i] = zi;
-          d0.add_prod(ri, zi);
-          d1.add_prod(ri, ri);
-        }
-      }
+      cg_update_f32<true>(u, p_new, q, r, z, dinv, 3 * n_node, (float)alpha,
+                          blockIdx.x * blockDim.x + tid, G * blockDim.x, d0, d1);
       const double b0 = block_sum_w0(d0.finish(), sh);
       const double b1 = block_sum_w0(d1.finish(), sh);
       if (tid == 0) {
@@ -177,7 +152,8 @@ pcg_persist_f32(const float* __restrict__ E, const uint8_t* __restrict__ fixed,
         part[2 * MFTO_RED_SLOTS + blockIdx.x] = b1;
       }
     }
-    grid_barrier_tree(bar, &s->bar_error);
+    nbar += G;
+    grid_barrier_count(bar, nbar, &s->bar_error);
     if (*(volatile int32_t*)&s->bar_error) break;
     double t[2];
     grid_allsum<2>(part + MFTO_RED_SLOTS, G, t, sh);
@@ -210,7 +186,7 @@ pcg_persist_f32(const float* __restrict__ E, const uint8_t* __restrict__ fixed,
 }
 
 int persist_smem() { return (int)ColShape::smem_bytes; }
-constexpr size_t kBarBytes = sizeof(unsigned int) * (kBarGroups + 2) * kBarStride;
+constexpr size_t kBarBytes = 128;   // the barrier counter, alone in its line
 
 }  // namespace
 

@@ -27,6 +27,7 @@ NOALLOC_MAX_ELEMENTS = 2048 * 256
  FORM_F16X3) = range(8)
 FORMS = {"f64": FORM_F64, "f32": FORM_F32, "tf32": FORM_TF32, "tf32x3": FORM_TF32X3,
          "bf16": FORM_BF16, "bf16x3": FORM_BF16X3, "f16": FORM_F16, "f16x3": FORM_F16X3}
+IR_RESTART, IR_CONTINUE = 0, 1
 
 
 class Mesh(C.Structure):
@@ -94,6 +95,9 @@ SIGNATURES = {
     "mfto_jacobi_diag": (C.c_int32, [_P, C.c_int32, _P, _P]),
     "mfto_set_kv_variant": (C.c_int32, [_P, C.c_int32]),
     "mfto_set_cg_engine": (C.c_int32, [_P, C.c_int32]),
+    "mfto_set_ir_mode": (C.c_int32, [_P, C.c_int32]),
+    "mfto_kv_autotune": (C.c_int32, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_float)]),
     "mfto_cg_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double)]),
     "mfto_pcg": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
@@ -332,6 +336,19 @@ class Handle:
         """FP32 inner CG: 1 = one persistent cooperative kernel per solve,
         0 = per-iteration kernels replayed from a CUDA graph."""
         _check("mfto_set_cg_engine", lib().mfto_set_cg_engine(self._h, engine), self._h)
+
+    def set_ir_mode(self, mode: int):
+        """IR_RESTART (0): each inner CG starts with p = z; IR_CONTINUE (1): it
+        keeps the previous search direction (reliable updating)."""
+        _check("mfto_set_ir_mode", lib().mfto_set_ir_mode(self._h, mode), self._h)
+
+    def kv_autotune(self):
+        """Pick the fastest z-chunk and register budget of the FP32 column K.v;
+        returns (nzc, ctas_per_sm, us)."""
+        n, mb, us = C.c_int32(), C.c_int32(), C.c_float()
+        _check("mfto_kv_autotune", lib().mfto_kv_autotune(self._h, C.byref(n), C.byref(mb),
+                                                          C.byref(us)), self._h)
+        return n.value, mb.value, us.value
 
     def jacobi_diag(self, E, d, form=FORM_F64):
         dt = self._dt(form)

@@ -327,3 +327,28 @@ def test_oc_unreachable_target_terminates(cuda):
                                                                 device=cuda), out)
         got = out.cpu().numpy()
     assert np.array_equal(got, ref)
+
+
+def test_kv_f32_after_autotune(cuda):
+    """The autotuned launch shape (z-chunk, register budget) of the FP32
+    column K.v gives the same result as the default one, bit for bit (the
+    tiling changes which CTA computes an element, not the order of any sum),
+    and matches the oracle."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    shape = (40, 30, 9)
+    m, fixed, edof, fd = _setup(*shape)
+    KE = fem.ke_exact()
+    E32 = fem.simp_modulus(W.rho_random(m, seed=23), 3.0).astype(np.float32)
+    v32 = W.vec_random(m.n_dof, seed=24).astype(np.float32)
+    with mfto.Handle(*shape, fixed) as h:
+        tE, tv = torch.tensor(E32, device=cuda), torch.tensor(v32, device=cuda)
+        y0 = torch.empty(m.n_dof, dtype=torch.float32, device=cuda)
+        h.kv(tE, tv, y0, form=mfto.FORM_F32)
+        nzc, ctas, us = h.kv_autotune()
+        assert 1 <= nzc <= m.nelz + 1 and ctas in (2, 3) and us > 0
+        y1 = torch.empty_like(y0)
+        h.kv(tE, tv, y1, form=mfto.FORM_F32)
+        assert torch.equal(y0, y1)
+    ref = fem.kv(KE, E32.astype(np.float64), edof, v32.astype(np.float64), fd)
+    assert _rel_inf(y1.cpu().numpy().astype(np.float64), ref) <= 1e-5
