@@ -411,6 +411,8 @@ def profile_run(args):
         h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
         h.set_cg_engine(args.cg_engine)
         h.set_ir_mode(IR_MODES[args.ir_mode])
+        if not args.no_autotune:
+            h.kv_autotune()
     f = torch.tensor(P.f, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
     if args.mode == "profile":

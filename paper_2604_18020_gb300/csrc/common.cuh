@@ -288,8 +288,8 @@ struct DotAcc<float> {
   // adds one FP32 value (e.g. a short FP32 sum of products)
   __device__ __forceinline__ void add(float t) { s = df_add(s, DFloat{t, 0.f}); }
   // must be called by all 32 lanes of the warp: lane 0 returns the warp's
-  // sum in FP64, the other lanes 0
-  __device__ __forceinline__ double finish() const {
+  // sum as a double-float pair (the other lanes hold partial sums)
+  __device__ __forceinline__ DFloat finish_df() const {
     DFloat v = s;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -298,9 +298,93 @@ struct DotAcc<float> {
       w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
       v = df_add(v, w);
     }
-    return (threadIdx.x & 31) == 0 ? (double)v.hi + (double)v.lo : 0.0;
+    return v;
+  }
+  // as finish_df, converted to FP64 by lane 0 alone (the other lanes return
+  // 0 and execute no FP64 instruction: the FP64 pipe is 1/64 of FP32 here)
+  __device__ __forceinline__ double finish() const {
+    const DFloat v = finish_df();
+    double r = 0.0;
+    if ((threadIdx.x & 31) == 0) r = (double)v.hi + (double)v.lo;
+    return r;
   }
 };
+
+// Block sum of double-float values that live in lane 0 of each warp; the
+// result is valid in thread 0 (FP32 arithmetic only).  sh: 32 float2.
+__device__ __forceinline__ DFloat block_sum_df(DFloat v, float2* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = make_float2(v.hi, v.lo);
+  __syncthreads();
+  DFloat t{0.f, 0.f};
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) t = df_add(t, DFloat{sh[w].x, sh[w].y});
+  }
+  return t;
+}
+
+// last_block_reduce for FP32 dot products held as double-float pairs in lane
+// 0 of each warp (DotAcc<float>::finish_df): block partials are published as
+// pairs, and the last block sums them with warp 0 in double-float, in block
+// order, converting to FP64 once per total.  No FP64 instruction runs outside
+// that conversion.  out[0..K) is valid in every thread of the last block.
+template <int K>
+__device__ __forceinline__ bool last_block_reduce_df(const DFloat (&v)[K], double* partials,
+                                                     unsigned int* ticket, double* out,
+                                                     double* sh) {
+  __shared__ bool s_last;
+  float2* shf = reinterpret_cast<float2*>(sh);          // [0, 32): warp values
+  float2* pf = reinterpret_cast<float2*>(partials);     // one pair per double slot
+  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  DFloat bs[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) bs[c] = block_sum_df(v[c], shf);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) pf[c * MFTO_RED_SLOTS + bid] = make_float2(bs[c].hi, bs[c].lo);
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    s_last = (t == nb - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      DFloat t{0.f, 0.f};
+      for (int b = threadIdx.x; b < (int)nb; b += 32) {
+        const float2 x = __ldcg(&pf[c * MFTO_RED_SLOTS + b]);
+        t = df_add(t, DFloat{x.x, x.y});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        DFloat w;
+        w.hi = __shfl_down_sync(0xffffffffu, t.hi, o);
+        w.lo = __shfl_down_sync(0xffffffffu, t.lo, o);
+        t = df_add(t, w);
+      }
+      if (threadIdx.x == 0) sh[32 + c] = (double)t.hi + (double)t.lo;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < K; ++c) out[c] = sh[32 + c];
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// A device FP64 scalar as FP32 for every thread of the block: one conversion
+// by thread 0, broadcast through shared memory (call once per kernel).
+__device__ __forceinline__ float scalar_as_f32(const double* p) {
+  __shared__ float s_val;
+  if (threadIdx.x == 0) s_val = (float)*p;
+  __syncthreads();
+  return s_val;
+}
 
 // Publish K per-block partial sums and let the last block to arrive reduce
 // them in block-index order.  Returns true in every thread of that last
@@ -343,6 +427,43 @@ __device__ __forceinline__ bool last_block_reduce(const double (&v)[K],
   for (int c = 0; c < K; ++c) out[c] = sh[32 + c];
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
+}
+
+// Sum of K doubles over the block in a fixed order; every thread receives
+// the totals.  sh must hold 8 K doubles (256 threads).
+template <int K>
+__device__ __forceinline__ void block_allsum(double (&v)[K], double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh[w * K + k];
+    v[k] = t;
+  }
+}
+
+// Totals of K partial rows (G entries each), identical in every thread of
+// every CTA.
+template <int K>
+__device__ __forceinline__ void grid_allsum(const double* part, int G, double (&out)[K],
+                                            double* sh) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) t += __ldcg(part + k * MFTO_RED_SLOTS + b);
+    out[k] = t;
+  }
+  block_allsum<K>(out, sh);
 }
 
 // Grid-wide barrier for a cooperative launch.  Every wait is bounded: after

@@ -77,6 +77,12 @@ static inline int col_chunk(const Grid& g, int64_t ctas, int min_nzc) {
   return nzc;
 }
 
+// Column tiling and grid of a standalone launch of a column kernel for a
+// handle (kv_tile.cu): z-chunks of the autotuned length, else sized for
+// per_sm resident CTAs per SM.
+struct mfto_handle;
+ColTiling col_launch_tiling(const mfto_handle* h, int per_sm, int* grid);
+
 // Loaders of one node's 3 components (already masked by the caller).
 struct ColLoadPlain {                 // v, through L1
   const float* v;
@@ -342,12 +348,7 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
 // Warp sum of double-float shares; lane 0 returns the warp's total in FP64,
 // the other lanes 0 (the convention of DotAcc<float>::finish).
 __device__ __forceinline__ double col_warp_finish(DFloat v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    DFloat w;
-    w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
-    w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
-    v = df_add(v, w);
-  }
-  return (threadIdx.x & 31) == 0 ? (double)v.hi + (double)v.lo : 0.0;
+  DotAcc<float> acc;
+  acc.s = v;
+  return acc.finish();
 }

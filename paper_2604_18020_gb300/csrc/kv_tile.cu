@@ -82,12 +82,13 @@ pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
   if (*(volatile int32_t*)&s->done) return;  // uniform over the grid
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[64];
-  const float beta = (float)s->beta;
-  const DFloat red = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{z, p_old, beta},
-                                    ColPcg{p_new, q}, reinterpret_cast<float*>(smem_raw));
-  const double w[1] = {col_warp_finish(red)};
+  const float beta = scalar_as_f32(&s->beta);
+  DotAcc<float> acc;
+  acc.s = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{z, p_old, beta}, ColPcg{p_new, q},
+                         reinterpret_cast<float*>(smem_raw));
+  const DFloat w[1] = {acc.finish_df()};
   double tot[1];
-  if (last_block_reduce<1, true>(w, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce_df<1>(w, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
     s->pq = tot[0];
     if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
       s->done = 1;
@@ -97,19 +98,6 @@ pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
       s->alpha = s->rz / tot[0];
     }
   }
-}
-
-// column tiling for a standalone launch: chunks of h->col_nzc node layers if
-// set (mfto_kv_autotune), else sized for the resident CTAs
-ColTiling col_launch_tiling(const mfto_handle* h, int per_sm, int* grid) {
-  const Grid g = make_grid(h->mesh);
-  const int64_t ctas = (int64_t)per_sm * h->num_sms;
-  const ColTiling tl = col_tiling(g, h->col_nzc > 0 ? h->col_nzc : col_chunk(g, ctas, 4));
-  int64_t n = tl.count();
-  if (n > ctas) n = ctas;
-  if (n > MFTO_RED_SLOTS) n = MFTO_RED_SLOTS;
-  *grid = (int)n;
-  return tl;
 }
 
 template <typename T>
@@ -152,6 +140,19 @@ mfto_status set_attrs(mfto_handle* h) {
 }
 
 }  // namespace
+
+// column tiling for a standalone launch: chunks of h->col_nzc node layers if
+// set (mfto_kv_autotune), else sized for the resident CTAs
+ColTiling col_launch_tiling(const mfto_handle* h, int per_sm, int* grid) {
+  const Grid g = make_grid(h->mesh);
+  const int64_t ctas = (int64_t)per_sm * h->num_sms;
+  const ColTiling tl = col_tiling(g, h->col_nzc > 0 ? h->col_nzc : col_chunk(g, ctas, 4));
+  int64_t n = tl.count();
+  if (n > ctas) n = ctas;
+  if (n > MFTO_RED_SLOTS) n = MFTO_RED_SLOTS;
+  *grid = (int)n;
+  return tl;
+}
 
 mfto_status kv_tile_init(mfto_handle* h) {
   mfto_status s = set_attrs<double>(h);

@@ -162,13 +162,13 @@ pcg_update_f32(float* __restrict__ u, const float* __restrict__ p, const float* 
                int n, PcgScalars* s, double* partials) {
   if (*(volatile int32_t*)&s->done) return;
   __shared__ double sh[64];
-  const float alpha = (float)s->alpha;
+  const float alpha = scalar_as_f32(&s->alpha);
   DotAcc<float> d0, d1;
   cg_update_f32<false>(u, p, q, r, z, dinv, n, alpha, blockIdx.x * blockDim.x + threadIdx.x,
                        gridDim.x * blockDim.x, d0, d1);
-  const double acc[2] = {d0.finish(), d1.finish()};
+  const DFloat acc[2] = {d0.finish_df(), d1.finish_df()};
   double tot[2];
-  if (last_block_reduce<2, true>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
+  if (last_block_reduce_df<2>(acc, partials, &s->ticket_c, tot, sh) && threadIdx.x == 0) {
     s->it += 1;
     s->rr = tot[1];
     s->beta = tot[0] / s->rz;
@@ -338,9 +338,11 @@ mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalar
   for (;;) {
     MFTO_CUDA(h, cudaMemcpyAsync(host_s, v.s, sizeof(PcgScalars), cudaMemcpyDeviceToHost, h->stream));
     MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+    const int progress = host_s->it;   // iterations completed so far
     if (pg->timed) {
       // harvest the K.v launches of the previous chunk that did work
-      const int ran = host_s->it - it_before + (host_s->status == MFTO_BREAKDOWN ? 1 : 0);
+      const int ran = progress - it_before +
+                      (host_s->done && host_s->status == MFTO_BREAKDOWN ? 1 : 0);
       for (int i = 0; i < ran && i < pg->chunk; ++i) {
         float ms = 0.f;
         MFTO_CUDA(h, cudaEventElapsedTime(&ms, pg->ev[2 * i], pg->ev[2 * i + 1]));
@@ -348,7 +350,7 @@ mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalar
         h->ev.total_ms[f] += ms;
         h->ev.launches[f]++;
       }
-      it_before = host_s->it;
+      it_before = progress;
     }
     if (host_s->tc_error)
       return mfto_fail(h, MFTO_CUDA_ERROR, "tensor-core completion wait timed out");

@@ -61,43 +61,6 @@ __device__ __forceinline__ void grid_barrier_count(unsigned int* count, unsigned
   __syncthreads();
 }
 
-// Sum of K doubles over the block in a fixed order; every thread receives
-// the totals.  sh must hold 8 K doubles (256 threads).
-template <int K>
-__device__ __forceinline__ void block_allsum(double (&v)[K], double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += sh[w * K + k];
-    v[k] = t;
-  }
-}
-
-// Totals of K partial rows (G entries each), identical in every thread of
-// every CTA.
-template <int K>
-__device__ __forceinline__ void grid_allsum(const double* part, int G, double (&out)[K],
-                                            double* sh) {
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double t = 0.0;
-    for (int b = threadIdx.x; b < G; b += blockDim.x) t += __ldcg(part + k * MFTO_RED_SLOTS + b);
-    out[k] = t;
-  }
-  block_allsum<K>(out, sh);
-}
-
 __global__ void __launch_bounds__(MFTO_BLOCK, 2)
 pcg_persist_f32(const float* __restrict__ E, const uint8_t* __restrict__ fixed,
                 const float* __restrict__ dinv, ModeCoef<float> K, Grid g, ColTiling tl,
