@@ -49,6 +49,14 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 IR_MODES = {"restart": 0, "continue": 1}
+# DRAM bytes (read + write) per launch of the dominant kernels from one ncu
+# capture (profiles/kv_f32_col_cg_cantilever_120x60x30_full.md,
+# profiles/kv_f64_pcg_cantilever_256x128x150_full.md, the latter scaled from
+# 4,915,200 to 216,000 elements by the bytes it reads per element); cold
+# caches, so an upper bound for launches inside the CG, whose vectors stay in
+# L2.  To be refreshed whenever those kernels change.
+NCU_DRAM_BYTES = {("pcg_kv_col_kernel<2>", WORKLOAD): 6.621696e6,
+                  ("pcg_kv_tile_kernel<double>", WORKLOAD): (294.4e6 + 199.3e6) * 216000 / 4915200}
 REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
 
@@ -315,6 +323,8 @@ def gpu_bench(args, rank, local_rank, world):
         bytes_per_launch = m.n_node * (4 * 12 + 1) + 4 * m.n_elem
         kname = ("pcg_kv_tile_kernel<float>" if args.inner_form == "f32"
                  else f"pcg_kv_tc_kernel ({args.inner_form})")
+        if args.inner_form == "f32" and not persistent:
+            kname = "pcg_kv_col_kernel<2>" if tuned is None or tuned[1] == 0 else "pcg_kv_col_kernel<3>"
         if persistent:
             # one CG iteration of the persistent kernel: the K.v phase above plus
             # the vector update (reads u, p, q, r, 1/d; writes u, r, z: 32 B/DOF);
@@ -336,7 +346,8 @@ def gpu_bench(args, rank, local_rank, world):
                     "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                     "peak_source": f"FP32 FMA pipe, {n_sm} SMs x 128 FMA/clk x 2 flop x "
                                    f"{sm_mhz:.0f} MHz median SM clock under load"}
-        roof.update({"traffic": None, "kernel": kname, "bytes_per_launch": bytes_per_launch,
+        roof.update({"traffic": NCU_DRAM_BYTES.get((kname, WORKLOAD)), "kernel": kname,
+                     "bytes_per_launch": bytes_per_launch,
                      "flop_per_elem": FLOP_PER_ELEM, "frac_hbm": frac_hbm,
                      "frac_fp32_pipe": frac_alu})
         if persistent:
@@ -346,8 +357,9 @@ def gpu_bench(args, rank, local_rank, world):
     else:
         fp64_peak_tflops = n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12   # 2 DFMA/clk/SM, measured clock
         roof = {"bound": "alu", "achieved": FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12,
-                "peak": fp64_peak_tflops, "unit": "TFLOP/s", "traffic": None,
+                "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                 "kernel": "pcg_kv_tile_kernel<double>",
+                "traffic": NCU_DRAM_BYTES.get(("pcg_kv_tile_kernel<double>", WORKLOAD)),
                 "peak_source": f"FP64 FMA pipe, {n_sm} SMs x 2 DFMA/clk x 2 flop x "
                                f"{sm_mhz:.0f} MHz median SM clock under load",
                 "flop_per_elem": FLOP_PER_ELEM}
@@ -365,7 +377,7 @@ def gpu_bench(args, rank, local_rank, world):
                    "kv_kernel": "tiled mode-space",
                    "cg_engine": ("persistent" if persistent else "graph") if args.form == "mixed" else "graph",
                    "kv_f32_zchunk": tuned[0] if tuned else None,
-                   "kv_f32_ctas_per_sm": tuned[1] if tuned else None,
+                   "kv_f32_kernel_kind": tuned[1] if tuned else None,
                    "ir_mode": args.ir_mode if args.form == "mixed" else None,
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -217,13 +217,17 @@ mfto_status mfto_set_cg_engine(mfto_handle* h, int32_t engine);
 
 /* Autotune the FP32 K.v (variant 0): times the column kernel for several
  * lengths of its z-chunks (node layers per CTA tile; longer chunks recompute
- * fewer element layers, shorter ones give more CTAs) and two register
- * budgets (2 or 3 resident CTAs per SM) on the handle's own work vectors, and
- * keeps the fastest pair for mfto_kv and the FP32 inner CG.  Returns the
- * chosen chunk length, CTAs per SM and time per launch in microseconds (any
- * may be NULL).  Overwrites the handle's FP32 work vectors; synchronises the
- * stream. */
-mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc, int32_t* ctas_per_sm, float* us);
+ * fewer element layers, shorter ones give more CTAs) and each kernel kind
+ * (register allocation held to 2 (kind 0) or 3 (kind 1) resident CTAs per
+ * SM) on the handle's own work vectors, and keeps the fastest pair for
+ * mfto_kv and the FP32 inner CG.  All shapes give bit-identical K.v
+ * results.  Returns the chosen chunk length, kind and
+ * time per launch in microseconds (any may be NULL).  Overwrites the
+ * handle's FP32 work vectors; synchronises the stream. */
+mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc, int32_t* kind, float* us);
+/* Set the FP32 column K.v's launch shape by hand: z-chunk length nzc (0:
+ * automatic) and kernel kind 0 or 1 (as in mfto_kv_autotune). */
+mfto_status mfto_set_kv_shape(mfto_handle* h, int32_t nzc, int32_t kind);
 
 /* Jacobi diagonal of the masked K (Sec. 3.6), one element pass:
  * d_diag[k] = sum_{e owning k} E_e KE[l, l], 1 on fixed DOFs. */
@@ -362,11 +366,13 @@ mfto_status mfto_oc_update(mfto_handle* h, const double* d_rho,
                            const double* d_dc, double* d_rho_new,
                            mfto_iter_stats* st);
 
-/* One SIMP iteration (the loop of Sec. 3.1 / 3.7): rho_phys = filter(rho);
+/* One SIMP iteration (the loop of Sec. 3.1 / 3.7): rho_phys = filter(rho)
+ * (then the Heaviside projection when mfto_set_projection turned it on);
  * E = E(rho_phys); Jacobi-PCG on K(E) u = f warm-started from d_u;
- * compliance and sensitivities; filter transpose; OC.  d_rho is updated in
- * place, d_u holds the new displacement, d_rho_phys (may be NULL) receives
- * the filtered field used in this iteration. */
+ * compliance and sensitivities (through the projection's derivative when
+ * on); filter transpose; OC.  d_rho is updated in place, d_u holds the new
+ * displacement, d_rho_phys (may be NULL) receives the physical field used in
+ * this iteration. */
 mfto_status mfto_simp_step(mfto_handle* h, double* d_rho, double* d_u,
                            const double* d_f, double* d_rho_phys,
                            mfto_iter_stats* st);
@@ -494,6 +500,100 @@ mfto_status mfto_set_learned(mfto_handle* h, mfto_nn* nn, int32_t every);
  * FP64 residual meets rtol.  Synchronises the stream. */
 mfto_status mfto_learned_solve(mfto_handle* h, const double* d_E, const double* d_rho_phys,
                                const double* d_f, double* d_u, mfto_learned_stats* st);
+
+/* ---------------------------------- three-field SIMP, SIMP-120 protocol -- */
+
+/* Smoothed Heaviside projection of the filtered field (Sec. 3.1):
+ * rho_phys = (tanh(beta eta) + tanh(beta (rho_bar - eta))) /
+ *            (tanh(beta eta) + tanh(beta (1 - eta))), clipped to [0, 1];
+ * mfto_simp_step applies it after the filter and chains the sensitivities
+ * through its derivative.  beta = 0 turns it off (the plain path, the
+ * default); eta in (0, 1), the paper's 0.5. */
+mfto_status mfto_set_projection(mfto_handle* h, double beta, double eta);
+/* The projection alone (testing): d_rho_phys (may be NULL) = H(d_rho_bar);
+ * d_dc (may be NULL) *= H'(d_rho_bar), in place.  MFTO_INVALID_ARG when the
+ * projection is off. */
+mfto_status mfto_project(mfto_handle* h, const double* d_rho_bar, double* d_rho_phys,
+                         double* d_dc);
+
+typedef struct {
+  int32_t n_iter;           /* iterations (120; beyond, the last phase holds) */
+  double rmin0;             /* filter radius of phase 1                       */
+  double eta;               /* projection threshold (0.5)                     */
+  double restart_factor;    /* restart when c > factor x selected c (1.12)    */
+  double select_min_penal;  /* selectable iterates: p >= this (3.0) ...       */
+  double select_max_gray;   /* ... and grayness < this (0.25)                 */
+} mfto_protocol_params;
+
+typedef struct {
+  int32_t iterations;       /* iterations run                                 */
+  int32_t selected_iteration; /* 1-based; 0 when no iterate was selectable    */
+  double selected_compliance;
+  int32_t restarts;
+  int32_t cg_iterations;    /* solver iterations of all steps                 */
+} mfto_protocol_stats;
+
+void mfto_default_protocol_params(mfto_protocol_params* p);
+
+/* The benchmark protocol of Sec. 4.1 with mfto_simp_step and the handle's
+ * solver: iteration i (1-based) runs with the phase values (p, beta, m) =
+ * (1.5, 1, 0.20) for i <= 15, (3.5, 4, 0.15) for i <= 40, (4.5, 16, 0.08)
+ * for i <= 65, (4.5, 32, 0.05) after; r_min = rmin0 in phase 1 and, in each
+ * later phase, ramps linearly from the previous phase's end value to 1.35,
+ * 1.25, 1.20, reached at the phase's last iteration.  The compliance of
+ * iteration i belongs to the design entering it; when it exceeds
+ * restart_factor times the selected compliance the next design is the
+ * selected one (the displacement keeps its warm start); otherwise the OC
+ * result.  The selected design is the lowest-compliance entering design
+ * among iterates with p >= select_min_penal and grayness < select_max_gray.
+ * d_rho: initial design in (the paper starts from V_f), final design out;
+ * d_rho_selected: the selected design (unchanged if none).  Host arrays of
+ * n_iter entries (each may be NULL): compliance, grayness, restarted (1 when
+ * a restart followed the iteration).  The handle's parameters and projection
+ * setting are restored at exit.  Synchronises the stream. */
+mfto_status mfto_simp_protocol(mfto_handle* h, double* d_rho, double* d_u, const double* d_f,
+                               double* d_rho_selected, const mfto_protocol_params* p,
+                               double* compliance, double* grayness, int32_t* restarted,
+                               mfto_protocol_stats* st);
+
+/* ------------------------------------------- condition-number estimate -- */
+
+typedef struct {
+  int32_t power_maxit;      /* power-iteration step cap (50)                   */
+  double power_tol;         /* stop when lambda_max changes by < tol (1e-6)    */
+  int32_t inverse_maxit;    /* inverse-iteration step cap (50)                 */
+  double inverse_tol;       /* stop when 1/lambda_min changes by < tol (1e-4)  */
+  double inner_rtol;        /* inner PCG: ||r|| <= rtol ||v||, ||v|| = 1 (1e-8) */
+  int32_t inner_maxit;      /* inner PCG iteration cap (2000)                  */
+} mfto_kappa_params;
+
+typedef struct {
+  double lambda_max;        /* Rayleigh quotient of the last power step        */
+  double lambda_min;        /* 1 / (v . K^-1 v) of the last inverse step        */
+  double kappa;             /* lambda_max / lambda_min                         */
+  int32_t power_steps, inverse_steps;
+  int32_t inner_iterations; /* PCG iterations of all inverse steps             */
+  int32_t inner_capped;     /* inner solves that stopped at the cap            */
+} mfto_kappa_stats;
+
+/* The defaults above: the paper's caps and tolerances (Sec. 3.5). */
+void mfto_default_kappa_params(mfto_kappa_params* p);
+
+/* Matrix-free estimate of kappa(K) on the free DOFs (Sec. 3.5, "Condition
+ * number of the SIMP stiffness matrix"): power iteration for lambda_max and
+ * inverse iteration for lambda_min, every product an FP64 K(E).v of this
+ * handle, every inverse step a Jacobi-PCG solve from zero (the paper's
+ * SciPy CG is unpreconditioned; converged, both give K^-1 v).  d_E: FP64
+ * moduli.  d_v_power, d_v_inverse: the start vectors (n_dof doubles; the
+ * caller seeds them); they are zeroed on the fixed DOFs, normalised, and
+ * overwritten with the final unit iterates.  d_work: n_dof doubles of
+ * scratch.  p may be NULL (defaults).  Capped estimates bound the spectrum
+ * from inside, so kappa is not overestimated.  MFTO_INVALID_ARG for a start
+ * vector that vanishes on the free DOFs, MFTO_BREAKDOWN for a vanishing
+ * iterate.  Synchronises the stream. */
+mfto_status mfto_kappa(mfto_handle* h, const double* d_E, double* d_v_power,
+                       double* d_v_inverse, double* d_work, const mfto_kappa_params* p,
+                       mfto_kappa_stats* st);
 
 /* ------------------------------------------------------------- timing -- */
 

@@ -93,9 +93,9 @@ struct mfto_handle {
   int persist_grid;         // CTAs of the persistent CG launch (0: unavailable)
   int persist_tiling[4];    // its column tiling: tiles in x, y, z and node layers per chunk
   int occ_kv32, occ_pcg32;  // resident CTAs per SM of the FP32 block kernels
-  int occ_col[2];           // ... of the FP32 column kernels (K.v, CG K.v)
+  int occ_col[2];           // ... of the FP32 column kernel kinds (kv_tile.cu)
   int col_nzc;              // node layers per z-chunk of the column kernels (0: automatic)
-  int col_minb;             // register budget of the column kernels: 2 or 3 CTAs per SM
+  int col_kind;             // column kernel kind (mfto_kv_autotune)
   unsigned int* d_bar;      // tree grid-barrier counters of the persistent CG (zeroed)
   int occ_tc[12];           // ... of the tensor-core kernels, [2 * (2 kind + split) + pcg]
   int occ_multi[3];         // ... of the multi-RHS kernels (F64 K.V, F32 K.V, F32 CG step)
@@ -116,6 +116,8 @@ struct mfto_handle {
   MiscScalars* h_misc;      // pinned mirror
   // SIMP step workspace
   double *d_rho_phys, *d_E, *d_dc, *d_dc_phys;
+  double *d_rho_bar, *d_rho_in;   // filtered field (projection on); design entering a step
+  double proj_beta, proj_eta;     // Heaviside projection (beta = 0: off), mfto_set_projection
   // FP32 workspace of the inner solve of the iterative refinement
   float *d_r32, *d_z32, *d_p0_32, *d_p1_32, *d_q32, *d_dinv32, *d_e32, *d_E32;
   PcgScalars* d_pcg32;
@@ -506,6 +508,10 @@ mfto_status modulus_launch(mfto_handle* h, mfto_form form,
                            const double* rho_phys, void* E);
 mfto_status filter_launch(mfto_handle* h, const double* x, double* y,
                           int transpose);
+mfto_status filter_setup(mfto_handle* h);
+bool projection_active(const mfto_handle* h);
+mfto_status project_launch(mfto_handle* h, const double* rho_bar, double* rho_phys);
+mfto_status project_chain_launch(mfto_handle* h, const double* rho_bar, double* dc);
 mfto_status compliance_launch(mfto_handle* h, const double* rho_phys,
                               const double* u, double* dc, double* c_out,
                               double* gray_out);

@@ -133,7 +133,7 @@ static void free_handle(mfto_handle* h) {
                   h->d_E, h->d_dc, h->d_dc_phys, h->d_r32, h->d_z32, h->d_p0_32,
                   h->d_p1_32, h->d_q32, h->d_dinv32, h->d_e32, h->d_E32, h->d_pcg32,
                   h->d_btc, h->m_q64, h->m_r32, h->m_z32, h->m_p0, h->m_p1, h->m_q32,
-                  h->m_e32, h->m_pcg, h->m_out, h->d_bar};
+                  h->m_e32, h->m_pcg, h->m_out, h->d_bar, h->d_rho_bar, h->d_rho_in};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -175,6 +175,8 @@ void mode_coefficients(double nu, double hh, ModeCoef<double>* c64, ModeCoef<flo
   }
 }
 
+mfto_status filter_setup(mfto_handle* h);
+
 static mfto_status upload_params(mfto_handle* h) {
   double ke[576];
   float ke32[576];
@@ -188,6 +190,11 @@ static mfto_status upload_params(mfto_handle* h) {
   mode_coefficients(h->p.nu, h->mesh.h, &h->mc64, &h->mc32);
   MFTO_CUDA(h, cudaMemcpyAsync(h->d_ke64, ke, sizeof(ke), cudaMemcpyHostToDevice, h->stream));
   MFTO_CUDA(h, cudaMemcpyAsync(h->d_ke32, ke32, sizeof(ke32), cudaMemcpyHostToDevice, h->stream));
+  return filter_setup(h);
+}
+
+// Cone-filter stencil and row sums of the radius h->p.rmin.
+mfto_status filter_setup(mfto_handle* h) {
   int32_t n = 0;
   mfto_filter_stencil(h->p.rmin, 0, nullptr, nullptr, &n);
   std::vector<int32_t> off(3 * n);
@@ -234,6 +241,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   h->inner_tol = 1e-2;
   h->inner_maxit = 10000;
   h->max_outer = 50;
+  h->proj_beta = 0.0;       // no projection unless asked (the plain path)
+  h->proj_eta = 0.5;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -263,6 +272,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   A((void**)&h->d_E, ne);
   A((void**)&h->d_dc, ne);
   A((void**)&h->d_dc_phys, ne);
+  A((void**)&h->d_rho_bar, ne);
+  A((void**)&h->d_rho_in, ne);
   const size_t nd32 = sizeof(float) * h->n_dof;
   A((void**)&h->d_r32, nd32);
   A((void**)&h->d_z32, nd32);

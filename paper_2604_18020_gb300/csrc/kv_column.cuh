@@ -63,13 +63,13 @@ static inline ColTiling col_tiling(const Grid& g, int nzc) {
 }
 
 // Chunk length along z for a grid of at most `ctas` resident CTAs: split
-// the columns just enough to give every CTA a tile, but keep chunks of at
-// least `min_nzc` node layers (a chunk of n layers recomputes n + 1 element
-// layers).
+// the columns into about three tiles per resident CTA (so that the
+// grid-stride loop balances), but keep chunks of at least `min_nzc` node
+// layers (a chunk of n layers recomputes n + 1 element layers).
 static inline int col_chunk(const Grid& g, int64_t ctas, int min_nzc) {
   const int64_t txy = (int64_t)((g.nx + ColShape::OX - 1) / ColShape::OX) *
                       ((g.ny + ColShape::OY - 1) / ColShape::OY);
-  int64_t zch = ctas / txy;
+  int64_t zch = (3 * ctas + txy - 1) / txy;
   if (zch < 1) zch = 1;
   int nzc = (int)((g.nz + zch - 1) / zch);
   if (nzc < min_nzc) nzc = min_nzc;

@@ -100,6 +100,11 @@ pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
   }
 }
 
+// Column kernel kinds, chosen by mfto_kv_autotune: the register allocation
+// held to 2 (kind 0, up to 128 registers) or 3 (kind 1, up to 80) resident
+// CTAs per SM.
+constexpr int kColKinds = 2;
+
 template <typename T>
 dim3 tile_grid(const mfto_handle* h, int* nzc_out, int per_sm = 1) {
   const Grid g = make_grid(h->mesh);
@@ -165,12 +170,13 @@ mfto_status kv_tile_init(mfto_handle* h) {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel<3>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
-  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[0], kv_col_kernel<2>,
+  // resident CTAs per SM of each kind (the CG form, which is the heavier one)
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[0], pcg_kv_col_kernel<2>,
                                                              MFTO_BLOCK, csm));
-  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[1], kv_col_kernel<3>,
+  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_col[1], pcg_kv_col_kernel<3>,
                                                              MFTO_BLOCK, csm));
-  if (h->occ_col[0] < 1) h->occ_col[0] = 1;
-  if (h->occ_col[1] < 1) h->occ_col[1] = 1;
+  for (int k = 0; k < kColKinds; ++k)
+    if (h->occ_col[k] < 1) h->occ_col[k] = 1;
   MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                    &h->occ_kv32, kv_tile_kernel<float>, MFTO_BLOCK, tile_smem<float>()));
   MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -191,13 +197,16 @@ template <typename T>
 mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStream_t st) {
   if (sizeof(T) == 4 && h->kv_variant == 0) {
     int grid = 0;
-    const ColTiling tl = col_launch_tiling(h, h->occ_col[h->col_minb == 3], &grid);
-    if (h->col_minb == 3)
-      kv_col_kernel<3><<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
-          (const float*)E, (const float*)v, (float*)y, h->d_fixed, h->mc32, make_grid(h->mesh), tl);
+    const int kind = h->col_kind;
+    const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
+    const Grid g = make_grid(h->mesh);
+    const float *Ef = (const float*)E, *vf = (const float*)v;
+    float* yf = (float*)y;
+    const size_t sm = ColShape::smem_bytes;
+    if (kind == 1)
+      kv_col_kernel<3><<<grid, MFTO_BLOCK, sm, st>>>(Ef, vf, yf, h->d_fixed, h->mc32, g, tl);
     else
-      kv_col_kernel<2><<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
-          (const float*)E, (const float*)v, (float*)y, h->d_fixed, h->mc32, make_grid(h->mesh), tl);
+      kv_col_kernel<2><<<grid, MFTO_BLOCK, sm, st>>>(Ef, vf, yf, h->d_fixed, h->mc32, g, tl);
     MFTO_LAUNCH_CHECK(h);
     return MFTO_OK;
   }
@@ -215,15 +224,18 @@ mfto_status pcg_kv_tile_launch(mfto_handle* h, const T* E, const T* z, const T* 
                                T* q, PcgScalars* s, double* partials, cudaStream_t st) {
   if (sizeof(T) == 4 && h->kv_variant == 0) {
     int grid = 0;
-    const ColTiling tl = col_launch_tiling(h, h->occ_col[h->col_minb == 3], &grid);
-    if (h->col_minb == 3)
-      pcg_kv_col_kernel<3><<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
-          (const float*)E, (const float*)z, (const float*)p_old, (float*)p_new, (float*)q,
-          h->d_fixed, h->mc32, make_grid(h->mesh), tl, s, partials);
+    const int kind = h->col_kind;
+    const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
+    const Grid g = make_grid(h->mesh);
+    const float *Ef = (const float*)E, *zf = (const float*)z, *pf = (const float*)p_old;
+    float *pn = (float*)p_new, *qf = (float*)q;
+    const size_t sm = ColShape::smem_bytes;
+    if (kind == 1)
+      pcg_kv_col_kernel<3><<<grid, MFTO_BLOCK, sm, st>>>(Ef, zf, pf, pn, qf, h->d_fixed, h->mc32,
+                                                         g, tl, s, partials);
     else
-      pcg_kv_col_kernel<2><<<grid, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
-          (const float*)E, (const float*)z, (const float*)p_old, (float*)p_new, (float*)q,
-          h->d_fixed, h->mc32, make_grid(h->mesh), tl, s, partials);
+      pcg_kv_col_kernel<2><<<grid, MFTO_BLOCK, sm, st>>>(Ef, zf, pf, pn, qf, h->d_fixed, h->mc32,
+                                                         g, tl, s, partials);
     MFTO_LAUNCH_CHECK(h);
     return MFTO_OK;
   }
@@ -247,10 +259,10 @@ template mfto_status pcg_kv_tile_launch<float>(mfto_handle*, const float*, const
                                                const float*, float*, float*, PcgScalars*,
                                                double*, cudaStream_t);
 
-// Times the FP32 column K.v for several chunk lengths along z and both
-// register budgets on the handle's FP32 work vectors and keeps the fastest
+// Times the FP32 column K.v for several chunk lengths along z and every
+// kernel kind on the handle's FP32 work vectors and keeps the fastest pair
 // (mfto_kv, the CG K.v of the FP32 inner solves).
-extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_t* minb_out,
+extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_t* kind_out,
                                         float* us_out) {
   if (!h) return MFTO_INVALID_ARG;
   const Grid g = make_grid(h->mesh);
@@ -260,24 +272,24 @@ extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_
   cudaEvent_t a, b;
   MFTO_CUDA(h, cudaEventCreate(&a));
   MFTO_CUDA(h, cudaEventCreate(&b));
-  const int saved_nzc = h->col_nzc, saved_minb = h->col_minb;
-  int best = 0, best_minb = 2;
+  const int saved_nzc = h->col_nzc, saved_kind = h->col_kind;
+  int best = 0, best_kind = 0;
   float best_ms = 0.f;
-  for (int minb = 2; minb <= 3; ++minb) {
+  for (int kind = 0; kind < kColKinds; ++kind) {
     int last = -1;
     for (int c : cand) {
       const int nzc = c > g.nz ? g.nz : c;
       if (nzc == last) continue;
       last = nzc;
       h->col_nzc = nzc;
-      h->col_minb = minb;
+      h->col_kind = kind;
       const int reps = 20;
       for (int rep = 0; rep < reps + 2; ++rep) {   // 2 warm-up launches
         if (rep == 2) cudaEventRecord(a, h->stream);
         mfto_status st = kv_tile_launch<float>(h, h->d_E32, h->d_r32, h->d_q32, h->stream);
         if (st != MFTO_OK) {
           h->col_nzc = saved_nzc;
-          h->col_minb = saved_minb;
+          h->col_kind = saved_kind;
           cudaEventDestroy(a);
           cudaEventDestroy(b);
           return st;
@@ -289,23 +301,33 @@ extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
       if (e != cudaSuccess) {
         h->col_nzc = saved_nzc;
-        h->col_minb = saved_minb;
+        h->col_kind = saved_kind;
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         return mfto_fail(h, MFTO_CUDA_ERROR, "mfto_kv_autotune: %s", cudaGetErrorString(e));
       }
       h->launches += reps + 2;
       ms /= reps;
-      if (best == 0 || ms < best_ms) { best = nzc; best_minb = minb; best_ms = ms; }
+      if (best == 0 || ms < best_ms) { best = nzc; best_kind = kind; best_ms = ms; }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->col_nzc = best;
-  h->col_minb = best_minb;
+  h->col_kind = best_kind;
   pcg_graph_release(h);   // captured CG graphs hold the old launch shape
   if (nzc_out) *nzc_out = best;
-  if (minb_out) *minb_out = best_minb;
+  if (kind_out) *kind_out = best_kind;
   if (us_out) *us_out = best_ms * 1000.f;
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_set_kv_shape(mfto_handle* h, int32_t nzc, int32_t kind) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, nzc >= 0, "mfto_set_kv_shape: nzc must be >= 0");
+  MFTO_REQUIRE(h, kind >= 0 && kind < kColKinds, "mfto_set_kv_shape: kind must be 0 or 1");
+  h->col_nzc = nzc;
+  h->col_kind = kind;
+  pcg_graph_release(h);
   return MFTO_OK;
 }

@@ -184,8 +184,14 @@ extern "C" mfto_status mfto_simp_step(mfto_handle* h, double* rho, double* u, co
   if (!h) return MFTO_INVALID_ARG;
   MFTO_REQUIRE(h, rho && u && f, "mfto_simp_step: null pointer");
   double* rho_phys = rho_phys_out ? rho_phys_out : h->d_rho_phys;
-  mfto_status s = filter_launch(h, rho, rho_phys, 0);
+  // filter, then (three-field form) project: rho -> rho_bar -> rho_phys
+  const bool proj = projection_active(h);
+  mfto_status s = filter_launch(h, rho, proj ? h->d_rho_bar : rho_phys, 0);
   if (s != MFTO_OK) return s;
+  if (proj) {
+    s = project_launch(h, h->d_rho_bar, rho_phys);
+    if (s != MFTO_OK) return s;
+  }
   s = modulus_launch(h, MFTO_FORM_F64, rho_phys, h->d_E);
   if (s != MFTO_OK) return s;
   mfto_solve_stats ss;
@@ -212,6 +218,10 @@ extern "C" mfto_status mfto_simp_step(mfto_handle* h, double* rho, double* u, co
   double c = 0.0, gray = 0.0;
   s = compliance_launch(h, rho_phys, u, h->d_dc_phys, &c, &gray);
   if (s != MFTO_OK) return s;
+  if (proj) {   // dc/drho_bar = dc/drho_phys * drho_phys/drho_bar
+    s = project_chain_launch(h, h->d_rho_bar, h->d_dc_phys);
+    if (s != MFTO_OK) return s;
+  }
   s = filter_launch(h, h->d_dc_phys, h->d_dc, 1);
   if (s != MFTO_OK) return s;
   mfto_iter_stats local;

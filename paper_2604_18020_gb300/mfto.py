@@ -60,6 +60,30 @@ class IrStats(C.Structure):
                 ("fnorm", C.c_double), ("history", C.c_double * 64)]
 
 
+class KappaParams(C.Structure):
+    _fields_ = [("power_maxit", C.c_int32), ("power_tol", C.c_double),
+                ("inverse_maxit", C.c_int32), ("inverse_tol", C.c_double),
+                ("inner_rtol", C.c_double), ("inner_maxit", C.c_int32)]
+
+
+class KappaStats(C.Structure):
+    _fields_ = [("lambda_max", C.c_double), ("lambda_min", C.c_double), ("kappa", C.c_double),
+                ("power_steps", C.c_int32), ("inverse_steps", C.c_int32),
+                ("inner_iterations", C.c_int32), ("inner_capped", C.c_int32)]
+
+
+class ProtocolParams(C.Structure):
+    _fields_ = [("n_iter", C.c_int32), ("rmin0", C.c_double), ("eta", C.c_double),
+                ("restart_factor", C.c_double), ("select_min_penal", C.c_double),
+                ("select_max_gray", C.c_double)]
+
+
+class ProtocolStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("selected_iteration", C.c_int32),
+                ("selected_compliance", C.c_double), ("restarts", C.c_int32),
+                ("cg_iterations", C.c_int32)]
+
+
 class LearnedStats(C.Structure):
     _fields_ = [("outer_iterations", C.c_int32), ("inner_iterations", C.c_int32),
                 ("fp64_iterations", C.c_int32), ("nn_calls", C.c_int32),
@@ -96,6 +120,14 @@ SIGNATURES = {
     "mfto_set_kv_variant": (C.c_int32, [_P, C.c_int32]),
     "mfto_set_cg_engine": (C.c_int32, [_P, C.c_int32]),
     "mfto_set_ir_mode": (C.c_int32, [_P, C.c_int32]),
+    "mfto_default_kappa_params": (None, [C.POINTER(KappaParams)]),
+    "mfto_set_projection": (C.c_int32, [_P, C.c_double, C.c_double]),
+    "mfto_project": (C.c_int32, [_P, _P, _P, _P]),
+    "mfto_default_protocol_params": (None, [C.POINTER(ProtocolParams)]),
+    "mfto_simp_protocol": (C.c_int32, [_P, _P, _P, _P, _P, C.POINTER(ProtocolParams), _P, _P,
+                                       _P, C.POINTER(ProtocolStats)]),
+    "mfto_kappa": (C.c_int32, [_P, _P, _P, _P, _P, C.POINTER(KappaParams), C.POINTER(KappaStats)]),
+    "mfto_set_kv_shape": (C.c_int32, [_P, C.c_int32, C.c_int32]),
     "mfto_kv_autotune": (C.c_int32, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_float)]),
     "mfto_cg_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -178,6 +210,22 @@ def _check(fn, code, handle=None):
             raw = lib().mfto_last_error(handle)
             msg = raw.decode() if raw else ""
         raise MftoError(fn, code, msg)
+
+
+def default_protocol_params(**kw) -> ProtocolParams:
+    p = ProtocolParams()
+    lib().mfto_default_protocol_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def default_kappa_params(**kw) -> KappaParams:
+    p = KappaParams()
+    lib().mfto_default_kappa_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
 
 
 def default_params(**kw) -> Params:
@@ -337,14 +385,59 @@ class Handle:
         0 = per-iteration kernels replayed from a CUDA graph."""
         _check("mfto_set_cg_engine", lib().mfto_set_cg_engine(self._h, engine), self._h)
 
+    def set_projection(self, beta: float, eta: float = 0.5):
+        _check("mfto_set_projection", lib().mfto_set_projection(self._h, beta, eta), self._h)
+
+    def project(self, rho_bar, rho_phys=None, dc=None):
+        import torch
+        _check("mfto_project", lib().mfto_project(
+            self._h, _ptr(rho_bar, torch.float64, self.n_elem, "rho_bar"),
+            _ptr(rho_phys, torch.float64, self.n_elem, "rho_phys") if rho_phys is not None else None,
+            _ptr(dc, torch.float64, self.n_elem, "dc") if dc is not None else None), self._h)
+
+    def simp_protocol(self, rho, u, f, rho_selected, params):
+        """The SIMP-120 continuation protocol; returns (stats, compliance,
+        grayness, restarted) with the per-iteration host histories."""
+        import torch
+        n = params.n_iter
+        comp = np.zeros(n)
+        gray = np.zeros(n)
+        rest = np.zeros(n, dtype=np.int32)
+        st = ProtocolStats()
+        _check("mfto_simp_protocol", lib().mfto_simp_protocol(
+            self._h, _ptr(rho, torch.float64, self.n_elem, "rho"),
+            _ptr(u, torch.float64, self.n_dof, "u"), _ptr(f, torch.float64, self.n_dof, "f"),
+            _ptr(rho_selected, torch.float64, self.n_elem, "rho_selected"), C.byref(params),
+            comp.ctypes.data, gray.ctypes.data, rest.ctypes.data, C.byref(st)), self._h)
+        return st, comp, gray, rest
+
+    def kappa(self, E, v_power, v_inverse, params=None) -> KappaStats:
+        """Condition-number estimate of K(E) on the free DOFs; v_power and
+        v_inverse (FP64 device vectors, seeded by the caller) are overwritten
+        with the final unit iterates."""
+        import torch
+        st = KappaStats()
+        work = torch.empty(self.n_dof, dtype=torch.float64, device=E.device)
+        prm = params if params is not None else default_kappa_params()
+        _check("mfto_kappa", lib().mfto_kappa(
+            self._h, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(v_power, torch.float64, self.n_dof, "v_power"),
+            _ptr(v_inverse, torch.float64, self.n_dof, "v_inverse"),
+            _ptr(work, torch.float64, self.n_dof, "work"), C.byref(prm), C.byref(st)), self._h)
+        return st
+
     def set_ir_mode(self, mode: int):
         """IR_RESTART (0): each inner CG starts with p = z; IR_CONTINUE (1): it
         keeps the previous search direction (reliable updating)."""
         _check("mfto_set_ir_mode", lib().mfto_set_ir_mode(self._h, mode), self._h)
 
+    def set_kv_shape(self, nzc: int, kind: int):
+        """Pin the FP32 column K.v launch shape (nzc 0 = automatic, kind 0 or 1)."""
+        _check("mfto_set_kv_shape", lib().mfto_set_kv_shape(self._h, nzc, kind), self._h)
+
     def kv_autotune(self):
-        """Pick the fastest z-chunk and register budget of the FP32 column K.v;
-        returns (nzc, ctas_per_sm, us)."""
+        """Pick the fastest z-chunk and kernel kind of the FP32 column K.v;
+        returns (nzc, kind, us)."""
         n, mb, us = C.c_int32(), C.c_int32(), C.c_float()
         _check("mfto_kv_autotune", lib().mfto_kv_autotune(self._h, C.byref(n), C.byref(mb),
                                                           C.byref(us)), self._h)
