@@ -621,6 +621,80 @@ def learned_run(args):
     h.close()
 
 
+def kappa_run(args):
+    """kappa(K) on the free DOFs by power and inverse iteration (the paper's
+    caps and tolerances, start vectors from seeds 42 and 123) for the paper's
+    cantilever sizes at uniform density 0.5, p = 3 and 5; one JSON line each,
+    with the paper's printed estimate for the size."""
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+    paper = {64000: 6.1e5, 216000: 1.3e6, 512000: 2.3e6}
+    for dims in ((80, 40, 20), (120, 60, 30), (160, 80, 40)):
+        P = W.cantilever_point(*dims)
+        m = P.mesh
+        with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
+            for penal in (3.0, 5.0):
+                rho = torch.full((m.n_elem,), 0.5, dtype=torch.float64, device=dev)
+                E = torch.empty_like(rho)
+                h.set_params(mfto.default_params(penal=penal))
+                h.simp_modulus(rho, E)
+                vp = torch.tensor(W.vec_random(m.n_dof, seed=42), device=dev)
+                vi = torch.tensor(W.vec_random(m.n_dof, seed=123), device=dev)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                st = h.kappa(E, vp, vi)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t
+                print(json.dumps({
+                    "case": f"cantilever_{dims[0]}x{dims[1]}x{dims[2]}", "elements": m.n_elem,
+                    "penal": penal, "lambda_max": st.lambda_max, "lambda_min": st.lambda_min,
+                    "kappa": st.kappa, "paper_kappa": paper[m.n_elem],
+                    "power_steps": st.power_steps, "inverse_steps": st.inverse_steps,
+                    "inner_iterations": st.inner_iterations, "inner_capped": st.inner_capped,
+                    "seconds": dt}), flush=True)
+
+
+def protocol_run(args):
+    """The SIMP-120 continuation protocol (projection, four phases, restarts,
+    selected iterate) on the paper's point-load cantilever of --workload's
+    size, with the mixed solve and with plain FP64 Jacobi-PCG: wall time,
+    selected compliance and iteration counts, one JSON line each."""
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+    base = W.WORKLOADS[args.workload]()
+    m0 = base.mesh
+    P = W.cantilever_point(m0.nelx, m0.nely, m0.nelz)
+    m = P.mesh
+    for solver in ("mixed", "f64"):
+        params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
+        with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params) as h:
+            if solver == "mixed":
+                h.set_solver(mfto.FORM_F32, args.inner_tol)
+                h.set_ir_mode(IR_MODES[args.ir_mode])
+                tuned = h.kv_autotune()
+            rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
+            u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+            f = torch.tensor(P.f, device=dev)
+            sel = torch.zeros_like(rho)
+            pp = mfto.default_protocol_params(n_iter=args.protocol_iters, rmin0=P.rmin)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st, comp, gray, rest = h.simp_protocol(rho, u, f, sel, pp)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            print(json.dumps({
+                "case": f"cantilever_point_{m.nelx}x{m.nely}x{m.nelz}", "elements": m.n_elem,
+                "solver": solver, "iterations": st.iterations, "seconds": dt,
+                "ms_per_iteration": 1e3 * dt / st.iterations,
+                "solver_iterations": st.cg_iterations, "restarts": st.restarts,
+                "selected_iteration": st.selected_iteration,
+                "selected_compliance": st.selected_compliance,
+                "final_compliance": float(comp[-1]), "final_grayness": float(gray[-1])}),
+                flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -629,7 +703,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-maxit", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "pcg", "compare", "learned"])
+    ap.add_argument("--mode", default="bench",
+                    choices=["bench", "profile", "pcg", "compare", "learned", "kappa", "protocol"])
+    ap.add_argument("--protocol-iters", type=int, default=120)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--form", default="mixed", choices=["f64", "mixed"],
                     help="f64: plain FP64 Jacobi-PCG; mixed: FP64 iterative refinement "
@@ -657,6 +733,12 @@ def main():
         return
     if args.mode == "learned":
         learned_run(args)
+        return
+    if args.mode == "kappa":
+        kappa_run(args)
+        return
+    if args.mode == "protocol":
+        protocol_run(args)
         return
     if args.mode != "bench":
         profile_run(args)
