@@ -89,7 +89,7 @@ struct mfto_handle {
   ModeCoef<double> mc64;    // mode-space element operator (kv_tile.cuh)
   ModeCoef<float> mc32;
   int kv_variant;           // 0: tiled mode-space kernel, 1: node-centric dense KE
-  int cg_engine;            // FP32 inner CG: 0 graph of per-iteration kernels, 1 persistent
+  int cg_engine;            // FP32 inner CG: 0 two kernels per iteration, 1 persistent
   int persist_grid;         // CTAs of the persistent CG launch (0: unavailable)
   int persist_tiling[4];    // its column tiling: tiles in x, y, z and node layers per chunk
   int occ_kv32, occ_pcg32;  // resident CTAs per SM of the FP32 block kernels

@@ -128,7 +128,7 @@ mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const doub
     // p0 first.
     rz_prev = 0.0;
     if (h->ir_mode == MFTO_IR_CONTINUE && fin.it >= 1 && fin.beta > 0.0 &&
-        isfinite(fin.rz / fin.beta)) {
+               isfinite(fin.rz / fin.beta)) {
       if (fin.it & 1)
         MFTO_CUDA(h, cudaMemcpyAsync(h->d_p0_32, h->d_p1_32, sizeof(float) * h->n_dof,
                                      cudaMemcpyDeviceToDevice, h->stream));

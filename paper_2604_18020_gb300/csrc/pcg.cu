@@ -318,6 +318,8 @@ template <typename T>
 mfto_status pcg_start(mfto_handle* h, const PcgVecs<T>& v, const T* rhs, const T* Ku, double rtol,
                       int maxit, double rz_prev) {
   const int nb_dof = reduction_blocks(h->n_dof, MFTO_BLOCK);
+  // the first iteration reads its previous direction from p0: zero unless a
+  // direction is continued
   if (!(rz_prev > 0.0)) {
     rz_prev = 0.0;
     MFTO_CUDA(h, cudaMemsetAsync(v.p0, 0, sizeof(T) * h->n_dof, h->stream));
