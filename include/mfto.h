@@ -285,8 +285,9 @@ mfto_status mfto_kv_multi(mfto_handle* h, mfto_form form, const void* d_E, const
 /* Mixed-precision solve of K(E) U_r = F_r for nrhs load cases (nrhs <=
  * max_rhs of mfto_create): the refinement of mfto_ir_solve for every case
  * (FP64 residuals, norms and accumulation), around one inner FP32 CG that
- * advances all live cases together (one multi-RHS K.V and one vector update
- * per iteration, per-case scalars and stopping).  d_E FP64 [n_elem];
+ * advances all live cases together (one launch of the K.v for all cases and
+ * one vector update per iteration, a grid row per case, per-case scalars and
+ * stopping; mfto_set_ir_mode applies per case).  d_E FP64 [n_elem];
  * d_F, d_U FP64 [nrhs][n_dof] (d_U: initial guesses in, solutions out);
  * st: nrhs entries.  Synchronises the stream. */
 mfto_status mfto_ir_solve_multi(mfto_handle* h, double inner_tol, const double* d_E,

@@ -52,6 +52,10 @@ struct MultiScalars {
   int32_t done[MFTO_MAX_RHS], status[MFTO_MAX_RHS], it[MFTO_MAX_RHS];
   int32_t all_done, maxit, nrhs;
   unsigned int ticket_a, ticket_b, ticket_c;
+  // column kernels (one grid row per case): per-case tickets, and the count
+  // of cases done (the last case to finish raises all_done)
+  unsigned int ticket_kv[MFTO_MAX_RHS], ticket_up[MFTO_MAX_RHS];
+  int32_t ndone;
 };
 
 struct MiscScalars {
@@ -341,6 +345,54 @@ __device__ __forceinline__ bool last_block_reduce_df(const DFloat (&v)[K], doubl
   float2* pf = reinterpret_cast<float2*>(partials);     // one pair per double slot
   const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
   const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  DFloat bs[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) bs[c] = block_sum_df(v[c], shf);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) pf[c * MFTO_RED_SLOTS + bid] = make_float2(bs[c].hi, bs[c].lo);
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    s_last = (t == nb - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      DFloat t{0.f, 0.f};
+      for (int b = threadIdx.x; b < (int)nb; b += 32) {
+        const float2 x = __ldcg(&pf[c * MFTO_RED_SLOTS + b]);
+        t = df_add(t, DFloat{x.x, x.y});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        DFloat w;
+        w.hi = __shfl_down_sync(0xffffffffu, t.hi, o);
+        w.lo = __shfl_down_sync(0xffffffffu, t.lo, o);
+        t = df_add(t, w);
+      }
+      if (threadIdx.x == 0) sh[32 + c] = (double)t.hi + (double)t.lo;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < K; ++c) out[c] = sh[32 + c];
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// last_block_reduce_df over the blocks of one grid row (blockIdx.y fixed):
+// bid = blockIdx.x among gridDim.x blocks, the row's own partial rows and
+// ticket.  Used where each grid row is an independent problem (a load case).
+template <int K>
+__device__ __forceinline__ bool row_reduce_df(const DFloat (&v)[K], double* partials,
+                                              unsigned int* ticket, double* out, double* sh) {
+  __shared__ bool s_last;
+  float2* shf = reinterpret_cast<float2*>(sh);
+  float2* pf = reinterpret_cast<float2*>(partials);
+  const unsigned int nb = gridDim.x, bid = blockIdx.x;
   DFloat bs[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) bs[c] = block_sum_df(v[c], shf);

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "kv_column.cuh"
 #include "kv_tile.cuh"
 
 namespace {
@@ -241,6 +242,104 @@ pcg_update_multi(float* __restrict__ U, const float* __restrict__ P, const float
   }
 }
 
+// The same two CG steps with the column K.v (kv_column.cuh) and 16-byte
+// vector updates: grid row blockIdx.y is load case r, so every case has its
+// own tiles, partial rows (2r, 2r + 1 of the partial buffers) and tickets,
+// and a converged case's blocks return at entry.  The last case to finish
+// raises all_done.
+__device__ __forceinline__ void multi_case_done(MultiScalars* s) {
+  if (atomicAdd(&s->ndone, 1) + 1 >= s->nrhs) s->all_done = 1;
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(MFTO_BLOCK, MINB)
+pcg_kv_multi_col(const float* __restrict__ E, const float* __restrict__ Z,
+                 const float* __restrict__ P0, float* __restrict__ P1, float* __restrict__ Q,
+                 const uint8_t* __restrict__ fixed, ModeCoef<float> K, Grid g, ColTiling tl,
+                 int n_dof, MultiScalars* s, double* partials) {
+  const int r = blockIdx.y;
+  if (*(volatile int32_t*)&s->done[r]) return;   // uniform over the case's blocks
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sh[64];
+  const float beta = scalar_as_f32(&s->beta[r]);
+  const size_t o = (size_t)r * n_dof;
+  DotAcc<float> acc;
+  acc.s = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{Z + o, P0 + o, beta},
+                         ColPcg{P1 + o, Q + o}, reinterpret_cast<float*>(smem_raw));
+  const DFloat w[1] = {acc.finish_df()};
+  double tot[1];
+  if (row_reduce_df<1>(w, partials + (size_t)2 * r * MFTO_RED_SLOTS, &s->ticket_kv[r], tot, sh) &&
+      threadIdx.x == 0) {
+    s->pq[r] = tot[0];
+    if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+      s->done[r] = 1;
+      s->status[r] = MFTO_BREAKDOWN;
+      s->alpha[r] = 0.0;
+      multi_case_done(s);
+    } else {
+      s->alpha[r] = s->rz[r] / tot[0];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(MFTO_BLOCK)
+pcg_update_multi_col(float* __restrict__ U, const float* __restrict__ P,
+                     const float* __restrict__ Q, float* __restrict__ R, float* __restrict__ Z,
+                     const float* __restrict__ dinv, int n_dof, MultiScalars* s,
+                     double* partials) {
+  const int r = blockIdx.y;
+  if (*(volatile int32_t*)&s->done[r]) return;
+  __shared__ double sh[64];
+  const float alpha = scalar_as_f32(&s->alpha[r]);
+  const size_t o = (size_t)r * n_dof;
+  DotAcc<float> d0, d1;
+  // groups of 4 consecutive DOFs (a case's vectors start at r n_dof, which
+  // need not be 16-byte aligned, so scalar accesses); each group's products
+  // are summed in FP32 before the double-float accumulation
+  float* u = U + o;
+  const float* p = P + o;
+  const float* q = Q + o;
+  float* rv = R + o;
+  float* z = Z + o;
+  for (int g4 = blockIdx.x * blockDim.x + threadIdx.x; 4 * g4 < n_dof;
+       g4 += gridDim.x * blockDim.x) {
+    float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = 4 * g4 + c;
+      if (i < n_dof) {
+        u[i] += alpha * p[i];
+        const float ri = rv[i] - alpha * q[i];
+        const float zi = ri * dinv[i];
+        rv[i] = ri;
+        z[i] = zi;
+        t0 = fmaf(ri, zi, t0);
+        t1 = fmaf(ri, ri, t1);
+      }
+    }
+    d0.add(t0);
+    d1.add(t1);
+  }
+  const DFloat w[2] = {d0.finish_df(), d1.finish_df()};
+  double tot[2];
+  if (row_reduce_df<2>(w, partials + (size_t)2 * r * MFTO_RED_SLOTS, &s->ticket_up[r], tot, sh) &&
+      threadIdx.x == 0) {
+    s->it[r] += 1;
+    s->rr[r] = tot[1];
+    s->beta[r] = tot[0] / s->rz[r];
+    s->rz[r] = tot[0];
+    int fin = 1;
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) s->status[r] = MFTO_BREAKDOWN;
+    else if (tot[1] <= s->rtol2ff[r]) s->status[r] = MFTO_OK;
+    else if (s->it[r] >= s->maxit) s->status[r] = MFTO_NOT_CONVERGED;
+    else fin = 0;
+    if (fin) {
+      s->done[r] = 1;
+      multi_case_done(s);
+    }
+  }
+}
+
 // Outer FP64 residual of every case: R = F - KU; r.r, f.f per case; the FP32
 // right-hand side of the inner solve (zero for cases marked converged).
 __global__ void __launch_bounds__(MFTO_BLOCK)
@@ -269,10 +368,16 @@ ir_residual_multi(const double* __restrict__ F, const double* __restrict__ KU,
   }
 }
 
+// r.z of the direction each case continues with (0: a new start, p = z)
+struct RzPrev {
+  double v[MFTO_MAX_RHS];
+};
+
 // Inner solve start for every case: r = rhs (in place), z = r / d, sums.
 __global__ void __launch_bounds__(MFTO_BLOCK)
 pcg_init_multi(float* R, float* __restrict__ Z, const float* __restrict__ dinv, int n_dof,
-               int nrhs, double rtol, int maxit, MultiScalars* s, double* partials) {
+               int nrhs, double rtol, int maxit, RzPrev rz_prev, MultiScalars* s,
+               double* partials) {
   __shared__ double sh[64];
   DotAcc<float> d[2 * MFTO_MAX_RHS];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_dof; i += gridDim.x * blockDim.x) {
@@ -301,12 +406,15 @@ pcg_init_multi(float* R, float* __restrict__ Z, const float* __restrict__ dinv, 
       s->ff[r] = s->rr[r];                       // the inner right-hand side is r0
       s->rtol2ff[r] = rtol * rtol * s->ff[r];
       s->alpha[r] = 0.0;
-      s->beta[r] = 0.0;
+      s->beta[r] = (live && rz_prev.v[r] > 0.0) ? s->rz[r] / rz_prev.v[r] : 0.0;
       s->it[r] = 0;
       s->status[r] = MFTO_OK;
       s->done[r] = (!live || s->ff[r] == 0.0) ? 1 : 0;
       all &= s->done[r];
     }
+    int nd = 0;
+    for (int r = 0; r < nrhs; ++r) nd += s->done[r];
+    s->ndone = nd;
     s->nrhs = nrhs;
     s->maxit = maxit;
     s->all_done = all;
@@ -354,6 +462,10 @@ mfto_status multi_init(mfto_handle* h) {
                                                              MFTO_BLOCK, block_smem(4)));
   for (int i = 0; i < 3; ++i)
     if (h->occ_multi[i] < 1) h->occ_multi[i] = 1;
+  MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_multi_col<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ColShape::smem_bytes));
+  MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_multi_col<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ColShape::smem_bytes));
   return MFTO_OK;
 }
 
@@ -390,22 +502,43 @@ extern "C" mfto_status mfto_kv_multi(mfto_handle* h, mfto_form form, const void*
 struct MultiGraph {
   const void* key = nullptr;
   int chunk = 0;
+  int nrhs = 0, variant = 0, kind = 0, nzc = 0;
   cudaGraphExec_t exec = nullptr;
 };
 
-static mfto_status multi_chunk(mfto_handle* h, cudaStream_t st, int chunk) {
+static mfto_status multi_chunk(mfto_handle* h, cudaStream_t st, int chunk, int nrhs) {
   const Grid g = make_grid(h->mesh);
   int nb_node = (int)((h->n_node + MFTO_BLOCK - 1) / MFTO_BLOCK);
   if (nb_node > MFTO_RED_MAX_BLOCKS) nb_node = MFTO_RED_MAX_BLOCKS;
+  // column kernels: one grid row per case, the K.v tiling of a single case
+  int grid = 0;
+  const ColTiling tl = col_launch_tiling(h, h->occ_col[h->col_kind], &grid);
+  int64_t nb_up = ((int64_t)h->n_dof / 4 + MFTO_BLOCK) / MFTO_BLOCK;
+  if (nb_up > 2 * (int64_t)h->num_sms) nb_up = 2 * (int64_t)h->num_sms;
   for (int it = 0; it < chunk; ++it) {
     float* p_old = (it & 1) ? h->m_p1 : h->m_p0;
     float* p_new = (it & 1) ? h->m_p0 : h->m_p1;
-    pcg_kv_multi<<<multi_grid(h, h->occ_multi[2]), MFTO_BLOCK, block_smem(4), st>>>(
-        h->d_E32, h->m_z32, p_old, p_new, h->m_q32, h->d_fixed, h->mc32, g, (int)h->n_dof,
-        h->m_pcg, h->d_partials);
-    pcg_update_multi<<<nb_node, MFTO_BLOCK, 0, st>>>(h->m_e32, p_new, h->m_q32, h->m_r32,
-                                                     h->m_z32, h->d_dinv32, (int)h->n_node,
-                                                     (int)h->n_dof, h->m_pcg, h->d_partials2);
+    if (h->kv_variant == 0) {
+      const dim3 gk((unsigned)grid, (unsigned)nrhs);
+      if (h->col_kind == 1)
+        pcg_kv_multi_col<3><<<gk, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+            h->d_E32, h->m_z32, p_old, p_new, h->m_q32, h->d_fixed, h->mc32, g, tl,
+            (int)h->n_dof, h->m_pcg, h->d_partials);
+      else
+        pcg_kv_multi_col<2><<<gk, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+            h->d_E32, h->m_z32, p_old, p_new, h->m_q32, h->d_fixed, h->mc32, g, tl,
+            (int)h->n_dof, h->m_pcg, h->d_partials);
+      pcg_update_multi_col<<<dim3((unsigned)nb_up, (unsigned)nrhs), MFTO_BLOCK, 0, st>>>(
+          h->m_e32, p_new, h->m_q32, h->m_r32, h->m_z32, h->d_dinv32, (int)h->n_dof, h->m_pcg,
+          h->d_partials2);
+    } else {
+      pcg_kv_multi<<<multi_grid(h, h->occ_multi[2]), MFTO_BLOCK, block_smem(4), st>>>(
+          h->d_E32, h->m_z32, p_old, p_new, h->m_q32, h->d_fixed, h->mc32, g, (int)h->n_dof,
+          h->m_pcg, h->d_partials);
+      pcg_update_multi<<<nb_node, MFTO_BLOCK, 0, st>>>(h->m_e32, p_new, h->m_q32, h->m_r32,
+                                                       h->m_z32, h->d_dinv32, (int)h->n_node,
+                                                       (int)h->n_dof, h->m_pcg, h->d_partials2);
+    }
   }
   MFTO_LAUNCH_CHECK(h);
   return MFTO_OK;
@@ -420,9 +553,10 @@ void multi_graph_release(mfto_handle* h) {
   h->m_graph = nullptr;
 }
 
-static mfto_status multi_graph(mfto_handle* h, MultiGraph** out) {
+static mfto_status multi_graph(mfto_handle* h, int nrhs, MultiGraph** out) {
   MultiGraph* mg = reinterpret_cast<MultiGraph*>(h->m_graph);
-  if (mg && mg->key == h->d_E32 && mg->chunk == h->p.check_every) {
+  if (mg && mg->key == h->d_E32 && mg->chunk == h->p.check_every && mg->nrhs == nrhs &&
+      mg->variant == h->kv_variant && mg->kind == h->col_kind && mg->nzc == h->col_nzc) {
     *out = mg;
     return MFTO_OK;
   }
@@ -430,6 +564,10 @@ static mfto_status multi_graph(mfto_handle* h, MultiGraph** out) {
   mg = new MultiGraph();
   mg->key = h->d_E32;
   mg->chunk = h->p.check_every;
+  mg->nrhs = nrhs;
+  mg->variant = h->kv_variant;
+  mg->kind = h->col_kind;
+  mg->nzc = h->col_nzc;
   if (!h->cap_stream &&
       cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete mg;
@@ -437,7 +575,7 @@ static mfto_status multi_graph(mfto_handle* h, MultiGraph** out) {
   }
   cudaGraph_t graph = nullptr;
   MFTO_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  mfto_status s = multi_chunk(h, h->cap_stream, mg->chunk);
+  mfto_status s = multi_chunk(h, h->cap_stream, mg->chunk, nrhs);
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
   if (s != MFTO_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -478,6 +616,8 @@ extern "C" mfto_status mfto_ir_solve_multi(mfto_handle* h, double inner_tol, con
   if (s != MFTO_OK) return s;
   double prev[MFTO_MAX_RHS] = {0};
   int stalls[MFTO_MAX_RHS] = {0};
+  RzPrev rzp;                 // continued directions (MFTO_IR_CONTINUE), per case
+  for (int r = 0; r < MFTO_MAX_RHS; ++r) rzp.v[r] = 0.0;
   unsigned int converged = 0, stopped = 0;
   double* d_out = h->m_out;   // per-case r.r, f.f of the outer residual
   double out[2 * MFTO_MAX_RHS];
@@ -522,16 +662,21 @@ extern "C" mfto_status mfto_ir_solve_multi(mfto_handle* h, double inner_tol, con
     for (int r = 0; r < nrhs; ++r)
       if ((stopped >> r) & 1u)
         MFTO_CUDA(h, cudaMemsetAsync(h->m_r32 + (size_t)r * n, 0, sizeof(float) * n, h->stream));
-    // inner solve of every live case from e = 0
+    // inner solve of every live case from e = 0; a case continuing its
+    // direction keeps it in p0, the others start from p = z
     MFTO_CUDA(h, cudaMemsetAsync(h->m_e32, 0, sizeof(float) * total, h->stream));
-    MFTO_CUDA(h, cudaMemsetAsync(h->m_p0, 0, sizeof(float) * total, h->stream));
+    for (int r = 0; r < nrhs; ++r) {
+      if (((converged | stopped) >> r) & 1u) rzp.v[r] = 0.0;
+      if (!(rzp.v[r] > 0.0))
+        MFTO_CUDA(h, cudaMemsetAsync(h->m_p0 + (size_t)r * n, 0, sizeof(float) * n, h->stream));
+    }
     h->launches++;
     pcg_init_multi<<<nb, MFTO_BLOCK, 0, h->stream>>>(h->m_r32, h->m_z32, h->d_dinv32, n, nrhs,
-                                                     inner_tol, h->inner_maxit, h->m_pcg,
+                                                     inner_tol, h->inner_maxit, rzp, h->m_pcg,
                                                      h->d_partials);
     MFTO_LAUNCH_CHECK(h);
     MultiGraph* mg = nullptr;
-    s = multi_graph(h, &mg);
+    s = multi_graph(h, nrhs, &mg);
     if (s != MFTO_OK) return s;
     for (;;) {
       MFTO_CUDA(h, cudaMemcpyAsync(h->h_mpcg, h->m_pcg, sizeof(MultiScalars),
@@ -543,8 +688,19 @@ extern "C" mfto_status mfto_ir_solve_multi(mfto_handle* h, double inner_tol, con
     }
     for (int r = 0; r < nrhs; ++r) {
       if (((converged | stopped) >> r) & 1u) continue;
-      st[r].inner_iterations += h->h_mpcg->it[r];
+      const MultiScalars& fin = *h->h_mpcg;
+      st[r].inner_iterations += fin.it[r];
       st[r].outer_iterations++;
+      // continued direction: iteration j wrote its direction into p1 (j even)
+      // or p0 (j odd); the next inner solve reads p0 first
+      rzp.v[r] = 0.0;
+      if (h->ir_mode == MFTO_IR_CONTINUE && fin.it[r] >= 1 && fin.status[r] != MFTO_BREAKDOWN &&
+          fin.beta[r] > 0.0 && isfinite(fin.rz[r] / fin.beta[r])) {
+        if (fin.it[r] & 1)
+          MFTO_CUDA(h, cudaMemcpyAsync(h->m_p0 + (size_t)r * n, h->m_p1 + (size_t)r * n,
+                                       sizeof(float) * n, cudaMemcpyDeviceToDevice, h->stream));
+        rzp.v[r] = fin.rz[r] / fin.beta[r];
+      }
     }
     h->launches++;
     ir_accumulate_multi<<<nb, MFTO_BLOCK, 0, h->stream>>>(U, h->m_e32, total);

@@ -35,7 +35,8 @@ def test_kv_multi(cuda, form, shape, nrhs):
         assert np.abs(got[r] - ref).max() / np.abs(ref).max() <= tol
 
 
-def test_ir_solve_multi_8_load_cases(cuda):
+@pytest.mark.parametrize("mode,inner_tol", [("restart", 1e-2), ("continue", 1e-1)])
+def test_ir_solve_multi_8_load_cases(cuda, mode, inner_tol):
     import torch
     from paper_2604_18020_gb300 import mfto
     P = W.multi_rhs_cantilever(24, 12, 12, nrhs=8, seed=3)
@@ -47,9 +48,11 @@ def test_ir_solve_multi_8_load_cases(cuda):
     d = fem.jacobi_diag(KE, E, edof, fd)
     with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed,
                      params=mfto.default_params(max_rhs=8)) as h:
+        h.set_ir_mode(mfto.IR_CONTINUE if mode == "continue" else mfto.IR_RESTART)
         U = torch.zeros(8 * m.n_dof, dtype=torch.float64, device=cuda)
         sts = h.ir_solve_multi(torch.tensor(E, device=cuda),
-                               torch.tensor(P.f.reshape(-1), device=cuda), U, 8, inner_tol=1e-2)
+                               torch.tensor(P.f.reshape(-1), device=cuda), U, 8,
+                               inner_tol=inner_tol)
         got = U.cpu().numpy().reshape(8, -1)
     for r in range(8):
         assert sts[r].status == mfto.OK
@@ -78,3 +81,36 @@ def test_ir_solve_multi_matches_single(cuda):
             assert s1.status == sts[r].status == mfto.OK
             assert torch.allclose(u, U[r * m.n_dof:(r + 1) * m.n_dof], rtol=0,
                                   atol=1e-7 * float(u.abs().max()))
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_ir_solve_multi_ragged_and_variants(cuda, variant):
+    """Odd n_dof (case vectors not 16-byte aligned) and both K.v kernels of
+    the inner CG (column kernel, block kernel): every case meets the FP64
+    tolerance; a case with a zero load stays zero."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.multi_rhs_cantilever(12, 6, 4, nrhs=5, seed=6)
+    m = P.mesh
+    assert m.n_dof % 4 != 0
+    F = P.f.copy()
+    F[2] = 0.0
+    edof = fem.edof_table_fast(m.nelx, m.nely, m.nelz)
+    fd = fem.dof_mask(P.fixed)
+    KE = fem.ke_exact()
+    E = fem.simp_modulus(W.rho_random(m, seed=54, lo=0.05, hi=1.0), 3.0)
+    with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed,
+                     params=mfto.default_params(max_rhs=8)) as h:
+        h.set_kv_variant(variant)
+        h.set_ir_mode(mfto.IR_CONTINUE)
+        U = torch.zeros(5 * m.n_dof, dtype=torch.float64, device=cuda)
+        sts = h.ir_solve_multi(torch.tensor(E, device=cuda), torch.tensor(F.reshape(-1), device=cuda),
+                               U, 5, inner_tol=1e-1)
+        got = U.cpu().numpy().reshape(5, -1)
+    for r in range(5):
+        assert sts[r].status == mfto.OK
+        if r == 2:
+            assert np.abs(got[r]).max() == 0.0
+            continue
+        true_rel = np.linalg.norm(F[r] - fem.kv(KE, E, edof, got[r], fd)) / np.linalg.norm(F[r])
+        assert true_rel <= 1.5e-8
