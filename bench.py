@@ -717,6 +717,76 @@ def protocol_run(args):
                 flush=True)
 
 
+def hard_run(args):
+    """The paper's hard problems (MBB, bridge, 150 x 50 x 25 = 187,500
+    elements): cold-start FEA solves at the uniform initial density (p = 3;
+    mean of 5 after one warm-up) and the 60-iteration cold-start SIMP runs of
+    the protocol, each with plain FP64 Jacobi-PCG and the mixed solve; one
+    JSON line per problem and mode."""
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+    for name in ("mbb_150x50x25", "bridge_150x50x25"):
+        P = W.WORKLOADS[name]()
+        m = P.mesh
+        f = torch.tensor(P.f, device=dev)
+        res = {}
+        for solver in ("f64", "mixed"):
+            params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8, maxit=20000)
+            with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params) as h:
+                if solver == "mixed":
+                    h.set_solver(mfto.FORM_F32, args.inner_tol, 20000, 80)
+                    h.set_ir_mode(IR_MODES[args.ir_mode])
+                    h.kv_autotune()
+                rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
+                E = torch.empty_like(rho)
+                rho_phys = torch.empty_like(rho)
+                h.filter(rho, rho_phys)
+                h.simp_modulus(rho_phys, E)
+                u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+                times, its, rel = [], [], []
+                for rep in range(6):
+                    u.zero_()
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    if solver == "f64":
+                        st = h.pcg(E, f, u)
+                        it = st.iterations
+                    else:
+                        st = h.ir_solve(E, f, u, inner_tol=args.inner_tol)
+                        it = st.inner_iterations
+                    torch.cuda.synchronize()
+                    if rep:
+                        times.append(time.perf_counter() - t)
+                        its.append(it)
+                        rel.append(st.rel_residual)
+                c_fea = float((f * u).sum())
+                sel = torch.zeros_like(rho)
+                rho.fill_(P.volfrac)
+                u.zero_()
+                pp = mfto.default_protocol_params(n_iter=60, rmin0=P.rmin, cold_start=1)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                pst, comp, gray, rest = h.simp_protocol(rho, u, f, sel, pp)
+                torch.cuda.synchronize()
+                t60 = time.perf_counter() - t
+                res[solver] = {"fea_ms": 1e3 * sum(times) / len(times), "fea_iterations": its[-1],
+                               "fea_rel_residual": rel[-1], "fea_compliance": c_fea,
+                               "simp60_s": t60, "simp60_solver_iterations": pst.cg_iterations,
+                               "simp60_selected_iteration": pst.selected_iteration,
+                               "simp60_selected_compliance": pst.selected_compliance,
+                               "simp60_restarts": pst.restarts}
+        a, b = res["f64"], res["mixed"]
+        print(json.dumps({
+            "case": name, "elements": m.n_elem, "f64": a, "mixed": b,
+            "fea_speedup": a["fea_ms"] / b["fea_ms"], "simp60_speedup": a["simp60_s"] / b["simp60_s"],
+            "fea_compliance_rel_diff": abs(b["fea_compliance"] - a["fea_compliance"]) / abs(a["fea_compliance"]),
+            "simp60_selected_compliance_rel_diff":
+                abs(b["simp60_selected_compliance"] - a["simp60_selected_compliance"])
+                / abs(a["simp60_selected_compliance"]) if a["simp60_selected_iteration"] else None}),
+            flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -726,7 +796,8 @@ def main():
     ap.add_argument("--cpu-maxit", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench",
-                    choices=["bench", "profile", "pcg", "compare", "learned", "kappa", "protocol"])
+                    choices=["bench", "profile", "pcg", "compare", "learned", "kappa", "protocol",
+                             "hard"])
     ap.add_argument("--protocol-iters", type=int, default=120)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--form", default="mixed", choices=["f64", "mixed"],
@@ -761,6 +832,9 @@ def main():
         return
     if args.mode == "protocol":
         protocol_run(args)
+        return
+    if args.mode == "hard":
+        hard_run(args)
         return
     if args.mode != "bench":
         profile_run(args)

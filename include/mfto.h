@@ -524,6 +524,7 @@ typedef struct {
   double restart_factor;    /* restart when c > factor x selected c (1.12)    */
   double select_min_penal;  /* selectable iterates: p >= this (3.0) ...       */
   double select_max_gray;   /* ... and grayness < this (0.25)                 */
+  int32_t cold_start;       /* 1: every solve starts from u = 0 (no warm start) */
 } mfto_protocol_params;
 
 typedef struct {
@@ -550,7 +551,8 @@ void mfto_default_protocol_params(mfto_protocol_params* p);
  * d_rho: initial design in (the paper starts from V_f), final design out;
  * d_rho_selected: the selected design (unchanged if none).  Host arrays of
  * n_iter entries (each may be NULL): compliance, grayness, restarted (1 when
- * a restart followed the iteration).  The handle's parameters and projection
+ * a restart followed the iteration).  cold_start = 1 zeroes d_u before every
+ * solve (the paper's cold-start hard-problem runs).  The handle's parameters and projection
  * setting are restored at exit.  Synchronises the stream. */
 mfto_status mfto_simp_protocol(mfto_handle* h, double* d_rho, double* d_u, const double* d_f,
                                double* d_rho_selected, const mfto_protocol_params* p,

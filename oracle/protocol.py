@@ -29,7 +29,8 @@ Readings (the same in the CUDA library):
     grayness is evaluated on rho_phys, as on the plain path;
   * iteration i's compliance belongs to the design rho_i that entered it; the
     selected design is that rho_i; a restart replaces the next design by the
-    selected one (the displacement keeps its warm start); the restart test
+    selected one (the displacement keeps its warm start, unless every solve
+    starts cold, as in the paper's hard-problem runs); the restart test
     comes before the selection update, against the selection so far.
 """
 from __future__ import annotations
@@ -120,7 +121,7 @@ def select_and_restart(c, penal, gray, sel_c):
 
 
 def protocol(nelx, nely, nelz, f, fixed_nodes, volfrac, rmin0, n_iter=120, nu=0.3,
-             schedule=SCHEDULE_120, rtol=1e-8, maxit=10000):
+             schedule=SCHEDULE_120, rtol=1e-8, maxit=10000, cold_start=False):
     KE = fem.ke_exact(1.0, nu)
     edof = fem.edof_table_fast(nelx, nely, nelz)
     fixed = fem.dof_mask(fixed_nodes)
@@ -130,6 +131,8 @@ def protocol(nelx, nely, nelz, f, fixed_nodes, volfrac, rmin0, n_iter=120, nu=0.
     sel_c = None
     for it in range(1, n_iter + 1):
         penal, beta, move, rmin = phase_params(it, rmin0, schedule)
+        if cold_start:
+            u = np.zeros_like(f)
         rho_new, u, c, rho_phys, _ = step(KE, edof, fixed, nelx, nely, nelz, f, rho, u, volfrac,
                                           penal, beta, move, rmin, rtol=rtol, maxit=maxit)
         gray = simp.grayness(rho_phys)

@@ -135,6 +135,7 @@ extern "C" void mfto_default_protocol_params(mfto_protocol_params* p) {
   p->restart_factor = 1.12;
   p->select_min_penal = 3.0;
   p->select_max_gray = 0.25;
+  p->cold_start = 0;
 }
 
 extern "C" mfto_status mfto_simp_protocol(mfto_handle* h, double* rho, double* u, const double* f,
@@ -171,6 +172,13 @@ extern "C" mfto_status mfto_simp_protocol(mfto_handle* h, double* rho, double* u
       return MFTO_OK;
     }();
     if (s != MFTO_OK) break;
+    if (prm->cold_start) {
+      s = [&]() -> mfto_status {
+        MFTO_CUDA(h, cudaMemsetAsync(u, 0, sizeof(double) * h->n_dof, h->stream));
+        return MFTO_OK;
+      }();
+      if (s != MFTO_OK) break;
+    }
     mfto_iter_stats is;
     s = mfto_simp_step(h, rho, u, f, nullptr, &is);
     if (s != MFTO_OK) break;

@@ -75,7 +75,7 @@ class KappaStats(C.Structure):
 class ProtocolParams(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("rmin0", C.c_double), ("eta", C.c_double),
                 ("restart_factor", C.c_double), ("select_min_penal", C.c_double),
-                ("select_max_gray", C.c_double)]
+                ("select_max_gray", C.c_double), ("cold_start", C.c_int32)]
 
 
 class ProtocolStats(C.Structure):

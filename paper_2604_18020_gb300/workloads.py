@@ -195,6 +195,46 @@ def fixed_dofs(fixed: np.ndarray) -> np.ndarray:
     return np.stack([(fixed >> c) & 1 for c in range(3)], axis=1).reshape(-1).astype(bool)
 
 
+def mbb(nelx: int = 150, nely: int = 50, nelz: int = 25, volfrac: float = 0.5,
+        rmin: float = 1.5) -> Problem:
+    """MBB hard problem of Sec. 4.1 (domain 3 x 1 x 0.5): u_x = 0 on the
+    left face x = 0, u_y = 0 at the bottom-right node of the middle depth
+    (nelx, 0, nelz // 2), a unit -y point load at the top-left node of the
+    middle depth (0, nely, nelz // 2).  The z translation and the rotation
+    about the x axis through the support stay free (the near-rigid-body
+    modes the paper names as what makes it hard); the load is orthogonal to
+    both, so the masked system is consistent."""
+    mesh = Mesh(nelx, nely, nelz)
+    i, j, k = _node_grid(mesh)
+    m = np.zeros(mesh.node_dims[::-1], dtype=np.uint8)
+    m[i == 0] |= FIX_X
+    fixed = m.reshape(-1)
+    fixed[mesh.node(nelx, 0, nelz // 2)] |= FIX_Y
+    f = np.zeros(mesh.n_dof)
+    f[3 * mesh.node(0, nely, nelz // 2) + 1] = -1.0
+    return Problem("mbb", mesh, f, fixed, volfrac, rmin,
+                   {"load": "unit point load, top-left node of the middle depth"})
+
+
+def bridge(nelx: int = 150, nely: int = 50, nelz: int = 25, volfrac: float = 0.3,
+           rmin: float = 1.5) -> Problem:
+    """Bridge hard problem of Sec. 4.1 (domain 3 x 1 x 0.5): every DOF fixed
+    on the left lower edge (0, 0, k), rollers along x on the right lower edge
+    (nelx, 0, k: u_y = u_z = 0), a unit total -y load shared equally by the
+    nodes of the top face (j = nely)."""
+    mesh = Mesh(nelx, nely, nelz)
+    fixed = np.zeros(mesh.n_node, dtype=np.uint8)
+    for k in range(nelz + 1):
+        fixed[mesh.node(0, 0, k)] = FIX_ALL
+        fixed[mesh.node(nelx, 0, k)] = FIX_Y | FIX_Z
+    f = np.zeros(mesh.n_dof)
+    top = [mesh.node(i, nely, k) for k in range(nelz + 1) for i in range(nelx + 1)]
+    for n in top:
+        f[3 * n + 1] = -1.0 / len(top)
+    return Problem("bridge", mesh, f, fixed, volfrac, rmin,
+                   {"load": "unit total load, equal shares on the top face"})
+
+
 # Named workloads: sizes of the paper's benchmarks and the configurations
 # the library is measured on.
 WORKLOADS = {
@@ -203,4 +243,6 @@ WORKLOADS = {
     "torsion_55x55x165": lambda: torsion(55, 55, 165, 0.2, 2.0),
     "cantilever_100x50x50_8rhs": lambda: multi_rhs_cantilever(100, 50, 50, 8, 3),
     "cantilever_256x128x150": lambda: cantilever(256, 128, 150, 0.12, 1.5),
+    "mbb_150x50x25": lambda: mbb(150, 50, 25),
+    "bridge_150x50x25": lambda: bridge(150, 50, 25),
 }
