@@ -549,12 +549,18 @@ def compare_run(args):
         Eb = torch.full((b.n_elem,), 0.3 ** 3, dtype=torch.float64, device=dev)
         Fb = torch.tensor(np.concatenate([p.f for p in probs]), device=dev)
         Ub = torch.zeros(b.n_dof, dtype=torch.float64, device=dev)
-        b.solve(Eb, Fb, Ub)                      # warm-up (graph capture)
-        Ub.zero_()
-        t_batch, sts = sync_time(lambda: b.solve(Eb, Fb, Ub))
+        t_batch, c_batch, sts = {}, {}, {}
         offs = b.dof_off
-        c_batch = [float(Fb[offs[i]:offs[i + 1]] @ Ub[offs[i]:offs[i + 1]]) for i in range(64)]
-    t_single = t_f64 = 0.0
+        for mode, tol in (("restart", 1e-2), ("continue", 1e-1)):
+            b.set_ir_mode(IR_MODES[mode])
+            b.solve(Eb, Fb, Ub, inner_tol=tol)      # warm-up (graph capture)
+            Ub.zero_()
+            t_batch[mode], sts[mode] = sync_time(lambda: b.solve(Eb, Fb, Ub, inner_tol=tol))
+            c_batch[mode] = [float(Fb[offs[i]:offs[i + 1]] @ Ub[offs[i]:offs[i + 1]])
+                             for i in range(64)]
+            Ub.zero_()
+    t_single = {"restart": 0.0, "continue": 0.0}
+    t_f64 = 0.0
     c64 = []
     for i, p in enumerate(probs):
         mm = p.mesh
@@ -562,21 +568,28 @@ def compare_run(args):
             Ei = torch.full((mm.n_elem,), 0.3 ** 3, dtype=torch.float64, device=dev)
             fi = torch.tensor(p.f, device=dev)
             ui = torch.zeros(mm.n_dof, dtype=torch.float64, device=dev)
-            hs.ir_solve(Ei, fi, ui)               # warm-up
-            ui.zero_()
-            dt, _ = sync_time(lambda: hs.ir_solve(Ei, fi, ui))
-            t_single += dt
+            for mode, tol in (("restart", 1e-2), ("continue", 1e-1)):
+                hs.set_ir_mode(IR_MODES[mode])
+                hs.ir_solve(Ei, fi, ui, inner_tol=tol)   # warm-up
+                ui.zero_()
+                dt, _ = sync_time(lambda: hs.ir_solve(Ei, fi, ui, inner_tol=tol))
+                t_single[mode] += dt
+                ui.zero_()
             ui.zero_()
             hs.pcg(Ei, fi, ui)
             ui.zero_()
             dt, _ = sync_time(lambda: hs.pcg(Ei, fi, ui))
             t_f64 += dt
             c64.append(float(fi @ ui))
-    out.append({"case": "64_uneven_cantilevers", "autotuned_shape": shape,
-                "shape_ms": [float(x) for x in ms], "batched_mixed_s": t_batch,
-                "single_mixed_x64_s": t_single, "plain_f64_x64_s": t_f64,
-                "all_ok": all(s.status == mfto.OK for s in sts),
-                "compliance_rel_err_vs_f64": max(abs(a - b) / abs(b) for a, b in zip(c_batch, c64))})
+    for mode, tol in (("restart", 1e-2), ("continue", 1e-1)):
+        out.append({"case": "64_uneven_cantilevers", "refinement": mode, "inner_tol": tol,
+                    "autotuned_shape": shape, "shape_ms": [float(x) for x in ms],
+                    "batched_mixed_s": t_batch[mode], "single_mixed_x64_s": t_single[mode],
+                    "plain_f64_x64_s": t_f64,
+                    "inner_iterations": sum(s.inner_iterations for s in sts[mode]),
+                    "all_ok": all(s.status == mfto.OK for s in sts[mode]),
+                    "compliance_rel_err_vs_f64": max(abs(a - b) / abs(b)
+                                                     for a, b in zip(c_batch[mode], c64))})
     for o in out:
         print(json.dumps(o))
 

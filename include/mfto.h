@@ -333,6 +333,11 @@ mfto_status mfto_batch_solve(mfto_batch* b, double inner_tol, const double* d_E,
                              mfto_ir_stats* st);
 /* Kernels launched for this batch so far (graph kernel nodes included). */
 mfto_status mfto_batch_launch_count(const mfto_batch* b, int64_t* n);
+/* Refinement mode of mfto_batch_solve, per instance as in mfto_set_ir_mode:
+ * MFTO_IR_RESTART (default, every correction restarts with p = z) or
+ * MFTO_IR_CONTINUE (each instance's inner CG continues its previous search
+ * direction with beta = r.z / (r.z)_prev).  MFTO_INVALID_ARG otherwise. */
+mfto_status mfto_batch_set_ir_mode(mfto_batch* b, int32_t mode);
 
 /* Select the linear solver of mfto_simp_step: form MFTO_FORM_F64 = plain FP64
  * Jacobi-PCG (default); any other form = mfto_ir_solve with that inner form,

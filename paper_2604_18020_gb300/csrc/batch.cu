@@ -75,6 +75,8 @@ struct mfto_batch {
   double *d_part_a, *d_part_b;     // [2][max blocks]
   double* d_res;                   // [2 * count] outer residual sums
   int* d_mask;                     // [count] 1 = instance converged/stopped
+  double* d_rzp;                   // [count] r.z of a continued direction (0: p = z)
+  int ir_mode;                     // MFTO_IR_RESTART or MFTO_IR_CONTINUE
   BatchGraph* graph;
   int64_t launches;
   char msg[512];
@@ -389,7 +391,8 @@ batch_update(float* __restrict__ U, const float* __restrict__ P, const float* __
 __global__ void __launch_bounds__(MFTO_BLOCK)
 batch_init(float* R, float* __restrict__ Z, const float* __restrict__ dinv,
            const BatchInst* __restrict__ inst, BatchScal* sc, BatchCtl* ctl, double* part,
-           int total, int stride, double rtol, int maxit, int count) {
+           int total, int stride, double rtol, int maxit, int count,
+           const double* __restrict__ rz_prev) {
   __shared__ int first[MFTO_BATCH_MAX];
   __shared__ double sh[64];
   for (int i = threadIdx.x; i < count; i += blockDim.x) first[i] = inst[i].up_blk0;
@@ -426,7 +429,7 @@ batch_init(float* R, float* __restrict__ Z, const float* __restrict__ dinv,
       s.ff = s.rr;
       s.rtol2ff = rtol * rtol * s.ff;
       s.alpha = 0.0;
-      s.beta = 0.0;
+      s.beta = rz_prev[i] > 0.0 ? s.rz / rz_prev[i] : 0.0;   // continued direction
       s.it = 0;
       s.status = MFTO_OK;
       s.done = s.ff == 0.0 ? 1 : 0;
@@ -680,6 +683,7 @@ void free_batch(mfto_batch* b) {
   }
   void* ptrs[] = {b->d_fixed, b->r32, b->z32, b->p0, b->p1, b->q32, b->e32, b->dinv32, b->E32,
                   b->q64, b->d_scal, b->d_ctl, b->d_part_a, b->d_part_b, b->d_res, b->d_mask,
+                  b->d_rzp,
                   b->d_inst[0], b->d_inst[1], b->d_inst[2], b->d_inst[3]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -761,6 +765,7 @@ extern "C" mfto_status mfto_batch_create(int32_t count, const mfto_mesh* meshes,
   A((void**)&b->d_part_a, sizeof(double) * 2 * max_blocks);
   A((void**)&b->d_part_b, sizeof(double) * 2 * max_blocks);
   A((void**)&b->d_res, sizeof(double) * 2 * count);
+  A((void**)&b->d_rzp, sizeof(double) * count);
   A((void**)&b->d_mask, sizeof(int) * count);
   for (int s = 0; s < MFTO_BATCH_SHAPES; ++s) A((void**)&b->d_inst[s], sizeof(BatchInst) * count);
   if (ok && (cudaMallocHost(&b->h_scal, sizeof(BatchScal) * count) != cudaSuccess ||
@@ -887,6 +892,7 @@ extern "C" mfto_status mfto_batch_solve(mfto_batch* b, double inner_tol, const d
   std::vector<int> mask(count, 0);
   std::vector<double> prev(count, 0.0), res(2 * count);
   std::vector<int> stalls(count, 0);
+  std::vector<double> rzp(count, 0.0);   // continued directions (MFTO_IR_CONTINUE)
   for (int outer = 0;; ++outer) {
     BCUDA(b, cudaMemcpyAsync(b->d_mask, mask.data(), sizeof(int) * count, cudaMemcpyHostToDevice,
                              b->stream));
@@ -934,11 +940,22 @@ extern "C" mfto_status mfto_batch_solve(mfto_batch* b, double inner_tol, const d
       BCUDA(b, cudaGetLastError());
     }
     BCUDA(b, cudaMemsetAsync(b->e32, 0, sizeof(float) * b->n_dof, b->stream));
-    BCUDA(b, cudaMemsetAsync(b->p0, 0, sizeof(float) * b->n_dof, b->stream));
+    // instances that continue their direction keep it in p0; the others start from p = z
+    for (int i = 0; i < count; ++i) {
+      if (mask[i]) rzp[i] = 0.0;
+      if (!(rzp[i] > 0.0)) {
+        const long long o = 3 * b->node_off[i];
+        const long long n = 3 * ((long long)(b->meshes[i].nelx + 1) * (b->meshes[i].nely + 1) *
+                                 (b->meshes[i].nelz + 1));
+        BCUDA(b, cudaMemsetAsync(b->p0 + o, 0, sizeof(float) * n, b->stream));
+      }
+    }
+    BCUDA(b, cudaMemcpyAsync(b->d_rzp, rzp.data(), sizeof(double) * count, cudaMemcpyHostToDevice,
+                             b->stream));
     b->launches++;
     batch_init<<<ug, MFTO_BLOCK, 0, b->stream>>>(b->r32, b->z32, b->dinv32, b->d_inst[b->shape],
                                                  b->d_scal, b->d_ctl, b->d_part_a, b->up_total,
-                                                 stride, inner_tol, inner_maxit, count);
+                                                 stride, inner_tol, inner_maxit, count, b->d_rzp);
     BCUDA(b, cudaGetLastError());
     BatchGraph* g = nullptr;
     s = get_graph(b, &g);
@@ -956,8 +973,23 @@ extern "C" mfto_status mfto_batch_solve(mfto_batch* b, double inner_tol, const d
     BCUDA(b, cudaStreamSynchronize(b->stream));
     for (int i = 0; i < count; ++i) {
       if (mask[i]) continue;
-      st[i].inner_iterations += b->h_scal[i].it;
+      const BatchScal& fin = b->h_scal[i];
+      st[i].inner_iterations += fin.it;
       st[i].outer_iterations++;
+      // continued direction: iteration j writes its direction into p1 (j even)
+      // or p0 (j odd); the next inner solve reads p0 first
+      rzp[i] = 0.0;
+      if (b->ir_mode == MFTO_IR_CONTINUE && fin.it >= 1 && fin.status != MFTO_BREAKDOWN &&
+          fin.beta > 0.0 && isfinite(fin.rz / fin.beta)) {
+        if (fin.it & 1) {
+          const long long o = 3 * b->node_off[i];
+          const long long n = 3 * ((long long)(b->meshes[i].nelx + 1) * (b->meshes[i].nely + 1) *
+                                   (b->meshes[i].nelz + 1));
+          BCUDA(b, cudaMemcpyAsync(b->p0 + o, b->p1 + o, sizeof(float) * n,
+                                   cudaMemcpyDeviceToDevice, b->stream));
+        }
+        rzp[i] = fin.rz / fin.beta;
+      }
     }
     b->launches++;
     batch_accumulate<<<ug, MFTO_BLOCK, 0, b->stream>>>(U, b->e32, b->n_dof);
@@ -969,5 +1001,13 @@ extern "C" mfto_status mfto_batch_solve(mfto_batch* b, double inner_tol, const d
 extern "C" mfto_status mfto_batch_launch_count(const mfto_batch* b, int64_t* n) {
   if (!b || !n) return MFTO_INVALID_ARG;
   *n = b->launches;
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_batch_set_ir_mode(mfto_batch* b, int32_t mode) {
+  if (!b) return MFTO_INVALID_ARG;
+  if (mode != MFTO_IR_RESTART && mode != MFTO_IR_CONTINUE)
+    return bfail(b, MFTO_INVALID_ARG, "mfto_batch_set_ir_mode: MFTO_IR_RESTART or MFTO_IR_CONTINUE");
+  b->ir_mode = mode;
   return MFTO_OK;
 }

@@ -431,14 +431,25 @@ __device__ __forceinline__ bool row_reduce_df(const DFloat (&v)[K], double* part
   return true;
 }
 
-// A device FP64 scalar as FP32 for every thread of the block: one conversion
-// by thread 0, broadcast through shared memory (call once per kernel).
-__device__ __forceinline__ float scalar_as_f32(const double* p) {
+// A solver's done flag and one FP64 scalar, read in a single round trip by
+// thread 0 (the scalar converted to FP32 there) and broadcast through shared
+// memory: *done_out and the returned value are the same in every thread.
+// Call once per kernel, before anything else uses shared memory.
+__device__ __forceinline__ float flag_and_scalar_f32(const int32_t* done, const double* p,
+                                                     int* done_out) {
   __shared__ float s_val;
-  if (threadIdx.x == 0) s_val = (float)*p;
+  __shared__ int s_done;
+  if (threadIdx.x == 0) {
+    const int d = *(const volatile int32_t*)done;
+    const double v = *p;
+    s_done = d;
+    s_val = (float)v;
+  }
   __syncthreads();
+  *done_out = s_done;
   return s_val;
 }
+
 
 // Publish K per-block partial sums and let the last block to arrive reduce
 // them in block-index order.  Returns true in every thread of that last

@@ -79,10 +79,11 @@ pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
                   const float* __restrict__ p_old, float* __restrict__ p_new,
                   float* __restrict__ q, const uint8_t* __restrict__ fixed, ModeCoef<float> K,
                   Grid g, ColTiling tl, PcgScalars* s, double* partials) {
-  if (*(volatile int32_t*)&s->done) return;  // uniform over the grid
+  int done = 0;
+  const float beta = flag_and_scalar_f32(&s->done, &s->beta, &done);
+  if (done) return;   // uniform over the grid
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[64];
-  const float beta = scalar_as_f32(&s->beta);
   DotAcc<float> acc;
   acc.s = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{z, p_old, beta}, ColPcg{p_new, q},
                          reinterpret_cast<float*>(smem_raw));

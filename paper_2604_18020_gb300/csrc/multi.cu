@@ -258,10 +258,11 @@ pcg_kv_multi_col(const float* __restrict__ E, const float* __restrict__ Z,
                  const uint8_t* __restrict__ fixed, ModeCoef<float> K, Grid g, ColTiling tl,
                  int n_dof, MultiScalars* s, double* partials) {
   const int r = blockIdx.y;
-  if (*(volatile int32_t*)&s->done[r]) return;   // uniform over the case's blocks
+  int done = 0;
+  const float beta = flag_and_scalar_f32(&s->done[r], &s->beta[r], &done);
+  if (done) return;   // uniform over the case's blocks
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[64];
-  const float beta = scalar_as_f32(&s->beta[r]);
   const size_t o = (size_t)r * n_dof;
   DotAcc<float> acc;
   acc.s = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{Z + o, P0 + o, beta},
@@ -288,9 +289,10 @@ pcg_update_multi_col(float* __restrict__ U, const float* __restrict__ P,
                      const float* __restrict__ dinv, int n_dof, MultiScalars* s,
                      double* partials) {
   const int r = blockIdx.y;
-  if (*(volatile int32_t*)&s->done[r]) return;
+  int done = 0;
+  const float alpha = flag_and_scalar_f32(&s->done[r], &s->alpha[r], &done);
+  if (done) return;
   __shared__ double sh[64];
-  const float alpha = scalar_as_f32(&s->alpha[r]);
   const size_t o = (size_t)r * n_dof;
   DotAcc<float> d0, d1;
   // groups of 4 consecutive DOFs (a case's vectors start at r n_dof, which

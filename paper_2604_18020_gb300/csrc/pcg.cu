@@ -160,9 +160,10 @@ __global__ void __launch_bounds__(MFTO_BLOCK)
 pcg_update_f32(float* __restrict__ u, const float* __restrict__ p, const float* __restrict__ q,
                float* __restrict__ r, float* __restrict__ z, const float* __restrict__ dinv,
                int n, PcgScalars* s, double* partials) {
-  if (*(volatile int32_t*)&s->done) return;
+  int done = 0;
+  const float alpha = flag_and_scalar_f32(&s->done, &s->alpha, &done);
+  if (done) return;
   __shared__ double sh[64];
-  const float alpha = scalar_as_f32(&s->alpha);
   DotAcc<float> d0, d1;
   cg_update_f32<false>(u, p, q, r, z, dinv, n, alpha, blockIdx.x * blockDim.x + threadIdx.x,
                        gridDim.x * blockDim.x, d0, d1);

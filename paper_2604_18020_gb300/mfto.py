@@ -147,6 +147,7 @@ SIGNATURES = {
     "mfto_batch_solve": (C.c_int32, [_P, C.c_double, _P, _P, _P, C.c_int32, C.c_int32,
                                      C.POINTER(IrStats)]),
     "mfto_batch_launch_count": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
+    "mfto_batch_set_ir_mode": (C.c_int32, [_P, C.c_int32]),
     "mfto_ir_solve_multi": (C.c_int32, [_P, C.c_double, _P, _P, _P, C.c_int32,
                                         C.POINTER(IrStats)]),
     "mfto_filter": (C.c_int32, [_P, _P, _P, C.c_int32]),
@@ -764,6 +765,9 @@ class Batch:
             _ptr(F, torch.float64, self.n_dof, "F"), _ptr(U, torch.float64, self.n_dof, "U"),
             inner_maxit, max_outer, st))
         return list(st)
+
+    def set_ir_mode(self, mode):
+        self._chk("mfto_batch_set_ir_mode", lib().mfto_batch_set_ir_mode(self._b, mode))
 
     def launch_count(self):
         n = C.c_int64()

@@ -47,7 +47,19 @@ def test_batch_kv(cuda, shape, form):
         assert np.abs(gi - ref).max() / np.abs(ref).max() <= tol, (i, shape)
 
 
-def test_batch_solve_and_autotune(cuda):
+def test_batch_ir_mode_rejects_unknown(cuda):
+    from paper_2604_18020_gb300 import mfto
+    problems = W.uneven_instances(count=2, seed=3, kmin=3, kmax=4)
+    with mfto.Batch([(P.mesh.nelx, P.mesh.nely, P.mesh.nelz) for P in problems],
+                    [P.fixed for P in problems]) as b:
+        with pytest.raises(mfto.MftoError):
+            b.set_ir_mode(2)
+
+
+@pytest.mark.parametrize("mode,inner_tol", [(0, 1e-2), (1, 1e-1)])
+def test_batch_solve_and_autotune(cuda, mode, inner_tol):
+    """Restarted and continued refinement (each instance keeps its own
+    direction) both reach the outer tolerance on every instance."""
     import torch
     from paper_2604_18020_gb300 import mfto
     problems = W.uneven_instances(count=6, seed=12, kmin=3, kmax=8)
@@ -56,9 +68,10 @@ def test_batch_solve_and_autotune(cuda):
                     [P.fixed for P in problems]) as b:
         choice, ms = b.autotune(reps=3)
         assert 0 <= choice < 4 and np.all(ms > 0) and ms[choice] == ms.min()
+        b.set_ir_mode(mode)
         U = torch.zeros(b.n_dof, dtype=torch.float64, device=cuda)
         sts = b.solve(torch.tensor(np.concatenate(Es), device=cuda),
-                      torch.tensor(np.concatenate(fs), device=cuda), U)
+                      torch.tensor(np.concatenate(fs), device=cuda), U, inner_tol=inner_tol)
         got = U.cpu().numpy()
         offs = b.dof_off
     for i, P in enumerate(problems):
