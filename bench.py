@@ -800,6 +800,65 @@ def hard_run(args):
             flush=True)
 
 
+def ubench_run(args):
+    """The synthetic hot-path microbenchmark of Sec. 5 (Tab. profiling) at
+    its four sizes (cantilever shapes 80x40x20 .. 200x100x50, 64k .. 1M
+    elements) on random element connectivity (seed 42): the staged FP64
+    pipeline (gather, element contraction, scatter) and the fused FP64 and
+    FP32 kernels, device times from CUDA events, median of the timed calls;
+    beside them the structured-mesh K.v of the library (FP64 and the FP32
+    column kernel, no atomics) on the same shapes.  One JSON line per size."""
+    import numpy as np
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+    reps = max(args.steps, 20)
+    for shape in ((80, 40, 20), (120, 60, 30), (160, 80, 40), (200, 100, 50)):
+        m = W.Mesh(*shape)
+        edof = torch.tensor(W.edof_random(m, 42), device=dev)
+        E64 = torch.tensor(W.rho_random(m, seed=1), device=dev)
+        v64 = torch.tensor(W.vec_random(m.n_dof, seed=2), device=dev)
+        E32, v32 = E64.float(), v64.float()
+        y64 = torch.empty_like(v64)
+        y32 = torch.empty_like(v32)
+        row = {"case": "ubench_random_index", "mesh": "x".join(map(str, shape)),
+               "elements": m.n_elem, "dofs": m.n_dof, "timed_calls": reps}
+        with mfto.Ebe(m.n_elem, m.n_dof) as e:
+            for variant, key in ((0, "staged_f64"), (1, "fused_f64"), (2, "fused_f32")):
+                Ev, vv, yv = (E32, v32, y32) if variant == 2 else (E64, v64, y64)
+                for _ in range(args.warmup):
+                    e.kv(variant, edof, Ev, vv, yv, timed=True)
+                ts = np.array([e.kv(variant, edof, Ev, vv, yv, timed=True) for _ in range(reps)])
+                med = np.median(ts, axis=0) * 1e3
+                if variant == 0:
+                    row["t_gather_us"], row["t_contract_us"], row["t_scatter_us"] = map(float, med)
+                    row["t_full64_us"] = float(np.median(ts.sum(axis=1)) * 1e3)
+                else:
+                    row[f"t_{key}_us"] = float(med[0])
+        # the library's structured operator on the same shape (clamped x = 0 face)
+        P = W.cantilever(*shape)
+        with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
+            h.kv_autotune()
+            for form, key, Ev, vv, yv in ((mfto.FORM_F64, "structured_f64", E64, v64, y64),
+                                          (mfto.FORM_F32, "structured_f32", E32, v32, y32)):
+                for _ in range(args.warmup):
+                    h.kv(Ev, vv, yv, form)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ts = []
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    ev0.record()
+                    h.kv(Ev, vv, yv, form)
+                    ev1.record()
+                    torch.cuda.synchronize()
+                    ts.append(ev0.elapsed_time(ev1))
+                row[f"t_{key}_us"] = float(np.median(ts) * 1e3)
+        row["fused_f32_speedup_vs_staged_f64"] = row["t_full64_us"] / row["t_fused_f32_us"]
+        row["structured_f32_speedup_vs_staged_f64"] = row["t_full64_us"] / row["t_structured_f32_us"]
+        print(json.dumps(row), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -810,7 +869,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench",
                     choices=["bench", "profile", "pcg", "compare", "learned", "kappa", "protocol",
-                             "hard"])
+                             "hard", "ubench"])
     ap.add_argument("--protocol-iters", type=int, default=120)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--form", default="mixed", choices=["f64", "mixed"],
@@ -848,6 +907,9 @@ def main():
         return
     if args.mode == "hard":
         hard_run(args)
+        return
+    if args.mode == "ubench":
+        ubench_run(args)
         return
     if args.mode != "bench":
         profile_run(args)

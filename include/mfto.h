@@ -660,6 +660,45 @@ mfto_status mfto_compliance_sens_noalloc(const mfto_mesh* mesh, double E0, doubl
                                          const double* d_u, double* d_dc, double* h_c_out,
                                          void* stream);
 
+/* ------------------------------------- element-by-element microbenchmark -- */
+
+/* y = sum_e B_e^T (E_e KE) B_e v over an ARBITRARY element DOF table (no
+ * Dirichlet rows): the synthetic hot-path microbenchmark of Sec. 5 (Tab.
+ * profiling), whose element DOF indices are random rather than the
+ * structured mesh's.  Variants:
+ *   MFTO_EBE_STAGED_F64: three kernels, as the paper's unfused FP64 pipeline
+ *     (t_full64): gather V_e = v[edof_e] into an [n_elem][24] buffer, the
+ *     element contraction Y_e = V_e KE into a second one, and the scatter
+ *     y[edof_e] += E_e Y_e with FP64 atomics;
+ *   MFTO_EBE_FUSED_F64 / MFTO_EBE_FUSED_F32: one kernel, an element per
+ *     thread (gather, contraction, atomic scatter), in FP64 / FP32.
+ * The atomics make the sums' order, and so their last bits, vary from run to
+ * run.  mfto_ebe_create: n_elem >= 1 (at most 2^31 / 24), 1 <= n_dof < 2^31,
+ * h_KE the 576 doubles of the unit element matrix (row-major, e.g. from
+ * mfto_unit_ke), stream a cudaStream_t (NULL = legacy stream); it allocates
+ * two [n_elem][24] FP64 stage buffers (MFTO_OOM if that fails).
+ * mfto_ebe_kv: d_edof int32 [n_elem][24] row-major, 16-byte aligned, entries
+ * in [0, n_dof); d_E, d_v, d_y FP64 (FP32 for MFTO_EBE_FUSED_F32) of n_elem,
+ * n_dof, n_dof entries; d_y is overwritten.  Synchronises the stream.  With
+ * h_stage_ms non-NULL the device times (CUDA events, ms) are written there:
+ * gather, contraction and scatter (3 floats, the scatter's zeroing of y
+ * included) for the staged variant, one total for the fused ones.  An index
+ * outside [0, n_dof) is skipped and the call returns MFTO_INVALID_ARG. */
+typedef enum {
+  MFTO_EBE_STAGED_F64 = 0,
+  MFTO_EBE_FUSED_F64 = 1,
+  MFTO_EBE_FUSED_F32 = 2
+} mfto_ebe_variant;
+typedef struct mfto_ebe mfto_ebe;
+mfto_status mfto_ebe_create(int64_t n_elem, int64_t n_dof, const double* h_KE, void* stream,
+                            mfto_ebe** out);
+mfto_status mfto_ebe_destroy(mfto_ebe* e);
+const char* mfto_ebe_last_error(const mfto_ebe* e);
+mfto_status mfto_ebe_kv(mfto_ebe* e, int32_t variant, const int32_t* d_edof, const void* d_E,
+                        const void* d_v, void* d_y, float* h_stage_ms);
+/* Kernels launched by this object so far. */
+mfto_status mfto_ebe_launch_count(const mfto_ebe* e, int64_t* n);
+
 /* ------------------------------------------------------- measurement aid -- */
 
 /* Arithmetic-pipe probe: launches `blocks` x 256 threads, each running

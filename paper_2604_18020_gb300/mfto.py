@@ -148,6 +148,11 @@ SIGNATURES = {
                                      C.POINTER(IrStats)]),
     "mfto_batch_launch_count": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
     "mfto_batch_set_ir_mode": (C.c_int32, [_P, C.c_int32]),
+    "mfto_ebe_create": (C.c_int32, [C.c_int64, C.c_int64, _P, _P, _P]),
+    "mfto_ebe_destroy": (C.c_int32, [_P]),
+    "mfto_ebe_last_error": (C.c_char_p, [_P]),
+    "mfto_ebe_kv": (C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, _P]),
+    "mfto_ebe_launch_count": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
     "mfto_ir_solve_multi": (C.c_int32, [_P, C.c_double, _P, _P, _P, C.c_int32,
                                         C.POINTER(IrStats)]),
     "mfto_filter": (C.c_int32, [_P, _P, _P, C.c_int32]),
@@ -693,6 +698,67 @@ class Net:
         n = C.c_int64()
         self._chk("mfto_nn_launch_count", lib().mfto_nn_launch_count(self._n, C.byref(n)))
         return n.value
+
+
+EBE_STAGED_F64, EBE_FUSED_F64, EBE_FUSED_F32 = 0, 1, 2
+
+
+class Ebe:
+    """Owns one mfto_ebe: K.v over an arbitrary element DOF table (int32
+    [n_elem, 24]), staged FP64 or fused FP64 / FP32, with atomic scatter."""
+
+    def __init__(self, n_elem, n_dof, KE=None, stream=None):
+        import torch
+        self.n_elem, self.n_dof = int(n_elem), int(n_dof)
+        ke = np.ascontiguousarray(unit_ke() if KE is None else np.asarray(KE, np.float64))
+        assert ke.shape == (24, 24)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ep = C.c_void_p()
+        _check("mfto_ebe_create", lib().mfto_ebe_create(self.n_elem, self.n_dof, ke.ctypes.data,
+                                                        C.c_void_p(self.stream.cuda_stream),
+                                                        C.byref(ep)))
+        self._e = ep
+
+    def _chk(self, fn, code):
+        if code != OK:
+            raw = lib().mfto_ebe_last_error(self._e) if getattr(self, "_e", None) else b""
+            raise MftoError(fn, code, raw.decode() if raw else "")
+
+    def kv(self, variant, edof, E, v, y, timed=False):
+        """y = K(E) v; with timed=True returns the device times in ms
+        ([gather, contraction, scatter] staged, [total] fused)."""
+        import torch
+        dt = torch.float32 if variant == EBE_FUSED_F32 else torch.float64
+        ms = np.zeros(3, dtype=np.float32)
+        self._chk("mfto_ebe_kv", lib().mfto_ebe_kv(
+            self._e, variant, _ptr(edof, torch.int32, 24 * self.n_elem, "edof"),
+            _ptr(E, dt, self.n_elem, "E"), _ptr(v, dt, self.n_dof, "v"),
+            _ptr(y, dt, self.n_dof, "y"), ms.ctypes.data if timed else None))
+        if timed:
+            return [float(x) for x in (ms if variant == EBE_STAGED_F64 else ms[:1])]
+        return None
+
+    def launch_count(self):
+        n = C.c_int64()
+        self._chk("mfto_ebe_launch_count", lib().mfto_ebe_launch_count(self._e, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_e", None):
+            lib().mfto_ebe_destroy(self._e)
+            self._e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Batch:

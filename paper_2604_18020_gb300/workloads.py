@@ -195,6 +195,18 @@ def fixed_dofs(fixed: np.ndarray) -> np.ndarray:
     return np.stack([(fixed >> c) & 1 for c in range(3)], axis=1).reshape(-1).astype(bool)
 
 
+def edof_random(mesh: Mesh, seed: int = 42) -> np.ndarray:
+    """Random element connectivity of the synthetic hot-path microbenchmark
+    (Sec. 5, Tab. profiling): the tensor shapes of the mesh's operator (its
+    element and node counts) with each element's 8 node ids drawn uniformly
+    from all nodes, then expanded to DOFs 3 n + c in the local order of the
+    structured table.  int32 [n_elem, 24]."""
+    rng = np.random.default_rng(seed)
+    nodes = rng.integers(0, mesh.n_node, size=(mesh.n_elem, 8), dtype=np.int64)
+    edof = (3 * nodes[:, :, None] + np.arange(3)[None, None, :]).reshape(mesh.n_elem, 24)
+    return np.ascontiguousarray(edof.astype(np.int32))
+
+
 def mbb(nelx: int = 150, nely: int = 50, nelz: int = 25, volfrac: float = 0.5,
         rmin: float = 1.5) -> Problem:
     """MBB hard problem of Sec. 4.1 (domain 3 x 1 x 0.5): u_x = 0 on the

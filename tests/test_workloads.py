@@ -52,3 +52,25 @@ def test_bridge_preset():
     edof = fem.edof_table_fast(m.nelx, m.nely, m.nelz)
     K = fem.assemble_masked(KE, np.ones(m.n_elem), edof, m.n_dof, W.fixed_dofs(P.fixed))
     assert np.linalg.eigvalsh(K)[0] > 1e-8
+
+
+def test_edof_random_shape_and_oracle_pin():
+    """The random connectivity keeps the structured table's per-node DOF
+    triples, is seeded, and the oracle's gather-contract-scatter K.v on it
+    equals the assembled sparse matrix (duplicates summed by the COO
+    conversion) times v."""
+    from oracle import fem
+    m = W.Mesh(5, 4, 3)
+    edof = W.edof_random(m, 42)
+    assert edof.dtype == np.int32 and edof.shape == (m.n_elem, 24)
+    assert edof.min() >= 0 and edof.max() < m.n_dof
+    trip = edof.reshape(m.n_elem, 8, 3)
+    assert np.all(trip % 3 == np.arange(3)) and np.all(trip[:, :, 1] == trip[:, :, 0] + 1)
+    assert np.array_equal(edof, W.edof_random(m, 42))
+    assert not np.array_equal(edof, W.edof_random(m, 43))
+    E = W.rho_random(m, seed=1)
+    v = W.vec_random(m.n_dof, seed=2)
+    KE = fem.ke_exact()
+    K = fem.assemble(KE, E, edof.astype(np.int64), m.n_dof)
+    y = fem.kv_unmasked(KE, E, edof.astype(np.int64), v)
+    assert np.abs(K @ v - y).max() <= 1e-13 * np.abs(y).max()
