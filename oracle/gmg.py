@@ -1,0 +1,206 @@
+"""Oracle: geometric multigrid for the masked SIMP stiffness operator and CG
+preconditioned by its V-cycle.
+
+TEST INFRASTRUCTURE ONLY (see oracle/fem.py).
+
+Paper passages (arXiv 2604.18020):
+  * Sec. 6 ("Path to Geometric Multigrid Integration"): the components a GMG
+    preconditioner adds to the matrix-free operator -- a restriction R from
+    the fine to the coarse grid, the prolongation P = R^T, a direct solve on
+    the coarsest level, and pre/post-smoothing steps that each apply the
+    operator once -- all with closed-form stencils on the structured mesh;
+  * Sec. 3.5 ("Path forward"): the low-precision K.v as the smoother inside
+    a V-cycle, where the coarse-grid correction bounds the spectrum each
+    level sees.
+
+The paper names the components only; the textbook V-cycle (Briggs, Henson
+and McCormick, "A Multigrid Tutorial", ch. 3 and 5) is written out here with
+these readings (the same in the CUDA library):
+  * coarsening halves the element count per axis, rounding up: a level with
+    n elements along an axis has ceil(n / 2) coarse elements there; a coarse
+    element whose 2 x 2 x 2 children are not all present simply has fewer;
+  * P is trilinear interpolation from the coarse nodes (fine coordinates 2I)
+    to the fine nodes: per axis, an even fine node 2I takes coarse node I,
+    an odd one 2I + 1 the mean of coarse nodes I and I + 1 (which exists even
+    when 2I + 2 lies past the fine mesh); the 3-D operator is the tensor
+    product, applied to each displacement component;
+  * Dirichlet DOFs: a coarse DOF is fixed when the fine DOF at the same
+    position is; with M_f, M_c the 0/1 diagonals of the free DOFs,
+    Phat = M_f P M_c, and the coarse operator is the Galerkin product
+    A_c = Phat^T A Phat plus the identity on the fixed coarse DOFs (the same
+    masking as the fine operator, so every level is SPD);
+  * the coarsening stops at the first level with at most coarse_max_dofs
+    DOFs or at max_levels levels; that level is solved exactly;
+  * smoother: l1-Jacobi (Baker, Falgout, Kolev and Yang, SIAM J. Sci. Comput.
+    2011), x <- x + omega D1^-1 (b - A x) with D1_ii = sum_j |A_ij|, which
+    converges for every SPD A at omega = 1 without a spectral estimate;
+    nu_pre sweeps from x = 0 before, nu_post after the coarse correction;
+  * the outer CG takes z = V(r) with the Polak-Ribiere form of beta
+    (flexible CG), so a preconditioner applied in lower precision keeps the
+    iteration convergent.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import fem
+
+
+def coarse_dims(n):
+    return tuple((a + 1) // 2 for a in n)
+
+
+def level_dims(nelx, nely, nelz, max_levels=8, coarse_max_dofs=200):
+    """Element counts (nx, ny, nz) of every level, finest first."""
+    dims = [(nelx, nely, nelz)]
+    while len(dims) < max_levels:
+        nx, ny, nz = dims[-1]
+        if 3 * (nx + 1) * (ny + 1) * (nz + 1) <= coarse_max_dofs or (nx, ny, nz) == (1, 1, 1):
+            break
+        dims.append(coarse_dims(dims[-1]))
+    return dims
+
+
+def prolong_1d(n):
+    """(n + 1) x (ceil(n/2) + 1) interpolation along one axis."""
+    m = (n + 1) // 2
+    rows, cols, vals = [], [], []
+    for i in range(n + 1):
+        if i % 2 == 0:
+            rows.append(i); cols.append(i // 2); vals.append(1.0)
+        else:
+            rows += [i, i]; cols += [(i - 1) // 2, (i + 1) // 2]; vals += [0.5, 0.5]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n + 1, m + 1))
+
+
+def prolong_nodes(n):
+    """Nodal trilinear interpolation, x fastest (node = i + (nx+1)(j + (ny+1)k))."""
+    nx, ny, nz = n
+    return sp.kron(prolong_1d(nz), sp.kron(prolong_1d(ny), prolong_1d(nx))).tocsr()
+
+
+def prolong_dofs(n):
+    return sp.kron(prolong_nodes(n), sp.identity(3)).tocsr()
+
+
+def coarse_fixed(n, fixed_dofs):
+    """Fixed-DOF mask of the coarse level: coarse node (I, J, K) takes the
+    mask of the fine node (2I, 2J, 2K) where that node exists."""
+    nx, ny, nz = n
+    mx, my, mz = coarse_dims(n)
+    fd = np.asarray(fixed_dofs, bool).reshape(nz + 1, ny + 1, nx + 1, 3)
+    out = np.zeros((mz + 1, my + 1, mx + 1, 3), bool)
+    I = np.arange(mx + 1); J = np.arange(my + 1); K = np.arange(mz + 1)
+    ok_i, ok_j, ok_k = 2 * I <= nx, 2 * J <= ny, 2 * K <= nz
+    sub = fd[np.ix_(2 * K[ok_k], 2 * J[ok_j], 2 * I[ok_i])]
+    out[np.ix_(K[ok_k], J[ok_j], I[ok_i])] = sub
+    return out.reshape(-1)
+
+
+def masked_operator(KE, E, edof, n_dof, fixed_dofs):
+    """Sparse masked fine operator: M K M + diag(fixed)."""
+    K = fem.assemble(KE, E, edof, n_dof)
+    m = sp.diags((~np.asarray(fixed_dofs, bool)).astype(float))
+    return (m @ K @ m + sp.diags(np.asarray(fixed_dofs, bool).astype(float))).tocsr()
+
+
+@dataclass
+class Level:
+    dims: tuple
+    A: sp.csr_matrix          # masked operator of this level
+    fixed: np.ndarray         # bool [n_dof]
+    d1inv: np.ndarray         # 1 / sum_j |A_ij|
+    P: sp.csr_matrix | None   # Phat from the next coarser level to this one
+
+
+@dataclass
+class Hierarchy:
+    levels: list
+    coarse_inv: np.ndarray    # dense inverse of the coarsest operator
+    omega: float
+    nu_pre: int
+    nu_post: int
+
+
+def build(KE, E, nelx, nely, nelz, fixed_dofs, max_levels=8, coarse_max_dofs=200, omega=1.0,
+          nu_pre=2, nu_post=2):
+    dims = level_dims(nelx, nely, nelz, max_levels, coarse_max_dofs)
+    edof = fem.edof_table_fast(nelx, nely, nelz)
+    n_dof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
+    fixed = np.asarray(fixed_dofs, bool)
+    A = masked_operator(KE, E, edof, n_dof, fixed)
+    levels = []
+    for li, n in enumerate(dims):
+        d1 = np.asarray(abs(A).sum(axis=1)).reshape(-1)
+        lev = Level(n, A, fixed, 1.0 / d1, None)
+        levels.append(lev)
+        if li + 1 < len(dims):
+            cf = coarse_fixed(n, fixed)
+            Ph = sp.diags((~fixed).astype(float)) @ prolong_dofs(n) @ sp.diags((~cf).astype(float))
+            lev.P = Ph.tocsr()
+            A = (lev.P.T @ A @ lev.P + sp.diags(cf.astype(float))).tocsr()
+            fixed = cf
+    coarse_inv = np.linalg.inv(levels[-1].A.toarray())
+    return Hierarchy(levels, coarse_inv, omega, nu_pre, nu_post)
+
+
+def smooth(lev, x, b, omega, sweeps):
+    for _ in range(sweeps):
+        x = x + omega * lev.d1inv * (b - lev.A @ x)
+    return x
+
+
+def vcycle(H, b, li=0):
+    lev = H.levels[li]
+    if li == len(H.levels) - 1:
+        return H.coarse_inv @ b
+    x = smooth(lev, np.zeros_like(b), b, H.omega, H.nu_pre)
+    r = b - lev.A @ x
+    xc = vcycle(H, lev.P.T @ r, li + 1)
+    x = x + lev.P @ xc
+    return smooth(lev, x, b, H.omega, H.nu_post)
+
+
+@dataclass
+class GmgStats:
+    iterations: int
+    rel_residual: float
+    true_rel_residual: float
+    converged: bool
+
+
+def pcg(H, apply_K, f, u0, rtol=1e-8, maxit=1000, precond=None):
+    """CG preconditioned by the V-cycle (or by precond(r) when given), beta in
+    the Polak-Ribiere form z_k+1 . (r_k+1 - r_k) / (z_k . r_k)."""
+    M = precond if precond is not None else (lambda r: vcycle(H, r))
+    f = np.asarray(f, dtype=np.float64)
+    u = np.array(u0, dtype=np.float64, copy=True)
+    fnorm = np.linalg.norm(f)
+    if fnorm == 0.0:
+        return np.zeros_like(f), GmgStats(0, 0.0, 0.0, True)
+    r = f - apply_K(u)
+    z = M(r)
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    rel = np.linalg.norm(r) / fnorm
+    while rel > rtol and it < maxit:
+        q = apply_K(p)
+        alpha = rz / (p @ q)
+        u += alpha * p
+        r_old = r
+        r = r - alpha * q
+        it += 1
+        rel = np.linalg.norm(r) / fnorm
+        if rel <= rtol:
+            break
+        z = M(r)
+        rz_new = r @ z
+        beta = (rz_new - z @ r_old) / rz
+        p = z + beta * p
+        rz = rz_new
+    true_rel = np.linalg.norm(f - apply_K(u)) / fnorm
+    return u, GmgStats(it, rel, true_rel, rel <= rtol)
