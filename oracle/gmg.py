@@ -32,9 +32,17 @@ these readings (the same in the CUDA library):
   * the coarsening stops at the first level with at most coarse_max_dofs
     DOFs or at max_levels levels; that level is solved exactly;
   * smoother: l1-Jacobi (Baker, Falgout, Kolev and Yang, SIAM J. Sci. Comput.
-    2011), x <- x + omega D1^-1 (b - A x) with D1_ii = sum_j |A_ij|, which
-    converges for every SPD A at omega = 1 without a spectral estimate;
-    nu_pre sweeps from x = 0 before, nu_post after the coarse correction;
+    2011), x <- x + omega D1^-1 (b - A x), with the l1 row sums taken over
+    the unassembled element matrices, D1_ii = sum_E sum_j |(A_E)_ij| (1 on
+    fixed DOFs), which needs no assembled matrix; D1_ii >= sum_j |A_ij|, so
+    lambda_max(D1^-1 A) <= 1 and the sweep converges for 0 < omega < 2
+    without a spectral estimate; nu_pre sweeps from x = 0 before, nu_post
+    after the coarse correction;
+  * the element matrices of a level: E_e D_e KE D_e on the finest (D_e the
+    0/1 diagonal of the element's free DOFs); on a coarse level, the
+    Galerkin product of coarse element E alone, Phat_E^T (sum over E's
+    children c of B_c^T A_c B_c) Phat_E with Phat_E the columns of Phat at
+    E's DOFs -- their assembly is the Galerkin operator above;
   * the outer CG takes z = V(r) with the Polak-Ribiere form of beta
     (flexible CG), so a preconditioner applied in lower precision keeps the
     iteration convergent.
@@ -112,8 +120,46 @@ class Level:
     dims: tuple
     A: sp.csr_matrix          # masked operator of this level
     fixed: np.ndarray         # bool [n_dof]
-    d1inv: np.ndarray         # 1 / sum_j |A_ij|
+    Ke: np.ndarray            # [n_elem, 24, 24] element matrices (masked)
+    d1inv: np.ndarray         # 1 / (element-wise l1 row sums), 1 on fixed DOFs
     P: sp.csr_matrix | None   # Phat from the next coarser level to this one
+
+
+def fine_element_matrices(KE, E, edof, fixed_dofs):
+    free = (~np.asarray(fixed_dofs, bool)[edof]).astype(float)          # [n, 24]
+    return E[:, None, None] * KE[None] * free[:, :, None] * free[:, None, :]
+
+
+def coarse_element_matrices(n, Ke, Phat):
+    """Galerkin matrix of each coarse element from its children's matrices."""
+    nx, ny, nz = n
+    mx, my, mz = coarse_dims(n)
+    edof_f = fem.edof_table_fast(nx, ny, nz)
+    edof_c = fem.edof_table_fast(mx, my, mz)
+    out = np.zeros((mx * my * mz, 24, 24))
+    for K in range(mz):
+        for J in range(my):
+            for I in range(mx):
+                kids = [i + nx * (j + ny * k)
+                        for k in (2 * K, 2 * K + 1) for j in (2 * J, 2 * J + 1)
+                        for i in (2 * I, 2 * I + 1) if i < nx and j < ny and k < nz]
+                F = np.unique(edof_f[kids].reshape(-1))
+                pos = {d: t for t, d in enumerate(F)}
+                Kloc = np.zeros((len(F), len(F)))
+                for c in kids:
+                    ix = [pos[d] for d in edof_f[c]]
+                    Kloc[np.ix_(ix, ix)] += Ke[c]
+                e = I + mx * (J + my * K)
+                Ploc = Phat[F][:, edof_c[e]].toarray()
+                out[e] = Ploc.T @ Kloc @ Ploc
+    return out
+
+
+def l1_inverse(Ke, edof, fixed_dofs, n_dof):
+    rows = np.abs(Ke).sum(axis=2)                                        # [n, 24]
+    d1 = np.bincount(edof.reshape(-1), weights=rows.reshape(-1), minlength=n_dof)
+    d1[np.asarray(fixed_dofs, bool)] = 1.0
+    return 1.0 / d1
 
 
 @dataclass
@@ -132,16 +178,18 @@ def build(KE, E, nelx, nely, nelz, fixed_dofs, max_levels=8, coarse_max_dofs=200
     n_dof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
     fixed = np.asarray(fixed_dofs, bool)
     A = masked_operator(KE, E, edof, n_dof, fixed)
+    Ke = fine_element_matrices(KE, E, edof, fixed)
     levels = []
     for li, n in enumerate(dims):
-        d1 = np.asarray(abs(A).sum(axis=1)).reshape(-1)
-        lev = Level(n, A, fixed, 1.0 / d1, None)
+        edof_l = fem.edof_table_fast(*n)
+        lev = Level(n, A, fixed, Ke, l1_inverse(Ke, edof_l, fixed, A.shape[0]), None)
         levels.append(lev)
         if li + 1 < len(dims):
             cf = coarse_fixed(n, fixed)
             Ph = sp.diags((~fixed).astype(float)) @ prolong_dofs(n) @ sp.diags((~cf).astype(float))
             lev.P = Ph.tocsr()
             A = (lev.P.T @ A @ lev.P + sp.diags(cf.astype(float))).tocsr()
+            Ke = coarse_element_matrices(n, Ke, lev.P)
             fixed = cf
     coarse_inv = np.linalg.inv(levels[-1].A.toarray())
     return Hierarchy(levels, coarse_inv, omega, nu_pre, nu_post)

@@ -6,6 +6,7 @@ positive operator, the two-level cycle without smoothing is the coarse-grid
 correction, the l1-Jacobi bound, and V-cycle CG against Jacobi-PCG."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from oracle import fem, gmg, solve, filter as cone
 from paper_2604_18020_gb300 import workloads as W
@@ -113,6 +114,20 @@ def test_single_level_is_exact_solve():
     edof = fem.edof_table_fast(4, 2, 2)
     u, st = gmg.pcg(H, lambda v: fem.kv(KE, E, edof, v, fd), P.f, np.zeros(m.n_dof), 1e-10)
     assert st.iterations == 1 and st.true_rel_residual <= 1e-12
+
+
+def test_element_matrices_assemble_to_galerkin_operator():
+    """The per-element Galerkin matrices of every level sum to the global
+    product Phat^T A Phat (masked), and the fine ones to the masked K."""
+    m, fd, E, KE, H = _hierarchy((5, 4, 3), coarse_max_dofs=1)
+    for lev in H.levels:
+        edof = fem.edof_table_fast(*lev.dims)
+        n = lev.A.shape[0]
+        rows = np.repeat(edof, 24, axis=1).reshape(-1)
+        cols = np.tile(edof, (1, 24)).reshape(-1)
+        S = sp.coo_matrix((lev.Ke.reshape(-1), (rows, cols)), shape=(n, n)).toarray()
+        S[lev.fixed, lev.fixed] = 1.0
+        assert np.abs(S - lev.A.toarray()).max() <= 1e-12 * np.abs(S).max()
 
 
 def test_l1_jacobi_bound():
