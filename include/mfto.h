@@ -660,6 +660,55 @@ mfto_status mfto_compliance_sens_noalloc(const mfto_mesh* mesh, double E0, doubl
                                          const double* d_u, double* d_dc, double* h_c_out,
                                          void* stream);
 
+/* ------------------------------------------------ geometric multigrid -- */
+
+/* Geometric multigrid for the masked operator, the solver follow-on of Sec. 6
+ * ("Path to Geometric Multigrid Integration": restriction, prolongation
+ * P = R^T, a direct coarsest solve, smoothing steps that apply the operator)
+ * with the FP32 K.v as the fine smoother (Sec. 3.5, "Path forward").
+ * Levels: level 0 is the handle's mesh; level l + 1 has ceil(n / 2) elements
+ * per axis of level l's n; coarsening stops at the first level with at most
+ * coarse_max_dofs DOFs, or after max_levels levels.  Interpolation is
+ * trilinear from the coarse nodes (fine coordinates 2I) with the fine fixed
+ * DOFs zeroed; a coarse DOF is fixed where the fine DOF at its position is;
+ * each coarse level is the Galerkin product Phat^T A Phat (formed element by
+ * element: each coarse element's 24 x 24 matrix from its children's) plus the
+ * identity on its fixed DOFs.  V-cycle: nu_pre l1-Jacobi sweeps
+ * x += omega D1^-1 (b - A x) from x = 0 (D1 the l1 row sums of the element
+ * matrices), residual, restriction, recursion, prolongation, nu_post sweeps;
+ * the coarsest level is solved by its dense inverse (FP64 Cholesky on the
+ * host, applied in FP32).  The cycle runs in FP32. */
+#define MFTO_GMG_MAX_LEVELS 10
+#define MFTO_GMG_MAX_COARSE 1000   /* DOFs of the densely inverted level */
+typedef struct {
+  int32_t max_levels;       /* 1 .. MFTO_GMG_MAX_LEVELS (default 10)      */
+  int32_t coarse_max_dofs;  /* 3 .. MFTO_GMG_MAX_COARSE (default 200)     */
+  int32_t nu_pre, nu_post;  /* 0 .. 8 sweeps (default 2, 2)               */
+  double omega;             /* l1-Jacobi weight in (0, 2) (default 1.3)   */
+} mfto_gmg_params;
+void mfto_default_gmg_params(mfto_gmg_params* p);
+/* Build the hierarchy for the moduli d_E (FP64 [elements]) with params p
+ * (NULL: the handle's current ones, initially the defaults).  Synchronises
+ * the stream (the coarsest inverse is formed on the host).  MFTO_TOO_LARGE
+ * when the coarsest level would exceed MFTO_GMG_MAX_COARSE DOFs,
+ * MFTO_BREAKDOWN when it is not positive definite. */
+mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E, const mfto_gmg_params* p);
+/* Levels of the last setup: *n_levels and dims[3 * l + axis] elements. */
+mfto_status mfto_gmg_levels(mfto_handle* h, int32_t* n_levels, int32_t* dims);
+/* d_y = A_level d_x (FP32 [DOFs of that level]); level 0 is the FP32 K.v. */
+mfto_status mfto_gmg_apply(mfto_handle* h, int32_t level, const float* d_x, float* d_y);
+/* d_z = V(d_r), one V-cycle on FP32 fine vectors (d_r and d_z distinct). */
+mfto_status mfto_gmg_vcycle(mfto_handle* h, const float* d_r, float* d_z);
+/* K(E) u = f by CG preconditioned with the V-cycle (Polak-Ribiere beta, FP64
+ * vectors, K.v and dot products): setup for d_E, then iterations from the
+ * initial guess in d_u until ||r|| <= rtol ||f|| (the handle's rtol) or the
+ * handle's maxit.  Outcome in st (iterations = CG iterations). */
+mfto_status mfto_gmg_solve(mfto_handle* h, const double* d_E, const double* d_f, double* d_u,
+                           mfto_solve_stats* st);
+/* on != 0: mfto_simp_step solves with mfto_gmg_solve (params p, NULL keeps the
+ * current ones); on = 0: back to the solver of mfto_set_solver. */
+mfto_status mfto_set_gmg_solver(mfto_handle* h, int32_t on, const mfto_gmg_params* p);
+
 /* ------------------------------------- element-by-element microbenchmark -- */
 
 /* y = sum_e B_e^T (E_e KE) B_e v over an ARBITRARY element DOF table (no

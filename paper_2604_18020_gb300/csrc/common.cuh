@@ -142,6 +142,8 @@ struct mfto_handle {
   int32_t ir_mode;          // MFTO_IR_RESTART or MFTO_IR_CONTINUE (mfto_set_ir_mode)
   // learned solve (learned.cu): network, correction period and its buffers
   struct LearnedWs* learned;
+  // geometric multigrid hierarchy and V-cycle solver (gmg.cu)
+  struct GmgWs* gmg;
   // PCG graph cache: one captured chunk of check_every iterations per solver
   struct PcgGraph* pcg_graph[MFTO_PCG_SLOTS];
   // kernels launched on behalf of this handle (graph kernel nodes included)
@@ -598,6 +600,10 @@ mfto_status learned_run(mfto_handle* h, const double* E, const double* rho_phys,
                         double* u, mfto_learned_stats* st);
 bool learned_active(const mfto_handle* h);
 void learned_release(mfto_handle* h);
+bool gmg_active(const mfto_handle* h);
+void gmg_release(mfto_handle* h);
+mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* u,
+                      mfto_solve_stats* st);
 void mode_coefficients(double nu, double h, ModeCoef<double>* c64, ModeCoef<float>* c32);
 mfto_status tc_init(mfto_handle* h);
 mfto_status multi_init(mfto_handle* h);

@@ -1,0 +1,1032 @@
+// Geometric multigrid preconditioner for the masked stiffness operator: the
+// follow-on the paper proposes (Sec. 6, "Path to Geometric Multigrid
+// Integration": restriction R, prolongation P = R^T, a direct coarsest solve,
+// smoothing steps that each apply the operator; Sec. 3.5, "Path forward": the
+// low-precision K.v as the smoother inside a V-cycle).
+//
+// Hierarchy (rebuilt for every modulus field):
+//   level 0 is the mesh itself, applied by the FP32 structured K.v;
+//   level l + 1 halves the element counts of level l per axis, rounding up;
+//   its element matrices are Galerkin products of the children's:
+//     A_E = sum_{children c} P_c^T A_c P_c,
+//   P_c (24 x 24) the trilinear interpolation from E's 8 corners to child c's
+//   8 nodes (per axis weights 1 - s, s at the child's node, s in {0, 1/2, 1}),
+//   A_c = E_c D_c KE D_c on level 0 (D_c zeroes the child's fixed DOFs) or the
+//   child's stored matrix; rows and columns of E's fixed DOFs are then zeroed.
+//   For nested trilinear spaces the assembly of these matrices is exactly
+//   Phat^T A Phat, Phat = M_f P M_c (the masked interpolation), so every level
+//   is the Galerkin operator plus the identity on its fixed DOFs.  A coarse
+//   DOF is fixed where the fine DOF at the same position is.
+// V-cycle: nu_pre l1-Jacobi sweeps from x = 0, residual, restriction,
+// recursion, prolongation, nu_post sweeps; the coarsest level is solved with
+// its dense inverse (Cholesky on the host in FP64, stored as FP32).  The
+// l1 row sums come from the element matrices, D1 = sum_E sum_j |(A_E)_ij|
+// (1 on fixed DOFs), so lambda_max(D1^-1 A) <= 1 and any weight in (0, 2)
+// smooths.  Coarse levels apply their operator node by node from the element
+// matrices (each node sums its rows of its <= 8 elements: no atomics).
+// Outer solver: FP64 CG with z = V(r) (FP32 inside the cycle) and the
+// Polak-Ribiere beta, FP64 K.v and fixed-order FP64 reductions.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+struct GmgScalars {
+  double sum[4];
+  unsigned int ticket;
+};
+
+struct GmgLevel {
+  int nx = 0, ny = 0, nz = 0;
+  int64_t n_elem = 0, n_node = 0, n_dof = 0;
+  uint8_t* d_fixed = nullptr;   // per-node mask (level 0: the handle's, not owned)
+  float* d_K = nullptr;         // [n_elem][576] element matrices (levels >= 1)
+  float* d_dinv = nullptr;      // 1 / l1 row sums
+  float* x = nullptr;           // correction (levels >= 1)
+  float* b = nullptr;           // right-hand side (levels >= 1)
+  float* t = nullptr;           // operator applied to x
+};
+
+struct GmgWs {
+  int n_levels = 0;
+  GmgLevel lv[MFTO_GMG_MAX_LEVELS];
+  mfto_gmg_params prm{};
+  float* d_E32 = nullptr;
+  float* d_cinv = nullptr;          // dense inverse of the coarsest operator
+  int n_c = 0;                      // its DOFs
+  std::vector<std::vector<uint8_t>> h_fixed;   // per-level node masks
+  GmgScalars* d_s = nullptr;
+  GmgScalars* h_s = nullptr;
+  bool ready = false;               // a hierarchy is built
+  bool use_in_simp = false;         // mfto_simp_step solves with mfto_gmg_solve
+  // the V-cycle captured as a CUDA graph for one (r, z) pair and parameter set
+  cudaGraphExec_t vexec = nullptr;
+  const float* vkey_r = nullptr;
+  float* vkey_z = nullptr;
+  mfto_gmg_params vprm{};
+  int64_t vnodes = 0;               // kernels in the graph
+};
+
+namespace {
+
+constexpr int kB = MFTO_BLOCK;
+
+__host__ __device__ inline int64_t nid(int i, int j, int k, int nx, int ny) {
+  return i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
+}
+
+int g_sms = 148;   // SM count of the device (set from the handle at setup)
+
+int grid_of(int64_t n) {
+  const int64_t want = (n + kB - 1) / kB;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, 16LL * g_sms));
+}
+
+// trilinear weight of coarse local node m at child ch's local node n
+__device__ __forceinline__ float phi(int ch, int n, int m) {
+  float w = 1.0f;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int p = ((ch >> ax) & 1) + ((n >> ax) & 1);   // 0, 1, 2 in fine units
+    w *= ((m >> ax) & 1) ? 0.5f * p : 1.0f - 0.5f * p;
+  }
+  return w;
+}
+
+__global__ void __launch_bounds__(kB) gmg_cast(const double* __restrict__ a, float* __restrict__ b,
+                                               int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// l1 row sums of level 0 from E_e D_e KE D_e, node by node
+__global__ void __launch_bounds__(kB)
+gmg_l1_fine(const float* __restrict__ E, const uint8_t* __restrict__ fixed,
+            const float* __restrict__ ke, int nx, int ny, int nz, float* __restrict__ dinv) {
+  __shared__ float ka[576];
+  for (int i = threadIdx.x; i < 576; i += blockDim.x) ka[i] = fabsf(ke[i]);
+  __syncthreads();
+  const int64_t n_node = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  for (int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nd < n_node;
+       nd += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(nd % (nx + 1));
+    const int j = (int)((nd / (nx + 1)) % (ny + 1));
+    const int k = (int)(nd / ((int64_t)(nx + 1) * (ny + 1)));
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int ex = i - dx, ey = j - dy, ez = k - dz;
+          if (ex < 0 || ey < 0 || ez < 0 || ex >= nx || ey >= ny || ez >= nz) continue;
+          const int l = dx + 2 * dy + 4 * dz;
+          uint8_t fm[8];
+#pragma unroll
+          for (int lb = 0; lb < 8; ++lb)
+            fm[lb] = fixed[nid(ex + (lb & 1), ey + ((lb >> 1) & 1), ez + (lb >> 2), nx, ny)];
+          const float Ee = E[ex + (int64_t)nx * (ey + (int64_t)ny * ez)];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float s = 0.0f;
+#pragma unroll
+            for (int lb = 0; lb < 8; ++lb)
+#pragma unroll
+              for (int cb = 0; cb < 3; ++cb)
+                if (!((fm[lb] >> cb) & 1)) s += ka[(3 * l + c) * 24 + 3 * lb + cb];
+            acc[c] += (double)Ee * s;
+          }
+        }
+    const uint8_t fm = fixed[nd];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      dinv[3 * nd + c] = ((fm >> c) & 1) ? 1.0f : (float)(1.0 / acc[c]);
+  }
+}
+
+// Element matrices of level l + 1 (dims mx, my, mz) from level l (nx, ny, nz):
+// one CTA per coarse element, children one after another through shared
+// memory (T = A_c P_c, then M += P_c^T T), M held in registers.
+template <bool FINE0>
+__global__ void __launch_bounds__(kB)
+gmg_galerkin(const float* __restrict__ Kf, const float* __restrict__ E,
+             const float* __restrict__ ke, const uint8_t* __restrict__ fixf, int nx, int ny,
+             int nz, const uint8_t* __restrict__ fixc, int mx, int my, int mz,
+             float* __restrict__ Kc) {
+  __shared__ float A[576], T[576], KEs[576];
+  if (FINE0)
+    for (int i = threadIdx.x; i < 576; i += blockDim.x) KEs[i] = ke[i];
+  const int64_t n_c = (int64_t)mx * my * mz;
+  for (int64_t e = blockIdx.x; e < n_c; e += gridDim.x) {
+    const int I = (int)(e % mx), J = (int)((e / mx) % my), K = (int)(e / ((int64_t)mx * my));
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    for (int ch = 0; ch < 8; ++ch) {
+      const int fx = 2 * I + (ch & 1), fy = 2 * J + ((ch >> 1) & 1), fz = 2 * K + (ch >> 2);
+      if (fx >= nx || fy >= ny || fz >= nz) continue;            // uniform over the CTA
+      const int64_t c = fx + (int64_t)nx * (fy + (int64_t)ny * fz);
+      __syncthreads();                                            // A, T free again
+      for (int idx = threadIdx.x; idx < 576; idx += blockDim.x) {
+        if (FINE0) {
+          const int r = idx / 24, q = idx - 24 * (idx / 24);
+          const int nr = r / 3, nq = q / 3;
+          const uint8_t fr = fixf[nid(fx + (nr & 1), fy + ((nr >> 1) & 1), fz + (nr >> 2), nx, ny)];
+          const uint8_t fq = fixf[nid(fx + (nq & 1), fy + ((nq >> 1) & 1), fz + (nq >> 2), nx, ny)];
+          const bool free_rq = !((fr >> (r % 3)) & 1) && !((fq >> (q % 3)) & 1);
+          A[idx] = free_rq ? E[c] * KEs[idx] : 0.0f;
+        } else {
+          A[idx] = Kf[c * 576 + idx];
+        }
+      }
+      __syncthreads();
+      // T[i][3m + cc] = sum_n A[i][3n + cc] phi(ch, n, m)
+      for (int idx = threadIdx.x; idx < 576; idx += blockDim.x) {
+        const int i = idx / 24, col = idx - 24 * (idx / 24);
+        const int m = col / 3, cc = col - 3 * (col / 3);
+        float s = 0.0f;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) s = fmaf(A[i * 24 + 3 * n + cc], phi(ch, n, m), s);
+        T[idx] = s;
+      }
+      __syncthreads();
+      // M[3m + cc][q] += sum_n phi(ch, n, m) T[3n + cc][q]
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int idx = threadIdx.x + r * kB;
+        if (idx < 576) {
+          const int row = idx / 24, q = idx - 24 * (idx / 24);
+          const int m = row / 3, cc = row - 3 * (row / 3);
+          float s = 0.0f;
+#pragma unroll
+          for (int n = 0; n < 8; ++n) s = fmaf(phi(ch, n, m), T[(3 * n + cc) * 24 + q], s);
+          acc[r] += s;
+        }
+      }
+    }
+    // zero the rows and columns of E's fixed DOFs
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int idx = threadIdx.x + r * kB;
+      if (idx < 576) {
+        const int row = idx / 24, q = idx - 24 * (idx / 24);
+        const int nr = row / 3, nq = q / 3;
+        const uint8_t fr = fixc[nid(I + (nr & 1), J + ((nr >> 1) & 1), K + (nr >> 2), mx, my)];
+        const uint8_t fq = fixc[nid(I + (nq & 1), J + ((nq >> 1) & 1), K + (nq >> 2), mx, my)];
+        const bool free_rq = !((fr >> (row % 3)) & 1) && !((fq >> (q % 3)) & 1);
+        Kc[e * 576 + idx] = free_rq ? acc[r] : 0.0f;
+      }
+    }
+  }
+}
+
+// l1 row sums of a coarse level from its element matrices
+__global__ void __launch_bounds__(kB)
+gmg_l1_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, int nx, int ny,
+              int nz, float* __restrict__ dinv) {
+  const int64_t n_node = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  for (int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nd < n_node;
+       nd += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(nd % (nx + 1));
+    const int j = (int)((nd / (nx + 1)) % (ny + 1));
+    const int k = (int)(nd / ((int64_t)(nx + 1) * (ny + 1)));
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int ex = i - dx, ey = j - dy, ez = k - dz;
+          if (ex < 0 || ey < 0 || ez < 0 || ex >= nx || ey >= ny || ez >= nz) continue;
+          const int l = dx + 2 * dy + 4 * dz;
+          const float* Ke = K + (ex + (int64_t)nx * (ey + (int64_t)ny * ez)) * 576;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float s = 0.0f;
+            for (int q = 0; q < 24; ++q) s += fabsf(Ke[(3 * l + c) * 24 + q]);
+            acc[c] += s;
+          }
+        }
+    const uint8_t fm = fixed[nd];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      dinv[3 * nd + c] = ((fm >> c) & 1) ? 1.0f : (float)(1.0 / acc[c]);
+  }
+}
+
+// y = A x on a coarse level: 8 lanes per node, lane s taking the node's three
+// rows of adjacent element s (corner offsets the bits of s), summed over the
+// 8 lanes in a fixed order; identity rows on fixed DOFs (their columns are
+// zero in the element matrices)
+__global__ void __launch_bounds__(kB)
+gmg_kv_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, int nx, int ny,
+              int nz, const float* __restrict__ x, float* __restrict__ y) {
+  const int64_t n_node = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const int sub = threadIdx.x & 7;
+  const int dx = sub & 1, dy = (sub >> 1) & 1, dz = sub >> 2;
+  // every lane of a warp runs the same number of trips (the shuffles need all 32)
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+  const int64_t trips = (n_node + groups - 1) / groups;
+  for (int64_t tr = 0; tr < trips; ++tr) {
+    const int64_t nd = tr * groups + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3);
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    if (nd < n_node) {
+      const int i = (int)(nd % (nx + 1));
+      const int j = (int)((nd / (nx + 1)) % (ny + 1));
+      const int k = (int)(nd / ((int64_t)(nx + 1) * (ny + 1)));
+      const int ex = i - dx, ey = j - dy, ez = k - dz;
+      if (ex >= 0 && ey >= 0 && ez >= 0 && ex < nx && ey < ny && ez < nz) {
+        const int l = dx + 2 * dy + 4 * dz;
+        const float* Ke = K + (ex + (int64_t)nx * (ey + (int64_t)ny * ez)) * 576;
+        float xe[24];
+#pragma unroll
+        for (int lb = 0; lb < 8; ++lb) {
+          const int64_t m = nid(ex + (lb & 1), ey + ((lb >> 1) & 1), ez + (lb >> 2), nx, ny);
+          xe[3 * lb] = x[3 * m];
+          xe[3 * lb + 1] = x[3 * m + 1];
+          xe[3 * lb + 2] = x[3 * m + 2];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float4* row = reinterpret_cast<const float4*>(Ke + (3 * l + c) * 24);
+          float s = 0.0f;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            const float4 w = row[q];
+            s = fmaf(w.x, xe[4 * q], s);
+            s = fmaf(w.y, xe[4 * q + 1], s);
+            s = fmaf(w.z, xe[4 * q + 2], s);
+            s = fmaf(w.w, xe[4 * q + 3], s);
+          }
+          acc[c] = s;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
+      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 4);
+    }
+    if (sub < 3 && nd < n_node) {
+      const uint8_t fm = fixed[nd];
+      const float a = sub == 0 ? acc[0] : (sub == 1 ? acc[1] : acc[2]);
+      y[3 * nd + sub] = ((fm >> sub) & 1) ? x[3 * nd + sub] : a;
+    }
+  }
+}
+
+// x = omega dinv b (first sweep from x = 0) or x += omega dinv (b - t)
+__global__ void __launch_bounds__(kB)
+gmg_smooth(float* __restrict__ x, const float* __restrict__ b, const float* __restrict__ t,
+           const float* __restrict__ dinv, int64_t n, float omega, int first) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (first) x[i] = omega * dinv[i] * b[i];
+    else x[i] += omega * dinv[i] * (b[i] - t[i]);
+  }
+}
+
+// bc = Phat^T (b - t) (t = NULL: the residual is b); zero on fixed coarse
+// DOFs.  One thread per coarse DOF.
+__global__ void __launch_bounds__(kB)
+gmg_restrict(const float* __restrict__ bf, const float* __restrict__ tf,
+             const uint8_t* __restrict__ fixf, int nx, int ny, int nz,
+             const uint8_t* __restrict__ fixc, int mx, int my, int mz, float* __restrict__ bc) {
+  const int64_t n_cd = 3 * (int64_t)(mx + 1) * (my + 1) * (mz + 1);
+  for (int64_t cd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cd < n_cd;
+       cd += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cn = cd / 3;
+    const int c = (int)(cd - 3 * cn);
+    if ((fixc[cn] >> c) & 1) {
+      bc[cd] = 0.0f;
+      continue;
+    }
+    const int I = (int)(cn % (mx + 1));
+    const int J = (int)((cn / (mx + 1)) % (my + 1));
+    const int K = (int)(cn / ((int64_t)(mx + 1) * (my + 1)));
+    float acc = 0.0f;
+    for (int dk = -1; dk <= 1; ++dk) {
+      const int k = 2 * K + dk;
+      if (k < 0 || k > nz) continue;
+      const float wk = dk == 0 ? 1.0f : 0.5f;
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int j = 2 * J + dj;
+        if (j < 0 || j > ny) continue;
+        const float wjk = wk * (dj == 0 ? 1.0f : 0.5f);
+        for (int di = -1; di <= 1; ++di) {
+          const int i = 2 * I + di;
+          if (i < 0 || i > nx) continue;
+          const int64_t f = nid(i, j, k, nx, ny);
+          if ((fixf[f] >> c) & 1) continue;
+          const float w = wjk * (di == 0 ? 1.0f : 0.5f);
+          const float r = tf ? bf[3 * f + c] - tf[3 * f + c] : bf[3 * f + c];
+          acc = fmaf(w, r, acc);
+        }
+      }
+    }
+    bc[cd] = acc;
+  }
+}
+
+// xf += Phat xc on the free fine DOFs
+__global__ void __launch_bounds__(kB)
+gmg_prolong(const float* __restrict__ xc, const uint8_t* __restrict__ fixc, int mx, int my,
+            const uint8_t* __restrict__ fixf, int nx, int ny, int nz, float* __restrict__ xf) {
+  const int64_t n_fn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n_fn;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(f % (nx + 1));
+    const int j = (int)((f / (nx + 1)) % (ny + 1));
+    const int k = (int)(f / ((int64_t)(nx + 1) * (ny + 1)));
+    const uint8_t fm = fixf[f];
+    if (fm == 7) continue;
+    const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+    const int k0 = k >> 1, k1 = (k + 1) >> 1;
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    for (int a = 0; a < 2; ++a) {
+      const int K = a ? k1 : k0;
+      if (a && k1 == k0) continue;
+      const float wk = (k1 == k0) ? 1.0f : 0.5f;
+      for (int b = 0; b < 2; ++b) {
+        const int J = b ? j1 : j0;
+        if (b && j1 == j0) continue;
+        const float wjk = wk * ((j1 == j0) ? 1.0f : 0.5f);
+        for (int d = 0; d < 2; ++d) {
+          const int I = d ? i1 : i0;
+          if (d && i1 == i0) continue;
+          const float w = wjk * ((i1 == i0) ? 1.0f : 0.5f);
+          const int64_t cn = nid(I, J, K, mx, my);
+          const uint8_t cm = fixc[cn];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (!((cm >> c) & 1)) acc[c] = fmaf(w, xc[3 * cn + c], acc[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (!((fm >> c) & 1)) xf[3 * f + c] += acc[c];
+  }
+}
+
+// x = Cinv b, one warp per row
+__global__ void __launch_bounds__(kB)
+gmg_coarse_solve(const float* __restrict__ cinv, const float* __restrict__ b,
+                 float* __restrict__ x, int n) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int r = w; r < n; r += nw) {
+    float s = 0.0f;
+    for (int q = lane; q < n; q += 32) s = fmaf(cinv[(int64_t)r * n + q], b[q], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[r] = s;
+  }
+}
+
+// ---- outer FP64 CG kernels (fixed-order reductions through the handle's partials)
+
+// r = f - q, r32 = r; sums r.r, f.f -> s[0], s[1]
+__global__ void __launch_bounds__(kB)
+gmg_resid0(const double* __restrict__ f, const double* __restrict__ q, double* __restrict__ r,
+           float* __restrict__ r32, int64_t n, GmgScalars* s, double* partials) {
+  __shared__ double sh[64];
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = f[i] - q[i];
+    r[i] = ri;
+    r32[i] = (float)ri;
+    acc[0] += ri * ri;
+    acc[1] += f[i] * f[i];
+  }
+  double tot[2];
+  if (last_block_reduce<2>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0) {
+    s->sum[0] = tot[0];
+    s->sum[1] = tot[1];
+  }
+}
+
+// z = z32; sums r.z, z.r_old -> s[0], s[1]
+__global__ void __launch_bounds__(kB)
+gmg_zdot(const float* __restrict__ z32, const double* __restrict__ r,
+         const double* __restrict__ r_old, double* __restrict__ z, int64_t n, int first,
+         GmgScalars* s, double* partials) {
+  __shared__ double sh[64];
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (double)z32[i];
+    z[i] = zi;
+    acc[0] += r[i] * zi;
+    if (!first) acc[1] += r_old[i] * zi;
+  }
+  double tot[2];
+  if (last_block_reduce<2>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0) {
+    s->sum[0] = tot[0];
+    s->sum[1] = tot[1];
+  }
+}
+
+__global__ void __launch_bounds__(kB)
+gmg_dir(const double* __restrict__ z, double* __restrict__ p, double beta, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// p.q -> s[3]
+__global__ void __launch_bounds__(kB)
+gmg_pq(const double* __restrict__ p, const double* __restrict__ q, int64_t n, GmgScalars* s,
+       double* partials) {
+  __shared__ double sh[64];
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc[0] += p[i] * q[i];
+  double tot[1];
+  if (last_block_reduce<1>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0)
+    s->sum[3] = tot[0];
+}
+
+// u += alpha p; r_old = r; r -= alpha q; r32 = r; r.r -> s[2]
+__global__ void __launch_bounds__(kB)
+gmg_update(double* __restrict__ u, double* __restrict__ r, double* __restrict__ r_old,
+           const double* __restrict__ p, const double* __restrict__ q, float* __restrict__ r32,
+           double alpha, int64_t n, GmgScalars* s, double* partials) {
+  __shared__ double sh[64];
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    u[i] += alpha * p[i];
+    const double ro = r[i];
+    r_old[i] = ro;
+    const double rn = ro - alpha * q[i];
+    r[i] = rn;
+    r32[i] = (float)rn;
+    acc[0] += rn * rn;
+  }
+  double tot[1];
+  if (last_block_reduce<1>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0)
+    s->sum[2] = tot[0];
+}
+
+// ---------------------------------------------------------------- host side
+
+void level_dims(const mfto_handle* h, const mfto_gmg_params& p, int* n_levels, int dims[][3]) {
+  int nx = h->mesh.nelx, ny = h->mesh.nely, nz = h->mesh.nelz;
+  int L = 0;
+  dims[0][0] = nx; dims[0][1] = ny; dims[0][2] = nz;
+  L = 1;
+  while (L < p.max_levels) {
+    const int64_t dofs = 3LL * (nx + 1) * (ny + 1) * (nz + 1);
+    if (dofs <= p.coarse_max_dofs || (nx == 1 && ny == 1 && nz == 1)) break;
+    nx = (nx + 1) / 2; ny = (ny + 1) / 2; nz = (nz + 1) / 2;
+    dims[L][0] = nx; dims[L][1] = ny; dims[L][2] = nz;
+    ++L;
+  }
+  *n_levels = L;
+}
+
+void drop_graph(GmgWs* w) {
+  if (w->vexec) cudaGraphExecDestroy(w->vexec);
+  w->vexec = nullptr;
+  w->vkey_r = nullptr;
+  w->vkey_z = nullptr;
+}
+
+void free_levels(GmgWs* w) {
+  drop_graph(w);
+  for (int l = 0; l < MFTO_GMG_MAX_LEVELS; ++l) {
+    GmgLevel& v = w->lv[l];
+    if (l > 0 && v.d_fixed) cudaFree(v.d_fixed);
+    void* ptrs[] = {v.d_K, v.d_dinv, v.x, v.b, v.t};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+    v = GmgLevel();
+  }
+  if (w->d_cinv) cudaFree(w->d_cinv);
+  w->d_cinv = nullptr;
+  w->n_levels = 0;
+  w->ready = false;
+}
+
+mfto_status gmg_alloc(mfto_handle* h, GmgWs* w, const mfto_gmg_params& p) {
+  int L;
+  int dims[MFTO_GMG_MAX_LEVELS][3];
+  level_dims(h, p, &L, dims);
+  bool same = L == w->n_levels && w->d_cinv;
+  for (int l = 0; same && l < L; ++l)
+    same = w->lv[l].nx == dims[l][0] && w->lv[l].ny == dims[l][1] && w->lv[l].nz == dims[l][2];
+  if (same) return MFTO_OK;
+  free_levels(w);
+  const int64_t nc = 3LL * (dims[L - 1][0] + 1) * (dims[L - 1][1] + 1) * (dims[L - 1][2] + 1);
+  if (nc > MFTO_GMG_MAX_COARSE)
+    return mfto_fail(h, MFTO_TOO_LARGE,
+                     "mfto_gmg_setup: the coarsest level has %lld DOFs (at most %d): allow more "
+                     "levels", (long long)nc, MFTO_GMG_MAX_COARSE);
+  // per-level node masks on the host: level 0 from the handle
+  w->h_fixed.assign(L, {});
+  w->h_fixed[0].resize(h->n_node);
+  MFTO_CUDA(h, cudaMemcpy(w->h_fixed[0].data(), h->d_fixed, h->n_node, cudaMemcpyDeviceToHost));
+  for (int l = 1; l < L; ++l) {
+    const int nx = dims[l - 1][0], ny = dims[l - 1][1], nz = dims[l - 1][2];
+    const int mx = dims[l][0], my = dims[l][1], mz = dims[l][2];
+    std::vector<uint8_t>& fc = w->h_fixed[l];
+    fc.assign((size_t)(mx + 1) * (my + 1) * (mz + 1), 0);
+    for (int K = 0; K <= mz; ++K)
+      for (int J = 0; J <= my; ++J)
+        for (int I = 0; I <= mx; ++I)
+          if (2 * I <= nx && 2 * J <= ny && 2 * K <= nz)
+            fc[nid(I, J, K, mx, my)] = w->h_fixed[l - 1][nid(2 * I, 2 * J, 2 * K, nx, ny)];
+  }
+  w->n_levels = L;
+  for (int l = 0; l < L; ++l) {
+    GmgLevel& v = w->lv[l];
+    v.nx = dims[l][0]; v.ny = dims[l][1]; v.nz = dims[l][2];
+    v.n_elem = (int64_t)v.nx * v.ny * v.nz;
+    v.n_node = (int64_t)(v.nx + 1) * (v.ny + 1) * (v.nz + 1);
+    v.n_dof = 3 * v.n_node;
+    auto A = [&](void** ptr, size_t bytes) -> mfto_status {
+      const cudaError_t e = cudaMalloc(ptr, bytes);
+      if (e == cudaSuccess) return MFTO_OK;
+      cudaGetLastError();
+      free_levels(w);
+      return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: cudaMalloc of %zu bytes failed", bytes);
+    };
+    mfto_status s;
+    if (l == 0) {
+      v.d_fixed = h->d_fixed;
+    } else {
+      if ((s = A((void**)&v.d_fixed, v.n_node)) != MFTO_OK) return s;
+      MFTO_CUDA(h, cudaMemcpy(v.d_fixed, w->h_fixed[l].data(), v.n_node, cudaMemcpyHostToDevice));
+      if ((s = A((void**)&v.d_K, sizeof(float) * 576 * v.n_elem)) != MFTO_OK) return s;
+      if ((s = A((void**)&v.x, sizeof(float) * v.n_dof)) != MFTO_OK) return s;
+      if ((s = A((void**)&v.b, sizeof(float) * v.n_dof)) != MFTO_OK) return s;
+    }
+    if ((s = A((void**)&v.d_dinv, sizeof(float) * v.n_dof)) != MFTO_OK) return s;
+    if ((s = A((void**)&v.t, sizeof(float) * v.n_dof)) != MFTO_OK) return s;
+  }
+  w->n_c = (int)nc;
+  if (cudaMalloc((void**)&w->d_cinv, sizeof(float) * nc * nc) != cudaSuccess) {
+    cudaGetLastError();
+    free_levels(w);
+    return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: cudaMalloc of the coarse inverse failed");
+  }
+  return MFTO_OK;
+}
+
+// Dense inverse of the coarsest operator from its element matrices (FP64 on
+// the host: Cholesky, then the inverse column by column).
+mfto_status coarse_inverse(mfto_handle* h, GmgWs* w) {
+  const int L = w->n_levels - 1;
+  const GmgLevel& v = w->lv[L];
+  const int n = (int)v.n_dof;
+  std::vector<float> Ke((size_t)576 * v.n_elem);
+  if (L == 0) {   // single level: E_e D_e KE D_e from the moduli and the unit matrix
+    std::vector<float> E(v.n_elem), ke(576);
+    MFTO_CUDA(h, cudaMemcpyAsync(E.data(), w->d_E32, sizeof(float) * v.n_elem,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    MFTO_CUDA(h, cudaMemcpyAsync(ke.data(), h->d_ke32, sizeof(float) * 576,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int64_t e = 0; e < v.n_elem; ++e)
+      for (int q = 0; q < 576; ++q) Ke[e * 576 + q] = E[e] * ke[q];
+  } else {
+    MFTO_CUDA(h, cudaMemcpyAsync(Ke.data(), v.d_K, sizeof(float) * 576 * v.n_elem,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  const std::vector<uint8_t>& fx = w->h_fixed[L];
+  auto is_fixed = [&](int64_t dof) { return (fx[dof / 3] >> (dof % 3)) & 1; };
+  std::vector<double> Am((size_t)n * n, 0.0);
+  for (int ez = 0; ez < v.nz; ++ez)
+    for (int ey = 0; ey < v.ny; ++ey)
+      for (int ex = 0; ex < v.nx; ++ex) {
+        const int64_t e = ex + (int64_t)v.nx * (ey + (int64_t)v.ny * ez);
+        int64_t dof[24];
+        for (int lb = 0; lb < 8; ++lb) {
+          const int64_t m = nid(ex + (lb & 1), ey + ((lb >> 1) & 1), ez + (lb >> 2), v.nx, v.ny);
+          for (int c = 0; c < 3; ++c) dof[3 * lb + c] = 3 * m + c;
+        }
+        for (int a = 0; a < 24; ++a) {
+          if (is_fixed(dof[a])) continue;
+          for (int b = 0; b < 24; ++b)
+            if (!is_fixed(dof[b])) Am[dof[a] * n + dof[b]] += Ke[e * 576 + a * 24 + b];
+        }
+      }
+  for (int64_t d = 0; d < n; ++d)
+    if (is_fixed(d)) Am[d * n + d] = 1.0;
+  // Cholesky, lower triangle in place
+  for (int j = 0; j < n; ++j) {
+    double s = Am[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= Am[(size_t)j * n + k] * Am[(size_t)j * n + k];
+    if (!(s > 0.0) || !std::isfinite(s))
+      return mfto_fail(h, MFTO_BREAKDOWN, "mfto_gmg_setup: coarsest operator not positive definite");
+    const double d = sqrt(s);
+    Am[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = Am[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= Am[(size_t)i * n + k] * Am[(size_t)j * n + k];
+      Am[(size_t)i * n + j] = t / d;
+    }
+  }
+  std::vector<float> inv((size_t)n * n);
+  std::vector<double> col(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {       // L y = e_c
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= Am[(size_t)i * n + k] * col[k];
+      col[i] = t / Am[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+      double t = col[i];
+      for (int k = i + 1; k < n; ++k) t -= Am[(size_t)k * n + i] * col[k];
+      col[i] = t / Am[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = (float)col[i];
+  }
+  MFTO_CUDA(h, cudaMemcpy(w->d_cinv, inv.data(), sizeof(float) * inv.size(),
+                          cudaMemcpyHostToDevice));
+  return MFTO_OK;
+}
+
+mfto_status apply_level(mfto_handle* h, GmgWs* w, int l, const float* x, float* y) {
+  if (l == 0) return kv_launch(h, MFTO_FORM_F32, w->d_E32, x, y);
+  const GmgLevel& v = w->lv[l];
+  h->launches++;
+  gmg_kv_coarse<<<grid_of(8 * v.n_node), kB, 0, h->stream>>>(v.d_K, v.d_fixed, v.nx, v.ny, v.nz, x,
+                                                             y);
+  MFTO_LAUNCH_CHECK(h);
+  return MFTO_OK;
+}
+
+mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x) {
+  const int L = w->n_levels - 1;
+  const GmgLevel& v = w->lv[l];
+  const mfto_gmg_params& p = w->prm;
+  mfto_status s;
+  if (l == L) {
+    h->launches++;
+    gmg_coarse_solve<<<std::max(1, std::min(1024, (w->n_c + 7) / 8)), kB, 0, h->stream>>>(
+        w->d_cinv, b, x, w->n_c);
+    MFTO_LAUNCH_CHECK(h);
+    return MFTO_OK;
+  }
+  const int g = grid_of(v.n_dof);
+  const float om = (float)p.omega;
+  for (int k = 0; k < p.nu_pre; ++k) {
+    if (k > 0 && (s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
+    h->launches++;
+    gmg_smooth<<<g, kB, 0, h->stream>>>(x, b, v.t, v.d_dinv, v.n_dof, om, k == 0);
+    MFTO_LAUNCH_CHECK(h);
+  }
+  if (p.nu_pre == 0) MFTO_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * v.n_dof, h->stream));
+  else if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
+  const GmgLevel& c = w->lv[l + 1];
+  h->launches++;
+  gmg_restrict<<<grid_of(c.n_dof), kB, 0, h->stream>>>(
+      b, p.nu_pre ? v.t : nullptr, v.d_fixed, v.nx, v.ny, v.nz, c.d_fixed, c.nx, c.ny, c.nz, c.b);
+  MFTO_LAUNCH_CHECK(h);
+  if ((s = vcycle(h, w, l + 1, c.b, c.x)) != MFTO_OK) return s;
+  h->launches++;
+  gmg_prolong<<<grid_of(v.n_node), kB, 0, h->stream>>>(c.x, c.d_fixed, c.nx, c.ny, v.d_fixed,
+                                                       v.nx, v.ny, v.nz, x);
+  MFTO_LAUNCH_CHECK(h);
+  for (int k = 0; k < p.nu_post; ++k) {
+    if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
+    h->launches++;
+    gmg_smooth<<<g, kB, 0, h->stream>>>(x, b, v.t, v.d_dinv, v.n_dof, om, 0);
+    MFTO_LAUNCH_CHECK(h);
+  }
+  return MFTO_OK;
+}
+
+// The V-cycle for (r, z) as one graph launch: captured on the handle's
+// private capture stream the first time (and again when the buffers, the
+// parameters or the hierarchy's storage change), replayed on the stream.
+mfto_status vcycle_graph(mfto_handle* h, GmgWs* w, const float* r, float* z) {
+  const bool same = w->vexec && w->vkey_r == r && w->vkey_z == z &&
+                    memcmp(&w->vprm, &w->prm, sizeof(mfto_gmg_params)) == 0;
+  if (!same) {
+    drop_graph(w);
+    if (!h->cap_stream &&
+        cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return mfto_fail(h, MFTO_CUDA_ERROR, "V-cycle graph: cannot create the capture stream");
+    cudaStream_t saved = h->stream;
+    const bool timing = h->kv_timing;
+    const int64_t launches = h->launches;
+    h->kv_timing = false;
+    h->stream = h->cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    mfto_status s = e == cudaSuccess ? vcycle(h, w, 0, r, z) : MFTO_CUDA_ERROR;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(h->cap_stream, &graph);
+    h->stream = saved;
+    h->kv_timing = timing;
+    w->vnodes = h->launches - launches;
+    h->launches = launches;
+    if (s != MFTO_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return s != MFTO_OK ? s
+                          : mfto_fail(h, MFTO_CUDA_ERROR, "V-cycle graph capture: %s",
+                                      cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&w->vexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      w->vexec = nullptr;
+      return mfto_fail(h, MFTO_CUDA_ERROR, "V-cycle graph instantiate: %s", cudaGetErrorString(e));
+    }
+    w->vkey_r = r;
+    w->vkey_z = z;
+    w->vprm = w->prm;
+  }
+  MFTO_CUDA(h, cudaGraphLaunch(w->vexec, h->stream));
+  h->launches += w->vnodes;
+  return MFTO_OK;
+}
+
+mfto_status check_params(mfto_handle* h, const mfto_gmg_params& p) {
+  MFTO_REQUIRE(h, p.max_levels >= 1 && p.max_levels <= MFTO_GMG_MAX_LEVELS,
+               "mfto_gmg_setup: max_levels in [1, MFTO_GMG_MAX_LEVELS]");
+  MFTO_REQUIRE(h, p.coarse_max_dofs >= 3 && p.coarse_max_dofs <= MFTO_GMG_MAX_COARSE,
+               "mfto_gmg_setup: coarse_max_dofs in [3, MFTO_GMG_MAX_COARSE]");
+  MFTO_REQUIRE(h, p.nu_pre >= 0 && p.nu_post >= 0 && p.nu_pre <= 8 && p.nu_post <= 8,
+               "mfto_gmg_setup: sweeps in [0, 8]");
+  MFTO_REQUIRE(h, p.omega > 0.0 && p.omega < 2.0, "mfto_gmg_setup: omega in (0, 2)");
+  return MFTO_OK;
+}
+
+GmgWs* ws(mfto_handle* h) {
+  if (!h->gmg) {
+    GmgWs* w = new GmgWs();
+    mfto_default_gmg_params(&w->prm);
+    if (cudaMalloc((void**)&w->d_s, sizeof(GmgScalars)) != cudaSuccess ||
+        cudaMallocHost((void**)&w->h_s, sizeof(GmgScalars)) != cudaSuccess ||
+        cudaMemset(w->d_s, 0, sizeof(GmgScalars)) != cudaSuccess) {
+      cudaGetLastError();
+      if (w->d_s) cudaFree(w->d_s);
+      if (w->h_s) cudaFreeHost(w->h_s);
+      delete w;
+      return nullptr;
+    }
+    h->gmg = w;
+  }
+  return h->gmg;
+}
+
+mfto_status read_scalars(mfto_handle* h, GmgWs* w) {
+  MFTO_CUDA(h, cudaMemcpyAsync(w->h_s, w->d_s, sizeof(GmgScalars), cudaMemcpyDeviceToHost,
+                               h->stream));
+  MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MFTO_OK;
+}
+
+}  // namespace
+
+void gmg_release(mfto_handle* h) {
+  if (!h || !h->gmg) return;
+  GmgWs* w = h->gmg;
+  free_levels(w);
+  if (w->d_s) cudaFree(w->d_s);
+  if (w->h_s) cudaFreeHost(w->h_s);
+  delete w;
+  h->gmg = nullptr;
+}
+
+bool gmg_active(const mfto_handle* h) { return h->gmg && h->gmg->use_in_simp; }
+
+extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
+  if (!p) return;
+  p->max_levels = MFTO_GMG_MAX_LEVELS;
+  p->coarse_max_dofs = 200;
+  p->nu_pre = 2;
+  p->nu_post = 2;
+  p->omega = 1.3;
+}
+
+extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
+                                      const mfto_gmg_params* prm) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, d_E, "mfto_gmg_setup: null pointer");
+  GmgWs* w = ws(h);
+  if (!w) return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: workspace allocation failed");
+  mfto_gmg_params p = w->prm;
+  if (prm) p = *prm;
+  mfto_status s = check_params(h, p);
+  if (s != MFTO_OK) return s;
+  w->prm = p;
+  g_sms = h->num_sms;
+  if ((s = gmg_alloc(h, w, p)) != MFTO_OK) return s;
+  if (!w->d_E32) {
+    if (cudaMalloc((void**)&w->d_E32, sizeof(float) * h->n_elem) != cudaSuccess) {
+      cudaGetLastError();
+      return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: cudaMalloc failed");
+    }
+  }
+  w->ready = false;
+  h->launches++;
+  gmg_cast<<<grid_of(h->n_elem), kB, 0, h->stream>>>(d_E, w->d_E32, h->n_elem);
+  MFTO_LAUNCH_CHECK(h);
+  const GmgLevel& v0 = w->lv[0];
+  h->launches++;
+  gmg_l1_fine<<<grid_of(v0.n_node), kB, 0, h->stream>>>(w->d_E32, v0.d_fixed, h->d_ke32, v0.nx,
+                                                        v0.ny, v0.nz, v0.d_dinv);
+  MFTO_LAUNCH_CHECK(h);
+  for (int l = 0; l + 1 < w->n_levels; ++l) {
+    const GmgLevel& f = w->lv[l];
+    const GmgLevel& c = w->lv[l + 1];
+    const int g = (int)std::min<int64_t>(c.n_elem, 8LL * h->num_sms);
+    h->launches++;
+    if (l == 0)
+      gmg_galerkin<true><<<g, kB, 0, h->stream>>>(nullptr, w->d_E32, h->d_ke32, f.d_fixed, f.nx,
+                                                  f.ny, f.nz, c.d_fixed, c.nx, c.ny, c.nz, c.d_K);
+    else
+      gmg_galerkin<false><<<g, kB, 0, h->stream>>>(f.d_K, nullptr, nullptr, f.d_fixed, f.nx, f.ny,
+                                                   f.nz, c.d_fixed, c.nx, c.ny, c.nz, c.d_K);
+    MFTO_LAUNCH_CHECK(h);
+    h->launches++;
+    gmg_l1_coarse<<<grid_of(c.n_node), kB, 0, h->stream>>>(c.d_K, c.d_fixed, c.nx, c.ny, c.nz,
+                                                           c.d_dinv);
+    MFTO_LAUNCH_CHECK(h);
+  }
+  if ((s = coarse_inverse(h, w)) != MFTO_OK) return s;
+  w->ready = true;
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_gmg_levels(mfto_handle* h, int32_t* n_levels, int32_t* dims) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, n_levels && dims, "mfto_gmg_levels: null pointer");
+  MFTO_REQUIRE(h, h->gmg && h->gmg->ready, "mfto_gmg_levels: call mfto_gmg_setup first");
+  *n_levels = h->gmg->n_levels;
+  for (int l = 0; l < h->gmg->n_levels; ++l) {
+    dims[3 * l] = h->gmg->lv[l].nx;
+    dims[3 * l + 1] = h->gmg->lv[l].ny;
+    dims[3 * l + 2] = h->gmg->lv[l].nz;
+  }
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_gmg_apply(mfto_handle* h, int32_t level, const float* d_x,
+                                      float* d_y) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, d_x && d_y, "mfto_gmg_apply: null pointer");
+  MFTO_REQUIRE(h, h->gmg && h->gmg->ready, "mfto_gmg_apply: call mfto_gmg_setup first");
+  MFTO_REQUIRE(h, level >= 0 && level < h->gmg->n_levels, "mfto_gmg_apply: no such level");
+  return apply_level(h, h->gmg, level, d_x, d_y);
+}
+
+extern "C" mfto_status mfto_gmg_vcycle(mfto_handle* h, const float* d_r, float* d_z) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, d_r && d_z && d_r != d_z, "mfto_gmg_vcycle: null or aliased pointers");
+  MFTO_REQUIRE(h, h->gmg && h->gmg->ready, "mfto_gmg_vcycle: call mfto_gmg_setup first");
+  return vcycle_graph(h, h->gmg, d_r, d_z);
+}
+
+mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* u,
+                      mfto_solve_stats* st) {
+  memset(st, 0, sizeof(*st));
+  mfto_status s = mfto_gmg_setup(h, E, nullptr);
+  if (s != MFTO_OK) return s;
+  GmgWs* w = h->gmg;
+  const int64_t n = h->n_dof;
+  double *r = h->d_r, *z = h->d_z, *pv = h->d_p0, *q = h->d_q, *r_old = h->d_p1;
+  float *r32 = h->d_r32, *z32 = h->d_z32;
+  const int g = reduction_blocks(n, kB);
+  // r = f - K u
+  if ((s = kv_launch(h, MFTO_FORM_F64, E, u, q)) != MFTO_OK) return s;
+  h->launches++;
+  gmg_resid0<<<g, kB, 0, h->stream>>>(f, q, r, r32, n, w->d_s, h->d_partials);
+  MFTO_LAUNCH_CHECK(h);
+  if ((s = read_scalars(h, w)) != MFTO_OK) return s;
+  const double ff = w->h_s->sum[1];
+  st->fnorm = sqrt(ff);
+  if (ff == 0.0) {
+    MFTO_CUDA(h, cudaMemsetAsync(u, 0, sizeof(double) * n, h->stream));
+    MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+    st->status = MFTO_OK;
+    return MFTO_OK;
+  }
+  double rr = w->h_s->sum[0];
+  st->rel_residual = sqrt(rr / ff);
+  const double rtol = h->p.rtol;
+  if (st->rel_residual <= rtol) {
+    st->status = MFTO_OK;
+    return MFTO_OK;
+  }
+  if ((s = vcycle_graph(h, w, r32, z32)) != MFTO_OK) return s;
+  h->launches += 2;
+  gmg_zdot<<<g, kB, 0, h->stream>>>(z32, r, r_old, z, n, 1, w->d_s, h->d_partials);
+  MFTO_LAUNCH_CHECK(h);
+  gmg_dir<<<g, kB, 0, h->stream>>>(z, pv, 0.0, n);
+  MFTO_LAUNCH_CHECK(h);
+  if ((s = read_scalars(h, w)) != MFTO_OK) return s;
+  double rz = w->h_s->sum[0];
+  st->status = MFTO_NOT_CONVERGED;
+  for (int it = 1; it <= h->p.maxit; ++it) {
+    if ((s = kv_launch(h, MFTO_FORM_F64, E, pv, q)) != MFTO_OK) return s;
+    h->launches++;
+    gmg_pq<<<g, kB, 0, h->stream>>>(pv, q, n, w->d_s, h->d_partials);
+    MFTO_LAUNCH_CHECK(h);
+    if ((s = read_scalars(h, w)) != MFTO_OK) return s;
+    const double pq = w->h_s->sum[3];
+    if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rz)) {
+      st->status = MFTO_BREAKDOWN;
+      st->iterations = it - 1;
+      return MFTO_OK;
+    }
+    const double alpha = rz / pq;
+    h->launches++;
+    gmg_update<<<g, kB, 0, h->stream>>>(u, r, r_old, pv, q, r32, alpha, n, w->d_s,
+                                        h->d_partials);
+    MFTO_LAUNCH_CHECK(h);
+    if ((s = vcycle_graph(h, w, r32, z32)) != MFTO_OK) return s;
+    h->launches++;
+    gmg_zdot<<<g, kB, 0, h->stream>>>(z32, r, r_old, z, n, 0, w->d_s, h->d_partials);
+    MFTO_LAUNCH_CHECK(h);
+    if ((s = read_scalars(h, w)) != MFTO_OK) return s;
+    rr = w->h_s->sum[2];
+    st->iterations = it;
+    st->rel_residual = sqrt(rr / ff);
+    if (st->rel_residual <= rtol) {
+      st->status = MFTO_OK;
+      break;
+    }
+    if (!std::isfinite(st->rel_residual)) {
+      st->status = MFTO_BREAKDOWN;
+      break;
+    }
+    const double rz_new = w->h_s->sum[0], zr_old = w->h_s->sum[1];
+    const double beta = (rz_new - zr_old) / rz;
+    rz = rz_new;
+    h->launches++;
+    gmg_dir<<<g, kB, 0, h->stream>>>(z, pv, beta, n);
+    MFTO_LAUNCH_CHECK(h);
+  }
+  MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_gmg_solve(mfto_handle* h, const double* d_E, const double* d_f,
+                                      double* d_u, mfto_solve_stats* st) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, d_E && d_f && d_u && st, "mfto_gmg_solve: null pointer");
+  return gmg_solve(h, d_E, d_f, d_u, st);
+}
+
+extern "C" mfto_status mfto_set_gmg_solver(mfto_handle* h, int32_t on,
+                                           const mfto_gmg_params* prm) {
+  if (!h) return MFTO_INVALID_ARG;
+  GmgWs* w = ws(h);
+  if (!w) return mfto_fail(h, MFTO_OOM, "mfto_set_gmg_solver: workspace allocation failed");
+  if (prm) {
+    mfto_status s = check_params(h, *prm);
+    if (s != MFTO_OK) return s;
+    w->prm = *prm;
+  }
+  w->use_in_simp = on != 0;
+  return MFTO_OK;
+}

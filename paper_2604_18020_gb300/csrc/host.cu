@@ -127,6 +127,7 @@ static void free_handle(mfto_handle* h) {
   pcg_graph_release(h);
   multi_graph_release(h);
   learned_release(h);
+  gmg_release(h);
   void* ptrs[] = {h->d_ke64, h->d_ke32, h->d_fixed, h->d_stencil_off, h->d_stencil_w,
                   h->d_filter_W, h->d_r, h->d_z, h->d_p0, h->d_p1, h->d_q, h->d_dinv,
                   h->d_partials, h->d_partials2, h->d_pcg, h->d_misc, h->d_rho_phys,

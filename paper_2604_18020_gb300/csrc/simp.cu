@@ -203,7 +203,10 @@ extern "C" mfto_status mfto_simp_step(mfto_handle* h, double* rho, double* u, co
     ss.status = ls.status;
     ss.rel_residual = ls.rel_residual;
     ss.fnorm = ls.fnorm;
-  } else if (h->solver_form == MFTO_FORM_F64) {
+  } else if (gmg_active(h)) {
+    s = gmg_solve(h, h->d_E, f, u, &ss);
+    if (s != MFTO_OK) return s;
+} else if (h->solver_form == MFTO_FORM_F64) {
     s = pcg_run(h, h->d_E, f, u, &ss);
     if (s != MFTO_OK) return s;
   } else {

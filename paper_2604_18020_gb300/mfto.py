@@ -66,6 +66,13 @@ class KappaParams(C.Structure):
                 ("inner_rtol", C.c_double), ("inner_maxit", C.c_int32)]
 
 
+class GmgParams(C.Structure):
+    _fields_ = [("max_levels", C.c_int32), ("coarse_max_dofs", C.c_int32),
+                ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("omega", C.c_double)]
+
+
+GMG_MAX_LEVELS = 10
+
 class KappaStats(C.Structure):
     _fields_ = [("lambda_max", C.c_double), ("lambda_min", C.c_double), ("kappa", C.c_double),
                 ("power_steps", C.c_int32), ("inverse_steps", C.c_int32),
@@ -121,6 +128,13 @@ SIGNATURES = {
     "mfto_set_cg_engine": (C.c_int32, [_P, C.c_int32]),
     "mfto_set_ir_mode": (C.c_int32, [_P, C.c_int32]),
     "mfto_default_kappa_params": (None, [C.POINTER(KappaParams)]),
+    "mfto_default_gmg_params": (None, [C.POINTER(GmgParams)]),
+    "mfto_gmg_setup": (C.c_int32, [_P, _P, C.POINTER(GmgParams)]),
+    "mfto_gmg_levels": (C.c_int32, [_P, C.POINTER(C.c_int32), _P]),
+    "mfto_gmg_apply": (C.c_int32, [_P, C.c_int32, _P, _P]),
+    "mfto_gmg_vcycle": (C.c_int32, [_P, _P, _P]),
+    "mfto_gmg_solve": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
+    "mfto_set_gmg_solver": (C.c_int32, [_P, C.c_int32, C.POINTER(GmgParams)]),
     "mfto_set_projection": (C.c_int32, [_P, C.c_double, C.c_double]),
     "mfto_project": (C.c_int32, [_P, _P, _P, _P]),
     "mfto_default_protocol_params": (None, [C.POINTER(ProtocolParams)]),
@@ -243,6 +257,14 @@ def default_params(**kw) -> Params:
 
 
 # ------------------------------------------------------------------ host calls
+
+def default_gmg_params(**kw) -> GmgParams:
+    p = GmgParams()
+    lib().mfto_default_gmg_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
 
 def unit_ke(E0=1.0, nu=0.3, h=1.0) -> np.ndarray:
     out = np.zeros(576)
@@ -431,6 +453,45 @@ class Handle:
             _ptr(v_inverse, torch.float64, self.n_dof, "v_inverse"),
             _ptr(work, torch.float64, self.n_dof, "work"), C.byref(prm), C.byref(st)), self._h)
         return st
+
+    # ---- geometric multigrid
+    def gmg_setup(self, E, params=None):
+        import torch
+        _check("mfto_gmg_setup", lib().mfto_gmg_setup(
+            self._h, _ptr(E, torch.float64, self.n_elem, "E"),
+            C.byref(params) if params is not None else None), self._h)
+
+    def gmg_levels(self):
+        n = C.c_int32()
+        dims = np.zeros(3 * GMG_MAX_LEVELS, dtype=np.int32)
+        _check("mfto_gmg_levels", lib().mfto_gmg_levels(self._h, C.byref(n), dims.ctypes.data),
+               self._h)
+        return [tuple(int(x) for x in dims[3 * l:3 * l + 3]) for l in range(n.value)]
+
+    def gmg_apply(self, level, x, y):
+        import torch
+        _check("mfto_gmg_apply", lib().mfto_gmg_apply(
+            self._h, level, _ptr(x, torch.float32, None, "x"), _ptr(y, torch.float32, None, "y")),
+            self._h)
+
+    def gmg_vcycle(self, r, z):
+        import torch
+        _check("mfto_gmg_vcycle", lib().mfto_gmg_vcycle(
+            self._h, _ptr(r, torch.float32, self.n_dof, "r"), _ptr(z, torch.float32, self.n_dof, "z")),
+            self._h)
+
+    def gmg_solve(self, E, f, u) -> SolveStats:
+        import torch
+        st = SolveStats()
+        _check("mfto_gmg_solve", lib().mfto_gmg_solve(
+            self._h, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(f, torch.float64, self.n_dof, "f"), _ptr(u, torch.float64, self.n_dof, "u"),
+            C.byref(st)), self._h)
+        return st
+
+    def set_gmg_solver(self, on=True, params=None):
+        _check("mfto_set_gmg_solver", lib().mfto_set_gmg_solver(
+            self._h, 1 if on else 0, C.byref(params) if params is not None else None), self._h)
 
     def set_ir_mode(self, mode: int):
         """IR_RESTART (0): each inner CG starts with p = z; IR_CONTINUE (1): it

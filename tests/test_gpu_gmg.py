@@ -1,0 +1,139 @@
+"""Geometric multigrid on the GPU against the oracle (oracle/gmg.py): the
+level hierarchy, every level's Galerkin operator applied to a vector, one
+V-cycle, the V-cycle CG solve and SIMP steps with it, on meshes with odd
+(ragged) element counts; the argument checks."""
+import numpy as np
+import pytest
+
+from oracle import fem, gmg, solve, simp as osimp, filter as cone
+from paper_2604_18020_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(shape, seed=3, **kw):
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(*shape)
+    m = P.mesh
+    fd = fem.dof_mask(P.fixed)
+    E = fem.simp_modulus(W.rho_random(m, seed=seed, lo=0.1, hi=1.0), 3.0)
+    h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed)
+    prm = mfto.default_gmg_params(**kw)
+    Ed = torch.tensor(E, device="cuda:0")
+    h.gmg_setup(Ed, prm)
+    H = gmg.build(fem.ke_exact(), E, *shape, fd, max_levels=prm.max_levels,
+                  coarse_max_dofs=prm.coarse_max_dofs, omega=prm.omega, nu_pre=prm.nu_pre,
+                  nu_post=prm.nu_post)
+    return P, m, fd, E, Ed, h, H
+
+
+@pytest.mark.parametrize("shape", [(24, 12, 12), (13, 7, 5)])
+def test_levels_and_operators_match_oracle(cuda, shape):
+    import torch
+    P, m, fd, E, Ed, h, H = _setup(shape)
+    with h:
+        assert h.gmg_levels() == [lev.dims for lev in H.levels]
+        rng = np.random.default_rng(7)
+        for li, lev in enumerate(H.levels):
+            x = rng.uniform(-1, 1, lev.A.shape[0])
+            y = torch.empty(len(x), dtype=torch.float32, device=cuda)
+            h.gmg_apply(li, torch.tensor(x, dtype=torch.float32, device=cuda), y)
+            ref = lev.A @ x
+            got = y.cpu().numpy().astype(np.float64)
+            assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max(), li
+
+
+@pytest.mark.parametrize("shape,nu", [((24, 12, 12), 2), ((13, 7, 5), 1), ((9, 6, 4), 0)])
+def test_vcycle_matches_oracle(cuda, shape, nu):
+    import torch
+    P, m, fd, E, Ed, h, H = _setup(shape, nu_pre=nu, nu_post=nu)
+    with h:
+        r = W.vec_random(m.n_dof, seed=11)
+        r[fd] = 0.0
+        z = torch.empty(m.n_dof, dtype=torch.float32, device=cuda)
+        h.gmg_vcycle(torch.tensor(r, dtype=torch.float32, device=cuda), z)
+        ref = gmg.vcycle(H, r)
+        got = z.cpu().numpy().astype(np.float64)
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+def test_single_level_is_dense_solve(cuda):
+    import torch
+    P, m, fd, E, Ed, h, H = _setup((4, 2, 2), coarse_max_dofs=1000)
+    with h:
+        assert h.gmg_levels() == [(4, 2, 2)]
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+        st = h.gmg_solve(Ed, torch.tensor(P.f, device=cuda), u)
+        assert st.status == 0 and st.iterations <= 4
+
+
+def _simp_state(shape, n_iter=6):
+    P = W.cantilever(*shape)
+    rho, _, _ = osimp.simp(*shape, P.f, P.fixed, 0.3, 1.5, n_iter)
+    return P, cone.filter_fwd(rho, *shape, 1.5)
+
+
+def test_gmg_solve_matches_oracle(cuda):
+    """A SIMP state of the 24 x 12 x 12 cantilever (E from 1e-9 to 1): the
+    V-cycle CG reaches the tolerance with the oracle's true residual, the
+    oracle's compliance, and about the oracle's iteration count."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    shape = (24, 12, 12)
+    P, rho_phys = _simp_state(shape)
+    m = P.mesh
+    fd = fem.dof_mask(P.fixed)
+    KE = fem.ke_exact()
+    edof = fem.edof_table_fast(*shape)
+    E = fem.simp_modulus(rho_phys, 3.0)
+    K = lambda v: fem.kv(KE, E, edof, v, fd)
+    u_j, _ = solve.pcg(K, fem.jacobi_diag(KE, E, edof, fd), P.f, np.zeros(m.n_dof), 1e-10)
+    H = gmg.build(KE, E, *shape, fd, omega=1.3)
+    _, st_o = gmg.pcg(H, K, P.f, np.zeros(m.n_dof), 1e-8)
+    with mfto.Handle(*shape, P.fixed) as h:
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+        st = h.gmg_solve(torch.tensor(E, device=cuda), torch.tensor(P.f, device=cuda), u)
+        assert h.gmg_levels() == [lev.dims for lev in H.levels]
+    ug = u.cpu().numpy()
+    assert st.status == 0 and st.rel_residual <= 1e-8
+    assert np.linalg.norm(P.f - K(ug)) / np.linalg.norm(P.f) <= 1.5e-8
+    assert abs(P.f @ ug - P.f @ u_j) <= 1e-7 * abs(P.f @ u_j)
+    assert st.iterations <= 1.5 * st_o.iterations + 3
+
+
+def test_simp_steps_with_gmg_solver(cuda):
+    """Three SIMP iterations on 16 x 8 x 8 with the V-cycle CG as the solver
+    against the oracle's SIMP loop (Jacobi-PCG): the same compliances."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    shape = (16, 8, 8)
+    P = W.cantilever(*shape)
+    m = P.mesh
+    _, _, hist = osimp.simp(*shape, P.f, P.fixed, 0.3, 1.5, 3)
+    with mfto.Handle(*shape, P.fixed, params=mfto.default_params(volfrac=0.3, rmin=1.5)) as h:
+        h.set_gmg_solver(True)
+        rho = torch.full((m.n_elem,), 0.3, dtype=torch.float64, device=cuda)
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+        f = torch.tensor(P.f, device=cuda)
+        cs = [h.simp_step(rho, u, f) for _ in range(3)]
+    for st, c_ref in zip(cs, hist.compliance):
+        assert st.cg_status == 0
+        assert abs(st.compliance - c_ref) <= 1e-6 * abs(c_ref)
+
+
+def test_gmg_argument_checks(cuda):
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(24, 12, 12)
+    m = P.mesh
+    E = torch.ones(m.n_elem, dtype=torch.float64, device=cuda)
+    with mfto.Handle(24, 12, 12, P.fixed) as h:
+        z = torch.empty(m.n_dof, dtype=torch.float32, device=cuda)
+        with pytest.raises(mfto.MftoError):          # no hierarchy yet
+            h.gmg_vcycle(torch.zeros(m.n_dof, dtype=torch.float32, device=cuda), z)
+        with pytest.raises(mfto.MftoError):          # weight outside (0, 2)
+            h.gmg_setup(E, mfto.default_gmg_params(omega=2.0))
+        with pytest.raises(mfto.MftoError) as ei:    # a single 4,875-DOF level is too large
+            h.gmg_setup(E, mfto.default_gmg_params(max_levels=1))
+        assert ei.value.code == mfto.TOO_LARGE
