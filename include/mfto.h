@@ -685,6 +685,10 @@ typedef struct {
   int32_t coarse_max_dofs;  /* 3 .. MFTO_GMG_MAX_COARSE (default 200)     */
   int32_t nu_pre, nu_post;  /* 0 .. 8 sweeps (default 2, 2)               */
   double omega;             /* l1-Jacobi weight in (0, 2) (default 1.3)   */
+  int32_t mixed;            /* mfto_gmg_solve: 0 FP64 CG, 1 FP64 refinement
+                               around an FP32 CG (default 1)              */
+  double inner_tol;         /* relative tolerance of each FP32 CG, (0, 1)
+                               (default 1e-2)                             */
 } mfto_gmg_params;
 void mfto_default_gmg_params(mfto_gmg_params* p);
 /* Build the hierarchy for the moduli d_E (FP64 [elements]) with params p
@@ -699,10 +703,17 @@ mfto_status mfto_gmg_levels(mfto_handle* h, int32_t* n_levels, int32_t* dims);
 mfto_status mfto_gmg_apply(mfto_handle* h, int32_t level, const float* d_x, float* d_y);
 /* d_z = V(d_r), one V-cycle on FP32 fine vectors (d_r and d_z distinct). */
 mfto_status mfto_gmg_vcycle(mfto_handle* h, const float* d_r, float* d_z);
-/* K(E) u = f by CG preconditioned with the V-cycle (Polak-Ribiere beta, FP64
- * vectors, K.v and dot products): setup for d_E, then iterations from the
- * initial guess in d_u until ||r|| <= rtol ||f|| (the handle's rtol) or the
- * handle's maxit.  Outcome in st (iterations = CG iterations). */
+/* K(E) u = f by CG preconditioned with the V-cycle (Polak-Ribiere beta),
+ * after a setup for d_E, from the initial guess in d_u until
+ * ||r|| <= rtol ||f|| (the handle's rtol):
+ *   mixed = 0: one CG with FP64 vectors, K.v and dot products, at most the
+ *     handle's maxit iterations;
+ *   mixed = 1: FP64 refinement (r = f - K u with the FP64 K.v, u += e) around
+ *     CGs in FP32 (FP32 K.v and vectors, FP64 dot products) that each reduce
+ *     their residual by inner_tol, at most maxit iterations each; at most 50
+ *     corrections, MFTO_STALLED when the residual fails twice in a row to
+ *     fall below 0.9 of the previous one.
+ * Outcome in st (iterations = CG iterations, summed over the corrections). */
 mfto_status mfto_gmg_solve(mfto_handle* h, const double* d_E, const double* d_f, double* d_u,
                            mfto_solve_stats* st);
 /* on != 0: mfto_simp_step solves with mfto_gmg_solve (params p, NULL keeps the

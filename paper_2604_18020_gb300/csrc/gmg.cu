@@ -512,6 +512,77 @@ gmg_update(double* __restrict__ u, double* __restrict__ r, double* __restrict__ 
     s->sum[2] = tot[0];
 }
 
+// ---- FP32 inner CG kernels of the mixed solve (FP64 sums)
+
+// r.z, z.r_old -> s[0], s[1]
+__global__ void __launch_bounds__(kB)
+gmg_dot2_f32(const float* __restrict__ r, const float* __restrict__ r_old,
+             const float* __restrict__ z, int64_t n, int first, GmgScalars* s, double* partials) {
+  __shared__ double sh[64];
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+    acc[0] += (double)r[i] * zi;
+    if (!first) acc[1] += (double)r_old[i] * zi;
+  }
+  double tot[2];
+  if (last_block_reduce<2>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0) {
+    s->sum[0] = tot[0];
+    s->sum[1] = tot[1];
+  }
+}
+
+__global__ void __launch_bounds__(kB)
+gmg_dir_f32(const float* __restrict__ z, float* __restrict__ p, float beta, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// p.q -> s[3]
+__global__ void __launch_bounds__(kB)
+gmg_pq_f32(const float* __restrict__ p, const float* __restrict__ q, int64_t n, GmgScalars* s,
+           double* partials) {
+  __shared__ double sh[64];
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc[0] += (double)p[i] * q[i];
+  double tot[1];
+  if (last_block_reduce<1>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0)
+    s->sum[3] = tot[0];
+}
+
+// e += alpha p; r_old = r; r -= alpha q; r.r -> s[2]
+__global__ void __launch_bounds__(kB)
+gmg_update_f32(float* __restrict__ e, float* __restrict__ r, float* __restrict__ r_old,
+               const float* __restrict__ p, const float* __restrict__ q, float alpha, int64_t n,
+               GmgScalars* s, double* partials) {
+  __shared__ double sh[64];
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    e[i] += alpha * p[i];
+    const float ro = r[i];
+    r_old[i] = ro;
+    const float rn = ro - alpha * q[i];
+    r[i] = rn;
+    acc[0] += (double)rn * rn;
+  }
+  double tot[1];
+  if (last_block_reduce<1>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0)
+    s->sum[2] = tot[0];
+}
+
+// u += e
+__global__ void __launch_bounds__(kB)
+gmg_correct(double* __restrict__ u, const float* __restrict__ e, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    u[i] += (double)e[i];
+}
+
 // ---------------------------------------------------------------- host side
 
 void level_dims(const mfto_handle* h, const mfto_gmg_params& p, int* n_levels, int dims[][3]) {
@@ -747,8 +818,10 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x) {
 // private capture stream the first time (and again when the buffers, the
 // parameters or the hierarchy's storage change), replayed on the stream.
 mfto_status vcycle_graph(mfto_handle* h, GmgWs* w, const float* r, float* z) {
+  const mfto_gmg_params &a = w->vprm, &b = w->prm;
   const bool same = w->vexec && w->vkey_r == r && w->vkey_z == z &&
-                    memcmp(&w->vprm, &w->prm, sizeof(mfto_gmg_params)) == 0;
+                    a.max_levels == b.max_levels && a.coarse_max_dofs == b.coarse_max_dofs &&
+                    a.nu_pre == b.nu_pre && a.nu_post == b.nu_post && a.omega == b.omega;
   if (!same) {
     drop_graph(w);
     if (!h->cap_stream &&
@@ -796,6 +869,8 @@ mfto_status check_params(mfto_handle* h, const mfto_gmg_params& p) {
   MFTO_REQUIRE(h, p.nu_pre >= 0 && p.nu_post >= 0 && p.nu_pre <= 8 && p.nu_post <= 8,
                "mfto_gmg_setup: sweeps in [0, 8]");
   MFTO_REQUIRE(h, p.omega > 0.0 && p.omega < 2.0, "mfto_gmg_setup: omega in (0, 2)");
+  MFTO_REQUIRE(h, p.mixed == 0 || p.mixed == 1, "mfto_gmg_setup: mixed is 0 or 1");
+  MFTO_REQUIRE(h, p.inner_tol > 0.0 && p.inner_tol < 1.0, "mfto_gmg_setup: inner_tol in (0, 1)");
   return MFTO_OK;
 }
 
@@ -845,6 +920,8 @@ extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
   p->nu_pre = 2;
   p->nu_post = 2;
   p->omega = 1.3;
+  p->mixed = 1;
+  p->inner_tol = 1e-2;
 }
 
 extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
@@ -926,12 +1003,98 @@ extern "C" mfto_status mfto_gmg_vcycle(mfto_handle* h, const float* d_r, float* 
   return vcycle_graph(h, h->gmg, d_r, d_z);
 }
 
+namespace {
+
+// FP64 refinement around FP32 V-cycle CGs (mfto_gmg_params.mixed = 1)
+mfto_status gmg_solve_mixed(mfto_handle* h, GmgWs* w, const double* E, const double* f, double* u,
+                            mfto_solve_stats* st) {
+  const int64_t n = h->n_dof;
+  double *r = h->d_r, *q = h->d_q;
+  float *r32 = h->d_r32, *z32 = h->d_z32, *p32 = h->d_p0_32, *q32 = h->d_q32, *e32 = h->d_e32,
+        *ro32 = h->d_p1_32;
+  const int g = reduction_blocks(n, kB);
+  const double rtol = h->p.rtol, itol = w->prm.inner_tol;
+  mfto_status s;
+  double prev = 0.0;
+  int stalls = 0;
+  st->status = MFTO_NOT_CONVERGED;
+  for (int outer = 0; outer <= 50; ++outer) {
+    if ((s = kv_launch(h, MFTO_FORM_F64, E, u, q)) != MFTO_OK) return s;
+    h->launches++;
+    gmg_resid0<<<g, kB, 0, h->stream>>>(f, q, r, r32, n, w->d_s, h->d_partials);
+    MFTO_LAUNCH_CHECK(h);
+    if ((s = read_scalars(h, w)) != MFTO_OK) return s;
+    const double rr = w->h_s->sum[0], ff = w->h_s->sum[1];
+    st->fnorm = sqrt(ff);
+    if (ff == 0.0) {
+      MFTO_CUDA(h, cudaMemsetAsync(u, 0, sizeof(double) * n, h->stream));
+      MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+      st->status = MFTO_OK;
+      return MFTO_OK;
+    }
+    const double rel = sqrt(rr / ff);
+    st->rel_residual = rel;
+    if (rel <= rtol) { st->status = MFTO_OK; break; }
+    if (!std::isfinite(rel)) { st->status = MFTO_BREAKDOWN; break; }
+    if (outer > 0) {
+      stalls = rel > 0.9 * prev ? stalls + 1 : 0;
+      if (stalls >= 2) { st->status = MFTO_STALLED; break; }
+    }
+    if (outer == 50) break;
+    prev = rel;
+    // FP32 CG on K e = r from e = 0
+    MFTO_CUDA(h, cudaMemsetAsync(e32, 0, sizeof(float) * n, h->stream));
+    if ((s = vcycle_graph(h, w, r32, z32)) != MFTO_OK) return s;
+    h->launches += 2;
+    gmg_dot2_f32<<<g, kB, 0, h->stream>>>(r32, ro32, z32, n, 1, w->d_s, h->d_partials);
+    MFTO_LAUNCH_CHECK(h);
+    gmg_dir_f32<<<g, kB, 0, h->stream>>>(z32, p32, 0.0f, n);
+    MFTO_LAUNCH_CHECK(h);
+    if ((s = read_scalars(h, w)) != MFTO_OK) return s;
+    double rz = w->h_s->sum[0];
+    for (int it = 1; it <= h->p.maxit; ++it) {
+      if ((s = kv_launch(h, MFTO_FORM_F32, w->d_E32, p32, q32)) != MFTO_OK) return s;
+      h->launches++;
+      gmg_pq_f32<<<g, kB, 0, h->stream>>>(p32, q32, n, w->d_s, h->d_partials);
+      MFTO_LAUNCH_CHECK(h);
+      if ((s = read_scalars(h, w)) != MFTO_OK) return s;
+      const double pq = w->h_s->sum[3];
+      if (!(pq > 0.0) || !std::isfinite(pq) || !(rz > 0.0)) break;
+      h->launches++;
+      gmg_update_f32<<<g, kB, 0, h->stream>>>(e32, r32, ro32, p32, q32, (float)(rz / pq), n,
+                                              w->d_s, h->d_partials);
+      MFTO_LAUNCH_CHECK(h);
+      st->iterations++;
+      if ((s = vcycle_graph(h, w, r32, z32)) != MFTO_OK) return s;
+      h->launches++;
+      gmg_dot2_f32<<<g, kB, 0, h->stream>>>(r32, ro32, z32, n, 0, w->d_s, h->d_partials);
+      MFTO_LAUNCH_CHECK(h);
+      if ((s = read_scalars(h, w)) != MFTO_OK) return s;
+      const double rr_in = w->h_s->sum[2];
+      if (!(sqrt(rr_in / rr) > itol)) break;     // reached (or not a number: stop)
+      const double beta = (w->h_s->sum[0] - w->h_s->sum[1]) / rz;
+      rz = w->h_s->sum[0];
+      h->launches++;
+      gmg_dir_f32<<<g, kB, 0, h->stream>>>(z32, p32, (float)beta, n);
+      MFTO_LAUNCH_CHECK(h);
+    }
+    h->launches++;
+    gmg_correct<<<g, kB, 0, h->stream>>>(u, e32, n);
+    MFTO_LAUNCH_CHECK(h);
+  }
+  MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MFTO_OK;
+}
+
+}  // namespace
+
 mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* u,
                       mfto_solve_stats* st) {
   memset(st, 0, sizeof(*st));
   mfto_status s = mfto_gmg_setup(h, E, nullptr);
   if (s != MFTO_OK) return s;
   GmgWs* w = h->gmg;
+  if (w->prm.mixed) return gmg_solve_mixed(h, w, E, f, u, st);
   const int64_t n = h->n_dof;
   double *r = h->d_r, *z = h->d_z, *pv = h->d_p0, *q = h->d_q, *r_old = h->d_p1;
   float *r32 = h->d_r32, *z32 = h->d_z32;
