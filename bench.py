@@ -859,6 +859,117 @@ def ubench_run(args):
         print(json.dumps(row), flush=True)
 
 
+def gmg_run(args):
+    """Geometric multigrid against the Jacobi solvers on SIMP states (one
+    JSON line per case): the 120x60x30 cantilever after 20 and the torsion
+    problem after 10 SIMP iterations (mixed Jacobi solver, continued
+    refinement), and the 256x128x150 cantilever at its uniform initial
+    density; cold-start solves to rtol 1e-8 (mean of the timed calls after
+    one warm-up), the hierarchy, the V-cycle time (CUDA events), and the
+    time per SIMP iteration with each solver from the same state."""
+    import numpy as np
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+
+    def sync_time(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
+    reps = max(1, min(args.steps, 5))
+    cases = (("cantilever_120x60x30", 20), ("torsion_55x55x165", 10),
+             ("cantilever_256x128x150", 0))
+    if args.gmg_case:
+        cases = [(n, k if args.gmg_simp_iters is None else args.gmg_simp_iters)
+                 for n, k in cases if n == args.gmg_case]
+    for name, n_simp in cases:
+        P = W.WORKLOADS[name]()
+        m = P.mesh
+        h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed,
+                        params=mfto.default_params(volfrac=P.volfrac, rmin=P.rmin))
+        if not args.no_autotune:
+            h.kv_autotune()
+        h.set_solver(mfto.FORM_F32, 1e-1, 10000, 50)
+        h.set_ir_mode(IR_MODES["continue"])
+        rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+        f = torch.tensor(P.f, device=dev)
+        for _ in range(n_simp):
+            h.simp_step(rho, u, f)
+        rho_phys, E = torch.empty_like(rho), torch.empty_like(rho)
+        h.filter(rho, rho_phys)
+        h.simp_modulus(rho_phys, E)
+        row = {"case": name, "elements": m.n_elem, "dofs": m.n_dof,
+               "state": f"after {n_simp} SIMP iterations" if n_simp else "uniform initial density"}
+        uu = torch.zeros_like(u)
+        solvers = [("jacobi_f64", lambda: h.pcg(E, f, uu)),
+                   ("jacobi_mixed_continue_0.1", lambda: h.ir_solve(E, f, uu, inner_tol=0.1))]
+        gmg_cfg = [("gmg_f64", dict(mixed=0)), ("gmg_mixed", dict(mixed=1)),
+                   ("gmg_mixed_nu2", dict(mixed=1, nu_pre=2, nu_post=2))]
+        if name == "cantilever_256x128x150":
+            solvers = solvers[1:]                      # FP64 Jacobi: minutes at this size
+        if args.gmg_only:                              # the default multigrid solve alone
+            solvers, gmg_cfg = [], gmg_cfg[1:2]
+        c_ref = None
+        for key, fn in solvers + [(k, None) for k, _ in gmg_cfg]:
+            if fn is None:
+                prm = mfto.default_gmg_params(**dict(gmg_cfg)[key])
+                h.set_gmg_solver(False, prm)
+                fn = lambda: h.gmg_solve(E, f, uu)
+            uu.zero_()
+            fn()
+            ts, st = [], None
+            for _ in range(reps):
+                uu.zero_()
+                dt, st = sync_time(fn)
+                ts.append(dt)
+            its = st.inner_iterations if hasattr(st, "inner_iterations") else st.iterations
+            c = float((f * uu).sum())
+            c_ref = c if c_ref is None else c_ref
+            row[key] = {"ms": 1e3 * float(np.mean(ts)), "iterations": its,
+                        "status": mfto.STATUS_NAMES[st.status], "rel_residual": st.rel_residual,
+                        "compliance_rel_diff": abs(c - c_ref) / abs(c_ref)}
+        prm = mfto.default_gmg_params()
+        h.set_gmg_solver(False, prm)
+        dt, _ = sync_time(lambda: h.gmg_setup(E, prm))
+        row["gmg_setup_ms"] = 1e3 * dt
+        row["gmg_levels"] = h.gmg_levels()
+        r32 = torch.tensor(W.vec_random(m.n_dof, seed=3), dtype=torch.float32, device=dev)
+        z32 = torch.empty_like(r32)
+        h.gmg_vcycle(r32, z32)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(20):
+            h.gmg_vcycle(r32, z32)
+        ev1.record()
+        torch.cuda.synchronize()
+        row["vcycle_ms"] = ev0.elapsed_time(ev1) / 20
+        if args.gmg_only:
+            h.close()
+            print(json.dumps(row), flush=True)
+            continue
+        # SIMP iterations from the same state with each solver
+        rho0, u0 = rho.clone(), u.clone()
+        for key, use_gmg in (("simp_iter_ms_jacobi_mixed", False), ("simp_iter_ms_gmg_mixed", True)):
+            h.set_gmg_solver(use_gmg, prm)
+            rho.copy_(rho0)
+            u.copy_(u0)
+            ts, cs = [], []
+            for _ in range(reps):
+                dt, st = sync_time(lambda: h.simp_step(rho, u, f))
+                ts.append(dt)
+                cs.append(st.compliance)
+            row[key] = 1e3 * float(np.mean(ts))
+            row[key.replace("simp_iter_ms", "simp_compliances")] = cs
+        h.set_gmg_solver(False)
+        h.close()
+        print(json.dumps(row), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -869,8 +980,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench",
                     choices=["bench", "profile", "pcg", "compare", "learned", "kappa", "protocol",
-                             "hard", "ubench"])
+                             "hard", "ubench", "gmg"])
     ap.add_argument("--protocol-iters", type=int, default=120)
+    ap.add_argument("--gmg-case", default=None,
+                    choices=["cantilever_120x60x30", "torsion_55x55x165", "cantilever_256x128x150"],
+                    help="--mode gmg: run this case only")
+    ap.add_argument("--gmg-simp-iters", type=int, default=None,
+                    help="--mode gmg: SIMP iterations before the solves (default per case)")
+    ap.add_argument("--gmg-only", action="store_true",
+                    help="--mode gmg: the default multigrid solve and V-cycle only")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--form", default="mixed", choices=["f64", "mixed"],
                     help="f64: plain FP64 Jacobi-PCG; mixed: FP64 iterative refinement "
@@ -910,6 +1028,9 @@ def main():
         return
     if args.mode == "ubench":
         ubench_run(args)
+        return
+    if args.mode == "gmg":
+        gmg_run(args)
         return
     if args.mode != "bench":
         profile_run(args)

@@ -683,7 +683,7 @@ mfto_status mfto_compliance_sens_noalloc(const mfto_mesh* mesh, double E0, doubl
 typedef struct {
   int32_t max_levels;       /* 1 .. MFTO_GMG_MAX_LEVELS (default 10)      */
   int32_t coarse_max_dofs;  /* 3 .. MFTO_GMG_MAX_COARSE (default 200)     */
-  int32_t nu_pre, nu_post;  /* 0 .. 8 sweeps (default 2, 2)               */
+  int32_t nu_pre, nu_post;  /* 0 .. 8 sweeps (default 1, 1)               */
   double omega;             /* l1-Jacobi weight in (0, 2) (default 1.3)   */
   int32_t mixed;            /* mfto_gmg_solve: 0 FP64 CG, 1 FP64 refinement
                                around an FP32 CG (default 1)              */

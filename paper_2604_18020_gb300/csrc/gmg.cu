@@ -917,8 +917,8 @@ extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
   if (!p) return;
   p->max_levels = MFTO_GMG_MAX_LEVELS;
   p->coarse_max_dofs = 200;
-  p->nu_pre = 2;
-  p->nu_post = 2;
+  p->nu_pre = 1;
+  p->nu_post = 1;
   p->omega = 1.3;
   p->mixed = 1;
   p->inner_tol = 1e-2;

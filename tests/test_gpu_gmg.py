@@ -91,11 +91,14 @@ def test_gmg_solve_matches_oracle(cuda, mixed):
     E = fem.simp_modulus(rho_phys, 3.0)
     K = lambda v: fem.kv(KE, E, edof, v, fd)
     u_j, _ = solve.pcg(K, fem.jacobi_diag(KE, E, edof, fd), P.f, np.zeros(m.n_dof), 1e-10)
-    H = gmg.build(KE, E, *shape, fd, omega=1.3)
+    prm = mfto.default_gmg_params(mixed=mixed)
+    H = gmg.build(KE, E, *shape, fd, max_levels=prm.max_levels,
+                  coarse_max_dofs=prm.coarse_max_dofs, omega=prm.omega, nu_pre=prm.nu_pre,
+                  nu_post=prm.nu_post)
     _, st_o = gmg.pcg(H, K, P.f, np.zeros(m.n_dof), 1e-8)
     with mfto.Handle(*shape, P.fixed) as h:
         u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
-        h.set_gmg_solver(False, mfto.default_gmg_params(mixed=mixed))
+        h.set_gmg_solver(False, prm)
         st = h.gmg_solve(torch.tensor(E, device=cuda), torch.tensor(P.f, device=cuda), u)
         assert h.gmg_levels() == [lev.dims for lev in H.levels]
     ug = u.cpu().numpy()
