@@ -40,6 +40,14 @@ struct GmgScalars {
   unsigned int ticket;
 };
 
+// Scalars of the FP32 inner CG when its iterations run from a graph: every
+// step reads and writes them on the device; the host polls done / it.
+struct GmgCg {
+  double rz, alpha, beta, tol2;
+  int32_t it, maxit, done, breakdown;
+  unsigned int ticket;
+};
+
 struct GmgLevel {
   int nx = 0, ny = 0, nz = 0;
   int64_t n_elem = 0, n_node = 0, n_dof = 0;
@@ -69,7 +77,20 @@ struct GmgWs {
   float* vkey_z = nullptr;
   mfto_gmg_params vprm{};
   int64_t vnodes = 0;               // kernels in the graph
+  // cchunk inner CG iterations (K.v, step, V-cycle, direction) as one graph
+  cudaGraphExec_t cexec = nullptr;
+  mfto_gmg_params cprm{};
+  int64_t cnodes = 0;
+  int cchunk = 0;
+  GmgCg* d_cg = nullptr;
+  GmgCg* h_cg = nullptr;
 };
+
+// Iterations per replayed chunk: the host polls once per chunk, and up to
+// chunk - 1 iterations after convergence still run their K.v and V-cycle
+// (their CG steps skip).  Four on meshes whose cycle is short; one where a
+// cycle costs far more than a poll (above 2M DOFs, a cycle takes > 0.5 ms).
+int cg_chunk_len(const mfto_handle* h) { return h->n_dof > 2000000 ? 1 : 4; }
 
 namespace {
 
@@ -469,11 +490,13 @@ gmg_zdot(const float* __restrict__ z32, const double* __restrict__ r,
   }
 }
 
+// p = z + beta p; first: p = z without reading p (it may hold anything,
+// NaN bit patterns included, and 0 * NaN is NaN)
 __global__ void __launch_bounds__(kB)
-gmg_dir(const double* __restrict__ z, double* __restrict__ p, double beta, int64_t n) {
+gmg_dir(const double* __restrict__ z, double* __restrict__ p, double beta, int64_t n, int first) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+    p[i] = first ? z[i] : z[i] + beta * p[i];
 }
 
 // p.q -> s[3]
@@ -533,33 +556,64 @@ gmg_dot2_f32(const float* __restrict__ r, const float* __restrict__ r_old,
   }
 }
 
+// first direction of an inner CG: p = z (p itself is not read)
 __global__ void __launch_bounds__(kB)
-gmg_dir_f32(const float* __restrict__ z, float* __restrict__ p, float beta, int64_t n) {
+gmg_first_dir_f32(const float* __restrict__ z, float* __restrict__ p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+    p[i] = z[i];
 }
 
-// p.q -> s[3]
+// u += e
 __global__ void __launch_bounds__(kB)
-gmg_pq_f32(const float* __restrict__ p, const float* __restrict__ q, int64_t n, GmgScalars* s,
-           double* partials) {
+gmg_correct(double* __restrict__ u, const float* __restrict__ e, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    u[i] += (double)e[i];
+}
+
+// ---- FP32 inner CG steps with device-side scalars (graph-replayed chunks)
+
+// start: rz from the first r.z (s[0]); done when there is nothing to do
+__global__ void gmg_cg_start(GmgCg* cg, const GmgScalars* s, double tol2, int maxit) {
+  cg->rz = s->sum[0];
+  cg->alpha = cg->beta = 0.0;
+  cg->tol2 = tol2;
+  cg->it = 0;
+  cg->maxit = maxit;
+  cg->breakdown = 0;
+  cg->done = (maxit < 1 || !(cg->rz > 0.0)) ? 1 : 0;
+}
+
+// p.q, then alpha = rz / p.q (breakdown ends the solve)
+__global__ void __launch_bounds__(kB)
+gmg_cg_pq(const float* __restrict__ p, const float* __restrict__ q, int64_t n, GmgCg* cg,
+          double* partials) {
+  if (*(volatile int32_t*)&cg->done) return;
   __shared__ double sh[64];
   double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     acc[0] += (double)p[i] * q[i];
   double tot[1];
-  if (last_block_reduce<1>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0)
-    s->sum[3] = tot[0];
+  if (last_block_reduce<1>(acc, partials, &cg->ticket, tot, sh) && threadIdx.x == 0) {
+    if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+      cg->breakdown = 1;
+      cg->done = 1;
+    } else {
+      cg->alpha = cg->rz / tot[0];
+    }
+  }
 }
 
-// e += alpha p; r_old = r; r -= alpha q; r.r -> s[2]
+// e += alpha p; r_old = r; r -= alpha q; done when r.r <= tol2 or at maxit
 __global__ void __launch_bounds__(kB)
-gmg_update_f32(float* __restrict__ e, float* __restrict__ r, float* __restrict__ r_old,
-               const float* __restrict__ p, const float* __restrict__ q, float alpha, int64_t n,
-               GmgScalars* s, double* partials) {
+gmg_cg_update(float* __restrict__ e, float* __restrict__ r, float* __restrict__ r_old,
+              const float* __restrict__ p, const float* __restrict__ q, int64_t n, GmgCg* cg,
+              double* partials) {
+  if (*(volatile int32_t*)&cg->done) return;
   __shared__ double sh[64];
+  const float alpha = (float)cg->alpha;
   double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -571,16 +625,39 @@ gmg_update_f32(float* __restrict__ e, float* __restrict__ r, float* __restrict__
     acc[0] += (double)rn * rn;
   }
   double tot[1];
-  if (last_block_reduce<1>(acc, partials, &s->ticket, tot, sh) && threadIdx.x == 0)
-    s->sum[2] = tot[0];
+  if (last_block_reduce<1>(acc, partials, &cg->ticket, tot, sh) && threadIdx.x == 0) {
+    cg->it += 1;
+    if (!(tot[0] > cg->tol2) || cg->it >= cg->maxit) cg->done = 1;
+  }
 }
 
-// u += e
+// r.z, z.r_old, then the Polak-Ribiere beta and rz
 __global__ void __launch_bounds__(kB)
-gmg_correct(double* __restrict__ u, const float* __restrict__ e, int64_t n) {
+gmg_cg_beta(const float* __restrict__ r, const float* __restrict__ r_old,
+            const float* __restrict__ z, int64_t n, GmgCg* cg, double* partials) {
+  if (*(volatile int32_t*)&cg->done) return;
+  __shared__ double sh[64];
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+    acc[0] += (double)r[i] * zi;
+    acc[1] += (double)r_old[i] * zi;
+  }
+  double tot[2];
+  if (last_block_reduce<2>(acc, partials, &cg->ticket, tot, sh) && threadIdx.x == 0) {
+    cg->beta = (tot[0] - tot[1]) / cg->rz;
+    cg->rz = tot[0];
+  }
+}
+
+__global__ void __launch_bounds__(kB)
+gmg_cg_dir(const float* __restrict__ z, float* __restrict__ p, int64_t n, const GmgCg* cg) {
+  if (*(volatile const int32_t*)&cg->done) return;
+  const float beta = (float)cg->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    u[i] += (double)e[i];
+    p[i] = z[i] + beta * p[i];
 }
 
 // ---------------------------------------------------------------- host side
@@ -603,6 +680,8 @@ void level_dims(const mfto_handle* h, const mfto_gmg_params& p, int* n_levels, i
 void drop_graph(GmgWs* w) {
   if (w->vexec) cudaGraphExecDestroy(w->vexec);
   w->vexec = nullptr;
+  if (w->cexec) cudaGraphExecDestroy(w->cexec);
+  w->cexec = nullptr;
   w->vkey_r = nullptr;
   w->vkey_z = nullptr;
 }
@@ -861,6 +940,67 @@ mfto_status vcycle_graph(mfto_handle* h, GmgWs* w, const float* r, float* z) {
   return MFTO_OK;
 }
 
+// cg_chunk_len inner CG iterations on the handle's FP32 vectors as one graph
+mfto_status cg_chunk_graph(mfto_handle* h, GmgWs* w) {
+  const mfto_gmg_params &a = w->cprm, &b = w->prm;
+  const int chunk = cg_chunk_len(h);
+  const bool same = w->cexec && w->cchunk == chunk && a.max_levels == b.max_levels &&
+                    a.coarse_max_dofs == b.coarse_max_dofs && a.nu_pre == b.nu_pre &&
+                    a.nu_post == b.nu_post && a.omega == b.omega;
+  if (!same) {
+    if (w->cexec) cudaGraphExecDestroy(w->cexec);
+    w->cexec = nullptr;
+    if (!h->cap_stream &&
+        cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return mfto_fail(h, MFTO_CUDA_ERROR, "CG graph: cannot create the capture stream");
+    const int64_t n = h->n_dof;
+    const int g = reduction_blocks(n, kB);
+    float *r32 = h->d_r32, *z32 = h->d_z32, *p32 = h->d_p0_32, *q32 = h->d_q32,
+          *e32 = h->d_e32, *ro32 = h->d_p1_32;
+    cudaStream_t saved = h->stream;
+    const bool timing = h->kv_timing;
+    const int64_t launches = h->launches;
+    h->kv_timing = false;
+    h->stream = h->cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    mfto_status s = e == cudaSuccess ? MFTO_OK : MFTO_CUDA_ERROR;
+    for (int k = 0; k < chunk && s == MFTO_OK; ++k) {
+      s = kv_launch(h, MFTO_FORM_F32, w->d_E32, p32, q32);
+      if (s != MFTO_OK) break;
+      h->launches += 2;
+      gmg_cg_pq<<<g, kB, 0, h->stream>>>(p32, q32, n, w->d_cg, h->d_partials);
+      gmg_cg_update<<<g, kB, 0, h->stream>>>(e32, r32, ro32, p32, q32, n, w->d_cg,
+                                             h->d_partials);
+      s = vcycle(h, w, 0, r32, z32);
+      if (s != MFTO_OK) break;
+      h->launches += 2;
+      gmg_cg_beta<<<g, kB, 0, h->stream>>>(r32, ro32, z32, n, w->d_cg, h->d_partials);
+      gmg_cg_dir<<<g, kB, 0, h->stream>>>(z32, p32, n, w->d_cg);
+    }
+    if (e == cudaSuccess) e = cudaStreamEndCapture(h->cap_stream, &graph);
+    h->stream = saved;
+    h->kv_timing = timing;
+    w->cnodes = h->launches - launches;
+    h->launches = launches;
+    if (s != MFTO_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return s != MFTO_OK ? s
+                          : mfto_fail(h, MFTO_CUDA_ERROR, "CG graph capture: %s",
+                                      cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&w->cexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      w->cexec = nullptr;
+      return mfto_fail(h, MFTO_CUDA_ERROR, "CG graph instantiate: %s", cudaGetErrorString(e));
+    }
+    w->cprm = w->prm;
+    w->cchunk = chunk;
+  }
+  return MFTO_OK;
+}
+
 mfto_status check_params(mfto_handle* h, const mfto_gmg_params& p) {
   MFTO_REQUIRE(h, p.max_levels >= 1 && p.max_levels <= MFTO_GMG_MAX_LEVELS,
                "mfto_gmg_setup: max_levels in [1, MFTO_GMG_MAX_LEVELS]");
@@ -880,10 +1020,15 @@ GmgWs* ws(mfto_handle* h) {
     mfto_default_gmg_params(&w->prm);
     if (cudaMalloc((void**)&w->d_s, sizeof(GmgScalars)) != cudaSuccess ||
         cudaMallocHost((void**)&w->h_s, sizeof(GmgScalars)) != cudaSuccess ||
-        cudaMemset(w->d_s, 0, sizeof(GmgScalars)) != cudaSuccess) {
+        cudaMemset(w->d_s, 0, sizeof(GmgScalars)) != cudaSuccess ||
+        cudaMalloc((void**)&w->d_cg, sizeof(GmgCg)) != cudaSuccess ||
+        cudaMallocHost((void**)&w->h_cg, sizeof(GmgCg)) != cudaSuccess ||
+        cudaMemset(w->d_cg, 0, sizeof(GmgCg)) != cudaSuccess) {
       cudaGetLastError();
       if (w->d_s) cudaFree(w->d_s);
       if (w->h_s) cudaFreeHost(w->h_s);
+      if (w->d_cg) cudaFree(w->d_cg);
+      if (w->h_cg) cudaFreeHost(w->h_cg);
       delete w;
       return nullptr;
     }
@@ -907,6 +1052,8 @@ void gmg_release(mfto_handle* h) {
   free_levels(w);
   if (w->d_s) cudaFree(w->d_s);
   if (w->h_s) cudaFreeHost(w->h_s);
+  if (w->d_cg) cudaFree(w->d_cg);
+  if (w->h_cg) cudaFreeHost(w->h_cg);
   delete w;
   h->gmg = nullptr;
 }
@@ -1010,8 +1157,7 @@ mfto_status gmg_solve_mixed(mfto_handle* h, GmgWs* w, const double* E, const dou
                             mfto_solve_stats* st) {
   const int64_t n = h->n_dof;
   double *r = h->d_r, *q = h->d_q;
-  float *r32 = h->d_r32, *z32 = h->d_z32, *p32 = h->d_p0_32, *q32 = h->d_q32, *e32 = h->d_e32,
-        *ro32 = h->d_p1_32;
+  float *r32 = h->d_r32, *z32 = h->d_z32, *p32 = h->d_p0_32, *e32 = h->d_e32, *ro32 = h->d_p1_32;
   const int g = reduction_blocks(n, kB);
   const double rtol = h->p.rtol, itol = w->prm.inner_tol;
   mfto_status s;
@@ -1042,42 +1188,27 @@ mfto_status gmg_solve_mixed(mfto_handle* h, GmgWs* w, const double* E, const dou
     }
     if (outer == 50) break;
     prev = rel;
-    // FP32 CG on K e = r from e = 0
+    // FP32 CG on K e = r from e = 0: start, then graph chunks of iterations
+    // with the scalars on the device, polled once per chunk
     MFTO_CUDA(h, cudaMemsetAsync(e32, 0, sizeof(float) * n, h->stream));
     if ((s = vcycle_graph(h, w, r32, z32)) != MFTO_OK) return s;
-    h->launches += 2;
+    h->launches += 3;
     gmg_dot2_f32<<<g, kB, 0, h->stream>>>(r32, ro32, z32, n, 1, w->d_s, h->d_partials);
     MFTO_LAUNCH_CHECK(h);
-    gmg_dir_f32<<<g, kB, 0, h->stream>>>(z32, p32, 0.0f, n);
+    gmg_first_dir_f32<<<g, kB, 0, h->stream>>>(z32, p32, n);
     MFTO_LAUNCH_CHECK(h);
-    if ((s = read_scalars(h, w)) != MFTO_OK) return s;
-    double rz = w->h_s->sum[0];
-    for (int it = 1; it <= h->p.maxit; ++it) {
-      if ((s = kv_launch(h, MFTO_FORM_F32, w->d_E32, p32, q32)) != MFTO_OK) return s;
-      h->launches++;
-      gmg_pq_f32<<<g, kB, 0, h->stream>>>(p32, q32, n, w->d_s, h->d_partials);
-      MFTO_LAUNCH_CHECK(h);
-      if ((s = read_scalars(h, w)) != MFTO_OK) return s;
-      const double pq = w->h_s->sum[3];
-      if (!(pq > 0.0) || !std::isfinite(pq) || !(rz > 0.0)) break;
-      h->launches++;
-      gmg_update_f32<<<g, kB, 0, h->stream>>>(e32, r32, ro32, p32, q32, (float)(rz / pq), n,
-                                              w->d_s, h->d_partials);
-      MFTO_LAUNCH_CHECK(h);
-      st->iterations++;
-      if ((s = vcycle_graph(h, w, r32, z32)) != MFTO_OK) return s;
-      h->launches++;
-      gmg_dot2_f32<<<g, kB, 0, h->stream>>>(r32, ro32, z32, n, 0, w->d_s, h->d_partials);
-      MFTO_LAUNCH_CHECK(h);
-      if ((s = read_scalars(h, w)) != MFTO_OK) return s;
-      const double rr_in = w->h_s->sum[2];
-      if (!(sqrt(rr_in / rr) > itol)) break;     // reached (or not a number: stop)
-      const double beta = (w->h_s->sum[0] - w->h_s->sum[1]) / rz;
-      rz = w->h_s->sum[0];
-      h->launches++;
-      gmg_dir_f32<<<g, kB, 0, h->stream>>>(z32, p32, (float)beta, n);
-      MFTO_LAUNCH_CHECK(h);
+    gmg_cg_start<<<1, 1, 0, h->stream>>>(w->d_cg, w->d_s, itol * itol * rr, h->p.maxit);
+    MFTO_LAUNCH_CHECK(h);
+    if ((s = cg_chunk_graph(h, w)) != MFTO_OK) return s;
+    for (;;) {
+      MFTO_CUDA(h, cudaGraphLaunch(w->cexec, h->stream));
+      h->launches += w->cnodes;
+      MFTO_CUDA(h, cudaMemcpyAsync(w->h_cg, w->d_cg, sizeof(GmgCg), cudaMemcpyDeviceToHost,
+                                   h->stream));
+      MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+      if (w->h_cg->done) break;
     }
+    st->iterations += w->h_cg->it;
     h->launches++;
     gmg_correct<<<g, kB, 0, h->stream>>>(u, e32, n);
     MFTO_LAUNCH_CHECK(h);
@@ -1124,7 +1255,7 @@ mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* 
   h->launches += 2;
   gmg_zdot<<<g, kB, 0, h->stream>>>(z32, r, r_old, z, n, 1, w->d_s, h->d_partials);
   MFTO_LAUNCH_CHECK(h);
-  gmg_dir<<<g, kB, 0, h->stream>>>(z, pv, 0.0, n);
+  gmg_dir<<<g, kB, 0, h->stream>>>(z, pv, 0.0, n, 1);
   MFTO_LAUNCH_CHECK(h);
   if ((s = read_scalars(h, w)) != MFTO_OK) return s;
   double rz = w->h_s->sum[0];
@@ -1166,7 +1297,7 @@ mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* 
     const double beta = (rz_new - zr_old) / rz;
     rz = rz_new;
     h->launches++;
-    gmg_dir<<<g, kB, 0, h->stream>>>(z, pv, beta, n);
+    gmg_dir<<<g, kB, 0, h->stream>>>(z, pv, beta, n, 0);
     MFTO_LAUNCH_CHECK(h);
   }
   MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
