@@ -693,8 +693,9 @@ def kappa_run(args):
 def protocol_run(args):
     """The SIMP-120 continuation protocol (projection, four phases, restarts,
     selected iterate) on the paper's point-load cantilever of --workload's
-    size, with the mixed solve and with plain FP64 Jacobi-PCG: wall time,
-    selected compliance and iteration counts, one JSON line each."""
+    size, with the solvers of --protocol-solvers (mixed: FP32 Jacobi-PCG in
+    FP64 refinement; f64: plain FP64 Jacobi-PCG; gmg: the multigrid solve):
+    wall time, selected compliance and iteration counts, one JSON line each."""
     import torch
     from paper_2604_18020_gb300 import mfto, workloads as W
     dev = torch.device("cuda:0")
@@ -702,13 +703,15 @@ def protocol_run(args):
     m0 = base.mesh
     P = W.cantilever_point(m0.nelx, m0.nely, m0.nelz)
     m = P.mesh
-    for solver in ("mixed", "f64"):
+    for solver in args.protocol_solvers.split(","):
         params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
         with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params) as h:
-            if solver == "mixed":
+            if solver in ("mixed", "gmg"):
                 h.set_solver(mfto.FORM_F32, args.inner_tol)
                 h.set_ir_mode(IR_MODES[args.ir_mode])
                 tuned = h.kv_autotune()
+            if solver == "gmg":                        # V-cycle CG, default parameters
+                h.set_gmg_solver(True)
             rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
             u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
             f = torch.tensor(P.f, device=dev)
@@ -982,6 +985,8 @@ def main():
                     choices=["bench", "profile", "pcg", "compare", "learned", "kappa", "protocol",
                              "hard", "ubench", "gmg"])
     ap.add_argument("--protocol-iters", type=int, default=120)
+    ap.add_argument("--protocol-solvers", default="mixed,f64",
+                    help="--mode protocol: comma-separated solvers among mixed, f64, gmg")
     ap.add_argument("--gmg-case", default=None,
                     choices=["cantilever_120x60x30", "torsion_55x55x165", "cantilever_256x128x150"],
                     help="--mode gmg: run this case only")
