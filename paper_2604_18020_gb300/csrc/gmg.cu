@@ -55,6 +55,7 @@ struct GmgLevel {
   float* d_K = nullptr;         // [n_elem][576] element matrices (levels >= 1)
   float* d_dinv = nullptr;      // 1 / l1 row sums
   float* x = nullptr;           // correction (levels >= 1)
+  float* x2 = nullptr;          // its other half when a fused sweep writes a copy
   float* b = nullptr;           // right-hand side (levels >= 1)
   float* t = nullptr;           // operator applied to x
 };
@@ -274,16 +275,29 @@ gmg_l1_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, in
   }
 }
 
-// y = A x on a coarse level: 8 lanes per node, lane s taking the node's three
-// rows of adjacent element s (corner offsets the bits of s), summed over the
-// 8 lanes in a fixed order; identity rows on fixed DOFs (their columns are
-// zero in the element matrices)
+// Coarse-level operator, 8 lanes per node: lane s takes the node's three
+// rows of adjacent element s (corner offsets the bits of s), and the 8 lanes
+// are summed in a fixed order; identity rows on fixed DOFs (their columns are
+// zero in the element matrices).  Three forms, so that a smoothing sweep and
+// its operator application are one launch:
+//   KV_PLAIN:  y = A x;
+//   KV_FIRST:  the first sweep from zero, x = omega D1^-1 b (neighbours' values
+//              formed on the fly), written to xo, and y = A x;
+//   KV_SMOOTH: xo = x + omega D1^-1 (b - A x) (xo distinct from x).
+enum { KV_PLAIN = 0, KV_FIRST = 1, KV_SMOOTH = 2 };
+
+template <int MODE>
 __global__ void __launch_bounds__(kB)
 gmg_kv_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, int nx, int ny,
-              int nz, const float* __restrict__ x, float* __restrict__ y) {
+              int nz, const float* __restrict__ x, const float* __restrict__ b,
+              const float* __restrict__ dinv, float omega, float* __restrict__ y,
+              float* __restrict__ xo) {
   const int64_t n_node = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   const int sub = threadIdx.x & 7;
   const int dx = sub & 1, dy = (sub >> 1) & 1, dz = sub >> 2;
+  auto val = [&](int64_t d) -> float {
+    return MODE == KV_FIRST ? omega * dinv[d] * b[d] : x[d];
+  };
   // every lane of a warp runs the same number of trips (the shuffles need all 32)
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
   const int64_t trips = (n_node + groups - 1) / groups;
@@ -302,9 +316,9 @@ gmg_kv_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, in
 #pragma unroll
         for (int lb = 0; lb < 8; ++lb) {
           const int64_t m = nid(ex + (lb & 1), ey + ((lb >> 1) & 1), ez + (lb >> 2), nx, ny);
-          xe[3 * lb] = x[3 * m];
-          xe[3 * lb + 1] = x[3 * m + 1];
-          xe[3 * lb + 2] = x[3 * m + 2];
+          xe[3 * lb] = val(3 * m);
+          xe[3 * lb + 1] = val(3 * m + 1);
+          xe[3 * lb + 2] = val(3 * m + 2);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -329,9 +343,17 @@ gmg_kv_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, in
       acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 4);
     }
     if (sub < 3 && nd < n_node) {
+      const int64_t d = 3 * nd + sub;
       const uint8_t fm = fixed[nd];
       const float a = sub == 0 ? acc[0] : (sub == 1 ? acc[1] : acc[2]);
-      y[3 * nd + sub] = ((fm >> sub) & 1) ? x[3 * nd + sub] : a;
+      const float xd = val(d);
+      const float yd = ((fm >> sub) & 1) ? xd : a;
+      if (MODE == KV_SMOOTH) {
+        xo[d] = xd + omega * dinv[d] * (b[d] - yd);
+      } else {
+        y[d] = yd;
+        if (MODE == KV_FIRST) xo[d] = xd;
+      }
     }
   }
 }
@@ -691,7 +713,7 @@ void free_levels(GmgWs* w) {
   for (int l = 0; l < MFTO_GMG_MAX_LEVELS; ++l) {
     GmgLevel& v = w->lv[l];
     if (l > 0 && v.d_fixed) cudaFree(v.d_fixed);
-    void* ptrs[] = {v.d_K, v.d_dinv, v.x, v.b, v.t};
+    void* ptrs[] = {v.d_K, v.d_dinv, v.x, v.x2, v.b, v.t};
     for (void* q : ptrs)
       if (q) cudaFree(q);
     v = GmgLevel();
@@ -753,6 +775,7 @@ mfto_status gmg_alloc(mfto_handle* h, GmgWs* w, const mfto_gmg_params& p) {
       MFTO_CUDA(h, cudaMemcpy(v.d_fixed, w->h_fixed[l].data(), v.n_node, cudaMemcpyHostToDevice));
       if ((s = A((void**)&v.d_K, sizeof(float) * 576 * v.n_elem)) != MFTO_OK) return s;
       if ((s = A((void**)&v.x, sizeof(float) * v.n_dof)) != MFTO_OK) return s;
+      if ((s = A((void**)&v.x2, sizeof(float) * v.n_dof)) != MFTO_OK) return s;
       if ((s = A((void**)&v.b, sizeof(float) * v.n_dof)) != MFTO_OK) return s;
     }
     if ((s = A((void**)&v.d_dinv, sizeof(float) * v.n_dof)) != MFTO_OK) return s;
@@ -822,18 +845,25 @@ mfto_status coarse_inverse(mfto_handle* h, GmgWs* w) {
       Am[(size_t)i * n + j] = t / d;
     }
   }
+  // L^T row-major, so that both substitutions read contiguous rows
+  std::vector<double> Lt((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k <= i; ++k) Lt[(size_t)k * n + i] = Am[(size_t)i * n + k];
   std::vector<float> inv((size_t)n * n);
   std::vector<double> col(n);
   for (int c = 0; c < n; ++c) {
-    for (int i = 0; i < n; ++i) {       // L y = e_c
+    for (int i = 0; i < c; ++i) col[i] = 0.0;
+    for (int i = c; i < n; ++i) {       // L y = e_c (y is zero above row c)
       double t = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) t -= Am[(size_t)i * n + k] * col[k];
-      col[i] = t / Am[(size_t)i * n + i];
+      const double* Li = &Am[(size_t)i * n];
+      for (int k = c; k < i; ++k) t -= Li[k] * col[k];
+      col[i] = t / Li[i];
     }
     for (int i = n - 1; i >= 0; --i) {  // L^T x = y
       double t = col[i];
-      for (int k = i + 1; k < n; ++k) t -= Am[(size_t)k * n + i] * col[k];
-      col[i] = t / Am[(size_t)i * n + i];
+      const double* Ri = &Lt[(size_t)i * n];
+      for (int k = i + 1; k < n; ++k) t -= Ri[k] * col[k];
+      col[i] = t / Ri[i];
     }
     for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = (float)col[i];
   }
@@ -846,17 +876,22 @@ mfto_status apply_level(mfto_handle* h, GmgWs* w, int l, const float* x, float* 
   if (l == 0) return kv_launch(h, MFTO_FORM_F32, w->d_E32, x, y);
   const GmgLevel& v = w->lv[l];
   h->launches++;
-  gmg_kv_coarse<<<grid_of(8 * v.n_node), kB, 0, h->stream>>>(v.d_K, v.d_fixed, v.nx, v.ny, v.nz, x,
-                                                             y);
+  gmg_kv_coarse<KV_PLAIN><<<grid_of(8 * v.n_node), kB, 0, h->stream>>>(
+      v.d_K, v.d_fixed, v.nx, v.ny, v.nz, x, nullptr, nullptr, 0.0f, y, nullptr);
   MFTO_LAUNCH_CHECK(h);
   return MFTO_OK;
 }
 
-mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x) {
+// One V-cycle from level l: b the right-hand side, x the caller's output
+// buffer on level 0; on coarse levels the result lands in lv[l].x or
+// lv[l].x2 (fused sweeps alternate between them) and *out says which.
+mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
+                   float** out = nullptr) {
   const int L = w->n_levels - 1;
   const GmgLevel& v = w->lv[l];
   const mfto_gmg_params& p = w->prm;
   mfto_status s;
+  if (out) *out = x;
   if (l == L) {
     h->launches++;
     gmg_coarse_solve<<<std::max(1, std::min(1024, (w->n_c + 7) / 8)), kB, 0, h->stream>>>(
@@ -865,31 +900,61 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x) {
     return MFTO_OK;
   }
   const int g = grid_of(v.n_dof);
+  const int gk = grid_of(8 * v.n_node);
   const float om = (float)p.omega;
-  for (int k = 0; k < p.nu_pre; ++k) {
-    if (k > 0 && (s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
+  const bool fused = l > 0;              // coarse levels: sweep and operator in one launch
+  float* other = fused ? (x == v.x ? v.x2 : v.x) : nullptr;
+  // pre-smoothing; on exit v.t = A x
+  if (p.nu_pre == 0) {
+    MFTO_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * v.n_dof, h->stream));
+  } else if (fused) {
     h->launches++;
-    gmg_smooth<<<g, kB, 0, h->stream>>>(x, b, v.t, v.d_dinv, v.n_dof, om, k == 0);
+    gmg_kv_coarse<KV_FIRST><<<gk, kB, 0, h->stream>>>(v.d_K, v.d_fixed, v.nx, v.ny, v.nz, nullptr,
+                                                      b, v.d_dinv, om, v.t, x);
     MFTO_LAUNCH_CHECK(h);
+    for (int k = 1; k < p.nu_pre; ++k) {
+      h->launches++;
+      gmg_kv_coarse<KV_SMOOTH><<<gk, kB, 0, h->stream>>>(v.d_K, v.d_fixed, v.nx, v.ny, v.nz, x,
+                                                         b, v.d_dinv, om, nullptr, other);
+      MFTO_LAUNCH_CHECK(h);
+      std::swap(x, other);
+    }
+    if (p.nu_pre > 1 && (s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
+  } else {
+    for (int k = 0; k < p.nu_pre; ++k) {
+      if (k > 0 && (s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
+      h->launches++;
+      gmg_smooth<<<g, kB, 0, h->stream>>>(x, b, v.t, v.d_dinv, v.n_dof, om, k == 0);
+      MFTO_LAUNCH_CHECK(h);
+    }
+    if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
   }
-  if (p.nu_pre == 0) MFTO_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * v.n_dof, h->stream));
-  else if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
   const GmgLevel& c = w->lv[l + 1];
   h->launches++;
   gmg_restrict<<<grid_of(c.n_dof), kB, 0, h->stream>>>(
       b, p.nu_pre ? v.t : nullptr, v.d_fixed, v.nx, v.ny, v.nz, c.d_fixed, c.nx, c.ny, c.nz, c.b);
   MFTO_LAUNCH_CHECK(h);
-  if ((s = vcycle(h, w, l + 1, c.b, c.x)) != MFTO_OK) return s;
+  float* xc = nullptr;
+  if ((s = vcycle(h, w, l + 1, c.b, c.x, &xc)) != MFTO_OK) return s;
   h->launches++;
-  gmg_prolong<<<grid_of(v.n_node), kB, 0, h->stream>>>(c.x, c.d_fixed, c.nx, c.ny, v.d_fixed,
+  gmg_prolong<<<grid_of(v.n_node), kB, 0, h->stream>>>(xc, c.d_fixed, c.nx, c.ny, v.d_fixed,
                                                        v.nx, v.ny, v.nz, x);
   MFTO_LAUNCH_CHECK(h);
   for (int k = 0; k < p.nu_post; ++k) {
-    if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
-    h->launches++;
-    gmg_smooth<<<g, kB, 0, h->stream>>>(x, b, v.t, v.d_dinv, v.n_dof, om, 0);
-    MFTO_LAUNCH_CHECK(h);
+    if (fused) {
+      h->launches++;
+      gmg_kv_coarse<KV_SMOOTH><<<gk, kB, 0, h->stream>>>(v.d_K, v.d_fixed, v.nx, v.ny, v.nz, x,
+                                                         b, v.d_dinv, om, nullptr, other);
+      MFTO_LAUNCH_CHECK(h);
+      std::swap(x, other);
+    } else {
+      if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
+      h->launches++;
+      gmg_smooth<<<g, kB, 0, h->stream>>>(x, b, v.t, v.d_dinv, v.n_dof, om, 0);
+      MFTO_LAUNCH_CHECK(h);
+    }
   }
+  if (out) *out = x;
   return MFTO_OK;
 }
 
