@@ -912,6 +912,9 @@ def gmg_run(args):
                    ("jacobi_mixed_continue_0.1", lambda: h.ir_solve(E, f, uu, inner_tol=0.1))]
         gmg_cfg = [("gmg_f64", dict(mixed=0)), ("gmg_mixed", dict(mixed=1)),
                    ("gmg_mixed_nu2", dict(mixed=1, nu_pre=2, nu_post=2))]
+        # the fine sweeps on tensor-core K.v forms (a BF16 smoother inside a V-cycle)
+        gmg_cfg += [(f"gmg_mixed_smoother_{fm}", dict(mixed=1, smoother_form=mfto.FORMS[fm]))
+                    for fm in ("tf32", "bf16", "f16", "bf16x3")]
         if name == "cantilever_256x128x150":
             solvers = solvers[1:]                      # FP64 Jacobi: minutes at this size
         if args.gmg_only:                              # the default multigrid solve alone

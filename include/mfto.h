@@ -689,6 +689,10 @@ typedef struct {
                                around an FP32 CG (default 1)              */
   double inner_tol;         /* relative tolerance of each FP32 CG, (0, 1)
                                (default 1e-2)                             */
+  int32_t smoother_form;    /* K.v form of the level-0 sweeps and residual
+                               inside the cycle: MFTO_FORM_F32 (default) or
+                               a tensor-core form (TF32, BF16, FP16 and
+                               their split variants)                      */
 } mfto_gmg_params;
 void mfto_default_gmg_params(mfto_gmg_params* p);
 /* Build the hierarchy for the moduli d_E (FP64 [elements]) with params p

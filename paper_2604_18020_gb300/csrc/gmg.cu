@@ -873,7 +873,7 @@ mfto_status coarse_inverse(mfto_handle* h, GmgWs* w) {
 }
 
 mfto_status apply_level(mfto_handle* h, GmgWs* w, int l, const float* x, float* y) {
-  if (l == 0) return kv_launch(h, MFTO_FORM_F32, w->d_E32, x, y);
+  if (l == 0) return kv_launch(h, (mfto_form)w->prm.smoother_form, w->d_E32, x, y);
   const GmgLevel& v = w->lv[l];
   h->launches++;
   gmg_kv_coarse<KV_PLAIN><<<grid_of(8 * v.n_node), kB, 0, h->stream>>>(
@@ -965,7 +965,8 @@ mfto_status vcycle_graph(mfto_handle* h, GmgWs* w, const float* r, float* z) {
   const mfto_gmg_params &a = w->vprm, &b = w->prm;
   const bool same = w->vexec && w->vkey_r == r && w->vkey_z == z &&
                     a.max_levels == b.max_levels && a.coarse_max_dofs == b.coarse_max_dofs &&
-                    a.nu_pre == b.nu_pre && a.nu_post == b.nu_post && a.omega == b.omega;
+                    a.nu_pre == b.nu_pre && a.nu_post == b.nu_post && a.omega == b.omega &&
+                    a.smoother_form == b.smoother_form;
   if (!same) {
     drop_graph(w);
     if (!h->cap_stream &&
@@ -1011,7 +1012,8 @@ mfto_status cg_chunk_graph(mfto_handle* h, GmgWs* w) {
   const int chunk = cg_chunk_len(h);
   const bool same = w->cexec && w->cchunk == chunk && a.max_levels == b.max_levels &&
                     a.coarse_max_dofs == b.coarse_max_dofs && a.nu_pre == b.nu_pre &&
-                    a.nu_post == b.nu_post && a.omega == b.omega;
+                    a.nu_post == b.nu_post && a.omega == b.omega &&
+                    a.smoother_form == b.smoother_form;
   if (!same) {
     if (w->cexec) cudaGraphExecDestroy(w->cexec);
     w->cexec = nullptr;
@@ -1076,6 +1078,8 @@ mfto_status check_params(mfto_handle* h, const mfto_gmg_params& p) {
   MFTO_REQUIRE(h, p.omega > 0.0 && p.omega < 2.0, "mfto_gmg_setup: omega in (0, 2)");
   MFTO_REQUIRE(h, p.mixed == 0 || p.mixed == 1, "mfto_gmg_setup: mixed is 0 or 1");
   MFTO_REQUIRE(h, p.inner_tol > 0.0 && p.inner_tol < 1.0, "mfto_gmg_setup: inner_tol in (0, 1)");
+  MFTO_REQUIRE(h, p.smoother_form == MFTO_FORM_F32 || tc_form(p.smoother_form),
+               "mfto_gmg_setup: smoother_form is MFTO_FORM_F32 or a tensor-core form");
   return MFTO_OK;
 }
 
@@ -1134,6 +1138,7 @@ extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
   p->omega = 1.3;
   p->mixed = 1;
   p->inner_tol = 1e-2;
+  p->smoother_form = MFTO_FORM_F32;
 }
 
 extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
@@ -1284,13 +1289,12 @@ mfto_status gmg_solve_mixed(mfto_handle* h, GmgWs* w, const double* E, const dou
 
 }  // namespace
 
-mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* u,
-                      mfto_solve_stats* st) {
-  memset(st, 0, sizeof(*st));
-  mfto_status s = mfto_gmg_setup(h, E, nullptr);
-  if (s != MFTO_OK) return s;
-  GmgWs* w = h->gmg;
-  if (w->prm.mixed) return gmg_solve_mixed(h, w, E, f, u, st);
+namespace {
+
+// FP64 CG preconditioned by the V-cycle (mfto_gmg_params.mixed = 0)
+mfto_status gmg_solve_f64(mfto_handle* h, GmgWs* w, const double* E, const double* f, double* u,
+                          mfto_solve_stats* st) {
+  mfto_status s;
   const int64_t n = h->n_dof;
   double *r = h->d_r, *z = h->d_z, *pv = h->d_p0, *q = h->d_q, *r_old = h->d_p1;
   float *r32 = h->d_r32, *z32 = h->d_z32;
@@ -1366,6 +1370,28 @@ mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* 
     MFTO_LAUNCH_CHECK(h);
   }
   MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+  return MFTO_OK;
+}
+
+}  // namespace
+
+mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* u,
+                      mfto_solve_stats* st) {
+  memset(st, 0, sizeof(*st));
+  mfto_status s = mfto_gmg_setup(h, E, nullptr);
+  if (s != MFTO_OK) return s;
+  GmgWs* w = h->gmg;
+  // a tensor-core smoother reports a completion wait that gave up in the
+  // handle's error word
+  const bool tc = tc_form(w->prm.smoother_form);
+  if (tc) MFTO_CUDA(h, cudaMemsetAsync(&h->d_misc->error, 0, sizeof(int32_t), h->stream));
+  s = w->prm.mixed ? gmg_solve_mixed(h, w, E, f, u, st) : gmg_solve_f64(h, w, E, f, u, st);
+  if (s != MFTO_OK || !tc) return s;
+  MFTO_CUDA(h, cudaMemcpyAsync(h->h_misc, h->d_misc, sizeof(MiscScalars), cudaMemcpyDeviceToHost,
+                               h->stream));
+  MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->h_misc->error)
+    return mfto_fail(h, MFTO_CUDA_ERROR, "mfto_gmg_solve: tensor-core completion wait timed out");
   return MFTO_OK;
 }
 

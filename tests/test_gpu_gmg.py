@@ -108,6 +108,36 @@ def test_gmg_solve_matches_oracle(cuda, mixed):
     assert st.iterations <= (1.5 if mixed == 0 else 2.0) * st_o.iterations + 3
 
 
+@pytest.mark.parametrize("form", ["tf32", "bf16", "f16", "bf16x3"])
+def test_tensor_core_smoother(cuda, form):
+    """The level-0 sweeps on a tensor-core K.v (the paper's proposal of a BF16
+    smoother inside a V-cycle): the solve still reaches the oracle's solution,
+    in a bounded number of iterations."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    shape = (24, 12, 12)
+    P, rho_phys = _simp_state(shape)
+    m = P.mesh
+    fd = fem.dof_mask(P.fixed)
+    KE = fem.ke_exact()
+    edof = fem.edof_table_fast(*shape)
+    E = fem.simp_modulus(rho_phys, 3.0)
+    K = lambda v: fem.kv(KE, E, edof, v, fd)
+    u_j, _ = solve.pcg(K, fem.jacobi_diag(KE, E, edof, fd), P.f, np.zeros(m.n_dof), 1e-10)
+    its = {}
+    with mfto.Handle(*shape, P.fixed) as h:
+        for name in ("f32", form):
+            u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+            h.set_gmg_solver(False, mfto.default_gmg_params(smoother_form=mfto.FORMS[name]))
+            st = h.gmg_solve(torch.tensor(E, device=cuda), torch.tensor(P.f, device=cuda), u)
+            assert st.status == 0 and st.rel_residual <= 1e-8, name
+            ug = u.cpu().numpy()
+            assert np.linalg.norm(P.f - K(ug)) / np.linalg.norm(P.f) <= 1.5e-8
+            assert abs(P.f @ ug - P.f @ u_j) <= 1e-7 * abs(P.f @ u_j)
+            its[name] = st.iterations
+    assert its[form] <= 3 * its["f32"] + 5
+
+
 @pytest.mark.parametrize("mixed", [0, 1])
 def test_simp_steps_with_gmg_solver(cuda, mixed):
     """Three SIMP iterations on 16 x 8 x 8 with the V-cycle CG as the solver
@@ -141,6 +171,8 @@ def test_gmg_argument_checks(cuda):
             h.gmg_vcycle(torch.zeros(m.n_dof, dtype=torch.float32, device=cuda), z)
         with pytest.raises(mfto.MftoError):          # weight outside (0, 2)
             h.gmg_setup(E, mfto.default_gmg_params(omega=2.0))
+        with pytest.raises(mfto.MftoError):          # FP64 is no smoother form
+            h.gmg_setup(E, mfto.default_gmg_params(smoother_form=mfto.FORM_F64))
         with pytest.raises(mfto.MftoError) as ei:    # a single 4,875-DOF level is too large
             h.gmg_setup(E, mfto.default_gmg_params(max_levels=1))
         assert ei.value.code == mfto.TOO_LARGE
