@@ -12,7 +12,9 @@ steps are its first iterations).  The solve is the chosen form (--form
 mixed, default: FP64 iterative refinement around an FP32 inner Jacobi-PCG)
 or plain FP64 Jacobi-PCG (--form f64); with the mixed form the same steps
 are also run with plain FP64 from the same state ("plain_fp64": its SIMP
-iteration time and the largest relative compliance difference).
+iteration time and the largest relative compliance difference), and with the
+multigrid solver ("gmg": V-cycle CG in FP64 refinement, its SIMP iteration
+time and speed-ups).
 
 value: K.v throughput of the whole step, n_elem x (K.v applications in the
 timed steps) / (device time of the timed steps), in Gelem/s, with inputs
@@ -293,7 +295,7 @@ def gpu_bench(args, rank, local_rank, world):
         h_u.copy_(o_u)
     # plain FP64 Jacobi-PCG over the same steps from the same state, for the
     # "plain FP64 vs chosen form" comparison (skipped when the bench is FP64)
-    fp64 = None
+    fp64 = gmg_leg = None
     if args.form != "f64":
         h.set_solver(mfto.FORM_F64)
         t64, stats64, _, _, _, _ = timed_pass(False)
@@ -305,6 +307,18 @@ def gpu_bench(args, rank, local_rank, world):
                 "max_compliance_rel_err": max(abs(a - b) / abs(b) for a, b in zip(cf, c64)),
                 "speedup_of_chosen_form": t64 / t_ms}
         h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
+        # the same steps with the multigrid solver (V-cycle CG in FP64
+        # refinement): the library's fastest SIMP iteration, beside the K.v one
+        h.set_gmg_solver(True)
+        h.simp_step(rho, u, f)            # warm-up: hierarchy storage, graph captures
+        tg, statsg, _, _, _, _ = timed_pass(False)
+        h.set_gmg_solver(False)
+        cg_ = [s.compliance for s in statsg]
+        gmg_leg = {"simp_iter_ms": tg / args.steps,
+                   "solver_iterations": [s.cg_iterations for s in statsg],
+                   "max_compliance_rel_err_vs_fp64": max(abs(a - b) / abs(b)
+                                                         for a, b in zip(cg_, c64)),
+                   "speedup_vs_plain_fp64": t64 / tg, "speedup_vs_chosen_form": t_ms / tg}
     h2d = (h_rho.numel() + h_u.numel() + h_f.numel()) * 8
     d2h = (o_rho.numel() + o_u.numel()) * 8
     if dist:
@@ -395,6 +409,7 @@ def gpu_bench(args, rank, local_rank, world):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "plain_fp64": fp64,
+        "gmg": gmg_leg,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"]},
     }
