@@ -65,6 +65,7 @@ struct GmgWs {
   GmgLevel lv[MFTO_GMG_MAX_LEVELS];
   mfto_gmg_params prm{};
   float* d_E32 = nullptr;
+  float* d_G = nullptr;             // [8][576] unit-modulus child Galerkin matrices
   float* d_cinv = nullptr;          // dense inverse of the coarsest operator
   int n_c = 0;                      // its DOFs
   std::vector<std::vector<uint8_t>> h_fixed;   // per-level node masks
@@ -169,22 +170,80 @@ gmg_l1_fine(const float* __restrict__ E, const uint8_t* __restrict__ fixed,
   }
 }
 
+// G_c = P_c^T KE P_c for the 8 child positions (one CTA each): the Galerkin
+// matrix of a unit-modulus child, so that an interior coarse element of
+// level 1 is just sum_c E_c G_c.
+__global__ void __launch_bounds__(kB)
+gmg_child_galerkin(const float* __restrict__ ke, float* __restrict__ G) {
+  __shared__ float T[576];
+  const int ch = blockIdx.x;
+  for (int idx = threadIdx.x; idx < 576; idx += blockDim.x) {
+    const int i = idx / 24, col = idx - 24 * (idx / 24);
+    const int m = col / 3, cc = col - 3 * (col / 3);
+    float s = 0.0f;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) s = fmaf(ke[i * 24 + 3 * n + cc], phi(ch, n, m), s);
+    T[idx] = s;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 576; idx += blockDim.x) {
+    const int row = idx / 24, q = idx - 24 * (idx / 24);
+    const int m = row / 3, cc = row - 3 * (row / 3);
+    float s = 0.0f;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) s = fmaf(phi(ch, n, m), T[(3 * n + cc) * 24 + q], s);
+    G[ch * 576 + idx] = s;
+  }
+}
+
 // Element matrices of level l + 1 (dims mx, my, mz) from level l (nx, ny, nz):
 // one CTA per coarse element, children one after another through shared
 // memory (T = A_c P_c, then M += P_c^T T), M held in registers.
 template <bool FINE0>
 __global__ void __launch_bounds__(kB)
 gmg_galerkin(const float* __restrict__ Kf, const float* __restrict__ E,
-             const float* __restrict__ ke, const uint8_t* __restrict__ fixf, int nx, int ny,
-             int nz, const uint8_t* __restrict__ fixc, int mx, int my, int mz,
-             float* __restrict__ Kc) {
-  __shared__ float A[576], T[576], KEs[576];
-  if (FINE0)
+             const float* __restrict__ ke, const float* __restrict__ G,
+             const uint8_t* __restrict__ fixf, int nx, int ny, int nz,
+             const uint8_t* __restrict__ fixc, int mx, int my, int mz, float* __restrict__ Kc) {
+  __shared__ float A[576], T[576], KEs[FINE0 ? 576 : 1], Gs[FINE0 ? 8 * 576 : 1];
+  if (FINE0) {
     for (int i = threadIdx.x; i < 576; i += blockDim.x) KEs[i] = ke[i];
+    for (int i = threadIdx.x; i < 8 * 576; i += blockDim.x) Gs[i] = G[i];
+  }
   const int64_t n_c = (int64_t)mx * my * mz;
   for (int64_t e = blockIdx.x; e < n_c; e += gridDim.x) {
     const int I = (int)(e % mx), J = (int)((e / mx) % my), K = (int)(e / ((int64_t)mx * my));
     float acc[3] = {0.0f, 0.0f, 0.0f};
+    if (FINE0) {
+      // interior element: all 8 children present and no fixed DOF among the
+      // 27 fine nodes -> sum_c E_c G_c
+      bool fixed_here = false;
+      if (threadIdx.x < 27) {
+        const int a = threadIdx.x % 3, b = (threadIdx.x / 3) % 3, c = threadIdx.x / 9;
+        const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
+        fixed_here = i > nx || j > ny || k > nz || fixf[nid(i, j, k, nx, ny)] != 0;
+      }
+      const bool slow = __syncthreads_or(fixed_here) != 0 || 2 * I + 1 >= nx ||
+                        2 * J + 1 >= ny || 2 * K + 1 >= nz;
+      if (!slow) {
+        float Ec[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch)
+          Ec[ch] = E[(2 * I + (ch & 1)) + (int64_t)nx * ((2 * J + ((ch >> 1) & 1)) +
+                                                         (int64_t)ny * (2 * K + (ch >> 2)))];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int idx = threadIdx.x + r * kB;
+          if (idx < 576) {
+            float s = 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) s = fmaf(Ec[ch], Gs[ch * 576 + idx], s);
+            Kc[e * 576 + idx] = s;
+          }
+        }
+        continue;                                                 // uniform over the CTA
+      }
+    }
     for (int ch = 0; ch < 8; ++ch) {
       const int fx = 2 * I + (ch & 1), fy = 2 * J + ((ch >> 1) & 1), fz = 2 * K + (ch >> 2);
       if (fx >= nx || fy >= ny || fz >= nz) continue;            // uniform over the CTA
@@ -1119,6 +1178,8 @@ void gmg_release(mfto_handle* h) {
   if (!h || !h->gmg) return;
   GmgWs* w = h->gmg;
   free_levels(w);
+  if (w->d_E32) cudaFree(w->d_E32);
+  if (w->d_G) cudaFree(w->d_G);
   if (w->d_s) cudaFree(w->d_s);
   if (w->h_s) cudaFreeHost(w->h_s);
   if (w->d_cg) cudaFree(w->d_cg);
@@ -1154,8 +1215,9 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
   w->prm = p;
   g_sms = h->num_sms;
   if ((s = gmg_alloc(h, w, p)) != MFTO_OK) return s;
-  if (!w->d_E32) {
-    if (cudaMalloc((void**)&w->d_E32, sizeof(float) * h->n_elem) != cudaSuccess) {
+  if (!w->d_E32 || !w->d_G) {
+    if ((!w->d_E32 && cudaMalloc((void**)&w->d_E32, sizeof(float) * h->n_elem) != cudaSuccess) ||
+        (!w->d_G && cudaMalloc((void**)&w->d_G, sizeof(float) * 8 * 576) != cudaSuccess)) {
       cudaGetLastError();
       return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: cudaMalloc failed");
     }
@@ -1174,12 +1236,17 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
     const GmgLevel& c = w->lv[l + 1];
     const int g = (int)std::min<int64_t>(c.n_elem, 8LL * h->num_sms);
     h->launches++;
-    if (l == 0)
-      gmg_galerkin<true><<<g, kB, 0, h->stream>>>(nullptr, w->d_E32, h->d_ke32, f.d_fixed, f.nx,
-                                                  f.ny, f.nz, c.d_fixed, c.nx, c.ny, c.nz, c.d_K);
-    else
-      gmg_galerkin<false><<<g, kB, 0, h->stream>>>(f.d_K, nullptr, nullptr, f.d_fixed, f.nx, f.ny,
-                                                   f.nz, c.d_fixed, c.nx, c.ny, c.nz, c.d_K);
+    if (l == 0) {
+      h->launches++;
+      gmg_child_galerkin<<<8, kB, 0, h->stream>>>(h->d_ke32, w->d_G);
+      gmg_galerkin<true><<<g, kB, 0, h->stream>>>(nullptr, w->d_E32, h->d_ke32, w->d_G, f.d_fixed,
+                                                  f.nx, f.ny, f.nz, c.d_fixed, c.nx, c.ny, c.nz,
+                                                  c.d_K);
+    } else {
+      gmg_galerkin<false><<<g, kB, 0, h->stream>>>(f.d_K, nullptr, nullptr, nullptr, f.d_fixed,
+                                                   f.nx, f.ny, f.nz, c.d_fixed, c.nx, c.ny, c.nz,
+                                                   c.d_K);
+    }
     MFTO_LAUNCH_CHECK(h);
     h->launches++;
     gmg_l1_coarse<<<grid_of(c.n_node), kB, 0, h->stream>>>(c.d_K, c.d_fixed, c.nx, c.ny, c.nz,
