@@ -752,8 +752,8 @@ def hard_run(args):
     """The paper's hard problems (MBB, bridge, 150 x 50 x 25 = 187,500
     elements): cold-start FEA solves at the uniform initial density (p = 3;
     mean of 5 after one warm-up) and the 60-iteration cold-start SIMP runs of
-    the protocol, each with plain FP64 Jacobi-PCG and the mixed solve; one
-    JSON line per problem and mode."""
+    the protocol, each with plain FP64 Jacobi-PCG, the mixed solve and the
+    multigrid solve; one JSON line per problem."""
     import torch
     from paper_2604_18020_gb300 import mfto, workloads as W
     dev = torch.device("cuda:0")
@@ -762,13 +762,15 @@ def hard_run(args):
         m = P.mesh
         f = torch.tensor(P.f, device=dev)
         res = {}
-        for solver in ("f64", "mixed"):
+        for solver in ("f64", "mixed", "gmg"):
             params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8, maxit=20000)
             with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params) as h:
-                if solver == "mixed":
+                if solver in ("mixed", "gmg"):
                     h.set_solver(mfto.FORM_F32, args.inner_tol, 20000, 80)
                     h.set_ir_mode(IR_MODES[args.ir_mode])
                     h.kv_autotune()
+                if solver == "gmg":
+                    h.set_gmg_solver(True)
                 rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
                 E = torch.empty_like(rho)
                 rho_phys = torch.empty_like(rho)
@@ -782,6 +784,9 @@ def hard_run(args):
                     t = time.perf_counter()
                     if solver == "f64":
                         st = h.pcg(E, f, u)
+                        it = st.iterations
+                    elif solver == "gmg":
+                        st = h.gmg_solve(E, f, u)
                         it = st.iterations
                     else:
                         st = h.ir_solve(E, f, u, inner_tol=args.inner_tol)
@@ -808,8 +813,11 @@ def hard_run(args):
                                "simp60_selected_compliance": pst.selected_compliance,
                                "simp60_restarts": pst.restarts}
         a, b = res["f64"], res["mixed"]
+        g = res["gmg"]
         print(json.dumps({
-            "case": name, "elements": m.n_elem, "f64": a, "mixed": b,
+            "case": name, "elements": m.n_elem, "f64": a, "mixed": b, "gmg": g,
+            "gmg_fea_speedup_vs_f64": a["fea_ms"] / g["fea_ms"],
+            "gmg_simp60_speedup_vs_f64": a["simp60_s"] / g["simp60_s"],
             "fea_speedup": a["fea_ms"] / b["fea_ms"], "simp60_speedup": a["simp60_s"] / b["simp60_s"],
             "fea_compliance_rel_diff": abs(b["fea_compliance"] - a["fea_compliance"]) / abs(a["fea_compliance"]),
             "simp60_selected_compliance_rel_diff":

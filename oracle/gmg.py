@@ -43,6 +43,15 @@ these readings (the same in the CUDA library):
     Galerkin product of coarse element E alone, Phat_E^T (sum over E's
     children c of B_c^T A_c B_c) Phat_E with Phat_E the columns of Phat at
     E's DOFs -- their assembly is the Galerkin operator above;
+  * the coarsest inverse comes from an FP64 Cholesky factorisation; when a
+    pivot falls below 1e-5 of its diagonal entry the operator is taken as
+    rank deficient (a consistent singular problem such as the MBB preset,
+    whose z translation and one rotation stay free) and the inverse is that
+    of A_c + 1e-6 diag(A_c): the V-cycle stays SPD and CG still solves the
+    consistent system (the load is orthogonal to the null space); the CUDA
+    library, whose coarsest operator comes from FP32-rounded element
+    matrices, raises the shift tenfold (up to 1e-2) until its factorisation
+    succeeds, which this exact FP64 operator never needs;
   * the outer CG takes z = V(r) with the Polak-Ribiere form of beta
     (flexible CG), so a preconditioner applied in lower precision keeps the
     iteration convergent.
@@ -191,8 +200,32 @@ def build(KE, E, nelx, nely, nelz, fixed_dofs, max_levels=8, coarse_max_dofs=200
             A = (lev.P.T @ A @ lev.P + sp.diags(cf.astype(float))).tocsr()
             Ke = coarse_element_matrices(n, Ke, lev.P)
             fixed = cf
-    coarse_inv = np.linalg.inv(levels[-1].A.toarray())
+    coarse_inv = coarsest_inverse(levels[-1].A.toarray())
     return Hierarchy(levels, coarse_inv, omega, nu_pre, nu_post)
+
+
+PIVOT_RTOL = 1e-5        # pivot / diagonal below this: rank deficient
+SHIFT = 1e-6             # relative diagonal shift of a rank-deficient coarsest operator
+
+
+def cholesky_pivots_ok(A):
+    """Plain Cholesky; False when a pivot falls below PIVOT_RTOL of its
+    diagonal entry."""
+    n = A.shape[0]
+    L = np.zeros_like(A)
+    for j in range(n):
+        s = A[j, j] - L[j, :j] @ L[j, :j]
+        if not (s > PIVOT_RTOL * A[j, j]):
+            return False
+        L[j, j] = np.sqrt(s)
+        L[j + 1:, j] = (A[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return True
+
+
+def coarsest_inverse(Ac):
+    if not cholesky_pivots_ok(Ac):
+        Ac = Ac + SHIFT * np.diag(np.diag(Ac))
+    return np.linalg.inv(Ac)
 
 
 def smooth(lev, x, b, omega, sweeps):

@@ -890,12 +890,29 @@ mfto_status coarse_inverse(mfto_handle* h, GmgWs* w) {
       }
   for (int64_t d = 0; d < n; ++d)
     if (is_fixed(d)) Am[d * n + d] = 1.0;
-  // Cholesky, lower triangle in place
+  // Cholesky, lower triangle in place.  A pivot below 1e-5 of its diagonal
+  // entry marks a rank-deficient operator (a consistent singular problem:
+  // free rigid motions, as in the MBB preset); it is then factorised again
+  // with the diagonal scaled by 1 + delta, delta = 1e-6, 1e-5, ... 1e-2, the
+  // first that makes it positive definite (the FP32-rounded element matrices
+  // can leave the null space's eigenvalues slightly negative), which keeps
+  // the cycle SPD.
+  const std::vector<double> A0 = Am;
+  double shift = 0.0;
   for (int j = 0; j < n; ++j) {
     double s = Am[(size_t)j * n + j];
     for (int k = 0; k < j; ++k) s -= Am[(size_t)j * n + k] * Am[(size_t)j * n + k];
-    if (!(s > 0.0) || !std::isfinite(s))
-      return mfto_fail(h, MFTO_BREAKDOWN, "mfto_gmg_setup: coarsest operator not positive definite");
+    // a shifted operator only has to be positive definite
+    if (!(s > (shift > 0.0 ? 0.0 : 1e-5 * A0[(size_t)j * n + j])) || !std::isfinite(s)) {
+      shift = shift > 0.0 ? 10.0 * shift : 1e-6;
+      if (shift > 1.5e-2 || !std::isfinite(s))
+        return mfto_fail(h, MFTO_BREAKDOWN,
+                         "mfto_gmg_setup: coarsest operator not positive definite");
+      Am = A0;
+      for (int i = 0; i < n; ++i) Am[(size_t)i * n + i] *= 1.0 + shift;
+      j = -1;                           // restart the factorisation
+      continue;
+    }
     const double d = sqrt(s);
     Am[(size_t)j * n + j] = d;
     for (int i = j + 1; i < n; ++i) {
