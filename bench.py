@@ -319,6 +319,13 @@ def gpu_bench(args, rank, local_rank, world):
                    "max_compliance_rel_err_vs_fp64": max(abs(a - b) / abs(b)
                                                          for a, b in zip(cg_, c64)),
                    "speedup_vs_plain_fp64": t64 / tg, "speedup_vs_chosen_form": t_ms / tg}
+    # memory snapshot (the paper's VRAM table): the library's own device memory
+    # (workspace and, after the multigrid leg, its hierarchy), PyTorch's peak
+    # and the whole device's use
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    vram = {"library_bytes": h.device_bytes(),
+            "torch_max_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
+            "device_used_bytes": int(total_b - free_b)}
     h2d = (h_rho.numel() + h_u.numel() + h_f.numel()) * 8
     d2h = (o_rho.numel() + o_u.numel()) * 8
     if dist:
@@ -410,6 +417,7 @@ def gpu_bench(args, rank, local_rank, world):
         "gpu_launches": launches,
         "plain_fp64": fp64,
         "gmg": gmg_leg,
+        "vram": vram,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"]},
     }

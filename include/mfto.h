@@ -174,6 +174,12 @@ const char* mfto_last_error(const mfto_handle* h);
 /* Sizes of the mesh: elements, nodes, DOFs. */
 mfto_status mfto_sizes(const mfto_handle* h, int64_t* n_elem, int64_t* n_node,
                        int64_t* n_dof);
+/* Device memory this handle holds now, in bytes: the workspace of
+ * mfto_create (vectors, reduction buffers, scalars, element matrices), the
+ * filter stencil, and what optional parts allocated on first use (the
+ * multigrid hierarchy, the learned solve's buffers); the caller's arrays are
+ * not counted.  For VRAM reports (the paper's memory snapshots). */
+mfto_status mfto_device_bytes(const mfto_handle* h, int64_t* bytes);
 
 /* -------------------------------------------------------- device steps -- */
 

@@ -144,6 +144,8 @@ struct mfto_handle {
   struct LearnedWs* learned;
   // geometric multigrid hierarchy and V-cycle solver (gmg.cu)
   struct GmgWs* gmg;
+  // bytes of the workspace mfto_create allocated (mfto_device_bytes)
+  int64_t ws_bytes;
   // PCG graph cache: one captured chunk of check_every iterations per solver
   struct PcgGraph* pcg_graph[MFTO_PCG_SLOTS];
   // kernels launched on behalf of this handle (graph kernel nodes included)
@@ -601,6 +603,8 @@ mfto_status learned_run(mfto_handle* h, const double* E, const double* rho_phys,
 bool learned_active(const mfto_handle* h);
 void learned_release(mfto_handle* h);
 bool gmg_active(const mfto_handle* h);
+int64_t gmg_bytes(const mfto_handle* h);
+int64_t learned_bytes(const mfto_handle* h);
 void gmg_release(mfto_handle* h);
 mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* u,
                       mfto_solve_stats* st);

@@ -1207,6 +1207,22 @@ void gmg_release(mfto_handle* h) {
 
 bool gmg_active(const mfto_handle* h) { return h->gmg && h->gmg->use_in_simp; }
 
+int64_t gmg_bytes(const mfto_handle* h) {
+  const GmgWs* w = h->gmg;
+  if (!w) return 0;
+  int64_t b = sizeof(GmgScalars) + sizeof(GmgCg);
+  if (w->d_E32) b += (int64_t)sizeof(float) * h->n_elem;
+  if (w->d_G) b += (int64_t)sizeof(float) * 8 * 576;
+  for (int l = 0; l < w->n_levels; ++l) {
+    const GmgLevel& v = w->lv[l];
+    b += 2 * (int64_t)sizeof(float) * v.n_dof;                  // dinv, t
+    if (l > 0)
+      b += v.n_node + (int64_t)sizeof(float) * (576 * v.n_elem + 3 * v.n_dof);  // mask, K, x, x2, b
+  }
+  if (w->d_cinv) b += (int64_t)sizeof(float) * w->n_c * w->n_c;
+  return b;
+}
+
 extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
   if (!p) return;
   p->max_levels = MFTO_GMG_MAX_LEVELS;

@@ -254,6 +254,7 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   bool ok = true;
   auto A = [&](void** p, size_t bytes) {
     if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
+    if (ok) h->ws_bytes += (int64_t)bytes;
   };
   A((void**)&h->d_ke64, sizeof(double) * 576);
   A((void**)&h->d_ke32, sizeof(float) * 576);
@@ -418,4 +419,14 @@ extern "C" mfto_status mfto_kv_timing_read(mfto_handle* h, mfto_form form, int64
   h->ev.launches[f] = 0;
   h->ev.total_ms[f] = 0.0;
   return s;
+}
+
+extern "C" mfto_status mfto_device_bytes(const mfto_handle* h, int64_t* bytes) {
+  if (!h || !bytes) return MFTO_INVALID_ARG;
+  int64_t b = h->ws_bytes;
+  b += (int64_t)h->n_stencil * (int64_t)(3 * sizeof(int32_t) + sizeof(double));
+  if (h->d_bar) b += 128;                       // the persistent CG's barrier line
+  b += learned_bytes(h) + gmg_bytes(h);
+  *bytes = b;
+  return MFTO_OK;
 }

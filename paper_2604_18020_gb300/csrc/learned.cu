@@ -736,3 +736,15 @@ extern "C" mfto_status mfto_nn_train_energy(mfto_handle* h, mfto_nn* nn, const d
   }
   return MFTO_OK;
 }
+
+int64_t learned_bytes(const mfto_handle* h) {
+  const LearnedWs* w = h->learned;
+  if (!w) return 0;
+  int64_t b = 0;
+  if (w->x) b += (int64_t)sizeof(float) * 7 * (int64_t)w->D * w->H * w->W;
+  if (w->c) b += (int64_t)sizeof(float) * h->n_dof;
+  if (w->uk) b += (int64_t)sizeof(double) * h->n_dof;
+  if (w->amax) b += (int64_t)sizeof(unsigned int) * 2;
+  if (w->ctl) b += (int64_t)sizeof(FpcgCtl);
+  return b;
+}

@@ -131,6 +131,7 @@ SIGNATURES = {
     "mfto_set_ir_mode": (C.c_int32, [_P, C.c_int32]),
     "mfto_default_kappa_params": (None, [C.POINTER(KappaParams)]),
     "mfto_default_gmg_params": (None, [C.POINTER(GmgParams)]),
+    "mfto_device_bytes": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
     "mfto_gmg_setup": (C.c_int32, [_P, _P, C.POINTER(GmgParams)]),
     "mfto_gmg_levels": (C.c_int32, [_P, C.POINTER(C.c_int32), _P]),
     "mfto_gmg_apply": (C.c_int32, [_P, C.c_int32, _P, _P]),
@@ -455,6 +456,12 @@ class Handle:
             _ptr(v_inverse, torch.float64, self.n_dof, "v_inverse"),
             _ptr(work, torch.float64, self.n_dof, "work"), C.byref(prm), C.byref(st)), self._h)
         return st
+
+    def device_bytes(self) -> int:
+        """Device memory the handle holds (workspace and optional parts)."""
+        n = C.c_int64()
+        _check("mfto_device_bytes", lib().mfto_device_bytes(self._h, C.byref(n)), self._h)
+        return n.value
 
     # ---- geometric multigrid
     def gmg_setup(self, E, params=None):

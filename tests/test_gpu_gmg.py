@@ -202,3 +202,29 @@ def test_gmg_on_singular_mbb(cuda):
             assert st.status == 0 and st.rel_residual <= 1e-8, mixed
             assert np.linalg.norm(P.f - K(ug)) / np.linalg.norm(P.f) <= 1.5e-8
             assert abs(P.f @ ug - P.f @ u_j) <= 1e-7 * abs(P.f @ u_j)
+
+
+def test_device_bytes_accounts_for_the_hierarchy(cuda):
+    """mfto_device_bytes: at least the handle's DOF vectors after creation,
+    and exactly the hierarchy's arrays more after a multigrid setup (element
+    matrices, masks, vectors of every level, the coarsest inverse)."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(24, 12, 12)
+    m = P.mesh
+    with mfto.Handle(24, 12, 12, P.fixed) as h:
+        b0 = h.device_bytes()
+        assert b0 >= m.n_dof * (6 * 8 + 7 * 4) + m.n_elem * (6 * 8 + 4)
+        h.gmg_setup(torch.ones(m.n_elem, dtype=torch.float64, device=cuda))
+        dims = h.gmg_levels()
+        exp = 8 * 576 * 4 + m.n_elem * 4                        # G table, FP32 moduli
+        for l, (nx, ny, nz) in enumerate(dims):
+            n_node = (nx + 1) * (ny + 1) * (nz + 1)
+            exp += 2 * 4 * 3 * n_node
+            if l > 0:
+                exp += n_node + 4 * (576 * nx * ny * nz + 3 * 3 * n_node)
+        nx, ny, nz = dims[-1]
+        n_c = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+        exp += 4 * n_c * n_c
+        grown = h.device_bytes() - b0
+        assert exp <= grown <= exp + 256                          # plus two scalar blocks
