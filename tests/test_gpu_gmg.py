@@ -228,3 +228,27 @@ def test_device_bytes_accounts_for_the_hierarchy(cuda):
         exp += 4 * n_c * n_c
         grown = h.device_bytes() - b0
         assert exp <= grown <= exp + 256                          # plus two scalar blocks
+
+
+def test_gmg_is_bit_reproducible(cuda):
+    """No atomics anywhere in the hierarchy, the cycle or the CG sums: two
+    setups, V-cycles and solves from the same inputs agree bit for bit."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    shape = (20, 10, 10)
+    P, rho_phys = _simp_state(shape, n_iter=4)
+    m = P.mesh
+    E = torch.tensor(fem.simp_modulus(rho_phys, 3.0), device=cuda)
+    f = torch.tensor(P.f, device=cuda)
+    r = torch.tensor(W.vec_random(m.n_dof, seed=9), dtype=torch.float32, device=cuda)
+    outs = []
+    for _ in range(2):
+        with mfto.Handle(*shape, P.fixed) as h:
+            h.gmg_setup(E)
+            z = torch.empty_like(r)
+            h.gmg_vcycle(r, z)
+            u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+            st = h.gmg_solve(E, f, u)
+            outs.append((z.clone(), u.clone(), st.iterations))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
