@@ -538,7 +538,7 @@ mfto_status learned_run(mfto_handle* h, const double* E, const double* rho_phys,
     if (outer < 64) out->history[outer] = rel;
     if (!isfinite(rel)) { out->status = MFTO_BREAKDOWN; break; }
     if (rel <= h->p.rtol) { out->status = MFTO_OK; break; }
-    if (mode == 2) { out->status = MFTO_NOT_CONVERGED; break; }   // FP64 PCG ran: final verdict
+    if (mode == 2) { out->status = MFTO_NOT_CONVERGED; break; }   // FP64 PCG ran: its outcome is final
     if (outer > 0) {
       stalls = rel > 0.9 * prev ? stalls + 1 : 0;
       if (stalls >= 2) {
