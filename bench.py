@@ -1007,6 +1007,66 @@ def gmg_run(args):
         print(json.dumps(row), flush=True)
 
 
+def scaling_run(args):
+    """Cold-start FEA solves of the paper's point-load cantilever at uniform
+    density 0.5 (p = 3) on its size ladder (216k, 512k, 1M, 2.0M, 4.9M, 8M
+    elements: 120x60x30 .. 400x200x100) and one size beyond it (600x300x150,
+    27M elements), to rtol 1e-8: plain FP64 Jacobi-PCG up to 1M, the mixed
+    Jacobi solve up to 8M, the multigrid solve everywhere; mean of the timed
+    calls after one warm-up, with the handle's device memory.  One JSON line
+    per size."""
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+    reps = max(1, min(args.steps, 3))
+    sizes = [(120, 60, 30), (160, 80, 40), (200, 100, 50), (252, 126, 63), (340, 170, 85),
+             (400, 200, 100), (600, 300, 150)]
+    for shape in sizes:
+        P = W.cantilever_point(*shape)
+        m = P.mesh
+        params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8, maxit=50000)
+        row = {"case": "cantilever_point_" + "x".join(map(str, shape)), "elements": m.n_elem,
+               "dofs": m.n_dof}
+        with mfto.Handle(*shape, P.fixed, params=params) as h:
+            h.kv_autotune()
+            h.set_solver(mfto.FORM_F32, 1e-1, 50000, 80)
+            h.set_ir_mode(IR_MODES["continue"])
+            E = torch.full((m.n_elem,), 0.5 ** 3, dtype=torch.float64, device=dev)
+            f = torch.tensor(P.f, device=dev)
+            u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+            solvers = [("gmg_mixed", lambda: h.gmg_solve(E, f, u))]
+            if m.n_elem <= 8_000_000:
+                solvers.insert(0, ("jacobi_mixed", lambda: h.ir_solve(E, f, u, inner_tol=0.1)))
+            if m.n_elem <= 1_000_000:
+                solvers.insert(0, ("jacobi_f64", lambda: h.pcg(E, f, u)))
+            c_ref = None
+            for key, fn in solvers:
+                u.zero_()
+                fn()
+                ts = []
+                for _ in range(reps):
+                    u.zero_()
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    st = fn()
+                    torch.cuda.synchronize()
+                    ts.append(time.perf_counter() - t)
+                its = st.inner_iterations if hasattr(st, "inner_iterations") else st.iterations
+                c = float((f * u).sum())
+                c_ref = c if c_ref is None else c_ref
+                row[key] = {"s": sum(ts) / len(ts), "iterations": its,
+                            "status": mfto.STATUS_NAMES[st.status],
+                            "rel_residual": st.rel_residual,
+                            "compliance_rel_diff": abs(c - c_ref) / abs(c_ref)}
+            free_b, total_b = torch.cuda.mem_get_info(dev)
+            row["library_bytes"] = h.device_bytes()
+            row["device_used_bytes"] = int(total_b - free_b)
+            row["gmg_levels"] = len(h.gmg_levels())
+        del E, f, u
+        torch.cuda.empty_cache()
+        print(json.dumps(row), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1017,7 +1077,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench",
                     choices=["bench", "profile", "pcg", "compare", "learned", "kappa", "protocol",
-                             "hard", "ubench", "gmg"])
+                             "hard", "ubench", "gmg", "scaling"])
     ap.add_argument("--protocol-iters", type=int, default=120)
     ap.add_argument("--protocol-solvers", default="mixed,f64",
                     help="--mode protocol: comma-separated solvers among mixed, f64, gmg")
@@ -1070,6 +1130,9 @@ def main():
         return
     if args.mode == "gmg":
         gmg_run(args)
+        return
+    if args.mode == "scaling":
+        scaling_run(args)
         return
     if args.mode != "bench":
         profile_run(args)
