@@ -557,7 +557,17 @@ def compare_run(args):
         dt, _ = sync_time(lambda: h.pcg(E, fr, ur))
         t_f64 += dt
         c64.append(float(fr @ ur))
+    # the multigrid solve of the 8 cases on one hierarchy
+    h.gmg_solve_multi(E, F, U, nr)                       # warm-up (storage, graph captures)
+    U.zero_()
+    t_gmg, sts_g = sync_time(lambda: h.gmg_solve_multi(E, F, U, nr))
+    c_gmg = [float(F[r * m.n_dof:(r + 1) * m.n_dof] @ U[r * m.n_dof:(r + 1) * m.n_dof])
+             for r in range(nr)]
     out.append({"case": "cantilever_100x50x50_8rhs", "multi_rhs_mixed_s": t_multi,
+                "gmg_multi_s": t_gmg, "gmg_statuses": [mfto.STATUS_NAMES[s.status] for s in sts_g],
+                "gmg_iterations": [s.iterations for s in sts_g],
+                "gmg_compliance_rel_err_vs_f64": max(abs(a - b) / abs(b)
+                                                     for a, b in zip(c_gmg, c64)),
                 "single_mixed_x8_s": t_single, "plain_f64_x8_s": t_f64,
                 "statuses": [mfto.STATUS_NAMES[s.status] for s in sts],
                 "max_rel_residual": max(s.rel_residual for s in sts),

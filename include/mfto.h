@@ -726,6 +726,12 @@ mfto_status mfto_gmg_vcycle(mfto_handle* h, const float* d_r, float* d_z);
  * Outcome in st (iterations = CG iterations, summed over the corrections). */
 mfto_status mfto_gmg_solve(mfto_handle* h, const double* d_E, const double* d_f, double* d_u,
                            mfto_solve_stats* st);
+/* nrhs load cases with one modulus field (the multi-RHS workload): one
+ * hierarchy for d_E, then mfto_gmg_solve's iteration for each case.  d_F and
+ * d_U FP64 [nrhs][DOFs] (d_U: initial guesses in, solutions out), st: nrhs
+ * entries. */
+mfto_status mfto_gmg_solve_multi(mfto_handle* h, const double* d_E, const double* d_F,
+                                 double* d_U, int32_t nrhs, mfto_solve_stats* st);
 /* on != 0: mfto_simp_step solves with mfto_gmg_solve (params p, NULL keeps the
  * current ones); on = 0: back to the solver of mfto_set_solver. */
 mfto_status mfto_set_gmg_solver(mfto_handle* h, int32_t on, const mfto_gmg_params* p);

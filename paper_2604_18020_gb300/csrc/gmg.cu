@@ -1475,11 +1475,11 @@ mfto_status gmg_solve_f64(mfto_handle* h, GmgWs* w, const double* E, const doubl
 
 }  // namespace
 
-mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* u,
-                      mfto_solve_stats* st) {
+// One solve on the hierarchy already built for E.
+static mfto_status gmg_solve_built(mfto_handle* h, const double* E, const double* f, double* u,
+                                   mfto_solve_stats* st) {
   memset(st, 0, sizeof(*st));
-  mfto_status s = mfto_gmg_setup(h, E, nullptr);
-  if (s != MFTO_OK) return s;
+  mfto_status s;
   GmgWs* w = h->gmg;
   // a tensor-core smoother reports a completion wait that gave up in the
   // handle's error word
@@ -1493,6 +1493,28 @@ mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* 
   if (h->h_misc->error)
     return mfto_fail(h, MFTO_CUDA_ERROR, "mfto_gmg_solve: tensor-core completion wait timed out");
   return MFTO_OK;
+}
+
+mfto_status gmg_solve(mfto_handle* h, const double* E, const double* f, double* u,
+                      mfto_solve_stats* st) {
+  mfto_status s = mfto_gmg_setup(h, E, nullptr);
+  if (s != MFTO_OK) {
+    memset(st, 0, sizeof(*st));
+    return s;
+  }
+  return gmg_solve_built(h, E, f, u, st);
+}
+
+extern "C" mfto_status mfto_gmg_solve_multi(mfto_handle* h, const double* d_E, const double* d_F,
+                                            double* d_U, int32_t nrhs, mfto_solve_stats* st) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, d_E && d_F && d_U && st, "mfto_gmg_solve_multi: null pointer");
+  MFTO_REQUIRE(h, nrhs >= 1, "mfto_gmg_solve_multi: nrhs >= 1");
+  mfto_status s = mfto_gmg_setup(h, d_E, nullptr);           // one hierarchy for every case
+  if (s != MFTO_OK) return s;
+  for (int32_t r = 0; r < nrhs && s == MFTO_OK; ++r)
+    s = gmg_solve_built(h, d_E, d_F + (size_t)r * h->n_dof, d_U + (size_t)r * h->n_dof, &st[r]);
+  return s;
 }
 
 extern "C" mfto_status mfto_gmg_solve(mfto_handle* h, const double* d_E, const double* d_f,

@@ -132,6 +132,7 @@ SIGNATURES = {
     "mfto_default_kappa_params": (None, [C.POINTER(KappaParams)]),
     "mfto_default_gmg_params": (None, [C.POINTER(GmgParams)]),
     "mfto_device_bytes": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
+    "mfto_gmg_solve_multi": (C.c_int32, [_P, _P, _P, _P, C.c_int32, _P]),
     "mfto_gmg_setup": (C.c_int32, [_P, _P, C.POINTER(GmgParams)]),
     "mfto_gmg_levels": (C.c_int32, [_P, C.POINTER(C.c_int32), _P]),
     "mfto_gmg_apply": (C.c_int32, [_P, C.c_int32, _P, _P]),
@@ -497,6 +498,16 @@ class Handle:
             _ptr(f, torch.float64, self.n_dof, "f"), _ptr(u, torch.float64, self.n_dof, "u"),
             C.byref(st)), self._h)
         return st
+
+    def gmg_solve_multi(self, E, F, U, nrhs):
+        """nrhs load cases (F, U: [nrhs * n_dof] FP64) on one hierarchy."""
+        import torch
+        st = (SolveStats * nrhs)()
+        _check("mfto_gmg_solve_multi", lib().mfto_gmg_solve_multi(
+            self._h, _ptr(E, torch.float64, self.n_elem, "E"),
+            _ptr(F, torch.float64, nrhs * self.n_dof, "F"),
+            _ptr(U, torch.float64, nrhs * self.n_dof, "U"), nrhs, st), self._h)
+        return list(st)
 
     def set_gmg_solver(self, on=True, params=None):
         _check("mfto_set_gmg_solver", lib().mfto_set_gmg_solver(

@@ -252,3 +252,60 @@ def test_gmg_is_bit_reproducible(cuda):
             outs.append((z.clone(), u.clone(), st.iterations))
     assert torch.equal(outs[0][0], outs[1][0])
     assert torch.equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
+
+
+def test_gmg_full_size_bench_configuration(cuda):
+    """120x60x30 (216,000 elements, 686,433 DOFs), the configuration and
+    solver settings the benchmark's multigrid leg uses, on a filtered random
+    design (E from 1e-9 to 1): the hierarchy equals the oracle's, the solve's
+    true residual (the oracle's K.v of the GPU solution) holds the tolerance,
+    and its compliance f.u equals the sum of the oracle's element energies."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    from oracle import simp as osimp
+    shape = (120, 60, 30)
+    P = W.cantilever(*shape)
+    m = P.mesh
+    fd = fem.dof_mask(P.fixed)
+    KE = fem.ke_exact()
+    edof = fem.edof_table_fast(*shape)
+    rho = cone.filter_fwd(W.rho_binary(m, seed=2, volfrac=0.3), *shape, 1.5)
+    E = fem.simp_modulus(rho, 3.0)
+    with mfto.Handle(*shape, P.fixed) as h:
+        prm = mfto.default_gmg_params()
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+        st = h.gmg_solve(torch.tensor(E, device=cuda), torch.tensor(P.f, device=cuda), u)
+        assert h.gmg_levels() == gmg.level_dims(*shape, max_levels=prm.max_levels,
+                                                coarse_max_dofs=prm.coarse_max_dofs)
+    ug = u.cpu().numpy()
+    assert st.status == 0 and st.rel_residual <= 1e-8
+    r = P.f - fem.kv(KE, E, edof, ug, fd)
+    assert np.linalg.norm(r) / np.linalg.norm(P.f) <= 1.5e-8
+    c_elem = float(np.sum(E * osimp.element_energy(KE, edof, ug)))
+    assert abs(c_elem - P.f @ ug) <= 1e-7 * abs(P.f @ ug)
+
+
+def test_gmg_solve_multi_load_cases(cuda):
+    """Four load cases of the multi-RHS cantilever on one hierarchy: each case
+    reaches the oracle's Jacobi-PCG compliance and true residual."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    shape = (16, 8, 8)
+    P = W.multi_rhs_cantilever(*shape, nrhs=4, seed=3)
+    m = P.mesh
+    fd = fem.dof_mask(P.fixed)
+    KE = fem.ke_exact()
+    edof = fem.edof_table_fast(*shape)
+    E = fem.simp_modulus(W.rho_random(m, seed=4, lo=0.05, hi=1.0), 3.0)
+    K = lambda v: fem.kv(KE, E, edof, v, fd)
+    d = fem.jacobi_diag(KE, E, edof, fd)
+    with mfto.Handle(*shape, P.fixed) as h:
+        U = torch.zeros(4 * m.n_dof, dtype=torch.float64, device=cuda)
+        sts = h.gmg_solve_multi(torch.tensor(E, device=cuda),
+                                torch.tensor(P.f.reshape(-1), device=cuda), U, 4)
+    Ug = U.cpu().numpy().reshape(4, m.n_dof)
+    for r in range(4):
+        assert sts[r].status == 0 and sts[r].rel_residual <= 1e-8
+        u_j, _ = solve.pcg(K, d, P.f[r], np.zeros(m.n_dof), 1e-10)
+        assert np.linalg.norm(P.f[r] - K(Ug[r])) / np.linalg.norm(P.f[r]) <= 1.5e-8
+        assert abs(P.f[r] @ Ug[r] - P.f[r] @ u_j) <= 1e-7 * abs(P.f[r] @ u_j)
