@@ -699,6 +699,10 @@ typedef struct {
                                inside the cycle: MFTO_FORM_F32 (default) or
                                a tensor-core form (TF32, BF16, FP16 and
                                their split variants)                      */
+  int32_t matfree_level1;   /* level 1 applied as Phat^T K Phat with the
+                               FP32 fine operator instead of its element
+                               matrices: 1 always, -1 never, 0 (default)
+                               when those matrices exceed 96 MiB          */
 } mfto_gmg_params;
 void mfto_default_gmg_params(mfto_gmg_params* p);
 /* Build the hierarchy for the moduli d_E (FP64 [elements]) with params p

@@ -66,6 +66,9 @@ struct GmgWs {
   mfto_gmg_params prm{};
   float* d_E32 = nullptr;
   float* d_G = nullptr;             // [8][576] unit-modulus child Galerkin matrices
+  bool mf1 = false;                 // level 1 applied as Phat^T K Phat (no matrices read)
+  float* mf_s0 = nullptr;           // its two fine-level scratch vectors
+  float* mf_s1 = nullptr;
   float* d_cinv = nullptr;          // dense inverse of the coarsest operator
   int n_c = 0;                      // its DOFs
   std::vector<std::vector<uint8_t>> h_fixed;   // per-level node masks
@@ -428,19 +431,21 @@ gmg_smooth(float* __restrict__ x, const float* __restrict__ b, const float* __re
   }
 }
 
-// bc = Phat^T (b - t) (t = NULL: the residual is b); zero on fixed coarse
-// DOFs.  One thread per coarse DOF.
+// bc = Phat^T (b - t) (t = NULL: the residual is b); on fixed coarse DOFs
+// zero, or xid there when given (the identity rows of a coarse operator
+// applied as Phat^T A Phat).  One thread per coarse DOF.
 __global__ void __launch_bounds__(kB)
 gmg_restrict(const float* __restrict__ bf, const float* __restrict__ tf,
              const uint8_t* __restrict__ fixf, int nx, int ny, int nz,
-             const uint8_t* __restrict__ fixc, int mx, int my, int mz, float* __restrict__ bc) {
+             const uint8_t* __restrict__ fixc, int mx, int my, int mz, float* __restrict__ bc,
+             const float* __restrict__ xid) {
   const int64_t n_cd = 3 * (int64_t)(mx + 1) * (my + 1) * (mz + 1);
   for (int64_t cd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cd < n_cd;
        cd += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cn = cd / 3;
     const int c = (int)(cd - 3 * cn);
     if ((fixc[cn] >> c) & 1) {
-      bc[cd] = 0.0f;
+      bc[cd] = xid ? xid[cd] : 0.0f;
       continue;
     }
     const int I = (int)(cn % (mx + 1));
@@ -470,10 +475,12 @@ gmg_restrict(const float* __restrict__ bf, const float* __restrict__ tf,
   }
 }
 
-// xf += Phat xc on the free fine DOFs
+// xf += Phat xc on the free fine DOFs (add = 1), or xf = Phat xc (add = 0:
+// the fixed fine DOFs written as zero)
 __global__ void __launch_bounds__(kB)
 gmg_prolong(const float* __restrict__ xc, const uint8_t* __restrict__ fixc, int mx, int my,
-            const uint8_t* __restrict__ fixf, int nx, int ny, int nz, float* __restrict__ xf) {
+            const uint8_t* __restrict__ fixf, int nx, int ny, int nz, float* __restrict__ xf,
+            int add) {
   const int64_t n_fn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n_fn;
        f += (int64_t)gridDim.x * blockDim.x) {
@@ -481,7 +488,7 @@ gmg_prolong(const float* __restrict__ xc, const uint8_t* __restrict__ fixc, int 
     const int j = (int)((f / (nx + 1)) % (ny + 1));
     const int k = (int)(f / ((int64_t)(nx + 1) * (ny + 1)));
     const uint8_t fm = fixf[f];
-    if (fm == 7) continue;
+    if (fm == 7 && add) continue;
     const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
     const int k0 = k >> 1, k1 = (k + 1) >> 1;
     float acc[3] = {0.0f, 0.0f, 0.0f};
@@ -506,8 +513,14 @@ gmg_prolong(const float* __restrict__ xc, const uint8_t* __restrict__ fixc, int 
       }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      if (!((fm >> c) & 1)) xf[3 * f + c] += acc[c];
+    for (int c = 0; c < 3; ++c) {
+      const bool fixed_c = (fm >> c) & 1;
+      if (add) {
+        if (!fixed_c) xf[3 * f + c] += acc[c];
+      } else {
+        xf[3 * f + c] = fixed_c ? 0.0f : acc[c];
+      }
+    }
   }
 }
 
@@ -779,6 +792,10 @@ void free_levels(GmgWs* w) {
   }
   if (w->d_cinv) cudaFree(w->d_cinv);
   w->d_cinv = nullptr;
+  if (w->mf_s0) cudaFree(w->mf_s0);
+  if (w->mf_s1) cudaFree(w->mf_s1);
+  w->mf_s0 = w->mf_s1 = nullptr;
+  w->mf1 = false;
   w->n_levels = 0;
   w->ready = false;
 }
@@ -951,6 +968,22 @@ mfto_status coarse_inverse(mfto_handle* h, GmgWs* w) {
 mfto_status apply_level(mfto_handle* h, GmgWs* w, int l, const float* x, float* y) {
   if (l == 0) return kv_launch(h, (mfto_form)w->prm.smoother_form, w->d_E32, x, y);
   const GmgLevel& v = w->lv[l];
+  if (l == 1 && w->mf1) {
+    // A_1 x = Phat^T K (Phat x) with the FP32 fine operator: no element
+    // matrices read (the stored ones serve the setup only)
+    const GmgLevel& f = w->lv[0];
+    h->launches++;
+    gmg_prolong<<<grid_of(f.n_node), kB, 0, h->stream>>>(x, v.d_fixed, v.nx, v.ny, f.d_fixed, f.nx,
+                                                         f.ny, f.nz, w->mf_s0, 0);
+    MFTO_LAUNCH_CHECK(h);
+    mfto_status s = kv_launch(h, MFTO_FORM_F32, w->d_E32, w->mf_s0, w->mf_s1);
+    if (s != MFTO_OK) return s;
+    h->launches++;
+    gmg_restrict<<<grid_of(v.n_dof), kB, 0, h->stream>>>(w->mf_s1, nullptr, f.d_fixed, f.nx, f.ny,
+                                                         f.nz, v.d_fixed, v.nx, v.ny, v.nz, y, x);
+    MFTO_LAUNCH_CHECK(h);
+    return MFTO_OK;
+  }
   h->launches++;
   gmg_kv_coarse<KV_PLAIN><<<grid_of(8 * v.n_node), kB, 0, h->stream>>>(
       v.d_K, v.d_fixed, v.nx, v.ny, v.nz, x, nullptr, nullptr, 0.0f, y, nullptr);
@@ -978,7 +1011,8 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
   const int g = grid_of(v.n_dof);
   const int gk = grid_of(8 * v.n_node);
   const float om = (float)p.omega;
-  const bool fused = l > 0;              // coarse levels: sweep and operator in one launch
+  // coarse levels with stored matrices: sweep and operator in one launch
+  const bool fused = l > 0 && !(l == 1 && w->mf1);
   float* other = fused ? (x == v.x ? v.x2 : v.x) : nullptr;
   // pre-smoothing; on exit v.t = A x
   if (p.nu_pre == 0) {
@@ -1008,13 +1042,14 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
   const GmgLevel& c = w->lv[l + 1];
   h->launches++;
   gmg_restrict<<<grid_of(c.n_dof), kB, 0, h->stream>>>(
-      b, p.nu_pre ? v.t : nullptr, v.d_fixed, v.nx, v.ny, v.nz, c.d_fixed, c.nx, c.ny, c.nz, c.b);
+      b, p.nu_pre ? v.t : nullptr, v.d_fixed, v.nx, v.ny, v.nz, c.d_fixed, c.nx, c.ny, c.nz, c.b,
+      nullptr);
   MFTO_LAUNCH_CHECK(h);
   float* xc = nullptr;
   if ((s = vcycle(h, w, l + 1, c.b, c.x, &xc)) != MFTO_OK) return s;
   h->launches++;
   gmg_prolong<<<grid_of(v.n_node), kB, 0, h->stream>>>(xc, c.d_fixed, c.nx, c.ny, v.d_fixed,
-                                                       v.nx, v.ny, v.nz, x);
+                                                       v.nx, v.ny, v.nz, x, 1);
   MFTO_LAUNCH_CHECK(h);
   for (int k = 0; k < p.nu_post; ++k) {
     if (fused) {
@@ -1042,7 +1077,7 @@ mfto_status vcycle_graph(mfto_handle* h, GmgWs* w, const float* r, float* z) {
   const bool same = w->vexec && w->vkey_r == r && w->vkey_z == z &&
                     a.max_levels == b.max_levels && a.coarse_max_dofs == b.coarse_max_dofs &&
                     a.nu_pre == b.nu_pre && a.nu_post == b.nu_post && a.omega == b.omega &&
-                    a.smoother_form == b.smoother_form;
+                    a.smoother_form == b.smoother_form && a.matfree_level1 == b.matfree_level1;
   if (!same) {
     drop_graph(w);
     if (!h->cap_stream &&
@@ -1089,7 +1124,7 @@ mfto_status cg_chunk_graph(mfto_handle* h, GmgWs* w) {
   const bool same = w->cexec && w->cchunk == chunk && a.max_levels == b.max_levels &&
                     a.coarse_max_dofs == b.coarse_max_dofs && a.nu_pre == b.nu_pre &&
                     a.nu_post == b.nu_post && a.omega == b.omega &&
-                    a.smoother_form == b.smoother_form;
+                    a.smoother_form == b.smoother_form && a.matfree_level1 == b.matfree_level1;
   if (!same) {
     if (w->cexec) cudaGraphExecDestroy(w->cexec);
     w->cexec = nullptr;
@@ -1156,6 +1191,8 @@ mfto_status check_params(mfto_handle* h, const mfto_gmg_params& p) {
   MFTO_REQUIRE(h, p.inner_tol > 0.0 && p.inner_tol < 1.0, "mfto_gmg_setup: inner_tol in (0, 1)");
   MFTO_REQUIRE(h, p.smoother_form == MFTO_FORM_F32 || tc_form(p.smoother_form),
                "mfto_gmg_setup: smoother_form is MFTO_FORM_F32 or a tensor-core form");
+  MFTO_REQUIRE(h, p.matfree_level1 >= -1 && p.matfree_level1 <= 1,
+               "mfto_gmg_setup: matfree_level1 is -1, 0 or 1");
   return MFTO_OK;
 }
 
@@ -1220,6 +1257,7 @@ int64_t gmg_bytes(const mfto_handle* h) {
       b += v.n_node + (int64_t)sizeof(float) * (576 * v.n_elem + 3 * v.n_dof);  // mask, K, x, x2, b
   }
   if (w->d_cinv) b += (int64_t)sizeof(float) * w->n_c * w->n_c;
+  if (w->mf_s0) b += 2 * (int64_t)sizeof(float) * h->n_dof;
   return b;
 }
 
@@ -1233,6 +1271,7 @@ extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
   p->mixed = 1;
   p->inner_tol = 1e-2;
   p->smoother_form = MFTO_FORM_F32;
+  p->matfree_level1 = 0;
 }
 
 extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
@@ -1248,6 +1287,22 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
   w->prm = p;
   g_sms = h->num_sms;
   if ((s = gmg_alloc(h, w, p)) != MFTO_OK) return s;
+  // level 1 matrix-free when its matrices would not stay in L2 (auto), or as
+  // asked; the matrices are still formed for the smoother and level 2
+  {
+    const bool want = w->n_levels >= 2 &&
+                      (p.matfree_level1 == 1 ||
+                       (p.matfree_level1 == 0 &&
+                        (int64_t)sizeof(float) * 576 * w->lv[1].n_elem > (int64_t)96 << 20));
+    if (want && !w->mf_s0) {
+      if (cudaMalloc((void**)&w->mf_s0, sizeof(float) * h->n_dof) != cudaSuccess ||
+          cudaMalloc((void**)&w->mf_s1, sizeof(float) * h->n_dof) != cudaSuccess) {
+        cudaGetLastError();
+        return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: cudaMalloc failed");
+      }
+    }
+    w->mf1 = want;
+  }
   if (!w->d_E32 || !w->d_G) {
     if ((!w->d_E32 && cudaMalloc((void**)&w->d_E32, sizeof(float) * h->n_elem) != cudaSuccess) ||
         (!w->d_G && cudaMalloc((void**)&w->d_G, sizeof(float) * 8 * 576) != cudaSuccess)) {

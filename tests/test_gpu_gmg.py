@@ -28,10 +28,13 @@ def _setup(shape, seed=3, **kw):
     return P, m, fd, E, Ed, h, H
 
 
+@pytest.mark.parametrize("matfree", [-1, 1])
 @pytest.mark.parametrize("shape", [(24, 12, 12), (13, 7, 5)])
-def test_levels_and_operators_match_oracle(cuda, shape):
+def test_levels_and_operators_match_oracle(cuda, shape, matfree):
+    """Every level's operator against the oracle's Galerkin product; level 1
+    from its element matrices (-1) and as Phat^T K Phat (1)."""
     import torch
-    P, m, fd, E, Ed, h, H = _setup(shape)
+    P, m, fd, E, Ed, h, H = _setup(shape, matfree_level1=matfree)
     with h:
         assert h.gmg_levels() == [lev.dims for lev in H.levels]
         rng = np.random.default_rng(7)
@@ -44,10 +47,12 @@ def test_levels_and_operators_match_oracle(cuda, shape):
             assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max(), li
 
 
-@pytest.mark.parametrize("shape,nu", [((24, 12, 12), 2), ((13, 7, 5), 1), ((9, 6, 4), 0)])
-def test_vcycle_matches_oracle(cuda, shape, nu):
+@pytest.mark.parametrize("shape,nu,matfree", [((24, 12, 12), 2, -1), ((13, 7, 5), 1, -1),
+                                              ((9, 6, 4), 0, -1), ((24, 12, 12), 1, 1),
+                                              ((13, 7, 5), 2, 1)])
+def test_vcycle_matches_oracle(cuda, shape, nu, matfree):
     import torch
-    P, m, fd, E, Ed, h, H = _setup(shape, nu_pre=nu, nu_post=nu)
+    P, m, fd, E, Ed, h, H = _setup(shape, nu_pre=nu, nu_post=nu, matfree_level1=matfree)
     with h:
         r = W.vec_random(m.n_dof, seed=11)
         r[fd] = 0.0
@@ -74,8 +79,8 @@ def _simp_state(shape, n_iter=6):
     return P, cone.filter_fwd(rho, *shape, 1.5)
 
 
-@pytest.mark.parametrize("mixed", [0, 1])
-def test_gmg_solve_matches_oracle(cuda, mixed):
+@pytest.mark.parametrize("mixed,matfree", [(0, 0), (1, 0), (1, 1)])
+def test_gmg_solve_matches_oracle(cuda, mixed, matfree):
     """A SIMP state of the 24 x 12 x 12 cantilever (E from 1e-9 to 1): the
     V-cycle CG (FP64, or FP64 refinement around FP32 CGs) reaches the
     tolerance with the oracle's true residual, the oracle's compliance, and
@@ -91,7 +96,7 @@ def test_gmg_solve_matches_oracle(cuda, mixed):
     E = fem.simp_modulus(rho_phys, 3.0)
     K = lambda v: fem.kv(KE, E, edof, v, fd)
     u_j, _ = solve.pcg(K, fem.jacobi_diag(KE, E, edof, fd), P.f, np.zeros(m.n_dof), 1e-10)
-    prm = mfto.default_gmg_params(mixed=mixed)
+    prm = mfto.default_gmg_params(mixed=mixed, matfree_level1=matfree)
     H = gmg.build(KE, E, *shape, fd, max_levels=prm.max_levels,
                   coarse_max_dofs=prm.coarse_max_dofs, omega=prm.omega, nu_pre=prm.nu_pre,
                   nu_post=prm.nu_post)
