@@ -703,6 +703,10 @@ typedef struct {
                                FP32 fine operator instead of its element
                                matrices: 1 always, -1 never, 0 (default)
                                when those matrices exceed 96 MiB          */
+  int32_t continue_dir;     /* mixed solve: each FP32 CG after the first
+                               continues the previous one's direction,
+                               p = z + (r.z / (r.z)_prev) p (1, default),
+                               or starts from p = z (0)                   */
 } mfto_gmg_params;
 void mfto_default_gmg_params(mfto_gmg_params* p);
 /* Build the hierarchy for the moduli d_E (FP64 [elements]) with params p

@@ -650,6 +650,19 @@ gmg_dot2_f32(const float* __restrict__ r, const float* __restrict__ r_old,
   }
 }
 
+// first direction of a continued inner CG: p = z + (r.z / (r.z)_prev) p, with
+// r.z from the start's dot product (s[0]) and (r.z)_prev the previous inner
+// CG's last (cg->rz, read before gmg_cg_start replaces it)
+__global__ void __launch_bounds__(kB)
+gmg_cont_dir_f32(const float* __restrict__ z, float* __restrict__ p, int64_t n,
+                 const GmgScalars* s, const GmgCg* cg) {
+  const double prev = cg->rz;
+  const float beta = (prev > 0.0 && isfinite(prev)) ? (float)(s->sum[0] / prev) : 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = beta == 0.0f ? z[i] : z[i] + beta * p[i];
+}
+
 // first direction of an inner CG: p = z (p itself is not read)
 __global__ void __launch_bounds__(kB)
 gmg_first_dir_f32(const float* __restrict__ z, float* __restrict__ p, int64_t n) {
@@ -1193,6 +1206,8 @@ mfto_status check_params(mfto_handle* h, const mfto_gmg_params& p) {
                "mfto_gmg_setup: smoother_form is MFTO_FORM_F32 or a tensor-core form");
   MFTO_REQUIRE(h, p.matfree_level1 >= -1 && p.matfree_level1 <= 1,
                "mfto_gmg_setup: matfree_level1 is -1, 0 or 1");
+  MFTO_REQUIRE(h, p.continue_dir == 0 || p.continue_dir == 1,
+               "mfto_gmg_setup: continue_dir is 0 or 1");
   return MFTO_OK;
 }
 
@@ -1272,6 +1287,7 @@ extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
   p->inner_tol = 1e-2;
   p->smoother_form = MFTO_FORM_F32;
   p->matfree_level1 = 0;
+  p->continue_dir = 1;
 }
 
 extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
@@ -1388,6 +1404,7 @@ mfto_status gmg_solve_mixed(mfto_handle* h, GmgWs* w, const double* E, const dou
   mfto_status s;
   double prev = 0.0;
   int stalls = 0;
+  bool cont = false;                   // continue the last inner direction
   st->status = MFTO_NOT_CONVERGED;
   for (int outer = 0; outer <= 50; ++outer) {
     if ((s = kv_launch(h, MFTO_FORM_F64, E, u, q)) != MFTO_OK) return s;
@@ -1420,7 +1437,10 @@ mfto_status gmg_solve_mixed(mfto_handle* h, GmgWs* w, const double* E, const dou
     h->launches += 3;
     gmg_dot2_f32<<<g, kB, 0, h->stream>>>(r32, ro32, z32, n, 1, w->d_s, h->d_partials);
     MFTO_LAUNCH_CHECK(h);
-    gmg_first_dir_f32<<<g, kB, 0, h->stream>>>(z32, p32, n);
+    // continue the previous inner CG's direction (reliable updating), or
+    // start from p = z
+    if (cont) gmg_cont_dir_f32<<<g, kB, 0, h->stream>>>(z32, p32, n, w->d_s, w->d_cg);
+    else gmg_first_dir_f32<<<g, kB, 0, h->stream>>>(z32, p32, n);
     MFTO_LAUNCH_CHECK(h);
     gmg_cg_start<<<1, 1, 0, h->stream>>>(w->d_cg, w->d_s, itol * itol * rr, h->p.maxit);
     MFTO_LAUNCH_CHECK(h);
@@ -1434,6 +1454,7 @@ mfto_status gmg_solve_mixed(mfto_handle* h, GmgWs* w, const double* E, const dou
       if (w->h_cg->done) break;
     }
     st->iterations += w->h_cg->it;
+    cont = w->prm.continue_dir && w->h_cg->it > 0 && !w->h_cg->breakdown;
     h->launches++;
     gmg_correct<<<g, kB, 0, h->stream>>>(u, e32, n);
     MFTO_LAUNCH_CHECK(h);

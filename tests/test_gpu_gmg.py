@@ -79,8 +79,8 @@ def _simp_state(shape, n_iter=6):
     return P, cone.filter_fwd(rho, *shape, 1.5)
 
 
-@pytest.mark.parametrize("mixed,matfree", [(0, 0), (1, 0), (1, 1)])
-def test_gmg_solve_matches_oracle(cuda, mixed, matfree):
+@pytest.mark.parametrize("mixed,matfree,cont", [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 0, 1)])
+def test_gmg_solve_matches_oracle(cuda, mixed, matfree, cont):
     """A SIMP state of the 24 x 12 x 12 cantilever (E from 1e-9 to 1): the
     V-cycle CG (FP64, or FP64 refinement around FP32 CGs) reaches the
     tolerance with the oracle's true residual, the oracle's compliance, and
@@ -96,7 +96,7 @@ def test_gmg_solve_matches_oracle(cuda, mixed, matfree):
     E = fem.simp_modulus(rho_phys, 3.0)
     K = lambda v: fem.kv(KE, E, edof, v, fd)
     u_j, _ = solve.pcg(K, fem.jacobi_diag(KE, E, edof, fd), P.f, np.zeros(m.n_dof), 1e-10)
-    prm = mfto.default_gmg_params(mixed=mixed, matfree_level1=matfree)
+    prm = mfto.default_gmg_params(mixed=mixed, matfree_level1=matfree, continue_dir=cont)
     H = gmg.build(KE, E, *shape, fd, max_levels=prm.max_levels,
                   coarse_max_dofs=prm.coarse_max_dofs, omega=prm.omega, nu_pre=prm.nu_pre,
                   nu_post=prm.nu_post)
