@@ -43,6 +43,12 @@ these readings (the same in the CUDA library):
     Galerkin product of coarse element E alone, Phat_E^T (sum over E's
     children c of B_c^T A_c B_c) Phat_E with Phat_E the columns of Phat at
     E's DOFs -- their assembly is the Galerkin operator above;
+  * optional Chebyshev smoother (Adams, Brezina, Hu and Tuminaro, J. Comput.
+    Phys. 2003): each sweep is the degree-k Chebyshev iteration for
+    D1^-1 A x = D1^-1 b on the interval [lmax / 30, lmax] with lmax = 1, the
+    l1 bound (so no eigenvalue estimate is needed); from x the error is
+    multiplied by T_k((theta - D1^-1 A) / delta) / T_k(theta / delta),
+    theta and delta the interval's centre and half width;
   * the coarsest inverse comes from an FP64 Cholesky factorisation; when a
     pivot falls below 1e-5 of its diagonal entry the operator is taken as
     rank deficient (a consistent singular problem such as the MBB preset,
@@ -178,10 +184,14 @@ class Hierarchy:
     omega: float
     nu_pre: int
     nu_post: int
+    cheb_degree: int = 0      # 0: l1-Jacobi sweeps; k >= 1: Chebyshev sweeps of degree k
+
+
+CHEB_RATIO = 30.0            # lmax / lmin of the Chebyshev interval, lmax = 1
 
 
 def build(KE, E, nelx, nely, nelz, fixed_dofs, max_levels=8, coarse_max_dofs=200, omega=1.0,
-          nu_pre=2, nu_post=2):
+          nu_pre=2, nu_post=2, cheb_degree=0):
     dims = level_dims(nelx, nely, nelz, max_levels, coarse_max_dofs)
     edof = fem.edof_table_fast(nelx, nely, nelz)
     n_dof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
@@ -201,7 +211,7 @@ def build(KE, E, nelx, nely, nelz, fixed_dofs, max_levels=8, coarse_max_dofs=200
             Ke = coarse_element_matrices(n, Ke, lev.P)
             fixed = cf
     coarse_inv = coarsest_inverse(levels[-1].A.toarray())
-    return Hierarchy(levels, coarse_inv, omega, nu_pre, nu_post)
+    return Hierarchy(levels, coarse_inv, omega, nu_pre, nu_post, cheb_degree)
 
 
 PIVOT_RTOL = 1e-5        # pivot / diagonal below this: rank deficient
@@ -234,15 +244,49 @@ def smooth(lev, x, b, omega, sweeps):
     return x
 
 
+def cheb_coefficients(degree, ratio=CHEB_RATIO):
+    """(1/theta, [(c1, c2)] for steps 1 .. degree-1) of the three-term
+    recurrence d_k = c1 d_(k-1) + c2 r_k on [1/ratio, 1]."""
+    lmax, lmin = 1.0, 1.0 / ratio
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    steps = []
+    for _ in range(degree - 1):
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        steps.append((rho_new * rho, 2.0 * rho_new / delta))
+        rho = rho_new
+    return 1.0 / theta, steps
+
+
+def cheb_smooth(lev, x, b, degree, sweeps):
+    inv_theta, steps = cheb_coefficients(degree)
+    for _ in range(sweeps):
+        r = lev.d1inv * (b - lev.A @ x)
+        d = inv_theta * r
+        x = x + d
+        for c1, c2 in steps:
+            r = r - lev.d1inv * (lev.A @ d)
+            d = c1 * d + c2 * r
+            x = x + d
+    return x
+
+
+def level_smooth(H, lev, x, b, sweeps):
+    if H.cheb_degree:
+        return cheb_smooth(lev, x, b, H.cheb_degree, sweeps)
+    return smooth(lev, x, b, H.omega, sweeps)
+
+
 def vcycle(H, b, li=0):
     lev = H.levels[li]
     if li == len(H.levels) - 1:
         return H.coarse_inv @ b
-    x = smooth(lev, np.zeros_like(b), b, H.omega, H.nu_pre)
+    x = level_smooth(H, lev, np.zeros_like(b), b, H.nu_pre)
     r = b - lev.A @ x
     xc = vcycle(H, lev.P.T @ r, li + 1)
     x = x + lev.P @ xc
-    return smooth(lev, x, b, H.omega, H.nu_post)
+    return level_smooth(H, lev, x, b, H.nu_post)
 
 
 @dataclass

@@ -189,3 +189,42 @@ def test_pivot_test_leaves_constrained_problems_alone():
     Ac = H.levels[-1].A.toarray()
     assert gmg.cholesky_pivots_ok(Ac)
     assert np.abs(H.coarse_inv - np.linalg.inv(Ac)).max() <= 1e-10 * np.abs(H.coarse_inv).max()
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 4])
+def test_chebyshev_sweep_is_the_scaled_chebyshev_polynomial(degree):
+    """On the eigenvectors of the symmetric D1^-1/2 A D1^-1/2, one sweep from
+    x multiplies the error by T_k((theta - lam)/delta) / T_k(theta/delta)
+    (closed form, T_k the Chebyshev polynomial of the first kind)."""
+    m, fd, E, KE, H = _hierarchy((4, 3, 2), coarse_max_dofs=1)
+    lev = H.levels[0]
+    A = lev.A.toarray()
+    s = np.sqrt(lev.d1inv)
+    lam, Q = np.linalg.eigh(s[:, None] * A * s[None, :])
+    u = np.random.default_rng(3).normal(size=A.shape[0])          # exact solution
+    b = A @ u
+    x0 = np.random.default_rng(4).normal(size=A.shape[0])
+    x1 = gmg.cheb_smooth(lev, x0, b, degree, 1)
+    lmin, lmax = 1.0 / gmg.CHEB_RATIO, 1.0
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    T = lambda t: np.cos(degree * np.arccos(t)) if abs(t) <= 1 else np.cosh(degree * np.arccosh(abs(t))) * (np.sign(t) ** degree)
+    gain = np.array([T((theta - l) / delta) for l in lam]) / T(theta / delta)
+    e0 = Q.T @ ((x0 - u) / s)                    # error in the symmetric basis
+    e1 = Q.T @ ((x1 - u) / s)
+    assert np.abs(e1 - gain * e0).max() <= 1e-9 * np.abs(e0).max()
+
+
+def test_chebyshev_vcycle_symmetric_and_converging():
+    m, fd, E, KE, H = _hierarchy((8, 4, 4), nu_pre=1, nu_post=1, cheb_degree=2)
+    rng = np.random.default_rng(1)
+    b1, b2 = rng.normal(size=m.n_dof), rng.normal(size=m.n_dof)
+    b1[fd] = 0.0
+    b2[fd] = 0.0
+    v1, v2 = gmg.vcycle(H, b1), gmg.vcycle(H, b2)
+    assert abs(b1 @ v2 - b2 @ v1) <= 1e-11 * abs(b1 @ v2)
+    assert b1 @ v1 > 0
+    edof = fem.edof_table_fast(8, 4, 4)
+    P = W.cantilever(8, 4, 4)
+    K = lambda v: fem.kv(KE, E, edof, v, fd)
+    u, st = gmg.pcg(H, K, P.f, np.zeros(m.n_dof), 1e-10)
+    assert st.converged and st.true_rel_residual <= 1e-9
