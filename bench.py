@@ -953,8 +953,9 @@ def gmg_run(args):
                    ("jacobi_mixed_continue_0.1", lambda: h.ir_solve(E, f, uu, inner_tol=0.1))]
         gmg_cfg = [("gmg_f64", dict(mixed=0)), ("gmg_mixed", dict(mixed=1)),
                    ("gmg_mixed_nu2", dict(mixed=1, nu_pre=2, nu_post=2)),
-                   ("gmg_mixed_continue", dict(mixed=1, continue_dir=1)),
-                   ("gmg_mixed_continue_0.1", dict(mixed=1, continue_dir=1, inner_tol=0.1))]
+                   ("gmg_mixed_restart", dict(mixed=1, continue_dir=0)),
+                   ("gmg_mixed_cheb2", dict(mixed=1, cheb_degree=2)),
+                   ("gmg_mixed_cheb3", dict(mixed=1, cheb_degree=3))]
         # the fine sweeps on tensor-core K.v forms (a BF16 smoother inside a V-cycle)
         gmg_cfg += [(f"gmg_mixed_smoother_{fm}", dict(mixed=1, smoother_form=mfto.FORMS[fm]))
                     for fm in ("tf32", "bf16", "f16", "bf16x3")]

@@ -707,6 +707,10 @@ typedef struct {
                                continues the previous one's direction,
                                p = z + (r.z / (r.z)_prev) p (1, default),
                                or starts from p = z (0)                   */
+  int32_t cheb_degree;      /* 0 (default): l1-Jacobi sweeps with omega;
+                               k = 1 .. 8: Chebyshev sweeps of degree k on
+                               [1/30, 1] of D1^-1 A (1 = the l1 bound), a
+                               sweep costing k operator applications      */
 } mfto_gmg_params;
 void mfto_default_gmg_params(mfto_gmg_params* p);
 /* Build the hierarchy for the moduli d_E (FP64 [elements]) with params p

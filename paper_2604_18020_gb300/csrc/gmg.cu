@@ -56,6 +56,8 @@ struct GmgLevel {
   float* d_dinv = nullptr;      // 1 / l1 row sums
   float* x = nullptr;           // correction (levels >= 1)
   float* x2 = nullptr;          // its other half when a fused sweep writes a copy
+  float* cr = nullptr;          // Chebyshev residual and step (Chebyshev smoother only)
+  float* cd = nullptr;
   float* b = nullptr;           // right-hand side (levels >= 1)
   float* t = nullptr;           // operator applied to x
 };
@@ -431,6 +433,54 @@ gmg_smooth(float* __restrict__ x, const float* __restrict__ b, const float* __re
   }
 }
 
+// Chebyshev sweeps (the degree-k Chebyshev iteration for D1^-1 A x = D1^-1 b
+// on [1/30, 1], 1 the l1 bound of lambda_max): r is the preconditioned
+// residual, d the step.
+//   first sweep from x = 0: r = D1^-1 b, d = r / theta, x = d;
+//   later sweeps:           r = D1^-1 (b - t), t = A x, d = r / theta, x += d;
+//   each further step:      r -= D1^-1 t, t = A d, d = c1 d + c2 r, x += d.
+__global__ void __launch_bounds__(kB)
+gmg_cheb_first(float* __restrict__ x, float* __restrict__ d, float* __restrict__ r,
+               const float* __restrict__ b, const float* __restrict__ dinv, int64_t n,
+               float inv_theta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = dinv[i] * b[i];
+    const float di = inv_theta * ri;
+    r[i] = ri;
+    d[i] = di;
+    x[i] = di;
+  }
+}
+
+__global__ void __launch_bounds__(kB)
+gmg_cheb_begin(float* __restrict__ x, float* __restrict__ d, float* __restrict__ r,
+               const float* __restrict__ b, const float* __restrict__ t,
+               const float* __restrict__ dinv, int64_t n, float inv_theta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = dinv[i] * (b[i] - t[i]);
+    const float di = inv_theta * ri;
+    r[i] = ri;
+    d[i] = di;
+    x[i] += di;
+  }
+}
+
+__global__ void __launch_bounds__(kB)
+gmg_cheb_step(float* __restrict__ x, float* __restrict__ d, float* __restrict__ r,
+              const float* __restrict__ t, const float* __restrict__ dinv, int64_t n, float c1,
+              float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = r[i] - dinv[i] * t[i];
+    const float di = c1 * d[i] + c2 * ri;
+    r[i] = ri;
+    d[i] = di;
+    x[i] += di;
+  }
+}
+
 // bc = Phat^T (b - t) (t = NULL: the residual is b); on fixed coarse DOFs
 // zero, or xid there when given (the identity rows of a coarse operator
 // applied as Phat^T A Phat).  One thread per coarse DOF.
@@ -798,7 +848,7 @@ void free_levels(GmgWs* w) {
   for (int l = 0; l < MFTO_GMG_MAX_LEVELS; ++l) {
     GmgLevel& v = w->lv[l];
     if (l > 0 && v.d_fixed) cudaFree(v.d_fixed);
-    void* ptrs[] = {v.d_K, v.d_dinv, v.x, v.x2, v.b, v.t};
+    void* ptrs[] = {v.d_K, v.d_dinv, v.x, v.x2, v.b, v.t, v.cr, v.cd};
     for (void* q : ptrs)
       if (q) cudaFree(q);
     v = GmgLevel();
@@ -1004,6 +1054,57 @@ mfto_status apply_level(mfto_handle* h, GmgWs* w, int l, const float* x, float* 
   return MFTO_OK;
 }
 
+// Chebyshev coefficients on [1/30, 1]: 1/theta and (c1, c2) per further step
+struct ChebCoef {
+  float inv_theta;
+  float c1[8], c2[8];
+};
+
+ChebCoef cheb_coef(int degree) {
+  ChebCoef c{};
+  const double lmax = 1.0, lmin = 1.0 / 30.0;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  c.inv_theta = (float)(1.0 / theta);
+  for (int k = 0; k + 1 < degree && k < 8; ++k) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    c.c1[k] = (float)(rho_new * rho);
+    c.c2[k] = (float)(2.0 * rho_new / delta);
+    rho = rho_new;
+  }
+  return c;
+}
+
+// `sweeps` Chebyshev sweeps on level l (from zero when first); on exit v.t is
+// not A x.
+mfto_status cheb_sweeps(mfto_handle* h, GmgWs* w, int l, const float* b, float* x, int sweeps,
+                        bool from_zero) {
+  const GmgLevel& v = w->lv[l];
+  const ChebCoef c = cheb_coef(w->prm.cheb_degree);
+  const int g = grid_of(v.n_dof);
+  mfto_status s;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    h->launches++;
+    if (sw == 0 && from_zero) {
+      gmg_cheb_first<<<g, kB, 0, h->stream>>>(x, v.cd, v.cr, b, v.d_dinv, v.n_dof, c.inv_theta);
+    } else {
+      if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
+      gmg_cheb_begin<<<g, kB, 0, h->stream>>>(x, v.cd, v.cr, b, v.t, v.d_dinv, v.n_dof,
+                                              c.inv_theta);
+    }
+    MFTO_LAUNCH_CHECK(h);
+    for (int k = 0; k + 1 < w->prm.cheb_degree; ++k) {
+      if ((s = apply_level(h, w, l, v.cd, v.t)) != MFTO_OK) return s;
+      h->launches++;
+      gmg_cheb_step<<<g, kB, 0, h->stream>>>(x, v.cd, v.cr, v.t, v.d_dinv, v.n_dof, c.c1[k],
+                                             c.c2[k]);
+      MFTO_LAUNCH_CHECK(h);
+    }
+  }
+  return MFTO_OK;
+}
+
 // One V-cycle from level l: b the right-hand side, x the caller's output
 // buffer on level 0; on coarse levels the result lands in lv[l].x or
 // lv[l].x2 (fused sweeps alternate between them) and *out says which.
@@ -1025,11 +1126,15 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
   const int gk = grid_of(8 * v.n_node);
   const float om = (float)p.omega;
   // coarse levels with stored matrices: sweep and operator in one launch
-  const bool fused = l > 0 && !(l == 1 && w->mf1);
+  const bool cheb = p.cheb_degree > 0;
+  const bool fused = l > 0 && !(l == 1 && w->mf1) && !cheb;
   float* other = fused ? (x == v.x ? v.x2 : v.x) : nullptr;
   // pre-smoothing; on exit v.t = A x
   if (p.nu_pre == 0) {
     MFTO_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * v.n_dof, h->stream));
+  } else if (cheb) {
+    if ((s = cheb_sweeps(h, w, l, b, x, p.nu_pre, true)) != MFTO_OK) return s;
+    if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
   } else if (fused) {
     h->launches++;
     gmg_kv_coarse<KV_FIRST><<<gk, kB, 0, h->stream>>>(v.d_K, v.d_fixed, v.nx, v.ny, v.nz, nullptr,
@@ -1064,6 +1169,11 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
   gmg_prolong<<<grid_of(v.n_node), kB, 0, h->stream>>>(xc, c.d_fixed, c.nx, c.ny, v.d_fixed,
                                                        v.nx, v.ny, v.nz, x, 1);
   MFTO_LAUNCH_CHECK(h);
+  if (cheb) {
+    if ((s = cheb_sweeps(h, w, l, b, x, p.nu_post, false)) != MFTO_OK) return s;
+    if (out) *out = x;
+    return MFTO_OK;
+  }
   for (int k = 0; k < p.nu_post; ++k) {
     if (fused) {
       h->launches++;
@@ -1090,7 +1200,8 @@ mfto_status vcycle_graph(mfto_handle* h, GmgWs* w, const float* r, float* z) {
   const bool same = w->vexec && w->vkey_r == r && w->vkey_z == z &&
                     a.max_levels == b.max_levels && a.coarse_max_dofs == b.coarse_max_dofs &&
                     a.nu_pre == b.nu_pre && a.nu_post == b.nu_post && a.omega == b.omega &&
-                    a.smoother_form == b.smoother_form && a.matfree_level1 == b.matfree_level1;
+                    a.smoother_form == b.smoother_form && a.matfree_level1 == b.matfree_level1 &&
+                    a.cheb_degree == b.cheb_degree;
   if (!same) {
     drop_graph(w);
     if (!h->cap_stream &&
@@ -1137,7 +1248,8 @@ mfto_status cg_chunk_graph(mfto_handle* h, GmgWs* w) {
   const bool same = w->cexec && w->cchunk == chunk && a.max_levels == b.max_levels &&
                     a.coarse_max_dofs == b.coarse_max_dofs && a.nu_pre == b.nu_pre &&
                     a.nu_post == b.nu_post && a.omega == b.omega &&
-                    a.smoother_form == b.smoother_form && a.matfree_level1 == b.matfree_level1;
+                    a.smoother_form == b.smoother_form && a.matfree_level1 == b.matfree_level1 &&
+                    a.cheb_degree == b.cheb_degree;
   if (!same) {
     if (w->cexec) cudaGraphExecDestroy(w->cexec);
     w->cexec = nullptr;
@@ -1208,6 +1320,8 @@ mfto_status check_params(mfto_handle* h, const mfto_gmg_params& p) {
                "mfto_gmg_setup: matfree_level1 is -1, 0 or 1");
   MFTO_REQUIRE(h, p.continue_dir == 0 || p.continue_dir == 1,
                "mfto_gmg_setup: continue_dir is 0 or 1");
+  MFTO_REQUIRE(h, p.cheb_degree >= 0 && p.cheb_degree <= 8,
+               "mfto_gmg_setup: cheb_degree in [0, 8]");
   return MFTO_OK;
 }
 
@@ -1273,6 +1387,8 @@ int64_t gmg_bytes(const mfto_handle* h) {
   }
   if (w->d_cinv) b += (int64_t)sizeof(float) * w->n_c * w->n_c;
   if (w->mf_s0) b += 2 * (int64_t)sizeof(float) * h->n_dof;
+  for (int l = 0; l < w->n_levels; ++l)
+    if (w->lv[l].cr) b += 2 * (int64_t)sizeof(float) * w->lv[l].n_dof;
   return b;
 }
 
@@ -1288,6 +1404,7 @@ extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
   p->smoother_form = MFTO_FORM_F32;
   p->matfree_level1 = 0;
   p->continue_dir = 1;
+  p->cheb_degree = 0;
 }
 
 extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
@@ -1318,6 +1435,17 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
       }
     }
     w->mf1 = want;
+  }
+  if (p.cheb_degree > 0) {                  // Chebyshev step and residual per level
+    for (int l = 0; l + 1 < w->n_levels; ++l) {
+      GmgLevel& v = w->lv[l];
+      if (v.cr) continue;
+      if (cudaMalloc((void**)&v.cr, sizeof(float) * v.n_dof) != cudaSuccess ||
+          cudaMalloc((void**)&v.cd, sizeof(float) * v.n_dof) != cudaSuccess) {
+        cudaGetLastError();
+        return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: cudaMalloc failed");
+      }
+    }
   }
   if (!w->d_E32 || !w->d_G) {
     if ((!w->d_E32 && cudaMalloc((void**)&w->d_E32, sizeof(float) * h->n_elem) != cudaSuccess) ||

@@ -71,7 +71,7 @@ class GmgParams(C.Structure):
                 ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("omega", C.c_double),
                 ("mixed", C.c_int32), ("inner_tol", C.c_double),
                 ("smoother_form", C.c_int32), ("matfree_level1", C.c_int32),
-                ("continue_dir", C.c_int32)]
+                ("continue_dir", C.c_int32), ("cheb_degree", C.c_int32)]
 
 
 GMG_MAX_LEVELS = 10

@@ -24,7 +24,7 @@ def _setup(shape, seed=3, **kw):
     h.gmg_setup(Ed, prm)
     H = gmg.build(fem.ke_exact(), E, *shape, fd, max_levels=prm.max_levels,
                   coarse_max_dofs=prm.coarse_max_dofs, omega=prm.omega, nu_pre=prm.nu_pre,
-                  nu_post=prm.nu_post)
+                  nu_post=prm.nu_post, cheb_degree=prm.cheb_degree)
     return P, m, fd, E, Ed, h, H
 
 
@@ -47,12 +47,14 @@ def test_levels_and_operators_match_oracle(cuda, shape, matfree):
             assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max(), li
 
 
-@pytest.mark.parametrize("shape,nu,matfree", [((24, 12, 12), 2, -1), ((13, 7, 5), 1, -1),
-                                              ((9, 6, 4), 0, -1), ((24, 12, 12), 1, 1),
-                                              ((13, 7, 5), 2, 1)])
-def test_vcycle_matches_oracle(cuda, shape, nu, matfree):
+@pytest.mark.parametrize("shape,nu,matfree,cheb", [((24, 12, 12), 2, -1, 0), ((13, 7, 5), 1, -1, 0),
+                                                   ((9, 6, 4), 0, -1, 0), ((24, 12, 12), 1, 1, 0),
+                                                   ((13, 7, 5), 2, 1, 0), ((24, 12, 12), 1, -1, 2),
+                                                   ((13, 7, 5), 2, 1, 3)])
+def test_vcycle_matches_oracle(cuda, shape, nu, matfree, cheb):
     import torch
-    P, m, fd, E, Ed, h, H = _setup(shape, nu_pre=nu, nu_post=nu, matfree_level1=matfree)
+    P, m, fd, E, Ed, h, H = _setup(shape, nu_pre=nu, nu_post=nu, matfree_level1=matfree,
+                                   cheb_degree=cheb)
     with h:
         r = W.vec_random(m.n_dof, seed=11)
         r[fd] = 0.0
@@ -79,8 +81,9 @@ def _simp_state(shape, n_iter=6):
     return P, cone.filter_fwd(rho, *shape, 1.5)
 
 
-@pytest.mark.parametrize("mixed,matfree,cont", [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 0, 1)])
-def test_gmg_solve_matches_oracle(cuda, mixed, matfree, cont):
+@pytest.mark.parametrize("mixed,matfree,cont,cheb", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 1, 0, 0),
+                                                    (1, 0, 1, 0), (1, 0, 1, 2), (0, 0, 0, 2)])
+def test_gmg_solve_matches_oracle(cuda, mixed, matfree, cont, cheb):
     """A SIMP state of the 24 x 12 x 12 cantilever (E from 1e-9 to 1): the
     V-cycle CG (FP64, or FP64 refinement around FP32 CGs) reaches the
     tolerance with the oracle's true residual, the oracle's compliance, and
@@ -96,10 +99,11 @@ def test_gmg_solve_matches_oracle(cuda, mixed, matfree, cont):
     E = fem.simp_modulus(rho_phys, 3.0)
     K = lambda v: fem.kv(KE, E, edof, v, fd)
     u_j, _ = solve.pcg(K, fem.jacobi_diag(KE, E, edof, fd), P.f, np.zeros(m.n_dof), 1e-10)
-    prm = mfto.default_gmg_params(mixed=mixed, matfree_level1=matfree, continue_dir=cont)
+    prm = mfto.default_gmg_params(mixed=mixed, matfree_level1=matfree, continue_dir=cont,
+                                  cheb_degree=cheb)
     H = gmg.build(KE, E, *shape, fd, max_levels=prm.max_levels,
                   coarse_max_dofs=prm.coarse_max_dofs, omega=prm.omega, nu_pre=prm.nu_pre,
-                  nu_post=prm.nu_post)
+                  nu_post=prm.nu_post, cheb_degree=prm.cheb_degree)
     _, st_o = gmg.pcg(H, K, P.f, np.zeros(m.n_dof), 1e-8)
     with mfto.Handle(*shape, P.fixed) as h:
         u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
