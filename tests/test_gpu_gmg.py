@@ -318,3 +318,30 @@ def test_gmg_solve_multi_load_cases(cuda):
         u_j, _ = solve.pcg(K, d, P.f[r], np.zeros(m.n_dof), 1e-10)
         assert np.linalg.norm(P.f[r] - K(Ug[r])) / np.linalg.norm(P.f[r]) <= 1.5e-8
         assert abs(P.f[r] @ Ug[r] - P.f[r] @ u_j) <= 1e-7 * abs(P.f[r] @ u_j)
+
+
+@pytest.mark.parametrize("shape", [(12, 6, 1), (7, 1, 3), (1, 1, 5)])
+def test_degenerate_one_element_axes(cuda, shape):
+    """Meshes one element thick along an axis: that axis keeps one coarse
+    element on every level (its coarse node 1 lies past the fine mesh); the
+    hierarchy, every level's operator and one V-cycle match the oracle.  The
+    cycle's bound is 5e-4 of max|z| here: a one-element column is badly
+    conditioned (the cycle amplifies r by ~500 on 1 x 1 x 5), and the FP32
+    coarse solves carry kappa times the unit roundoff."""
+    import torch
+    P, m, fd, E, Ed, h, H = _setup(shape, coarse_max_dofs=30)
+    with h:
+        assert h.gmg_levels() == [lev.dims for lev in H.levels]
+        rng = np.random.default_rng(5)
+        for li, lev in enumerate(H.levels):
+            x = rng.uniform(-1, 1, lev.A.shape[0])
+            y = torch.empty(len(x), dtype=torch.float32, device=cuda)
+            h.gmg_apply(li, torch.tensor(x, dtype=torch.float32, device=cuda), y)
+            ref = lev.A @ x
+            assert np.abs(y.cpu().numpy() - ref).max() <= 2e-5 * np.abs(ref).max(), li
+        r = W.vec_random(m.n_dof, seed=6)
+        r[fd] = 0.0
+        z = torch.empty(m.n_dof, dtype=torch.float32, device=cuda)
+        h.gmg_vcycle(torch.tensor(r, dtype=torch.float32, device=cuda), z)
+        ref = gmg.vcycle(H, r)
+        assert np.abs(z.cpu().numpy() - ref).max() <= 5e-4 * np.abs(ref).max()
