@@ -17,15 +17,26 @@
 //   Phat^T A Phat, Phat = M_f P M_c (the masked interpolation), so every level
 //   is the Galerkin operator plus the identity on its fixed DOFs.  A coarse
 //   DOF is fixed where the fine DOF at the same position is.
-// V-cycle: nu_pre l1-Jacobi sweeps from x = 0, residual, restriction,
-// recursion, prolongation, nu_post sweeps; the coarsest level is solved with
-// its dense inverse (Cholesky on the host in FP64, stored as FP32).  The
-// l1 row sums come from the element matrices, D1 = sum_E sum_j |(A_E)_ij|
-// (1 on fixed DOFs), so lambda_max(D1^-1 A) <= 1 and any weight in (0, 2)
-// smooths.  Coarse levels apply their operator node by node from the element
-// matrices (each node sums its rows of its <= 8 elements: no atomics).
-// Outer solver: FP64 CG with z = V(r) (FP32 inside the cycle) and the
-// Polak-Ribiere beta, FP64 K.v and fixed-order FP64 reductions.
+//   Interior coarse elements of level 1 (all 8 children, no fixed DOF) are
+//   formed as sum_c E_c G_c from the unit-modulus child matrices
+//   G_c = P_c^T KE P_c.
+// V-cycle: nu_pre sweeps from x = 0, residual, restriction, recursion,
+// prolongation, nu_post sweeps; the coarsest level is solved with its dense
+// inverse (Cholesky on the host in FP64, stored as FP32; a rank-deficient
+// operator -- a consistent singular problem -- factorised with a small
+// diagonal shift).  Sweeps are l1-Jacobi, x += omega D1^-1 (b - A x), or
+// Chebyshev of a chosen degree on [1/30, 1]; the l1 row sums come from the
+// element matrices, D1 = sum_E sum_j |(A_E)_ij| (1 on fixed DOFs), so
+// lambda_max(D1^-1 A) <= 1 bounds both.  Coarse levels apply their operator
+// node by node from the element matrices (each node sums its rows of its
+// <= 8 elements: no atomics), with a sweep fused into the same launch; level
+// 1 is applied as Phat^T K Phat through the fine FP32 K.v instead when its
+// matrices would not stay in L2.  The cycle is replayed from a CUDA graph.
+// Outer solvers (CG with z = V(r) and the Polak-Ribiere beta, because the
+// cycle runs in FP32): one FP64 CG, or FP64 refinement around FP32 CGs whose
+// scalars stay on the device and whose iterations are replayed in graph
+// chunks, each continuing the previous one's direction; fixed-order sums
+// throughout, so every result is bit-reproducible.
 #include <math.h>
 #include <string.h>
 
