@@ -212,7 +212,14 @@ def gpu_bench(args, rank, local_rank, world):
         h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
         h.set_cg_engine(args.cg_engine)
         h.set_ir_mode(IR_MODES[args.ir_mode])
-        if not args.no_autotune:
+        if args.kv_shape:
+            # a pinned launch shape: profiling runs reproduce the shape the
+            # autotuner picks in a plain run (its timings are distorted under a
+            # profiler that serialises launches)
+            nzc, kind = (int(x) for x in args.kv_shape.split(","))
+            h.set_kv_shape(nzc, kind)
+            tuned = (nzc, kind, None)
+        elif not args.no_autotune:
             tuned = h.kv_autotune()
     rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
@@ -1110,6 +1117,8 @@ def main():
                     help="inner CG at each outer step: restart (p = z) or continue the direction")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default z-chunk of the FP32 column K.v")
+    ap.add_argument("--kv-shape", default=None,
+                    help="NZC,KIND: pin the FP32 column K.v launch shape instead of autotuning")
     ap.add_argument("--cg-engine", type=int, default=0, choices=[0, 1],
                     help="FP32 inner CG: 1 persistent cooperative kernel, 0 per-iteration graph")
     ap.add_argument("--inner-form", default="f32",
