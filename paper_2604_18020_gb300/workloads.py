@@ -255,6 +255,9 @@ WORKLOADS = {
     "torsion_55x55x165": lambda: torsion(55, 55, 165, 0.2, 2.0),
     "cantilever_100x50x50_8rhs": lambda: multi_rhs_cantilever(100, 50, 50, 8, 3),
     "cantilever_256x128x150": lambda: cantilever(256, 128, 150, 0.12, 1.5),
+    "cantilever_160x80x40": lambda: cantilever(160, 80, 40, 0.3, 1.5),
+    "cantilever_200x100x50": lambda: cantilever(200, 100, 50, 0.3, 1.5),
+    "cantilever_252x126x63": lambda: cantilever(252, 126, 63, 0.3, 1.5),
     "cantilever_600x300x150": lambda: cantilever(600, 300, 150, 0.3, 1.5),
     "mbb_150x50x25": lambda: mbb(150, 50, 25),
     "bridge_150x50x25": lambda: bridge(150, 50, 25),
