@@ -258,6 +258,7 @@ WORKLOADS = {
     "cantilever_160x80x40": lambda: cantilever(160, 80, 40, 0.3, 1.5),
     "cantilever_200x100x50": lambda: cantilever(200, 100, 50, 0.3, 1.5),
     "cantilever_252x126x63": lambda: cantilever(252, 126, 63, 0.3, 1.5),
+    "cantilever_340x170x85": lambda: cantilever(340, 170, 85, 0.3, 1.5),
     "cantilever_600x300x150": lambda: cantilever(600, 300, 150, 0.3, 1.5),
     "mbb_150x50x25": lambda: mbb(150, 50, 25),
     "bridge_150x50x25": lambda: bridge(150, 50, 25),
