@@ -89,8 +89,10 @@ def test_batch_solve_and_autotune(cuda, mode, inner_tol):
         assert abs(fs[i] @ ui - fs[i] @ u_ref) / abs(fs[i] @ u_ref) <= 1e-7
 
 
-def test_batch_64_uneven_instances(cuda):
-    """The configuration of 64 seeded instances from 16x8x8 to 48x24x24."""
+@pytest.mark.parametrize("mode,inner_tol", [(0, 1e-2), (1, 1e-1)])
+def test_batch_64_uneven_instances(cuda, mode, inner_tol):
+    """The configuration of 64 seeded instances from 16x8x8 to 48x24x24, with
+    restarted and continued refinement."""
     import torch
     from paper_2604_18020_gb300 import mfto
     problems = W.uneven_instances(count=64, seed=5)
@@ -98,9 +100,10 @@ def test_batch_64_uneven_instances(cuda):
     with mfto.Batch([(P.mesh.nelx, P.mesh.nely, P.mesh.nelz) for P in problems],
                     [P.fixed for P in problems]) as b:
         b.autotune(reps=2)
+        b.set_ir_mode(mode)
         U = torch.zeros(b.n_dof, dtype=torch.float64, device=cuda)
         sts = b.solve(torch.tensor(np.concatenate(Es), device=cuda),
-                      torch.tensor(np.concatenate(fs), device=cuda), U)
+                      torch.tensor(np.concatenate(fs), device=cuda), U, inner_tol=inner_tol)
         got = U.cpu().numpy()
         offs = b.dof_off
     assert all(s.status == mfto.OK and s.rel_residual <= 1e-8 for s in sts)

@@ -57,3 +57,20 @@ def test_ebe_rejects_out_of_range_index(cuda):
             e.kv(1, torch.tensor(edof, device=dev),
                  torch.ones(m.n_elem, dtype=torch.float64, device=dev),
                  torch.ones(m.n_dof, dtype=torch.float64, device=dev), y)
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_ebe_kv_full_size(cuda, variant):
+    """The microbenchmark's largest configuration (200x100x50 element and
+    node counts, 1,000,000 elements, random table seed 42), in the launch
+    configuration the benchmark times: the whole output against the oracle."""
+    m = W.Mesh(200, 100, 50)
+    edof = W.edof_random(m, 42)
+    E = W.rho_random(m, seed=1)
+    v = W.vec_random(m.n_dof, seed=2)
+    if variant == 2:
+        E = E.astype(np.float32).astype(np.float64)
+        v = v.astype(np.float32).astype(np.float64)
+    ref = fem.kv_unmasked(fem.ke_exact(), E, edof.astype(np.int64), v)
+    got = _run(variant, edof, E, v, m.n_dof)
+    assert np.abs(got - ref).max() <= TOL[variant] * np.abs(ref).max()
