@@ -603,6 +603,9 @@ mfto_status learned_run(mfto_handle* h, const double* E, const double* rho_phys,
 bool learned_active(const mfto_handle* h);
 void learned_release(mfto_handle* h);
 bool gmg_active(const mfto_handle* h);
+mfto_status gmg_sweep_col_launch(mfto_handle* h, bool first, const float* E, const float* b,
+                                 const float* dinv, float omega, const float* x, float* xo,
+                                 float* t);
 int64_t gmg_bytes(const mfto_handle* h);
 int64_t learned_bytes(const mfto_handle* h);
 void gmg_release(mfto_handle* h);

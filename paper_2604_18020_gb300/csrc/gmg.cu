@@ -1116,11 +1116,65 @@ mfto_status cheb_sweeps(mfto_handle* h, GmgWs* w, int l, const float* b, float* 
   return MFTO_OK;
 }
 
+mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
+                   float** out = nullptr);
+
+// Level 0 with its l1-Jacobi sweeps fused into the FP32 column K.v: the
+// pre-smoothed iterate lives in the level's two scratch buffers, the last
+// post-sweep writes the caller's x.
+mfto_status vcycle_level0_fused(mfto_handle* h, GmgWs* w, const float* b, float* x) {
+  const GmgLevel& v = w->lv[0];
+  const GmgLevel& c = w->lv[1];
+  const mfto_gmg_params& p = w->prm;
+  const float om = (float)p.omega;
+  float* cur = v.x;
+  auto other = [&](const float* q) { return q == v.x ? v.x2 : v.x; };
+  mfto_status s;
+  if (p.nu_pre == 0) {
+    MFTO_CUDA(h, cudaMemsetAsync(cur, 0, sizeof(float) * v.n_dof, h->stream));
+  } else {
+    if ((s = gmg_sweep_col_launch(h, true, w->d_E32, b, v.d_dinv, om, nullptr, cur, v.t)) !=
+        MFTO_OK)
+      return s;
+    for (int k = 1; k < p.nu_pre; ++k) {
+      float* dst = other(cur);
+      if ((s = gmg_sweep_col_launch(h, false, w->d_E32, b, v.d_dinv, om, cur, dst, nullptr)) !=
+          MFTO_OK)
+        return s;
+      cur = dst;
+    }
+    if (p.nu_pre > 1 && (s = apply_level(h, w, 0, cur, v.t)) != MFTO_OK) return s;
+  }
+  h->launches++;
+  gmg_restrict<<<grid_of(c.n_dof), kB, 0, h->stream>>>(
+      b, p.nu_pre ? v.t : nullptr, v.d_fixed, v.nx, v.ny, v.nz, c.d_fixed, c.nx, c.ny, c.nz, c.b,
+      nullptr);
+  MFTO_LAUNCH_CHECK(h);
+  float* xc = nullptr;
+  if ((s = vcycle(h, w, 1, c.b, c.x, &xc)) != MFTO_OK) return s;
+  h->launches++;
+  gmg_prolong<<<grid_of(v.n_node), kB, 0, h->stream>>>(xc, c.d_fixed, c.nx, c.ny, v.d_fixed,
+                                                       v.nx, v.ny, v.nz, cur, 1);
+  MFTO_LAUNCH_CHECK(h);
+  if (p.nu_post == 0) {
+    MFTO_CUDA(h, cudaMemcpyAsync(x, cur, sizeof(float) * v.n_dof, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+    return MFTO_OK;
+  }
+  for (int k = 0; k < p.nu_post; ++k) {
+    float* dst = k + 1 == p.nu_post ? x : other(cur);
+    if ((s = gmg_sweep_col_launch(h, false, w->d_E32, b, v.d_dinv, om, cur, dst, nullptr)) !=
+        MFTO_OK)
+      return s;
+    cur = dst;
+  }
+  return MFTO_OK;
+}
+
 // One V-cycle from level l: b the right-hand side, x the caller's output
 // buffer on level 0; on coarse levels the result lands in lv[l].x or
 // lv[l].x2 (fused sweeps alternate between them) and *out says which.
-mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
-                   float** out = nullptr) {
+mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x, float** out) {
   const int L = w->n_levels - 1;
   const GmgLevel& v = w->lv[l];
   const mfto_gmg_params& p = w->prm;
@@ -1139,6 +1193,8 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
   // coarse levels with stored matrices: sweep and operator in one launch
   const bool cheb = p.cheb_degree > 0;
   const bool fused = l > 0 && !(l == 1 && w->mf1) && !cheb;
+  if (l == 0 && v.x && v.x2 && !cheb && p.smoother_form == MFTO_FORM_F32 && h->kv_variant == 0)
+    return vcycle_level0_fused(h, w, b, x);
   float* other = fused ? (x == v.x ? v.x2 : v.x) : nullptr;
   // pre-smoothing; on exit v.t = A x
   if (p.nu_pre == 0) {
@@ -1393,6 +1449,7 @@ int64_t gmg_bytes(const mfto_handle* h) {
   for (int l = 0; l < w->n_levels; ++l) {
     const GmgLevel& v = w->lv[l];
     b += 2 * (int64_t)sizeof(float) * v.n_dof;                  // dinv, t
+    if (l == 0 && v.x) b += 2 * (int64_t)sizeof(float) * v.n_dof;   // fused-sweep scratch
     if (l > 0)
       b += v.n_node + (int64_t)sizeof(float) * (576 * v.n_elem + 3 * v.n_dof);  // mask, K, x, x2, b
   }
@@ -1446,6 +1503,15 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
       }
     }
     w->mf1 = want;
+  }
+  if (p.cheb_degree == 0 && p.smoother_form == MFTO_FORM_F32 && w->n_levels >= 2 &&
+      !w->lv[0].x) {                        // level-0 scratch of the fused sweeps
+    GmgLevel& v = w->lv[0];
+    if (cudaMalloc((void**)&v.x, sizeof(float) * v.n_dof) != cudaSuccess ||
+        cudaMalloc((void**)&v.x2, sizeof(float) * v.n_dof) != cudaSuccess) {
+      cudaGetLastError();
+      return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: cudaMalloc failed");
+    }
   }
   if (p.cheb_degree > 0) {                  // Chebyshev step and residual per level
     for (int l = 0; l + 1 < w->n_levels; ++l) {

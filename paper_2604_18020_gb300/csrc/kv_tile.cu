@@ -73,6 +73,62 @@ kv_col_kernel(const float* __restrict__ E, const float* __restrict__ v, float* _
                  reinterpret_cast<float*>(smem_raw));
 }
 
+// Multigrid l1-Jacobi sweeps on the level-0 operator (gmg.cu), fused into the
+// column K.v: the first sweep from zero loads omega D1^-1 b as its vector and
+// writes x and A x; a later sweep loads x and writes x + omega D1^-1 (b - A x)
+// to another buffer.  The masked loads give 0 on fixed DOFs, where A is the
+// identity and b is 0, so both stay 0 there.
+struct ColLoadScaled {
+  const float* b;
+  const float* dinv;
+  float omega;
+  __device__ __forceinline__ float operator()(int idx) const { return omega * dinv[idx] * b[idx]; }
+};
+
+struct ColSweepFirst {
+  float* x;
+  float* t;
+  __device__ __forceinline__ void operator()(int node, const float (&acc)[3], const float (&pn)[3],
+                                             uint8_t fm, DFloat& red) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x[3 * node + c] = pn[c];
+      t[3 * node + c] = ((fm >> c) & 1) ? pn[c] : acc[c];
+    }
+  }
+};
+
+struct ColSweep {
+  const float* b;
+  const float* dinv;
+  float omega;
+  float* xo;
+  __device__ __forceinline__ void operator()(int node, const float (&acc)[3], const float (&pn)[3],
+                                             uint8_t fm, DFloat& red) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int d = 3 * node + c;
+      const float y = ((fm >> c) & 1) ? pn[c] : acc[c];
+      xo[d] = pn[c] + omega * dinv[d] * (b[d] - y);
+    }
+  }
+};
+
+template <int MINB, int FIRST>
+__global__ void __launch_bounds__(MFTO_BLOCK, MINB)
+gmg_sweep_col_kernel(const float* __restrict__ E, const float* __restrict__ b,
+                     const float* __restrict__ dinv, float omega, const float* __restrict__ x,
+                     float* __restrict__ xo, float* __restrict__ t,
+                     const uint8_t* __restrict__ fixed, ModeCoef<float> K, Grid g, ColTiling tl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (FIRST)
+    kv_column_body(E, fixed, K, g, tl, ColLoadScaled{b, dinv, omega}, ColSweepFirst{xo, t},
+                   reinterpret_cast<float*>(smem_raw));
+  else
+    kv_column_body(E, fixed, K, g, tl, ColLoadPlain{x}, ColSweep{b, dinv, omega, xo},
+                   reinterpret_cast<float*>(smem_raw));
+}
+
 template <int MINB>
 __global__ void __launch_bounds__(MFTO_BLOCK, MINB)
 pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
@@ -167,6 +223,14 @@ mfto_status kv_tile_init(mfto_handle* h) {
   const int csm = (int)ColShape::smem_bytes;
   MFTO_CUDA(h, cudaFuncSetAttribute(kv_col_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(kv_col_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_sweep_col_kernel<2, 0>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_sweep_col_kernel<2, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_sweep_col_kernel<3, 0>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_sweep_col_kernel<3, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel<2>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel<3>,
@@ -193,6 +257,38 @@ template <>
 const ModeCoef<double>& coef<double>(const mfto_handle* h) { return h->mc64; }
 template <>
 const ModeCoef<float>& coef<float>(const mfto_handle* h) { return h->mc32; }
+
+// One l1-Jacobi sweep on the FP32 operator fused with it (first: from x = 0,
+// writing x and A x; otherwise x -> xo).  Needs the column kernel (variant 0).
+mfto_status gmg_sweep_col_launch(mfto_handle* h, bool first, const float* E, const float* b,
+                                 const float* dinv, float omega, const float* x, float* xo,
+                                 float* t) {
+  if (h->kv_variant != 0)
+    return mfto_fail(h, MFTO_UNSUPPORTED, "fused sweeps need the column K.v");
+  int grid = 0;
+  const int kind = h->col_kind;
+  const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
+  const Grid g = make_grid(h->mesh);
+  const size_t sm = ColShape::smem_bytes;
+  h->launches++;
+  if (kind == 1) {
+    if (first)
+      gmg_sweep_col_kernel<3, 1><<<grid, MFTO_BLOCK, sm, h->stream>>>(
+          E, b, dinv, omega, x, xo, t, h->d_fixed, h->mc32, g, tl);
+    else
+      gmg_sweep_col_kernel<3, 0><<<grid, MFTO_BLOCK, sm, h->stream>>>(
+          E, b, dinv, omega, x, xo, t, h->d_fixed, h->mc32, g, tl);
+  } else {
+    if (first)
+      gmg_sweep_col_kernel<2, 1><<<grid, MFTO_BLOCK, sm, h->stream>>>(
+          E, b, dinv, omega, x, xo, t, h->d_fixed, h->mc32, g, tl);
+    else
+      gmg_sweep_col_kernel<2, 0><<<grid, MFTO_BLOCK, sm, h->stream>>>(
+          E, b, dinv, omega, x, xo, t, h->d_fixed, h->mc32, g, tl);
+  }
+  MFTO_LAUNCH_CHECK(h);
+  return MFTO_OK;
+}
 
 template <typename T>
 mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStream_t st) {

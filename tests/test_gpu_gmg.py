@@ -230,6 +230,8 @@ def test_device_bytes_accounts_for_the_hierarchy(cuda):
         for l, (nx, ny, nz) in enumerate(dims):
             n_node = (nx + 1) * (ny + 1) * (nz + 1)
             exp += 2 * 4 * 3 * n_node
+            if l == 0:
+                exp += 2 * 4 * 3 * n_node                         # fused-sweep scratch
             if l > 0:
                 exp += n_node + 4 * (576 * nx * ny * nz + 3 * 3 * n_node)
         nx, ny, nz = dims[-1]
