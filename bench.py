@@ -750,8 +750,9 @@ def protocol_run(args):
                 h.set_solver(mfto.FORM_F32, args.inner_tol)
                 h.set_ir_mode(IR_MODES[args.ir_mode])
                 tuned = h.kv_autotune()
-            if solver == "gmg":                        # V-cycle CG, default parameters
-                h.set_gmg_solver(True)
+            if solver == "gmg":                        # V-cycle CG (default parameters,
+                h.set_gmg_solver(                      # Chebyshev sweeps if asked)
+                    True, mfto.default_gmg_params(cheb_degree=args.gmg_cheb))
             rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
             u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
             f = torch.tensor(P.f, device=dev)
@@ -764,7 +765,9 @@ def protocol_run(args):
             dt = time.perf_counter() - t
             print(json.dumps({
                 "case": f"cantilever_point_{m.nelx}x{m.nely}x{m.nelz}", "elements": m.n_elem,
-                "solver": solver, "iterations": st.iterations, "seconds": dt,
+                "solver": solver + (f"_cheb{args.gmg_cheb}" if solver == "gmg" and args.gmg_cheb
+                                    else ""),
+                "iterations": st.iterations, "seconds": dt,
                 "ms_per_iteration": 1e3 * dt / st.iterations,
                 "solver_iterations": st.cg_iterations, "restarts": st.restarts,
                 "selected_iteration": st.selected_iteration,
@@ -1106,6 +1109,8 @@ def main():
                     help="--mode gmg: run this case only")
     ap.add_argument("--gmg-simp-iters", type=int, default=None,
                     help="--mode gmg: SIMP iterations before the solves (default per case)")
+    ap.add_argument("--gmg-cheb", type=int, default=0,
+                    help="--mode protocol: Chebyshev degree of the multigrid sweeps (0: l1-Jacobi)")
     ap.add_argument("--gmg-only", action="store_true",
                     help="--mode gmg: the default multigrid solve and V-cycle only")
     ap.add_argument("--workload", default=WORKLOAD)
