@@ -74,3 +74,14 @@ def test_ebe_kv_full_size(cuda, variant):
     ref = fem.kv_unmasked(fem.ke_exact(), E, edof.astype(np.int64), v)
     got = _run(variant, edof, E, v, m.n_dof)
     assert np.abs(got - ref).max() <= TOL[variant] * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_ebe_single_element(cuda, variant):
+    m = W.Mesh(1, 1, 1)
+    edof = fem.edof_table_fast(1, 1, 1).astype(np.int32)
+    E = np.array([0.3])
+    v = W.vec_random(m.n_dof, seed=8)
+    ref = fem.kv_unmasked(fem.ke_exact(), E, edof.astype(np.int64), v)
+    got = _run(variant, edof, E, v, m.n_dof)
+    assert np.abs(got - ref).max() <= TOL[variant] * np.abs(ref).max()

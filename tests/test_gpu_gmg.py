@@ -375,3 +375,24 @@ def test_gmg_solve_at_4_9M_elements(cuda):
     assert np.linalg.norm(r) / np.linalg.norm(P.f) <= 1.5e-8
     c_elem = float(np.sum(E * osimp.element_energy(KE, edof, ug)))
     assert abs(c_elem - P.f @ ug) <= 1e-7 * abs(P.f @ ug)
+
+
+def test_single_element_mesh(cuda):
+    """1 x 1 x 1: a single level solved by its dense inverse, both precisions."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(1, 1, 1)
+    m = P.mesh
+    fd = fem.dof_mask(P.fixed)
+    E = np.array([0.7])
+    KE = fem.ke_exact()
+    edof = fem.edof_table_fast(1, 1, 1)
+    u_ref = solve.dense_solve(fem.assemble_masked(KE, E, edof, m.n_dof, fd), P.f)
+    with mfto.Handle(1, 1, 1, P.fixed) as h:
+        for mixed in (0, 1):
+            u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+            h.set_gmg_solver(False, mfto.default_gmg_params(mixed=mixed))
+            st = h.gmg_solve(torch.tensor(E, device=cuda), torch.tensor(P.f, device=cuda), u)
+            assert h.gmg_levels() == [(1, 1, 1)]
+            assert st.status == 0
+            assert np.abs(u.cpu().numpy() - u_ref).max() <= 1e-6 * np.abs(u_ref).max()
