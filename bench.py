@@ -765,8 +765,8 @@ def protocol_run(args):
             dt = time.perf_counter() - t
             print(json.dumps({
                 "case": f"cantilever_point_{m.nelx}x{m.nely}x{m.nelz}", "elements": m.n_elem,
-                "solver": solver + (f"_cheb{args.gmg_cheb}" if solver == "gmg" and args.gmg_cheb
-                                    else ""),
+                "solver": solver + (f"_cheb{args.gmg_cheb}" if solver == "gmg" and
+                                    args.gmg_cheb >= 0 else ""),
                 "iterations": st.iterations, "seconds": dt,
                 "ms_per_iteration": 1e3 * dt / st.iterations,
                 "solver_iterations": st.cg_iterations, "restarts": st.restarts,
@@ -962,8 +962,9 @@ def gmg_run(args):
         solvers = [("jacobi_f64", lambda: h.pcg(E, f, uu)),
                    ("jacobi_mixed_continue_0.1", lambda: h.ir_solve(E, f, uu, inner_tol=0.1))]
         gmg_cfg = [("gmg_f64", dict(mixed=0)), ("gmg_mixed", dict(mixed=1)),
-                   ("gmg_mixed_nu2", dict(mixed=1, nu_pre=2, nu_post=2)),
-                   ("gmg_mixed_restart", dict(mixed=1, continue_dir=0)),
+                   ("gmg_mixed_l1", dict(mixed=1, cheb_degree=0)),
+                   ("gmg_mixed_nu2", dict(mixed=1, nu_pre=2, nu_post=2, cheb_degree=0)),
+                   ("gmg_mixed_restart", dict(mixed=1, continue_dir=0, cheb_degree=0)),
                    ("gmg_mixed_cheb2", dict(mixed=1, cheb_degree=2)),
                    ("gmg_mixed_cheb3", dict(mixed=1, cheb_degree=3))]
         # the fine sweeps on tensor-core K.v forms (a BF16 smoother inside a V-cycle)
@@ -1109,8 +1110,9 @@ def main():
                     help="--mode gmg: run this case only")
     ap.add_argument("--gmg-simp-iters", type=int, default=None,
                     help="--mode gmg: SIMP iterations before the solves (default per case)")
-    ap.add_argument("--gmg-cheb", type=int, default=0,
-                    help="--mode protocol: Chebyshev degree of the multigrid sweeps (0: l1-Jacobi)")
+    ap.add_argument("--gmg-cheb", type=int, default=-1,
+                    help="--mode protocol: Chebyshev degree of the multigrid sweeps (0: l1-Jacobi, "
+                         "-1: the library's automatic choice)")
     ap.add_argument("--gmg-only", action="store_true",
                     help="--mode gmg: the default multigrid solve and V-cycle only")
     ap.add_argument("--workload", default=WORKLOAD)

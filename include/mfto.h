@@ -707,10 +707,11 @@ typedef struct {
                                continues the previous one's direction,
                                p = z + (r.z / (r.z)_prev) p (1, default),
                                or starts from p = z (0)                   */
-  int32_t cheb_degree;      /* 0 (default): l1-Jacobi sweeps with omega;
-                               k = 1 .. 8: Chebyshev sweeps of degree k on
-                               [1/30, 1] of D1^-1 A (1 = the l1 bound), a
-                               sweep costing k operator applications      */
+  int32_t cheb_degree;      /* 0: l1-Jacobi sweeps with omega; k = 1 .. 8:
+                               Chebyshev sweeps of degree k on [1/30, 1]
+                               of D1^-1 A (1 = the l1 bound), a sweep
+                               costing k operator applications; -1
+                               (default): 2 up to 4,000,000 DOFs, else 0  */
 } mfto_gmg_params;
 void mfto_default_gmg_params(mfto_gmg_params* p);
 /* Build the hierarchy for the moduli d_E (FP64 [elements]) with params p
@@ -719,6 +720,9 @@ void mfto_default_gmg_params(mfto_gmg_params* p);
  * when the coarsest level would exceed MFTO_GMG_MAX_COARSE DOFs,
  * MFTO_BREAKDOWN when it is not positive definite. */
 mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E, const mfto_gmg_params* p);
+/* The parameters of the last setup with its automatic choices resolved
+ * (cheb_degree >= 0; matfree_level1 1 or -1 as applied). */
+mfto_status mfto_gmg_params_in_use(mfto_handle* h, mfto_gmg_params* p);
 /* Levels of the last setup: *n_levels and dims[3 * l + axis] elements. */
 mfto_status mfto_gmg_levels(mfto_handle* h, int32_t* n_levels, int32_t* dims);
 /* d_y = A_level d_x (FP32 [DOFs of that level]); level 0 is the FP32 K.v. */

@@ -79,6 +79,7 @@ struct GmgWs {
   mfto_gmg_params prm{};
   float* d_E32 = nullptr;
   float* d_G = nullptr;             // [8][576] unit-modulus child Galerkin matrices
+  int cheb = 0;                     // Chebyshev degree in use (cheb_degree resolved)
   bool mf1 = false;                 // level 1 applied as Phat^T K Phat (no matrices read)
   float* mf_s0 = nullptr;           // its two fine-level scratch vectors
   float* mf_s1 = nullptr;
@@ -1092,7 +1093,7 @@ ChebCoef cheb_coef(int degree) {
 mfto_status cheb_sweeps(mfto_handle* h, GmgWs* w, int l, const float* b, float* x, int sweeps,
                         bool from_zero) {
   const GmgLevel& v = w->lv[l];
-  const ChebCoef c = cheb_coef(w->prm.cheb_degree);
+  const ChebCoef c = cheb_coef(w->cheb);
   const int g = grid_of(v.n_dof);
   mfto_status s;
   for (int sw = 0; sw < sweeps; ++sw) {
@@ -1105,7 +1106,7 @@ mfto_status cheb_sweeps(mfto_handle* h, GmgWs* w, int l, const float* b, float* 
                                               c.inv_theta);
     }
     MFTO_LAUNCH_CHECK(h);
-    for (int k = 0; k + 1 < w->prm.cheb_degree; ++k) {
+    for (int k = 0; k + 1 < w->cheb; ++k) {
       if ((s = apply_level(h, w, l, v.cd, v.t)) != MFTO_OK) return s;
       h->launches++;
       gmg_cheb_step<<<g, kB, 0, h->stream>>>(x, v.cd, v.cr, v.t, v.d_dinv, v.n_dof, c.c1[k],
@@ -1191,7 +1192,7 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x, fl
   const int gk = grid_of(8 * v.n_node);
   const float om = (float)p.omega;
   // coarse levels with stored matrices: sweep and operator in one launch
-  const bool cheb = p.cheb_degree > 0;
+  const bool cheb = w->cheb > 0;
   const bool fused = l > 0 && !(l == 1 && w->mf1) && !cheb;
   if (l == 0 && v.x && v.x2 && !cheb && p.smoother_form == MFTO_FORM_F32 && h->kv_variant == 0)
     return vcycle_level0_fused(h, w, b, x);
@@ -1387,8 +1388,8 @@ mfto_status check_params(mfto_handle* h, const mfto_gmg_params& p) {
                "mfto_gmg_setup: matfree_level1 is -1, 0 or 1");
   MFTO_REQUIRE(h, p.continue_dir == 0 || p.continue_dir == 1,
                "mfto_gmg_setup: continue_dir is 0 or 1");
-  MFTO_REQUIRE(h, p.cheb_degree >= 0 && p.cheb_degree <= 8,
-               "mfto_gmg_setup: cheb_degree in [0, 8]");
+  MFTO_REQUIRE(h, p.cheb_degree >= -1 && p.cheb_degree <= 8,
+               "mfto_gmg_setup: cheb_degree in [-1, 8]");
   return MFTO_OK;
 }
 
@@ -1472,7 +1473,7 @@ extern "C" void mfto_default_gmg_params(mfto_gmg_params* p) {
   p->smoother_form = MFTO_FORM_F32;
   p->matfree_level1 = 0;
   p->continue_dir = 1;
-  p->cheb_degree = 0;
+  p->cheb_degree = -1;
 }
 
 extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
@@ -1504,7 +1505,10 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
     }
     w->mf1 = want;
   }
-  if (p.cheb_degree == 0 && p.smoother_form == MFTO_FORM_F32 && w->n_levels >= 2 &&
+  // Chebyshev sweeps: as asked, or (cheb_degree = -1) degree 2 up to 4M DOFs,
+  // where they were measured faster, l1-Jacobi above
+  w->cheb = p.cheb_degree >= 0 ? p.cheb_degree : (h->n_dof <= 4000000 ? 2 : 0);
+  if (w->cheb == 0 && p.smoother_form == MFTO_FORM_F32 && w->n_levels >= 2 &&
       !w->lv[0].x) {                        // level-0 scratch of the fused sweeps
     GmgLevel& v = w->lv[0];
     if (cudaMalloc((void**)&v.x, sizeof(float) * v.n_dof) != cudaSuccess ||
@@ -1513,7 +1517,7 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
       return mfto_fail(h, MFTO_OOM, "mfto_gmg_setup: cudaMalloc failed");
     }
   }
-  if (p.cheb_degree > 0) {                  // Chebyshev step and residual per level
+  if (w->cheb > 0) {                        // Chebyshev step and residual per level
     for (int l = 0; l + 1 < w->n_levels; ++l) {
       GmgLevel& v = w->lv[l];
       if (v.cr) continue;
@@ -1564,6 +1568,16 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
   }
   if ((s = coarse_inverse(h, w)) != MFTO_OK) return s;
   w->ready = true;
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_gmg_params_in_use(mfto_handle* h, mfto_gmg_params* p) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, p, "mfto_gmg_params_in_use: null pointer");
+  MFTO_REQUIRE(h, h->gmg && h->gmg->ready, "mfto_gmg_params_in_use: call mfto_gmg_setup first");
+  *p = h->gmg->prm;
+  p->cheb_degree = h->gmg->cheb;
+  p->matfree_level1 = h->gmg->mf1 ? 1 : -1;
   return MFTO_OK;
 }
 

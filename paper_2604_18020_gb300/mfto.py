@@ -133,6 +133,7 @@ SIGNATURES = {
     "mfto_default_kappa_params": (None, [C.POINTER(KappaParams)]),
     "mfto_default_gmg_params": (None, [C.POINTER(GmgParams)]),
     "mfto_device_bytes": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
+    "mfto_gmg_params_in_use": (C.c_int32, [_P, C.POINTER(GmgParams)]),
     "mfto_gmg_solve_multi": (C.c_int32, [_P, _P, _P, _P, C.c_int32, _P]),
     "mfto_gmg_setup": (C.c_int32, [_P, _P, C.POINTER(GmgParams)]),
     "mfto_gmg_levels": (C.c_int32, [_P, C.POINTER(C.c_int32), _P]),
@@ -471,6 +472,13 @@ class Handle:
         _check("mfto_gmg_setup", lib().mfto_gmg_setup(
             self._h, _ptr(E, torch.float64, self.n_elem, "E"),
             C.byref(params) if params is not None else None), self._h)
+
+    def gmg_params_in_use(self) -> GmgParams:
+        """The last setup's parameters with its automatic choices resolved."""
+        p = GmgParams()
+        _check("mfto_gmg_params_in_use", lib().mfto_gmg_params_in_use(self._h, C.byref(p)),
+               self._h)
+        return p
 
     def gmg_levels(self):
         n = C.c_int32()

@@ -19,9 +19,9 @@ def _setup(shape, seed=3, **kw):
     fd = fem.dof_mask(P.fixed)
     E = fem.simp_modulus(W.rho_random(m, seed=seed, lo=0.1, hi=1.0), 3.0)
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed)
-    prm = mfto.default_gmg_params(**kw)
     Ed = torch.tensor(E, device="cuda:0")
-    h.gmg_setup(Ed, prm)
+    h.gmg_setup(Ed, mfto.default_gmg_params(**kw))
+    prm = h.gmg_params_in_use()                   # automatic choices resolved
     H = gmg.build(fem.ke_exact(), E, *shape, fd, max_levels=prm.max_levels,
                   coarse_max_dofs=prm.coarse_max_dofs, omega=prm.omega, nu_pre=prm.nu_pre,
                   nu_post=prm.nu_post, cheb_degree=prm.cheb_degree)
@@ -226,11 +226,14 @@ def test_device_bytes_accounts_for_the_hierarchy(cuda):
         assert b0 >= m.n_dof * (6 * 8 + 7 * 4) + m.n_elem * (6 * 8 + 4)
         h.gmg_setup(torch.ones(m.n_elem, dtype=torch.float64, device=cuda))
         dims = h.gmg_levels()
+        cheb = h.gmg_params_in_use().cheb_degree
         exp = 8 * 576 * 4 + m.n_elem * 4                        # G table, FP32 moduli
         for l, (nx, ny, nz) in enumerate(dims):
             n_node = (nx + 1) * (ny + 1) * (nz + 1)
             exp += 2 * 4 * 3 * n_node
-            if l == 0:
+            if cheb > 0 and l + 1 < len(dims):
+                exp += 2 * 4 * 3 * n_node                         # Chebyshev step, residual
+            if cheb == 0 and l == 0:
                 exp += 2 * 4 * 3 * n_node                         # fused-sweep scratch
             if l > 0:
                 exp += n_node + 4 * (576 * nx * ny * nz + 3 * 3 * n_node)
@@ -396,3 +399,19 @@ def test_single_element_mesh(cuda):
             assert h.gmg_levels() == [(1, 1, 1)]
             assert st.status == 0
             assert np.abs(u.cpu().numpy() - u_ref).max() <= 1e-6 * np.abs(u_ref).max()
+
+
+def test_automatic_chebyshev_choice(cuda):
+    """cheb_degree = -1 resolves to degree 2 up to 4M DOFs and to l1-Jacobi
+    sweeps above; an explicit degree is kept."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    for shape, expect in (((24, 12, 12), 2), ((200, 100, 50), 2), ((252, 126, 63), 0)):
+        P = W.cantilever(*shape)
+        m = P.mesh
+        with mfto.Handle(*shape, P.fixed) as h:
+            E = torch.ones(m.n_elem, dtype=torch.float64, device=cuda)
+            h.gmg_setup(E)
+            assert h.gmg_params_in_use().cheb_degree == expect, shape
+            h.gmg_setup(E, mfto.default_gmg_params(cheb_degree=3))
+            assert h.gmg_params_in_use().cheb_degree == 3
