@@ -1,6 +1,6 @@
 """The paper's hard-problem presets on the GPU (small versions): the FP64
 PCG and the mixed solve reach the FP64 tolerance on the singular but
-consistent MBB system and on the bridge, judged by the oracle's residual; the
+consistent MBB system and on the bridge, measured by the oracle's residual; the
 bridge solution equals the oracle's dense solve."""
 import numpy as np
 import pytest
