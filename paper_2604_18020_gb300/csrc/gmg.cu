@@ -351,11 +351,62 @@ gmg_l1_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, in
   }
 }
 
-// Coarse-level operator, 8 lanes per node: lane s takes the node's three
-// rows of adjacent element s (corner offsets the bits of s), and the 8 lanes
-// are summed in a fixed order; identity rows on fixed DOFs (their columns are
-// zero in the element matrices).  Three forms, so that a smoothing sweep and
-// its operator application are one launch:
+// The coarse-level operator's rows of node nd, 8 lanes per node: lane `sub`
+// takes the node's three rows of adjacent element sub (corner offsets the bits
+// of sub) against that element's 24 input values val(DOF), and the 8 lanes'
+// sums are added in a fixed order, so every lane ends with the node's three
+// sums (zero for nd >= n_node).  Fixed DOFs are not special here: their
+// columns are zero in the element matrices.  Every lane of the warp must call
+// it (the shuffles need all 32).
+template <class Val>
+__device__ __forceinline__ void coarse_rows(const float* __restrict__ K, int nx, int ny, int nz,
+                                            int64_t nd, int64_t n_node, int sub, Val val,
+                                            float acc[3]) {
+  const int dx = sub & 1, dy = (sub >> 1) & 1, dz = sub >> 2;
+  acc[0] = acc[1] = acc[2] = 0.0f;
+  if (nd < n_node) {
+    const int i = (int)(nd % (nx + 1));
+    const int j = (int)((nd / (nx + 1)) % (ny + 1));
+    const int k = (int)(nd / ((int64_t)(nx + 1) * (ny + 1)));
+    const int ex = i - dx, ey = j - dy, ez = k - dz;
+    if (ex >= 0 && ey >= 0 && ez >= 0 && ex < nx && ey < ny && ez < nz) {
+      const int l = dx + 2 * dy + 4 * dz;
+      const float* Ke = K + (ex + (int64_t)nx * (ey + (int64_t)ny * ez)) * 576;
+      float xe[24];
+#pragma unroll
+      for (int lb = 0; lb < 8; ++lb) {
+        const int64_t m = nid(ex + (lb & 1), ey + ((lb >> 1) & 1), ez + (lb >> 2), nx, ny);
+        xe[3 * lb] = val(3 * m);
+        xe[3 * lb + 1] = val(3 * m + 1);
+        xe[3 * lb + 2] = val(3 * m + 2);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4* row = reinterpret_cast<const float4*>(Ke + (3 * l + c) * 24);
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const float4 w = row[q];
+          s = fmaf(w.x, xe[4 * q], s);
+          s = fmaf(w.y, xe[4 * q + 1], s);
+          s = fmaf(w.z, xe[4 * q + 2], s);
+          s = fmaf(w.w, xe[4 * q + 3], s);
+        }
+        acc[c] = s;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+    acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
+    acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 4);
+  }
+}
+
+// Coarse-level operator with identity rows on fixed DOFs, one node per 8
+// lanes (coarse_rows).  Three forms, so that a smoothing sweep and its
+// operator application are one launch:
 //   KV_PLAIN:  y = A x;
 //   KV_FIRST:  the first sweep from zero, x = omega D1^-1 b (neighbours' values
 //              formed on the fly), written to xo, and y = A x;
@@ -370,7 +421,6 @@ gmg_kv_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, in
               float* __restrict__ xo) {
   const int64_t n_node = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   const int sub = threadIdx.x & 7;
-  const int dx = sub & 1, dy = (sub >> 1) & 1, dz = sub >> 2;
   auto val = [&](int64_t d) -> float {
     return MODE == KV_FIRST ? omega * dinv[d] * b[d] : x[d];
   };
@@ -379,45 +429,8 @@ gmg_kv_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, in
   const int64_t trips = (n_node + groups - 1) / groups;
   for (int64_t tr = 0; tr < trips; ++tr) {
     const int64_t nd = tr * groups + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3);
-    float acc[3] = {0.0f, 0.0f, 0.0f};
-    if (nd < n_node) {
-      const int i = (int)(nd % (nx + 1));
-      const int j = (int)((nd / (nx + 1)) % (ny + 1));
-      const int k = (int)(nd / ((int64_t)(nx + 1) * (ny + 1)));
-      const int ex = i - dx, ey = j - dy, ez = k - dz;
-      if (ex >= 0 && ey >= 0 && ez >= 0 && ex < nx && ey < ny && ez < nz) {
-        const int l = dx + 2 * dy + 4 * dz;
-        const float* Ke = K + (ex + (int64_t)nx * (ey + (int64_t)ny * ez)) * 576;
-        float xe[24];
-#pragma unroll
-        for (int lb = 0; lb < 8; ++lb) {
-          const int64_t m = nid(ex + (lb & 1), ey + ((lb >> 1) & 1), ez + (lb >> 2), nx, ny);
-          xe[3 * lb] = val(3 * m);
-          xe[3 * lb + 1] = val(3 * m + 1);
-          xe[3 * lb + 2] = val(3 * m + 2);
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float4* row = reinterpret_cast<const float4*>(Ke + (3 * l + c) * 24);
-          float s = 0.0f;
-#pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const float4 w = row[q];
-            s = fmaf(w.x, xe[4 * q], s);
-            s = fmaf(w.y, xe[4 * q + 1], s);
-            s = fmaf(w.z, xe[4 * q + 2], s);
-            s = fmaf(w.w, xe[4 * q + 3], s);
-          }
-          acc[c] = s;
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
-      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
-      acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 4);
-    }
+    float acc[3];
+    coarse_rows(K, nx, ny, nz, nd, n_node, sub, val, acc);
     if (sub < 3 && nd < n_node) {
       const int64_t d = 3 * nd + sub;
       const uint8_t fm = fixed[nd];
@@ -429,6 +442,60 @@ gmg_kv_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, in
       } else {
         y[d] = yd;
         if (MODE == KV_FIRST) xo[d] = xd;
+      }
+    }
+  }
+}
+
+// Chebyshev sweeps on a coarse level with stored element matrices, each
+// operator application and the vector update after it in one launch (the
+// operator's result is not stored).  With d the step and r the
+// preconditioned residual (the recurrences of gmg_cheb_*):
+//   CH_FIRST: the first sweep from x = 0 through its first further step:
+//             d0 = D1^-1 b / theta formed on the fly, r = D1^-1 b - D1^-1 A d0,
+//             dn = c1 d0 + c2 r, x = d0 + dn;
+//   CH_BEGIN: a later sweep's start, in = x: r = D1^-1 (b - A x), dn = r / theta,
+//             xo = x + dn (xo distinct from x);
+//   CH_STEP:  in = d: r -= D1^-1 A d, dn = c1 d + c2 r, x += dn (dn distinct
+//             from d).
+enum { CH_FIRST = 0, CH_BEGIN = 1, CH_STEP = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(kB)
+gmg_cheb_coarse(const float* __restrict__ K, const uint8_t* __restrict__ fixed, int nx, int ny,
+                int nz, const float* __restrict__ in, const float* __restrict__ b,
+                const float* __restrict__ dinv, float inv_theta, float c1, float c2,
+                float* __restrict__ r, float* __restrict__ dn, float* __restrict__ x,
+                float* __restrict__ xo) {
+  const int64_t n_node = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const int sub = threadIdx.x & 7;
+  auto val = [&](int64_t q) -> float {
+    return MODE == CH_FIRST ? inv_theta * (dinv[q] * b[q]) : in[q];
+  };
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+  const int64_t trips = (n_node + groups - 1) / groups;
+  for (int64_t tr = 0; tr < trips; ++tr) {
+    const int64_t nd = tr * groups + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3);
+    float acc[3];
+    coarse_rows(K, nx, ny, nz, nd, n_node, sub, val, acc);
+    if (sub < 3 && nd < n_node) {
+      const int64_t q = 3 * nd + sub;
+      const float a = sub == 0 ? acc[0] : (sub == 1 ? acc[1] : acc[2]);
+      const float vq = val(q);
+      const float t = ((fixed[nd] >> sub) & 1) ? vq : a;
+      if (MODE == CH_BEGIN) {
+        const float ri = dinv[q] * (b[q] - t);
+        const float di = inv_theta * ri;
+        r[q] = ri;
+        dn[q] = di;
+        xo[q] = vq + di;
+      } else {
+        const float r0 = MODE == CH_FIRST ? dinv[q] * b[q] : r[q];
+        const float ri = r0 - dinv[q] * t;
+        const float di = c1 * vq + c2 * ri;
+        r[q] = ri;
+        dn[q] = di;
+        x[q] = (MODE == CH_FIRST ? vq : x[q]) + di;
       }
     }
   }
@@ -1117,6 +1184,45 @@ mfto_status cheb_sweeps(mfto_handle* h, GmgWs* w, int l, const float* b, float* 
   return MFTO_OK;
 }
 
+// The same sweeps on a coarse level with stored matrices (degree >= 2), one
+// launch per operator application (gmg_cheb_coarse): a sweep from zero is
+// degree - 1 launches, a later one degree.  A later sweep writes its iterate
+// to `other` and swaps the two; the step alternates between v.cd and v.t (on
+// exit v.t is not A x).
+mfto_status cheb_sweeps_coarse(mfto_handle* h, GmgWs* w, int l, const float* b, float*& x,
+                               float*& other, int sweeps, bool from_zero) {
+  const GmgLevel& v = w->lv[l];
+  const ChebCoef c = cheb_coef(w->cheb);
+  const int gk = grid_of(8 * v.n_node);
+  float* d = v.cd;
+  float* dn = v.t;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    int k = 0;
+    h->launches++;
+    if (sw == 0 && from_zero) {
+      gmg_cheb_coarse<CH_FIRST><<<gk, kB, 0, h->stream>>>(
+          v.d_K, v.d_fixed, v.nx, v.ny, v.nz, nullptr, b, v.d_dinv, c.inv_theta, c.c1[0],
+          c.c2[0], v.cr, d, x, nullptr);
+      k = 1;
+    } else {
+      gmg_cheb_coarse<CH_BEGIN><<<gk, kB, 0, h->stream>>>(
+          v.d_K, v.d_fixed, v.nx, v.ny, v.nz, x, b, v.d_dinv, c.inv_theta, 0.0f, 0.0f, v.cr, d,
+          nullptr, other);
+      std::swap(x, other);
+    }
+    MFTO_LAUNCH_CHECK(h);
+    for (; k + 1 < w->cheb; ++k) {
+      h->launches++;
+      gmg_cheb_coarse<CH_STEP><<<gk, kB, 0, h->stream>>>(
+          v.d_K, v.d_fixed, v.nx, v.ny, v.nz, d, nullptr, v.d_dinv, 0.0f, c.c1[k], c.c2[k], v.cr,
+          dn, x, nullptr);
+      MFTO_LAUNCH_CHECK(h);
+      std::swap(d, dn);
+    }
+  }
+  return MFTO_OK;
+}
+
 mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x,
                    float** out = nullptr);
 
@@ -1193,15 +1299,19 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x, fl
   const float om = (float)p.omega;
   // coarse levels with stored matrices: sweep and operator in one launch
   const bool cheb = w->cheb > 0;
-  const bool fused = l > 0 && !(l == 1 && w->mf1) && !cheb;
+  const bool stored = l > 0 && !(l == 1 && w->mf1);
+  const bool fused = stored && !cheb;
+  const bool cheb_fused = stored && w->cheb >= 2;
   if (l == 0 && v.x && v.x2 && !cheb && p.smoother_form == MFTO_FORM_F32 && h->kv_variant == 0)
     return vcycle_level0_fused(h, w, b, x);
-  float* other = fused ? (x == v.x ? v.x2 : v.x) : nullptr;
+  float* other = fused || cheb_fused ? (x == v.x ? v.x2 : v.x) : nullptr;
   // pre-smoothing; on exit v.t = A x
   if (p.nu_pre == 0) {
     MFTO_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * v.n_dof, h->stream));
   } else if (cheb) {
-    if ((s = cheb_sweeps(h, w, l, b, x, p.nu_pre, true)) != MFTO_OK) return s;
+    if ((s = cheb_fused ? cheb_sweeps_coarse(h, w, l, b, x, other, p.nu_pre, true)
+                        : cheb_sweeps(h, w, l, b, x, p.nu_pre, true)) != MFTO_OK)
+      return s;
     if ((s = apply_level(h, w, l, x, v.t)) != MFTO_OK) return s;
   } else if (fused) {
     h->launches++;
@@ -1238,7 +1348,9 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x, fl
                                                        v.nx, v.ny, v.nz, x, 1);
   MFTO_LAUNCH_CHECK(h);
   if (cheb) {
-    if ((s = cheb_sweeps(h, w, l, b, x, p.nu_post, false)) != MFTO_OK) return s;
+    if ((s = cheb_fused ? cheb_sweeps_coarse(h, w, l, b, x, other, p.nu_post, false)
+                        : cheb_sweeps(h, w, l, b, x, p.nu_post, false)) != MFTO_OK)
+      return s;
     if (out) *out = x;
     return MFTO_OK;
   }
