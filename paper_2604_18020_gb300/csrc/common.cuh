@@ -606,6 +606,11 @@ bool gmg_active(const mfto_handle* h);
 mfto_status gmg_sweep_col_launch(mfto_handle* h, bool first, const float* E, const float* b,
                                  const float* dinv, float omega, const float* x, float* xo,
                                  float* t);
+// Multigrid Chebyshev launches fused into the FP32 column K.v (kv_tile.cu).
+enum { GMG_CHEB_FIRST = 0, GMG_CHEB_BEGIN = 1, GMG_CHEB_STEP = 2 };
+mfto_status gmg_cheb_col_launch(mfto_handle* h, int mode, const float* E, const float* in,
+                                const float* b, const float* dinv, float inv_theta, float c1,
+                                float c2, float* r, float* dn, const float* x, float* xo);
 int64_t gmg_bytes(const mfto_handle* h);
 int64_t learned_bytes(const mfto_handle* h);
 void gmg_release(mfto_handle* h);

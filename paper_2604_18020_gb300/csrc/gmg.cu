@@ -1278,6 +1278,74 @@ mfto_status vcycle_level0_fused(mfto_handle* h, GmgWs* w, const float* b, float*
   return MFTO_OK;
 }
 
+// Level 0 with Chebyshev sweeps (degree >= 2) fused into the FP32 column K.v
+// (gmg_cheb_col_launch): the iterate lives in the level's two scratch buffers,
+// the step alternates between v.cd and v.t, and the last post-smoothing
+// launch (always a step) writes the caller's x.
+mfto_status vcycle_level0_cheb(mfto_handle* h, GmgWs* w, const float* b, float* x) {
+  const GmgLevel& v = w->lv[0];
+  const GmgLevel& c = w->lv[1];
+  const mfto_gmg_params& p = w->prm;
+  const ChebCoef cc = cheb_coef(w->cheb);
+  float* cur = v.x;
+  float* oth = v.x2;
+  float* d = v.cd;
+  float* dn = v.t;
+  // `sweeps` sweeps; the last step of the last one writes `dst` when given
+  auto sweeps = [&](int n, bool from_zero, float* dst) -> mfto_status {
+    mfto_status s;
+    for (int sw = 0; sw < n; ++sw) {
+      int k = 0;
+      if (sw == 0 && from_zero) {
+        if ((s = gmg_cheb_col_launch(h, GMG_CHEB_FIRST, w->d_E32, nullptr, b, v.d_dinv,
+                                     cc.inv_theta, cc.c1[0], cc.c2[0], v.cr, d, nullptr, cur)) !=
+            MFTO_OK)
+          return s;
+        k = 1;
+      } else {
+        if ((s = gmg_cheb_col_launch(h, GMG_CHEB_BEGIN, w->d_E32, cur, b, v.d_dinv,
+                                     cc.inv_theta, 0.0f, 0.0f, v.cr, d, nullptr, oth)) != MFTO_OK)
+          return s;
+        std::swap(cur, oth);
+      }
+      for (; k + 1 < w->cheb; ++k) {
+        const bool last = dst && sw + 1 == n && k + 2 == w->cheb;
+        if ((s = gmg_cheb_col_launch(h, GMG_CHEB_STEP, w->d_E32, d, nullptr, v.d_dinv, 0.0f,
+                                     cc.c1[k], cc.c2[k], v.cr, dn, cur, last ? dst : cur)) !=
+            MFTO_OK)
+          return s;
+        std::swap(d, dn);
+        if (last) cur = dst;
+      }
+    }
+    return MFTO_OK;
+  };
+  mfto_status s;
+  if (p.nu_pre == 0) {
+    MFTO_CUDA(h, cudaMemsetAsync(cur, 0, sizeof(float) * v.n_dof, h->stream));
+  } else {
+    if ((s = sweeps(p.nu_pre, true, nullptr)) != MFTO_OK) return s;
+    if ((s = apply_level(h, w, 0, cur, v.t)) != MFTO_OK) return s;
+  }
+  h->launches++;
+  gmg_restrict<<<grid_of(c.n_dof), kB, 0, h->stream>>>(
+      b, p.nu_pre ? v.t : nullptr, v.d_fixed, v.nx, v.ny, v.nz, c.d_fixed, c.nx, c.ny, c.nz, c.b,
+      nullptr);
+  MFTO_LAUNCH_CHECK(h);
+  float* xc = nullptr;
+  if ((s = vcycle(h, w, 1, c.b, c.x, &xc)) != MFTO_OK) return s;
+  h->launches++;
+  gmg_prolong<<<grid_of(v.n_node), kB, 0, h->stream>>>(xc, c.d_fixed, c.nx, c.ny, v.d_fixed,
+                                                       v.nx, v.ny, v.nz, cur, 1);
+  MFTO_LAUNCH_CHECK(h);
+  if (p.nu_post == 0) {
+    MFTO_CUDA(h, cudaMemcpyAsync(x, cur, sizeof(float) * v.n_dof, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+    return MFTO_OK;
+  }
+  return sweeps(p.nu_post, false, x);
+}
+
 // One V-cycle from level l: b the right-hand side, x the caller's output
 // buffer on level 0; on coarse levels the result lands in lv[l].x or
 // lv[l].x2 (fused sweeps alternate between them) and *out says which.
@@ -1302,8 +1370,10 @@ mfto_status vcycle(mfto_handle* h, GmgWs* w, int l, const float* b, float* x, fl
   const bool stored = l > 0 && !(l == 1 && w->mf1);
   const bool fused = stored && !cheb;
   const bool cheb_fused = stored && w->cheb >= 2;
-  if (l == 0 && v.x && v.x2 && !cheb && p.smoother_form == MFTO_FORM_F32 && h->kv_variant == 0)
-    return vcycle_level0_fused(h, w, b, x);
+  if (l == 0 && v.x && v.x2 && p.smoother_form == MFTO_FORM_F32 && h->kv_variant == 0) {
+    if (!cheb) return vcycle_level0_fused(h, w, b, x);
+    if (w->cheb >= 2) return vcycle_level0_cheb(h, w, b, x);
+  }
   float* other = fused || cheb_fused ? (x == v.x ? v.x2 : v.x) : nullptr;
   // pre-smoothing; on exit v.t = A x
   if (p.nu_pre == 0) {
@@ -1620,7 +1690,7 @@ extern "C" mfto_status mfto_gmg_setup(mfto_handle* h, const double* d_E,
   // Chebyshev sweeps: as asked, or (cheb_degree = -1) degree 2 up to 4M DOFs,
   // where they were measured faster, l1-Jacobi above
   w->cheb = p.cheb_degree >= 0 ? p.cheb_degree : (h->n_dof <= 4000000 ? 2 : 0);
-  if (w->cheb == 0 && p.smoother_form == MFTO_FORM_F32 && w->n_levels >= 2 &&
+  if (w->cheb != 1 && p.smoother_form == MFTO_FORM_F32 && w->n_levels >= 2 &&
       !w->lv[0].x) {                        // level-0 scratch of the fused sweeps
     GmgLevel& v = w->lv[0];
     if (cudaMalloc((void**)&v.x, sizeof(float) * v.n_dof) != cudaSuccess ||

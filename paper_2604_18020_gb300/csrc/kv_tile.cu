@@ -129,6 +129,100 @@ gmg_sweep_col_kernel(const float* __restrict__ E, const float* __restrict__ b,
                    reinterpret_cast<float*>(smem_raw));
 }
 
+// Multigrid Chebyshev sweeps on the level-0 operator, fused into the column
+// K.v the same way (the recurrences of the gmg_cheb_* kernels in gmg.cu; d
+// the step, r the preconditioned residual, t = A of the loaded vector):
+//   ColChebFirst (loads d0 = D1^-1 b / theta): r = D1^-1 b - D1^-1 t,
+//     dn = c1 d0 + c2 r, x = d0 + dn;
+//   ColChebBegin (loads x): r = D1^-1 (b - t), dn = r / theta, xo = x + dn;
+//   ColChebStep (loads d): r -= D1^-1 t, dn = c1 d + c2 r, xo = x + dn (xo
+//     may be x, which no other thread reads).
+// The written step dn and a Begin's xo are buffers the launch does not load.
+struct ColChebFirst {
+  const float* b;
+  const float* dinv;
+  float c1, c2;
+  float* r;
+  float* dn;
+  float* x;
+  __device__ __forceinline__ void operator()(int node, const float (&acc)[3], const float (&pn)[3],
+                                             uint8_t fm, DFloat& red) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int q = 3 * node + c;
+      const float t = ((fm >> c) & 1) ? pn[c] : acc[c];
+      const float ri = dinv[q] * b[q] - dinv[q] * t;
+      const float di = c1 * pn[c] + c2 * ri;
+      r[q] = ri;
+      dn[q] = di;
+      x[q] = pn[c] + di;
+    }
+  }
+};
+
+struct ColChebBegin {
+  const float* b;
+  const float* dinv;
+  float inv_theta;
+  float* r;
+  float* dn;
+  float* xo;
+  __device__ __forceinline__ void operator()(int node, const float (&acc)[3], const float (&pn)[3],
+                                             uint8_t fm, DFloat& red) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int q = 3 * node + c;
+      const float t = ((fm >> c) & 1) ? pn[c] : acc[c];
+      const float ri = dinv[q] * (b[q] - t);
+      const float di = inv_theta * ri;
+      r[q] = ri;
+      dn[q] = di;
+      xo[q] = pn[c] + di;
+    }
+  }
+};
+
+struct ColChebStep {
+  const float* dinv;
+  float c1, c2;
+  float* r;
+  float* dn;
+  const float* x;
+  float* xo;
+  __device__ __forceinline__ void operator()(int node, const float (&acc)[3], const float (&pn)[3],
+                                             uint8_t fm, DFloat& red) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int q = 3 * node + c;
+      const float t = ((fm >> c) & 1) ? pn[c] : acc[c];
+      const float ri = r[q] - dinv[q] * t;
+      const float di = c1 * pn[c] + c2 * ri;
+      r[q] = ri;
+      dn[q] = di;
+      xo[q] = x[q] + di;
+    }
+  }
+};
+
+template <int MINB, int MODE>
+__global__ void __launch_bounds__(MFTO_BLOCK, MINB)
+gmg_cheb_col_kernel(const float* __restrict__ E, const float* in, const float* b,
+                    const float* dinv, float inv_theta, float c1, float c2, float* r, float* dn,
+                    const float* x, float* xo, const uint8_t* __restrict__ fixed,
+                    ModeCoef<float> K, Grid g, ColTiling tl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  if (MODE == GMG_CHEB_FIRST)
+    kv_column_body(E, fixed, K, g, tl, ColLoadScaled{b, dinv, inv_theta},
+                   ColChebFirst{b, dinv, c1, c2, r, dn, xo}, sm);
+  else if (MODE == GMG_CHEB_BEGIN)
+    kv_column_body(E, fixed, K, g, tl, ColLoadPlain{in},
+                   ColChebBegin{b, dinv, inv_theta, r, dn, xo}, sm);
+  else
+    kv_column_body(E, fixed, K, g, tl, ColLoadPlain{in}, ColChebStep{dinv, c1, c2, r, dn, x, xo},
+                   sm);
+}
+
 template <int MINB>
 __global__ void __launch_bounds__(MFTO_BLOCK, MINB)
 pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
@@ -231,6 +325,18 @@ mfto_status kv_tile_init(mfto_handle* h) {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(gmg_sweep_col_kernel<3, 1>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_cheb_col_kernel<2, GMG_CHEB_FIRST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_cheb_col_kernel<2, GMG_CHEB_BEGIN>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_cheb_col_kernel<2, GMG_CHEB_STEP>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_cheb_col_kernel<3, GMG_CHEB_FIRST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_cheb_col_kernel<3, GMG_CHEB_BEGIN>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(gmg_cheb_col_kernel<3, GMG_CHEB_STEP>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel<2>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_col_kernel<3>,
@@ -286,6 +392,37 @@ mfto_status gmg_sweep_col_launch(mfto_handle* h, bool first, const float* E, con
       gmg_sweep_col_kernel<2, 0><<<grid, MFTO_BLOCK, sm, h->stream>>>(
           E, b, dinv, omega, x, xo, t, h->d_fixed, h->mc32, g, tl);
   }
+  MFTO_LAUNCH_CHECK(h);
+  return MFTO_OK;
+}
+
+// One Chebyshev launch on the FP32 operator fused with it (mode and buffers as
+// gmg_cheb_col_kernel: in the loaded vector of BEGIN and STEP, x the iterate
+// STEP adds to, xo where the new iterate goes).  Needs the column kernel.
+mfto_status gmg_cheb_col_launch(mfto_handle* h, int mode, const float* E, const float* in,
+                                const float* b, const float* dinv, float inv_theta, float c1,
+                                float c2, float* r, float* dn, const float* x, float* xo) {
+  if (h->kv_variant != 0)
+    return mfto_fail(h, MFTO_UNSUPPORTED, "fused sweeps need the column K.v");
+  int grid = 0;
+  const int kind = h->col_kind;
+  const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
+  const Grid g = make_grid(h->mesh);
+  const size_t sm = ColShape::smem_bytes;
+  h->launches++;
+#define MFTO_CHEB_COL(MINB, MODE)                                                               \
+  gmg_cheb_col_kernel<MINB, MODE><<<grid, MFTO_BLOCK, sm, h->stream>>>(                         \
+      E, in, b, dinv, inv_theta, c1, c2, r, dn, x, xo, h->d_fixed, h->mc32, g, tl)
+  if (kind == 1) {
+    if (mode == GMG_CHEB_FIRST) MFTO_CHEB_COL(3, GMG_CHEB_FIRST);
+    else if (mode == GMG_CHEB_BEGIN) MFTO_CHEB_COL(3, GMG_CHEB_BEGIN);
+    else MFTO_CHEB_COL(3, GMG_CHEB_STEP);
+  } else {
+    if (mode == GMG_CHEB_FIRST) MFTO_CHEB_COL(2, GMG_CHEB_FIRST);
+    else if (mode == GMG_CHEB_BEGIN) MFTO_CHEB_COL(2, GMG_CHEB_BEGIN);
+    else MFTO_CHEB_COL(2, GMG_CHEB_STEP);
+  }
+#undef MFTO_CHEB_COL
   MFTO_LAUNCH_CHECK(h);
   return MFTO_OK;
 }

@@ -233,7 +233,7 @@ def test_device_bytes_accounts_for_the_hierarchy(cuda):
             exp += 2 * 4 * 3 * n_node
             if cheb > 0 and l + 1 < len(dims):
                 exp += 2 * 4 * 3 * n_node                         # Chebyshev step, residual
-            if cheb == 0 and l == 0:
+            if cheb != 1 and l == 0:
                 exp += 2 * 4 * 3 * n_node                         # fused-sweep scratch
             if l > 0:
                 exp += n_node + 4 * (576 * nx * ny * nz + 3 * 3 * n_node)
