@@ -104,24 +104,51 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        rows = []
+        lines = []
         if self.path and os.path.exists(self.path):
-            for line in open(self.path):
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-                except ValueError:
-                    continue
+            with open(self.path) as fh:
+                lines = fh.readlines()
             os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        reasons = sorted({REASONS[i] for _, _, flags in rows for i, f in enumerate(flags)
-                          if f.lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows),
-                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+        return clock_summary(lines)
+
+
+def clock_summary(lines):
+    """Median SM clock, the largest max-clock reading and the throttle
+    reasons seen active, from nvidia-smi CSV rows of SMI_FIELDS (no header,
+    no units); malformed rows are skipped."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    reasons = sorted({REASONS[i] for _, _, flags in rows for i, f in enumerate(flags)
+                      if f.lower() == "active"})
+    return {"sm_mhz": statistics.median(r[0] for r in rows),
+            "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+            "samples": len(rows)}
+
+
+def reduce_over_ranks(dist, device, maxes, sums):
+    """The benchmark's reduction over ranks: the largest of each timing in
+    `maxes` and the total of each count in `sums` (the ranks are independent
+    replicas; besides this and the barriers around the timed region they
+    exchange nothing).  dist = None (one process) returns both lists
+    unchanged."""
+    maxes, sums = [float(x) for x in maxes], [float(x) for x in sums]
+    if dist is None:
+        return maxes, sums
+    import torch
+    tm = torch.tensor(maxes, dtype=torch.float64, device=device)
+    ts = torch.tensor(sums, dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return tm.tolist(), ts.tolist()
 
 
 # ------------------------------------------------------------ CPU oracle leg
@@ -260,10 +287,6 @@ def gpu_bench(args, rank, local_rank, world):
     with ClockSampler(local_rank) as clocks:
         t_ms, stats, launches, _, _, _ = timed_pass(False)
     torch.cuda.synchronize()
-    if dist:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = tt.item()
     clk = clocks.summary()
     # replay with events around every K.v launch (same steps, same state)
     _, stats_b, _, kv64, kv32, cgt = timed_pass(True)
@@ -335,12 +358,9 @@ def gpu_bench(args, rank, local_rank, world):
             "device_used_bytes": int(total_b - free_b)}
     h2d = (h_rho.numel() + h_u.numel() + h_f.numel()) * 8
     d2h = (o_rho.numel() + o_u.numel()) * 8
-    if dist:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = tt.item()
-
-    units = m.n_elem * kv_per_pass * world
+    # the slowest rank's times and the K.v element applications of all ranks
+    (t_ms, e2e_ms), (units,) = reduce_over_ranks(dist, dev, [t_ms, e2e_ms],
+                                                 [m.n_elem * kv_per_pass])
     value = units / (t_ms * 1e-3) / 1e9
     e2e_value = units / (e2e_ms * 1e-3) / 1e9
     kv_avg_s = kv_ms * 1e-3 / max(kv_n, 1)
