@@ -50,8 +50,13 @@ def test_levels_and_operators_match_oracle(cuda, shape, matfree):
 @pytest.mark.parametrize("shape,nu,matfree,cheb", [((24, 12, 12), 2, -1, 0), ((13, 7, 5), 1, -1, 0),
                                                    ((9, 6, 4), 0, -1, 0), ((24, 12, 12), 1, 1, 0),
                                                    ((13, 7, 5), 2, 1, 0), ((24, 12, 12), 1, -1, 2),
-                                                   ((13, 7, 5), 2, 1, 3)])
+                                                   ((13, 7, 5), 2, 1, 3), ((13, 7, 5), 2, -1, 2),
+                                                   ((9, 6, 4), 0, -1, 2)])
 def test_vcycle_matches_oracle(cuda, shape, nu, matfree, cheb):
+    """One V-cycle against the oracle's: l1-Jacobi (cheb 0) and Chebyshev
+    sweeps, 0-2 sweeps each side (two sweeps start the second from the
+    current iterate, the fused kernels' second-buffer path), level 1 from
+    its matrices (-1) or as Phat^T K Phat (1)."""
     import torch
     P, m, fd, E, Ed, h, H = _setup(shape, nu_pre=nu, nu_post=nu, matfree_level1=matfree,
                                    cheb_degree=cheb)
