@@ -207,10 +207,37 @@ def run_cpu_sample(workload, steps, maxit):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def host_cpu():
+    """The host's logical core count and CPU model name (from lscpu, else
+    /proc/cpuinfo, else the machine type)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return os.cpu_count(), model or platform.machine()
+
+
 def cpu_baseline_entry(res, maxit):
     tot_t = sum(res["times"])
     tot_kv = sum(res["kv"])
+    n_cores, model = host_cpu()
     return {"value": res["n_elem"] * tot_kv / tot_t / 1e9, "unit": "Gelem/s", "cores": 1,
+            "host_cores": n_cores, "cpu_model": model,
             "kind": "oracle",
             "sample": f"{len(res['times'])} SIMP iteration(s) of {WORKLOAD} by the FP64 numpy "
                       f"oracle from the uniform start, PCG capped at {maxit} iterations "

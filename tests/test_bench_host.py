@@ -76,3 +76,13 @@ def test_reference_arm_other_ranks_exit_without_work(rank):
                          capture_output=True, text=True, env=env, cwd=str(ROOT), timeout=120)
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.strip() == ""
+
+
+def test_cpu_baseline_entry_records_the_host():
+    """The oracle leg's entry: element applications per second over the
+    sample, one thread, the host's core count and CPU model."""
+    e = bench.cpu_baseline_entry({"times": [1.0, 3.0], "kv": [40, 40], "n_elem": 216000}, 40)
+    assert e["value"] == 216000 * 80 / 4.0 / 1e9
+    assert e["cores"] == 1 and e["kind"] == "oracle"
+    assert isinstance(e["host_cores"], int) and e["host_cores"] >= 1
+    assert isinstance(e["cpu_model"], str) and e["cpu_model"]
