@@ -679,11 +679,14 @@ mfto_status mfto_compliance_sens_noalloc(const mfto_mesh* mesh, double E0, doubl
  * DOFs zeroed; a coarse DOF is fixed where the fine DOF at its position is;
  * each coarse level is the Galerkin product Phat^T A Phat (formed element by
  * element: each coarse element's 24 x 24 matrix from its children's) plus the
- * identity on its fixed DOFs.  V-cycle: nu_pre l1-Jacobi sweeps
- * x += omega D1^-1 (b - A x) from x = 0 (D1 the l1 row sums of the element
- * matrices), residual, restriction, recursion, prolongation, nu_post sweeps;
- * the coarsest level is solved by its dense inverse (FP64 Cholesky on the
- * host, applied in FP32).  The cycle runs in FP32. */
+ * identity on its fixed DOFs.  V-cycle: nu_pre sweeps from x = 0, either
+ * l1-Jacobi, x += omega D1^-1 (b - A x) (D1 the l1 row sums of the element
+ * matrices), or Chebyshev sweeps of degree cheb_degree for D1^-1 A; residual,
+ * restriction, recursion, prolongation, nu_post sweeps; the coarsest level is
+ * solved by its dense inverse (FP64 Cholesky on the host, applied in FP32).
+ * The cycle runs in FP32, each sweep's vector update inside the launch that
+ * applies the operator where the operator is the FP32 column K.v or stored
+ * element matrices. */
 #define MFTO_GMG_MAX_LEVELS 10
 #define MFTO_GMG_MAX_COARSE 1000   /* DOFs of the densely inverted level */
 typedef struct {
