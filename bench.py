@@ -246,6 +246,73 @@ def cpu_baseline_entry(res, maxit):
 
 # ------------------------------------------------------------- GPU leg
 
+def cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm):
+    """Roofline of one launch of the FP32 CG K.v on mesh m: algorithmic
+    bytes (reads z, p_old, E, the node mask; writes p_new, q) and the dense
+    element contraction (1152 flop per element) against the measured HBM
+    copy bandwidth and the FP32 FMA pipe at the sampled SM clock; the slower
+    of the two is the bound."""
+    bytes_per_launch = m.n_node * (4 * 12 + 1) + 4 * m.n_elem
+    hbm = measured_hbm_gbs()
+    fp32_peak_tflops = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    t_bytes = bytes_per_launch / (hbm * 1e9)
+    t_flops = FLOP_PER_ELEM * m.n_elem / (fp32_peak_tflops * 1e12)
+    out = {"bytes_per_launch": bytes_per_launch, "flop_per_elem": FLOP_PER_ELEM,
+           "frac_hbm": t_bytes / kv_avg_s, "frac_fp32_pipe": t_flops / kv_avg_s}
+    if t_bytes >= t_flops:
+        out.update({"bound": "hbm", "achieved": bytes_per_launch / kv_avg_s / 1e9, "peak": hbm,
+                    "unit": "GB/s",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy benchmark), of measured"})
+    else:
+        out.update({"bound": "alu", "achieved": FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12,
+                    "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "peak_source": f"FP32 FMA pipe, {n_sm} SMs x 128 FMA/clk x 2 flop x "
+                                   f"{sm_mhz:.0f} MHz median SM clock under load"})
+    out["frac"] = out["achieved"] / out["peak"]
+    return out
+
+
+def large_kv_leg(dev, sm_mhz, n_sm, iters=400, workload="cantilever_256x128x150"):
+    """The FP32 CG K.v on the 256 x 128 x 150 cantilever (4,915,200 elements,
+    15.0M DOFs; another workload if given): one mixed solve of a filtered
+    random design from u = 0, its inner CG capped at `iters` iterations (one
+    refinement step), the launch shape autotuned, CUDA events around every
+    K.v launch."""
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    P = W.WORKLOADS[workload]()
+    m = P.mesh
+    h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed,
+                    params=mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8))
+    try:
+        tuned = h.kv_autotune()
+        h.set_solver(mfto.FORM_F32, 1e-8, iters, 1)
+        h.set_ir_mode(IR_MODES["continue"])
+        rho = torch.tensor(W.rho_binary(m, seed=2, volfrac=P.volfrac), device=dev)
+        rho_phys = torch.empty_like(rho)
+        h.filter(rho, rho_phys)
+        E = torch.empty_like(rho)
+        h.simp_modulus(rho_phys, E)
+        f = torch.tensor(P.f, device=dev)
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+        h.ir_solve(E, f, u, inner_tol=1e-8)          # warm-up: graph capture
+        u.zero_()
+        h.kv_timing(True)
+        st = h.ir_solve(E, f, u, inner_tol=1e-8)
+        n, ms = h.kv_timing_read(mfto.FORM_F32)
+        h.kv_timing(False)
+    finally:
+        h.close()
+    kv_avg_s = ms * 1e-3 / max(n, 1)
+    roof = cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm)
+    roof.update({"workload": workload, "elements": m.n_elem,
+                 "kernel": f"pcg_kv_col_kernel<{2 if tuned[1] == 0 else 3}>",
+                 "kv_f32_zchunk": tuned[0], "kv_f32_kernel_kind": tuned[1],
+                 "launches_timed": n, "kv_kernel_us": kv_avg_s * 1e6,
+                 "kv_kernel_gelem_s": m.n_elem / kv_avg_s / 1e9,
+                 "inner_iterations": st.inner_iterations})
+    return roof
+
 def gpu_bench(args, rank, local_rank, world):
     import numpy as np
     import torch
@@ -394,37 +461,20 @@ def gpu_bench(args, rank, local_rank, world):
     sm_mhz = clk["sm_mhz"] or 1950.0
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
     if args.form == "mixed":
-        # the CG K.v launch: reads z, p_old, E, the node mask; writes p_new, q
-        bytes_per_launch = m.n_node * (4 * 12 + 1) + 4 * m.n_elem
         kname = ("pcg_kv_tile_kernel<float>" if args.inner_form == "f32"
                  else f"pcg_kv_tc_kernel ({args.inner_form})")
         if args.inner_form == "f32" and not persistent:
             kname = "pcg_kv_col_kernel<2>" if tuned is None or tuned[1] == 0 else "pcg_kv_col_kernel<3>"
+        roof = cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm)
         if persistent:
-            # one CG iteration of the persistent kernel: the K.v phase above plus
-            # the vector update (reads u, p, q, r, 1/d; writes u, r, z: 32 B/DOF);
+            # one CG iteration of the persistent kernel: the K.v phase plus the
+            # vector update (reads u, p, q, r, 1/d; writes u, r, z: 32 B/DOF);
             # its time includes both grid barriers
-            bytes_per_launch += 32 * m.n_dof
             kname = "pcg_persist_f32 (per CG iteration: K.v + vector update + 2 grid barriers)"
-        hbm = measured_hbm_gbs()
-        fp32_peak_tflops = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
-        t_bytes = bytes_per_launch / (hbm * 1e9)
-        t_flops = FLOP_PER_ELEM * m.n_elem / (fp32_peak_tflops * 1e12)
-        frac_hbm = t_bytes / kv_avg_s
-        frac_alu = t_flops / kv_avg_s
-        if t_bytes >= t_flops:
-            roof = {"bound": "hbm", "achieved": bytes_per_launch / kv_avg_s / 1e9, "peak": hbm,
-                    "unit": "GB/s",
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy benchmark), of measured"}
-        else:
-            roof = {"bound": "alu", "achieved": FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12,
-                    "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                    "peak_source": f"FP32 FMA pipe, {n_sm} SMs x 128 FMA/clk x 2 flop x "
-                                   f"{sm_mhz:.0f} MHz median SM clock under load"}
-        roof.update({"traffic": NCU_DRAM_BYTES.get((kname, WORKLOAD)), "kernel": kname,
-                     "bytes_per_launch": bytes_per_launch,
-                     "flop_per_elem": FLOP_PER_ELEM, "frac_hbm": frac_hbm,
-                     "frac_fp32_pipe": frac_alu})
+            roof = cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm)
+            roof["bytes_per_launch"] += 32 * m.n_dof
+            roof["frac_hbm"] = roof["bytes_per_launch"] / (measured_hbm_gbs() * 1e9) / kv_avg_s
+        roof.update({"traffic": NCU_DRAM_BYTES.get((kname, WORKLOAD)), "kernel": kname})
         if persistent:
             roof.update({"unit_of_work": "one CG iteration (one K.v application)",
                          "launches": cgt[0], "iterations_per_launch": cgt[1] / cgt[0],
@@ -439,6 +489,9 @@ def gpu_bench(args, rank, local_rank, world):
                                f"{sm_mhz:.0f} MHz median SM clock under load",
                 "flop_per_elem": FLOP_PER_ELEM}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    large = None
+    if args.form == "mixed" and args.inner_form == "f32" and not args.no_large and rank == 0:
+        large = large_kv_leg(dev, sm_mhz, n_sm)
     out = {
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
@@ -449,7 +502,7 @@ def gpu_bench(args, rank, local_rank, world):
                    "form": args.form, "pcg_rtol": 1e-8,
                    "inner_tol": args.inner_tol if args.form == "mixed" else None,
                    "inner_form": args.inner_form if args.form == "mixed" else None,
-                   "kv_kernel": "tiled mode-space",
+                   "kv_kernel": roof.get("kernel"),
                    "cg_engine": ("persistent" if persistent else "graph") if args.form == "mixed" else "graph",
                    "kv_f32_zchunk": tuned[0] if tuned else None,
                    "kv_f32_kernel_kind": tuned[1] if tuned else None,
@@ -466,6 +519,7 @@ def gpu_bench(args, rank, local_rank, world):
         "kv_kernel_gelem_s": m.n_elem / kv_avg_s / 1e9,
         "kv_f64_kernel_us": kv64[1] * 1e3 / max(kv64[0], 1),
         "roofline": roof,
+        "kv_large": large,
         "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -1147,8 +1201,8 @@ def main():
     ap.add_argument("--cpu-maxit", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench",
-                    choices=["bench", "profile", "pcg", "compare", "learned", "kappa", "protocol",
-                             "hard", "ubench", "gmg", "scaling"])
+                    choices=["bench", "profile", "pcg", "cgkv", "compare", "learned", "kappa",
+                             "protocol", "hard", "ubench", "gmg", "scaling"])
     ap.add_argument("--protocol-iters", type=int, default=120)
     ap.add_argument("--protocol-solvers", default="mixed,f64",
                     help="--mode protocol: comma-separated solvers among mixed, f64, gmg")
@@ -1178,6 +1232,8 @@ def main():
     ap.add_argument("--inner-form", default="f32",
                     choices=["f32", "tf32", "tf32x3", "bf16", "bf16x3", "f16", "f16x3"],
                     help="K.v form of the inner solve of --form mixed")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the FP32 CG K.v timing on the 256x128x150 cantilever")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--maxit", type=int, default=40, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -1209,6 +1265,13 @@ def main():
         return
     if args.mode == "scaling":
         scaling_run(args)
+        return
+    if args.mode == "cgkv":
+        # the FP32 CG K.v alone on --workload (inner CG capped at --maxit)
+        import torch
+        dev = torch.device("cuda:0")
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        print(json.dumps(large_kv_leg(dev, 2070.0, n_sm, args.maxit, args.workload)))
         return
     if args.mode != "bench":
         profile_run(args)

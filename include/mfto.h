@@ -28,9 +28,22 @@
  * Memory and streams: every array argument named d_* is a DEVICE pointer
  * owned by the caller (the library never frees it); h_* is a HOST pointer.
  * All device work is enqueued on the stream given at mfto_create; calls that
- * return host scalars synchronise that stream before returning.  The library
- * allocates device memory only in mfto_create (its own workspace, freed by
- * mfto_destroy).  Arguments must not alias unless a function says so.
+ * return host scalars synchronise that stream before returning.  Arguments
+ * must not alias unless a function says so.
+ *
+ * Device allocations by the library (everything is freed by the matching
+ * destroy call): mfto_create (the handle's workspace and the filter
+ * stencil); mfto_set_params and mfto_simp_protocol when the filter radius
+ * changes (the stencil is made again); mfto_gmg_setup, and the multigrid
+ * solves and SIMP steps that build a hierarchy on first use or when its
+ * shape changes (levels, coarse inverse, sweep vectors); the learned-part
+ * calls on a handle (mfto_nn_features, mfto_nn_target, mfto_nn_to_dofs,
+ * mfto_nn_sample, mfto_set_learned, mfto_nn_train_energy) on first use of a
+ * grid depth; and the constructors of the separate objects, mfto_batch_create,
+ * mfto_ebe_create and mfto_nn_create.  Every other call works in memory that
+ * already exists.  There is no separate workspace-size query: a handle's
+ * whole device footprint, workspace and optional parts included, is reported
+ * by mfto_device_bytes.  mfto_compliance_sens_noalloc allocates nothing.
  *
  * Errors: every function returns an mfto_status; nothing is thrown across the
  * ABI.  On an error the handle's message is available from mfto_last_error.
@@ -655,8 +668,13 @@ mfto_status mfto_launch_count(const mfto_handle* h, int64_t* n);
  * KE, 2048 per-block partial sums, a ticket and the result) that every GPU
  * which loads the library holds until the process exits; meshes of more than
  * 2048 x 256 = 524,288 elements are rejected with MFTO_TOO_LARGE.  The first
- * call on a device looks up the array's device address (set-up); make that
- * first call before any stream capture.  All calls share the array and it
+ * call on a device looks up the array's device address (set-up) and keeps it
+ * for the rest of the process; make that first call before any stream
+ * capture, and do not call the entry point again on a device after a
+ * cudaDeviceReset of it (the kept address belongs to the reset context).
+ * Every call copies the unit KE in, reads the result back and synchronises
+ * the stream before it returns.  The pointers must be memory of the current
+ * device.  All calls share the array and it
  * keeps the last call's contents (the ticket is cleared by every call), so
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * and must be serialised by the caller.  Returns MFTO_INVALID_ARG for null

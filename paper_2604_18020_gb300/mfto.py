@@ -315,6 +315,16 @@ def compliance_sens_noalloc(nelx, nely, nelz, rho_phys, u, dc=None, E0=1.0, Emin
     n_elem = nelx * nely * nelz
     n_dof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
     st = stream if stream is not None else torch.cuda.current_stream()
+    # the library launches on the current device: every array and the stream
+    # must live there
+    cur = torch.cuda.current_device()
+    for name, t in (("rho_phys", rho_phys), ("u", u), ("dc", dc)):
+        if t is not None and t.is_cuda and t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
+                             f"cuda:{cur}")
+    if st.device.index != cur:
+        raise ValueError(f"the stream is on cuda:{st.device.index}, the current device is "
+                         f"cuda:{cur}")
     c = C.c_double()
     m = Mesh(nelx, nely, nelz, h)
     code = lib().mfto_compliance_sens_noalloc(

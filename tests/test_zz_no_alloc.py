@@ -50,3 +50,23 @@ def test_noalloc_two_calls_in_a_row_and_capacity(cuda):
                                      torch.zeros(big.n_elem, dtype=torch.float64, device=cuda),
                                      torch.zeros(big.n_dof, dtype=torch.float64, device=cuda))
     assert err.value.code == mfto.TOO_LARGE
+
+
+def test_noalloc_at_capacity(cuda):
+    """Exactly 524,288 elements (128 x 64 x 64): every partial-sum slot and the
+    last-block ticket in use; two calls in a row against the handle's result."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    m = W.Mesh(128, 64, 64)
+    assert m.n_elem == mfto.NOALLOC_MAX_ELEMENTS
+    fixed = W.fixed_face(m, "x0")
+    rho, u = _inputs(m, 23, cuda)
+    with mfto.Handle(m.nelx, m.nely, m.nelz, fixed) as h:
+        dc_ref = torch.empty(m.n_elem, dtype=torch.float64, device=cuda)
+        c_ref = h.compliance_sens(rho, u, dc_ref)
+    ref = dc_ref.cpu().numpy()
+    for call in range(2):
+        dc = torch.full((m.n_elem,), float("nan"), dtype=torch.float64, device=cuda)
+        c = mfto.compliance_sens_noalloc(m.nelx, m.nely, m.nelz, rho, u, dc)
+        assert abs(c - c_ref) <= 1e-12 * abs(c_ref), (call, c, c_ref)
+        assert np.abs(dc.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max(), call
