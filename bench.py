@@ -272,7 +272,8 @@ def cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm):
     return out
 
 
-def large_kv_leg(dev, sm_mhz, n_sm, iters=400, workload="cantilever_256x128x150"):
+def large_kv_leg(dev, sm_mhz, n_sm, iters=400, workload="cantilever_256x128x150", shape=None,
+                 engine=2):
     """The FP32 CG K.v on the 256 x 128 x 150 cantilever (4,915,200 elements,
     15.0M DOFs; another workload if given): one mixed solve of a filtered
     random design from u = 0, its inner CG capped at `iters` iterations (one
@@ -285,7 +286,12 @@ def large_kv_leg(dev, sm_mhz, n_sm, iters=400, workload="cantilever_256x128x150"
     h = mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed,
                     params=mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8))
     try:
-        tuned = h.kv_autotune()
+        h.set_cg_engine(engine)
+        if shape:
+            h.set_kv_shape(*shape)
+            tuned = (shape[0], shape[1], None)
+        else:
+            tuned = h.kv_autotune()
         h.set_solver(mfto.FORM_F32, 1e-8, iters, 1)
         h.set_ir_mode(IR_MODES["continue"])
         rho = torch.tensor(W.rho_binary(m, seed=2, volfrac=P.volfrac), device=dev)
@@ -306,7 +312,8 @@ def large_kv_leg(dev, sm_mhz, n_sm, iters=400, workload="cantilever_256x128x150"
     kv_avg_s = ms * 1e-3 / max(n, 1)
     roof = cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm)
     roof.update({"workload": workload, "elements": m.n_elem,
-                 "kernel": f"pcg_kv_col_kernel<{2 if tuned[1] == 0 else 3}>",
+                 "kernel": (f"{'cg2_kv_kernel' if engine == 2 else 'pcg_kv_col_kernel'}"
+                            f"<{2 if tuned[1] == 0 else 3}>"),
                  "kv_f32_zchunk": tuned[0], "kv_f32_kernel_kind": tuned[1],
                  "launches_timed": n, "kv_kernel_us": kv_avg_s * 1e6,
                  "kv_kernel_gelem_s": m.n_elem / kv_avg_s / 1e9,
@@ -464,7 +471,8 @@ def gpu_bench(args, rank, local_rank, world):
         kname = ("pcg_kv_tile_kernel<float>" if args.inner_form == "f32"
                  else f"pcg_kv_tc_kernel ({args.inner_form})")
         if args.inner_form == "f32" and not persistent:
-            kname = "pcg_kv_col_kernel<2>" if tuned is None or tuned[1] == 0 else "pcg_kv_col_kernel<3>"
+            kbase = "cg2_kv_kernel" if args.cg_engine == 2 else "pcg_kv_col_kernel"
+            kname = f"{kbase}<{2 if tuned is None or tuned[1] == 0 else 3}>"
         roof = cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm)
         if persistent:
             # one CG iteration of the persistent kernel: the K.v phase plus the
@@ -491,7 +499,7 @@ def gpu_bench(args, rank, local_rank, world):
     roof["frac"] = roof["achieved"] / roof["peak"]
     large = None
     if args.form == "mixed" and args.inner_form == "f32" and not args.no_large and rank == 0:
-        large = large_kv_leg(dev, sm_mhz, n_sm)
+        large = large_kv_leg(dev, sm_mhz, n_sm, engine=args.cg_engine)
     out = {
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
@@ -503,7 +511,9 @@ def gpu_bench(args, rank, local_rank, world):
                    "inner_tol": args.inner_tol if args.form == "mixed" else None,
                    "inner_form": args.inner_form if args.form == "mixed" else None,
                    "kv_kernel": roof.get("kernel"),
-                   "cg_engine": ("persistent" if persistent else "graph") if args.form == "mixed" else "graph",
+                   "cg_engine": ({0: "graph, last-block tickets", 1: "persistent",
+                                  2: "graph, ticket-free"}[args.cg_engine]
+                                 if args.form == "mixed" else "graph"),
                    "kv_f32_zchunk": tuned[0] if tuned else None,
                    "kv_f32_kernel_kind": tuned[1] if tuned else None,
                    "ir_mode": args.ir_mode if args.form == "mixed" else None,
@@ -554,7 +564,9 @@ def profile_run(args):
         h.set_solver(mfto.FORMS[args.inner_form], args.inner_tol)
         h.set_cg_engine(args.cg_engine)
         h.set_ir_mode(IR_MODES[args.ir_mode])
-        if not args.no_autotune:
+        if args.kv_shape:
+            h.set_kv_shape(*(int(x) for x in args.kv_shape.split(",")))
+        elif not args.no_autotune:
             h.kv_autotune()
     f = torch.tensor(P.f, device=dev)
     u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
@@ -1227,8 +1239,9 @@ def main():
                     help="keep the default z-chunk of the FP32 column K.v")
     ap.add_argument("--kv-shape", default=None,
                     help="NZC,KIND: pin the FP32 column K.v launch shape instead of autotuning")
-    ap.add_argument("--cg-engine", type=int, default=0, choices=[0, 1],
-                    help="FP32 inner CG: 1 persistent cooperative kernel, 0 per-iteration graph")
+    ap.add_argument("--cg-engine", type=int, default=2, choices=[0, 1, 2],
+                    help="FP32 inner CG: 0 per-iteration graph, 1 persistent cooperative kernel, "
+                         "2 per-iteration graph without grid tickets")
     ap.add_argument("--inner-form", default="f32",
                     choices=["f32", "tf32", "tf32x3", "bf16", "bf16x3", "f16", "f16x3"],
                     help="K.v form of the inner solve of --form mixed")
@@ -1271,7 +1284,9 @@ def main():
         import torch
         dev = torch.device("cuda:0")
         n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-        print(json.dumps(large_kv_leg(dev, 2070.0, n_sm, args.maxit, args.workload)))
+        shape = tuple(int(x) for x in args.kv_shape.split(",")) if args.kv_shape else None
+        print(json.dumps(large_kv_leg(dev, 2070.0, n_sm, args.maxit, args.workload, shape,
+                                      args.cg_engine)))
         return
     if args.mode != "bench":
         profile_run(args)

@@ -223,13 +223,18 @@ mfto_status mfto_set_kv_variant(mfto_handle* h, int32_t variant);
 
 /* Choose how the FP32 inner Jacobi-PCG of the mixed solve (mfto_ir_solve and
  * mfto_simp_step with an F32 inner form) runs its iterations (Sec. 3.6):
- * 0 (default) = two kernels per iteration (K.v, vector update) replayed
+ * 0 = two kernels per iteration (K.v, vector update) replayed
  * from a captured CUDA graph; 1 = one persistent cooperative kernel per
  * inner solve: each iteration's K.v with the direction update, the vector
  * update and both dot products run between two bounded grid barriers, every
- * CTA reducing the per-CTA partials in the same order.  Both compute the same per-entry arithmetic;
- * the dot products add the per-block partials in a different order.  The
- * tensor-core inner forms and mfto_set_kv_variant(h, 1) always use 0.
+ * CTA reducing the per-CTA partials in the same order; 2 (default) = two kernels per
+ * iteration from a captured graph like 0, without grid-wide tickets: each
+ * kernel sums the per-block partials of the dot products it needs (r.z and
+ * r.r in the K.v's pre-step, p.q before the vector update) while its first
+ * loads are in flight, every block in the same fixed order.  All compute the
+ * same per-entry arithmetic; the dot products add the per-block partials in
+ * different orders.  The tensor-core inner forms and
+ * mfto_set_kv_variant(h, 1) always use 0.
  * MFTO_UNSUPPORTED for 1 without cooperative launch.  A barrier wait that
  * gives up (about a second) makes the solve return MFTO_CUDA_ERROR. */
 mfto_status mfto_set_cg_engine(mfto_handle* h, int32_t engine);

@@ -42,6 +42,11 @@ struct PcgScalars {
   unsigned int ticket_a, ticket_b, ticket_c;
   int32_t tc_error;         // a tensor-core completion wait gave up
   int32_t bar_error;        // a grid-barrier wait of the persistent CG gave up
+  // ticket-free FP32 CG (pcg_f32.cu): r.z, its reciprocal and the
+  // completed-iteration count of iteration k in slot k & 1
+  double rz2[2];
+  double rinv2[2];
+  int32_t it2[2];
 };
 
 // Scalars of the multi-RHS inner CG: one set per load case, plus the flag
@@ -93,7 +98,8 @@ struct mfto_handle {
   ModeCoef<double> mc64;    // mode-space element operator (kv_tile.cuh)
   ModeCoef<float> mc32;
   int kv_variant;           // 0: tiled mode-space kernel, 1: node-centric dense KE
-  int cg_engine;            // FP32 inner CG: 0 two kernels per iteration, 1 persistent
+  int cg_engine;            // FP32 inner CG: 0 two kernels per iteration, 1 persistent,
+                            // 2 two ticket-free kernels per iteration
   int persist_grid;         // CTAs of the persistent CG launch (0: unavailable)
   int persist_tiling[4];    // its column tiling: tiles in x, y, z and node layers per chunk
   int occ_kv32, occ_pcg32;  // resident CTAs per SM of the FP32 block kernels
@@ -634,6 +640,13 @@ template <typename T>
 mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalars* host_s);
 void pcg_graph_release(mfto_handle* h);
 mfto_status pcg_persist_init(mfto_handle* h);
+// ticket-free FP32 CG, engine 2 (pcg_f32.cu)
+bool cg2_active(const mfto_handle* h, int form);
+mfto_status cg2_attrs(mfto_handle* h);
+mfto_status cg2_seed(mfto_handle* h, const PcgVecs<float>& v, double rz_prev);
+mfto_status cg2_enqueue(mfto_handle* h, cudaStream_t st, const PcgVecs<float>& v,
+                        const float* p_old, float* p_new, int par, cudaEvent_t ev0,
+                        cudaEvent_t ev1);
 mfto_status pcg_persist_iterate(mfto_handle* h, const PcgVecs<float>& v, PcgScalars* host_s);
 mfto_status kv_tile_init(mfto_handle* h);
 template <typename T>

@@ -258,7 +258,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   };
   A((void**)&h->d_ke64, sizeof(double) * 576);
   A((void**)&h->d_ke32, sizeof(float) * 576);
-  A((void**)&h->d_fixed, h->n_node);
+  // padded: the column K.v reads the mask as 32-bit words
+  A((void**)&h->d_fixed, h->n_node + 16);
   A((void**)&h->d_filter_W, ne);
   A((void**)&h->d_r, nd);
   A((void**)&h->d_z, nd);
@@ -319,7 +320,8 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   }
   mfto_status s = kv_tile_init(h);
   if (s == MFTO_OK) s = pcg_persist_init(h);
-  if (s == MFTO_OK) h->cg_engine = 0;
+  if (s == MFTO_OK) s = cg2_attrs(h);
+  if (s == MFTO_OK) h->cg_engine = 2;
   if (s == MFTO_OK) s = tc_init(h);
   if (s == MFTO_OK) s = multi_init(h);
   if (s == MFTO_OK) s = upload_params(h);

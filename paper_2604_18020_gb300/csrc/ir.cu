@@ -112,6 +112,10 @@ mfto_status ir_run(mfto_handle* h, mfto_form inner, double inner_tol, const doub
     MFTO_CUDA(h, cudaMemsetAsync(h->d_e32, 0, sizeof(float) * h->n_dof, h->stream));
     s = pcg_start<float>(h, v, h->d_r32, nullptr, inner_tol, h->inner_maxit, rz_prev);
     if (s != MFTO_OK) return s;
+    if (cg2_active(h, inner)) {
+      s = cg2_seed(h, v, rz_prev);
+      if (s != MFTO_OK) return s;
+    }
     if (h->cg_engine == 1 && inner == MFTO_FORM_F32 && h->kv_variant == 0)
       s = pcg_persist_iterate(h, v, h->h_pcg32);
     else

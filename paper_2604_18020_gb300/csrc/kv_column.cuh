@@ -39,7 +39,7 @@ struct ColShape {
   static constexpr int NV = NX * NY;               // 297 staged nodes
   static constexpr int OX = CX - 1, OY = CY - 1;   // owned nodes per layer: 31 x 7
   static constexpr int NEXTRA = NV - CX * CY;      // 41 nodes staged by a second thread
-  static constexpr size_t smem_bytes = sizeof(float) * (2 * 3 * NV + 12 * CX * CY);
+  static constexpr size_t smem_bytes = sizeof(float) * (2 * 3 * NV + 2 * 12 * CX * CY);
 };
 static_assert(ColShape::CX * ColShape::CY == MFTO_BLOCK, "one column per thread");
 static_assert(ColShape::NEXTRA <= MFTO_BLOCK, "extra nodes fit one pass");
@@ -83,26 +83,73 @@ static inline int col_chunk(const Grid& g, int64_t ctas, int min_nzc) {
 struct mfto_handle;
 ColTiling col_launch_tiling(const mfto_handle* h, int per_sm, int* grid);
 
-// Loaders of one node's 3 components (already masked by the caller).
+// Loaders of one node's 3 components (already masked by the caller).  A
+// loader reads a raw value (raw) and turns it into the loaded value (val);
+// only the direction loaders need a scalar for the second step, so a kernel
+// can issue its first loads before that scalar is known (the pre-steps
+// below).
 struct ColLoadPlain {                 // v, through L1
+  using Raw = float;
+  static constexpr bool kAsync = true;  // staged by asynchronous copies (src / combine)
+  static constexpr int kSrc = 1;
   const float* v;
+  __device__ __forceinline__ const float* src(int) const { return v; }
+  __device__ __forceinline__ float combine(const float (&r)[kSrc]) const { return r[0]; }
+  __device__ __forceinline__ Raw raw(int idx) const { return v[idx]; }
+  __device__ __forceinline__ float val(Raw r) const { return r; }
   __device__ __forceinline__ float operator()(int idx) const { return v[idx]; }
 };
 
 struct ColLoadDirectionL2 {           // z + beta p, from L2 (written inside a persistent launch)
+  struct Raw { float z, p; };
+  // 4-byte asynchronous copies go through L1, which may hold lines that other
+  // CTAs of the same launch have since rewritten: staged through registers
+  static constexpr bool kAsync = false;
   const float* z;
   const float* p;
   float beta;
-  __device__ __forceinline__ float operator()(int idx) const {
-    return __ldcg(z + idx) + beta * __ldcg(p + idx);
-  }
+  __device__ __forceinline__ Raw raw(int idx) const { return {__ldcg(z + idx), __ldcg(p + idx)}; }
+  __device__ __forceinline__ float val(Raw r) const { return r.z + beta * r.p; }
+  __device__ __forceinline__ float operator()(int idx) const { return val(raw(idx)); }
 };
 
 struct ColLoadDirection {             // z + beta p, through L1 (separate launches)
+  struct Raw { float z, p; };
+  static constexpr bool kAsync = true;
+  static constexpr int kSrc = 2;
   const float* z;
   const float* p;
   float beta;
-  __device__ __forceinline__ float operator()(int idx) const { return z[idx] + beta * p[idx]; }
+  __device__ __forceinline__ const float* src(int i) const { return i == 0 ? z : p; }
+  __device__ __forceinline__ float combine(const float (&r)[kSrc]) const { return r[0] + beta * r[1]; }
+  __device__ __forceinline__ Raw raw(int idx) const { return {z[idx], p[idx]}; }
+  __device__ __forceinline__ float val(Raw r) const { return r.z + beta * r.p; }
+  __device__ __forceinline__ float operator()(int idx) const { return val(raw(idx)); }
+};
+
+// Pre-steps: run once per launch by every thread of the CTA, after the first
+// two node layers of the first tile have been requested from memory and
+// before they are used.  run() may set the loader's scalar and returns false
+// when the launch has nothing to do (uniform over the grid); the body then
+// returns at once, with `*skipped` set.
+struct ColNoPre {
+  template <typename Load>
+  __device__ __forceinline__ bool run(Load&) const { return true; }
+};
+
+// The done flag and beta of a CG iteration whose scalars a previous launch
+// left on the device (one round trip, overlapped with the first loads).
+struct ColPreFlagBeta {
+  const int32_t* done;
+  const double* beta;
+  template <typename Load>
+  __device__ __forceinline__ bool run(Load& ld) const {
+    int d = 0;
+    const float b = flag_and_scalar_f32(done, beta, &d);
+    if (d) return false;
+    ld.beta = b;
+    return true;
+  }
 };
 
 // Epilogues: what the owner of a node does with its 3 sums.  red accumulates
@@ -139,6 +186,40 @@ struct ColNode {
   float v[3];
   uint8_t fm;
 };
+
+// One node's raw loads and mask (in: inside the node grid).
+template <typename Raw>
+struct ColNodeRaw {
+  Raw v[3];
+  uint8_t fm;
+  bool in;
+};
+
+template <typename Load>
+__device__ __forceinline__ ColNodeRaw<typename Load::Raw> col_fetch_raw(
+    const Load& ld, const uint8_t* __restrict__ fixed, const Grid& g, int gi, int gj, int gk) {
+  ColNodeRaw<typename Load::Raw> n;
+  n.fm = 0;
+  n.in = gi >= 0 && gj >= 0 && gk >= 0 && gi < g.nx && gj < g.ny && gk < g.nz;
+  if (n.in) {
+    const int node = gi + g.nx * (gj + g.ny * gk);
+    n.fm = fixed[node];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n.v[c] = ld.raw(3 * node + c);
+  }
+  return n;
+}
+
+template <typename Load>
+__device__ __forceinline__ ColNode col_finish(const Load& ld,
+                                              const ColNodeRaw<typename Load::Raw>& r) {
+  ColNode n{{0.f, 0.f, 0.f}, r.fm};
+  if (r.in) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n.v[c] = ((r.fm >> c) & 1) ? 0.f : ld.val(r.v[c]);
+  }
+  return n;
+}
 
 template <typename Load>
 __device__ __forceinline__ ColNode col_fetch(const Load& ld, const uint8_t* __restrict__ fixed,
@@ -230,19 +311,28 @@ __device__ __forceinline__ void face_inverse(const float (&M)[3][4], float (&S)[
     S[c][3] = a2 + a3;
   }
 }
-
 // Tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of `tl`.  Returns this
 // thread's double-float share of the epilogue reduction (sum over the block
 // with DotAcc-style finishing by the caller).
-template <typename Load, typename Epi>
-__device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
-                                                 const uint8_t* __restrict__ fixed,
-                                                 const ModeCoef<float>& K, const Grid& g,
-                                                 const ColTiling& tl, const Load& ld,
-                                                 const Epi& epi, float* smem) {
+//
+// One barrier per element layer.  Iteration ez (element layer ez, between
+// node layers ez and ez + 1) stages node layer ez + 1, crosses the barrier,
+// finishes node layer ez - 1 (the owners sum the corner sums that iteration
+// ez - 1 wrote), then computes element ez and writes the corner sums of node
+// layer ez.  Node layers and corner sums are double-buffered by layer
+// parity; a buffer is rewritten only after the barrier that follows its last
+// read.  Node layer ke - 1 is finished after the loop, behind one more
+// barrier.
+template <typename Load, typename Epi, typename Pre>
+__device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ E,
+                                                      const uint8_t* __restrict__ fixed,
+                                                      const ModeCoef<float>& K, const Grid& g,
+                                                      const ColTiling& tl, Load ld,
+                                                      const Epi& epi, float* smem,
+                                                      const Pre& pre, bool* skipped) {
   using S = ColShape;
   float* nodes = smem;                          // [2][3][NV], slot of node layer k: k & 1
-  float* sums = smem + 2 * 3 * S::NV;           // [12][256] corner sums of each column
+  float* sums = smem + 2 * 3 * S::NV;           // [2][12][256] corner sums, slot k & 1
   const int tid = threadIdx.x;
   const int ex = tid % S::CX, ey = tid / S::CX;
   // second staged node of threads < NEXTRA: the top row (y = CY), then the
@@ -252,14 +342,18 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
   const int xy = tid < S::CX ? S::CY : tid - S::CX;
   const bool owner = ex >= 1 && ey >= 1;
   DFloat red{0.f, 0.f};
+  *skipped = false;
   const int ntiles = tl.count();
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  bool first = true;
+  for (int t = blockIdx.x; t < ntiles || first; t += gridDim.x) {
+    const bool live = t < ntiles;   // false only for the pre-step of a CTA without tiles
     const int bx = t % tl.tx, by = (t / tl.tx) % tl.ty, bz = t / (tl.tx * tl.ty);
     const int x0 = bx * S::OX - 1, y0 = by * S::OY - 1;   // node / element origin of column 0
     const int kb = bz * tl.nzc;
     const int ke = min(kb + tl.nzc, g.nz);                // owned node layers [kb, ke)
     const int gi = x0 + ex, gj = y0 + ey;                  // this column's element (and node)
     const int hi = x0 + xx, hj = y0 + xy;                  // the extra node
+    const bool own_node = owner && gi < g.nx && gj < g.ny;
     auto stage = [&](int k, const ColNode& own, const ColNode& extra) {
       float* L = nodes + (k & 1) * 3 * S::NV;
 #pragma unroll
@@ -269,14 +363,32 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
         for (int c = 0; c < 3; ++c) L[c * S::NV + xy * S::NX + xx] = extra.v[c];
       }
     };
-    // prologue: node layer kb - 1 (face modes of the first element's lower face)
-    ColNode own = col_fetch(ld, fixed, g, gi, gj, kb - 1);
-    ColNode extra{{0.f, 0.f, 0.f}, 0};
-    if (has_extra) extra = col_fetch(ld, fixed, g, hi, hj, kb - 1);
+    // prologue: node layers kb - 1 and kb requested together (raw), then the
+    // pre-step, then layer kb - 1 staged
+    ColNodeRaw<typename Load::Raw> r0{}, r0x{}, r1{}, r1x{};
+    float Ecur = 0.f;
+    if (live) {
+      r0 = col_fetch_raw(ld, fixed, g, gi, gj, kb - 1);
+      r1 = col_fetch_raw(ld, fixed, g, gi, gj, kb);
+      if (has_extra) {
+        r0x = col_fetch_raw(ld, fixed, g, hi, hj, kb - 1);
+        r1x = col_fetch_raw(ld, fixed, g, hi, hj, kb);
+      }
+      Ecur = col_modulus(E, g, gi, gj, kb - 1);
+    }
+    if (first) {
+      first = false;
+      if (!pre.run(ld)) {
+        *skipped = true;
+        return red;
+      }
+    }
+    if (!live) break;
+    ColNode own = col_finish(ld, r0), extra{{0.f, 0.f, 0.f}, 0};
+    if (has_extra) extra = col_finish(ld, r0x);
     stage(kb - 1, own, extra);
-    own = col_fetch(ld, fixed, g, gi, gj, kb);
-    if (has_extra) extra = col_fetch(ld, fixed, g, hi, hj, kb);
-    float Ecur = col_modulus(E, g, gi, gj, kb - 1);
+    own = col_finish(ld, r1);
+    if (has_extra) extra = col_finish(ld, r1x);
     __syncthreads();
     // face modes and upper-face outputs ping-pong between two register sets
     // (the z loop is unrolled by two, so nothing is copied between layers)
@@ -286,15 +398,36 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int f = 0; f < 4; ++f) U0[c][f] = 0.f;
-    ColNode mine = own;          // this thread's node of layer ez + 1 (pn and mask of the owner)
+    ColNode mine = own;          // this column's node of layer ez + 1 (after staging)
+    ColNode mine_cur = own;      // of layer ez
+    ColNode mine_prev = own;     // of layer ez - 1 (finished in iteration ez)
+    // owner's sum of node layer k from the corner sums in slot k & 1:
+    // columns (ex-1, ey-1), (ex, ey-1), (ex-1, ey), (ex, ey) contribute their
+    // corners 3, 2, 1, 0
+    auto finish = [&](int k, const ColNode& nv) {
+      if (own_node) {
+        const float* Sm = sums + (k & 1) * 12 * MFTO_BLOCK;
+        float acc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float sacc = Sm[(4 * c + 3) * MFTO_BLOCK + tid - S::CX - 1];
+          sacc += Sm[(4 * c + 2) * MFTO_BLOCK + tid - S::CX];
+          sacc += Sm[(4 * c + 1) * MFTO_BLOCK + tid - 1];
+          sacc += Sm[(4 * c + 0) * MFTO_BLOCK + tid];
+          acc[c] = sacc;
+        }
+        epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, nv.fm, red);
+      }
+    };
     // one element layer: Flo = face modes of node layer ez (in), Fup = those of
     // ez + 1 (out), upp = upper-face outputs of element ez - 1 (in), up = those
     // of element ez (out)
     auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
                      const float (&upp)[3][4], float (&up)[3][4]) {
-      // 1. stage node layer ez + 1; fetch layer ez + 2 and the next modulus
+      // stage node layer ez + 1; fetch layer ez + 2 and the next modulus
       stage(ez + 1, own, extra);
-      const ColNode mine_cur = mine;   // node layer ez of this column (owned node values)
+      mine_prev = mine_cur;
+      mine_cur = mine;
       mine = own;
       const float Ee = Ecur;
       if (ez + 1 < ke) {
@@ -303,46 +436,304 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
         Ecur = col_modulus(E, g, gi, gj, ez + 1);
       }
       __syncthreads();
-      // 2, 3. upper face modes, element operator
+      // node layer ez - 1 (its corner sums were written in iteration ez - 1)
+      if (ez - 1 >= kb) finish(ez - 1, mine_prev);
+      // upper face modes, element operator
       float lo[3][4];
       face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, ey * S::NX + ex, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
       if (ez >= kb) {
-        // 4. node layer ez: upper face of element ez - 1 plus lower face of ez
+        // node layer ez: upper face of element ez - 1 plus lower face of ez
         float Ms[3][4], Sc[3][4];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int f = 0; f < 4; ++f) Ms[c][f] = upp[c][f] + lo[c][f];
         face_inverse(Ms, Sc);
+        float* Sm = sums + (ez & 1) * 12 * MFTO_BLOCK;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int a = 0; a < 4; ++a) sums[(4 * c + a) * MFTO_BLOCK + tid] = Sc[c][a];
-        __syncthreads();
-        // 5. owned node (x0 + ex, y0 + ey, ez): columns (ex-1, ey-1), (ex, ey-1),
-        //    (ex-1, ey), (ex, ey) contribute their corners 3, 2, 1, 0
-        if (owner && gi < g.nx && gj < g.ny) {
-          float acc[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float sacc = sums[(4 * c + 3) * MFTO_BLOCK + tid - S::CX - 1];
-            sacc += sums[(4 * c + 2) * MFTO_BLOCK + tid - S::CX];
-            sacc += sums[(4 * c + 1) * MFTO_BLOCK + tid - 1];
-            sacc += sums[(4 * c + 0) * MFTO_BLOCK + tid];
-            acc[c] = sacc;
-          }
-          epi(gi + g.nx * (gj + g.ny * ez), acc, mine_cur.v, mine_cur.fm, red);
-        }
+          for (int a = 0; a < 4; ++a) Sm[(4 * c + a) * MFTO_BLOCK + tid] = Sc[c][a];
       }
     };
     for (int ez = kb - 1; ez < ke; ez += 2) {
       layer(ez, F0, F1, U0, U1);
       if (ez + 1 < ke) layer(ez + 1, F1, F0, U1, U0);
     }
-    __syncthreads();   // the shared layers are restaged by the next tile
+    // the last owned node layer; the barrier also ends every read of this
+    // tile's node layers before the next tile stages its own
+    __syncthreads();
+    finish(ke - 1, mine_cur);
   }
   return red;
+}
+
+// Asynchronous 4-byte copy global -> shared (zero-filled when !valid: no
+// bytes are read) and its group operations.
+__device__ __forceinline__ void col_cp4(void* sdst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void col_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void col_cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Node layers prefetched ahead of the one being staged by the asynchronous
+// body; its ring holds kColPrefetch + 1 layers.
+constexpr int kColPrefetch = 2;
+constexpr int kColRing = kColPrefetch + 1;
+
+// Shared memory of the asynchronous body beyond ColShape::smem_bytes: per
+// ring slot, kSrc x 3 source values and the mask word of each staged node,
+// and the modulus of each column's element.
+template <int KSRC>
+constexpr size_t col_ring_bytes() {
+  return sizeof(float) * kColRing * ((3 * KSRC + 1) * ColShape::NV + MFTO_BLOCK);
+}
+
+// The column body with its node layers staged by asynchronous copies
+// kColPrefetch layers ahead into a ring in shared memory (each thread copies
+// and later reads only its own entries, so the ring needs no barrier: the
+// copies' wait_group makes them visible to the thread).  Per node the ring
+// holds the loader's source values, the 32-bit word of the mask array that
+// contains the node's mask byte (the mask array must be readable up to the
+// next multiple of 4 bytes) and, per column, the modulus of the element below
+// the node layer.  Out-of-grid entries are zero-filled.  Schedule, barrier
+// use and arithmetic are those of kv_column_body_regs.
+template <typename Load, typename Epi, typename Pre>
+__device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__ E,
+                                                       const uint8_t* __restrict__ fixed,
+                                                       const ModeCoef<float>& K, const Grid& g,
+                                                       const ColTiling& tl, Load ld,
+                                                       const Epi& epi, float* smem,
+                                                       const Pre& pre, bool* skipped) {
+  using S = ColShape;
+  constexpr int NS = 3 * Load::kSrc + 1;        // ring rows per node: sources, mask word
+  float* nodes = smem;                          // [2][3][NV], slot of node layer k: k & 1
+  float* sums = smem + 2 * 3 * S::NV;           // [2][12][256] corner sums, slot k & 1
+  float* ring = sums + 2 * 12 * MFTO_BLOCK;     // [kColRing][NS][NV]
+  float* ering = ring + kColRing * NS * S::NV;  // [kColRing][256]
+  const int tid = threadIdx.x;
+  const int ex = tid % S::CX, ey = tid / S::CX;
+  const bool has_extra = tid < S::NEXTRA;
+  const int xx = tid < S::CX ? tid : S::CX;
+  const int xy = tid < S::CX ? S::CY : tid - S::CX;
+  const int own_slot = ey * S::NX + ex, extra_slot = xy * S::NX + xx;
+  const bool owner = ex >= 1 && ey >= 1;
+  const uint32_t* fixed_words = reinterpret_cast<const uint32_t*>(fixed);
+  DFloat red{0.f, 0.f};
+  *skipped = false;
+  const int ntiles = tl.count();
+  // this thread's place in tile t
+  struct Ctx {
+    int kb, ke, gi, gj, hi, hj;
+  };
+  auto ctx_of = [&](int t) {
+    const int bx = t % tl.tx, by = (t / tl.tx) % tl.ty, bz = t / (tl.tx * tl.ty);
+    const int x0 = bx * S::OX - 1, y0 = by * S::OY - 1;   // node / element origin of column 0
+    Ctx c;
+    c.kb = bz * tl.nzc;
+    c.ke = min(c.kb + tl.nzc, g.nz);                      // owned node layers [kb, ke)
+    c.gi = x0 + ex;                                       // this column's element (and node)
+    c.gj = y0 + ey;
+    c.hi = x0 + xx;                                       // the extra node
+    c.hj = y0 + xy;
+    return c;
+  };
+  auto slot_of = [](int L) { return (L + 1) % kColRing; };   // L >= -1
+  // copies of node layer L (and the modulus of element layer L - 1) into
+  // the ring; layers past ke copy nothing but still commit a group
+  auto issue = [&](const Ctx& c, int L) {
+    const bool lay = L >= 0 && L <= c.ke && L < g.nz;
+    float* R = ring + slot_of(L) * NS * S::NV;
+    {
+      const bool in = lay && c.gi >= 0 && c.gj >= 0 && c.gi < g.nx && c.gj < g.ny;
+      const int node = in ? c.gi + g.nx * (c.gj + g.ny * L) : 0;
+#pragma unroll
+      for (int sidx = 0; sidx < Load::kSrc; ++sidx)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          col_cp4(R + (3 * sidx + k) * S::NV + own_slot, ld.src(sidx) + 3 * node + k, in);
+      col_cp4(R + 3 * Load::kSrc * S::NV + own_slot, fixed_words + (node >> 2), in);
+    }
+    if (has_extra) {
+      const bool in = lay && c.hi >= 0 && c.hj >= 0 && c.hi < g.nx && c.hj < g.ny;
+      const int node = in ? c.hi + g.nx * (c.hj + g.ny * L) : 0;
+#pragma unroll
+      for (int sidx = 0; sidx < Load::kSrc; ++sidx)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          col_cp4(R + (3 * sidx + k) * S::NV + extra_slot, ld.src(sidx) + 3 * node + k, in);
+      col_cp4(R + 3 * Load::kSrc * S::NV + extra_slot, fixed_words + (node >> 2), in);
+    }
+    {
+      const int el = L - 1;
+      const bool in = c.gi >= 0 && c.gj >= 0 && c.gi < g.nelx && c.gj < g.nely &&
+                      el >= c.kb - 1 && el >= 0 && el < g.nelz && L <= c.ke;
+      const int e = in ? c.gi + g.nelx * (c.gj + g.nely * el) : 0;
+      col_cp4(ering + slot_of(L) * MFTO_BLOCK + tid, E + e, in);
+    }
+    col_cp_commit();
+  };
+  // a staged node from the ring: masked loaded values and its mask
+  auto take = [&](int L, int sl, int ni, int nj) {
+    const float* R = ring + slot_of(L) * NS * S::NV;
+    ColNode n;
+    const uint32_t w = __float_as_uint(R[3 * Load::kSrc * S::NV + sl]);
+    const int node = ni + g.nx * (nj + g.ny * L);   // only its low 2 bits are used
+    n.fm = (uint8_t)(w >> (8 * (node & 3)));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float r[Load::kSrc];
+#pragma unroll
+      for (int sidx = 0; sidx < Load::kSrc; ++sidx) r[sidx] = R[(3 * sidx + k) * S::NV + sl];
+      n.v[k] = ((n.fm >> k) & 1) ? 0.f : ld.combine(r);
+    }
+    return n;
+  };
+  // first tile's prologue copies, then the pre-step while they are in flight
+  int t = blockIdx.x;
+  if (t < ntiles) {
+    const Ctx c = ctx_of(t);
+#pragma unroll
+    for (int j = 0; j <= kColPrefetch; ++j) issue(c, c.kb - 1 + j);
+  }
+  if (!pre.run(ld)) {
+    col_cp_wait<0>();
+    *skipped = true;
+    return red;
+  }
+  for (; t < ntiles; t += gridDim.x) {
+    const Ctx c = ctx_of(t);
+    if (t != (int)blockIdx.x) {
+#pragma unroll
+      for (int j = 0; j <= kColPrefetch; ++j) issue(c, c.kb - 1 + j);
+    }
+    const int kb = c.kb, ke = c.ke, gi = c.gi, gj = c.gj;
+    const bool own_node = owner && gi < g.nx && gj < g.ny;
+    auto stage = [&](int L) {
+      float* Lb = nodes + (L & 1) * 3 * S::NV;
+      const ColNode own = take(L, own_slot, gi, gj);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Lb[k * S::NV + own_slot] = own.v[k];
+      if (has_extra) {
+        const ColNode extra = take(L, extra_slot, c.hi, c.hj);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Lb[k * S::NV + extra_slot] = extra.v[k];
+      }
+      return own;
+    };
+    col_cp_wait<kColPrefetch>();
+    ColNode mine = stage(kb - 1);
+    __syncthreads();
+    float F0[3][4], F1[3][4], U0[3][4], U1[3][4];
+    face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, own_slot, F0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) U0[k][f] = 0.f;
+    ColNode mine_cur = mine, mine_prev = mine;
+    // owner's sum of node layer k from the corner sums in slot k & 1:
+    // columns (ex-1, ey-1), (ex, ey-1), (ex-1, ey), (ex, ey) contribute their
+    // corners 3, 2, 1, 0
+    auto finish = [&](int k, const ColNode& nv) {
+      if (own_node) {
+        const float* Sm = sums + (k & 1) * 12 * MFTO_BLOCK;
+        float acc[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          float sacc = Sm[(4 * q + 3) * MFTO_BLOCK + tid - S::CX - 1];
+          sacc += Sm[(4 * q + 2) * MFTO_BLOCK + tid - S::CX];
+          sacc += Sm[(4 * q + 1) * MFTO_BLOCK + tid - 1];
+          sacc += Sm[(4 * q + 0) * MFTO_BLOCK + tid];
+          acc[q] = sacc;
+        }
+        epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, nv.fm, red);
+      }
+    };
+    auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
+                     const float (&upp)[3][4], float (&up)[3][4]) {
+      // node layer ez + 1 has landed: stage it, then request layer
+      // ez + 1 + kColPrefetch into the ring slot layer ez used
+      col_cp_wait<kColPrefetch - 1>();
+      mine_prev = mine_cur;
+      mine_cur = mine;
+      mine = stage(ez + 1);
+      const float Ee = ering[slot_of(ez + 1) * MFTO_BLOCK + tid];
+      issue(c, ez + 1 + kColPrefetch);
+      __syncthreads();
+      // node layer ez - 1 (its corner sums were written in iteration ez - 1)
+      if (ez - 1 >= kb) finish(ez - 1, mine_prev);
+      float lo[3][4];
+      face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, own_slot, Fup);
+      col_element(Flo, Fup, Ee, K, lo, up);
+      if (ez >= kb) {
+        // node layer ez: upper face of element ez - 1 plus lower face of ez
+        float Ms[3][4], Sc[3][4];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) Ms[k][f] = upp[k][f] + lo[k][f];
+        face_inverse(Ms, Sc);
+        float* Sm = sums + (ez & 1) * 12 * MFTO_BLOCK;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int a = 0; a < 4; ++a) Sm[(4 * k + a) * MFTO_BLOCK + tid] = Sc[k][a];
+      }
+    };
+    for (int ez = kb - 1; ez < ke; ez += 2) {
+      layer(ez, F0, F1, U0, U1);
+      if (ez + 1 < ke) layer(ez + 1, F1, F0, U1, U0);
+    }
+    // the last owned node layer; the barrier also ends every read of this
+    // tile's node layers before the next tile stages its own
+    __syncthreads();
+    finish(ke - 1, mine_cur);
+  }
+  col_cp_wait<0>();   // the trailing (empty or unused) groups
+  return red;
+}
+
+template <typename Load, typename Epi, typename Pre>
+__device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
+                                                 const uint8_t* __restrict__ fixed,
+                                                 const ModeCoef<float>& K, const Grid& g,
+                                                 const ColTiling& tl, const Load& ld,
+                                                 const Epi& epi, float* smem, const Pre& pre,
+                                                 bool* skipped) {
+  if constexpr (Load::kAsync)
+    return kv_column_body_async(E, fixed, K, g, tl, ld, epi, smem, pre, skipped);
+  else
+    return kv_column_body_regs(E, fixed, K, g, tl, ld, epi, smem, pre, skipped);
+}
+
+template <typename Load, typename Epi>
+__device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
+                                                 const uint8_t* __restrict__ fixed,
+                                                 const ModeCoef<float>& K, const Grid& g,
+                                                 const ColTiling& tl, const Load& ld,
+                                                 const Epi& epi, float* smem) {
+  bool skipped;
+  return kv_column_body(E, fixed, K, g, tl, ld, epi, smem, ColNoPre{}, &skipped);
+}
+
+// Dynamic shared memory of every column-kernel launch whose loader is staged
+// asynchronously (at most two source arrays).
+constexpr size_t kColSmem = ColShape::smem_bytes + col_ring_bytes<2>();
+
+// Dynamic shared memory of a column-kernel launch with loader Load.
+template <typename Load>
+constexpr size_t col_smem_bytes() {
+  if constexpr (Load::kAsync)
+    return ColShape::smem_bytes + col_ring_bytes<Load::kSrc>();
+  else
+    return ColShape::smem_bytes;
 }
 
 // Warp sum of double-float shares; lane 0 returns the warp's total in FP64,

@@ -79,9 +79,14 @@ kv_col_kernel(const float* __restrict__ E, const float* __restrict__ v, float* _
 // to another buffer.  The masked loads give 0 on fixed DOFs, where A is the
 // identity and b is 0, so both stay 0 there.
 struct ColLoadScaled {
+  using Raw = float;
+  static constexpr bool kAsync = true;
+  static constexpr int kSrc = 2;
   const float* b;
   const float* dinv;
   float omega;
+  __device__ __forceinline__ const float* src(int i) const { return i == 0 ? b : dinv; }
+  __device__ __forceinline__ float combine(const float (&r)[kSrc]) const { return omega * r[1] * r[0]; }
   __device__ __forceinline__ float operator()(int idx) const { return omega * dinv[idx] * b[idx]; }
 };
 
@@ -229,14 +234,14 @@ pcg_kv_col_kernel(const float* __restrict__ E, const float* __restrict__ z,
                   const float* __restrict__ p_old, float* __restrict__ p_new,
                   float* __restrict__ q, const uint8_t* __restrict__ fixed, ModeCoef<float> K,
                   Grid g, ColTiling tl, PcgScalars* s, double* partials) {
-  int done = 0;
-  const float beta = flag_and_scalar_f32(&s->done, &s->beta, &done);
-  if (done) return;   // uniform over the grid
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[64];
   DotAcc<float> acc;
-  acc.s = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{z, p_old, beta}, ColPcg{p_new, q},
-                         reinterpret_cast<float*>(smem_raw));
+  bool skipped = false;   // the solve is done: uniform over the grid
+  acc.s = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{z, p_old, 0.f}, ColPcg{p_new, q},
+                         reinterpret_cast<float*>(smem_raw), ColPreFlagBeta{&s->done, &s->beta},
+                         &skipped);
+  if (skipped) return;
   const DFloat w[1] = {acc.finish_df()};
   double tot[1];
   if (last_block_reduce_df<1>(w, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
@@ -314,7 +319,7 @@ mfto_status kv_tile_init(mfto_handle* h) {
   mfto_status s = set_attrs<double>(h);
   if (s == MFTO_OK) s = set_attrs<float>(h);
   if (s != MFTO_OK) return s;
-  const int csm = (int)ColShape::smem_bytes;
+  const int csm = (int)kColSmem;
   MFTO_CUDA(h, cudaFuncSetAttribute(kv_col_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(kv_col_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(gmg_sweep_col_kernel<2, 0>,
@@ -375,7 +380,7 @@ mfto_status gmg_sweep_col_launch(mfto_handle* h, bool first, const float* E, con
   const int kind = h->col_kind;
   const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
   const Grid g = make_grid(h->mesh);
-  const size_t sm = ColShape::smem_bytes;
+  const size_t sm = kColSmem;
   h->launches++;
   if (kind == 1) {
     if (first)
@@ -408,7 +413,7 @@ mfto_status gmg_cheb_col_launch(mfto_handle* h, int mode, const float* E, const 
   const int kind = h->col_kind;
   const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
   const Grid g = make_grid(h->mesh);
-  const size_t sm = ColShape::smem_bytes;
+  const size_t sm = kColSmem;
   h->launches++;
 #define MFTO_CHEB_COL(MINB, MODE)                                                               \
   gmg_cheb_col_kernel<MINB, MODE><<<grid, MFTO_BLOCK, sm, h->stream>>>(                         \
@@ -436,7 +441,7 @@ mfto_status kv_tile_launch(mfto_handle* h, const T* E, const T* v, T* y, cudaStr
     const Grid g = make_grid(h->mesh);
     const float *Ef = (const float*)E, *vf = (const float*)v;
     float* yf = (float*)y;
-    const size_t sm = ColShape::smem_bytes;
+    const size_t sm = kColSmem;
     if (kind == 1)
       kv_col_kernel<3><<<grid, MFTO_BLOCK, sm, st>>>(Ef, vf, yf, h->d_fixed, h->mc32, g, tl);
     else
@@ -463,7 +468,7 @@ mfto_status pcg_kv_tile_launch(mfto_handle* h, const T* E, const T* z, const T* 
     const Grid g = make_grid(h->mesh);
     const float *Ef = (const float*)E, *zf = (const float*)z, *pf = (const float*)p_old;
     float *pn = (float*)p_new, *qf = (float*)q;
-    const size_t sm = ColShape::smem_bytes;
+    const size_t sm = kColSmem;
     if (kind == 1)
       pcg_kv_col_kernel<3><<<grid, MFTO_BLOCK, sm, st>>>(Ef, zf, pf, pn, qf, h->d_fixed, h->mc32,
                                                          g, tl, s, partials);

@@ -258,15 +258,15 @@ pcg_kv_multi_col(const float* __restrict__ E, const float* __restrict__ Z,
                  const uint8_t* __restrict__ fixed, ModeCoef<float> K, Grid g, ColTiling tl,
                  int n_dof, MultiScalars* s, double* partials) {
   const int r = blockIdx.y;
-  int done = 0;
-  const float beta = flag_and_scalar_f32(&s->done[r], &s->beta[r], &done);
-  if (done) return;   // uniform over the case's blocks
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[64];
   const size_t o = (size_t)r * n_dof;
   DotAcc<float> acc;
-  acc.s = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{Z + o, P0 + o, beta},
-                         ColPcg{P1 + o, Q + o}, reinterpret_cast<float*>(smem_raw));
+  bool skipped = false;   // the case is done: uniform over the case's blocks
+  acc.s = kv_column_body(E, fixed, K, g, tl, ColLoadDirection{Z + o, P0 + o, 0.f},
+                         ColPcg{P1 + o, Q + o}, reinterpret_cast<float*>(smem_raw),
+                         ColPreFlagBeta{&s->done[r], &s->beta[r]}, &skipped);
+  if (skipped) return;
   const DFloat w[1] = {acc.finish_df()};
   double tot[1];
   if (row_reduce_df<1>(w, partials + (size_t)2 * r * MFTO_RED_SLOTS, &s->ticket_kv[r], tot, sh) &&
@@ -465,9 +465,9 @@ mfto_status multi_init(mfto_handle* h) {
   for (int i = 0; i < 3; ++i)
     if (h->occ_multi[i] < 1) h->occ_multi[i] = 1;
   MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_multi_col<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)ColShape::smem_bytes));
+                                    (int)kColSmem));
   MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_multi_col<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)ColShape::smem_bytes));
+                                    (int)kColSmem));
   return MFTO_OK;
 }
 
@@ -523,11 +523,11 @@ static mfto_status multi_chunk(mfto_handle* h, cudaStream_t st, int chunk, int n
     if (h->kv_variant == 0) {
       const dim3 gk((unsigned)grid, (unsigned)nrhs);
       if (h->col_kind == 1)
-        pcg_kv_multi_col<3><<<gk, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+        pcg_kv_multi_col<3><<<gk, MFTO_BLOCK, kColSmem, st>>>(
             h->d_E32, h->m_z32, p_old, p_new, h->m_q32, h->d_fixed, h->mc32, g, tl,
             (int)h->n_dof, h->m_pcg, h->d_partials);
       else
-        pcg_kv_multi_col<2><<<gk, MFTO_BLOCK, ColShape::smem_bytes, st>>>(
+        pcg_kv_multi_col<2><<<gk, MFTO_BLOCK, kColSmem, st>>>(
             h->d_E32, h->m_z32, p_old, p_new, h->m_q32, h->d_fixed, h->mc32, g, tl,
             (int)h->n_dof, h->m_pcg, h->d_partials);
       pcg_update_multi_col<<<dim3((unsigned)nb_up, (unsigned)nrhs), MFTO_BLOCK, 0, st>>>(

@@ -28,6 +28,7 @@ struct PcgGraph {
   bool timed = false;
   int variant = 0;
   int form = 0;
+  int engine = 0;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> ev;  // 2 per K.v launch when timed
 };
@@ -221,6 +222,13 @@ mfto_status enqueue_chunk(mfto_handle* h, cudaStream_t st, const PcgVecs<T>& v, 
   for (int it = 0; it < chunk; ++it) {
     T* p_old = (it & 1) ? v.p1 : v.p0;
     T* p_new = (it & 1) ? v.p0 : v.p1;
+    if (sizeof(T) == 4 && cg2_active(h, v.form)) {
+      mfto_status s = cg2_enqueue(h, st, reinterpret_cast<const PcgVecs<float>&>(v),
+                                  (const float*)p_old, (float*)p_new, it & 1,
+                                  ev ? ev[2 * it] : nullptr, ev ? ev[2 * it + 1] : nullptr);
+      if (s != MFTO_OK) return s;
+      continue;
+    }
     // external record nodes: a plain record inside a capture would only add a
     // dependency edge, not record the event on each graph launch
     if (ev) MFTO_CUDA(h, cudaEventRecordWithFlags(ev[2 * it], st, cudaEventRecordExternal));
@@ -256,7 +264,8 @@ mfto_status get_graph(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgGraph** 
   const int chunk = h->p.check_every;
   PcgGraph* pg = h->pcg_graph[slot];
   if (pg && pg->key[0] == v.E && pg->key[1] == v.u && pg->key[2] == v.s && pg->chunk == chunk &&
-      pg->timed == h->kv_timing && pg->variant == h->kv_variant && pg->form == v.form) {
+      pg->timed == h->kv_timing && pg->variant == h->kv_variant && pg->form == v.form &&
+      pg->engine == h->cg_engine) {
     *out = pg;
     return MFTO_OK;
   }
@@ -270,6 +279,7 @@ mfto_status get_graph(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgGraph** 
   pg->timed = h->kv_timing;
   pg->variant = h->kv_variant;
   pg->form = v.form;
+  pg->engine = h->cg_engine;
   if (pg->timed) {
     pg->ev.resize(2 * chunk);
     for (auto& e : pg->ev) cudaEventCreate(&e);

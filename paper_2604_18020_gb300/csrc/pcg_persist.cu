@@ -250,7 +250,7 @@ mfto_status pcg_persist_iterate(mfto_handle* h, const PcgVecs<float>& v, PcgScal
 
 extern "C" mfto_status mfto_set_cg_engine(mfto_handle* h, int32_t engine) {
   if (!h) return MFTO_INVALID_ARG;
-  MFTO_REQUIRE(h, engine == 0 || engine == 1, "mfto_set_cg_engine: engine must be 0 or 1");
+  MFTO_REQUIRE(h, engine >= 0 && engine <= 2, "mfto_set_cg_engine: engine must be 0, 1 or 2");
   if (engine == 1 && h->persist_grid < 1)
     return mfto_fail(h, MFTO_UNSUPPORTED, "mfto_set_cg_engine: cooperative launch unavailable");
   if (h->cg_engine != engine) pcg_graph_release(h);   // captured chunks hold the engine's kernels

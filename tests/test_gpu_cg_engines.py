@@ -1,6 +1,7 @@
 """The FP32 inner CG engines -- two kernels per iteration from a CUDA graph
-(0), one persistent cooperative kernel per solve (1) -- against each other
-and the FP64 oracle.
+(0), one persistent cooperative kernel per solve (1), two ticket-free
+kernels per iteration from a CUDA graph (2) -- against each other and the
+FP64 oracle.
 
 The engines evaluate Hestenes-Stiefel CG with the same per-entry arithmetic;
 they differ in the order in which block partials are added, so the FP32
@@ -49,7 +50,7 @@ def test_engines_match_oracle(cuda, dims, case):
         for mode in (mfto.IR_RESTART, mfto.IR_CONTINUE):
             h.set_ir_mode(mode)
             tol = 1e-2 if mode == mfto.IR_RESTART else 1e-1
-            for engine in (0, 1):
+            for engine in (0, 1, 2):
                 res[(mode, engine)] = _solve(h, tE, tf, cuda, engine, inner_tol=tol)
     c_ref = P.f @ u_ref
     for (mode, engine), (st, u) in res.items():
@@ -72,14 +73,14 @@ def test_engines_first_inner_solve_agree(cuda):
     f = torch.tensor(P.f, device=cuda)
     out = []
     with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
-        for engine in (0, 1):
+        for engine in (0, 1, 2):
             h.set_cg_engine(engine)
             h.set_solver(mfto.FORM_F32, 1e-2, inner_maxit=50, max_outer=1)
             u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
             st = h.ir_solve(E, f, u)
             out.append((st, u.cpu().numpy()))
     s0, u0 = out[0]
-    for (st, u), bar in zip(out[1:], (1e-4,)):
+    for (st, u), bar in zip(out[1:], (1e-4, 1e-4)):
         assert st.inner_iterations == s0.inner_iterations == 50
         assert st.status == s0.status == mfto.NOT_CONVERGED
         rel = np.abs(u - u0).max() / np.abs(u0).max()
@@ -87,7 +88,7 @@ def test_engines_first_inner_solve_agree(cuda):
         assert abs(st.rel_residual - s0.rel_residual) <= bar * s0.rel_residual
 
 
-@pytest.mark.parametrize("engine", [1])
+@pytest.mark.parametrize("engine", [1, 2])
 def test_engine_zero_load(cuda, engine):
     """f = 0: the inner solve is never entered; u = 0 and status OK."""
     import torch

@@ -63,7 +63,14 @@ def test_benchmarked_simp_steps_match_oracle(cuda):
             # compliance: sum of element energies = f.u = the reported value
             c_ref, dc_phys = osimp.compliance_sens(KE, edof, ug, rp, 3.0)
             assert abs(c_ref - P.f @ ug) <= 1e-7 * abs(c_ref), step
-            assert abs(st.compliance - c_ref) <= 1e-12 * abs(c_ref), step
+            # the element energies u_e^T KE u_e cancel (the displacement is
+            # mostly rigid motion of each element), so the two FP64
+            # evaluations agree to the forward-error bound of a 24 x 24
+            # quadratic form, n eps |u_e|^T |KE| |u_e| with n = 64 >= 48 terms
+            ue = np.abs(ug[edof])
+            bound = 64 * np.finfo(float).eps * float(
+                np.sum(E * np.einsum("ei,ij,ej->e", ue, np.abs(KE), ue)))
+            assert abs(st.compliance - c_ref) <= bound, (step, st.compliance - c_ref, bound)
             # sensitivities through the filter transpose, then OC
             dc = cone.filter_T(dc_phys, m.nelx, m.nely, m.nelz, P.rmin)
             rho_ref, info = osimp.oc_update(rho_in, dc, P.volfrac, 0.2)
