@@ -193,14 +193,112 @@ def cpu_sample(workload: str, steps: int, maxit: int):
     return {"times": times, "kv": kvs, "n_elem": P.mesh.n_elem}
 
 
-def run_cpu_sample(workload, steps, maxit):
-    """The oracle in a fresh process (spawned, no CUDA), one BLAS thread."""
+# All-cores timing of the oracle's K.v: node slabs along z, one per worker
+# process (spawned, no CUDA); each worker applies the oracle's element loop to
+# the elements touching its slab and writes only its own nodes' rows, so the
+# slabs need no reduction (race-free node ownership).
+_MP = {}
+
+
+def _mp_init(workload, v_name, y_name):
+    import numpy as np
+    from multiprocessing import shared_memory
+    from oracle import fem
+    from paper_2604_18020_gb300 import workloads as W
+    P = W.WORKLOADS[workload]()
+    m = P.mesh
+    sv = shared_memory.SharedMemory(name=v_name)
+    sy = shared_memory.SharedMemory(name=y_name)
+    _MP.update(m=m, KE=fem.ke_exact(1.0, 0.3), edof=fem.edof_table_fast(m.nelx, m.nely, m.nelz),
+               fd=fem.dof_mask(P.fixed),
+               E=fem.simp_modulus(W.rho_random(m, seed=1), 3.0),
+               v=np.ndarray((m.n_dof,), dtype=np.float64, buffer=sv.buf),
+               y=np.ndarray((m.n_dof,), dtype=np.float64, buffer=sy.buf), shm=(sv, sy))
+
+
+def _mp_slab(k_range):
+    import numpy as np
+    from oracle import fem
+    k0, k1 = k_range
+    m, edof, fd, v, y = _MP["m"], _MP["edof"], _MP["fd"], _MP["v"], _MP["y"]
+    per_layer = m.nelx * m.nely
+    kl, kh = max(k0 - 1, 0), min(k1, m.nelz)           # element layers touching the slab
+    e0, e1 = kl * per_layer, kh * per_layer
+    dpl = 3 * (m.nelx + 1) * (m.nely + 1)              # DOFs per node layer
+    b0, b1 = kl * dpl, (kh + 1) * dpl                  # the DOFs those elements reach
+    pv = np.where(fd[b0:b1], 0.0, v[b0:b1])
+    w = fem.kv_unmasked(_MP["KE"], _MP["E"][e0:e1], edof[e0:e1] - b0, pv)
+    d0, d1 = k0 * dpl, k1 * dpl
+    y[d0:d1] = np.where(fd[d0:d1], v[d0:d1], w[d0 - b0:d1 - b0])
+    return k1 - k0
+
+
+def cpu_allcores_kv(workload: str, reps: int = 10):
+    """The oracle's K.v on all host cores (one worker process per core, node
+    slabs), checked against the single-process oracle; Gelem/s."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import numpy as np
+    from oracle import fem
+    from paper_2604_18020_gb300 import workloads as W
+    P = W.WORKLOADS[workload]()
+    m = P.mesh
+    ncore = os.cpu_count() or 1
+    sv = shared_memory.SharedMemory(create=True, size=8 * m.n_dof)
+    sy = shared_memory.SharedMemory(create=True, size=8 * m.n_dof)
+    try:
+        v = np.ndarray((m.n_dof,), dtype=np.float64, buffer=sv.buf)
+        y = np.ndarray((m.n_dof,), dtype=np.float64, buffer=sy.buf)
+        v[:] = W.vec_random(m.n_dof, seed=1)
+        nz = m.nelz + 1
+        bounds = np.linspace(0, nz, min(ncore, nz) + 1).astype(int)
+        slabs = [(int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(len(slabs), initializer=_mp_init, initargs=(workload, sv.name, sy.name)) as pool:
+            pool.map(_mp_slab, slabs)                      # warm-up
+            t = time.perf_counter()
+            for _ in range(reps):
+                pool.map(_mp_slab, slabs)
+            dt = (time.perf_counter() - t) / reps
+        ref = fem.kv(fem.ke_exact(1.0, 0.3), fem.simp_modulus(W.rho_random(m, seed=1), 3.0),
+                     fem.edof_table_fast(m.nelx, m.nely, m.nelz), np.array(v),
+                     fem.dof_mask(P.fixed))
+        err = float(np.abs(y - ref).max() / np.abs(ref).max())
+        if err > 1e-13:
+            raise RuntimeError(f"all-cores oracle K.v differs from the oracle by {err:.2e}")
+        return {"value": m.n_elem / dt / 1e9, "unit": "Gelem/s", "cores": len(slabs),
+                "kv_s": dt, "max_rel_diff_vs_single": err}
+    finally:
+        sv.close(); sv.unlink()
+        sy.close(); sy.unlink()
+
+
+def cpu_simp_cfg0(n_iter: int = 20):
+    """Uncapped SIMP iterations of the 24 x 12 x 12 cantilever by the oracle
+    (PCG to rtol 1e-8), single-threaded; wall time per SIMP iteration."""
+    from oracle import simp
+    from paper_2604_18020_gb300 import workloads as W
+    P = W.WORKLOADS["cantilever_24x12x12"]()
+    m = P.mesh
+    t = time.perf_counter()
+    _, _, hist = simp.simp(m.nelx, m.nely, m.nelz, P.f, P.fixed, P.volfrac, P.rmin, n_iter)
+    dt = time.perf_counter() - t
+    return {"workload": "cantilever_24x12x12", "iterations": n_iter, "wall_s": dt,
+            "s_per_iteration": dt / n_iter, "cg_iterations": int(sum(hist.cg_iterations)),
+            "final_compliance": hist.compliance[-1], "threads": 1}
+
+
+def run_cpu_sample(workload, steps, maxit, extra=False):
+    """The oracle in a fresh process (spawned, no CUDA), one BLAS thread per
+    process; extra: also the all-cores K.v and the uncapped 24 x 12 x 12 SIMP
+    iterations."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     out = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--cpu-sample", workload,
-                          "--steps", str(steps), "--maxit", str(maxit)],
+                          "--steps", str(steps), "--maxit", str(maxit)]
+                         + (["--cpu-extra"] if extra else []),
                          capture_output=True, text=True, env=env, cwd=str(ROOT))
     if out.returncode != 0:
         raise RuntimeError(f"CPU oracle sample failed:\n{out.stderr[-2000:]}")
@@ -236,12 +334,19 @@ def cpu_baseline_entry(res, maxit):
     tot_t = sum(res["times"])
     tot_kv = sum(res["kv"])
     n_cores, model = host_cpu()
-    return {"value": res["n_elem"] * tot_kv / tot_t / 1e9, "unit": "Gelem/s", "cores": 1,
-            "host_cores": n_cores, "cpu_model": model,
-            "kind": "oracle",
-            "sample": f"{len(res['times'])} SIMP iteration(s) of {WORKLOAD} by the FP64 numpy "
-                      f"oracle from the uniform start, PCG capped at {maxit} iterations "
-                      f"({tot_kv} K.v applications, {tot_t:.1f} s, 1 BLAS thread)"}
+    out = {"value": res["n_elem"] * tot_kv / tot_t / 1e9, "unit": "Gelem/s", "cores": 1,
+           "host_cores": n_cores, "cpu_model": model,
+           "kind": "oracle",
+           "sample": f"{len(res['times'])} SIMP iteration(s) of {WORKLOAD} by the FP64 numpy "
+                     f"oracle from the uniform start, PCG capped at {maxit} iterations "
+                     f"({tot_kv} K.v applications, {tot_t:.1f} s, 1 BLAS thread)"}
+    if "all_cores" in res:
+        out["all_cores_kv"] = dict(res["all_cores"], sample=(
+            f"the oracle's K.v on {WORKLOAD}, one spawned process per core over node slabs "
+            f"along z (race-free: each process writes its own nodes), 10 applications"))
+    if "simp_cfg0" in res:
+        out["simp_cfg0_uncapped"] = res["simp_cfg0"]
+    return out
 
 
 # ------------------------------------------------------------- GPU leg
@@ -1248,11 +1353,16 @@ def main():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the FP32 CG K.v timing on the 256x128x150 cantilever")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-extra", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--maxit", type=int, default=40, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
     if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.cpu_sample, args.steps, args.maxit)))
+        res = cpu_sample(args.cpu_sample, args.steps, args.maxit)
+        if args.cpu_extra:
+            res["all_cores"] = cpu_allcores_kv(args.cpu_sample)
+            res["simp_cfg0"] = cpu_simp_cfg0()
+        print(json.dumps(res))
         return
 
     if args.mode == "compare":
@@ -1316,7 +1426,7 @@ def main():
     out = gpu_bench(args, rank, local_rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:
-            res = run_cpu_sample(WORKLOAD, 1, args.cpu_maxit)
+            res = run_cpu_sample(WORKLOAD, 1, args.cpu_maxit, extra=True)
             out["cpu_baseline"] = cpu_baseline_entry(res, args.cpu_maxit)
         print(json.dumps(out))
 

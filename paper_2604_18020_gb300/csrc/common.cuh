@@ -118,6 +118,7 @@ struct mfto_handle {
   double* d_filter_W;       // row sums W_e
   // PCG workspace (FP64)
   double *d_r, *d_z, *d_p0, *d_p1, *d_q, *d_dinv;
+  double* d_oc;             // [3][n_elem] OC bisection scratch (simp.cu)
   double* d_partials;       // [MFTO_RED_ROWS * MFTO_RED_SLOTS]
   double* d_partials2;      // [MFTO_RED_ROWS * MFTO_RED_SLOTS]
   PcgScalars* d_pcg;

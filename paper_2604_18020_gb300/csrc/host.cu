@@ -134,7 +134,7 @@ static void free_handle(mfto_handle* h) {
                   h->d_E, h->d_dc, h->d_dc_phys, h->d_r32, h->d_z32, h->d_p0_32,
                   h->d_p1_32, h->d_q32, h->d_dinv32, h->d_e32, h->d_E32, h->d_pcg32,
                   h->d_btc, h->m_q64, h->m_r32, h->m_z32, h->m_p0, h->m_p1, h->m_q32,
-                  h->m_e32, h->m_pcg, h->m_out, h->d_bar, h->d_rho_bar, h->d_rho_in};
+                  h->m_e32, h->m_pcg, h->m_out, h->d_bar, h->d_rho_bar, h->d_rho_in, h->d_oc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -277,6 +277,7 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
   A((void**)&h->d_dc_phys, ne);
   A((void**)&h->d_rho_bar, ne);
   A((void**)&h->d_rho_in, ne);
+  A((void**)&h->d_oc, 3 * ne);        // OC bisection: a_e and the move-limit bounds
   const size_t nd32 = sizeof(float) * h->n_dof;
   A((void**)&h->d_r32, nd32);
   A((void**)&h->d_z32, nd32);

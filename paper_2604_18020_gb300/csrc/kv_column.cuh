@@ -495,6 +495,8 @@ template <int KSRC>
 constexpr size_t col_ring_bytes() {
   return sizeof(float) * kColRing * ((3 * KSRC + 1) * ColShape::NV + MFTO_BLOCK);
 }
+// Node layers and upper-row sums of the asynchronous body, both double-buffered.
+constexpr size_t kColAsyncBase = sizeof(float) * (2 * 3 * ColShape::NV + 2 * 3 * MFTO_BLOCK);
 
 // The column body with its node layers staged by asynchronous copies
 // kColPrefetch layers ahead into a ring in shared memory (each thread copies
@@ -515,8 +517,8 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
   using S = ColShape;
   constexpr int NS = 3 * Load::kSrc + 1;        // ring rows per node: sources, mask word
   float* nodes = smem;                          // [2][3][NV], slot of node layer k: k & 1
-  float* sums = smem + 2 * 3 * S::NV;           // [2][12][256] corner sums, slot k & 1
-  float* ring = sums + 2 * 12 * MFTO_BLOCK;     // [kColRing][NS][NV]
+  float* sums = smem + 2 * 3 * S::NV;           // [2][3][256] upper-row sums, slot k & 1
+  float* ring = sums + 2 * 3 * MFTO_BLOCK;      // [kColRing][NS][NV]
   float* ering = ring + kColRing * NS * S::NV;  // [kColRing][256]
   const int tid = threadIdx.x;
   const int ex = tid % S::CX, ey = tid / S::CX;
@@ -638,26 +640,25 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
 #pragma unroll
       for (int f = 0; f < 4; ++f) U0[k][f] = 0.f;
     ColNode mine_cur = mine, mine_prev = mine;
-    // owner's sum of node layer k from the corner sums in slot k & 1:
-    // columns (ex-1, ey-1), (ex, ey-1), (ex-1, ey), (ex, ey) contribute their
-    // corners 3, 2, 1, 0
-    auto finish = [&](int k, const ColNode& nv) {
+    // owner's sum of node layer k: the upper-row sums B of column row ey - 1
+    // (slot k & 1) plus this row's lower-row sums A (registers)
+    auto finish = [&](int k, const ColNode& nv, const float (&A)[3]) {
       if (own_node) {
-        const float* Sm = sums + (k & 1) * 12 * MFTO_BLOCK;
+        const float* Sm = sums + (k & 1) * 3 * MFTO_BLOCK;
         float acc[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          float sacc = Sm[(4 * q + 3) * MFTO_BLOCK + tid - S::CX - 1];
-          sacc += Sm[(4 * q + 2) * MFTO_BLOCK + tid - S::CX];
-          sacc += Sm[(4 * q + 1) * MFTO_BLOCK + tid - 1];
-          sacc += Sm[(4 * q + 0) * MFTO_BLOCK + tid];
-          acc[q] = sacc;
-        }
+        for (int q = 0; q < 3; ++q) acc[q] = Sm[q * MFTO_BLOCK + tid - S::CX] + A[q];
         epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, nv.fm, red);
       }
     };
+    // Corner sums of node layer ez: corners 0 (x0, y0) and 2 (x0, y1) of this
+    // column plus corners 1 and 3 of the column to the left (the lane to the
+    // left: a warp is one row of 32 columns) give A, this row's share of node
+    // (ex, ey), and B, its share of node (ex, ey + 1); B goes to shared
+    // memory for the row above.
     auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
-                     const float (&upp)[3][4], float (&up)[3][4]) {
+                     const float (&upp)[3][4], float (&up)[3][4], const float (&Aprev)[3],
+                     float (&Acur)[3]) {
       // node layer ez + 1 has landed: stage it, then request layer
       // ez + 1 + kColPrefetch into the ring slot layer ez used
       col_cp_wait<kColPrefetch - 1>();
@@ -668,7 +669,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       issue(c, ez + 1 + kColPrefetch);
       __syncthreads();
       // node layer ez - 1 (its corner sums were written in iteration ez - 1)
-      if (ez - 1 >= kb) finish(ez - 1, mine_prev);
+      if (ez - 1 >= kb) finish(ez - 1, mine_prev, Aprev);
       float lo[3][4];
       face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, own_slot, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
@@ -680,21 +681,26 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
 #pragma unroll
           for (int f = 0; f < 4; ++f) Ms[k][f] = upp[k][f] + lo[k][f];
         face_inverse(Ms, Sc);
-        float* Sm = sums + (ez & 1) * 12 * MFTO_BLOCK;
+        float* Sm = sums + (ez & 1) * 3 * MFTO_BLOCK;
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int a = 0; a < 4; ++a) Sm[(4 * k + a) * MFTO_BLOCK + tid] = Sc[k][a];
+        for (int k = 0; k < 3; ++k) {
+          const float l1 = __shfl_up_sync(0xffffffffu, Sc[k][1], 1);
+          const float l3 = __shfl_up_sync(0xffffffffu, Sc[k][3], 1);
+          Acur[k] = Sc[k][0] + l1;
+          Sm[k * MFTO_BLOCK + tid] = Sc[k][2] + l3;
+        }
       }
     };
+    float A0[3] = {0.f, 0.f, 0.f}, A1[3] = {0.f, 0.f, 0.f};
     for (int ez = kb - 1; ez < ke; ez += 2) {
-      layer(ez, F0, F1, U0, U1);
-      if (ez + 1 < ke) layer(ez + 1, F1, F0, U1, U0);
+      layer(ez, F0, F1, U0, U1, A1, A0);
+      if (ez + 1 < ke) layer(ez + 1, F1, F0, U1, U0, A0, A1);
     }
-    // the last owned node layer; the barrier also ends every read of this
-    // tile's node layers before the next tile stages its own
+    // the last owned node layer (layer ez's A is in A0 when ez - kb is odd,
+    // else in A1); the barrier also ends every read of this tile's node
+    // layers before the next tile stages its own
     __syncthreads();
-    finish(ke - 1, mine_cur);
+    finish(ke - 1, mine_cur, ((ke - kb) & 1) ? A1 : A0);
   }
   col_cp_wait<0>();   // the trailing (empty or unused) groups
   return red;
@@ -725,13 +731,13 @@ __device__ __forceinline__ DFloat kv_column_body(const float* __restrict__ E,
 
 // Dynamic shared memory of every column-kernel launch whose loader is staged
 // asynchronously (at most two source arrays).
-constexpr size_t kColSmem = ColShape::smem_bytes + col_ring_bytes<2>();
+constexpr size_t kColSmem = kColAsyncBase + col_ring_bytes<2>();
 
 // Dynamic shared memory of a column-kernel launch with loader Load.
 template <typename Load>
 constexpr size_t col_smem_bytes() {
   if constexpr (Load::kAsync)
-    return ColShape::smem_bytes + col_ring_bytes<Load::kSrc>();
+    return kColAsyncBase + col_ring_bytes<Load::kSrc>();
   else
     return ColShape::smem_bytes;
 }

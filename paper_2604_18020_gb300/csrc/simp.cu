@@ -49,18 +49,31 @@ compliance_kernel(const double* __restrict__ rho, const double* __restrict__ u,
   }
 }
 
-// OC with bisection on lambda.  One cooperative grid; each bisection step
-// sums the candidate field, crosses a bounded grid barrier and lets every
-// block reduce the per-block partials in the same order, so every block takes
-// the same branch.  Partials are double-buffered by step parity.
+// OC with bisection on lambda.  One cooperative grid.  A first pass stores
+// per element a_e = rho_e sqrt(max(0, -dc_e) n) and the move-limit bounds,
+// so that the candidate of a midpoint lambda is a_e / sqrt(lambda) (the
+// same value as rho_e sqrt(max(0, -dc_e) / (lambda / n)) up to rounding):
+// each bisection step is then one FP64 multiply and a clamp per element.
+// Each step sums the candidate field, crosses a bounded grid barrier and lets
+// every block reduce the per-block partials in the same order, so every block
+// takes the same branch.  Partials are double-buffered by step parity.  The
+// candidate of the last midpoint is written by a final pass.
 __global__ void __launch_bounds__(MFTO_BLOCK)
 oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
-          double* __restrict__ rho_new, int n, double volfrac, double move,
-          MiscScalars* s, double* partials) {
+          double* __restrict__ rho_new, double* __restrict__ a_s, double* __restrict__ lo_s,
+          double* __restrict__ hi_s, int n, double volfrac, double move, MiscScalars* s,
+          double* partials) {
   __shared__ double sh[64];
-  const double dv = 1.0 / (double)n;
   const double target = volfrac * (double)n;
-  double l1 = 0.0, l2 = 1e9, total = 0.0;
+  const int first = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = first; e < n; e += stride) {
+    const double r = rho[e];
+    a_s[e] = r * sqrt(fmax(0.0, -dc[e]) * (double)n);
+    lo_s[e] = fmax(0.0, r - move);
+    hi_s[e] = fmin(1.0, r + move);
+  }
+  double l1 = 0.0, l2 = 1e9, total = 0.0, last = -1.0;
   int step = 0;
   // Stops at the relative bracket width 1e-10, or when the midpoint no
   // longer lies strictly inside the bracket (lambda underflow when the target
@@ -68,16 +81,9 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
   while (l1 + l2 > 0.0 && (l2 - l1) / (l1 + l2) > 1e-10 && step < 4096) {
     const double lmid = 0.5 * (l1 + l2);
     if (!(l1 < lmid && lmid < l2)) break;   // uniform: every block holds the same l1, l2
+    const double sc = 1.0 / sqrt(lmid);
     double acc = 0.0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-      const double r = rho[e];
-      const double neg = fmax(0.0, -dc[e]);
-      const double cand = r * sqrt(neg / (lmid * dv));
-      const double lo = fmax(0.0, r - move), hi = fmin(1.0, r + move);
-      const double rn = fmax(lo, fmin(hi, cand));
-      rho_new[e] = rn;
-      acc += rn;
-    }
+    for (int e = first; e < n; e += stride) acc += fmax(lo_s[e], fmin(hi_s[e], a_s[e] * sc));
     double* buf = partials + (step & 1) * MFTO_RED_SLOTS;
     const double bs = block_sum(acc, sh);
     if (threadIdx.x == 0) buf[blockIdx.x] = bs;
@@ -88,14 +94,21 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
     if (threadIdx.x == 0) sh[40] = t;
     __syncthreads();
     total = sh[40];
+    last = lmid;
     if (total > target) l1 = lmid; else l2 = lmid;
     ++step;
     if (*(volatile int32_t*)&s->error) break;
   }
+  // the candidate of the last midpoint (rho itself if no step ran), and
   // change = max |rho_new - rho|
+  const double sc = last > 0.0 ? 1.0 / sqrt(last) : 0.0;
   double mx = 0.0;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-    mx = fmax(mx, fabs(rho_new[e] - rho[e]));
+  for (int e = first; e < n; e += stride) {
+    const double r = rho[e];
+    const double rn = last > 0.0 ? fmax(lo_s[e], fmin(hi_s[e], a_s[e] * sc)) : r;
+    rho_new[e] = rn;
+    mx = fmax(mx, fabs(rn - r));
+  }
   double* buf = partials + 2 * MFTO_RED_SLOTS;
   const double bm = block_max(mx, sh);
   if (threadIdx.x == 0) buf[blockIdx.x] = bm;
@@ -147,7 +160,11 @@ mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc, doubl
   double volfrac = h->p.volfrac, move = h->p.move;
   MiscScalars* s = h->d_misc;
   double* partials = h->d_partials2;
-  void* args[] = {(void*)&rho, (void*)&dc, (void*)&rho_new, &n, &volfrac, &move, &s, &partials};
+  double* a_s = h->d_oc;
+  double* lo_s = h->d_oc + h->n_elem;
+  double* hi_s = h->d_oc + 2 * h->n_elem;
+  void* args[] = {(void*)&rho, (void*)&dc, (void*)&rho_new, &a_s, &lo_s, &hi_s, &n, &volfrac,
+                  &move, &s, &partials};
   h->launches++;
   MFTO_CUDA(h, cudaLaunchCooperativeKernel((const void*)oc_kernel, dim3(blocks), dim3(MFTO_BLOCK),
                                            args, 0, h->stream));
