@@ -40,7 +40,7 @@ struct PcgScalars {
   double rtol2ff;   // rtol^2 * f.f
   int32_t it, maxit, done, status;
   unsigned int ticket_a, ticket_b, ticket_c;
-  int32_t tc_error;         // a tensor-core completion wait gave up
+  int32_t tc_error;         // a tensor-core or bulk-copy completion wait gave up
   int32_t bar_error;        // a grid-barrier wait of the persistent CG gave up
   // ticket-free FP32 CG (pcg_f32.cu): r.z, its reciprocal and the
   // completed-iteration count of iteration k in slot k & 1

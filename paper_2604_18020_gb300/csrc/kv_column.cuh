@@ -12,24 +12,28 @@
 // Per element layer ez a thread
 //   1. stages its own node of layer ez+1 (threads 0..40 also the tile's
 //      last node row / column) into a double-buffered shared layer, with the
-//      fixed DOFs zeroed; the global loads of layer ez+2 are issued at once
-//      and land in registers while the layer is computed;
-//   2. reads the 4 upper corners of its element and forms their face modes
+//      fixed DOFs zeroed.  The node layers come from a ring in shared memory
+//      filled by asynchronous copies two layers ahead (kv_column_body_async;
+//      loaders that must read L2 directly stage one layer ahead through
+//      registers instead, kv_column_body_regs);
+//   2. after the layer's one barrier, finishes node layer ez-1 (below);
+//   3. reads the 4 upper corners of its element and forms their face modes
 //      (x and y stages of the butterfly); the face modes of the lower corners
 //      are those of the previous layer, kept in registers, so each node
 //      layer's face transform is computed once per column, not twice;
-//   3. completes the z stage, applies the unit mode operator, and undoes the z
+//   4. completes the z stage, applies the unit mode operator, and undoes the z
 //      stage with the modulus folded in: lower = E (s - d), upper = E (s + d);
-//   4. adds its lower-face output to the upper-face output of the element
+//   5. adds its lower-face output to the upper-face output of the element
 //      below (still in mode space), undoes the y and x stages once per node
 //      layer, and publishes the 4 corner sums of the column (12 values);
-//   5. if it owns node (ex, ey) of layer ez, sums the 4 columns around the
-//      node in a fixed order and hands the result to the epilogue.
+//   6. one layer later (step 2), the owner of node (ex, ey) sums the 4
+//      columns around the node in a fixed order and hands the result to the
+//      epilogue.
 // The element operator costs 48 (forward) + 48 (mode operator) + 36 (inverse
 // z with E) + 12 (face sum) + 24 (inverse y, x) = 168 FP32 operations per
 // element, against 1152 for the dense 24 x 24 product; every output is
 // written once, by one thread, in a fixed order, so results are
-// bit-reproducible.
+// bit-reproducible and independent of the launch shape.
 #pragma once
 #include "common.cuh"
 
@@ -409,12 +413,12 @@ __device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ 
         const float* Sm = sums + (k & 1) * 12 * MFTO_BLOCK;
         float acc[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float sacc = Sm[(4 * c + 3) * MFTO_BLOCK + tid - S::CX - 1];
-          sacc += Sm[(4 * c + 2) * MFTO_BLOCK + tid - S::CX];
-          sacc += Sm[(4 * c + 1) * MFTO_BLOCK + tid - 1];
-          sacc += Sm[(4 * c + 0) * MFTO_BLOCK + tid];
-          acc[c] = sacc;
+        for (int q = 0; q < 3; ++q) {
+          float sacc = Sm[(4 * q + 3) * MFTO_BLOCK + tid - S::CX - 1];
+          sacc += Sm[(4 * q + 2) * MFTO_BLOCK + tid - S::CX];
+          sacc += Sm[(4 * q + 1) * MFTO_BLOCK + tid - 1];
+          sacc += Sm[(4 * q + 0) * MFTO_BLOCK + tid];
+          acc[q] = sacc;
         }
         epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, nv.fm, red);
       }
@@ -495,8 +499,8 @@ template <int KSRC>
 constexpr size_t col_ring_bytes() {
   return sizeof(float) * kColRing * ((3 * KSRC + 1) * ColShape::NV + MFTO_BLOCK);
 }
-// Node layers and upper-row sums of the asynchronous body, both double-buffered.
-constexpr size_t kColAsyncBase = sizeof(float) * (2 * 3 * ColShape::NV + 2 * 3 * MFTO_BLOCK);
+// Node layers and corner sums of the asynchronous body, both double-buffered.
+constexpr size_t kColAsyncBase = sizeof(float) * (2 * 3 * ColShape::NV + 2 * 12 * MFTO_BLOCK);
 
 // The column body with its node layers staged by asynchronous copies
 // kColPrefetch layers ahead into a ring in shared memory (each thread copies
@@ -517,8 +521,8 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
   using S = ColShape;
   constexpr int NS = 3 * Load::kSrc + 1;        // ring rows per node: sources, mask word
   float* nodes = smem;                          // [2][3][NV], slot of node layer k: k & 1
-  float* sums = smem + 2 * 3 * S::NV;           // [2][3][256] upper-row sums, slot k & 1
-  float* ring = sums + 2 * 3 * MFTO_BLOCK;      // [kColRing][NS][NV]
+  float* sums = smem + 2 * 3 * S::NV;           // [2][12][256] corner sums, slot k & 1
+  float* ring = sums + 2 * 12 * MFTO_BLOCK;     // [kColRing][NS][NV]
   float* ering = ring + kColRing * NS * S::NV;  // [kColRing][256]
   const int tid = threadIdx.x;
   const int ex = tid % S::CX, ey = tid / S::CX;
@@ -640,25 +644,26 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
 #pragma unroll
       for (int f = 0; f < 4; ++f) U0[k][f] = 0.f;
     ColNode mine_cur = mine, mine_prev = mine;
-    // owner's sum of node layer k: the upper-row sums B of column row ey - 1
-    // (slot k & 1) plus this row's lower-row sums A (registers)
-    auto finish = [&](int k, const ColNode& nv, const float (&A)[3]) {
+    // owner's sum of node layer k from the corner sums in slot k & 1:
+    // columns (ex-1, ey-1), (ex, ey-1), (ex-1, ey), (ex, ey) contribute their
+    // corners 3, 2, 1, 0
+    auto finish = [&](int k, const ColNode& nv) {
       if (own_node) {
-        const float* Sm = sums + (k & 1) * 3 * MFTO_BLOCK;
+        const float* Sm = sums + (k & 1) * 12 * MFTO_BLOCK;
         float acc[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) acc[q] = Sm[q * MFTO_BLOCK + tid - S::CX] + A[q];
+        for (int q = 0; q < 3; ++q) {
+          float sacc = Sm[(4 * q + 3) * MFTO_BLOCK + tid - S::CX - 1];
+          sacc += Sm[(4 * q + 2) * MFTO_BLOCK + tid - S::CX];
+          sacc += Sm[(4 * q + 1) * MFTO_BLOCK + tid - 1];
+          sacc += Sm[(4 * q + 0) * MFTO_BLOCK + tid];
+          acc[q] = sacc;
+        }
         epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, nv.fm, red);
       }
     };
-    // Corner sums of node layer ez: corners 0 (x0, y0) and 2 (x0, y1) of this
-    // column plus corners 1 and 3 of the column to the left (the lane to the
-    // left: a warp is one row of 32 columns) give A, this row's share of node
-    // (ex, ey), and B, its share of node (ex, ey + 1); B goes to shared
-    // memory for the row above.
     auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
-                     const float (&upp)[3][4], float (&up)[3][4], const float (&Aprev)[3],
-                     float (&Acur)[3]) {
+                     const float (&upp)[3][4], float (&up)[3][4]) {
       // node layer ez + 1 has landed: stage it, then request layer
       // ez + 1 + kColPrefetch into the ring slot layer ez used
       col_cp_wait<kColPrefetch - 1>();
@@ -669,7 +674,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       issue(c, ez + 1 + kColPrefetch);
       __syncthreads();
       // node layer ez - 1 (its corner sums were written in iteration ez - 1)
-      if (ez - 1 >= kb) finish(ez - 1, mine_prev, Aprev);
+      if (ez - 1 >= kb) finish(ez - 1, mine_prev);
       float lo[3][4];
       face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, own_slot, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
@@ -681,26 +686,21 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
 #pragma unroll
           for (int f = 0; f < 4; ++f) Ms[k][f] = upp[k][f] + lo[k][f];
         face_inverse(Ms, Sc);
-        float* Sm = sums + (ez & 1) * 3 * MFTO_BLOCK;
+        float* Sm = sums + (ez & 1) * 12 * MFTO_BLOCK;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float l1 = __shfl_up_sync(0xffffffffu, Sc[k][1], 1);
-          const float l3 = __shfl_up_sync(0xffffffffu, Sc[k][3], 1);
-          Acur[k] = Sc[k][0] + l1;
-          Sm[k * MFTO_BLOCK + tid] = Sc[k][2] + l3;
-        }
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int a = 0; a < 4; ++a) Sm[(4 * k + a) * MFTO_BLOCK + tid] = Sc[k][a];
       }
     };
-    float A0[3] = {0.f, 0.f, 0.f}, A1[3] = {0.f, 0.f, 0.f};
     for (int ez = kb - 1; ez < ke; ez += 2) {
-      layer(ez, F0, F1, U0, U1, A1, A0);
-      if (ez + 1 < ke) layer(ez + 1, F1, F0, U1, U0, A0, A1);
+      layer(ez, F0, F1, U0, U1);
+      if (ez + 1 < ke) layer(ez + 1, F1, F0, U1, U0);
     }
-    // the last owned node layer (layer ez's A is in A0 when ez - kb is odd,
-    // else in A1); the barrier also ends every read of this tile's node
-    // layers before the next tile stages its own
+    // the last owned node layer; the barrier also ends every read of this
+    // tile's node layers before the next tile stages its own
     __syncthreads();
-    finish(ke - 1, mine_cur, ((ke - kb) & 1) ? A1 : A0);
+    finish(ke - 1, mine_cur);
   }
   col_cp_wait<0>();   // the trailing (empty or unused) groups
   return red;

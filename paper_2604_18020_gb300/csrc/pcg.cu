@@ -366,7 +366,7 @@ mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalar
       it_before = progress;
     }
     if (host_s->tc_error)
-      return mfto_fail(h, MFTO_CUDA_ERROR, "tensor-core completion wait timed out");
+      return mfto_fail(h, MFTO_CUDA_ERROR, "a completion wait (tensor-core or bulk copy) timed out");
     if (host_s->done) break;
     MFTO_CUDA(h, cudaGraphLaunch(pg->exec, h->stream));
     h->launches += 2 * (int64_t)pg->chunk;
