@@ -52,13 +52,44 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 IR_MODES = {"restart": 0, "continue": 1}
 # DRAM bytes (read + write) per launch of the dominant kernels from one ncu
-# capture (profiles/kv_f32_col_cg_cantilever_120x60x30_full.md,
-# profiles/kv_f64_pcg_cantilever_256x128x150_full.md, the latter scaled from
-# 4,915,200 to 216,000 elements by the bytes it reads per element); cold
-# caches, so an upper bound for launches inside the CG, whose vectors stay in
-# L2.  To be refreshed whenever those kernels change.
-NCU_DRAM_BYTES = {("pcg_kv_col_kernel<2>", WORKLOAD): 6.62144e6,
-                  ("pcg_kv_tile_kernel<double>", WORKLOAD): (294.4e6 + 199.3e6) * 216000 / 4915200}
+# capture (profiles/kv_f32_cg2_cantilever_120x60x30_full.md,
+# profiles/kv_f32_cg2_cantilever_256x128x150_full.md,
+# profiles/kv_f64_pcg_cantilever_256x128x150_full.md, the FP64 figure scaled from
+# 4,915,200 to 216,000 elements by the bytes it reads per element), cold caches,
+# each with a digest of the kernel's source files at capture time: when the
+# sources change the figure is reported as stale (null) until it is re-taken.
+KERNEL_SOURCES = {
+    "cg2_kv_kernel": ["kv_column.cuh", "pcg_f32.cu", "modes.cuh"],
+    "pcg_kv_tile_kernel<double>": ["kv_tile.cuh", "kv_tile.cu", "modes.cuh"],
+}
+NCU_DRAM_BYTES = {
+    ("cg2_kv_kernel<2>", WORKLOAD): (6.642688e6, "bf43c09eaec4"),
+    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (145.194752e6 + 76.744192e6, "bf43c09eaec4"),
+    ("pcg_kv_tile_kernel<double>", WORKLOAD): ((294.4e6 + 199.3e6) * 216000 / 4915200,
+                                               "adcb1137b447"),
+}
+
+
+def source_digest(kernel: str) -> str:
+    import hashlib
+    base = kernel.split("<")[0] if kernel.startswith("cg2_") else kernel
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(base, []):
+        h.update((ROOT / "paper_2604_18020_gb300" / "csrc" / f).read_bytes())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """(bytes, note): the captured DRAM bytes per launch, or None when there is
+    no capture or the kernel's sources changed since it was taken."""
+    rec = NCU_DRAM_BYTES.get((kernel, workload))
+    if rec is None:
+        return None, "no ncu capture of this kernel and workload"
+    if source_digest(kernel) != rec[1]:
+        return None, "stale: the kernel's sources changed since the ncu capture"
+    return rec[0], "ncu dram__bytes_read.sum + dram__bytes_write.sum, one cold launch"
+
+
 REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
 
@@ -416,6 +447,10 @@ def large_kv_leg(dev, sm_mhz, n_sm, iters=400, workload="cantilever_256x128x150"
         h.close()
     kv_avg_s = ms * 1e-3 / max(n, 1)
     roof = cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm)
+    kname = (f"{'cg2_kv_kernel' if engine == 2 else 'pcg_kv_col_kernel'}"
+             f"<{2 if tuned[1] == 0 else 3}>")
+    tb, tnote = ncu_traffic(kname, workload)
+    roof.update({"traffic": tb, "traffic_note": tnote})
     roof.update({"workload": workload, "elements": m.n_elem,
                  "kernel": (f"{'cg2_kv_kernel' if engine == 2 else 'pcg_kv_col_kernel'}"
                             f"<{2 if tuned[1] == 0 else 3}>"),
@@ -587,7 +622,8 @@ def gpu_bench(args, rank, local_rank, world):
             roof = cg_kv_roofline(m, kv_avg_s, sm_mhz, n_sm)
             roof["bytes_per_launch"] += 32 * m.n_dof
             roof["frac_hbm"] = roof["bytes_per_launch"] / (measured_hbm_gbs() * 1e9) / kv_avg_s
-        roof.update({"traffic": NCU_DRAM_BYTES.get((kname, WORKLOAD)), "kernel": kname})
+        tb, tnote = ncu_traffic(kname, WORKLOAD)
+        roof.update({"traffic": tb, "traffic_note": tnote, "kernel": kname})
         if persistent:
             roof.update({"unit_of_work": "one CG iteration (one K.v application)",
                          "launches": cgt[0], "iterations_per_launch": cgt[1] / cgt[0],
@@ -597,7 +633,7 @@ def gpu_bench(args, rank, local_rank, world):
         roof = {"bound": "alu", "achieved": FLOP_PER_ELEM * m.n_elem / kv_avg_s / 1e12,
                 "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                 "kernel": "pcg_kv_tile_kernel<double>",
-                "traffic": NCU_DRAM_BYTES.get(("pcg_kv_tile_kernel<double>", WORKLOAD)),
+                "traffic": ncu_traffic("pcg_kv_tile_kernel<double>", WORKLOAD)[0],
                 "peak_source": f"FP64 FMA pipe, {n_sm} SMs x 2 DFMA/clk x 2 flop x "
                                f"{sm_mhz:.0f} MHz median SM clock under load",
                 "flop_per_elem": FLOP_PER_ELEM}
