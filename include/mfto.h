@@ -239,9 +239,11 @@ mfto_status mfto_set_kv_variant(mfto_handle* h, int32_t variant);
  * gives up (about a second) makes the solve return MFTO_CUDA_ERROR. */
 mfto_status mfto_set_cg_engine(mfto_handle* h, int32_t engine);
 
-/* Autotune the FP32 K.v (variant 0): times the column kernel for several
- * lengths of its z-chunks (node layers per CTA tile; longer chunks recompute
- * fewer element layers, shorter ones give more CTAs) and each kernel kind
+/* Autotune the FP32 K.v (variant 0): times the column kernel for every
+ * distinct length ceil(nz / t), t = 1 .. 64, of its z-chunks (node layers per
+ * CTA tile; longer chunks recompute fewer element layers, shorter ones give
+ * more CTAs, and the chunk count sets how evenly the tiles fill the resident
+ * CTAs) and each kernel kind
  * (register allocation held to 2 (kind 0) or 3 (kind 1) resident CTAs per
  * SM) on the handle's own work vectors, and keeps the fastest pair for
  * mfto_kv and the FP32 inner CG.  All shapes give bit-identical K.v

@@ -119,6 +119,7 @@ struct mfto_handle {
   // PCG workspace (FP64)
   double *d_r, *d_z, *d_p0, *d_p1, *d_q, *d_dinv;
   double* d_oc;             // [3][n_elem] OC bisection scratch (simp.cu)
+  uint8_t* d_tile_fixed;    // column K.v xy tiles that stage a fixed node (kv_column.cuh)
   double* d_partials;       // [MFTO_RED_ROWS * MFTO_RED_SLOTS]
   double* d_partials2;      // [MFTO_RED_ROWS * MFTO_RED_SLOTS]
   PcgScalars* d_pcg;

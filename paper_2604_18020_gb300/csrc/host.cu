@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "kv_column.cuh"
 #include "modes.cuh"
 
 mfto_status mfto_fail(mfto_handle* h, mfto_status code, const char* fmt, ...) {
@@ -134,7 +135,8 @@ static void free_handle(mfto_handle* h) {
                   h->d_E, h->d_dc, h->d_dc_phys, h->d_r32, h->d_z32, h->d_p0_32,
                   h->d_p1_32, h->d_q32, h->d_dinv32, h->d_e32, h->d_E32, h->d_pcg32,
                   h->d_btc, h->m_q64, h->m_r32, h->m_z32, h->m_p0, h->m_p1, h->m_q32,
-                  h->m_e32, h->m_pcg, h->m_out, h->d_bar, h->d_rho_bar, h->d_rho_in, h->d_oc};
+                  h->m_e32, h->m_pcg, h->m_out, h->d_bar, h->d_rho_bar, h->d_rho_in, h->d_oc,
+                  h->d_tile_fixed};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -306,12 +308,40 @@ extern "C" mfto_status mfto_create(const mfto_mesh* mesh, const mfto_params* par
              cudaMallocHost(&h->h_misc, sizeof(MiscScalars)) != cudaSuccess ||
              cudaMallocHost(&h->h_pcg32, sizeof(PcgScalars)) != cudaSuccess))
     ok = false;
+  // column K.v tiles (kv_column.cuh) that stage no fixed node: any z, the
+  // tile's node range x0 .. x0 + CX, y0 .. y0 + CY with x0 = OX bx - 1,
+  // y0 = OY by - 1
+  const int ntx = (int)((h->mesh.nelx + 1 + ColShape::OX - 1) / ColShape::OX);
+  const int nty = (int)((h->mesh.nely + 1 + ColShape::OY - 1) / ColShape::OY);
+  std::vector<uint8_t> tile_fixed((size_t)ntx * nty, 0);
+  {
+    const int nx = h->mesh.nelx + 1, ny = h->mesh.nely + 1, nz = h->mesh.nelz + 1;
+    std::vector<uint8_t> colfix((size_t)nx * ny, 0);
+    for (int64_t n = 0; n < h->n_node; ++n)
+      if (h_fixed[n]) colfix[n % ((int64_t)nx * ny)] = 1;
+    (void)nz;
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (!colfix[(size_t)i + (size_t)nx * j]) continue;
+        for (int by = 0; by < nty; ++by) {
+          const int y0 = ColShape::OY * by - 1;
+          if (j < y0 || j > y0 + ColShape::CY) continue;
+          for (int bx = 0; bx < ntx; ++bx) {
+            const int x0 = ColShape::OX * bx - 1;
+            if (i >= x0 && i <= x0 + ColShape::CX) tile_fixed[(size_t)bx + (size_t)ntx * by] = 1;
+          }
+        }
+      }
+  }
+  A((void**)&h->d_tile_fixed, tile_fixed.size());
   if (!ok) {
     cudaGetLastError();
     free_handle(h);
     return MFTO_OOM;
   }
-  if (cudaMemcpyAsync(h->d_fixed, h_fixed, h->n_node, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+  if (cudaMemcpy(h->d_tile_fixed, tile_fixed.data(), tile_fixed.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h->d_fixed, h_fixed, h->n_node, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_pcg, 0, sizeof(PcgScalars), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_misc, 0, sizeof(MiscScalars), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->d_pcg32, 0, sizeof(PcgScalars), h->stream) != cudaSuccess ||

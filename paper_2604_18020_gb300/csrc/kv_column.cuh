@@ -35,6 +35,8 @@
 // written once, by one thread, in a fixed order, so results are
 // bit-reproducible and independent of the launch shape.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 struct ColShape {
@@ -52,11 +54,15 @@ static_assert(ColShape::NEXTRA <= MFTO_BLOCK, "extra nodes fit one pass");
 // [tx OX, +OX) x [ty OY, +OY) x [tz nzc, +nzc) (clipped to the grid).
 struct ColTiling {
   int tx, ty, tz, nzc;
+  // per xy tile (bx + tx by): nonzero when a node the tile stages is fixed
+  // (any z); NULL: every tile is treated as having fixed nodes
+  const uint8_t* fixed_tiles;
   __host__ __device__ int count() const { return tx * ty * tz; }
 };
 
 static inline ColTiling col_tiling(const Grid& g, int nzc) {
   ColTiling t;
+  t.fixed_tiles = nullptr;
   t.tx = (g.nx + ColShape::OX - 1) / ColShape::OX;
   t.ty = (g.ny + ColShape::OY - 1) / ColShape::OY;
   if (nzc < 1) nzc = 1;
@@ -481,6 +487,19 @@ __device__ __forceinline__ void col_cp4(void* sdst, const void* gsrc, bool valid
                "r"(valid ? 4 : 0)
                : "memory");
 }
+// the 3 consecutive floats at gsrc into 3 shared rows NV floats apart, one
+// address register each side, immediate offsets
+__device__ __forceinline__ void col_cp4x3(float* sdst, const float* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  const int n = valid ? 4 : 0;
+  asm volatile(
+      "cp.async.ca.shared.global [%0], [%1], 4, %2;\n"
+      "cp.async.ca.shared.global [%0+1188], [%1+4], 4, %2;\n"
+      "cp.async.ca.shared.global [%0+2376], [%1+8], 4, %2;\n" ::"r"(d),
+      "l"(gsrc), "r"(n)
+      : "memory");
+}
+static_assert(ColShape::NV * 4 == 1188, "row stride of col_cp4x3");
 __device__ __forceinline__ void col_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void col_cp_wait() {
@@ -552,9 +571,15 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     return c;
   };
   auto slot_of = [](int L) { return (L + 1) % kColRing; };   // L >= -1
+  // tile t has no fixed node: its mask words are neither copied nor read
+  auto clean_of = [&](int t) {
+    const int bxy = t % (tl.tx * tl.ty);
+    return tl.fixed_tiles != nullptr && tl.fixed_tiles[bxy] == 0;
+  };
   // copies of node layer L (and the modulus of element layer L - 1) into
   // the ring; layers past ke copy nothing but still commit a group
-  auto issue = [&](const Ctx& c, int L) {
+  auto issue = [&](const Ctx& c, int L, auto clean_tag) {
+    constexpr bool CLEAN = decltype(clean_tag)::value;
     const bool lay = L >= 0 && L <= c.ke && L < g.nz;
     float* R = ring + slot_of(L) * NS * S::NV;
     {
@@ -562,20 +587,17 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       const int node = in ? c.gi + g.nx * (c.gj + g.ny * L) : 0;
 #pragma unroll
       for (int sidx = 0; sidx < Load::kSrc; ++sidx)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          col_cp4(R + (3 * sidx + k) * S::NV + own_slot, ld.src(sidx) + 3 * node + k, in);
-      col_cp4(R + 3 * Load::kSrc * S::NV + own_slot, fixed_words + (node >> 2), in);
+        col_cp4x3(R + 3 * sidx * S::NV + own_slot, ld.src(sidx) + 3 * node, in);
+      if (!CLEAN) col_cp4(R + 3 * Load::kSrc * S::NV + own_slot, fixed_words + (node >> 2), in);
     }
     if (has_extra) {
       const bool in = lay && c.hi >= 0 && c.hj >= 0 && c.hi < g.nx && c.hj < g.ny;
       const int node = in ? c.hi + g.nx * (c.hj + g.ny * L) : 0;
 #pragma unroll
       for (int sidx = 0; sidx < Load::kSrc; ++sidx)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          col_cp4(R + (3 * sidx + k) * S::NV + extra_slot, ld.src(sidx) + 3 * node + k, in);
-      col_cp4(R + 3 * Load::kSrc * S::NV + extra_slot, fixed_words + (node >> 2), in);
+        col_cp4x3(R + 3 * sidx * S::NV + extra_slot, ld.src(sidx) + 3 * node, in);
+      if (!CLEAN)
+        col_cp4(R + 3 * Load::kSrc * S::NV + extra_slot, fixed_words + (node >> 2), in);
     }
     {
       const int el = L - 1;
@@ -587,48 +609,54 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     col_cp_commit();
   };
   // a staged node from the ring: masked loaded values and its mask
-  auto take = [&](int L, int sl, int ni, int nj) {
+  auto take = [&](int L, int sl, int ni, int nj, auto clean_tag) {
+    constexpr bool CLEAN = decltype(clean_tag)::value;
     const float* R = ring + slot_of(L) * NS * S::NV;
     ColNode n;
-    const uint32_t w = __float_as_uint(R[3 * Load::kSrc * S::NV + sl]);
-    const int node = ni + g.nx * (nj + g.ny * L);   // only its low 2 bits are used
-    n.fm = (uint8_t)(w >> (8 * (node & 3)));
+    n.fm = 0;
+    if (!CLEAN) {
+      const uint32_t w = __float_as_uint(R[3 * Load::kSrc * S::NV + sl]);
+      const int node = ni + g.nx * (nj + g.ny * L);   // only its low 2 bits are used
+      n.fm = (uint8_t)(w >> (8 * (node & 3)));
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       float r[Load::kSrc];
 #pragma unroll
       for (int sidx = 0; sidx < Load::kSrc; ++sidx) r[sidx] = R[(3 * sidx + k) * S::NV + sl];
-      n.v[k] = ((n.fm >> k) & 1) ? 0.f : ld.combine(r);
+      n.v[k] = (!CLEAN && ((n.fm >> k) & 1)) ? 0.f : ld.combine(r);
     }
     return n;
   };
+  auto issue_prologue = [&](const Ctx& c, bool clean) {
+#pragma unroll
+    for (int j = 0; j <= kColPrefetch; ++j) {
+      if (clean)
+        issue(c, c.kb - 1 + j, std::true_type{});
+      else
+        issue(c, c.kb - 1 + j, std::false_type{});
+    }
+  };
   // first tile's prologue copies, then the pre-step while they are in flight
   int t = blockIdx.x;
-  if (t < ntiles) {
-    const Ctx c = ctx_of(t);
-#pragma unroll
-    for (int j = 0; j <= kColPrefetch; ++j) issue(c, c.kb - 1 + j);
-  }
+  if (t < ntiles) issue_prologue(ctx_of(t), clean_of(t));
   if (!pre.run(ld)) {
     col_cp_wait<0>();
     *skipped = true;
     return red;
   }
-  for (; t < ntiles; t += gridDim.x) {
-    const Ctx c = ctx_of(t);
-    if (t != (int)blockIdx.x) {
-#pragma unroll
-      for (int j = 0; j <= kColPrefetch; ++j) issue(c, c.kb - 1 + j);
-    }
+  // one tile; CLEAN (no fixed node in the tile) compiles the mask work out
+  auto run_tile = [&](const Ctx& c, auto clean_tag) {
+    constexpr bool CLEAN = decltype(clean_tag)::value;
     const int kb = c.kb, ke = c.ke, gi = c.gi, gj = c.gj;
     const bool own_node = owner && gi < g.nx && gj < g.ny;
     auto stage = [&](int L) {
       float* Lb = nodes + (L & 1) * 3 * S::NV;
-      const ColNode own = take(L, own_slot, gi, gj);
+      const ColNode own = take(L, own_slot, gi, gj, clean_tag);
 #pragma unroll
       for (int k = 0; k < 3; ++k) Lb[k * S::NV + own_slot] = own.v[k];
       if (has_extra) {
-        const ColNode extra = take(L, extra_slot, c.hi, c.hj);
+        const ColNode extra = take(L, extra_slot, c.hi, c.hj, clean_tag);
 #pragma unroll
         for (int k = 0; k < 3; ++k) Lb[k * S::NV + extra_slot] = extra.v[k];
       }
@@ -659,7 +687,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
           sacc += Sm[(4 * q + 0) * MFTO_BLOCK + tid];
           acc[q] = sacc;
         }
-        epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, nv.fm, red);
+        epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, CLEAN ? (uint8_t)0 : nv.fm, red);
       }
     };
     auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
@@ -671,7 +699,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       mine_cur = mine;
       mine = stage(ez + 1);
       const float Ee = ering[slot_of(ez + 1) * MFTO_BLOCK + tid];
-      issue(c, ez + 1 + kColPrefetch);
+      issue(c, ez + 1 + kColPrefetch, clean_tag);
       __syncthreads();
       // node layer ez - 1 (its corner sums were written in iteration ez - 1)
       if (ez - 1 >= kb) finish(ez - 1, mine_prev);
@@ -701,6 +729,15 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     // tile's node layers before the next tile stages its own
     __syncthreads();
     finish(ke - 1, mine_cur);
+  };
+  for (; t < ntiles; t += gridDim.x) {
+    const Ctx c = ctx_of(t);
+    const bool clean = clean_of(t);
+    if (t != (int)blockIdx.x) issue_prologue(c, clean);
+    if (clean)
+      run_tile(c, std::true_type{});
+    else
+      run_tile(c, std::false_type{});
   }
   col_cp_wait<0>();   // the trailing (empty or unused) groups
   return red;

@@ -307,7 +307,8 @@ mfto_status set_attrs(mfto_handle* h) {
 ColTiling col_launch_tiling(const mfto_handle* h, int per_sm, int* grid) {
   const Grid g = make_grid(h->mesh);
   const int64_t ctas = (int64_t)per_sm * h->num_sms;
-  const ColTiling tl = col_tiling(g, h->col_nzc > 0 ? h->col_nzc : col_chunk(g, ctas, 4));
+  ColTiling tl = col_tiling(g, h->col_nzc > 0 ? h->col_nzc : col_chunk(g, ctas, 4));
+  tl.fixed_tiles = h->d_tile_fixed;
   int64_t n = tl.count();
   if (n > ctas) n = ctas;
   if (n > MFTO_RED_SLOTS) n = MFTO_RED_SLOTS;
@@ -505,7 +506,14 @@ extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_
                                         float* us_out) {
   if (!h) return MFTO_INVALID_ARG;
   const Grid g = make_grid(h->mesh);
-  const int cand[] = {2, 3, 4, 5, 6, 8, 11, 16, 24, 32};
+  // chunk lengths: every distinct ceil(nz / tz) for up to 64 chunks along z
+  // (each the shortest chunk for its chunk count, so the z tiles are as even
+  // as the count allows), from the longest chunk down
+  std::vector<int> cand;
+  for (int tz = 1; tz <= 64 && tz <= g.nz; ++tz) {
+    const int c = (g.nz + tz - 1) / tz;
+    if (cand.empty() || cand.back() != c) cand.push_back(c);
+  }
   MFTO_CUDA(h, cudaMemsetAsync(h->d_r32, 0, sizeof(float) * h->n_dof, h->stream));
   MFTO_CUDA(h, cudaMemsetAsync(h->d_E32, 0, sizeof(float) * h->n_elem, h->stream));
   cudaEvent_t a, b;
@@ -515,11 +523,7 @@ extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_
   int best = 0, best_kind = 0;
   float best_ms = 0.f;
   for (int kind = 0; kind < kColKinds; ++kind) {
-    int last = -1;
-    for (int c : cand) {
-      const int nzc = c > g.nz ? g.nz : c;
-      if (nzc == last) continue;
-      last = nzc;
+    for (int nzc : cand) {
       h->col_nzc = nzc;
       h->col_kind = kind;
       const int reps = 20;

@@ -112,32 +112,40 @@ struct ColPreCg2 {
   __device__ __forceinline__ bool run(Load& ld) const {
     __shared__ float s_beta;
     __shared__ int s_skip;
+    // the scalars go out with the partials' loads (one round trip for both)
+    int done = 0, k = 0, maxit = 0;
+    double rtol2ff = 0.0, rinv = 0.0;
+    if (threadIdx.x == 0) {
+      done = *(const volatile int32_t*)&s->done;
+      k = s->it2[par ^ 1] + 1;                      // iterations completed so far
+      maxit = s->maxit;
+      rtol2ff = s->rtol2ff;
+      rinv = s->rinv2[par ^ 1];
+    }
     double tot[2];
     sum_partials_df<2>(pb, nb, tot);
     if (threadIdx.x == 0) {
-      int done = *(const volatile int32_t*)&s->done;
       double beta = 0.0;
       if (!done) {
         const double rz = tot[0], rr = tot[1];
-        const int k = s->it2[par ^ 1] + 1;         // iterations completed so far
         int status = MFTO_OK;
         if (!isfinite(rz) || !isfinite(rr)) {
           done = 1;
           status = MFTO_BREAKDOWN;
-        } else if (rr <= s->rtol2ff) {
+        } else if (rr <= rtol2ff) {
           done = 1;
-        } else if (k >= s->maxit) {
+        } else if (k >= maxit) {
           done = 1;
           status = MFTO_NOT_CONVERGED;
         } else {
-          beta = rz * s->rinv2[par ^ 1];
+          beta = rz * rinv;
         }
         if (blockIdx.x == 0) {
           s->rz2[par] = rz;
           s->it2[par] = k;
           s->it = k;
           s->rr = rr;
-          s->beta = rz * s->rinv2[par ^ 1];
+          s->beta = rz * rinv;
           s->rz = rz;
           if (done) {
             s->status = status;
@@ -201,10 +209,17 @@ cg2_update_kernel(float* __restrict__ u, const float* __restrict__ p, const floa
     rr = r4[first];
     dd = d4[first];
   }
+  // the scalars go out with the partials' loads (one round trip for both)
+  int done = 0, it = 0;
+  double rz = 0.0;
+  if (threadIdx.x == 0) {
+    done = *(const volatile int32_t*)&s->done;
+    rz = s->rz2[par];
+    it = s->it2[par];
+  }
   double tot[1];
   sum_partials_df<1>(reinterpret_cast<const float2*>(part_a), nb_a, tot);
   if (threadIdx.x == 0) {
-    int done = *(const volatile int32_t*)&s->done;
     double alpha = 0.0;
     if (!done) {
       const double pq = tot[0];
@@ -217,12 +232,12 @@ cg2_update_kernel(float* __restrict__ u, const float* __restrict__ p, const floa
           s->done = 1;
         }
       } else {
-        alpha = s->rz2[par] / pq;
+        alpha = rz / pq;
         if (blockIdx.x == 0) {
           s->pq = pq;
           s->alpha = alpha;
-          s->it = s->it2[par] + 1;
-          s->rinv2[par] = 1.0 / s->rz2[par];   // for the next beta
+          s->it = it + 1;
+          s->rinv2[par] = 1.0 / rz;   // for the next beta
         }
       }
     }

@@ -202,6 +202,7 @@ mfto_status pcg_persist_iterate(mfto_handle* h, const PcgVecs<float>& v, PcgScal
   PcgScalars* s = v.s;
   double* part = v.part_a;
   ColTiling tl;
+  tl.fixed_tiles = nullptr;
   tl.tx = h->persist_tiling[0];
   tl.ty = h->persist_tiling[1];
   tl.tz = h->persist_tiling[2];
