@@ -726,6 +726,88 @@ def profile_run(args):
     h.close()
 
 
+def kernel_case_run(args):
+    """Short runs of one kernel family on a moderate case, for ncu captures of
+    the kernels outside the benchmark's step (--case):
+      tc      FP32-input K.v in each tensor-core form, 120 x 60 x 30;
+      multi   the 8-load-case mixed solve, 100 x 50 x 50 (inner CG capped);
+      batch   the 64 uneven instances' batched mixed solve;
+      nn      U-Net forward and gradient on the 136 x 72 x 40 node grid of a
+              128 x 64 x 32 mesh (the learned part's training size);
+      simp    one SIMP iteration (filter, compliance, OC) of 120 x 60 x 30."""
+    import numpy as np
+    import torch
+    from paper_2604_18020_gb300 import mfto, workloads as W
+    dev = torch.device("cuda:0")
+    case = args.case
+    if case == "tc":
+        P = W.WORKLOADS["cantilever_120x60x30"]()
+        m = P.mesh
+        with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
+            E = torch.tensor(W.rho_random(m, seed=1), dtype=torch.float32, device=dev) ** 3
+            v = torch.tensor(W.vec_random(m.n_dof, seed=1), dtype=torch.float32, device=dev)
+            y = torch.empty_like(v)
+            for name in ("tf32", "tf32x3", "bf16", "bf16x3", "f16", "f16x3"):
+                for _ in range(3):
+                    h.kv(E, v, y, form=mfto.FORMS[name])
+            torch.cuda.synchronize()
+    elif case == "multi":
+        P = W.WORKLOADS["cantilever_100x50x50_8rhs"]()
+        m = P.mesh
+        nr = P.f.shape[0]
+        with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed,
+                         params=mfto.default_params(max_rhs=nr)) as h:
+            h.set_solver(mfto.FORM_F32, 1e-1, 64, 1)
+            h.set_ir_mode(IR_MODES["continue"])
+            E = torch.full((m.n_elem,), 0.3 ** 3, dtype=torch.float64, device=dev)
+            F = torch.tensor(P.f.reshape(-1), device=dev)
+            U = torch.zeros(nr * m.n_dof, dtype=torch.float64, device=dev)
+            h.ir_solve_multi(E, F, U, nr, inner_tol=1e-1)
+            Y = torch.empty(nr * m.n_dof, dtype=torch.float32, device=dev)
+            h.kv_multi(E.float(), U.float(), Y, nr, form=mfto.FORM_F32)
+            torch.cuda.synchronize()
+    elif case == "batch":
+        probs = W.uneven_instances(count=64, seed=5)
+        with mfto.Batch([(q.mesh.nelx, q.mesh.nely, q.mesh.nelz) for q in probs],
+                        [q.fixed for q in probs]) as b:
+            Eb = torch.full((b.n_elem,), 0.3 ** 3, dtype=torch.float64, device=dev)
+            Fb = torch.tensor(np.concatenate([q.f for q in probs]), device=dev)
+            Ub = torch.zeros(b.n_dof, dtype=torch.float64, device=dev)
+            b.solve(Eb, Fb, Ub, inner_tol=1e-2, inner_maxit=64, max_outer=1)
+            Y = torch.empty(b.n_dof, dtype=torch.float32, device=dev)
+            b.kv(Eb.float(), Ub.float(), Y, form=mfto.FORM_F32)
+            torch.cuda.synchronize()
+    elif case == "nn":
+        dims = mfto.nn_grid(128, 64, 32)
+        V = int(np.prod(dims))
+        net = mfto.Net(base=14, levels=4, max_voxels=V, max_train_voxels=V, seed=0)
+        try:
+            g = torch.Generator(device="cpu").manual_seed(0)
+            x = torch.rand(4 * V, generator=g).to(dev)
+            t = torch.rand(3 * V, generator=g).to(dev)
+            mask = torch.ones(3 * V, device=dev)
+            out = torch.empty(3 * V, device=dev)
+            for _ in range(2):
+                net.forward(x, out, dims)
+                net.gradient(x, t, mask, dims)
+            torch.cuda.synchronize()
+        finally:
+            net.close()
+    elif case == "simp":
+        P = W.WORKLOADS["cantilever_120x60x30"]()
+        m = P.mesh
+        params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
+        with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params) as h:
+            h.set_solver(mfto.FORM_F32, 1e-1)
+            rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=dev)
+            u = torch.zeros(m.n_dof, dtype=torch.float64, device=dev)
+            f = torch.tensor(P.f, device=dev)
+            for _ in range(2):
+                h.simp_step(rho, u, f)
+            torch.cuda.synchronize()
+    print(json.dumps({"case": case, "ok": True}))
+
+
 def compare_run(args):
     """Forms side by side on the GPU, one JSON line each (plain FP64 is the
     reference; the oracle is not used here):
@@ -1354,8 +1436,10 @@ def main():
     ap.add_argument("--cpu-maxit", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench",
-                    choices=["bench", "profile", "pcg", "cgkv", "compare", "learned", "kappa",
-                             "protocol", "hard", "ubench", "gmg", "scaling"])
+                    choices=["bench", "profile", "pcg", "cgkv", "kernels", "compare", "learned",
+                             "kappa", "protocol", "hard", "ubench", "gmg", "scaling"])
+    ap.add_argument("--case", default="simp", choices=["tc", "multi", "batch", "nn", "simp"],
+                    help="--mode kernels: the kernel family to run")
     ap.add_argument("--protocol-iters", type=int, default=120)
     ap.add_argument("--protocol-solvers", default="mixed,f64",
                     help="--mode protocol: comma-separated solvers among mixed, f64, gmg")
@@ -1403,6 +1487,9 @@ def main():
 
     if args.mode == "compare":
         compare_run(args)
+        return
+    if args.mode == "kernels":
+        kernel_case_run(args)
         return
     if args.mode == "learned":
         learned_run(args)

@@ -246,10 +246,12 @@ mfto_status mfto_set_cg_engine(mfto_handle* h, int32_t engine);
  * CTAs) and each kernel kind
  * (register allocation held to 2 (kind 0) or 3 (kind 1) resident CTAs per
  * SM) on the handle's own work vectors, and keeps the fastest pair for
- * mfto_kv and the FP32 inner CG.  All shapes give bit-identical K.v
- * results.  Returns the chosen chunk length, kind and
- * time per launch in microseconds (any may be NULL).  Overwrites the
- * handle's FP32 work vectors; synchronises the stream. */
+ * mfto_kv and the FP32 inner CG.  With the graph CG engines (0, 2) the timed
+ * unit is one inner CG iteration (the CG K.v with its vector update, from the
+ * captured graph), otherwise one plain K.v.  All shapes give bit-identical K.v
+ * results.  Returns the chosen chunk length, kind and the time of the timed
+ * unit in microseconds (any may be NULL).  Overwrites the handle's FP32 work
+ * vectors; synchronises the stream.  Call it after mfto_set_cg_engine. */
 mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc, int32_t* kind, float* us);
 /* Set the FP32 column K.v's launch shape by hand: z-chunk length nzc (0:
  * automatic) and kernel kind 0 or 1 (as in mfto_kv_autotune). */

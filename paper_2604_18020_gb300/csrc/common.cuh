@@ -573,6 +573,18 @@ __device__ __forceinline__ void grid_barrier(unsigned int* count,
   __syncthreads();
 }
 
+// Release-add and acquire-load of a global counter (grid barriers that count
+// arrivals: each block adds 1 and waits until the count reaches the number
+// of arrivals expected so far).
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // ------------------------------------------------------ host-side entries
 // (defined in the .cu files, used across them)
 mfto_status kv_launch(mfto_handle* h, mfto_form form, const void* E,
@@ -641,6 +653,7 @@ mfto_status pcg_start(mfto_handle* h, const PcgVecs<T>& v, const T* rhs, const T
 template <typename T>
 mfto_status pcg_iterate(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgScalars* host_s);
 void pcg_graph_release(mfto_handle* h);
+mfto_status pcg_time_iterations(mfto_handle* h, int chunks, float* us_per_iter);
 mfto_status pcg_persist_init(mfto_handle* h);
 // ticket-free FP32 CG, engine 2 (pcg_f32.cu)
 bool cg2_active(const mfto_handle* h, int form);

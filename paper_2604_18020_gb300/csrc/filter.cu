@@ -6,7 +6,9 @@
 // boundary; W_e = sum_{i in N(e)} w_ei.  Terms are added in stencil order with
 // separate IEEE multiply and add (no fused multiply-add), so the result does
 // not depend on the compiler's contraction choices.  The weight matrix is
-// symmetric, so the transpose visits the same offsets.
+// symmetric, so the transpose visits the same offsets; it divides x by W
+// once per element in a first pass (the same quotients the sum would form
+// term by term) and then runs the forward sum on the quotients.
 #include "common.cuh"
 
 namespace {
@@ -37,14 +39,19 @@ filter_kernel(const double* __restrict__ x, double* __restrict__ y,
       double term;
       if (rowsums_only)
         term = sw[t];
-      else if (transpose)
-        term = __dmul_rn(sw[t], __ddiv_rn(x[nb], W[nb]));
       else
         term = __dmul_rn(sw[t], x[nb]);
       acc = __dadd_rn(acc, term);
     }
     y[e] = (rowsums_only || transpose) ? acc : __ddiv_rn(acc, W[e]);
   }
+}
+
+__global__ void __launch_bounds__(MFTO_BLOCK)
+divide_kernel(const double* __restrict__ x, const double* __restrict__ W, double* __restrict__ q,
+              int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    q[e] = __ddiv_rn(x[e], W[e]);
 }
 
 }  // namespace
@@ -57,8 +64,14 @@ static mfto_status launch_filter(mfto_handle* h, const double* x, double* y, int
     MFTO_CUDA(h, cudaFuncSetAttribute(filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   int blocks = (int)((h->n_elem + MFTO_BLOCK - 1) / MFTO_BLOCK);
-  h->launches++;
   if (blocks > 16 * h->num_sms) blocks = 16 * h->num_sms;
+  if (transpose) {   // quotients x / W into the OC scratch (free outside the OC update)
+    h->launches++;
+    divide_kernel<<<blocks, MFTO_BLOCK, 0, h->stream>>>(x, h->d_filter_W, h->d_oc,
+                                                        (int)h->n_elem);
+    x = h->d_oc;
+  }
+  h->launches++;
   filter_kernel<<<blocks, MFTO_BLOCK, smem, h->stream>>>(x, y, h->d_filter_W, h->d_stencil_off,
                                                          h->d_stencil_w, h->n_stencil, g,
                                                          transpose, rowsums);

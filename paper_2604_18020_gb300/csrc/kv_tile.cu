@@ -499,9 +499,10 @@ template mfto_status pcg_kv_tile_launch<float>(mfto_handle*, const float*, const
                                                const float*, float*, float*, PcgScalars*,
                                                double*, cudaStream_t);
 
-// Times the FP32 column K.v for several chunk lengths along z and every
-// kernel kind on the handle's FP32 work vectors and keeps the fastest pair
-// (mfto_kv, the CG K.v of the FP32 inner solves).
+// Times the FP32 column K.v (as one inner CG iteration with the graph CG
+// engines, as a plain K.v otherwise) for every balanced chunk length along z
+// and every kernel kind on the handle's FP32 work vectors and keeps the
+// fastest pair (mfto_kv, the CG K.v of the FP32 inner solves).
 extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_t* kind_out,
                                         float* us_out) {
   if (!h) return MFTO_INVALID_ARG;
@@ -522,10 +523,28 @@ extern "C" mfto_status mfto_kv_autotune(mfto_handle* h, int32_t* nzc_out, int32_
   const int saved_nzc = h->col_nzc, saved_kind = h->col_kind;
   int best = 0, best_kind = 0;
   float best_ms = 0.f;
+  // the graph CG engines time one inner CG iteration (the K.v launch with
+  // its vector update) per shape, the others the plain K.v
+  const bool cg = h->cg_engine != 1;
   for (int kind = 0; kind < kColKinds; ++kind) {
     for (int nzc : cand) {
       h->col_nzc = nzc;
       h->col_kind = kind;
+      if (cg) {
+        pcg_graph_release(h);
+        float us = 0.f;
+        mfto_status st = pcg_time_iterations(h, 2, &us);
+        if (st != MFTO_OK) {
+          h->col_nzc = saved_nzc;
+          h->col_kind = saved_kind;
+          pcg_graph_release(h);
+          cudaEventDestroy(a);
+          cudaEventDestroy(b);
+          return st;
+        }
+        if (best == 0 || us < best_ms * 1000.f) { best = nzc; best_kind = kind; best_ms = us / 1000.f; }
+        continue;
+      }
       const int reps = 20;
       for (int rep = 0; rep < reps + 2; ++rep) {   // 2 warm-up launches
         if (rep == 2) cudaEventRecord(a, h->stream);

@@ -318,6 +318,55 @@ mfto_status get_graph(mfto_handle* h, const PcgVecs<T>& v, int slot, PcgGraph** 
 
 }  // namespace
 
+namespace {
+__global__ void fill_f32(float* x, int n, float v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = v;
+}
+}  // namespace
+
+// Device time of one FP32 inner CG iteration as the graph engines run it
+// (the captured chunk of K.v and vector-update launches, replayed `chunks`
+// times after one untimed replay) on the handle's FP32 work vectors: unit
+// moduli, a right-hand side of ones, a tolerance no iterate reaches.
+mfto_status pcg_time_iterations(mfto_handle* h, int chunks, float* us_per_iter) {
+  const int n = (int)h->n_dof;
+  const int nb = reduction_blocks(h->n_dof, MFTO_BLOCK);
+  const bool timed = h->kv_timing;
+  h->kv_timing = false;
+  h->launches += 2;
+  fill_f32<<<nb, MFTO_BLOCK, 0, h->stream>>>(h->d_E32, (int)h->n_elem, 1.f);
+  fill_f32<<<nb, MFTO_BLOCK, 0, h->stream>>>(h->d_r32, n, 1.f);
+  MFTO_LAUNCH_CHECK(h);
+  MFTO_CUDA(h, cudaMemsetAsync(h->d_e32, 0, sizeof(float) * h->n_dof, h->stream));
+  mfto_status s = diag_launch(h, MFTO_FORM_F32, h->d_E32, h->d_dinv32, true);
+  const PcgVecs<float> v{h->d_E32, h->d_e32, h->d_r32, h->d_z32, h->d_p0_32, h->d_p1_32,
+                         h->d_q32, h->d_dinv32, h->d_pcg32, h->d_partials, h->d_partials2,
+                         MFTO_FORM_F32};
+  if (s == MFTO_OK) s = pcg_start<float>(h, v, h->d_r32, nullptr, 1e-30, 1 << 30, 0.0);
+  if (s == MFTO_OK && cg2_active(h, MFTO_FORM_F32)) s = cg2_seed(h, v, 0.0);
+  PcgGraph* pg = nullptr;
+  if (s == MFTO_OK) s = get_graph<float>(h, v, 1, &pg);
+  h->kv_timing = timed;
+  if (s != MFTO_OK) return s;
+  cudaEvent_t a, b;
+  MFTO_CUDA(h, cudaEventCreate(&a));
+  MFTO_CUDA(h, cudaEventCreate(&b));
+  cudaError_t e = cudaGraphLaunch(pg->exec, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+  for (int c = 0; c < chunks && e == cudaSuccess; ++c) e = cudaGraphLaunch(pg->exec, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess)
+    return mfto_fail(h, MFTO_CUDA_ERROR, "CG iteration timing: %s", cudaGetErrorString(e));
+  h->launches += 2 * (int64_t)pg->chunk * (chunks + 1);
+  *us_per_iter = 1000.f * ms / (float)(chunks * pg->chunk);
+  return MFTO_OK;
+}
+
 void pcg_graph_release(mfto_handle* h) {
   for (int i = 0; i < MFTO_PCG_SLOTS; ++i) {
     destroy_graph(h->pcg_graph[i]);

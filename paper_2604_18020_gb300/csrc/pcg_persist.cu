@@ -36,15 +36,6 @@ constexpr int kItersPerLaunch = 4096;   // iterations per launch before the host
 // before every launch.  Every wait is bounded: after MFTO_SPIN_LIMIT polls
 // the CTA raises *error and stops waiting, and no later barrier waits once
 // *error is set.
-__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __device__ __forceinline__ void grid_barrier_count(unsigned int* count, unsigned int target,
                                                    int32_t* error) {

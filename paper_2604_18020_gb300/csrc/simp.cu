@@ -8,34 +8,63 @@ namespace {
 
 // ce_e = u_e^T KE u_e;  c = sum_e E_e ce_e;  dc_e = -p rho^(p-1) (E0-Emin) ce_e;
 // grayness sum 4 rho (1 - rho).  One thread per element, fixed-order sums.
+// The element energy is evaluated in the per-axis (sum, difference) mode
+// basis of modes.cuh: with x = T u_e (the three butterfly stages per
+// component) and KE = T^T Kt T / 8, u_e^T KE u_e = x . (Kt / 8) x, the sparse
+// mode operator the K.v applies (about 150 FP64 operations instead of the
+// 1,200 of the dense quadratic form).
 __global__ void __launch_bounds__(MFTO_BLOCK)
 compliance_kernel(const double* __restrict__ rho, const double* __restrict__ u,
-                  double* __restrict__ dc, const double* __restrict__ ke_g, Grid g,
+                  double* __restrict__ dc, ModeCoef<double> K, Grid g,
                   double E0, double Emin, double penal, MiscScalars* s, double* partials) {
-  __shared__ double ke[576];
   __shared__ double sh[64];
-  for (int t = threadIdx.x; t < 576; t += blockDim.x) ke[t] = ke_g[t];
-  __syncthreads();
   const int n = g.nelx * g.nely * g.nelz;
   double acc[2] = {0.0, 0.0};
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const int i = e % g.nelx, j = (e / g.nelx) % g.nely, k = e / (g.nelx * g.nely);
-    double ue[24];
+    double x[3][8];
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
       const int m = (i + (l & 1)) + g.nx * ((j + ((l >> 1) & 1)) + g.ny * (k + (l >> 2)));
-      ue[3 * l + 0] = u[3 * m + 0];
-      ue[3 * l + 1] = u[3 * m + 1];
-      ue[3 * l + 2] = u[3 * m + 2];
+      x[0][l] = u[3 * m + 0];
+      x[1][l] = u[3 * m + 1];
+      x[2][l] = u[3 * m + 2];
     }
-    double ce = 0.0;
-#pragma unroll 4
-    for (int a = 0; a < 24; ++a) {
-      double row = 0.0;
+    // butterflies (v0, v1) -> (v0 + v1, v1 - v0) along x, y, z
 #pragma unroll
-      for (int b = 0; b < 24; ++b) row += ke[a * 24 + b] * ue[b];
-      ce += ue[a] * row;
-    }
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          if (m & (1 << ax)) continue;
+          const double v0 = x[c][m], v1 = x[c][m | (1 << ax)];
+          x[c][m] = v0 + v1;
+          x[c][m | (1 << ax)] = v1 - v0;
+        }
+    double y[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) y[c][m] = K.diag[c][m] * x[c][m];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (a == b) continue;
+        const int t = 3 - a - b;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const int tb = mt << t;
+          y[a][(1 << a) | tb] = fma(K.lamM[mt], x[b][(1 << b) | tb], y[a][(1 << a) | tb]);
+          y[a][(1 << b) | tb] = fma(K.muM[mt], x[b][(1 << a) | tb], y[a][(1 << b) | tb]);
+        }
+      }
+    double ce = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) ce = fma(x[c][m], y[c][m], ce);
     const double r = rho[e];
     const double E = Emin + (E0 - Emin) * pow(r, penal);
     acc[0] += E * ce;
@@ -49,15 +78,19 @@ compliance_kernel(const double* __restrict__ rho, const double* __restrict__ u,
   }
 }
 
-// OC with bisection on lambda.  One cooperative grid.  A first pass stores
-// per element a_e = rho_e sqrt(max(0, -dc_e) n) and the move-limit bounds,
-// so that the candidate of a midpoint lambda is a_e / sqrt(lambda) (the
-// same value as rho_e sqrt(max(0, -dc_e) / (lambda / n)) up to rounding):
-// each bisection step is then one FP64 multiply and a clamp per element.
-// Each step sums the candidate field, crosses a bounded grid barrier and lets
-// every block reduce the per-block partials in the same order, so every block
-// takes the same branch.  Partials are double-buffered by step parity.  The
-// candidate of the last midpoint is written by a final pass.
+// OC with bisection on lambda.  One cooperative grid of one CTA per SM.  A
+// first pass forms per element a_e = rho_e sqrt(max(0, -dc_e) n) and the
+// move-limit bounds, so that the candidate of a midpoint lambda is
+// a_e / sqrt(lambda) (the same value as rho_e sqrt(max(0, -dc_e) / (lambda / n))
+// up to rounding): each bisection step is then one FP64 multiply and a clamp
+// per element, on values kept in registers (G > 0: up to G elements per
+// thread) or re-read from the scratch arrays (G == 0, larger meshes).  Each
+// step sums the candidate field, crosses a counting grid barrier (release-add
+// of one arrival per CTA, acquire-polls until every CTA of this step has
+// arrived; bounded) and lets every CTA add the per-CTA partials in the same
+// order, so every CTA takes the same branch.  Partials are double-buffered by
+// step parity.  The candidate of the last midpoint is written by a final pass.
+template <int G>
 __global__ void __launch_bounds__(MFTO_BLOCK)
 oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
           double* __restrict__ rho_new, double* __restrict__ a_s, double* __restrict__ lo_s,
@@ -67,12 +100,56 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
   const double target = volfrac * (double)n;
   const int first = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
-  for (int e = first; e < n; e += stride) {
-    const double r = rho[e];
-    a_s[e] = r * sqrt(fmax(0.0, -dc[e]) * (double)n);
-    lo_s[e] = fmax(0.0, r - move);
-    hi_s[e] = fmin(1.0, r + move);
+  double ra[G > 0 ? G : 1], rlo[G > 0 ? G : 1], rhi[G > 0 ? G : 1];
+  if constexpr (G > 0) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int e = first + g * stride;
+      ra[g] = 0.0;
+      rlo[g] = 0.0;
+      rhi[g] = 0.0;
+      if (e < n) {
+        const double r = rho[e];
+        ra[g] = r * sqrt(fmax(0.0, -dc[e]) * (double)n);
+        rlo[g] = fmax(0.0, r - move);
+        rhi[g] = fmin(1.0, r + move);
+      }
+    }
+  } else {
+    for (int e = first; e < n; e += stride) {
+      const double r = rho[e];
+      a_s[e] = r * sqrt(fmax(0.0, -dc[e]) * (double)n);
+      lo_s[e] = fmax(0.0, r - move);
+      hi_s[e] = fmin(1.0, r + move);
+    }
   }
+  // the candidate sum at the scale sc = 1 / sqrt(lambda)
+  auto volume = [&](double sc) {
+    double acc = 0.0;
+    if constexpr (G > 0) {
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (first + g * stride < n) acc += fmax(rlo[g], fmin(rhi[g], ra[g] * sc));
+    } else {
+      for (int e = first; e < n; e += stride) acc += fmax(lo_s[e], fmin(hi_s[e], a_s[e] * sc));
+    }
+    return acc;
+  };
+  unsigned int arrivals = 0;   // grid-barrier arrivals expected so far
+  auto grid_sync = [&]() {
+    arrivals += gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      red_release_add(&s->bar_count, 1u);
+      volatile int32_t* verr = &s->error;
+      unsigned int spins = 0;
+      while (ld_acquire(&s->bar_count) < arrivals) {
+        if (*verr) break;
+        if (++spins > MFTO_SPIN_LIMIT) { atomicExch(&s->error, 1); break; }
+      }
+    }
+    __syncthreads();
+  };
   double l1 = 0.0, l2 = 1e9, total = 0.0, last = -1.0;
   int step = 0;
   // Stops at the relative bracket width 1e-10, or when the midpoint no
@@ -81,13 +158,10 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
   while (l1 + l2 > 0.0 && (l2 - l1) / (l1 + l2) > 1e-10 && step < 4096) {
     const double lmid = 0.5 * (l1 + l2);
     if (!(l1 < lmid && lmid < l2)) break;   // uniform: every block holds the same l1, l2
-    const double sc = 1.0 / sqrt(lmid);
-    double acc = 0.0;
-    for (int e = first; e < n; e += stride) acc += fmax(lo_s[e], fmin(hi_s[e], a_s[e] * sc));
     double* buf = partials + (step & 1) * MFTO_RED_SLOTS;
-    const double bs = block_sum(acc, sh);
+    const double bs = block_sum(volume(1.0 / sqrt(lmid)), sh);
     if (threadIdx.x == 0) buf[blockIdx.x] = bs;
-    grid_barrier(&s->bar_count, &s->bar_gen, &s->error);
+    grid_sync();
     double t = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&buf[b]);
     t = block_sum(t, sh);
@@ -103,16 +177,23 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
   // change = max |rho_new - rho|
   const double sc = last > 0.0 ? 1.0 / sqrt(last) : 0.0;
   double mx = 0.0;
-  for (int e = first; e < n; e += stride) {
+  auto write = [&](int e, double a, double lo, double hi) {
     const double r = rho[e];
-    const double rn = last > 0.0 ? fmax(lo_s[e], fmin(hi_s[e], a_s[e] * sc)) : r;
+    const double rn = last > 0.0 ? fmax(lo, fmin(hi, a * sc)) : r;
     rho_new[e] = rn;
     mx = fmax(mx, fabs(rn - r));
+  };
+  if constexpr (G > 0) {
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (first + g * stride < n) write(first + g * stride, ra[g], rlo[g], rhi[g]);
+  } else {
+    for (int e = first; e < n; e += stride) write(e, a_s[e], lo_s[e], hi_s[e]);
   }
   double* buf = partials + 2 * MFTO_RED_SLOTS;
   const double bm = block_max(mx, sh);
   if (threadIdx.x == 0) buf[blockIdx.x] = bm;
-  grid_barrier(&s->bar_count, &s->bar_gen, &s->error);
+  grid_sync();
   if (blockIdx.x == 0) {
     double m2 = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m2 = fmax(m2, __ldcg(&buf[b]));
@@ -126,6 +207,8 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
   }
 }
 
+constexpr int kOcRegs = 8;   // elements per thread held in registers
+
 }  // namespace
 
 mfto_status compliance_launch(mfto_handle* h, const double* rho, const double* u, double* dc,
@@ -133,7 +216,7 @@ mfto_status compliance_launch(mfto_handle* h, const double* rho, const double* u
   const Grid g = make_grid(h->mesh);
   const int nb = reduction_blocks(h->n_elem, MFTO_BLOCK);
   h->launches++;
-  compliance_kernel<<<nb, MFTO_BLOCK, 0, h->stream>>>(rho, u, dc, h->d_ke64, g, h->p.E0,
+  compliance_kernel<<<nb, MFTO_BLOCK, 0, h->stream>>>(rho, u, dc, h->mc64, g, h->p.E0,
                                                      h->p.Emin, h->p.penal, h->d_misc,
                                                      h->d_partials);
   MFTO_LAUNCH_CHECK(h);
@@ -147,13 +230,13 @@ mfto_status compliance_launch(mfto_handle* h, const double* rho, const double* u
 
 mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc, double* rho_new,
                       mfto_iter_stats* st) {
-  int per_sm = 0;
-  MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oc_kernel, MFTO_BLOCK, 0));
-  int blocks = per_sm * h->num_sms;
+  // one CTA per SM (co-resident: the kernels use far fewer registers and no
+  // dynamic shared memory); elements in registers when they fit
+  int blocks = h->num_sms;
   const int need = (int)((h->n_elem + MFTO_BLOCK - 1) / MFTO_BLOCK);
   if (blocks > need) blocks = need;
-  if (blocks > MFTO_RED_MAX_BLOCKS) blocks = MFTO_RED_MAX_BLOCKS;
   if (blocks < 1) blocks = 1;
+  const bool regs = h->n_elem <= (int64_t)blocks * MFTO_BLOCK * kOcRegs;
   MFTO_CUDA(h, cudaMemsetAsync(&h->d_misc->error, 0, sizeof(int32_t), h->stream));
   MFTO_CUDA(h, cudaMemsetAsync(&h->d_misc->bar_count, 0, sizeof(unsigned int), h->stream));
   int n = (int)h->n_elem;
@@ -166,8 +249,8 @@ mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc, doubl
   void* args[] = {(void*)&rho, (void*)&dc, (void*)&rho_new, &a_s, &lo_s, &hi_s, &n, &volfrac,
                   &move, &s, &partials};
   h->launches++;
-  MFTO_CUDA(h, cudaLaunchCooperativeKernel((const void*)oc_kernel, dim3(blocks), dim3(MFTO_BLOCK),
-                                           args, 0, h->stream));
+  const void* fn = regs ? (const void*)oc_kernel<kOcRegs> : (const void*)oc_kernel<0>;
+  MFTO_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(MFTO_BLOCK), args, 0, h->stream));
   MFTO_CUDA(h, cudaMemcpyAsync(h->h_misc, h->d_misc, sizeof(MiscScalars), cudaMemcpyDeviceToHost,
                                h->stream));
   MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
