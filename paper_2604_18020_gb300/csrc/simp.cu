@@ -155,11 +155,16 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
   // Stops at the relative bracket width 1e-10, or when the midpoint no
   // longer lies strictly inside the bracket (lambda underflow when the target
   // is unreachable from above), and after at most 4096 steps in any case.
+  // 1 / sqrt(lambda) of each midpoint: formed once per CTA (the FP64 pipe
+  // runs 2 operations per clock per SM) and handed over in shared memory
+  __shared__ double s_sc;
   while (l1 + l2 > 0.0 && (l2 - l1) / (l1 + l2) > 1e-10 && step < 4096) {
     const double lmid = 0.5 * (l1 + l2);
     if (!(l1 < lmid && lmid < l2)) break;   // uniform: every block holds the same l1, l2
     double* buf = partials + (step & 1) * MFTO_RED_SLOTS;
-    const double bs = block_sum(volume(1.0 / sqrt(lmid)), sh);
+    if (threadIdx.x == 0) s_sc = 1.0 / sqrt(lmid);
+    __syncthreads();
+    const double bs = block_sum(volume(s_sc), sh);
     if (threadIdx.x == 0) buf[blockIdx.x] = bs;
     grid_sync();
     double t = 0.0;
@@ -234,9 +239,16 @@ mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc, doubl
   // dynamic shared memory); elements in registers when they fit
   int blocks = h->num_sms;
   const int need = (int)((h->n_elem + MFTO_BLOCK - 1) / MFTO_BLOCK);
+  const bool regs = h->n_elem <= (int64_t)blocks * MFTO_BLOCK * kOcRegs;
+  if (!regs) {
+    // larger meshes re-read the scratch arrays every step: more CTAs in flight
+    int per_sm = 0;
+    MFTO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oc_kernel<0>,
+                                                               MFTO_BLOCK, 0));
+    blocks = (per_sm < 4 ? (per_sm < 1 ? 1 : per_sm) : 4) * h->num_sms;
+  }
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  const bool regs = h->n_elem <= (int64_t)blocks * MFTO_BLOCK * kOcRegs;
   MFTO_CUDA(h, cudaMemsetAsync(&h->d_misc->error, 0, sizeof(int32_t), h->stream));
   MFTO_CUDA(h, cudaMemsetAsync(&h->d_misc->bar_count, 0, sizeof(unsigned int), h->stream));
   int n = (int)h->n_elem;
