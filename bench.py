@@ -729,7 +729,8 @@ def profile_run(args):
 def kernel_case_run(args):
     """Short runs of one kernel family on a moderate case, for ncu captures of
     the kernels outside the benchmark's step (--case):
-      tc      FP32-input K.v in each tensor-core form, 120 x 60 x 30;
+      tc      FP32-input K.v in each tensor-core form (3 launches each: TF32,
+              split TF32, BF16, split BF16, FP16, split FP16) on --workload;
       multi   the 8-load-case mixed solve, 100 x 50 x 50 (inner CG capped);
       batch   the 64 uneven instances' batched mixed solve;
       nn      U-Net forward and gradient on the 136 x 72 x 40 node grid of a
@@ -741,7 +742,7 @@ def kernel_case_run(args):
     dev = torch.device("cuda:0")
     case = args.case
     if case == "tc":
-        P = W.WORKLOADS["cantilever_120x60x30"]()
+        P = W.WORKLOADS[args.workload]()
         m = P.mesh
         with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
             E = torch.tensor(W.rho_random(m, seed=1), dtype=torch.float32, device=dev) ** 3

@@ -73,13 +73,18 @@ enum {
   MFTO_TOO_LARGE = 8        /* problem exceeds a fixed capacity          */
 };
 
-/* Arithmetic forms of the K.v contraction.  F64 and F32 run on the FMA
- * pipes; the others keep FP32 vectors and moduli, put the element
- * contraction on the tcgen05 tensor cores with FP32 accumulation, and round
- * the operands (E_e u_e and KE) to the form's type first.  The X3 forms split
- * each operand x into hi = round(x) and lo = round(x - hi) and add
- * A_hi B_lo + A_lo B_hi to A_hi B_hi (three products).  FP16 forms scale each
- * element's row by a power of two into [1, 2) to stay in range. */
+/* Arithmetic forms of the K.v contraction (Eq. matfree; the mixed-precision
+ * forms of Sec. 3.5).  F64 and F32 run on the FMA pipes; the others keep FP32
+ * vectors and moduli, put the element contraction on the tcgen05 tensor cores
+ * with FP32 accumulation, and round the operands to the form's type first.
+ * The X3 forms split each operand x into hi = round(x) and lo = round(x - hi)
+ * and add the products of the lo parts to A_hi B_hi (three products).
+ * TF32 forms: A = the element's nodal values minus a translation common to
+ * the tile of 30 x 7 owned nodes that contains it (KE annihilates
+ * translations, so the product is unchanged and its rounding scales with the
+ * deformation, not the rigid motion), the modulus applied to the product.
+ * BF16 and FP16 forms: A = E_e u_e; FP16 scales each element's row by a
+ * power of two into [1, 2) to stay in range. */
 typedef enum {
   MFTO_FORM_F64 = 0,        /* FP64 data, FP64 arithmetic                 */
   MFTO_FORM_F32 = 1,        /* FP32 data, FP32 arithmetic                 */

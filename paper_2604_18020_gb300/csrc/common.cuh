@@ -25,7 +25,7 @@ struct ModeCoef {
 #define MFTO_RED_MAX_BLOCKS 1024  // grid cap of the grid-stride vector kernels
 #define MFTO_RED_SLOTS 16384      // partial-sum slots per row of one grid reduction
 #define MFTO_PCG_SLOTS 2          // cached PCG graphs: FP64 solver, FP32 inner solver
-#define MFTO_TC_BTILE 3072        // bytes of one tensor-core B operand (KE, one part)
+#define MFTO_TC_BTILE 4096        // bytes of one tensor-core B operand (KE, one part)
 #define MFTO_MAX_RHS 8            // load cases of the multi-RHS calls
 #define MFTO_RED_ROWS 16          // rows of the partial-sum buffers (2 per load case)
 
@@ -106,6 +106,7 @@ struct mfto_handle {
   int occ_col[2];           // ... of the FP32 column kernel kinds (kv_tile.cu)
   int col_nzc;              // node layers per z-chunk of the column kernels (0: automatic)
   int col_kind;             // column kernel kind (mfto_kv_autotune)
+  int tcol_nzc;             // node layers per z-chunk of the tensor-core column kernel (0: automatic)
   unsigned int* d_bar;      // tree grid-barrier counters of the persistent CG (zeroed)
   int occ_tc[12];           // ... of the tensor-core kernels, [2 * (2 kind + split) + pcg]
   int occ_multi[3];         // ... of the multi-RHS kernels (F64 K.V, F32 K.V, F32 CG step)

@@ -2,25 +2,32 @@
 // split-TF32, BF16, split-BF16, FP16 and split-FP16 forms (FP32 vectors, FP32
 // accumulation in tensor memory).
 //
-// Same blocking as the FP32 block variant (kv_tile.cuh): a 256-thread CTA
-// owns the 7 x 7 x 3 interior nodes of a 9 x 9 x 5 node block and evaluates
-// its 8 x 8 x 4 elements, one per thread.  Here each thread writes its
-// element's 24 inputs, scaled by E_e and rounded to the form's type, as one
-// row of a 256 x K operand A in shared memory (the canonical K-major layout
-// without swizzle: 8-row x 16-byte core matrices); one thread then issues
+// TF32 and split TF32 run the pipelined column kernel of kv_tcol.cuh: the
+// staged node layers are the MMA's A operand in place, two TMEM accumulators
+// let the MMAs of one element layer overlap the staging of the next and the
+// node sums of the previous one.
+//
+// BF16 and FP16 (2-byte operands: four components of a node fill only half a
+// 16-byte core-matrix row, so a node layer cannot serve as the operand) use
+// the block kernel below, with the blocking of the FP32 block variant
+// (kv_tile.cuh): a 256-thread CTA owns the 7 x 7 x 3 interior nodes of a
+// 9 x 9 x 5 node block and evaluates its 8 x 8 x 4 elements, one per thread.
+// Each thread writes its element's 24 inputs, scaled by E_e and rounded to
+// the form's type, as one row of a 256 x K operand A in shared memory (the
+// canonical K-major layout without swizzle: 8-row x 16-byte core matrices);
+// one thread then issues
 //   D[128 x 32] (+)= A[128 x K] * B[K x 32],   two M-tiles,
 // with B = KE (rows = outputs, K-major; outputs 24..31 zero) resident in
 // shared memory and D in tensor memory (64 columns); the split forms add
 // A_hi B_lo + A_lo B_hi (hi = form(x), lo = form(x - hi)).  After the commit
 // mbarrier fires, every thread reads its element's 32-column row of D with
 // one tcgen05.ld and the node phase sums contributions as in the SIMT path.
-// The 576 multiply-adds per element move to the tensor cores; the SIMT work
-// per element drops to the gather, the conversions and the read-back.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <string.h>
 
 #include "common.cuh"
+#include "kv_tcol.cuh"
 #include "kv_tile.cuh"
 #include "tc.cuh"
 
@@ -29,17 +36,18 @@ namespace {
 constexpr int kTcCols = 64;            // TMEM columns per CTA: two 128 x 32 FP32 tiles
 constexpr uint32_t kTcSpin = 1u << 20; // bound of the mbarrier wait
 
-template <int KIND>                    // 0 TF32, 1 BF16, 2 FP16
+template <int KIND>                    // 1 BF16, 2 FP16
 struct TcKind {
-  static constexpr int ESZ = KIND == 0 ? 4 : 2;
-  static constexpr int KPAD = KIND == 0 ? 24 : 32;      // K per row (FP16/BF16 padded)
-  static constexpr int ROWB = KPAD * ESZ;               // 96 or 64 bytes per row
+  static_assert(KIND == 1 || KIND == 2, "2-byte kinds of the block kernel");
+  static constexpr int ESZ = 2;
+  static constexpr int KPAD = 32;                       // K per row (24 used)
+  static constexpr int ROWB = KPAD * ESZ;               // 64 bytes per row
   static constexpr int KC = ROWB / 16;                  // core matrices along K
   static constexpr int SBO = KC * 128;                  // bytes between 8-row groups
-  static constexpr int NKS = KIND == 0 ? 3 : 2;         // MMAs along K (K = 8 or 16 each)
+  static constexpr int NKS = 2;                         // MMAs along K (K = 16 each)
   static constexpr int ATILE = 256 * ROWB;
   static constexpr int BTILE = 32 * ROWB;
-  static constexpr uint32_t IDESC = make_idesc(KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u), 128, 32);
+  static constexpr uint32_t IDESC = make_idesc(KIND == 1 ? 1u : 0u, 128, 32);
 };
 
 constexpr int round128(int x) { return (x + 127) / 128 * 128; }
@@ -61,7 +69,7 @@ struct TcLayout {
   static constexpr int BYTES = OFF_BAR + 128;
   static constexpr int ALLOC = BYTES + 128;   // slack to align the dynamic base
 };
-static_assert(TcLayout<0, false>::OFF_BAR % 128 == 0 && TcLayout<2, true>::OFF_BAR % 128 == 0,
+static_assert(TcLayout<1, false>::OFF_BAR % 128 == 0 && TcLayout<2, true>::OFF_BAR % 128 == 0,
               "aligned regions");
 
 // byte offset of (row, k) in a K-major no-swizzle operand of the kind
@@ -73,27 +81,11 @@ __host__ __device__ inline int tc_offset(int row, int kbyte) {
 
 // Writes one A row (this thread's element) in the form; returns the factor
 // by which the row was scaled (FP16 forms scale each row into [1, 2) to stay
-// in range; the others return 1).
+// in range; BF16 returns 1).
 template <int KIND, bool SPLIT>
 __device__ __forceinline__ float write_a_row(unsigned char* A0, unsigned char* A1, int row,
                                              const float (&a)[24]) {
-  if constexpr (KIND == 0) {
-    float hi[24], lo[24];
-#pragma unroll
-    for (int k = 0; k < 24; ++k) {
-      hi[k] = to_tf32(a[k]);
-      lo[k] = to_tf32(a[k] - hi[k]);
-    }
-#pragma unroll
-    for (int kc = 0; kc < 6; ++kc) {
-      *reinterpret_cast<float4*>(A0 + tc_offset<0>(row, 16 * kc)) =
-          make_float4(hi[4 * kc], hi[4 * kc + 1], hi[4 * kc + 2], hi[4 * kc + 3]);
-      if (SPLIT)
-        *reinterpret_cast<float4*>(A1 + tc_offset<0>(row, 16 * kc)) =
-            make_float4(lo[4 * kc], lo[4 * kc + 1], lo[4 * kc + 2], lo[4 * kc + 3]);
-    }
-    return 1.0f;
-  } else {
+  {
     float scale = 1.0f, inv = 1.0f;
     if (KIND == 2) {
       float m = 0.f;
@@ -244,10 +236,7 @@ __device__ __forceinline__ double kv_tc_body(const float* __restrict__ E,
           for (int ks = 0; ks < C::NKS; ++ks) {
             const uint64_t da = smem_desc(aa + 256 * ks, 128, C::SBO);
             const uint64_t db = smem_desc(bb + 256 * ks, 128, C::SBO);
-            if (KIND == 0)
-              mma_tf32(d, da, db, C::IDESC, acc);
-            else
-              mma_f16(d, da, db, C::IDESC, acc);
+            mma_f16(d, da, db, C::IDESC, acc);
             acc = 1;
           }
         }
@@ -349,6 +338,55 @@ pcg_kv_tc_kernel(const float* __restrict__ E, const float* __restrict__ z,
   }
 }
 
+
+// ---- pipelined column kernels (TF32, split TF32) -------------------------
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(MFTO_BLOCK, 2)
+kv_tcol_kernel(const float* __restrict__ E, const float* __restrict__ v, float* __restrict__ y,
+               const uint8_t* __restrict__ fixed, const unsigned char* __restrict__ btile, Grid g,
+               TcolTiling tl, int32_t* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  bool skipped = false;
+  kv_tcol_body<TcolDefault, SPLIT>(E, fixed, btile, g, tl, ColLoadPlain{v}, ColStore{v, y}, smem,
+                                   ColNoPre{}, &skipped, err);
+}
+
+// CG K.v of the ticket graph engine: p = z + beta p_old, q = K p, p.q
+// reduced by the last block (alpha formed there).
+template <bool SPLIT>
+__global__ void __launch_bounds__(MFTO_BLOCK, 2)
+pcg_kv_tcol_kernel(const float* __restrict__ E, const float* __restrict__ z,
+                   const float* __restrict__ p_old, float* __restrict__ p_new,
+                   float* __restrict__ q, const uint8_t* __restrict__ fixed,
+                   const unsigned char* __restrict__ btile, Grid g, TcolTiling tl, PcgScalars* s,
+                   double* partials, int32_t* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double sh[64];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  bool skipped = false;
+  DotAcc<float> acc;
+  acc.s = kv_tcol_body<TcolDefault, SPLIT>(E, fixed, btile, g, tl, ColLoadDirection{z, p_old, 0.f},
+                                           ColPcg{p_new, q}, smem,
+                                           ColPreFlagBeta{&s->done, &s->beta}, &skipped, err);
+  if (skipped) return;   // uniform over the grid
+  const DFloat w[1] = {acc.finish_df()};
+  double tot[1];
+  if (last_block_reduce_df<1>(w, partials, &s->ticket_b, tot, sh) && threadIdx.x == 0) {
+    s->pq = tot[0];
+    if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+      s->done = 1;
+      s->status = MFTO_BREAKDOWN;
+      s->alpha = 0.0;
+    } else {
+      s->alpha = s->rz / tot[0];
+    }
+  }
+}
+
 // ---- host side -------------------------------------------------------------
 
 struct FormSpec {
@@ -388,11 +426,7 @@ void build_btile(const double* ke, unsigned char* hi, unsigned char* lo) {
     for (int k = 0; k < 24; ++k) {
       const float x = (float)ke[n * 24 + k];   // B[k][n] = KE[n][k], stored K-major by n
       const int off = tc_offset<KIND>(n, k * C::ESZ);
-      if (KIND == 0) {
-        const float h = host_tf32(x), l = host_tf32(x - h);
-        memcpy(hi + off, &h, 4);
-        memcpy(lo + off, &l, 4);
-      } else if (KIND == 1) {
+      if (KIND == 1) {
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
         const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
         memcpy(hi + off, &h, 2);
@@ -404,6 +438,27 @@ void build_btile(const double* ke, unsigned char* hi, unsigned char* lo) {
         memcpy(lo + off, &l, 2);
       }
     }
+}
+
+// B operands of the column kernel: for MMA step s = dy + 2 dz, the 32 x 8
+// block B_s[n][k] = KE[3 c_out + i][3 c_in + j] with n = 4 c_out + i (output
+// corner c_out, component i < 3) and k = 4 dx + j (input corner
+// c_in = dx + 2 dy + 4 dz, component j < 3); rows and columns of the 4th
+// components are zero.  hi = tf32(KE), lo = tf32(KE - hi).
+void build_btile_tcol(const double* ke, unsigned char* out) {
+  memset(out, 0, kTcolBBytes);
+  for (int st = 0; st < 4; ++st)
+    for (int co = 0; co < 8; ++co)
+      for (int i = 0; i < 3; ++i)
+        for (int dx = 0; dx < 2; ++dx)
+          for (int j = 0; j < 3; ++j) {
+            const int ci = dx + 2 * (st & 1) + 4 * (st >> 1);
+            const float x = (float)ke[(3 * co + i) * 24 + 3 * ci + j];
+            const float hv = host_tf32(x), lv = host_tf32(x - hv);
+            const int off = 1024 * st + tcol_b_offset(4 * co + i, 4 * dx + j);
+            memcpy(out + off, &hv, 4);
+            memcpy(out + kTcolBBytes / 2 + off, &lv, 4);
+          }
 }
 
 template <int KIND, bool SPLIT>
@@ -426,6 +481,39 @@ mfto_status tc_attrs(mfto_handle* h, int* occ_kv, int* occ_pcg) {
   return MFTO_OK;
 }
 
+// Resident CTAs per SM of a column-kernel launch: as many as shared memory
+// holds (dynamic + static + the per-block reservation), at most 2 (the
+// register budget of __launch_bounds__) and at most 512 / kTcolCols (TMEM).
+// The runtime's occupancy query reports one CTA per SM for kernels that
+// allocate tensor memory, so the count is derived here.
+template <typename K>
+mfto_status tcol_occupancy(mfto_handle* h, K kernel, int dyn, int* occ) {
+  int dev = 0, smem_sm = 0, reserved = 0;
+  MFTO_CUDA(h, cudaGetDevice(&dev));
+  MFTO_CUDA(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  MFTO_CUDA(h, cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  cudaFuncAttributes fa;
+  MFTO_CUDA(h, cudaFuncGetAttributes(&fa, kernel));
+  const int per_block = dyn + (int)fa.sharedSizeBytes + reserved;
+  int n = per_block > 0 ? smem_sm / per_block : 1;
+  if (n > 2) n = 2;
+  if (n > 512 / kTcolCols) n = 512 / kTcolCols;
+  if (n < 1) n = 1;
+  *occ = n;
+  return MFTO_OK;
+}
+
+template <bool SPLIT>
+mfto_status tcol_attrs(mfto_handle* h, int* occ_kv, int* occ_pcg) {
+  MFTO_CUDA(h, cudaFuncSetAttribute(kv_tcol_kernel<SPLIT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tcol_smem_bytes(1)));
+  MFTO_CUDA(h, cudaFuncSetAttribute(pcg_kv_tcol_kernel<SPLIT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tcol_smem_bytes(2)));
+  mfto_status s = tcol_occupancy(h, kv_tcol_kernel<SPLIT>, tcol_smem_bytes(1), occ_kv);
+  if (s == MFTO_OK) s = tcol_occupancy(h, pcg_kv_tcol_kernel<SPLIT>, tcol_smem_bytes(2), occ_pcg);
+  return s;
+}
+
 int tc_index(int kind, bool split) { return 2 * kind + (split ? 1 : 0); }
 
 unsigned grid_for(const mfto_handle* h, int per_sm) {
@@ -438,11 +526,38 @@ unsigned grid_for(const mfto_handle* h, int per_sm) {
 
 }  // namespace
 
+int tcol_smem_bytes(int ksrc) {
+  return ksrc == 1 ? TcolLayout<TcolDefault, 1>::ALLOC : TcolLayout<TcolDefault, 2>::ALLOC;
+}
+
+// Column tiling of a launch of the tensor-core column kernel: chunks of
+// h->tcol_nzc node layers if set, else about three tiles per resident CTA
+// with chunks of at least 4 layers.
+TcolTiling tcol_launch_tiling(const mfto_handle* h, int per_sm, int* grid) {
+  using S = TcolDefault;
+  const Grid g = make_grid(h->mesh);
+  const int64_t ctas = (int64_t)per_sm * h->num_sms;
+  int nzc = h->tcol_nzc;
+  if (nzc <= 0) {
+    const int64_t txy = (int64_t)((g.nx + S::OX - 1) / S::OX) * ((g.ny + S::OY - 1) / S::OY);
+    int64_t zch = (3 * ctas + txy - 1) / txy;
+    if (zch < 1) zch = 1;
+    nzc = (int)((g.nz + zch - 1) / zch);
+    if (nzc < 4) nzc = 4;
+  }
+  const TcolTiling tl = tcol_tiling<S>(g, nzc);
+  int64_t n = tl.count();
+  if (n > ctas) n = ctas;
+  if (n > MFTO_RED_SLOTS) n = MFTO_RED_SLOTS;
+  *grid = (int)n;
+  return tl;
+}
+
 mfto_status tc_init(mfto_handle* h) {
   mfto_status s = MFTO_OK;
   int* o = h->occ_tc;
-  if (s == MFTO_OK) s = tc_attrs<0, false>(h, &o[0], &o[1]);
-  if (s == MFTO_OK) s = tc_attrs<0, true>(h, &o[2], &o[3]);
+  if (s == MFTO_OK) s = tcol_attrs<false>(h, &o[0], &o[1]);
+  if (s == MFTO_OK) s = tcol_attrs<true>(h, &o[2], &o[3]);
   if (s == MFTO_OK) s = tc_attrs<1, false>(h, &o[4], &o[5]);
   if (s == MFTO_OK) s = tc_attrs<1, true>(h, &o[6], &o[7]);
   if (s == MFTO_OK) s = tc_attrs<2, false>(h, &o[8], &o[9]);
@@ -450,22 +565,16 @@ mfto_status tc_init(mfto_handle* h) {
   return s;
 }
 
-// B operands (KE, hi and lo parts) of the three kinds, in the device layout.
+// B operands (KE, hi and lo parts) in the device layouts: [kind][2 *
+// MFTO_TC_BTILE], the column kernel's blocks for TF32, hi then lo tiles for
+// BF16 and FP16.
 mfto_status tc_upload_b(mfto_handle* h, const double* ke) {
-  static_assert(TcKind<0>::BTILE <= MFTO_TC_BTILE && TcKind<1>::BTILE <= MFTO_TC_BTILE, "B tile");
-  unsigned char host[3][2][MFTO_TC_BTILE];
-  memset(host, 0, sizeof(host));
-  build_btile<0>(ke, host[0][0], host[0][1]);
-  build_btile<1>(ke, host[1][0], host[1][1]);
-  build_btile<2>(ke, host[2][0], host[2][1]);
-  // kind k: hi tile at (2k) * BTILE_k... stored as [kind][hi|lo] with the
-  // kind's own tile size, packed so that lo follows hi directly
+  static_assert(kTcolBBytes <= 2 * MFTO_TC_BTILE && TcKind<1>::BTILE <= MFTO_TC_BTILE, "B tile");
   unsigned char packed[3][2 * MFTO_TC_BTILE];
-  for (int k = 0; k < 3; ++k) {
-    const int bt = k == 0 ? TcKind<0>::BTILE : TcKind<1>::BTILE;
-    memcpy(packed[k], host[k][0], bt);
-    memcpy(packed[k] + bt, host[k][1], bt);
-  }
+  memset(packed, 0, sizeof(packed));
+  build_btile_tcol(ke, packed[0]);
+  build_btile<1>(ke, packed[1], packed[1] + TcKind<1>::BTILE);
+  build_btile<2>(ke, packed[2], packed[2] + TcKind<2>::BTILE);
   MFTO_CUDA(h, cudaMemcpyAsync(h->d_btc, packed, sizeof(packed), cudaMemcpyHostToDevice, h->stream));
   MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
   return MFTO_OK;
@@ -475,6 +584,8 @@ bool tc_form(int form) {
   FormSpec fs;
   return form_spec(form, &fs);
 }
+
+bool tcol_form(int form) { return form == MFTO_FORM_TF32 || form == MFTO_FORM_TF32X3; }
 
 #define MFTO_TC_DISPATCH(KIND_, SPLIT_, CALL)                                          \
   if (fs.kind == KIND_ && fs.split == SPLIT_) {                                         \
@@ -492,8 +603,17 @@ mfto_status kv_tc_launch(mfto_handle* h, int form, const float* E, const float* 
   const Grid g = make_grid(h->mesh);
   const int idx_occ = 0;
   int32_t* err = &h->d_misc->error;
-  MFTO_TC_DISPATCH(0, false, (kv_tc_kernel<0, false><<<grid, MFTO_BLOCK, smem, st>>>(E, v, y, h->d_fixed, bt, g, err)))
-  MFTO_TC_DISPATCH(0, true, (kv_tc_kernel<0, true><<<grid, MFTO_BLOCK, smem, st>>>(E, v, y, h->d_fixed, bt, g, err)))
+  if (fs.kind == 0) {
+    int grid = 0;
+    const TcolTiling tl = tcol_launch_tiling(h, h->occ_tc[2 * tc_index(0, fs.split)], &grid);
+    const size_t smem = tcol_smem_bytes(1);
+    if (fs.split)
+      kv_tcol_kernel<true><<<grid, MFTO_BLOCK, smem, st>>>(E, v, y, h->d_fixed, h->d_btc, g, tl, err);
+    else
+      kv_tcol_kernel<false><<<grid, MFTO_BLOCK, smem, st>>>(E, v, y, h->d_fixed, h->d_btc, g, tl, err);
+    MFTO_LAUNCH_CHECK(h);
+    return MFTO_OK;
+  }
   MFTO_TC_DISPATCH(1, false, (kv_tc_kernel<1, false><<<grid, MFTO_BLOCK, smem, st>>>(E, v, y, h->d_fixed, bt, g, err)))
   MFTO_TC_DISPATCH(1, true, (kv_tc_kernel<1, true><<<grid, MFTO_BLOCK, smem, st>>>(E, v, y, h->d_fixed, bt, g, err)))
   MFTO_TC_DISPATCH(2, false, (kv_tc_kernel<2, false><<<grid, MFTO_BLOCK, smem, st>>>(E, v, y, h->d_fixed, bt, g, err)))
@@ -510,8 +630,19 @@ mfto_status pcg_kv_tc_launch(mfto_handle* h, int form, const float* E, const flo
   const Grid g = make_grid(h->mesh);
   const int idx_occ = 1;
   int32_t* err = &s->tc_error;
-  MFTO_TC_DISPATCH(0, false, (pcg_kv_tc_kernel<0, false><<<grid, MFTO_BLOCK, smem, st>>>(E, z, p_old, p_new, q, h->d_fixed, bt, g, s, partials, err)))
-  MFTO_TC_DISPATCH(0, true, (pcg_kv_tc_kernel<0, true><<<grid, MFTO_BLOCK, smem, st>>>(E, z, p_old, p_new, q, h->d_fixed, bt, g, s, partials, err)))
+  if (fs.kind == 0) {
+    int grid = 0;
+    const TcolTiling tl = tcol_launch_tiling(h, h->occ_tc[2 * tc_index(0, fs.split) + 1], &grid);
+    const size_t smem = tcol_smem_bytes(2);
+    if (fs.split)
+      pcg_kv_tcol_kernel<true><<<grid, MFTO_BLOCK, smem, st>>>(E, z, p_old, p_new, q, h->d_fixed,
+                                                              h->d_btc, g, tl, s, partials, err);
+    else
+      pcg_kv_tcol_kernel<false><<<grid, MFTO_BLOCK, smem, st>>>(E, z, p_old, p_new, q, h->d_fixed,
+                                                               h->d_btc, g, tl, s, partials, err);
+    MFTO_LAUNCH_CHECK(h);
+    return MFTO_OK;
+  }
   MFTO_TC_DISPATCH(1, false, (pcg_kv_tc_kernel<1, false><<<grid, MFTO_BLOCK, smem, st>>>(E, z, p_old, p_new, q, h->d_fixed, bt, g, s, partials, err)))
   MFTO_TC_DISPATCH(1, true, (pcg_kv_tc_kernel<1, true><<<grid, MFTO_BLOCK, smem, st>>>(E, z, p_old, p_new, q, h->d_fixed, bt, g, s, partials, err)))
   MFTO_TC_DISPATCH(2, false, (pcg_kv_tc_kernel<2, false><<<grid, MFTO_BLOCK, smem, st>>>(E, z, p_old, p_new, q, h->d_fixed, bt, g, s, partials, err)))

@@ -25,6 +25,7 @@
 #include "cg_update.cuh"
 #include "common.cuh"
 #include "kv_column.cuh"
+#include "kv_tcol.cuh"
 
 namespace {
 
@@ -181,6 +182,27 @@ cg2_kv_kernel(const float* __restrict__ E, const float* __restrict__ z,
   publish_block_df<1>(w, reinterpret_cast<float2*>(part_a));
 }
 
+// A(k) with the tensor-core column K.v (TF32 forms, kv_tcol.cuh).
+template <bool SPLIT>
+__global__ void __launch_bounds__(MFTO_BLOCK, 2)
+cg2_kv_tcol_kernel(const float* __restrict__ E, const float* __restrict__ z,
+                   const float* __restrict__ p_old, float* __restrict__ p_new,
+                   float* __restrict__ q, const uint8_t* __restrict__ fixed,
+                   const unsigned char* __restrict__ btile, Grid g, TcolTiling tl, PcgScalars* s,
+                   const double* part_b, int nb_b, double* part_a, int par) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  DotAcc<float> acc;
+  bool skipped = false;   // uniform over the grid
+  acc.s = kv_tcol_body<TcolDefault, SPLIT>(
+      E, fixed, btile, g, tl, ColLoadDirection{z, p_old, 0.f}, ColPcg{p_new, q}, smem,
+      ColPreCg2{reinterpret_cast<const float2*>(part_b), nb_b, s, par}, &skipped, &s->tc_error);
+  if (skipped) return;
+  const DFloat w[1] = {acc.finish_df()};
+  publish_block_df<1>(w, reinterpret_cast<float2*>(part_a));
+}
+
 // B(k): u += alpha p; r -= alpha q; z = r / d over groups of 4 DOFs
 // (cg_update.cuh's per-group arithmetic); the first group's loads are
 // issued before alpha is formed.
@@ -320,7 +342,7 @@ int update_blocks(const mfto_handle* h) {
 }  // namespace
 
 bool cg2_active(const mfto_handle* h, int form) {
-  return h->cg_engine == 2 && form == MFTO_FORM_F32 && h->kv_variant == 0;
+  return h->cg_engine == 2 && ((form == MFTO_FORM_F32 && h->kv_variant == 0) || tcol_form(form));
 }
 
 mfto_status cg2_attrs(mfto_handle* h) {
@@ -329,6 +351,10 @@ mfto_status cg2_attrs(mfto_handle* h) {
                                     csm));
   MFTO_CUDA(h, cudaFuncSetAttribute(cg2_kv_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     csm));
+  MFTO_CUDA(h, cudaFuncSetAttribute(cg2_kv_tcol_kernel<false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tcol_smem_bytes(2)));
+  MFTO_CUDA(h, cudaFuncSetAttribute(cg2_kv_tcol_kernel<true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tcol_smem_bytes(2)));
   return MFTO_OK;
 }
 
@@ -345,11 +371,30 @@ mfto_status cg2_enqueue(mfto_handle* h, cudaStream_t st, const PcgVecs<float>& v
                         cudaEvent_t ev1) {
   int grid = 0;
   const int kind = h->col_kind;
-  const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
   const Grid g = make_grid(h->mesh);
-  const size_t sm = kColSmem;
   const int nb_b = update_blocks(h);
   if (ev0) MFTO_CUDA(h, cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal));
+  if (tcol_form(v.form)) {
+    const bool split = v.form == MFTO_FORM_TF32X3;
+    const TcolTiling tt = tcol_launch_tiling(h, h->occ_tc[split ? 3 : 1], &grid);
+    const size_t smt = tcol_smem_bytes(2);
+    if (split)
+      cg2_kv_tcol_kernel<true><<<grid, MFTO_BLOCK, smt, st>>>(
+          v.E, v.z, p_old, p_new, v.q, h->d_fixed, h->d_btc, g, tt, v.s, v.part_b, nb_b,
+          v.part_a, par);
+    else
+      cg2_kv_tcol_kernel<false><<<grid, MFTO_BLOCK, smt, st>>>(
+          v.E, v.z, p_old, p_new, v.q, h->d_fixed, h->d_btc, g, tt, v.s, v.part_b, nb_b,
+          v.part_a, par);
+    if (ev1) MFTO_CUDA(h, cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal));
+    cg2_update_kernel<<<nb_b, MFTO_BLOCK, 0, st>>>(v.u, p_new, v.q, v.r, v.z, v.dinv,
+                                                   (int)h->n_dof, v.s, v.part_a, grid, v.part_b,
+                                                   par);
+    MFTO_LAUNCH_CHECK(h);
+    return MFTO_OK;
+  }
+  const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
+  const size_t sm = kColSmem;
   if (kind == 1)
     cg2_kv_kernel<3><<<grid, MFTO_BLOCK, sm, st>>>(v.E, v.z, p_old, p_new, v.q, h->d_fixed,
                                                    h->mc32, g, tl, v.s, v.part_b, nb_b, v.part_a,
