@@ -79,10 +79,11 @@ enum {
  * with FP32 accumulation, and round the operands to the form's type first.
  * The X3 forms split each operand x into hi = round(x) and lo = round(x - hi)
  * and add the products of the lo parts to A_hi B_hi (three products).
- * TF32 forms: A = the element's nodal values minus a translation common to
- * the tile of 30 x 7 owned nodes that contains it (KE annihilates
- * translations, so the product is unchanged and its rounding scales with the
- * deformation, not the rigid motion), the modulus applied to the product.
+ * TF32 forms: A = the element's nodal values (split TF32: minus a
+ * translation common to the tile of 30 x 7 owned nodes that contains it; KE
+ * annihilates translations, so the product is unchanged and its rounding
+ * scales with the deformation, not the rigid motion), the modulus applied to
+ * the product.
  * BF16 and FP16 forms: A = E_e u_e; FP16 scales each element's row by a
  * power of two into [1, 2) to stay in range. */
 typedef enum {

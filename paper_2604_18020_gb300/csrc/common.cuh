@@ -67,6 +67,8 @@ struct MiscScalars {
   double sum[4];            // results of small reductions
   double lambda, change, volume;
   int32_t oc_steps;
+  int32_t oc_evals;         // candidate-volume evaluations (grid barriers) of the last OC
+  int32_t oc_kstar;         // its first-phase index k* (the next call's starting guess)
   int32_t error;            // set by device code that gave up on a wait
   unsigned int ticket;
   unsigned int bar_count, bar_gen;
@@ -120,6 +122,7 @@ struct mfto_handle {
   // PCG workspace (FP64)
   double *d_r, *d_z, *d_p0, *d_p1, *d_q, *d_dinv;
   double* d_oc;             // [3][n_elem] OC bisection scratch (simp.cu)
+  int oc_hint;              // k* of the previous OC update (0: none), simp.cu
   uint8_t* d_tile_fixed;    // column K.v xy tiles that stage a fixed node (kv_column.cuh)
   double* d_partials;       // [MFTO_RED_ROWS * MFTO_RED_SLOTS]
   double* d_partials2;      // [MFTO_RED_ROWS * MFTO_RED_SLOTS]

@@ -554,9 +554,13 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
   DFloat red{0.f, 0.f};
   *skipped = false;
   const int ntiles = tl.count();
-  // this thread's place in tile t
+  const int nxy = g.nx * g.ny, nexy = g.nelx * g.nely;
+  // this thread's place in tile t: its column's node and element and the
+  // extra node, as in-plane indices (layer 0) and whether they exist
   struct Ctx {
-    int kb, ke, gi, gj, hi, hj;
+    int kb, ke, gi, gj;
+    int own_base, extra_base, elem_base;
+    bool own_in, extra_in, elem_in;
   };
   auto ctx_of = [&](int t) {
     const int bx = t % tl.tx, by = (t / tl.tx) % tl.ty, bz = t / (tl.tx * tl.ty);
@@ -566,33 +570,40 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     c.ke = min(c.kb + tl.nzc, g.nz);                      // owned node layers [kb, ke)
     c.gi = x0 + ex;                                       // this column's element (and node)
     c.gj = y0 + ey;
-    c.hi = x0 + xx;                                       // the extra node
-    c.hj = y0 + xy;
+    const int hi = x0 + xx, hj = y0 + xy;                 // the extra node
+    c.own_in = c.gi >= 0 && c.gj >= 0 && c.gi < g.nx && c.gj < g.ny;
+    c.extra_in = hi >= 0 && hj >= 0 && hi < g.nx && hj < g.ny;
+    c.elem_in = c.gi >= 0 && c.gj >= 0 && c.gi < g.nelx && c.gj < g.nely;
+    c.own_base = c.gi + g.nx * c.gj;
+    c.extra_base = hi + g.nx * hj;
+    c.elem_base = c.gi + g.nelx * c.gj;
     return c;
   };
-  auto slot_of = [](int L) { return (L + 1) % kColRing; };   // L >= -1
+  // node layer L (>= -1) sits in ring slot (L + 1) mod kColRing; the slots
+  // are carried as rotating counters
+  auto next_slot = [](int sl) { return sl == kColRing - 1 ? 0 : sl + 1; };
   // tile t has no fixed node: its mask words are neither copied nor read
   auto clean_of = [&](int t) {
     const int bxy = t % (tl.tx * tl.ty);
     return tl.fixed_tiles != nullptr && tl.fixed_tiles[bxy] == 0;
   };
   // copies of node layer L (and the modulus of element layer L - 1) into
-  // the ring; layers past ke copy nothing but still commit a group
-  auto issue = [&](const Ctx& c, int L, auto clean_tag) {
+  // ring slot sl; layers past ke copy nothing but still commit a group
+  auto issue = [&](const Ctx& c, int L, int sl, auto clean_tag) {
     constexpr bool CLEAN = decltype(clean_tag)::value;
     const bool lay = L >= 0 && L <= c.ke && L < g.nz;
-    float* R = ring + slot_of(L) * NS * S::NV;
+    float* R = ring + sl * NS * S::NV;
     {
-      const bool in = lay && c.gi >= 0 && c.gj >= 0 && c.gi < g.nx && c.gj < g.ny;
-      const int node = in ? c.gi + g.nx * (c.gj + g.ny * L) : 0;
+      const bool in = lay && c.own_in;
+      const int node = in ? c.own_base + nxy * L : 0;
 #pragma unroll
       for (int sidx = 0; sidx < Load::kSrc; ++sidx)
         col_cp4x3(R + 3 * sidx * S::NV + own_slot, ld.src(sidx) + 3 * node, in);
       if (!CLEAN) col_cp4(R + 3 * Load::kSrc * S::NV + own_slot, fixed_words + (node >> 2), in);
     }
     if (has_extra) {
-      const bool in = lay && c.hi >= 0 && c.hj >= 0 && c.hi < g.nx && c.hj < g.ny;
-      const int node = in ? c.hi + g.nx * (c.hj + g.ny * L) : 0;
+      const bool in = lay && c.extra_in;
+      const int node = in ? c.extra_base + nxy * L : 0;
 #pragma unroll
       for (int sidx = 0; sidx < Load::kSrc; ++sidx)
         col_cp4x3(R + 3 * sidx * S::NV + extra_slot, ld.src(sidx) + 3 * node, in);
@@ -601,22 +612,23 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     }
     {
       const int el = L - 1;
-      const bool in = c.gi >= 0 && c.gj >= 0 && c.gi < g.nelx && c.gj < g.nely &&
-                      el >= c.kb - 1 && el >= 0 && el < g.nelz && L <= c.ke;
-      const int e = in ? c.gi + g.nelx * (c.gj + g.nely * el) : 0;
-      col_cp4(ering + slot_of(L) * MFTO_BLOCK + tid, E + e, in);
+      const bool in = c.elem_in && el >= c.kb - 1 && el >= 0 && el < g.nelz && L <= c.ke;
+      const int e = in ? c.elem_base + nexy * el : 0;
+      col_cp4(ering + sl * MFTO_BLOCK + tid, E + e, in);
     }
     col_cp_commit();
   };
-  // a staged node from the ring: masked loaded values and its mask
-  auto take = [&](int L, int sl, int ni, int nj, auto clean_tag) {
+  // a staged node from ring slot rs: masked loaded values and its mask
+  // (q: its place in the staged layer, base: its in-plane node index)
+  auto take = [&](int L, int rs, int q, int base, auto clean_tag) {
     constexpr bool CLEAN = decltype(clean_tag)::value;
-    const float* R = ring + slot_of(L) * NS * S::NV;
+    const float* R = ring + rs * NS * S::NV;
+    const int sl = q;
     ColNode n;
     n.fm = 0;
     if (!CLEAN) {
       const uint32_t w = __float_as_uint(R[3 * Load::kSrc * S::NV + sl]);
-      const int node = ni + g.nx * (nj + g.ny * L);   // only its low 2 bits are used
+      const int node = base + nxy * L;   // only its low 2 bits are used
       n.fm = (uint8_t)(w >> (8 * (node & 3)));
     }
 #pragma unroll
@@ -629,12 +641,14 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     return n;
   };
   auto issue_prologue = [&](const Ctx& c, bool clean) {
+    int sl = c.kb % kColRing;   // slot of node layer kb - 1
 #pragma unroll
     for (int j = 0; j <= kColPrefetch; ++j) {
       if (clean)
-        issue(c, c.kb - 1 + j, std::true_type{});
+        issue(c, c.kb - 1 + j, sl, std::true_type{});
       else
-        issue(c, c.kb - 1 + j, std::false_type{});
+        issue(c, c.kb - 1 + j, sl, std::false_type{});
+      sl = next_slot(sl);
     }
   };
   // first tile's prologue copies, then the pre-step while they are in flight
@@ -648,22 +662,26 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
   // one tile; CLEAN (no fixed node in the tile) compiles the mask work out
   auto run_tile = [&](const Ctx& c, auto clean_tag) {
     constexpr bool CLEAN = decltype(clean_tag)::value;
-    const int kb = c.kb, ke = c.ke, gi = c.gi, gj = c.gj;
-    const bool own_node = owner && gi < g.nx && gj < g.ny;
-    auto stage = [&](int L) {
+    const int kb = c.kb, ke = c.ke;
+    const bool own_node = owner && c.own_in;
+    auto stage = [&](int L, int rs) {
       float* Lb = nodes + (L & 1) * 3 * S::NV;
-      const ColNode own = take(L, own_slot, gi, gj, clean_tag);
+      const ColNode own = take(L, rs, own_slot, c.own_base, clean_tag);
 #pragma unroll
       for (int k = 0; k < 3; ++k) Lb[k * S::NV + own_slot] = own.v[k];
       if (has_extra) {
-        const ColNode extra = take(L, extra_slot, c.hi, c.hj, clean_tag);
+        const ColNode extra = take(L, rs, extra_slot, c.extra_base, clean_tag);
 #pragma unroll
         for (int k = 0; k < 3; ++k) Lb[k * S::NV + extra_slot] = extra.v[k];
       }
       return own;
     };
+    // ring slots: rs of the node layer staged next, rp of the one staged
+    // before it (free again: its copies landed and were read)
+    int rp = c.kb % kColRing;   // node layer kb - 1
     col_cp_wait<kColPrefetch>();
-    ColNode mine = stage(kb - 1);
+    ColNode mine = stage(kb - 1, rp);
+    int rs = next_slot(rp);
     __syncthreads();
     float F0[3][4], F1[3][4], U0[3][4], U1[3][4];
     face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, own_slot, F0);
@@ -687,7 +705,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
           sacc += Sm[(4 * q + 0) * MFTO_BLOCK + tid];
           acc[q] = sacc;
         }
-        epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, CLEAN ? (uint8_t)0 : nv.fm, red);
+        epi(c.own_base + nxy * k, acc, nv.v, CLEAN ? (uint8_t)0 : nv.fm, red);
       }
     };
     auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
@@ -697,9 +715,12 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       col_cp_wait<kColPrefetch - 1>();
       mine_prev = mine_cur;
       mine_cur = mine;
-      mine = stage(ez + 1);
-      const float Ee = ering[slot_of(ez + 1) * MFTO_BLOCK + tid];
-      issue(c, ez + 1 + kColPrefetch, clean_tag);
+      mine = stage(ez + 1, rs);
+      const float Ee = ering[rs * MFTO_BLOCK + tid];
+      // layer ez + 1 + kColPrefetch goes into the slot of layer ez
+      issue(c, ez + 1 + kColPrefetch, rp, clean_tag);
+      rp = rs;
+      rs = next_slot(rs);
       __syncthreads();
       // node layer ez - 1 (its corner sums were written in iteration ez - 1)
       if (ez - 1 >= kb) finish(ez - 1, mine_prev);

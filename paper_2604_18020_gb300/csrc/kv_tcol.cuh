@@ -20,10 +20,11 @@
 // dx = 1 corners wrap into the next row, and positions past the tile) give
 // rows that are never used.  A tile has 256 positions = two M = 128 MMA tiles.
 //
-// Split TF32 (SPLIT): every staged value is stored as hi = tf32(v) and
-// lo = tf32(v - hi), KE likewise, and D = A_lo B_hi + A_hi B_lo + A_hi B_hi
-// (small products first) in FP32 in tensor memory; without SPLIT only
-// A_hi B_hi.  The modulus multiplies the read-back row: E_e (KE u_e).
+// Split TF32 (SPLIT): every staged value w = v - r (r: a translation common
+// to the tile, below) is stored as hi = tf32(w) and lo = tf32(w - hi), KE
+// likewise, and D = A_lo B_hi + A_hi B_lo + A_hi B_hi (small products first)
+// in FP32 in tensor memory; without SPLIT, r = 0 and only A_hi B_hi.  The
+// modulus multiplies the read-back row: E_e (KE u_e).
 //
 // Pipeline (one CTA, 256 threads, thread t <-> position t; one barrier per
 // element layer).  Iteration i (element layer ez = kb - 1 + i):
@@ -203,11 +204,19 @@ __device__ __forceinline__ DFloat kv_tcol_body(const float* __restrict__ E,
     c.elem_base = gi + g.nelx * gj;
     return c;
   };
-  // r: the loaded value of the tile's central node of layer kb (any
-  // translation leaves KE u_e unchanged; subtracting one common to the tile
-  // makes the TF32 rounding relative to the tile's deformation instead of
-  // its rigid motion, which dominates in soft regions)
+  // r (split form): the loaded value of the tile's central node of layer
+  // kb.  Any translation leaves KE u_e unchanged; subtracting one common to
+  // the tile makes the TF32 rounding relative to the tile's deformation
+  // instead of its rigid motion, which dominates in soft regions.  As r
+  // depends on the operand, the product with the rounded KE picks up the
+  // term -(KE_used 1) r per element, which is linear but not symmetric in
+  // the operand: with the split KE (KE_hi + KE_lo = KE to about 2^-22) it
+  // stays below the rounding of the product itself, with the one-term TF32
+  // KE (2^-11) it would not, so the TF32 form keeps r = 0.
   auto reference = [&](Ctx& c) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c.r[k] = 0.f;
+    if (!SPLIT) return;
     const int ci = min(max(c.x0 + P / 2, 0), g.nx - 1);
     const int cj = min(max(c.y0 + S::R / 2, 0), g.ny - 1);
     const int node = ci + g.nx * (cj + g.ny * c.kb);

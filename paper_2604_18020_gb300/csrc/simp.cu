@@ -82,20 +82,32 @@ compliance_kernel(const double* __restrict__ rho, const double* __restrict__ u,
 // first pass forms per element a_e = rho_e sqrt(max(0, -dc_e) n) and the
 // move-limit bounds, so that the candidate of a midpoint lambda is
 // a_e / sqrt(lambda) (the same value as rho_e sqrt(max(0, -dc_e) / (lambda / n))
-// up to rounding): each bisection step is then one FP64 multiply and a clamp
-// per element, on values kept in registers (G > 0: up to G elements per
-// thread) or re-read from the scratch arrays (G == 0, larger meshes).  Each
-// step sums the candidate field, crosses a counting grid barrier (release-add
-// of one arrival per CTA, acquire-polls until every CTA of this step has
-// arrived; bounded) and lets every CTA add the per-CTA partials in the same
-// order, so every CTA takes the same branch.  Partials are double-buffered by
-// step parity.  The candidate of the last midpoint is written by a final pass.
+// up to rounding): each evaluation of the candidate volume is then one FP64
+// multiply and a clamp per element, on values kept in registers (G > 0: up
+// to G elements per thread) or re-read from the scratch arrays (G == 0,
+// larger meshes).  An evaluation sums the candidate field, crosses a
+// counting grid barrier (release-add of one arrival per CTA, acquire-polls
+// until every CTA has arrived; bounded), and warp 0 of every CTA adds the
+// per-CTA partials in the same order, so every CTA takes the same branch.
+// Partials are double-buffered by evaluation parity.
+//
+// The bisection starts from [0, 1e9].  While its lower end is still 0, its
+// midpoints are lambda_k = 1e9 / 2^k (k = 1, 2, ...: each the previous one
+// halved, so exact down to the subnormal range), and it moves the upper end
+// down until the first k* whose candidate volume exceeds the target.  That
+// volume is nondecreasing in k (every step of its evaluation is monotone:
+// rounded products, clamps and fixed-order rounded sums), so k* is found by
+// a binary search over k, started at the previous call's k* (a hint that
+// leaves the result unchanged and normally settles it in two evaluations),
+// and the bisection then continues from exactly the state it would have
+// reached step by step.  The candidate of the last midpoint is written by a
+// final pass.
 template <int G>
 __global__ void __launch_bounds__(MFTO_BLOCK)
 oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
           double* __restrict__ rho_new, double* __restrict__ a_s, double* __restrict__ lo_s,
           double* __restrict__ hi_s, int n, double volfrac, double move, MiscScalars* s,
-          double* partials) {
+          double* partials, int k_end, int k_hint) {
   __shared__ double sh[64];
   const double target = volfrac * (double)n;
   const int first = blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,29 +162,78 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
     }
     __syncthreads();
   };
-  double l1 = 0.0, l2 = 1e9, total = 0.0, last = -1.0;
-  int step = 0;
-  // Stops at the relative bracket width 1e-10, or when the midpoint no
-  // longer lies strictly inside the bracket (lambda underflow when the target
-  // is unreachable from above), and after at most 4096 steps in any case.
-  // 1 / sqrt(lambda) of each midpoint: formed once per CTA (the FP64 pipe
+  // 1 / sqrt(lambda) of each evaluation: formed once per CTA (the FP64 pipe
   // runs 2 operations per clock per SM) and handed over in shared memory
-  __shared__ double s_sc;
-  while (l1 + l2 > 0.0 && (l2 - l1) / (l1 + l2) > 1e-10 && step < 4096) {
-    const double lmid = 0.5 * (l1 + l2);
-    if (!(l1 < lmid && lmid < l2)) break;   // uniform: every block holds the same l1, l2
-    double* buf = partials + (step & 1) * MFTO_RED_SLOTS;
-    if (threadIdx.x == 0) s_sc = 1.0 / sqrt(lmid);
+  __shared__ double s_sc, s_tot;
+  int evals = 0;
+  // the candidate volume at lambda, identical in every CTA
+  auto eval_total = [&](double lam) {
+    double* buf = partials + (evals & 1) * MFTO_RED_SLOTS;
+    ++evals;
+    if (threadIdx.x == 0) s_sc = 1.0 / sqrt(lam);
     __syncthreads();
     const double bs = block_sum(volume(s_sc), sh);
     if (threadIdx.x == 0) buf[blockIdx.x] = bs;
     grid_sync();
-    double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&buf[b]);
-    t = block_sum(t, sh);
-    if (threadIdx.x == 0) sh[40] = t;
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(&buf[b]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) s_tot = t;
+    }
     __syncthreads();
-    total = sh[40];
+    return s_tot;
+  };
+  // lambda_k = 1e9 halved k times (0 <= k <= k_end; exact for k <= 1083)
+  auto lam_of = [](int k) {
+    if (k <= 1083) return ldexp(1e9, -k);
+    double x = ldexp(1e9, -1083);
+    for (int i = 1083; i < k; ++i) x = 0.5 * x;
+    return x;
+  };
+  const double target_v = target;
+  double l1 = 0.0, l2 = 1e9, total = 0.0, last = -1.0;
+  int step = 0, kstar = 0;
+  // the phase with lower end 0: k* = the first k in [1, k_end) whose volume
+  // exceeds the target (k_end: the first k with lambda_k = 0, where the
+  // step-by-step bisection stops); klo: volume known <= target (0: none
+  // evaluated), khi: volume known > target (k_end: none found yet)
+  if (k_end > 1) {
+    int klo = 0, khi = k_end;
+    double vlo = 0.0, vhi = 0.0;
+    auto probe = [&](int k) {
+      const double v = eval_total(lam_of(k));
+      if (v > target_v) { khi = k; vhi = v; } else { klo = k; vlo = v; }
+    };
+    if (k_hint >= 1 && k_hint < k_end) {
+      probe(k_hint);
+      if (khi == k_hint && k_hint - 1 >= 1) probe(k_hint - 1);
+      else if (klo == k_hint && k_hint + 1 < k_end) probe(k_hint + 1);
+    }
+    if (klo != k_end - 1 && khi == k_end) probe(k_end - 1);   // is there a k* at all?
+    while (khi - klo > 1 && !*(volatile int32_t*)&s->error) probe((klo + khi) / 2);
+    kstar = khi;
+    if (khi < k_end) {
+      l1 = lam_of(khi);
+      l2 = lam_of(khi - 1);
+      last = l1;
+      total = vhi;
+      step = khi;
+    } else {
+      l2 = lam_of(k_end - 1);
+      last = l2;
+      total = vlo;
+      step = k_end - 1;
+    }
+  }
+  // Stops at the relative bracket width 1e-10, or when the midpoint no
+  // longer lies strictly inside the bracket (lambda underflow when the target
+  // is unreachable from above), and after at most 4096 steps in any case.
+  while (l1 + l2 > 0.0 && (l2 - l1) / (l1 + l2) > 1e-10 && step < 4096) {
+    const double lmid = 0.5 * (l1 + l2);
+    if (!(l1 < lmid && lmid < l2)) break;   // uniform: every block holds the same l1, l2
+    total = eval_total(lmid);
     last = lmid;
     if (total > target) l1 = lmid; else l2 = lmid;
     ++step;
@@ -208,6 +269,8 @@ oc_kernel(const double* __restrict__ rho, const double* __restrict__ dc,
       s->volume = total / (double)n;
       s->lambda = 0.5 * (l1 + l2);
       s->oc_steps = step;
+      s->oc_evals = evals;
+      s->oc_kstar = kstar;
     }
   }
 }
@@ -258,8 +321,20 @@ mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc, doubl
   double* a_s = h->d_oc;
   double* lo_s = h->d_oc + h->n_elem;
   double* hi_s = h->d_oc + 2 * h->n_elem;
+  // k_end: the first k at which 1e9 halved k times is 0 (the bisection's
+  // midpoint with lower end 0 no longer lies inside its bracket)
+  static const int k_end = [] {
+    double x = 1e9;
+    int k = 0;
+    while (x > 0.0) {
+      x = 0.5 * x;
+      ++k;
+    }
+    return k;
+  }();
+  int k_hint = h->oc_hint;
   void* args[] = {(void*)&rho, (void*)&dc, (void*)&rho_new, &a_s, &lo_s, &hi_s, &n, &volfrac,
-                  &move, &s, &partials};
+                  &move, &s, &partials, (void*)&k_end, &k_hint};
   h->launches++;
   const void* fn = regs ? (const void*)oc_kernel<kOcRegs> : (const void*)oc_kernel<0>;
   MFTO_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(MFTO_BLOCK), args, 0, h->stream));
@@ -268,6 +343,7 @@ mfto_status oc_launch(mfto_handle* h, const double* rho, const double* dc, doubl
   MFTO_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->h_misc->error)
     return mfto_fail(h, MFTO_CUDA_ERROR, "OC: a grid barrier wait gave up (bounded spin)");
+  h->oc_hint = (h->h_misc->oc_kstar >= 1 && h->h_misc->oc_kstar < k_end) ? h->h_misc->oc_kstar : 0;
   if (st) {
     st->change = h->h_misc->change;
     st->volume = h->h_misc->volume;
