@@ -239,8 +239,9 @@ mfto_status mfto_set_kv_variant(mfto_handle* h, int32_t variant);
  * r.r in the K.v's pre-step, p.q before the vector update) while its first
  * loads are in flight, every block in the same fixed order.  All compute the
  * same per-entry arithmetic; the dot products add the per-block partials in
- * different orders.  The tensor-core inner forms and
- * mfto_set_kv_variant(h, 1) always use 0.
+ * different orders.  The TF32 and split-TF32 inner forms run 0 or 2 (1 acts
+ * as 0 for them); the BF16 and FP16 forms and mfto_set_kv_variant(h, 1)
+ * always use 0.
  * MFTO_UNSUPPORTED for 1 without cooperative launch.  A barrier wait that
  * gives up (about a second) makes the solve return MFTO_CUDA_ERROR. */
 mfto_status mfto_set_cg_engine(mfto_handle* h, int32_t engine);
