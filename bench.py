@@ -63,10 +63,10 @@ KERNEL_SOURCES = {
     "pcg_kv_tile_kernel<double>": ["kv_tile.cuh", "kv_tile.cu", "modes.cuh"],
 }
 NCU_DRAM_BYTES = {
-    ("cg2_kv_kernel<2>", WORKLOAD): (6.642688e6, "bf43c09eaec4"),
-    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (145.194752e6 + 76.744192e6, "bf43c09eaec4"),
-    ("pcg_kv_tile_kernel<double>", WORKLOAD): ((294.4e6 + 199.3e6) * 216000 / 4915200,
-                                               "adcb1137b447"),
+    ("cg2_kv_kernel<2>", WORKLOAD): (6.662656e6, "979c2c9819a6"),
+    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (143.068416e6 + 75.482112e6, "979c2c9819a6"),
+    ("pcg_kv_tile_kernel<double>", WORKLOAD): ((293.127936e6 + 199.873024e6) * 216000 / 4915200,
+                                               "6e176c6f4f1e"),
 }
 
 
