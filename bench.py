@@ -735,7 +735,7 @@ def kernel_case_run(args):
       batch   the 64 uneven instances' batched mixed solve;
       nn      U-Net forward and gradient on the 136 x 72 x 40 node grid of a
               128 x 64 x 32 mesh (the learned part's training size);
-      simp    one SIMP iteration (filter, compliance, OC) of 120 x 60 x 30."""
+      simp    two SIMP iterations (filter, solve, compliance, OC) on --workload."""
     import numpy as np
     import torch
     from paper_2604_18020_gb300 import mfto, workloads as W
@@ -795,7 +795,7 @@ def kernel_case_run(args):
         finally:
             net.close()
     elif case == "simp":
-        P = W.WORKLOADS["cantilever_120x60x30"]()
+        P = W.WORKLOADS[args.workload]()
         m = P.mesh
         params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
         with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params) as h:
