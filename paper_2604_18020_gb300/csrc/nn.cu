@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -316,6 +317,201 @@ __global__ void to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__
 
 unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
+// ---- 3x3x3 convolution on the tensor cores (implicit GEMM, tcgen05) ------
+//
+// out[co][v] = b[co] + sum_ci sum_k w[co][ci][k] in[ci][v + d_k] as the GEMM
+// D[128 voxels x N] = sum_k sum_ci A_k[voxel][ci] B_k[ci][co], N = a slice of
+// NS output channels, accumulated in FP32 in tensor memory.  A CTA computes an
+// output tile of 8 (x) x 16 (y) voxels of one z-plane (M = 128) and stages its
+// input halo tile, 10 x 18 x 3 voxels, 16 input channels at a time, as BF16 in
+// the canonical no-swizzle K-major layout: one 16-byte row per (voxel, 8
+// channels).  For tap (dx, dy, dz) the A operand is that staged tile read in
+// place: the core-matrix rows of output voxels x = 0..7 of one y-row are the
+// staged voxels x + dx of y-row y + dy (consecutive, 16 bytes apart), the
+// 8-row groups step one staged y-row (SBO = 160 bytes) and the two 8-channel
+// halves of the K = 16 step sit one channel part apart (LBO).  The FP32
+// activations are split into BF16 hi + lo (two products against the same
+// BF16 weights), so the result carries the activations to about 2^-16 and
+// the weights as stored.  Per stage one thread issues 27 taps x 2 parts
+// MMAs (M = 128, N = NS, K = 16), commits them to an mbarrier (bounded wait),
+// and the CTA stages the next 16 channels after they completed; three CTAs
+// per SM overlap one another's staging and MMAs.  The epilogue reads each
+// voxel's row of D with tcgen05.ld and writes bias + ReLU in FP32.
+constexpr int kCtTX = 8, kCtTY = 16;                  // output tile (M = 128)
+constexpr int kCtHX = kCtTX + 2, kCtHY = kCtTY + 2;   // staged halo tile, 3 z-planes
+constexpr int kCtPos = kCtHX * kCtHY * 3;             // 540 staged voxels
+constexpr int kCtPart = kCtPos * 16;                  // one 8-channel part: 8,640 bytes
+constexpr int kCtA = 4 * kCtPart;                     // hi 0-7, hi 8-15, lo 0-7, lo 8-15
+constexpr int kCtCin = 16;                            // input channels per stage
+constexpr uint32_t kCtSpin = 1u << 20;                // bound of the mbarrier wait
+template <int NS>
+struct CtShape {
+  static constexpr int B = 27 * 2 * (NS / 8) * 128;   // packed weights of one stage
+  static constexpr int COLS = NS < 32 ? 32 : NS;      // TMEM columns (allocation >= 32)
+  static constexpr int SMEM = kCtA + B + 128 + 128;   // + mbarrier / TMEM slot + alignment
+};
+
+// Packed weights of one 3x3x3 layer, slice by slice (NS output channels) and
+// stage by stage (16 input channels): [tap 27][kc 2][ng NS/8][r 8][c 8] BF16,
+// co = slice NS + 8 ng + r, ci = 16 stage + 8 kc + c, zero outside the layer
+// (B in the canonical K-major layout: N = output channels, K = input
+// channels; LBO = NS/8 x 128 bytes along K, SBO = 128 bytes along N).
+__global__ void pack_w3(const __nv_bfloat16* __restrict__ w, int Cin, int Cout, int NS, int S,
+                        size_t n, __nv_bfloat16* __restrict__ out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = (int)(i & 7), r = (int)((i >> 3) & 7);
+  size_t q = i >> 6;
+  const int ng = (int)(q % (NS / 8));
+  q /= NS / 8;
+  const int kc = (int)(q % 2);
+  q /= 2;
+  const int tap = (int)(q % 27);
+  q /= 27;
+  const int stage = (int)(q % S), slice = (int)(q / S);
+  const int co = slice * NS + 8 * ng + r, ci = 16 * stage + 8 * kc + c;
+  out[i] = (co < Cout && ci < Cin) ? w[((size_t)co * Cin + ci) * 27 + tap] : __float2bfloat16_rn(0.f);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128)
+conv3_tc(const float* __restrict__ in, int Cin, const __nv_bfloat16* __restrict__ wp,
+         const float* __restrict__ bias, float* __restrict__ out, int Cout, Dims d, int relu,
+         int tiles_x, int tiles_y, int32_t* err) {
+  using C = CtShape<NS>;
+  extern __shared__ __align__(16) unsigned char ct_raw[];
+  unsigned char* As = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(ct_raw) + 127) & ~(uintptr_t)127);
+  unsigned char* Bs = As + kCtA;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + C::B);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(Bs + C::B + 8);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int t = blockIdx.x;
+  const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, z = t / (tiles_x * tiles_y);
+  const int slice = blockIdx.y;
+  const int x0 = tx * kCtTX, y0 = ty * kCtTY;
+  const int S = (Cin + kCtCin - 1) / kCtCin;
+  const size_t V = (size_t)d.V();
+  if (warp == 0) {
+    tmem_alloc(tslot, C::COLS);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t a_addr = smem_u32(As), b_addr = smem_u32(Bs);
+  constexpr uint32_t IDESC = make_idesc(1u, 128, NS);
+  uint32_t phase = 0;
+  for (int s = 0; s < S; ++s) {
+    // A: (staged voxel, 8-channel group) units, FP32 -> BF16 hi and lo
+    for (int u = tid; u < 2 * kCtPos; u += 128) {
+      const int g = u >= kCtPos, pos = u - g * kCtPos;
+      const int xx = pos % kCtHX, yy = (pos / kCtHX) % kCtHY, zz = pos / (kCtHX * kCtHY);
+      const int gx = x0 - 1 + xx, gy = y0 - 1 + yy, gz = z - 1 + zz;
+      const bool inside = gx >= 0 && gy >= 0 && gz >= 0 && gx < d.W && gy < d.H && gz < d.D;
+      const int c0 = s * kCtCin + 8 * g;
+      const size_t vox = inside ? ((size_t)gz * d.H + gy) * d.W + gx : 0;
+      float v[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v[c] = (inside && c0 + c < Cin) ? in[(size_t)(c0 + c) * V + vox] : 0.f;
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+        hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+      }
+      *reinterpret_cast<uint4*>(As + g * kCtPart + pos * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(As + (2 + g) * kCtPart + pos * 16) =
+          make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    // B: the packed weights of this slice and stage
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(wp) + ((size_t)slice * S + s) * (C::B / 16);
+      uint4* dst = reinterpret_cast<uint4*>(Bs);
+      for (int i = tid; i < C::B / 16; i += 128) dst[i] = src[i];
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int tap = 0; tap < 27; ++tap) {
+        const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+        const uint32_t aoff = (uint32_t)(((dz * kCtHY + dy) * kCtHX + dx) * 16);
+        const uint64_t bd = smem_desc(b_addr + tap * (2 * (NS / 8) * 128), (NS / 8) * 128, 128);
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {   // activations hi, lo
+          const uint64_t ad = smem_desc(a_addr + part * 2 * kCtPart + aoff, kCtPart, kCtHX * 16);
+          mma_f16(tmem, ad, bd, IDESC, (s | tap | part) ? 1u : 0u);
+        }
+      }
+      mma_commit(bar);
+    }
+    // the next stage rewrites A and B: wait for these MMAs (one lane per warp
+    // polls; the warp barrier and the fence order the rest of the warp)
+    if ((tid & 31) == 0) {
+      uint32_t spins = 0;
+      bool ok;
+      while (!(ok = mbar_try_wait(bar, phase)))
+        if (++spins > kCtSpin) break;
+      if (!ok) {
+        atomicExch(err, 1);
+        for (uint32_t s2 = 0; s2 < kCtSpin && !mbar_try_wait(bar, phase); ++s2) {
+        }
+      }
+    }
+    __syncwarp();
+    phase ^= 1u;
+    tc_fence_after();
+  }
+  // epilogue: thread tid holds TMEM lane tid = output voxel (x0 + tid % 8, y0 + tid / 8)
+  float acc[NS];
+  const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+  if constexpr (NS == 16) {
+    tmem_ld16(lane_addr, acc);
+  } else {
+#pragma unroll
+    for (int h = 0; h < NS / 32; ++h) {
+      float part[32];
+      tmem_ld32(lane_addr + 32 * h, part);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[32 * h + j] = part[j];
+    }
+  }
+  tc_fence_before();
+  const int ox = x0 + (tid & 7), oy = y0 + (tid >> 3);
+  if (ox < d.W && oy < d.H) {
+    const size_t vox = ((size_t)z * d.H + oy) * d.W + ox;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const int co = slice * NS + j;
+      if (co < Cout) {
+        const float r = acc[j] + bias[co];
+        out[(size_t)co * V + vox] = relu ? fmaxf(r, 0.f) : r;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, C::COLS);
+}
+
+// output-channel slice of a layer: 16 for at most 16 channels, else 32
+int ct_ns(int cout) { return cout <= 16 ? 16 : 32; }
+size_t ct_packed_elems(int cin, int cout) {
+  const int ns = ct_ns(cout);
+  const size_t slices = (size_t)((cout + ns - 1) / ns), stages = (size_t)((cin + kCtCin - 1) / kCtCin);
+  return slices * stages * (size_t)(ns == 16 ? CtShape<16>::B : CtShape<32>::B) / 2;
+}
+
 }  // namespace
 
 __global__ void gate_relu_kernel(float* __restrict__ g, const float* __restrict__ act, size_t n) {
@@ -345,6 +541,13 @@ struct mfto_nn {
   size_t wpart_elems;
   double* lpart;                 // loss partials [2 kLossBlocks], loss, 1 / count
   float* dpred;                  // d loss / d output
+  // tensor-core 3x3x3 convolutions: weights packed per layer in the MMA
+  // layout (repacked after every weight change), offsets per layer, switch
+  __nv_bfloat16* wpack;
+  std::vector<size_t> wp_off;
+  bool wpack_dirty;
+  int tc_conv;                   // 1: 3x3x3 convolutions on tcgen05 (default), 0: SIMT FP32
+  int32_t* d_err;                // set when a tensor-core wait gave up
   int64_t launches;
   char msg[512];
 };
@@ -371,6 +574,22 @@ Dims level_dims(const Dims& d, int l) { return Dims{d.D >> l, d.H >> l, d.W >> l
 int chan(const mfto_nn* n, int l) { return n->base << l; }
 
 mfto_status conv_forward(mfto_nn* n, const NnLayer& L, const float* in, float* out, Dims d, int relu) {
+  if (L.k == 3 && n->tc_conv) {
+    const size_t li = (size_t)(&L - n->layers.data());
+    const int ns = ct_ns(L.cout);
+    const int tiles_x = (d.W + kCtTX - 1) / kCtTX, tiles_y = (d.H + kCtTY - 1) / kCtTY;
+    const dim3 grid((unsigned)((size_t)tiles_x * tiles_y * d.D), (unsigned)((L.cout + ns - 1) / ns));
+    const __nv_bfloat16* wp = n->wpack + n->wp_off[li];
+    n->launches++;
+    if (ns == 16)
+      conv3_tc<16><<<grid, 128, CtShape<16>::SMEM, n->stream>>>(in, L.cin, wp, n->w32 + L.b_off, out,
+                                                                L.cout, d, relu, tiles_x, tiles_y, n->d_err);
+    else
+      conv3_tc<32><<<grid, 128, CtShape<32>::SMEM, n->stream>>>(in, L.cin, wp, n->w32 + L.b_off, out,
+                                                                L.cout, d, relu, tiles_x, tiles_y, n->d_err);
+    NCUDA(n, cudaGetLastError());
+    return MFTO_OK;
+  }
   const dim3 grid(cdiv(d.V(), kNT), cdiv(L.cout, kCOB));
   n->launches++;
   if (L.k == 3)
@@ -419,9 +638,30 @@ mfto_status conv_backward(mfto_nn* n, const NnLayer& L, const float* in, const f
 // Block indices: encoders 0..L-2, bottleneck L-1, decoders L..2L-2 (level
 // L-2 .. 0).  Layer indices: block bi has convs 2 bi (a) and 2 bi + 1 (b);
 // the head is last.
+// the 3x3x3 layers' weights in the tensor-core kernel's layout
+mfto_status pack_weights(mfto_nn* n) {
+  for (size_t i = 0; i < n->layers.size(); ++i) {
+    const NnLayer& ly = n->layers[i];
+    if (ly.k != 3) continue;
+    const int ns = ct_ns(ly.cout);
+    const int S = (ly.cin + kCtCin - 1) / kCtCin;
+    const size_t cnt = ct_packed_elems(ly.cin, ly.cout);
+    n->launches++;
+    pack_w3<<<cdiv(cnt, 256), 256, 0, n->stream>>>(n->w16 + ly.w_off, ly.cin, ly.cout, ns, S, cnt,
+                                                   n->wpack + n->wp_off[i]);
+  }
+  NCUDA(n, cudaGetLastError());
+  n->wpack_dirty = false;
+  return MFTO_OK;
+}
+
 mfto_status net_forward(mfto_nn* n, const float* x, float* out, Dims d) {
   const int L = n->levels;
   mfto_status s = MFTO_OK;
+  if (n->tc_conv && n->wpack_dirty) {
+    s = pack_weights(n);
+    if (s != MFTO_OK) return s;
+  }
   for (int l = 0; l < L - 1; ++l) {                         // encoders
     const Dims dl = level_dims(d, l);
     if (l == 0) {
@@ -550,7 +790,7 @@ void free_nn(mfto_nn* n) {
   if (!n) return;
   for (float* p : n->bufs)
     if (p) cudaFree(p);
-  void* ptrs[] = {n->w32, n->grad, n->m1, n->m2, n->w16, n->gbuf0, n->gbuf1, n->gbuf2, n->wpart,
+  void* ptrs[] = {n->wpack, n->d_err, n->w32, n->grad, n->m1, n->m2, n->w16, n->gbuf0, n->gbuf1, n->gbuf2, n->wpart,
                   n->lpart, n->dpred};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -635,6 +875,18 @@ extern "C" mfto_status mfto_nn_create(int32_t base, int32_t levels, int64_t max_
     A((void**)&n->dpred, sizeof(float) * (size_t)(n->out_ch * TV));
   }
   A((void**)&n->lpart, sizeof(double) * (2 * kLossBlocks + 2));
+  {
+    size_t pk = 0;
+    n->wp_off.assign(n->layers.size(), 0);
+    for (size_t i = 0; i < n->layers.size(); ++i) {
+      n->wp_off[i] = pk;
+      if (n->layers[i].k == 3) pk += ct_packed_elems(n->layers[i].cin, n->layers[i].cout);
+    }
+    A((void**)&n->wpack, sizeof(__nv_bfloat16) * (pk + 8));
+    A((void**)&n->d_err, sizeof(int32_t));
+    n->tc_conv = 1;
+    n->wpack_dirty = true;
+  }
   if (!ok) {
     cudaGetLastError();
     free_nn(n);
@@ -654,7 +906,16 @@ extern "C" mfto_status mfto_nn_create(int32_t base, int32_t levels, int64_t max_
     return MFTO_CUDA_ERROR;
   }
   to_bf16<<<cdiv(off, 256), 256, 0, n->stream>>>(n->w32, n->w16, off);
-  if (cudaStreamSynchronize(n->stream) != cudaSuccess) { free_nn(n); return MFTO_CUDA_ERROR; }
+  if (cudaMemsetAsync(n->d_err, 0, sizeof(int32_t), n->stream) != cudaSuccess ||
+      cudaFuncSetAttribute(conv3_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           CtShape<16>::SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(conv3_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           CtShape<32>::SMEM) != cudaSuccess ||
+      cudaStreamSynchronize(n->stream) != cudaSuccess) {
+    cudaGetLastError();
+    free_nn(n);
+    return MFTO_CUDA_ERROR;
+  }
   *out = n;
   return MFTO_OK;
 }
@@ -687,9 +948,23 @@ extern "C" mfto_status mfto_nn_set_params(mfto_nn* n, const float* h_in) {
   to_bf16<<<cdiv(n->n_params, 256), 256, 0, n->stream>>>(n->w32, n->w16, n->n_params);
   NCUDA(n, cudaGetLastError());
   NCUDA(n, cudaStreamSynchronize(n->stream));
+  n->wpack_dirty = true;
   n->adam_t = 0;
   NCUDA(n, cudaMemsetAsync(n->m1, 0, sizeof(float) * n->n_params, n->stream));
   NCUDA(n, cudaMemsetAsync(n->m2, 0, sizeof(float) * n->n_params, n->stream));
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_nn_set_tensor_cores(mfto_nn* n, int32_t on) {
+  if (!n || (on != 0 && on != 1)) return MFTO_INVALID_ARG;
+  n->tc_conv = on;
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_nn_tc_status(mfto_nn* n, int32_t* gave_up) {
+  if (!n || !gave_up) return MFTO_INVALID_ARG;
+  NCUDA(n, cudaMemcpyAsync(gave_up, n->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, n->stream));
+  NCUDA(n, cudaStreamSynchronize(n->stream));
   return MFTO_OK;
 }
 
@@ -710,6 +985,7 @@ mfto_status adam(mfto_nn* n, float lr) {
   adam_step<<<cdiv(n->n_params, 256), 256, 0, n->stream>>>(n->w32, n->w16, n->grad, n->m1, n->m2,
                                                            n->n_params, lr, b1, b2, 1e-8f, c1, c2);
   NCUDA(n, cudaGetLastError());
+  n->wpack_dirty = true;
   return MFTO_OK;
 }
 

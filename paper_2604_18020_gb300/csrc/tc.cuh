@@ -1,6 +1,7 @@
 // Thin wrappers over the sm_100-family tensor-core PTX used by the tcgen05
-// K.v (kv_tc.cu): TMEM allocation, shared-memory matrix descriptors,
-// tcgen05.mma / commit / ld, mbarriers and the proxy fences between them.
+// kernels (the K.v forms of kv_tc.cu and kv_tcol.cuh, the U-Net convolutions
+// of nn.cu): TMEM allocation, shared-memory matrix descriptors, tcgen05.mma /
+// commit / ld, mbarriers and the proxy fences between them.
 #pragma once
 #include <stdint.h>
 
@@ -111,6 +112,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
       : "r"(taddr) : "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane, completed before
+// returning.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr) : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // round-to-nearest (ties away) to TF32, kept in an FP32 container

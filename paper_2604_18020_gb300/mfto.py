@@ -198,6 +198,8 @@ SIGNATURES = {
     "mfto_nn_train_step": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P,
                                        C.c_float, C.POINTER(C.c_double)]),
     "mfto_nn_launch_count": (C.c_int32, [_P, C.POINTER(C.c_int64)]),
+    "mfto_nn_set_tensor_cores": (C.c_int32, [_P, C.c_int32]),
+    "mfto_nn_tc_status": (C.c_int32, [_P, C.POINTER(C.c_int32)]),
     "mfto_nn_grid": (C.c_int32, [C.POINTER(Mesh), C.c_int32, _P]),
     "mfto_nn_features": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     "mfto_nn_target": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
@@ -761,6 +763,17 @@ class Net:
         if params.size != self.num_params:
             raise ValueError(f"expected {self.num_params} parameters, got {params.size}")
         self._chk("mfto_nn_set_params", lib().mfto_nn_set_params(self._n, params.ctypes.data))
+
+    def set_tensor_cores(self, on: bool):
+        """3x3x3 convolutions of the forward pass on tcgen05 (True, default)
+        or on the FP32 FMA pipe (False)."""
+        self._chk("mfto_nn_set_tensor_cores", lib().mfto_nn_set_tensor_cores(self._n, int(bool(on))))
+
+    def tc_gave_up(self) -> bool:
+        """True if a tensor-core convolution gave up waiting for its MMAs."""
+        v = C.c_int32()
+        self._chk("mfto_nn_tc_status", lib().mfto_nn_tc_status(self._n, C.byref(v)))
+        return bool(v.value)
 
     def forward(self, x, out, dims):
         import torch

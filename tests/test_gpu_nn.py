@@ -56,6 +56,32 @@ def test_forward_matches_oracle(cuda, base, dims):
     assert rel_err(got, ref) <= 1e-4
 
 
+def test_forward_tensor_cores_match_fma_pipe(cuda):
+    """The tcgen05 implicit-GEMM convolutions (activations split into BF16 hi +
+    lo) against the FP32 FMA-pipe ones, on a grid whose tiles are ragged in x
+    and y, at the learned part's width (14 .. 112 channels: one and several
+    output-channel slices, one and several 16-channel input stages); both
+    within 1e-4 of each other, the tensor-core pass bit-identical on repeat
+    and without a given-up wait."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    dims = (16, 40, 24)
+    D, H, Wd = dims
+    V = D * H * Wd
+    net = mfto.Net(base=14, levels=4, max_voxels=V, seed=3)
+    x = torch.randn(4 * V, generator=torch.Generator().manual_seed(4)).to(cuda)
+    outs = []
+    for tc in (True, True, False):
+        net.set_tensor_cores(tc)
+        out = torch.zeros(3 * V, dtype=torch.float32, device=cuda)
+        net.forward(x, out, dims)
+        outs.append(out.cpu().numpy())
+    assert not net.tc_gave_up()
+    assert np.array_equal(outs[0], outs[1])
+    assert rel_err(outs[0], outs[2].astype(np.float64)) <= 1e-4
+    assert np.abs(outs[2]).max() > 0
+
+
 def test_gradients_match_oracle(cuda):
     import torch
     from paper_2604_18020_gb300 import mfto
