@@ -734,7 +734,8 @@ def kernel_case_run(args):
       multi   the 8-load-case mixed solve, 100 x 50 x 50 (inner CG capped);
       batch   the 64 uneven instances' batched mixed solve;
       nn      U-Net forward and gradient on the 136 x 72 x 40 node grid of a
-              128 x 64 x 32 mesh (the learned part's training size);
+              128 x 64 x 32 mesh (the learned part's training size), or forward
+              passes on the node grid of --workload's mesh;
       simp    two SIMP iterations (filter, solve, compliance, OC) on --workload."""
     import numpy as np
     import torch
@@ -779,9 +780,16 @@ def kernel_case_run(args):
             b.kv(Eb.float(), Ub.float(), Y, form=mfto.FORM_F32)
             torch.cuda.synchronize()
     elif case == "nn":
-        dims = mfto.nn_grid(128, 64, 32)
+        # the training mesh 128 x 64 x 32 by default (forward and gradient);
+        # with --workload another mesh, forward passes only above 2M voxels
+        mesh = (128, 64, 32)
+        if args.workload != WORKLOAD:
+            pm = W.WORKLOADS[args.workload]().mesh
+            mesh = (pm.nelx, pm.nely, pm.nelz)
+        dims = mfto.nn_grid(*mesh)
         V = int(np.prod(dims))
-        net = mfto.Net(base=14, levels=4, max_voxels=V, max_train_voxels=V, seed=0)
+        train = V <= 2_000_000
+        net = mfto.Net(base=14, levels=4, max_voxels=V, max_train_voxels=V if train else 0, seed=0)
         try:
             g = torch.Generator(device="cpu").manual_seed(0)
             x = torch.rand(4 * V, generator=g).to(dev)
@@ -790,7 +798,8 @@ def kernel_case_run(args):
             out = torch.empty(3 * V, device=dev)
             for _ in range(2):
                 net.forward(x, out, dims)
-                net.gradient(x, t, mask, dims)
+                if train:
+                    net.gradient(x, t, mask, dims)
             torch.cuda.synchronize()
         finally:
             net.close()

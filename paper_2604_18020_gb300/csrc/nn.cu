@@ -386,11 +386,9 @@ conv3_tc(const float* __restrict__ in, int Cin, const __nv_bfloat16* __restrict_
   uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + C::B);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(Bs + C::B + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int t = blockIdx.x;
-  const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, z = t / (tiles_x * tiles_y);
   const int slice = blockIdx.y;
-  const int x0 = tx * kCtTX, y0 = ty * kCtTY;
   const int S = (Cin + kCtCin - 1) / kCtCin;
+  const int ntiles = tiles_x * tiles_y * d.D;
   const size_t V = (size_t)d.V();
   if (warp == 0) {
     tmem_alloc(tslot, C::COLS);
@@ -407,100 +405,122 @@ conv3_tc(const float* __restrict__ in, int Cin, const __nv_bfloat16* __restrict_
   const uint32_t a_addr = smem_u32(As), b_addr = smem_u32(Bs);
   constexpr uint32_t IDESC = make_idesc(1u, 128, NS);
   uint32_t phase = 0;
-  for (int s = 0; s < S; ++s) {
-    // A: (staged voxel, 8-channel group) units, FP32 -> BF16 hi and lo
-    for (int u = tid; u < 2 * kCtPos; u += 128) {
-      const int g = u >= kCtPos, pos = u - g * kCtPos;
-      const int xx = pos % kCtHX, yy = (pos / kCtHX) % kCtHY, zz = pos / (kCtHX * kCtHY);
-      const int gx = x0 - 1 + xx, gy = y0 - 1 + yy, gz = z - 1 + zz;
-      const bool inside = gx >= 0 && gy >= 0 && gz >= 0 && gx < d.W && gy < d.H && gz < d.D;
-      const int c0 = s * kCtCin + 8 * g;
-      const size_t vox = inside ? ((size_t)gz * d.H + gy) * d.W + gx : 0;
-      float v[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) v[c] = (inside && c0 + c < Cin) ? in[(size_t)(c0 + c) * V + vox] : 0.f;
-      uint32_t hi[4], lo[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
-        hi[q] = *reinterpret_cast<const uint32_t*>(&h);
-        lo[q] = *reinterpret_cast<const uint32_t*>(&l);
-      }
-      *reinterpret_cast<uint4*>(As + g * kCtPart + pos * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(As + (2 + g) * kCtPart + pos * 16) =
-          make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    }
-    // B: the packed weights of this slice and stage
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(wp) + ((size_t)slice * S + s) * (C::B / 16);
-      uint4* dst = reinterpret_cast<uint4*>(Bs);
-      for (int i = tid; i < C::B / 16; i += 128) dst[i] = src[i];
-    }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
+  // staging assignment, the same for every tile and stage: thread t < 120
+  // owns staged column xx = t % 10 of rows r = t / 10 + 12 k (row r = z-plane
+  // r / 18, y-row r % 18 of the halo tile), for both 8-channel groups
+  const bool stager = tid < 120;
+  const int xx = tid % kCtHX, r0 = tid / kCtHX;
+  auto stage_b = [&](int s) {
+    const uint4* src = reinterpret_cast<const uint4*>(wp) + ((size_t)slice * S + s) * (C::B / 16);
+    uint4* dst = reinterpret_cast<uint4*>(Bs);
+    for (int i = tid; i < C::B / 16; i += 128) dst[i] = src[i];
+  };
+  if (S == 1) stage_b(0);   // one stage: the weights stay for every tile
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, z = t / (tiles_x * tiles_y);
+    const int x0 = tx * kCtTX, y0 = ty * kCtTY;
+    const int gx = x0 - 1 + xx;
+    const bool xin = gx >= 0 && gx < d.W;
+    for (int s = 0; s < S; ++s) {
+      if (stager) {
 #pragma unroll 1
-      for (int tap = 0; tap < 27; ++tap) {
-        const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
-        const uint32_t aoff = (uint32_t)(((dz * kCtHY + dy) * kCtHX + dx) * 16);
-        const uint64_t bd = smem_desc(b_addr + tap * (2 * (NS / 8) * 128), (NS / 8) * 128, 128);
+        for (int r = r0; r < 3 * kCtHY; r += 12) {
+          const int zz = r / kCtHY, yy = r - zz * kCtHY;
+          const int gy = y0 - 1 + yy, gz = z - 1 + zz;
+          const bool inside = xin && gy >= 0 && gz >= 0 && gy < d.H && gz < d.D;
+          const size_t vox = inside ? ((size_t)gz * d.H + gy) * d.W + gx : 0;
+          const int pos = r * kCtHX + xx;
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {   // activations hi, lo
-          const uint64_t ad = smem_desc(a_addr + part * 2 * kCtPart + aoff, kCtPart, kCtHX * 16);
-          mma_f16(tmem, ad, bd, IDESC, (s | tap | part) ? 1u : 0u);
+          for (int g = 0; g < 2; ++g) {
+            const int c0 = s * kCtCin + 8 * g;
+            const float* p = in + (size_t)c0 * V + vox;
+            float v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[c] = (inside && c0 + c < Cin) ? p[(size_t)c * V] : 0.f;
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+              hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+              lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+            *reinterpret_cast<uint4*>(As + g * kCtPart + pos * 16) =
+                make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(As + (2 + g) * kCtPart + pos * 16) =
+                make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          }
         }
       }
-      mma_commit(bar);
-    }
-    // the next stage rewrites A and B: wait for these MMAs (one lane per warp
-    // polls; the warp barrier and the fence order the rest of the warp)
-    if ((tid & 31) == 0) {
-      uint32_t spins = 0;
-      bool ok;
-      while (!(ok = mbar_try_wait(bar, phase)))
-        if (++spins > kCtSpin) break;
-      if (!ok) {
-        atomicExch(err, 1);
-        for (uint32_t s2 = 0; s2 < kCtSpin && !mbar_try_wait(bar, phase); ++s2) {
+      if (S > 1) stage_b(s);
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+          const uint32_t aoff = (uint32_t)(((dz * kCtHY + dy) * kCtHX + dx) * 16);
+          const uint64_t bd = smem_desc(b_addr + tap * (2 * (NS / 8) * 128), (NS / 8) * 128, 128);
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {   // activations hi, lo
+            const uint64_t ad = smem_desc(a_addr + part * 2 * kCtPart + aoff, kCtPart, kCtHX * 16);
+            mma_f16(tmem, ad, bd, IDESC, (s | tap | part) ? 1u : 0u);
+          }
+        }
+        mma_commit(bar);
+      }
+      // the next stage (or tile) rewrites A and B, the epilogue reads D: wait
+      // for these MMAs (one lane per warp polls; the warp barrier and the
+      // fence order the rest of the warp)
+      if ((tid & 31) == 0) {
+        uint32_t spins = 0;
+        bool ok;
+        while (!(ok = mbar_try_wait(bar, phase)))
+          if (++spins > kCtSpin) break;
+        if (!ok) {
+          atomicExch(err, 1);
+          for (uint32_t s2 = 0; s2 < kCtSpin && !mbar_try_wait(bar, phase); ++s2) {
+          }
         }
       }
+      __syncwarp();
+      phase ^= 1u;
+      tc_fence_after();
     }
-    __syncwarp();
-    phase ^= 1u;
-    tc_fence_after();
-  }
-  // epilogue: thread tid holds TMEM lane tid = output voxel (x0 + tid % 8, y0 + tid / 8)
-  float acc[NS];
-  const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
-  if constexpr (NS == 16) {
-    tmem_ld16(lane_addr, acc);
-  } else {
+    // epilogue: thread tid holds TMEM lane tid = output voxel (x0 + tid % 8, y0 + tid / 8)
+    float acc[NS];
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+    if constexpr (NS == 16) {
+      tmem_ld16(lane_addr, acc);
+    } else {
 #pragma unroll
-    for (int h = 0; h < NS / 32; ++h) {
-      float part[32];
-      tmem_ld32(lane_addr + 32 * h, part);
+      for (int h = 0; h < NS / 32; ++h) {
+        float part[32];
+        tmem_ld32(lane_addr + 32 * h, part);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[32 * h + j] = part[j];
+        for (int j = 0; j < 32; ++j) acc[32 * h + j] = part[j];
+      }
+    }
+    tc_fence_before();   // the next tile's first MMA overwrites D after the next barrier
+    const int ox = x0 + (tid & 7), oy = y0 + (tid >> 3);
+    if (ox < d.W && oy < d.H) {
+      const size_t vox = ((size_t)z * d.H + oy) * d.W + ox;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const int co = slice * NS + j;
+        if (co < Cout) {
+          const float r = acc[j] + bias[co];
+          out[(size_t)co * V + vox] = relu ? fmaxf(r, 0.f) : r;
+        }
+      }
     }
   }
   tc_fence_before();
-  const int ox = x0 + (tid & 7), oy = y0 + (tid >> 3);
-  if (ox < d.W && oy < d.H) {
-    const size_t vox = ((size_t)z * d.H + oy) * d.W + ox;
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      const int co = slice * NS + j;
-      if (co < Cout) {
-        const float r = acc[j] + bias[co];
-        out[(size_t)co * V + vox] = relu ? fmaxf(r, 0.f) : r;
-      }
-    }
-  }
   __syncthreads();
+  tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, C::COLS);
 }
 
@@ -548,6 +568,7 @@ struct mfto_nn {
   bool wpack_dirty;
   int tc_conv;                   // 1: 3x3x3 convolutions on tcgen05 (default), 0: SIMT FP32
   int32_t* d_err;                // set when a tensor-core wait gave up
+  int num_sms;
   int64_t launches;
   char msg[512];
 };
@@ -578,7 +599,11 @@ mfto_status conv_forward(mfto_nn* n, const NnLayer& L, const float* in, float* o
     const size_t li = (size_t)(&L - n->layers.data());
     const int ns = ct_ns(L.cout);
     const int tiles_x = (d.W + kCtTX - 1) / kCtTX, tiles_y = (d.H + kCtTY - 1) / kCtTY;
-    const dim3 grid((unsigned)((size_t)tiles_x * tiles_y * d.D), (unsigned)((L.cout + ns - 1) / ns));
+    // persistent CTAs: as many as fit on the GPU (shared memory: 4 per SM for
+    // 16-channel slices, 3 for 32), at most one per tile
+    const size_t tiles = (size_t)tiles_x * tiles_y * d.D;
+    const size_t fit = (size_t)n->num_sms * (ns == 16 ? 4 : 3);
+    const dim3 grid((unsigned)(tiles < fit ? tiles : fit), (unsigned)((L.cout + ns - 1) / ns));
     const __nv_bfloat16* wp = n->wpack + n->wp_off[li];
     n->launches++;
     if (ns == 16)
@@ -886,6 +911,10 @@ extern "C" mfto_status mfto_nn_create(int32_t base, int32_t levels, int64_t max_
     A((void**)&n->d_err, sizeof(int32_t));
     n->tc_conv = 1;
     n->wpack_dirty = true;
+    int dev = 0;
+    n->num_sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, dev);
   }
   if (!ok) {
     cudaGetLastError();
