@@ -423,7 +423,7 @@ conv3_tc(const float* __restrict__ in, int Cin, const __nv_bfloat16* __restrict_
     const bool xin = gx >= 0 && gx < d.W;
     for (int s = 0; s < S; ++s) {
       if (stager) {
-#pragma unroll 1
+#pragma unroll 2
         for (int r = r0; r < 3 * kCtHY; r += 12) {
           const int zz = r / kCtHY, yy = r - zz * kCtHY;
           const int gy = y0 - 1 + yy, gz = z - 1 + zz;
@@ -478,8 +478,12 @@ conv3_tc(const float* __restrict__ in, int Cin, const __nv_bfloat16* __restrict_
       if ((tid & 31) == 0) {
         uint32_t spins = 0;
         bool ok;
-        while (!(ok = mbar_try_wait(bar, phase)))
+        // back off between polls: the other CTAs of the SM need the issue
+        // slots for their staging while these MMAs run
+        while (!(ok = mbar_try_wait(bar, phase))) {
           if (++spins > kCtSpin) break;
+          __nanosleep(128);
+        }
         if (!ok) {
           atomicExch(err, 1);
           for (uint32_t s2 = 0; s2 < kCtSpin && !mbar_try_wait(bar, phase); ++s2) {
