@@ -1042,6 +1042,72 @@ def learned_run(args):
     h.close()
 
 
+def unet_run(args):
+    """U-Net timing, tensor-core convolutions against the FMA-pipe ones: the
+    forward pass on the node grid of the learned workload's 256 x 128 x 150
+    mesh (264 x 136 x 152 voxels) and forward + gradient on the training
+    grid of a 128 x 64 x 32 mesh (136 x 72 x 40), base width 14, 4 levels;
+    device time from CUDA events, median of 5 calls after 2 warm-ups.  One
+    JSON line per grid and setting."""
+    import numpy as np
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    def forward_flops(V, base=14, levels=4, cin=4, cout=3):
+        # 2 flop per multiply-add: 27 taps per 3x3x3 layer, one per 1x1x1
+        f, prev = 0, cin
+        for l in range(levels - 1):                      # encoders
+            c = base << l
+            f += 2 * 27 * (prev * c + c * c) * (V >> (3 * l))
+            prev = c
+        cb, Vb = base << (levels - 1), V >> (3 * (levels - 1))
+        f += 2 * 27 * (prev * cb + cb * cb) * Vb          # bottleneck
+        for l in range(levels - 2, -1, -1):               # decoders
+            c = base << l
+            f += 2 * 27 * (((base << (l + 1)) + c) * c + c * c) * (V >> (3 * l))
+        return f + 2 * base * cout * V                    # head
+
+    for mesh, train in (((256, 128, 150), False), ((128, 64, 32), True)):
+        dims = mfto.nn_grid(*mesh)
+        V = int(np.prod(dims))
+        net = mfto.Net(base=14, levels=4, max_voxels=V, max_train_voxels=V if train else 0, seed=0)
+        try:
+            g = torch.Generator(device="cpu").manual_seed(0)
+            x = torch.rand(4 * V, generator=g).to(dev)
+            t = torch.rand(3 * V, generator=g).to(dev)
+            mask = torch.ones(3 * V, device=dev)
+            out = torch.empty(3 * V, device=dev)
+            for tc in (True, False):
+                net.set_tensor_cores(tc)
+                fwd = timed(lambda: net.forward(x, out, dims))
+                rec = {"case": "unet_b14_l4", "grid": list(dims), "voxels": V,
+                       "tensor_cores": tc, "forward_ms": fwd,
+                       "forward_gflop": forward_flops(V) / 1e9}
+                rec["forward_tflops"] = rec["forward_gflop"] / fwd
+                if train:
+                    # gradient: forward + backward, synchronised by the call
+                    rec["gradient_ms"] = timed(lambda: net.gradient(x, t, mask, dims))
+                rec["gave_up"] = net.tc_gave_up()
+                print(json.dumps(rec), flush=True)
+        finally:
+            net.close()
+
+
 def kappa_run(args):
     """kappa(K) on the free DOFs by power and inverse iteration (the paper's
     caps and tolerances, start vectors from seeds 42 and 123) for the paper's
@@ -1447,7 +1513,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench",
                     choices=["bench", "profile", "pcg", "cgkv", "kernels", "compare", "learned",
-                             "kappa", "protocol", "hard", "ubench", "gmg", "scaling"])
+                             "kappa", "protocol", "hard", "ubench", "gmg", "scaling", "unet"])
     ap.add_argument("--case", default="simp", choices=["tc", "multi", "batch", "nn", "simp"],
                     help="--mode kernels: the kernel family to run")
     ap.add_argument("--protocol-iters", type=int, default=120)
@@ -1503,6 +1569,9 @@ def main():
         return
     if args.mode == "learned":
         learned_run(args)
+        return
+    if args.mode == "unet":
+        unet_run(args)
         return
     if args.mode == "kappa":
         kappa_run(args)

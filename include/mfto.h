@@ -453,11 +453,15 @@ mfto_status mfto_nn_num_params(const mfto_nn* n, int64_t* count);
 /* host copies of the FP32 parameter vector (set_params also resets Adam) */
 mfto_status mfto_nn_get_params(mfto_nn* n, float* h_out);
 mfto_status mfto_nn_set_params(mfto_nn* n, const float* h_in);
-/* Where the 3x3x3 convolutions of the forward pass run: 1 (default) on the
- * tcgen05 tensor cores as implicit GEMMs (BF16 weights; FP32 activations
- * split into BF16 hi + lo, two products; FP32 accumulation in tensor
- * memory), 0 on the FP32 FMA pipe.  The backward passes run on the FMA pipe
- * either way.  No paper counterpart (the learned part is this library's). */
+/* Where the 3x3x3 convolutions run: 1 (default) on the tcgen05 tensor cores
+ * as implicit GEMMs (BF16 weights; FP32 activations split into BF16 hi + lo,
+ * two products; FP32 accumulation in tensor memory), 0 on the FP32 FMA pipe.
+ * The switch covers the forward pass and, for networks created with
+ * max_train_voxels > 0, the data gradient of the backward pass (the adjoint
+ * convolution: channel roles swapped, taps mirrored, the ReLU gate applied in
+ * its epilogue); weight and bias gradients and the 1x1x1 head run on the FMA
+ * pipe either way.  No paper counterpart (the learned part is this
+ * library's). */
 mfto_status mfto_nn_set_tensor_cores(mfto_nn* n, int32_t on);
 /* *gave_up = 1 if a tensor-core convolution stopped waiting for its MMAs
  * (bounded wait, about a second; its output is then not to be used), else

@@ -336,7 +336,10 @@ unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 // MMAs (M = 128, N = NS, K = 16), commits them to an mbarrier (bounded wait),
 // and the CTA stages the next 16 channels after they completed; three CTAs
 // per SM overlap one another's staging and MMAs.  The epilogue reads each
-// voxel's row of D with tcgen05.ld and writes bias + ReLU in FP32.
+// voxel's row of D with tcgen05.ld and writes bias + ReLU in FP32 (bias may
+// be NULL; with gate given, outputs whose gate value is not positive are
+// zero: the ReLU adjoint of the data gradient, which runs through this
+// kernel with the adjoint weights of pack_w3).
 constexpr int kCtTX = 8, kCtTY = 16;                  // output tile (M = 128)
 constexpr int kCtHX = kCtTX + 2, kCtHY = kCtTY + 2;   // staged halo tile, 3 z-planes
 constexpr int kCtPos = kCtHX * kCtHY * 3;             // 540 staged voxels
@@ -356,8 +359,12 @@ struct CtShape {
 // co = slice NS + 8 ng + r, ci = 16 stage + 8 kc + c, zero outside the layer
 // (B in the canonical K-major layout: N = output channels, K = input
 // channels; LBO = NS/8 x 128 bytes along K, SBO = 128 bytes along N).
+// With transpose set, the layer packed is the adjoint of a stored layer with
+// Cout inputs and Cin outputs: w'[co][ci][tap] = w[ci][co][26 - tap] (the data
+// gradient of a zero-padded 3x3x3 convolution is the zero-padded convolution
+// with the channel roles swapped and the taps mirrored).
 __global__ void pack_w3(const __nv_bfloat16* __restrict__ w, int Cin, int Cout, int NS, int S,
-                        size_t n, __nv_bfloat16* __restrict__ out) {
+                        size_t n, int transpose, __nv_bfloat16* __restrict__ out) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int c = (int)(i & 7), r = (int)((i >> 3) & 7);
@@ -370,14 +377,16 @@ __global__ void pack_w3(const __nv_bfloat16* __restrict__ w, int Cin, int Cout, 
   q /= 27;
   const int stage = (int)(q % S), slice = (int)(q / S);
   const int co = slice * NS + 8 * ng + r, ci = 16 * stage + 8 * kc + c;
-  out[i] = (co < Cout && ci < Cin) ? w[((size_t)co * Cin + ci) * 27 + tap] : __float2bfloat16_rn(0.f);
+  const size_t src = transpose ? ((size_t)ci * Cout + co) * 27 + (26 - tap)
+                               : ((size_t)co * Cin + ci) * 27 + tap;
+  out[i] = (co < Cout && ci < Cin) ? w[src] : __float2bfloat16_rn(0.f);
 }
 
 template <int NS>
 __global__ void __launch_bounds__(128)
 conv3_tc(const float* __restrict__ in, int Cin, const __nv_bfloat16* __restrict__ wp,
          const float* __restrict__ bias, float* __restrict__ out, int Cout, Dims d, int relu,
-         int tiles_x, int tiles_y, int32_t* err) {
+         const float* __restrict__ gate, int tiles_x, int tiles_y, int32_t* err) {
   using C = CtShape<NS>;
   extern __shared__ __align__(16) unsigned char ct_raw[];
   unsigned char* As = reinterpret_cast<unsigned char*>(
@@ -516,8 +525,10 @@ conv3_tc(const float* __restrict__ in, int Cin, const __nv_bfloat16* __restrict_
       for (int j = 0; j < NS; ++j) {
         const int co = slice * NS + j;
         if (co < Cout) {
-          const float r = acc[j] + bias[co];
-          out[(size_t)co * V + vox] = relu ? fmaxf(r, 0.f) : r;
+          float r = bias ? acc[j] + bias[co] : acc[j];
+          if (relu) r = fmaxf(r, 0.f);
+          if (gate && !(gate[(size_t)co * V + vox] > 0.f)) r = 0.f;
+          out[(size_t)co * V + vox] = r;
         }
       }
     }
@@ -569,6 +580,8 @@ struct mfto_nn {
   // layout (repacked after every weight change), offsets per layer, switch
   __nv_bfloat16* wpack;
   std::vector<size_t> wp_off;
+  __nv_bfloat16* wpack_t;        // adjoint layers for the data gradient (training only)
+  std::vector<size_t> wpt_off;
   bool wpack_dirty;
   int tc_conv;                   // 1: 3x3x3 convolutions on tcgen05 (default), 0: SIMT FP32
   int32_t* d_err;                // set when a tensor-core wait gave up
@@ -598,26 +611,34 @@ float* slot(mfto_nn* n, int bi, int s) { return n->bufs[3 * bi + s]; }
 Dims level_dims(const Dims& d, int l) { return Dims{d.D >> l, d.H >> l, d.W >> l}; }
 int chan(const mfto_nn* n, int l) { return n->base << l; }
 
+// One 3x3x3 convolution on the tensor cores: cin -> cout channels with the
+// packed weights wp (bias and gate may be NULL).
+mfto_status conv3_tc_launch(mfto_nn* n, const float* in, int cin, const __nv_bfloat16* wp,
+                            const float* bias, float* out, int cout, Dims d, int relu,
+                            const float* gate) {
+  const int ns = ct_ns(cout);
+  const int tiles_x = (d.W + kCtTX - 1) / kCtTX, tiles_y = (d.H + kCtTY - 1) / kCtTY;
+  // persistent CTAs: as many as fit on the GPU (shared memory: 4 per SM for
+  // 16-channel slices, 3 for 32), at most one per tile
+  const size_t tiles = (size_t)tiles_x * tiles_y * d.D;
+  const size_t fit = (size_t)n->num_sms * (ns == 16 ? 4 : 3);
+  const dim3 grid((unsigned)(tiles < fit ? tiles : fit), (unsigned)((cout + ns - 1) / ns));
+  n->launches++;
+  if (ns == 16)
+    conv3_tc<16><<<grid, 128, CtShape<16>::SMEM, n->stream>>>(in, cin, wp, bias, out, cout, d, relu,
+                                                              gate, tiles_x, tiles_y, n->d_err);
+  else
+    conv3_tc<32><<<grid, 128, CtShape<32>::SMEM, n->stream>>>(in, cin, wp, bias, out, cout, d, relu,
+                                                              gate, tiles_x, tiles_y, n->d_err);
+  NCUDA(n, cudaGetLastError());
+  return MFTO_OK;
+}
+
 mfto_status conv_forward(mfto_nn* n, const NnLayer& L, const float* in, float* out, Dims d, int relu) {
   if (L.k == 3 && n->tc_conv) {
     const size_t li = (size_t)(&L - n->layers.data());
-    const int ns = ct_ns(L.cout);
-    const int tiles_x = (d.W + kCtTX - 1) / kCtTX, tiles_y = (d.H + kCtTY - 1) / kCtTY;
-    // persistent CTAs: as many as fit on the GPU (shared memory: 4 per SM for
-    // 16-channel slices, 3 for 32), at most one per tile
-    const size_t tiles = (size_t)tiles_x * tiles_y * d.D;
-    const size_t fit = (size_t)n->num_sms * (ns == 16 ? 4 : 3);
-    const dim3 grid((unsigned)(tiles < fit ? tiles : fit), (unsigned)((L.cout + ns - 1) / ns));
-    const __nv_bfloat16* wp = n->wpack + n->wp_off[li];
-    n->launches++;
-    if (ns == 16)
-      conv3_tc<16><<<grid, 128, CtShape<16>::SMEM, n->stream>>>(in, L.cin, wp, n->w32 + L.b_off, out,
-                                                                L.cout, d, relu, tiles_x, tiles_y, n->d_err);
-    else
-      conv3_tc<32><<<grid, 128, CtShape<32>::SMEM, n->stream>>>(in, L.cin, wp, n->w32 + L.b_off, out,
-                                                                L.cout, d, relu, tiles_x, tiles_y, n->d_err);
-    NCUDA(n, cudaGetLastError());
-    return MFTO_OK;
+    return conv3_tc_launch(n, in, L.cin, n->wpack + n->wp_off[li], n->w32 + L.b_off, out, L.cout, d,
+                           relu, nullptr);
   }
   const dim3 grid(cdiv(d.V(), kNT), cdiv(L.cout, kCOB));
   n->launches++;
@@ -652,7 +673,13 @@ mfto_status conv_backward(mfto_nn* n, const NnLayer& L, const float* in, const f
   sum_chunks<<<cdiv(nw, 256), 256, 0, n->stream>>>(n->wpart, (int)nw, chunks, n->grad + L.w_off);
   bias_grad<<<dim3(L.cout, chunks), kNT, 0, n->stream>>>(dout, L.cout, V, chunk, n->wpart);
   sum_chunks<<<cdiv(L.cout, 256), 256, 0, n->stream>>>(n->wpart, L.cout, chunks, n->grad + L.b_off);
-  if (din) {
+  if (din && L.k == 3 && n->tc_conv && n->wpack_t) {
+    // the data gradient as the adjoint convolution on the tensor cores
+    const size_t li = (size_t)(&L - n->layers.data());
+    mfto_status s = conv3_tc_launch(n, dout, L.cout, n->wpack_t + n->wpt_off[li], nullptr, din,
+                                    L.cin, d, 0, gate);
+    if (s != MFTO_OK) return s;
+  } else if (din) {
     n->launches++;
     const dim3 grid(cdiv(V, kNT), cdiv(L.cin, kCOB));
     if (L.k == 3)
@@ -676,8 +703,15 @@ mfto_status pack_weights(mfto_nn* n) {
     const int S = (ly.cin + kCtCin - 1) / kCtCin;
     const size_t cnt = ct_packed_elems(ly.cin, ly.cout);
     n->launches++;
-    pack_w3<<<cdiv(cnt, 256), 256, 0, n->stream>>>(n->w16 + ly.w_off, ly.cin, ly.cout, ns, S, cnt,
+    pack_w3<<<cdiv(cnt, 256), 256, 0, n->stream>>>(n->w16 + ly.w_off, ly.cin, ly.cout, ns, S, cnt, 0,
                                                    n->wpack + n->wp_off[i]);
+    if (n->wpack_t) {   // the adjoint layer: cout inputs, cin outputs
+      const size_t cnt_t = ct_packed_elems(ly.cout, ly.cin);
+      n->launches++;
+      pack_w3<<<cdiv(cnt_t, 256), 256, 0, n->stream>>>(n->w16 + ly.w_off, ly.cout, ly.cin,
+                                                       ct_ns(ly.cin), (ly.cout + kCtCin - 1) / kCtCin,
+                                                       cnt_t, 1, n->wpack_t + n->wpt_off[i]);
+    }
   }
   NCUDA(n, cudaGetLastError());
   n->wpack_dirty = false;
@@ -819,7 +853,7 @@ void free_nn(mfto_nn* n) {
   if (!n) return;
   for (float* p : n->bufs)
     if (p) cudaFree(p);
-  void* ptrs[] = {n->wpack, n->d_err, n->w32, n->grad, n->m1, n->m2, n->w16, n->gbuf0, n->gbuf1, n->gbuf2, n->wpart,
+  void* ptrs[] = {n->wpack, n->wpack_t, n->d_err, n->w32, n->grad, n->m1, n->m2, n->w16, n->gbuf0, n->gbuf1, n->gbuf2, n->wpart,
                   n->lpart, n->dpred};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -912,6 +946,15 @@ extern "C" mfto_status mfto_nn_create(int32_t base, int32_t levels, int64_t max_
       if (n->layers[i].k == 3) pk += ct_packed_elems(n->layers[i].cin, n->layers[i].cout);
     }
     A((void**)&n->wpack, sizeof(__nv_bfloat16) * (pk + 8));
+    if (TV > 0) {
+      size_t pt = 0;
+      n->wpt_off.assign(n->layers.size(), 0);
+      for (size_t i = 0; i < n->layers.size(); ++i) {
+        n->wpt_off[i] = pt;
+        if (n->layers[i].k == 3) pt += ct_packed_elems(n->layers[i].cout, n->layers[i].cin);
+      }
+      A((void**)&n->wpack_t, sizeof(__nv_bfloat16) * (pt + 8));
+    }
     A((void**)&n->d_err, sizeof(int32_t));
     n->tc_conv = 1;
     n->wpack_dirty = true;
