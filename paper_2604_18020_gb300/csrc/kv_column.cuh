@@ -141,8 +141,14 @@ struct ColLoadDirection {             // z + beta p, through L1 (separate launch
 // two node layers of the first tile have been requested from memory and
 // before they are used.  run() may set the loader's scalar and returns false
 // when the launch has nothing to do (uniform over the grid); the body then
-// returns at once, with `*skipped` set.
+// returns at once, with `*skipped` set.  A pre-step's global loads may go out
+// before the body's first copies: issue() starts them and returns them in a
+// State, run(ld, state) finishes; run(ld) does both at once.
 struct ColNoPre {
+  struct State {};
+  __device__ __forceinline__ State issue() const { return {}; }
+  template <typename Load>
+  __device__ __forceinline__ bool run(Load&, const State&) const { return true; }
   template <typename Load>
   __device__ __forceinline__ bool run(Load&) const { return true; }
 };
@@ -152,6 +158,10 @@ struct ColNoPre {
 struct ColPreFlagBeta {
   const int32_t* done;
   const double* beta;
+  struct State {};
+  __device__ __forceinline__ State issue() const { return {}; }
+  template <typename Load>
+  __device__ __forceinline__ bool run(Load& ld, const State&) const { return run(ld); }
   template <typename Load>
   __device__ __forceinline__ bool run(Load& ld) const {
     int d = 0;
@@ -640,21 +650,24 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     }
     return n;
   };
-  auto issue_prologue = [&](const Ctx& c, bool clean) {
+  // The prologue's copies of a tile always include the mask words: waiting
+  // for the tile's clean flag (a global load) before the first copy would
+  // put that load's latency in front of every copy; a clean tile just does
+  // not read them.
+  auto issue_prologue = [&](const Ctx& c) {
     int sl = c.kb % kColRing;   // slot of node layer kb - 1
 #pragma unroll
     for (int j = 0; j <= kColPrefetch; ++j) {
-      if (clean)
-        issue(c, c.kb - 1 + j, sl, std::true_type{});
-      else
-        issue(c, c.kb - 1 + j, sl, std::false_type{});
+      issue(c, c.kb - 1 + j, sl, std::false_type{});
       sl = next_slot(sl);
     }
   };
-  // first tile's prologue copies, then the pre-step while they are in flight
+  // the pre-step's loads, the first tile's prologue copies, then the rest of
+  // the pre-step while the copies are in flight
+  const typename Pre::State pst = pre.issue();
   int t = blockIdx.x;
-  if (t < ntiles) issue_prologue(ctx_of(t), clean_of(t));
-  if (!pre.run(ld)) {
+  if (t < ntiles) issue_prologue(ctx_of(t));
+  if (!pre.run(ld, pst)) {
     col_cp_wait<0>();
     *skipped = true;
     return red;
@@ -753,8 +766,8 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
   };
   for (; t < ntiles; t += gridDim.x) {
     const Ctx c = ctx_of(t);
+    if (t != (int)blockIdx.x) issue_prologue(c);
     const bool clean = clean_of(t);
-    if (t != (int)blockIdx.x) issue_prologue(c, clean);
     if (clean)
       run_tile(c, std::true_type{});
     else

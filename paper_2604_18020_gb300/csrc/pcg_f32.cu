@@ -29,23 +29,53 @@
 
 namespace {
 
-// Sum of K rows of double-float partials pf[c * MFTO_RED_SLOTS + b],
-// b < nb, in a fixed order (threads stride the blocks, then a warp tree,
-// then the warps in order); the FP64 totals are returned in every thread.
-// Contains two barriers; call uniformly.
+// Sums of K rows of double-float partials pf[c * MFTO_RED_SLOTS + b], b < nb,
+// in a fixed order: threads stride the blocks, then a warp tree, then the
+// warps in order.  partials_load issues a thread's first kPartAhead loads
+// (so that they can go out before other memory traffic of the launch);
+// partials_sum adds them and any further strides.  Thread 0 gets the FP64
+// totals (the same bits in every block); the other threads get 0.  FP64
+// instructions stay in one thread: the FP64 pipe issues a warp instruction
+// at a small fraction of the FP32 rate whatever the number of active lanes.
+// One barrier; call uniformly, once per launch.
+constexpr int kPartAhead = 4;
 template <int K>
-__device__ __forceinline__ void sum_partials_df(const float2* __restrict__ pf, int nb,
-                                                double (&out)[K]) {
+struct PartialLoads {
+  float2 x[kPartAhead][K];
+};
+
+template <int K>
+__device__ __forceinline__ PartialLoads<K> partials_load(const float2* __restrict__ pf, int nb) {
+  PartialLoads<K> L;
+#pragma unroll
+  for (int j = 0; j < kPartAhead; ++j) {
+    const int b = threadIdx.x + j * blockDim.x;
+#pragma unroll
+    for (int c = 0; c < K; ++c)
+      L.x[j][c] = b < nb ? __ldcg(&pf[c * MFTO_RED_SLOTS + b]) : make_float2(0.f, 0.f);
+  }
+  return L;
+}
+
+template <int K>
+__device__ __forceinline__ void partials_sum(const PartialLoads<K>& L, const float2* __restrict__ pf,
+                                             int nb, double (&out)[K]) {
   __shared__ float2 sh[K][MFTO_BLOCK / 32];
-  __shared__ double tot[K];
   DFloat t[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) t[c] = DFloat{0.f, 0.f};
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+  for (int j = 0; j < kPartAhead; ++j) {
+    if (threadIdx.x + j * blockDim.x < nb) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) t[c] = df_add(t[c], DFloat{L.x[j][c].x, L.x[j][c].y});
+    }
+  }
+  for (int b = threadIdx.x + kPartAhead * blockDim.x; b < nb; b += blockDim.x) {
 #pragma unroll
     for (int c = 0; c < K; ++c) {
-      const float2 x = __ldcg(&pf[c * MFTO_RED_SLOTS + b]);
-      t[c] = df_add(t[c], DFloat{x.x, x.y});
+      const float2 y = __ldcg(&pf[c * MFTO_RED_SLOTS + b]);
+      t[c] = df_add(t[c], DFloat{y.x, y.y});
     }
   }
 #pragma unroll
@@ -64,18 +94,17 @@ __device__ __forceinline__ void sum_partials_df(const float2* __restrict__ pf, i
     for (int c = 0; c < K; ++c) sh[c][warp] = make_float2(t[c].hi, t[c].lo);
   }
   __syncthreads();
+#pragma unroll
+  for (int c = 0; c < K; ++c) out[c] = 0.0;
   if (threadIdx.x == 0) {
     const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
       DFloat s{0.f, 0.f};
       for (int w = 0; w < nw; ++w) s = df_add(s, DFloat{sh[c][w].x, sh[c][w].y});
-      tot[c] = (double)s.hi + (double)s.lo;
+      out[c] = (double)s.hi + (double)s.lo;
     }
   }
-  __syncthreads();
-#pragma unroll
-  for (int c = 0; c < K; ++c) out[c] = tot[c];
 }
 
 // Block sum of K double-float values held in lane 0 of each warp (as
@@ -85,7 +114,6 @@ template <int K>
 __device__ __forceinline__ void publish_block_df(const DFloat (&v)[K], float2* pf) {
   __shared__ float2 sh[K][MFTO_BLOCK / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
   if (lane == 0) {
 #pragma unroll
     for (int c = 0; c < K; ++c) sh[c][warp] = make_float2(v[c].hi, v[c].lo);
@@ -109,23 +137,40 @@ struct ColPreCg2 {
   int nb;             // B's blocks
   PcgScalars* s;
   int par;
+  // the partials and (thread 0) the scalars, loaded together: one round trip
+  struct State {
+    PartialLoads<2> part;
+    int done, k, maxit;
+    double rtol2ff, rinv;
+  };
+  __device__ __forceinline__ State issue() const {
+    State st;
+    st.part = partials_load<2>(pb, nb);
+    st.done = st.k = st.maxit = 0;
+    st.rtol2ff = st.rinv = 0.0;
+    if (threadIdx.x == 0) {
+      st.done = *(const volatile int32_t*)&s->done;
+      st.k = s->it2[par ^ 1] + 1;                   // iterations completed so far
+      st.maxit = s->maxit;
+      st.rtol2ff = s->rtol2ff;
+      st.rinv = s->rinv2[par ^ 1];
+    }
+    return st;
+  }
   template <typename Load>
-  __device__ __forceinline__ bool run(Load& ld) const {
+  __device__ __forceinline__ bool run(Load& ld) const { return run(ld, issue()); }
+  // thread 0 decides for the block and broadcasts through shared memory
+  template <typename Load>
+  __device__ __forceinline__ bool run(Load& ld, const State& st) const {
     __shared__ float s_beta;
     __shared__ int s_skip;
-    // the scalars go out with the partials' loads (one round trip for both)
-    int done = 0, k = 0, maxit = 0;
-    double rtol2ff = 0.0, rinv = 0.0;
-    if (threadIdx.x == 0) {
-      done = *(const volatile int32_t*)&s->done;
-      k = s->it2[par ^ 1] + 1;                      // iterations completed so far
-      maxit = s->maxit;
-      rtol2ff = s->rtol2ff;
-      rinv = s->rinv2[par ^ 1];
-    }
+    const bool lead = threadIdx.x == 0;
+    int done = st.done;
+    const int k = st.k, maxit = st.maxit;
+    const double rtol2ff = st.rtol2ff, rinv = st.rinv;
     double tot[2];
-    sum_partials_df<2>(pb, nb, tot);
-    if (threadIdx.x == 0) {
+    partials_sum<2>(st.part, pb, nb, tot);
+    if (lead) {
       double beta = 0.0;
       if (!done) {
         const double rz = tot[0], rr = tot[1];
@@ -211,8 +256,6 @@ cg2_update_kernel(float* __restrict__ u, const float* __restrict__ p, const floa
                   float* __restrict__ r, float* __restrict__ z, const float* __restrict__ dinv,
                   int n, PcgScalars* s, const double* part_a, int nb_a, double* part_b,
                   int par) {
-  __shared__ float s_alpha;
-  __shared__ int s_skip;
   const int n4 = n >> 2;
   const int first = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
@@ -231,17 +274,24 @@ cg2_update_kernel(float* __restrict__ u, const float* __restrict__ p, const floa
     rr = r4[first];
     dd = d4[first];
   }
-  // the scalars go out with the partials' loads (one round trip for both)
+  // the scalars go out with the partials' loads (one round trip for both);
+  // thread 0 decides for the block, as in the K.v's pre-step
+  __shared__ float s_alpha;
+  __shared__ int s_skip;
+  const bool lead = threadIdx.x == 0;
   int done = 0, it = 0;
   double rz = 0.0;
-  if (threadIdx.x == 0) {
+  if (lead) {
     done = *(const volatile int32_t*)&s->done;
     rz = s->rz2[par];
     it = s->it2[par];
   }
   double tot[1];
-  sum_partials_df<1>(reinterpret_cast<const float2*>(part_a), nb_a, tot);
-  if (threadIdx.x == 0) {
+  {
+    const float2* pa = reinterpret_cast<const float2*>(part_a);
+    partials_sum<1>(partials_load<1>(pa, nb_a), pa, nb_a, tot);
+  }
+  if (lead) {
     double alpha = 0.0;
     if (!done) {
       const double pq = tot[0];
