@@ -673,6 +673,24 @@ mfto_status mfto_kv_timing_read(mfto_handle* h, mfto_form form, int64_t* launche
 mfto_status mfto_cg_timing_read(mfto_handle* h, int64_t* launches, int64_t* iterations,
                                 double* total_ms);
 
+/* Device time of one launch of the FP32 CG K.v as the default inner CG
+ * (engine 2, FP32 column K.v) runs it on this handle: the first inner
+ * iteration's K.v launch, with the handle's mesh, autotuned launch shape and
+ * work vectors (unit moduli, a right-hand side of ones), captured `launches`
+ * times back to back into one CUDA graph; after one untimed replay, `reps`
+ * replays are timed between two CUDA events on the handle's stream, and
+ * *us_per_launch = elapsed / (reps x launches) in microseconds.  Every launch
+ * does the work of a CG iteration's K.v, so this is the kernel's duration
+ * plus the gap between consecutive graph kernels, without the event nodes
+ * that mfto_kv_timing places around every launch (which add several
+ * microseconds to each timed launch).  Overwrites the FP32 work vectors of
+ * the handle (as
+ * mfto_kv_autotune does); synchronises the stream.  MFTO_INVALID_ARG unless
+ * launches is in [1, 4096], reps >= 1, and the FP32 inner form with CG
+ * engine 2 and the column K.v (the defaults) is selected. */
+mfto_status mfto_cg_kv_time(mfto_handle* h, int32_t launches, int32_t reps,
+                            double* us_per_launch);
+
 /* Number of kernels the library has launched for this handle so far (the
  * kernel nodes of every launched CUDA graph included). */
 mfto_status mfto_launch_count(const mfto_handle* h, int64_t* n);

@@ -663,6 +663,8 @@ mfto_status pcg_persist_init(mfto_handle* h);
 bool cg2_active(const mfto_handle* h, int form);
 mfto_status cg2_attrs(mfto_handle* h);
 mfto_status cg2_seed(mfto_handle* h, const PcgVecs<float>& v, double rz_prev);
+mfto_status cg2_enqueue_kv(mfto_handle* h, cudaStream_t st, const PcgVecs<float>& v,
+                           const float* p_old, float* p_new, int par);
 mfto_status cg2_enqueue(mfto_handle* h, cudaStream_t st, const PcgVecs<float>& v,
                         const float* p_old, float* p_new, int par, cudaEvent_t ev0,
                         cudaEvent_t ev1);

@@ -367,6 +367,78 @@ mfto_status pcg_time_iterations(mfto_handle* h, int chunks, float* us_per_iter) 
   return MFTO_OK;
 }
 
+// Device time of the FP32 CG K.v launch of engine 2 on this handle's mesh,
+// launch shape and work vectors: `launches` launches of the first inner
+// iteration's K.v (the same kernel, grid and arguments as in the CG graphs;
+// unit moduli, a right-hand side of ones) captured back to back in one CUDA
+// graph, one untimed replay, then `reps` replays between two events.  Each
+// launch repeats the same work (it reads z and the seeded partials, writes
+// p_new, q and its p.q partials), so the time per launch is the kernel's
+// duration plus the gap between consecutive kernels of a graph, without the
+// cost of event nodes between launches.  Overwrites the FP32 work vectors.
+mfto_status pcg_time_kv(mfto_handle* h, int launches, int reps, double* us_per_launch) {
+  if (!cg2_active(h, MFTO_FORM_F32))
+    return mfto_fail(h, MFTO_INVALID_ARG,
+                     "K.v burst timing: needs CG engine 2 and the FP32 column K.v");
+  const int n = (int)h->n_dof;
+  const int nb = reduction_blocks(h->n_dof, MFTO_BLOCK);
+  h->launches += 2;
+  fill_f32<<<nb, MFTO_BLOCK, 0, h->stream>>>(h->d_E32, (int)h->n_elem, 1.f);
+  fill_f32<<<nb, MFTO_BLOCK, 0, h->stream>>>(h->d_r32, n, 1.f);
+  MFTO_LAUNCH_CHECK(h);
+  MFTO_CUDA(h, cudaMemsetAsync(h->d_e32, 0, sizeof(float) * h->n_dof, h->stream));
+  mfto_status s = diag_launch(h, MFTO_FORM_F32, h->d_E32, h->d_dinv32, true);
+  const PcgVecs<float> v{h->d_E32, h->d_e32, h->d_r32, h->d_z32, h->d_p0_32, h->d_p1_32,
+                         h->d_q32, h->d_dinv32, h->d_pcg32, h->d_partials, h->d_partials2,
+                         MFTO_FORM_F32};
+  if (s == MFTO_OK) s = pcg_start<float>(h, v, h->d_r32, nullptr, 1e-30, 1 << 30, 0.0);
+  if (s == MFTO_OK) s = cg2_seed(h, v, 0.0);
+  if (s != MFTO_OK) return s;
+  if (!h->cap_stream)
+    MFTO_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  MFTO_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < launches && s == MFTO_OK; ++i)
+    s = cg2_enqueue_kv(h, h->cap_stream, v, h->d_p0_32, h->d_p1_32, 0);
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (s != MFTO_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return s != MFTO_OK ? s : mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst capture: %s",
+                                        cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess)
+    return mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst instantiate: %s", cudaGetErrorString(e));
+  cudaEvent_t a = nullptr, b = nullptr;
+  e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess)
+    return mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst timing: %s", cudaGetErrorString(e));
+  h->launches += (int64_t)launches * (reps + 1);
+  *us_per_launch = 1000.0 * ms / ((double)reps * launches);
+  return MFTO_OK;
+}
+
+extern "C" mfto_status mfto_cg_kv_time(mfto_handle* h, int32_t launches, int32_t reps,
+                                       double* us_per_launch) {
+  if (!h) return MFTO_INVALID_ARG;
+  MFTO_REQUIRE(h, us_per_launch && launches >= 1 && launches <= 4096 && reps >= 1,
+               "mfto_cg_kv_time: launches in [1, 4096], reps >= 1, non-null output");
+  return pcg_time_kv(h, launches, reps, us_per_launch);
+}
+
 void pcg_graph_release(mfto_handle* h) {
   for (int i = 0; i < MFTO_PCG_SLOTS; ++i) {
     destroy_graph(h->pcg_graph[i]);

@@ -460,3 +460,24 @@ mfto_status cg2_enqueue(mfto_handle* h, cudaStream_t st, const PcgVecs<float>& v
   MFTO_LAUNCH_CHECK(h);
   return MFTO_OK;
 }
+
+// A(k) alone, as cg2_enqueue issues it for the FP32 SIMT form (burst timing
+// of the K.v launch, pcg.cu).
+mfto_status cg2_enqueue_kv(mfto_handle* h, cudaStream_t st, const PcgVecs<float>& v,
+                           const float* p_old, float* p_new, int par) {
+  int grid = 0;
+  const int kind = h->col_kind;
+  const Grid g = make_grid(h->mesh);
+  const int nb_b = update_blocks(h);
+  const ColTiling tl = col_launch_tiling(h, h->occ_col[kind], &grid);
+  if (kind == 1)
+    cg2_kv_kernel<3><<<grid, MFTO_BLOCK, kColSmem, st>>>(v.E, v.z, p_old, p_new, v.q,
+                                                         h->d_fixed, h->mc32, g, tl, v.s,
+                                                         v.part_b, nb_b, v.part_a, par);
+  else
+    cg2_kv_kernel<2><<<grid, MFTO_BLOCK, kColSmem, st>>>(v.E, v.z, p_old, p_new, v.q,
+                                                         h->d_fixed, h->mc32, g, tl, v.s,
+                                                         v.part_b, nb_b, v.part_a, par);
+  MFTO_LAUNCH_CHECK(h);
+  return MFTO_OK;
+}

@@ -152,6 +152,7 @@ SIGNATURES = {
                                      C.POINTER(C.c_float)]),
     "mfto_cg_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double)]),
+    "mfto_cg_kv_time": (C.c_int32, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "mfto_pcg": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
     "mfto_ir_solve": (C.c_int32, [_P, C.c_int32, C.c_double, _P, _P, _P, C.POINTER(IrStats)]),
     "mfto_set_solver": (C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, C.c_int32]),
@@ -648,6 +649,15 @@ class Handle:
         _check("mfto_cg_timing_read",
                lib().mfto_cg_timing_read(self._h, C.byref(n), C.byref(it), C.byref(ms)), self._h)
         return n.value, it.value, ms.value
+
+    def cg_kv_time(self, launches=64, reps=5):
+        """Microseconds per launch of the FP32 CG K.v, timed over a graph of
+        back-to-back launches (mfto_cg_kv_time; overwrites the FP32 work
+        vectors)."""
+        us = C.c_double()
+        _check("mfto_cg_kv_time", lib().mfto_cg_kv_time(self._h, launches, reps, C.byref(us)),
+               self._h)
+        return us.value
 
     # ---- learned part
     def nn_grid(self, levels=4):

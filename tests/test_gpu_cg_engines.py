@@ -123,3 +123,33 @@ def test_persistent_timing_counts_iterations(cuda):
     assert n == st.outer_iterations
     assert it == st.inner_iterations
     assert ms > 0.0
+
+
+def test_cg_kv_burst_time(cuda):
+    """mfto_cg_kv_time: a positive, finite time per launch of engine 2's K.v
+    (a solve afterwards still meets the tolerance: the call only overwrites
+    the FP32 work vectors), and MFTO_INVALID_ARG for another engine."""
+    import torch
+    from paper_2604_18020_gb300 import mfto
+    P = W.cantilever(24, 12, 12)
+    m = P.mesh
+    with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed) as h:
+        h.set_solver(mfto.FORM_F32, 0.1)
+        h.set_cg_engine(2)
+        us = h.cg_kv_time(8, 2)
+        assert np.isfinite(us) and 0.0 < us < 1e4
+        rho = torch.tensor(W.rho_random(m, seed=4, lo=0.05, hi=1.0), device=cuda)
+        E = torch.empty_like(rho)
+        h.simp_modulus(rho, E)
+        f = torch.tensor(P.f, device=cuda)
+        u = torch.zeros(m.n_dof, dtype=torch.float64, device=cuda)
+        st = h.ir_solve(E, f, u, inner_tol=0.1)
+        assert st.status == mfto.OK
+        edof = fem.edof_table_fast(m.nelx, m.nely, m.nelz)
+        r = P.f - fem.kv(fem.ke_exact(), E.cpu().numpy(), edof, u.cpu().numpy(),
+                         fem.dof_mask(P.fixed))
+        assert np.linalg.norm(r) / np.linalg.norm(P.f) <= 1.5e-8
+        h.set_cg_engine(0)
+        with pytest.raises(mfto.MftoError) as err:
+            h.cg_kv_time(8, 2)
+        assert err.value.code == mfto.INVALID_ARG
