@@ -66,8 +66,8 @@ KERNEL_SOURCES = {
     "pcg_kv_tile_kernel<double>": ["kv_tile.cuh", "kv_tile.cu", "modes.cuh"],
 }
 NCU_DRAM_BYTES = {
-    ("cg2_kv_kernel<2>", WORKLOAD): (6.662656e6, "979c2c9819a6"),
-    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (143.068416e6 + 75.482112e6, "979c2c9819a6"),
+    ("cg2_kv_kernel<2>", WORKLOAD): (6.658048e6, "93ace127773b"),
+    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (143.319296e6 + 74.673920e6, "93ace127773b"),
     ("pcg_kv_tile_kernel<double>", WORKLOAD): ((293.127936e6 + 199.873024e6) * 216000 / 4915200,
                                                "6e176c6f4f1e"),
 }
