@@ -619,10 +619,13 @@ def gpu_bench(args, rank, local_rank, world):
     # of the same kernel, grid and arguments (mfto_cg_kv_time; after every
     # other leg, since it overwrites the FP32 work vectors)
     kv_events_s = kv_ms * 1e-3 / max(kv_n, 1)
-    burst_us = None
+    burst_us = burst_ev_us = None
     if (args.form == "mixed" and args.inner_form == "f32" and args.cg_engine == 2
             and not persistent):
         burst_us = h.cg_kv_time(64, 5)
+        # the same burst with an event pair around every launch: what the
+        # event nodes of the per-launch timing add to identical launches
+        burst_ev_us = h.cg_kv_time(64, 5, events=True)
     kv_avg_s = burst_us * 1e-6 if burst_us else kv_events_s
     sm_mhz = clk["sm_mhz"] or 1950.0
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
@@ -647,7 +650,8 @@ def gpu_bench(args, rank, local_rank, world):
                      "duration_timing": ("graph of 64 back-to-back launches of the CG K.v, "
                                          "5 timed replays (mfto_cg_kv_time)" if burst_us else
                                          "CUDA events around every launch in the CG graph"),
-                     "duration_us_events_in_cg": kv_events_s * 1e6})
+                     "duration_us_events_in_cg": kv_events_s * 1e6,
+                     "duration_us_burst_with_event_nodes": burst_ev_us if burst_us else None})
         if persistent:
             roof.update({"unit_of_work": "one CG iteration (one K.v application)",
                          "launches": cgt[0], "iterations_per_launch": cgt[1] / cgt[0],

@@ -683,12 +683,16 @@ mfto_status mfto_cg_timing_read(mfto_handle* h, int64_t* launches, int64_t* iter
  * does the work of a CG iteration's K.v, so this is the kernel's duration
  * plus the gap between consecutive graph kernels, without the event nodes
  * that mfto_kv_timing places around every launch (which add several
- * microseconds to each timed launch).  Overwrites the FP32 work vectors of
- * the handle (as
- * mfto_kv_autotune does); synchronises the stream.  MFTO_INVALID_ARG unless
- * launches is in [1, 4096], reps >= 1, and the FP32 inner form with CG
- * engine 2 and the column K.v (the defaults) is selected. */
-mfto_status mfto_cg_kv_time(mfto_handle* h, int32_t launches, int32_t reps,
+ * microseconds to each timed launch).  With events = 1 the same graph also
+ * holds an external event record node before and after every launch, as
+ * mfto_kv_timing places them in the CG graphs, and *us_per_launch is the
+ * mean interval between each launch's two events in the last replay: the
+ * difference to events = 0 is what those nodes add.  Overwrites the FP32
+ * work vectors of the handle (as mfto_kv_autotune does); synchronises the
+ * stream.  MFTO_INVALID_ARG unless launches is in [1, 4096], reps >= 1,
+ * events is 0 or 1, and the FP32 inner form with CG engine 2 and the column
+ * K.v (the defaults) is selected. */
+mfto_status mfto_cg_kv_time(mfto_handle* h, int32_t launches, int32_t reps, int32_t events,
                             double* us_per_launch);
 
 /* Number of kernels the library has launched for this handle so far (the

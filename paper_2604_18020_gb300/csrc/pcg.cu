@@ -18,7 +18,10 @@
 // CUDA graph) and reads the scalars after each chunk.
 #include <math.h>
 
+#include <vector>
+
 #include "cg_update.cuh"
+
 #include "common.cuh"
 #include "kv_node.cuh"
 
@@ -376,7 +379,8 @@ mfto_status pcg_time_iterations(mfto_handle* h, int chunks, float* us_per_iter) 
 // p_new, q and its p.q partials), so the time per launch is the kernel's
 // duration plus the gap between consecutive kernels of a graph, without the
 // cost of event nodes between launches.  Overwrites the FP32 work vectors.
-mfto_status pcg_time_kv(mfto_handle* h, int launches, int reps, double* us_per_launch) {
+mfto_status pcg_time_kv(mfto_handle* h, int launches, int reps, bool events,
+                        double* us_per_launch) {
   if (!cg2_active(h, MFTO_FORM_F32))
     return mfto_fail(h, MFTO_INVALID_ARG,
                      "K.v burst timing: needs CG engine 2 and the FP32 column K.v");
@@ -396,21 +400,50 @@ mfto_status pcg_time_kv(mfto_handle* h, int launches, int reps, double* us_per_l
   if (s != MFTO_OK) return s;
   if (!h->cap_stream)
     MFTO_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  // with events: an external record node before and after every launch, as
+  // mfto_kv_timing places them in the CG graphs
+  std::vector<cudaEvent_t> ev(events ? 2 * launches : 0, nullptr);
+  for (auto& x : ev)
+    if (s == MFTO_OK && cudaEventCreate(&x) != cudaSuccess)
+      s = mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst timing: cannot create events");
+  auto destroy_events = [&]() {
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+  };
+  if (s != MFTO_OK) {
+    destroy_events();
+    return s;
+  }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  MFTO_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < launches && s == MFTO_OK; ++i)
-    s = cg2_enqueue_kv(h, h->cap_stream, v, h->d_p0_32, h->d_p1_32, 0);
-  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    destroy_events();
+    return mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst capture: %s", cudaGetErrorString(e));
+  }
+  for (int i = 0; i < launches && s == MFTO_OK; ++i) {
+    if (events && cudaEventRecordWithFlags(ev[2 * i], h->cap_stream, cudaEventRecordExternal) !=
+                      cudaSuccess)
+      s = mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst capture: event record");
+    if (s == MFTO_OK) s = cg2_enqueue_kv(h, h->cap_stream, v, h->d_p0_32, h->d_p1_32, 0);
+    if (s == MFTO_OK && events &&
+        cudaEventRecordWithFlags(ev[2 * i + 1], h->cap_stream, cudaEventRecordExternal) !=
+            cudaSuccess)
+      s = mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst capture: event record");
+  }
+  e = cudaStreamEndCapture(h->cap_stream, &graph);
   if (s != MFTO_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
+    destroy_events();
     return s != MFTO_OK ? s : mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst capture: %s",
                                         cudaGetErrorString(e));
   }
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (e != cudaSuccess)
+  if (e != cudaSuccess) {
+    destroy_events();
     return mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst instantiate: %s", cudaGetErrorString(e));
+  }
   cudaEvent_t a = nullptr, b = nullptr;
   e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -421,22 +454,32 @@ mfto_status pcg_time_kv(mfto_handle* h, int launches, int reps, double* us_per_l
   if (e == cudaSuccess) e = cudaEventSynchronize(b);
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  // with events: the mean of the per-launch event intervals of the last replay
+  double ev_ms = 0.0;
+  for (int i = 0; events && i < launches && e == cudaSuccess; ++i) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+    ev_ms += t;
+  }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
+  destroy_events();
   cudaGraphExecDestroy(exec);
   if (e != cudaSuccess)
     return mfto_fail(h, MFTO_CUDA_ERROR, "K.v burst timing: %s", cudaGetErrorString(e));
   h->launches += (int64_t)launches * (reps + 1);
-  *us_per_launch = 1000.0 * ms / ((double)reps * launches);
+  *us_per_launch = events ? 1000.0 * ev_ms / launches : 1000.0 * ms / ((double)reps * launches);
   return MFTO_OK;
 }
 
 extern "C" mfto_status mfto_cg_kv_time(mfto_handle* h, int32_t launches, int32_t reps,
-                                       double* us_per_launch) {
+                                       int32_t events, double* us_per_launch) {
   if (!h) return MFTO_INVALID_ARG;
-  MFTO_REQUIRE(h, us_per_launch && launches >= 1 && launches <= 4096 && reps >= 1,
-               "mfto_cg_kv_time: launches in [1, 4096], reps >= 1, non-null output");
-  return pcg_time_kv(h, launches, reps, us_per_launch);
+  MFTO_REQUIRE(h, us_per_launch && launches >= 1 && launches <= 4096 && reps >= 1 &&
+                      (events == 0 || events == 1),
+               "mfto_cg_kv_time: launches in [1, 4096], reps >= 1, events 0 or 1, non-null "
+               "output");
+  return pcg_time_kv(h, launches, reps, events != 0, us_per_launch);
 }
 
 void pcg_graph_release(mfto_handle* h) {

@@ -152,7 +152,7 @@ SIGNATURES = {
                                      C.POINTER(C.c_float)]),
     "mfto_cg_timing_read": (C.c_int32, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double)]),
-    "mfto_cg_kv_time": (C.c_int32, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "mfto_cg_kv_time": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "mfto_pcg": (C.c_int32, [_P, _P, _P, _P, C.POINTER(SolveStats)]),
     "mfto_ir_solve": (C.c_int32, [_P, C.c_int32, C.c_double, _P, _P, _P, C.POINTER(IrStats)]),
     "mfto_set_solver": (C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, C.c_int32]),
@@ -650,12 +650,14 @@ class Handle:
                lib().mfto_cg_timing_read(self._h, C.byref(n), C.byref(it), C.byref(ms)), self._h)
         return n.value, it.value, ms.value
 
-    def cg_kv_time(self, launches=64, reps=5):
+    def cg_kv_time(self, launches=64, reps=5, events=False):
         """Microseconds per launch of the FP32 CG K.v, timed over a graph of
         back-to-back launches (mfto_cg_kv_time; overwrites the FP32 work
-        vectors)."""
+        vectors); with events, the mean interval between event nodes placed
+        around every launch of that graph."""
         us = C.c_double()
-        _check("mfto_cg_kv_time", lib().mfto_cg_kv_time(self._h, launches, reps, C.byref(us)),
+        _check("mfto_cg_kv_time",
+               lib().mfto_cg_kv_time(self._h, launches, reps, int(bool(events)), C.byref(us)),
                self._h)
         return us.value
 

@@ -138,6 +138,8 @@ def test_cg_kv_burst_time(cuda):
         h.set_cg_engine(2)
         us = h.cg_kv_time(8, 2)
         assert np.isfinite(us) and 0.0 < us < 1e4
+        us_ev = h.cg_kv_time(8, 2, events=True)
+        assert np.isfinite(us_ev) and 0.0 < us_ev < 1e4
         rho = torch.tensor(W.rho_random(m, seed=4, lo=0.05, hi=1.0), device=cuda)
         E = torch.empty_like(rho)
         h.simp_modulus(rho, E)
