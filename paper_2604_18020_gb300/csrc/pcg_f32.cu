@@ -97,13 +97,17 @@ __device__ __forceinline__ void partials_sum(const PartialLoads<K>& L, const flo
 #pragma unroll
   for (int c = 0; c < K; ++c) out[c] = 0.0;
   if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
+    // the rows' sums over the warps in order, interleaved (launches use
+    // MFTO_BLOCK threads)
+    DFloat t2[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) {
-      DFloat s{0.f, 0.f};
-      for (int w = 0; w < nw; ++w) s = df_add(s, DFloat{sh[c][w].x, sh[c][w].y});
-      out[c] = (double)s.hi + (double)s.lo;
-    }
+    for (int c = 0; c < K; ++c) t2[c] = DFloat{0.f, 0.f};
+#pragma unroll
+    for (int w = 0; w < MFTO_BLOCK / 32; ++w)
+#pragma unroll
+      for (int c = 0; c < K; ++c) t2[c] = df_add(t2[c], DFloat{sh[c][w].x, sh[c][w].y});
+#pragma unroll
+    for (int c = 0; c < K; ++c) out[c] = (double)t2[c].hi + (double)t2[c].lo;
   }
 }
 
@@ -120,13 +124,18 @@ __device__ __forceinline__ void publish_block_df(const DFloat (&v)[K], float2* p
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
+    // the rows' sums over the warps in order, interleaved (launches use
+    // MFTO_BLOCK threads)
+    DFloat t2[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) {
-      DFloat s{0.f, 0.f};
-      for (int w = 0; w < nw; ++w) s = df_add(s, DFloat{sh[c][w].x, sh[c][w].y});
-      pf[c * MFTO_RED_SLOTS + blockIdx.x] = make_float2(s.hi, s.lo);
-    }
+    for (int c = 0; c < K; ++c) t2[c] = DFloat{0.f, 0.f};
+#pragma unroll
+    for (int w = 0; w < MFTO_BLOCK / 32; ++w)
+#pragma unroll
+      for (int c = 0; c < K; ++c) t2[c] = df_add(t2[c], DFloat{sh[c][w].x, sh[c][w].y});
+#pragma unroll
+    for (int c = 0; c < K; ++c)
+      pf[c * MFTO_RED_SLOTS + blockIdx.x] = make_float2(t2[c].hi, t2[c].lo);
   }
 }
 
@@ -266,6 +275,10 @@ cg2_update_kernel(float* __restrict__ u, const float* __restrict__ p, const floa
   const float4* q4 = reinterpret_cast<const float4*>(q);
   const float4* d4 = reinterpret_cast<const float4*>(dinv);
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // the p.q partials go out first: the block's decision waits for them,
+  // while the vector groups are only needed after it
+  const float2* pa = reinterpret_cast<const float2*>(part_a);
+  const PartialLoads<1> pl = partials_load<1>(pa, nb_a);
   float4 uu = zero4, pp = zero4, qq = zero4, rr = zero4, dd = zero4;
   if (first < n4) {
     uu = u4[first];
@@ -287,10 +300,7 @@ cg2_update_kernel(float* __restrict__ u, const float* __restrict__ p, const floa
     it = s->it2[par];
   }
   double tot[1];
-  {
-    const float2* pa = reinterpret_cast<const float2*>(part_a);
-    partials_sum<1>(partials_load<1>(pa, nb_a), pa, nb_a, tot);
-  }
+  partials_sum<1>(pl, pa, nb_a, tot);
   if (lead) {
     double alpha = 0.0;
     if (!done) {
