@@ -264,38 +264,76 @@ __device__ __forceinline__ float col_modulus(const float* __restrict__ E, const 
              : 0.f;
 }
 
+// Packed FP32 pairs (sm_100 and later): one instruction applies the same
+// IEEE operation, with the same rounding, to both lanes, so a pair computes
+// bit for bit what two scalar instructions would.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// Values of the three displacement components at the 4 places (a + 2b) of
+// one face: corner values, face modes or outputs.  The x and y components
+// go through identical butterflies, z stages and modulus scaling, so they
+// are held as one packed pair; z is a plain float.
+struct ColFace {
+  float2 xy[4];
+  float z[4];
+};
+
 // face modes (x then y stage) of the 4 corners (a + 2b) of one face, per component
 __device__ __forceinline__ void face_forward(const float* __restrict__ layer, int base,
-                                             float (&F)[3][4]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float* L = layer + c * ColShape::NV + base;
-    const float c0 = L[0], c1 = L[1], c2 = L[ColShape::NX], c3 = L[ColShape::NX + 1];
-    const float m0 = c0 + c1, m1 = c1 - c0, m2 = c2 + c3, m3 = c3 - c2;
-    F[c][0] = m0 + m2;
-    F[c][2] = m2 - m0;
-    F[c][1] = m1 + m3;
-    F[c][3] = m3 - m1;
-  }
+                                             ColFace& F) {
+  const float* Lx = layer + base;
+  const float* Ly = Lx + ColShape::NV;
+  const float* Lz = Ly + ColShape::NV;
+  constexpr int NX = ColShape::NX;
+  const float2 c0 = make_float2(Lx[0], Ly[0]), c1 = make_float2(Lx[1], Ly[1]);
+  const float2 c2 = make_float2(Lx[NX], Ly[NX]), c3 = make_float2(Lx[NX + 1], Ly[NX + 1]);
+  const float2 m0 = add2(c0, c1), m1 = sub2(c1, c0), m2 = add2(c2, c3), m3 = sub2(c3, c2);
+  F.xy[0] = add2(m0, m2);
+  F.xy[2] = sub2(m2, m0);
+  F.xy[1] = add2(m1, m3);
+  F.xy[3] = sub2(m3, m1);
+  const float z0 = Lz[0], z1 = Lz[1], z2 = Lz[NX], z3 = Lz[NX + 1];
+  const float n0 = z0 + z1, n1 = z1 - z0, n2 = z2 + z3, n3 = z3 - z2;
+  F.z[0] = n0 + n2;
+  F.z[2] = n2 - n0;
+  F.z[1] = n1 + n3;
+  F.z[3] = n3 - n1;
 }
 
 // Applies the element to face modes Flo (node layer ez) and Fup (layer ez+1):
 // lo, up receive E * (the inverse z stage of the mode operator's output).
-__device__ __forceinline__ void col_element(const float (&Flo)[3][4], const float (&Fup)[3][4],
-                                            float E, const ModeCoef<float>& K,
-                                            float (&lo)[3][4], float (&up)[3][4]) {
-  float x[3][8], y[3][8];
+// Mode m = f + 4 s of component c: face mode f, z sum (s = 0) or difference.
+__device__ __forceinline__ void col_element(const ColFace& Flo, const ColFace& Fup, float E,
+                                            const ModeCoef<float>& K, ColFace& lo, ColFace& up) {
+  float2 X[8], Y[8];   // components x, y
+  float xz[8], yz[8];  // component z
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+  for (int f = 0; f < 4; ++f) {
+    X[f] = add2(Flo.xy[f], Fup.xy[f]);       // z sum
+    X[f | 4] = sub2(Fup.xy[f], Flo.xy[f]);   // z difference
+    xz[f] = Flo.z[f] + Fup.z[f];
+    xz[f | 4] = Fup.z[f] - Flo.z[f];
+  }
+  // component c of mode m
+  auto xc = [&](int c, int m) -> float { return c == 0 ? X[m].x : (c == 1 ? X[m].y : xz[m]); };
+  auto yc = [&](int c, int m) -> float& { return c == 0 ? Y[m].x : (c == 1 ? Y[m].y : yz[m]); };
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      x[c][f] = Flo[c][f] + Fup[c][f];       // z sum
-      x[c][f | 4] = Fup[c][f] - Flo[c][f];   // z difference
-    }
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int m = 0; m < 8; ++m) y[c][m] = K.diag[c][m] * x[c][m];
+  for (int m = 0; m < 8; ++m) {
+    Y[m].x = K.diag[0][m] * X[m].x;
+    Y[m].y = K.diag[1][m] * X[m].y;
+    yz[m] = K.diag[2][m] * xz[m];
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -305,30 +343,87 @@ __device__ __forceinline__ void col_element(const float (&Flo)[3][4], const floa
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
         const int tb = mt << t;
-        y[i][(1 << i) | tb] = fmaf(K.lamM[mt], x[j][(1 << j) | tb], y[i][(1 << i) | tb]);
-        y[i][(1 << j) | tb] = fmaf(K.muM[mt], x[j][(1 << i) | tb], y[i][(1 << j) | tb]);
+        float& a = yc(i, (1 << i) | tb);
+        a = fmaf(K.lamM[mt], xc(j, (1 << j) | tb), a);
+        float& b = yc(i, (1 << j) | tb);
+        b = fmaf(K.muM[mt], xc(j, (1 << i) | tb), b);
       }
     }
+  // lo = E y - E y', up = E y + E y' (y' the z-difference partner), with
+  // E y' rounded once: -(E y') is formed as (-E) y', exactly its negation
+  const float2 E2 = make_float2(E, E), nE2 = make_float2(-E, -E);
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const float ed = E * y[c][f | 4];
-      lo[c][f] = fmaf(E, y[c][f], -ed);
-      up[c][f] = fmaf(E, y[c][f], ed);
-    }
+  for (int f = 0; f < 4; ++f) {
+    const float2 ed = mul2(E2, Y[f | 4]), ned = mul2(nE2, Y[f | 4]);
+    lo.xy[f] = fma2(E2, Y[f], ned);
+    up.xy[f] = fma2(E2, Y[f], ed);
+    const float edz = E * yz[f | 4];
+    lo.z[f] = fmaf(E, yz[f], -edz);
+    up.z[f] = fmaf(E, yz[f], edz);
+  }
 }
 
 // The 4 corner values (a + 2b) of summed face modes: inverse y, then x stage.
-__device__ __forceinline__ void face_inverse(const float (&M)[3][4], float (&S)[3][4]) {
+__device__ __forceinline__ void face_inverse(const ColFace& M, ColFace& S) {
+  {
+    const float2 a0 = sub2(M.xy[0], M.xy[2]), a2 = add2(M.xy[0], M.xy[2]);
+    const float2 a1 = sub2(M.xy[1], M.xy[3]), a3 = add2(M.xy[1], M.xy[3]);
+    S.xy[0] = sub2(a0, a1);
+    S.xy[1] = add2(a0, a1);
+    S.xy[2] = sub2(a2, a3);
+    S.xy[3] = add2(a2, a3);
+  }
+  const float a0 = M.z[0] - M.z[2], a2 = M.z[0] + M.z[2];
+  const float a1 = M.z[1] - M.z[3], a3 = M.z[1] + M.z[3];
+  S.z[0] = a0 - a1;
+  S.z[1] = a0 + a1;
+  S.z[2] = a2 - a3;
+  S.z[3] = a2 + a3;
+}
+
+// Sum of two faces (the upper face of one element and the lower face of the next).
+__device__ __forceinline__ void face_add(const ColFace& a, const ColFace& b, ColFace& s) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float a0 = M[c][0] - M[c][2], a2 = M[c][0] + M[c][2];
-    const float a1 = M[c][1] - M[c][3], a3 = M[c][1] + M[c][3];
-    S[c][0] = a0 - a1;
-    S[c][1] = a0 + a1;
-    S[c][2] = a2 - a3;
-    S[c][3] = a2 + a3;
+  for (int f = 0; f < 4; ++f) {
+    s.xy[f] = add2(a.xy[f], b.xy[f]);
+    s.z[f] = a.z[f] + b.z[f];
+  }
+}
+
+// The 12 corner sums of one column into the shared rows Sm[(4 c + a) MFTO_BLOCK + tid].
+__device__ __forceinline__ void face_store(const ColFace& S, float* Sm, int tid) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    Sm[a * MFTO_BLOCK + tid] = S.xy[a].x;
+    Sm[(4 + a) * MFTO_BLOCK + tid] = S.xy[a].y;
+    Sm[(8 + a) * MFTO_BLOCK + tid] = S.z[a];
+  }
+}
+
+// Owner's sum of one node from the corner sums of the 4 columns around it, in
+// the fixed order: columns (ex-1, ey-1), (ex, ey-1), (ex-1, ey), (ex, ey)
+// contribute their corners 3, 2, 1, 0.
+__device__ __forceinline__ void node_sum(const float* Sm, int tid, float (&acc)[3]) {
+  constexpr int B = MFTO_BLOCK, CX = ColShape::CX;
+  auto pair = [&](int a, int i) { return make_float2(Sm[a * B + i], Sm[(4 + a) * B + i]); };
+  float2 s = pair(3, tid - CX - 1);
+  s = add2(s, pair(2, tid - CX));
+  s = add2(s, pair(1, tid - 1));
+  s = add2(s, pair(0, tid));
+  float sz = Sm[(8 + 3) * B + tid - CX - 1];
+  sz += Sm[(8 + 2) * B + tid - CX];
+  sz += Sm[(8 + 1) * B + tid - 1];
+  sz += Sm[(8 + 0) * B + tid];
+  acc[0] = s.x;
+  acc[1] = s.y;
+  acc[2] = sz;
+}
+
+__device__ __forceinline__ void face_zero(ColFace& F) {
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    F.xy[f] = make_float2(0.f, 0.f);
+    F.z[f] = 0.f;
   }
 }
 // Tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of `tl`.  Returns this
@@ -412,12 +507,9 @@ __device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ 
     __syncthreads();
     // face modes and upper-face outputs ping-pong between two register sets
     // (the z loop is unrolled by two, so nothing is copied between layers)
-    float F0[3][4], F1[3][4], U0[3][4], U1[3][4];
+    ColFace F0, F1, U0, U1;
     face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, ey * S::NX + ex, F0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int f = 0; f < 4; ++f) U0[c][f] = 0.f;
+    face_zero(U0);
     ColNode mine = own;          // this column's node of layer ez + 1 (after staging)
     ColNode mine_cur = own;      // of layer ez
     ColNode mine_prev = own;     // of layer ez - 1 (finished in iteration ez)
@@ -426,24 +518,15 @@ __device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ 
     // corners 3, 2, 1, 0
     auto finish = [&](int k, const ColNode& nv) {
       if (own_node) {
-        const float* Sm = sums + (k & 1) * 12 * MFTO_BLOCK;
         float acc[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          float sacc = Sm[(4 * q + 3) * MFTO_BLOCK + tid - S::CX - 1];
-          sacc += Sm[(4 * q + 2) * MFTO_BLOCK + tid - S::CX];
-          sacc += Sm[(4 * q + 1) * MFTO_BLOCK + tid - 1];
-          sacc += Sm[(4 * q + 0) * MFTO_BLOCK + tid];
-          acc[q] = sacc;
-        }
+        node_sum(sums + (k & 1) * 12 * MFTO_BLOCK, tid, acc);
         epi(gi + g.nx * (gj + g.ny * k), acc, nv.v, nv.fm, red);
       }
     };
     // one element layer: Flo = face modes of node layer ez (in), Fup = those of
     // ez + 1 (out), upp = upper-face outputs of element ez - 1 (in), up = those
     // of element ez (out)
-    auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
-                     const float (&upp)[3][4], float (&up)[3][4]) {
+    auto layer = [&](int ez, const ColFace& Flo, ColFace& Fup, const ColFace& upp, ColFace& up) {
       // stage node layer ez + 1; fetch layer ez + 2 and the next modulus
       stage(ez + 1, own, extra);
       mine_prev = mine_cur;
@@ -459,22 +542,15 @@ __device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ 
       // node layer ez - 1 (its corner sums were written in iteration ez - 1)
       if (ez - 1 >= kb) finish(ez - 1, mine_prev);
       // upper face modes, element operator
-      float lo[3][4];
+      ColFace lo;
       face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, ey * S::NX + ex, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
       if (ez >= kb) {
         // node layer ez: upper face of element ez - 1 plus lower face of ez
-        float Ms[3][4], Sc[3][4];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) Ms[c][f] = upp[c][f] + lo[c][f];
+        ColFace Ms, Sc;
+        face_add(upp, lo, Ms);
         face_inverse(Ms, Sc);
-        float* Sm = sums + (ez & 1) * 12 * MFTO_BLOCK;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int a = 0; a < 4; ++a) Sm[(4 * c + a) * MFTO_BLOCK + tid] = Sc[c][a];
+        face_store(Sc, sums + (ez & 1) * 12 * MFTO_BLOCK, tid);
       }
     };
     for (int ez = kb - 1; ez < ke; ez += 2) {
@@ -696,33 +772,21 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     ColNode mine = stage(kb - 1, rp);
     int rs = next_slot(rp);
     __syncthreads();
-    float F0[3][4], F1[3][4], U0[3][4], U1[3][4];
+    ColFace F0, F1, U0, U1;
     face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, own_slot, F0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int f = 0; f < 4; ++f) U0[k][f] = 0.f;
+    face_zero(U0);
     ColNode mine_cur = mine, mine_prev = mine;
     // owner's sum of node layer k from the corner sums in slot k & 1:
     // columns (ex-1, ey-1), (ex, ey-1), (ex-1, ey), (ex, ey) contribute their
     // corners 3, 2, 1, 0
     auto finish = [&](int k, const ColNode& nv) {
       if (own_node) {
-        const float* Sm = sums + (k & 1) * 12 * MFTO_BLOCK;
         float acc[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          float sacc = Sm[(4 * q + 3) * MFTO_BLOCK + tid - S::CX - 1];
-          sacc += Sm[(4 * q + 2) * MFTO_BLOCK + tid - S::CX];
-          sacc += Sm[(4 * q + 1) * MFTO_BLOCK + tid - 1];
-          sacc += Sm[(4 * q + 0) * MFTO_BLOCK + tid];
-          acc[q] = sacc;
-        }
+        node_sum(sums + (k & 1) * 12 * MFTO_BLOCK, tid, acc);
         epi(c.own_base + nxy * k, acc, nv.v, CLEAN ? (uint8_t)0 : nv.fm, red);
       }
     };
-    auto layer = [&](int ez, const float (&Flo)[3][4], float (&Fup)[3][4],
-                     const float (&upp)[3][4], float (&up)[3][4]) {
+    auto layer = [&](int ez, const ColFace& Flo, ColFace& Fup, const ColFace& upp, ColFace& up) {
       // node layer ez + 1 has landed: stage it, then request layer
       // ez + 1 + kColPrefetch into the ring slot layer ez used
       col_cp_wait<kColPrefetch - 1>();
@@ -737,22 +801,15 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       __syncthreads();
       // node layer ez - 1 (its corner sums were written in iteration ez - 1)
       if (ez - 1 >= kb) finish(ez - 1, mine_prev);
-      float lo[3][4];
+      ColFace lo;
       face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, own_slot, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
       if (ez >= kb) {
         // node layer ez: upper face of element ez - 1 plus lower face of ez
-        float Ms[3][4], Sc[3][4];
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) Ms[k][f] = upp[k][f] + lo[k][f];
+        ColFace Ms, Sc;
+        face_add(upp, lo, Ms);
         face_inverse(Ms, Sc);
-        float* Sm = sums + (ez & 1) * 12 * MFTO_BLOCK;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int a = 0; a < 4; ++a) Sm[(4 * k + a) * MFTO_BLOCK + tid] = Sc[k][a];
+        face_store(Sc, sums + (ez & 1) * 12 * MFTO_BLOCK, tid);
       }
     };
     for (int ez = kb - 1; ez < ke; ez += 2) {

@@ -4,7 +4,8 @@
   686,433 DOFs) exactly as the benchmark runs it: FP64 iterative refinement
   around the FP32 inner Jacobi-PCG continuing its direction across
   refinement steps (inner tolerance 0.1, rtol 1e-8), the column K.v launch
-  shape picked by the autotuner, the CUDA-graph CG engine.  Three steps from
+  shape picked by the autotuner, with the benchmark's ticket-free CUDA-graph
+  CG engine (2) and with the last-block-ticket engine (0).  Three steps from
   the uniform start; each is recomputed by the oracle from the GPU's input
   design and the GPU's displacement (Sec. 3.1, 3.6): physical density (cone
   filter), true FP64 residual of the solve, compliance as the sum of element
@@ -30,7 +31,8 @@ TC_TOL = {"tf32": 1e-3, "f16": 1e-3, "bf16": 1e-2, "tf32x3": 2e-6, "f16x3": 2e-6
           "bf16x3": 2e-5}
 
 
-def test_benchmarked_simp_steps_match_oracle(cuda):
+@pytest.mark.parametrize("engine", [0, 2])
+def test_benchmarked_simp_steps_match_oracle(cuda, engine):
     import torch
     from paper_2604_18020_gb300 import mfto
     P = W.WORKLOADS["cantilever_120x60x30"]()
@@ -41,7 +43,7 @@ def test_benchmarked_simp_steps_match_oracle(cuda):
     params = mfto.default_params(volfrac=P.volfrac, rmin=P.rmin, rtol=1e-8)
     with mfto.Handle(m.nelx, m.nely, m.nelz, P.fixed, params=params) as h:
         h.set_solver(mfto.FORM_F32, 1e-1)
-        h.set_cg_engine(0)
+        h.set_cg_engine(engine)
         h.set_ir_mode(mfto.IR_CONTINUE)
         h.kv_autotune()
         rho = torch.full((m.n_elem,), P.volfrac, dtype=torch.float64, device=cuda)
