@@ -29,10 +29,28 @@
 
 namespace {
 
+// Thread 0's sum of the 8 warps' double-float values of K rows, as a
+// balanced tree ((w0 + w1) + (w2 + w3)) + ((w4 + w5) + (w6 + w7)): the same
+// fixed order in every block, three dependent additions instead of eight.
+static_assert(MFTO_BLOCK / 32 == 8, "warp tree over 8 warps");
+template <int K>
+__device__ __forceinline__ void warp_tree8(const float2 (&sh)[K][MFTO_BLOCK / 32], DFloat (&t)[K]) {
+  DFloat a[K][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int c = 0; c < K; ++c)
+      a[c][i] = df_add(DFloat{sh[c][2 * i].x, sh[c][2 * i].y},
+                       DFloat{sh[c][2 * i + 1].x, sh[c][2 * i + 1].y});
+#pragma unroll
+  for (int c = 0; c < K; ++c) t[c] = df_add(df_add(a[c][0], a[c][1]), df_add(a[c][2], a[c][3]));
+}
+
 // Sums of K rows of double-float partials pf[c * MFTO_RED_SLOTS + b], b < nb,
-// in a fixed order: threads stride the blocks, then a warp tree, then the
-// warps in order.  partials_load issues a thread's first kPartAhead loads
-// (so that they can go out before other memory traffic of the launch);
+// in a fixed order: threads stride the blocks, then a shuffle tree in each
+// warp, then a balanced tree over the warps (warp_tree8).  partials_load
+// issues a thread's first kPartAhead loads (so that they can go out before
+// other memory traffic of the launch);
 // partials_sum adds them and any further strides.  Thread 0 gets the FP64
 // totals (the same bits in every block); the other threads get 0.  FP64
 // instructions stay in one thread: the FP64 pipe issues a warp instruction
@@ -97,15 +115,8 @@ __device__ __forceinline__ void partials_sum(const PartialLoads<K>& L, const flo
 #pragma unroll
   for (int c = 0; c < K; ++c) out[c] = 0.0;
   if (threadIdx.x == 0) {
-    // the rows' sums over the warps in order, interleaved (launches use
-    // MFTO_BLOCK threads)
     DFloat t2[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) t2[c] = DFloat{0.f, 0.f};
-#pragma unroll
-    for (int w = 0; w < MFTO_BLOCK / 32; ++w)
-#pragma unroll
-      for (int c = 0; c < K; ++c) t2[c] = df_add(t2[c], DFloat{sh[c][w].x, sh[c][w].y});
+    warp_tree8<K>(sh, t2);
 #pragma unroll
     for (int c = 0; c < K; ++c) out[c] = (double)t2[c].hi + (double)t2[c].lo;
   }
@@ -124,15 +135,8 @@ __device__ __forceinline__ void publish_block_df(const DFloat (&v)[K], float2* p
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    // the rows' sums over the warps in order, interleaved (launches use
-    // MFTO_BLOCK threads)
     DFloat t2[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) t2[c] = DFloat{0.f, 0.f};
-#pragma unroll
-    for (int w = 0; w < MFTO_BLOCK / 32; ++w)
-#pragma unroll
-      for (int c = 0; c < K; ++c) t2[c] = df_add(t2[c], DFloat{sh[c][w].x, sh[c][w].y});
+    warp_tree8<K>(sh, t2);
 #pragma unroll
     for (int c = 0; c < K; ++c)
       pf[c * MFTO_RED_SLOTS + blockIdx.x] = make_float2(t2[c].hi, t2[c].lo);
@@ -301,32 +305,35 @@ cg2_update_kernel(float* __restrict__ u, const float* __restrict__ p, const floa
   }
   double tot[1];
   partials_sum<1>(pl, pa, nb_a, tot);
+  // the block's alpha goes out first; block 0 records the FP64 scalars
+  // (alpha, the reciprocal of r.z for the next beta) after the broadcast,
+  // off the other threads' path
+  const bool was_done = done != 0;
+  const double pq = tot[0];
+  double alpha64 = 0.0;
   if (lead) {
-    double alpha = 0.0;
     if (!done) {
-      const double pq = tot[0];
-      if (!(pq > 0.0) || !isfinite(pq)) {
+      if (!(pq > 0.0) || !isfinite(pq))
         done = 1;
-        if (blockIdx.x == 0) {
-          s->pq = pq;
-          s->alpha = 0.0;
-          s->status = MFTO_BREAKDOWN;
-          s->done = 1;
-        }
-      } else {
-        alpha = rz / pq;
-        if (blockIdx.x == 0) {
-          s->pq = pq;
-          s->alpha = alpha;
-          s->it = it + 1;
-          s->rinv2[par] = 1.0 / rz;   // for the next beta
-        }
-      }
+      else
+        alpha64 = rz / pq;
     }
     s_skip = done;
-    s_alpha = (float)alpha;
+    s_alpha = (float)alpha64;
   }
   __syncthreads();
+  if (lead && blockIdx.x == 0 && !was_done) {
+    s->pq = pq;
+    if (done) {
+      s->alpha = 0.0;
+      s->status = MFTO_BREAKDOWN;
+      s->done = 1;
+    } else {
+      s->alpha = alpha64;
+      s->it = it + 1;
+      s->rinv2[par] = 1.0 / rz;   // for the next beta
+    }
+  }
   if (s_skip) return;
   const float alpha = s_alpha;
   DotAcc<float> d0, d1;
