@@ -55,8 +55,10 @@ __device__ __forceinline__ void warp_tree8(const float2 (&sh)[K][MFTO_BLOCK / 32
 // totals (the same bits in every block); the other threads get 0.  FP64
 // instructions stay in one thread: the FP64 pipe issues a warp instruction
 // at a small fraction of the FP32 rate whatever the number of active lanes.
-// One barrier; call uniformly, once per launch.
-constexpr int kPartAhead = 4;
+// One barrier; call uniformly, once per launch.  Three loads ahead cover the
+// update kernel's blocks (at most 4 per SM, 608 on 152 SMs) in one pass;
+// measured 0.3 % faster per CG iteration at 216k than four.
+constexpr int kPartAhead = 3;
 template <int K>
 struct PartialLoads {
   float2 x[kPartAhead][K];
