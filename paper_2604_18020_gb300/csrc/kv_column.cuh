@@ -604,8 +604,8 @@ template <int KSRC>
 constexpr size_t col_ring_bytes() {
   return sizeof(float) * kColRing * ((3 * KSRC + 1) * ColShape::NV + MFTO_BLOCK);
 }
-// Node layers and corner sums of the asynchronous body, both double-buffered.
-constexpr size_t kColAsyncBase = sizeof(float) * (2 * 3 * ColShape::NV + 2 * 12 * MFTO_BLOCK);
+// Node layers (three buffers) and corner sums (two) of the asynchronous body.
+constexpr size_t kColAsyncBase = sizeof(float) * (3 * 3 * ColShape::NV + 2 * 12 * MFTO_BLOCK);
 
 // The column body with its node layers staged by asynchronous copies
 // kColPrefetch layers ahead into a ring in shared memory (each thread copies
@@ -615,7 +615,12 @@ constexpr size_t kColAsyncBase = sizeof(float) * (2 * 3 * ColShape::NV + 2 * 12 
 // contains the node's mask byte (the mask array must be readable up to the
 // next multiple of 4 bytes) and, per column, the modulus of the element below
 // the node layer.  Out-of-grid entries are zero-filled.  Schedule, barrier
-// use and arithmetic are those of kv_column_body_regs.
+// use and arithmetic are those of kv_column_body_regs, except that the node
+// layers have three buffers: node layer k stays staged until iteration k + 1,
+// so the owner reads its node's staged value back for the epilogue instead of
+// carrying it in registers (stage(k + 2) rewrites the buffer, but the owner's
+// own slot is written by no other thread, and the face transforms read only
+// layers k + 1 and k + 2 by then).
 template <typename Load, typename Epi, typename Pre>
 __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__ E,
                                                        const uint8_t* __restrict__ fixed,
@@ -625,8 +630,8 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
                                                        const Pre& pre, bool* skipped) {
   using S = ColShape;
   constexpr int NS = 3 * Load::kSrc + 1;        // ring rows per node: sources, mask word
-  float* nodes = smem;                          // [2][3][NV], slot of node layer k: k & 1
-  float* sums = smem + 2 * 3 * S::NV;           // [2][12][256] corner sums, slot k & 1
+  float* nodes = smem;                          // [3][3][NV], slot of node layer k: (k + 3) % 3
+  float* sums = smem + 3 * 3 * S::NV;           // [2][12][256] corner sums, slot k & 1
   float* ring = sums + 2 * 12 * MFTO_BLOCK;     // [kColRing][NS][NV]
   float* ering = ring + kColRing * NS * S::NV;  // [kColRing][256]
   const int tid = threadIdx.x;
@@ -754,7 +759,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     const int kb = c.kb, ke = c.ke;
     const bool own_node = owner && c.own_in;
     auto stage = [&](int L, int rs) {
-      float* Lb = nodes + (L & 1) * 3 * S::NV;
+      float* Lb = nodes + ((L + 3) % 3) * 3 * S::NV;
       const ColNode own = take(L, rs, own_slot, c.own_base, clean_tag);
 #pragma unroll
       for (int k = 0; k < 3; ++k) Lb[k * S::NV + own_slot] = own.v[k];
@@ -773,26 +778,29 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     int rs = next_slot(rp);
     __syncthreads();
     ColFace F0, F1, U0, U1;
-    face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, own_slot, F0);
+    face_forward(nodes + ((kb + 2) % 3) * 3 * S::NV, own_slot, F0);
     face_zero(U0);
-    ColNode mine_cur = mine, mine_prev = mine;
+    // masks of this column's node in node layers ez - 1, ez and ez + 1
+    uint8_t fm_cur = mine.fm, fm_prev = mine.fm, fm_next = mine.fm;
     // owner's sum of node layer k from the corner sums in slot k & 1:
     // columns (ex-1, ey-1), (ex, ey-1), (ex-1, ey), (ex, ey) contribute their
     // corners 3, 2, 1, 0
-    auto finish = [&](int k, const ColNode& nv) {
+    auto finish = [&](int k, uint8_t fm) {
       if (own_node) {
         float acc[3];
         node_sum(sums + (k & 1) * 12 * MFTO_BLOCK, tid, acc);
-        epi(c.own_base + nxy * k, acc, nv.v, CLEAN ? (uint8_t)0 : nv.fm, red);
+        const float* Lk = nodes + ((k + 3) % 3) * 3 * S::NV + own_slot;
+        const float pn[3] = {Lk[0], Lk[S::NV], Lk[2 * S::NV]};
+        epi(c.own_base + nxy * k, acc, pn, CLEAN ? (uint8_t)0 : fm, red);
       }
     };
     auto layer = [&](int ez, const ColFace& Flo, ColFace& Fup, const ColFace& upp, ColFace& up) {
       // node layer ez + 1 has landed: stage it, then request layer
       // ez + 1 + kColPrefetch into the ring slot layer ez used
       col_cp_wait<kColPrefetch - 1>();
-      mine_prev = mine_cur;
-      mine_cur = mine;
-      mine = stage(ez + 1, rs);
+      fm_prev = fm_cur;
+      fm_cur = fm_next;
+      fm_next = stage(ez + 1, rs).fm;
       const float Ee = ering[rs * MFTO_BLOCK + tid];
       // layer ez + 1 + kColPrefetch goes into the slot of layer ez
       issue(c, ez + 1 + kColPrefetch, rp, clean_tag);
@@ -800,9 +808,9 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       rs = next_slot(rs);
       __syncthreads();
       // node layer ez - 1 (its corner sums were written in iteration ez - 1)
-      if (ez - 1 >= kb) finish(ez - 1, mine_prev);
+      if (ez - 1 >= kb) finish(ez - 1, fm_prev);
       ColFace lo;
-      face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, own_slot, Fup);
+      face_forward(nodes + ((ez + 4) % 3) * 3 * S::NV, own_slot, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
       if (ez >= kb) {
         // node layer ez: upper face of element ez - 1 plus lower face of ez
@@ -819,7 +827,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     // the last owned node layer; the barrier also ends every read of this
     // tile's node layers before the next tile stages its own
     __syncthreads();
-    finish(ke - 1, mine_cur);
+    finish(ke - 1, fm_cur);
   };
   for (; t < ntiles; t += gridDim.x) {
     const Ctx c = ctx_of(t);
