@@ -66,8 +66,8 @@ KERNEL_SOURCES = {
     "pcg_kv_tile_kernel<double>": ["kv_tile.cuh", "kv_tile.cu", "modes.cuh"],
 }
 NCU_DRAM_BYTES = {
-    ("cg2_kv_kernel<2>", WORKLOAD): (6.647808e6, "a78892ee4e69"),
-    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (143.298560e6 + 74.955264e6, "a78892ee4e69"),
+    ("cg2_kv_kernel<2>", WORKLOAD): (6.647808e6, "f61032797fc2"),
+    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (143.275264e6 + 75.502592e6, "f61032797fc2"),
     ("pcg_kv_tile_kernel<double>", WORKLOAD): ((293.127936e6 + 199.873024e6) * 216000 / 4915200,
                                                "6e176c6f4f1e"),
 }
