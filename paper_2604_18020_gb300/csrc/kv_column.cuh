@@ -11,8 +11,9 @@
 //
 // Per element layer ez a thread
 //   1. stages its own node of layer ez+1 (threads 0..40 also the tile's
-//      last node row / column) into a double-buffered shared layer, with the
-//      fixed DOFs zeroed.  The node layers come from a ring in shared memory
+//      last node row / column) into a shared node layer (the x/y pair as one
+//      8-byte word, then z; two buffers, three in kv_column_body_async), with
+//      the fixed DOFs zeroed.  The node layers come from a ring in shared memory
 //      filled by asynchronous copies two layers ahead (kv_column_body_async;
 //      loaders that must read L2 directly stage one layer ahead through
 //      registers instead, kv_column_body_regs);
@@ -25,7 +26,8 @@
 //      stage with the modulus folded in: lower = E (s - d), upper = E (s + d);
 //   5. adds its lower-face output to the upper-face output of the element
 //      below (still in mode space), undoes the y and x stages once per node
-//      layer, and publishes the 4 corner sums of the column (12 values);
+//      layer, and publishes the 4 corner sums of the column (12 values: four
+//      x/y pairs as 8-byte words, four z);
 //   6. one layer later (step 2), the owner of node (ex, ey) sums the 4
 //      columns around the node in a fixed order and hands the result to the
 //      epilogue.
@@ -43,9 +45,12 @@ struct ColShape {
   static constexpr int CX = 32, CY = 8;            // element columns of a CTA
   static constexpr int NX = CX + 1, NY = CY + 1;   // node tile of one layer
   static constexpr int NV = NX * NY;               // 297 staged nodes
+  // a staged node layer: the x/y pairs of its NV nodes (float2), then their z;
+  // layers LS floats apart (even, so that every pair is 8-byte aligned)
+  static constexpr int LS = 3 * NV + 1;
   static constexpr int OX = CX - 1, OY = CY - 1;   // owned nodes per layer: 31 x 7
   static constexpr int NEXTRA = NV - CX * CY;      // 41 nodes staged by a second thread
-  static constexpr size_t smem_bytes = sizeof(float) * (2 * 3 * NV + 2 * 12 * CX * CY);
+  static constexpr size_t smem_bytes = sizeof(float) * (2 * LS + 2 * 12 * CX * CY);
 };
 static_assert(ColShape::CX * ColShape::CY == MFTO_BLOCK, "one column per thread");
 static_assert(ColShape::NEXTRA <= MFTO_BLOCK, "extra nodes fit one pass");
@@ -292,12 +297,10 @@ struct ColFace {
 // face modes (x then y stage) of the 4 corners (a + 2b) of one face, per component
 __device__ __forceinline__ void face_forward(const float* __restrict__ layer, int base,
                                              ColFace& F) {
-  const float* Lx = layer + base;
-  const float* Ly = Lx + ColShape::NV;
-  const float* Lz = Ly + ColShape::NV;
+  const float2* Lxy = reinterpret_cast<const float2*>(layer) + base;
+  const float* Lz = layer + 2 * ColShape::NV + base;
   constexpr int NX = ColShape::NX;
-  const float2 c0 = make_float2(Lx[0], Ly[0]), c1 = make_float2(Lx[1], Ly[1]);
-  const float2 c2 = make_float2(Lx[NX], Ly[NX]), c3 = make_float2(Lx[NX + 1], Ly[NX + 1]);
+  const float2 c0 = Lxy[0], c1 = Lxy[1], c2 = Lxy[NX], c3 = Lxy[NX + 1];
   const float2 m0 = add2(c0, c1), m1 = sub2(c1, c0), m2 = add2(c2, c3), m3 = sub2(c3, c2);
   F.xy[0] = add2(m0, m2);
   F.xy[2] = sub2(m2, m0);
@@ -390,12 +393,14 @@ __device__ __forceinline__ void face_add(const ColFace& a, const ColFace& b, Col
   }
 }
 
-// The 12 corner sums of one column into the shared rows Sm[(4 c + a) MFTO_BLOCK + tid].
+// The 12 corner sums of one column into shared memory: the x/y pairs of
+// corner a at Sm2[a MFTO_BLOCK + tid] (Sm2 = Sm as float2, 8-byte aligned),
+// z at Sm[(8 + a) MFTO_BLOCK + tid].
 __device__ __forceinline__ void face_store(const ColFace& S, float* Sm, int tid) {
+  float2* Sm2 = reinterpret_cast<float2*>(Sm);
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    Sm[a * MFTO_BLOCK + tid] = S.xy[a].x;
-    Sm[(4 + a) * MFTO_BLOCK + tid] = S.xy[a].y;
+    Sm2[a * MFTO_BLOCK + tid] = S.xy[a];
     Sm[(8 + a) * MFTO_BLOCK + tid] = S.z[a];
   }
 }
@@ -405,7 +410,8 @@ __device__ __forceinline__ void face_store(const ColFace& S, float* Sm, int tid)
 // contribute their corners 3, 2, 1, 0.
 __device__ __forceinline__ void node_sum(const float* Sm, int tid, float (&acc)[3]) {
   constexpr int B = MFTO_BLOCK, CX = ColShape::CX;
-  auto pair = [&](int a, int i) { return make_float2(Sm[a * B + i], Sm[(4 + a) * B + i]); };
+  const float2* Sm2 = reinterpret_cast<const float2*>(Sm);
+  auto pair = [&](int a, int i) { return Sm2[a * B + i]; };
   float2 s = pair(3, tid - CX - 1);
   s = add2(s, pair(2, tid - CX));
   s = add2(s, pair(1, tid - 1));
@@ -417,6 +423,12 @@ __device__ __forceinline__ void node_sum(const float* Sm, int tid, float (&acc)[
   acc[0] = s.x;
   acc[1] = s.y;
   acc[2] = sz;
+}
+
+// One staged node's 3 values into a node layer (x/y pair, then z).
+__device__ __forceinline__ void col_put_node(float* layer, int slot, const float (&v)[3]) {
+  reinterpret_cast<float2*>(layer)[slot] = make_float2(v[0], v[1]);
+  layer[2 * ColShape::NV + slot] = v[2];
 }
 
 __device__ __forceinline__ void face_zero(ColFace& F) {
@@ -446,8 +458,8 @@ __device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ 
                                                       const Epi& epi, float* smem,
                                                       const Pre& pre, bool* skipped) {
   using S = ColShape;
-  float* nodes = smem;                          // [2][3][NV], slot of node layer k: k & 1
-  float* sums = smem + 2 * 3 * S::NV;           // [2][12][256] corner sums, slot k & 1
+  float* nodes = smem;                          // [2][LS], slot of node layer k: k & 1
+  float* sums = smem + 2 * S::LS;               // [2][12][256] corner sums, slot k & 1
   const int tid = threadIdx.x;
   const int ex = tid % S::CX, ey = tid / S::CX;
   // second staged node of threads < NEXTRA: the top row (y = CY), then the
@@ -470,13 +482,9 @@ __device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ 
     const int hi = x0 + xx, hj = y0 + xy;                  // the extra node
     const bool own_node = owner && gi < g.nx && gj < g.ny;
     auto stage = [&](int k, const ColNode& own, const ColNode& extra) {
-      float* L = nodes + (k & 1) * 3 * S::NV;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) L[c * S::NV + ey * S::NX + ex] = own.v[c];
-      if (has_extra) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) L[c * S::NV + xy * S::NX + xx] = extra.v[c];
-      }
+      float* L = nodes + (k & 1) * S::LS;
+      col_put_node(L, ey * S::NX + ex, own.v);
+      if (has_extra) col_put_node(L, xy * S::NX + xx, extra.v);
     };
     // prologue: node layers kb - 1 and kb requested together (raw), then the
     // pre-step, then layer kb - 1 staged
@@ -508,7 +516,7 @@ __device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ 
     // face modes and upper-face outputs ping-pong between two register sets
     // (the z loop is unrolled by two, so nothing is copied between layers)
     ColFace F0, F1, U0, U1;
-    face_forward(nodes + ((kb - 1) & 1) * 3 * S::NV, ey * S::NX + ex, F0);
+    face_forward(nodes + ((kb - 1) & 1) * S::LS, ey * S::NX + ex, F0);
     face_zero(U0);
     ColNode mine = own;          // this column's node of layer ez + 1 (after staging)
     ColNode mine_cur = own;      // of layer ez
@@ -543,7 +551,7 @@ __device__ __forceinline__ DFloat kv_column_body_regs(const float* __restrict__ 
       if (ez - 1 >= kb) finish(ez - 1, mine_prev);
       // upper face modes, element operator
       ColFace lo;
-      face_forward(nodes + ((ez + 1) & 1) * 3 * S::NV, ey * S::NX + ex, Fup);
+      face_forward(nodes + ((ez + 1) & 1) * S::LS, ey * S::NX + ex, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
       if (ez >= kb) {
         // node layer ez: upper face of element ez - 1 plus lower face of ez
@@ -604,8 +612,12 @@ template <int KSRC>
 constexpr size_t col_ring_bytes() {
   return sizeof(float) * kColRing * ((3 * KSRC + 1) * ColShape::NV + MFTO_BLOCK);
 }
-// Node layers (three buffers) and corner sums (two) of the asynchronous body.
-constexpr size_t kColAsyncBase = sizeof(float) * (3 * 3 * ColShape::NV + 2 * 12 * MFTO_BLOCK);
+// Node layers (three buffers of ColShape::LS floats) and corner sums (two) of
+// the asynchronous body.
+// (three node buffers, padded to an even float count: the corner sums are
+// read and written as 8-byte pairs)
+constexpr int kColNodeFloats = 3 * ColShape::LS;
+constexpr size_t kColAsyncBase = sizeof(float) * (kColNodeFloats + 2 * 12 * MFTO_BLOCK);
 
 // The column body with its node layers staged by asynchronous copies
 // kColPrefetch layers ahead into a ring in shared memory (each thread copies
@@ -630,8 +642,8 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
                                                        const Pre& pre, bool* skipped) {
   using S = ColShape;
   constexpr int NS = 3 * Load::kSrc + 1;        // ring rows per node: sources, mask word
-  float* nodes = smem;                          // [3][3][NV], slot of node layer k: (k + 3) % 3
-  float* sums = smem + 3 * 3 * S::NV;           // [2][12][256] corner sums, slot k & 1
+  float* nodes = smem;                          // [3][LS], slot of node layer k: (k + 3) % 3
+  float* sums = smem + kColNodeFloats;          // [2][12][256] corner sums, slot k & 1
   float* ring = sums + 2 * 12 * MFTO_BLOCK;     // [kColRing][NS][NV]
   float* ering = ring + kColRing * NS * S::NV;  // [kColRing][256]
   const int tid = threadIdx.x;
@@ -759,14 +771,12 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     const int kb = c.kb, ke = c.ke;
     const bool own_node = owner && c.own_in;
     auto stage = [&](int L, int rs) {
-      float* Lb = nodes + ((L + 3) % 3) * 3 * S::NV;
+      float* Lb = nodes + ((L + 3) % 3) * S::LS;
       const ColNode own = take(L, rs, own_slot, c.own_base, clean_tag);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) Lb[k * S::NV + own_slot] = own.v[k];
+      col_put_node(Lb, own_slot, own.v);
       if (has_extra) {
         const ColNode extra = take(L, rs, extra_slot, c.extra_base, clean_tag);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Lb[k * S::NV + extra_slot] = extra.v[k];
+        col_put_node(Lb, extra_slot, extra.v);
       }
       return own;
     };
@@ -778,7 +788,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
     int rs = next_slot(rp);
     __syncthreads();
     ColFace F0, F1, U0, U1;
-    face_forward(nodes + ((kb + 2) % 3) * 3 * S::NV, own_slot, F0);
+    face_forward(nodes + ((kb + 2) % 3) * S::LS, own_slot, F0);
     face_zero(U0);
     // masks of this column's node in node layers ez - 1, ez and ez + 1
     uint8_t fm_cur = mine.fm, fm_prev = mine.fm, fm_next = mine.fm;
@@ -789,8 +799,9 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       if (own_node) {
         float acc[3];
         node_sum(sums + (k & 1) * 12 * MFTO_BLOCK, tid, acc);
-        const float* Lk = nodes + ((k + 3) % 3) * 3 * S::NV + own_slot;
-        const float pn[3] = {Lk[0], Lk[S::NV], Lk[2 * S::NV]};
+        const float* Lk = nodes + ((k + 3) % 3) * S::LS;
+        const float2 pxy = reinterpret_cast<const float2*>(Lk)[own_slot];
+        const float pn[3] = {pxy.x, pxy.y, Lk[2 * S::NV + own_slot]};
         epi(c.own_base + nxy * k, acc, pn, CLEAN ? (uint8_t)0 : fm, red);
       }
     };
@@ -810,7 +821,7 @@ __device__ __forceinline__ DFloat kv_column_body_async(const float* __restrict__
       // node layer ez - 1 (its corner sums were written in iteration ez - 1)
       if (ez - 1 >= kb) finish(ez - 1, fm_prev);
       ColFace lo;
-      face_forward(nodes + ((ez + 4) % 3) * 3 * S::NV, own_slot, Fup);
+      face_forward(nodes + ((ez + 4) % 3) * S::LS, own_slot, Fup);
       col_element(Flo, Fup, Ee, K, lo, up);
       if (ez >= kb) {
         // node layer ez: upper face of element ez - 1 plus lower face of ez
