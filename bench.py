@@ -66,8 +66,9 @@ KERNEL_SOURCES = {
     "pcg_kv_tile_kernel<double>": ["kv_tile.cuh", "kv_tile.cu", "modes.cuh"],
 }
 NCU_DRAM_BYTES = {
-    ("cg2_kv_kernel<2>", WORKLOAD): (6.647808e6, "f61032797fc2"),
-    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (143.275264e6 + 75.502592e6, "f61032797fc2"),
+    ("cg2_kv_kernel<2>", WORKLOAD): (6.646272e6, "0c045bd0c8e8"),
+    ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (143.325184e6 + 74.990592e6, "0c045bd0c8e8"),
+    ("cg2_kv_kernel<3>", "cantilever_256x128x150"): (144.233472e6 + 74.192384e6, "0c045bd0c8e8"),
     ("pcg_kv_tile_kernel<double>", WORKLOAD): ((293.127936e6 + 199.873024e6) * 216000 / 4915200,
                                                "6e176c6f4f1e"),
 }
