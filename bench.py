@@ -67,6 +67,7 @@ KERNEL_SOURCES = {
 }
 NCU_DRAM_BYTES = {
     ("cg2_kv_kernel<2>", WORKLOAD): (6.646272e6, "0c045bd0c8e8"),
+    ("cg2_kv_kernel<3>", WORKLOAD): (6.649088e6, "0c045bd0c8e8"),
     ("cg2_kv_kernel<2>", "cantilever_256x128x150"): (143.325184e6 + 74.990592e6, "0c045bd0c8e8"),
     ("cg2_kv_kernel<3>", "cantilever_256x128x150"): (144.233472e6 + 74.192384e6, "0c045bd0c8e8"),
     ("pcg_kv_tile_kernel<double>", WORKLOAD): ((293.127936e6 + 199.873024e6) * 216000 / 4915200,
